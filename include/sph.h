@@ -1,0 +1,186 @@
+/*
+ * sph.h -- C ABI of libsph, a GB300 (sm_103a) implementation of the per-step
+ * particle-interaction sweep of the 2D weakly-compressible SPH method for
+ * liquid-jet breakup of Pourabdian, Omidvar & Morad (arXiv 1603.02421).
+ *
+ * One step (Sec. 2-8) is: cell-linked-list neighbour build (Sec. 2-7), two
+ * evaluations of the semi-discrete equations -- colour (Eq. 14), surface
+ * normal (Eqs. 18, 20, 21), curvature (Eq. 23), continuity (Eq. 7), momentum
+ * with Tait pressure, artificial viscosity and CSF surface tension (Eqs. 9,
+ * 10, 24, 25, 26) and repulsive walls (Eq. 29) -- with the predictor-corrector
+ * update in between, the adaptive time step of Eqs. 30-32, and inflow /
+ * outflow of the planar jet.  The breakup length follows the criterion of
+ * Sec. 3-2.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an sph_status; nothing throws across the ABI.
+ *  - Pointer arguments are HOST pointers.  Inputs are copied by the library
+ *    (the caller keeps ownership); outputs are caller-allocated host buffers
+ *    of the stated length.
+ *  - The context owns all device memory it allocates (sph_init) and frees it
+ *    in sph_destroy.  Work is issued on params.cuda_stream (a cudaStream_t,
+ *    or NULL for a stream the library creates).  Calls that return host data
+ *    synchronise that stream.
+ *  - Particle ids: fluid and buffer particles get consecutive ids in the
+ *    order they are added; particles laid by the inflow get the next ids.
+ *    Boundary particles carry no id.  State queries return particles sorted
+ *    by id.
+ *  - On error the function returns a negative status and sph_last_error()
+ *    describes it.  A failed call leaves the particle state as it was,
+ *    except SPH_ERR_NONFINITE / SPH_ERR_SKIN / SPH_ERR_CAPACITY raised during
+ *    a step, after which the state is that of the completed step and should
+ *    be treated as suspect.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_ctx sph_ctx;
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_ARG = -1,        /* invalid argument or parameter                */
+    SPH_ERR_OOM = -2,        /* device allocation failed                     */
+    SPH_ERR_CAPACITY = -3,   /* particle capacity or output buffer too small */
+    SPH_ERR_CUDA = -4,       /* CUDA runtime / launch error                  */
+    SPH_ERR_NONFINITE = -5,  /* NaN / Inf in an acceleration or density rate */
+    SPH_ERR_TIMEOUT = -6,    /* a bounded device loop hit its limit          */
+    SPH_ERR_STATE = -7,      /* call not valid in the current state          */
+    SPH_ERR_SKIN = -8        /* a particle moved more than skin/2 between the
+                                cell build and an evaluation (reduce dt or
+                                raise skin_over_h)                           */
+} sph_status;
+
+typedef enum { SPH_KERNEL_CUBIC = 0, SPH_KERNEL_WENDLAND = 1 } sph_kernel;
+typedef enum { SPH_FP32 = 0, SPH_FP64 = 1 } sph_precision;
+enum { SPH_FLUID = 0, SPH_BOUNDARY = 1, SPH_BUFFER = 2 };
+
+/* Run parameters (all SI or consistently nondimensional). */
+typedef struct {
+    int kernel;            /* sph_kernel: cubic spline Eq. 27, Wendland C2 Eq. 28
+                              (2D unit-integral normalisation 10/(7 pi), 7/(64 pi)) */
+    int precision;         /* sph_precision of the pair sums; positions and time are
+                              always FP64                                           */
+    double dx;             /* initial particle spacing                              */
+    double h_over_dx;      /* h = h_over_dx * dx (the paper uses 1.3, Sec. 2-2)      */
+    double rho0, c0, gamma;/* Tait EOS Eq. 26, B = rho0 c0^2 / gamma                */
+    double alpha;          /* artificial viscosity coefficient, Eq. 10              */
+    double eta2_over_h2;   /* eta^2 / h^2 in Eq. 10 (0.01)                          */
+    double sigma;          /* surface tension coefficient, Eq. 24 (0: CSF off)      */
+    double eps_n_times_h;  /* normal filter eps * h in Eq. 20 (0.01)                */
+    double gx, gy;         /* gravity, Eq. 25                                       */
+    double courant;        /* Cr of Eq. 32 (0.2)                                    */
+    double dt_fixed;       /* > 0: fixed step; 0: adaptive Eqs. 30-32               */
+    double xmin, ymin, xmax, ymax;  /* domain box; fluid leaving it is deleted      */
+    double skin_over_h;    /* cell size = 2h + skin, skin = skin_over_h * h (>= 0.1) */
+    double wall_A_coef;    /* wall force strength A = wall_A_coef * c0^2 / h, Eq. 29 */
+    double wall_h0;        /* still-water depth of the eps(z) factor (0: eps(z) = 1) */
+    double wall_db_over_dx;/* boundary particle spacing db = wall_db_over_dx * dx   */
+    long long capacity;    /* maximum fluid + buffer particles held at once         */
+    long long boundary_capacity; /* maximum boundary particles                      */
+    void *cuda_stream;     /* cudaStream_t to issue work on, or NULL                */
+    int device;            /* CUDA device ordinal                                   */
+} sph_params;
+
+/* Create a context: validates *params, selects the device, allocates all
+ * device buffers for params->capacity particles.  *out receives the
+ * context, or NULL on failure (then sph_last_error(NULL) has the reason). */
+sph_status sph_init(const sph_params *params, sph_ctx **out);
+
+/* Release every device buffer and the library-created stream. NULL is ignored. */
+void sph_destroy(sph_ctx *ctx);
+
+/* Last error message of ctx (or of the last failed sph_init when ctx is NULL). */
+const char *sph_last_error(const sph_ctx *ctx);
+
+/* Append n particles (Sec. 2-2: each carries m, rho, u, r).  Arrays of length
+ * n: x, y (positions), u, v (velocity), rho (density), mass, type (SPH_FLUID,
+ * SPH_BOUNDARY or SPH_BUFFER).  nx, ny are the unit wall normals of boundary
+ * particles (pointing into the fluid, Eq. 29) and may be NULL when no
+ * boundary particle is added.  Fluid and buffer particles must lie inside the
+ * domain box.  Returns SPH_ERR_CAPACITY if a capacity would be exceeded. */
+sph_status sph_add_particles(sph_ctx *ctx, long long n, const double *x, const double *y,
+                             const double *u, const double *v, const double *rho,
+                             const double *mass, const unsigned char *type,
+                             const double *nx, const double *ny);
+
+/* Configure the planar-jet inflow (the paper's tank/nozzle is replaced by an
+ * inflow buffer, Sec. 3-2): `layers` layers of buffer particles at spacing dx
+ * across [y0, y1], laid at x_exit - (j + 0.5) dx (j = 0..layers-1), moving with
+ * u_in(t) = U (1 + amp sin(k U t + phase)), rho = rho0, mass rho0 dx^2.  A
+ * buffer particle becomes fluid when x >= x_exit; a new layer is laid one
+ * spacing upstream whenever the upstream-most layer passes its initial slot.
+ * At most 1024 particles per layer.  May be called once per context. */
+sph_status sph_inflow(sph_ctx *ctx, double x_exit, double y0, double y1, double U,
+                      double amp, double k, double phase, int layers);
+
+/* Advance one time step (Sec. 2-8).  *dt_used (nullable) receives the step
+ * size.  Synchronises the stream. */
+sph_status sph_step(sph_ctx *ctx, double *dt_used);
+
+/* Advance nsteps steps by replaying a CUDA graph of one step.  When
+ * breakup_every > 0, after every breakup_every steps the breakup length
+ * (L/D, see sph_breakup_length) is appended to L_out (capacity
+ * nsteps / breakup_every entries) and *nL receives the count; L_out and nL
+ * may be NULL when breakup_every <= 0. */
+sph_status sph_run(sph_ctx *ctx, long long nsteps, int breakup_every, double D,
+                   double *L_out, long long *nL);
+
+/* Breakup length of the jet (Sec. 3-2): particles closer than 1.5 h are
+ * linked; the jet is the union of connected components holding an inflow
+ * buffer particle; *L_over_D = (max x over the jet - x_exit) / D.  *broken
+ * (nullable) is set to 1 if some fluid particle lies outside the jet.
+ * Requires sph_inflow. */
+sph_status sph_breakup_length(sph_ctx *ctx, double D, double *L_over_D, int *broken);
+
+/* One evaluation of the right-hand sides at the current state, without
+ * advancing it (for inspection and tests).  Afterwards sph_get_state's ax,
+ * ay, drho and sph_get_csf return this evaluation. */
+sph_status sph_evaluate(sph_ctx *ctx);
+
+/* Copy out the fluid + buffer state, sorted by id.  cap = length of every
+ * output array; *n receives the particle count (SPH_ERR_CAPACITY if > cap).
+ * rho is the density; ax, ay, drho the derivatives du/dt (Eq. 25) and
+ * drho/dt (Eq. 7) of the last evaluation at the start of a step (or of
+ * sph_evaluate), zero for particles laid since.  Any output pointer except n
+ * may be NULL. */
+sph_status sph_get_state(sph_ctx *ctx, long long cap, long long *n, double *x, double *y,
+                         double *u, double *v, double *rho, double *mass,
+                         unsigned char *type, unsigned *id, double *ax, double *ay,
+                         double *drho);
+
+/* Replace the fluid + buffer state by n particles with the given ids (e.g.
+ * a checkpoint taken with sph_get_state).  Boundary particles, inflow, time
+ * and step count are kept. */
+sph_status sph_set_state(sph_ctx *ctx, long long n, const double *x, const double *y,
+                         const double *u, const double *v, const double *rho,
+                         const double *mass, const unsigned char *type,
+                         const unsigned *id);
+
+/* CSF intermediates of the last sph_evaluate, sorted by id: colour C (Eq. 14)
+ * and normal n (Eq. 18).  Zero when sigma = 0. */
+sph_status sph_get_csf(sph_ctx *ctx, long long cap, long long *n, unsigned *id,
+                       double *C, double *nx, double *ny);
+
+/* All ordered neighbour pairs (id_a, id_b), a != b, at distance < 2h
+ * (Sec. 2-7), from the cell build at the current state; order unspecified.
+ * *npairs receives the count (SPH_ERR_CAPACITY if > cap). */
+sph_status sph_get_pairs(sph_ctx *ctx, long long cap, unsigned *id_a, unsigned *id_b,
+                         long long *npairs);
+
+/* Simulated time, completed steps, live fluid + buffer particles, and
+ * particles deleted by the outflow so far. */
+sph_status sph_get_time(sph_ctx *ctx, double *t, long long *steps, long long *n_particles,
+                        long long *n_deleted);
+
+/* Number of device kernels one sph_step launches at the current settings. */
+sph_status sph_kernels_per_step(sph_ctx *ctx, int *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

@@ -1,0 +1,322 @@
+"""Python binding of libsph (include/sph.h): argument marshalling only.
+
+Every function below has the name of the C entry point it calls and does no
+computation of its own: all steps of the method run in the CUDA kernels
+behind the C ABI.  There is no fallback: if ``libsph.so`` has not been built
+(``paper_1603_02421_gb300.build.build()``) or no GPU is present, the calls
+raise.
+
+Arrays are numpy arrays on the host; the library copies inputs and fills
+caller-allocated outputs, exactly as the C ABI specifies.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsph.so")
+
+SPH_OK = 0
+STATUS = {0: "SPH_OK", -1: "SPH_ERR_ARG", -2: "SPH_ERR_OOM", -3: "SPH_ERR_CAPACITY",
+          -4: "SPH_ERR_CUDA", -5: "SPH_ERR_NONFINITE", -6: "SPH_ERR_TIMEOUT",
+          -7: "SPH_ERR_STATE", -8: "SPH_ERR_SKIN"}
+FLUID, BOUNDARY, BUFFER = 0, 1, 2
+KERNELS = {"cubic": 0, "wendland": 1}
+PRECISIONS = {"fp32": 0, "fp64": 1}
+
+
+class SphError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class sph_params(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("precision", ctypes.c_int),
+                ("dx", ctypes.c_double), ("h_over_dx", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("c0", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("eta2_over_h2", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("eps_n_times_h", ctypes.c_double),
+                ("gx", ctypes.c_double), ("gy", ctypes.c_double),
+                ("courant", ctypes.c_double), ("dt_fixed", ctypes.c_double),
+                ("xmin", ctypes.c_double), ("ymin", ctypes.c_double),
+                ("xmax", ctypes.c_double), ("ymax", ctypes.c_double),
+                ("skin_over_h", ctypes.c_double), ("wall_A_coef", ctypes.c_double),
+                ("wall_h0", ctypes.c_double), ("wall_db_over_dx", ctypes.c_double),
+                ("capacity", ctypes.c_longlong), ("boundary_capacity", ctypes.c_longlong),
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_U8 = ctypes.POINTER(ctypes.c_ubyte)
+_U32 = ctypes.POINTER(ctypes.c_uint)
+_LL = ctypes.POINTER(ctypes.c_longlong)
+_CTX = ctypes.c_void_p
+
+_SIGS = {
+    "sph_init": ([ctypes.POINTER(sph_params), ctypes.POINTER(_CTX)], ctypes.c_int),
+    "sph_destroy": ([_CTX], None),
+    "sph_last_error": ([_CTX], ctypes.c_char_p),
+    "sph_add_particles": ([_CTX, ctypes.c_longlong, _D, _D, _D, _D, _D, _D, _U8, _D, _D],
+                          ctypes.c_int),
+    "sph_inflow": ([_CTX] + [ctypes.c_double] * 7 + [ctypes.c_int], ctypes.c_int),
+    "sph_step": ([_CTX, _D], ctypes.c_int),
+    "sph_run": ([_CTX, ctypes.c_longlong, ctypes.c_int, ctypes.c_double, _D, _LL],
+                ctypes.c_int),
+    "sph_breakup_length": ([_CTX, ctypes.c_double, _D, ctypes.POINTER(ctypes.c_int)],
+                           ctypes.c_int),
+    "sph_evaluate": ([_CTX], ctypes.c_int),
+    "sph_get_state": ([_CTX, ctypes.c_longlong, _LL, _D, _D, _D, _D, _D, _D, _U8, _U32, _D,
+                       _D, _D], ctypes.c_int),
+    "sph_set_state": ([_CTX, ctypes.c_longlong, _D, _D, _D, _D, _D, _D, _U8, _U32],
+                      ctypes.c_int),
+    "sph_get_csf": ([_CTX, ctypes.c_longlong, _LL, _U32, _D, _D, _D], ctypes.c_int),
+    "sph_get_pairs": ([_CTX, ctypes.c_longlong, _U32, _U32, _LL], ctypes.c_int),
+    "sph_get_time": ([_CTX, _D, _LL, _LL, _LL], ctypes.c_int),
+    "sph_kernels_per_step": ([_CTX, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libsph.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError("libsph.so not built: run paper_1603_02421_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(ctx, st):
+    if st != SPH_OK:
+        raise SphError(st, lib().sph_last_error(ctx).decode(errors="replace"))
+
+
+def _d(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_params(p: dict, capacity=None, boundary_capacity=0, stream=None, device=0):
+    """sph_params from a configuration dict (see workloads.py)."""
+    cap = int(capacity if capacity is not None else p.get("capacity", 0))
+    return sph_params(
+        kernel=KERNELS[p.get("kernel", "wendland")],
+        precision=PRECISIONS[p.get("prec", "fp32")],
+        dx=p["dx"], h_over_dx=p.get("h_over_dx", 1.3), rho0=p.get("rho0", 1000.0),
+        c0=p["c0"], gamma=p.get("gamma", 7.0), alpha=p.get("alpha", 0.0),
+        eta2_over_h2=p.get("eta2_over_h2", 0.01), sigma=p.get("sigma", 0.0),
+        eps_n_times_h=p.get("eps_n_times_h", 0.01), gx=p.get("gx", 0.0),
+        gy=p.get("gy", 0.0), courant=p.get("courant", 0.2), dt_fixed=p.get("dt_fixed", 0.0),
+        xmin=p["xmin"], ymin=p["ymin"], xmax=p["xmax"], ymax=p["ymax"],
+        skin_over_h=p.get("skin_over_h", 0.2), wall_A_coef=p.get("wall_A_coef", 0.01),
+        wall_h0=p.get("wall_h0", 0.0), wall_db_over_dx=p.get("wall_db_over_dx", 0.5),
+        capacity=cap, boundary_capacity=int(boundary_capacity),
+        cuda_stream=stream, device=int(device))
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+def sph_init(params: sph_params):
+    ctx = _CTX()
+    st = lib().sph_init(ctypes.byref(params), ctypes.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def sph_destroy(ctx):
+    lib().sph_destroy(ctx)
+
+
+def sph_add_particles(ctx, x, y, u=None, v=None, rho=None, mass=None, type=None, nx=None,
+                      ny=None):
+    x, y = _f64(x), _f64(y)
+    n = len(x)
+    u, v, rho, mass, nx, ny = (_f64(a) for a in (u, v, rho, mass, nx, ny))
+    t = np.ascontiguousarray(type if type is not None else np.zeros(n), dtype=np.uint8)
+    _check(ctx, lib().sph_add_particles(ctx, n, _d(x), _d(y), _d(u), _d(v), _d(rho), _d(mass),
+                                        t.ctypes.data_as(_U8), _d(nx), _d(ny)))
+
+
+def sph_inflow(ctx, x_exit, y0, y1, U, amp, k, phase, layers):
+    _check(ctx, lib().sph_inflow(ctx, x_exit, y0, y1, U, amp, k, phase, int(layers)))
+
+
+def sph_step(ctx) -> float:
+    dt = ctypes.c_double()
+    _check(ctx, lib().sph_step(ctx, ctypes.byref(dt)))
+    return dt.value
+
+
+def sph_run(ctx, nsteps, breakup_every=0, D=1.0):
+    cnt = nsteps // breakup_every if breakup_every > 0 else 0
+    L = np.zeros(max(cnt, 1))
+    nL = ctypes.c_longlong()
+    _check(ctx, lib().sph_run(ctx, int(nsteps), int(breakup_every), float(D),
+                              _d(L) if breakup_every > 0 else None,
+                              ctypes.byref(nL) if breakup_every > 0 else None))
+    return L[:nL.value]
+
+
+def sph_breakup_length(ctx, D=1.0):
+    L = ctypes.c_double()
+    b = ctypes.c_int()
+    _check(ctx, lib().sph_breakup_length(ctx, float(D), ctypes.byref(L), ctypes.byref(b)))
+    return L.value, bool(b.value)
+
+
+def sph_evaluate(ctx):
+    _check(ctx, lib().sph_evaluate(ctx))
+
+
+def sph_get_state(ctx, cap=None) -> dict:
+    if cap is None:
+        n = ctypes.c_longlong()
+        st = lib().sph_get_state(ctx, 0, ctypes.byref(n), *([None] * 11))
+        if st not in (SPH_OK, -3):
+            _check(ctx, st)
+        cap = n.value
+    out = {k: np.zeros(max(cap, 1)) for k in ("x", "y", "u", "v", "rho", "m", "ax", "ay",
+                                                "drho")}
+    out["type"] = np.zeros(max(cap, 1), np.uint8)
+    out["id"] = np.zeros(max(cap, 1), np.uint32)
+    n = ctypes.c_longlong()
+    _check(ctx, lib().sph_get_state(ctx, cap, ctypes.byref(n), _d(out["x"]), _d(out["y"]),
+                                    _d(out["u"]), _d(out["v"]), _d(out["rho"]), _d(out["m"]),
+                                    out["type"].ctypes.data_as(_U8),
+                                    out["id"].ctypes.data_as(_U32), _d(out["ax"]),
+                                    _d(out["ay"]), _d(out["drho"])))
+    return {k: a[:n.value] for k, a in out.items()}
+
+
+def sph_set_state(ctx, st: dict):
+    x = _f64(st["x"])
+    n = len(x)
+    ids = np.ascontiguousarray(st["id"], dtype=np.uint32)
+    t = np.ascontiguousarray(st["type"], dtype=np.uint8)
+    _check(ctx, lib().sph_set_state(ctx, n, _d(x), _d(_f64(st["y"])), _d(_f64(st["u"])),
+                                    _d(_f64(st["v"])), _d(_f64(st["rho"])),
+                                    _d(_f64(st["m"])), t.ctypes.data_as(_U8),
+                                    ids.ctypes.data_as(_U32)))
+
+
+def sph_get_csf(ctx, cap) -> dict:
+    out = {"C": np.zeros(max(cap, 1)), "nx": np.zeros(max(cap, 1)), "ny": np.zeros(max(cap, 1)),
+           "id": np.zeros(max(cap, 1), np.uint32)}
+    n = ctypes.c_longlong()
+    _check(ctx, lib().sph_get_csf(ctx, cap, ctypes.byref(n), out["id"].ctypes.data_as(_U32),
+                                  _d(out["C"]), _d(out["nx"]), _d(out["ny"])))
+    return {k: a[:n.value] for k, a in out.items()}
+
+
+def sph_get_pairs(ctx, cap):
+    a = np.zeros(max(cap, 1), np.uint32)
+    b = np.zeros(max(cap, 1), np.uint32)
+    n = ctypes.c_longlong()
+    _check(ctx, lib().sph_get_pairs(ctx, cap, a.ctypes.data_as(_U32), b.ctypes.data_as(_U32),
+                                    ctypes.byref(n)))
+    return a[:n.value], b[:n.value]
+
+
+def sph_get_time(ctx):
+    t = ctypes.c_double()
+    s, n, d = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(ctx, lib().sph_get_time(ctx, ctypes.byref(t), ctypes.byref(s), ctypes.byref(n),
+                                   ctypes.byref(d)))
+    return {"t": t.value, "steps": s.value, "n": n.value, "deleted": d.value}
+
+
+def sph_kernels_per_step(ctx) -> int:
+    c = ctypes.c_int()
+    _check(ctx, lib().sph_kernels_per_step(ctx, ctypes.byref(c)))
+    return c.value
+
+
+# ---------------------------------------------------------------------------
+# convenience: a context built from a workload case
+# ---------------------------------------------------------------------------
+class Simulation:
+    """A libsph context for a case dict of ``workloads`` (owns the context)."""
+
+    def __init__(self, case: dict, capacity=None, stream=None, device=0, prec=None):
+        p = dict(case["params"])
+        if prec is not None:
+            p["prec"] = prec
+        fl = case["fluid"]
+        bd = case.get("boundary")
+        nb = 0 if bd is None else len(bd["x"])
+        cap = capacity or p.get("capacity") or (len(fl["x"]) + 64)
+        self.params = make_params(p, capacity=cap, boundary_capacity=nb, stream=stream,
+                                  device=device)
+        self.ctx = sph_init(self.params)
+        try:
+            sph_add_particles(self.ctx, fl["x"], fl["y"], fl["u"], fl["v"], fl["rho"], fl["m"],
+                              fl["type"])
+            if nb:
+                z = np.zeros(nb)
+                sph_add_particles(self.ctx, bd["x"], bd["y"], z, z, np.full(nb, p["rho0"]),
+                                  np.ones(nb), np.full(nb, BOUNDARY, np.uint8), bd["nx"],
+                                  bd["ny"])
+            inf = case.get("inflow")
+            if inf is not None:
+                sph_inflow(self.ctx, inf["x_exit"], inf["y0"], inf["y1"], inf["U"], inf["amp"],
+                           inf["k"], inf["phase"], inf["layers"])
+        except Exception:
+            sph_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def close(self):
+        if self.ctx is not None:
+            sph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self):
+        return sph_step(self.ctx)
+
+    def run(self, nsteps, breakup_every=0, D=1.0):
+        return sph_run(self.ctx, nsteps, breakup_every, D)
+
+    def evaluate(self):
+        sph_evaluate(self.ctx)
+
+    def state(self):
+        return sph_get_state(self.ctx)
+
+    def set_state(self, st):
+        sph_set_state(self.ctx, st)
+
+    def csf(self, cap):
+        return sph_get_csf(self.ctx, cap)
+
+    def pairs(self, cap):
+        return sph_get_pairs(self.ctx, cap)
+
+    def breakup_length(self, D=1.0):
+        return sph_breakup_length(self.ctx, D)
+
+    def time(self):
+        return sph_get_time(self.ctx)
+
+    def kernels_per_step(self):
+        return sph_kernels_per_step(self.ctx)

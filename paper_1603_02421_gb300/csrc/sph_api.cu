@@ -1,0 +1,916 @@
+// Host runtime and C ABI of libsph (declared in include/sph.h).
+//
+// The context owns every device buffer, issues all work on one stream, and
+// replays one captured step as a CUDA graph in sph_run.  Particle counts,
+// the time step and the simulated time live on the device, so a captured
+// step stays valid while particles enter and leave.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "sph.h"
+#include "sph_internal.cuh"
+
+using namespace sph;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct sph_ctx {
+    sph_params prm;
+    std::string err;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int cap = 0, bcap = 0;
+    size_t tsz = 4;              // sizeof(T)
+    Grid grid{};
+    PhysT<float> Pf{};
+    PhysT<double> Pd{};
+    Inflow inf{};
+    std::vector<DevBuf> allocs;
+
+    // device state
+    Scalars *sc = nullptr;       // device scalars
+    Scalars *hsc = nullptr;      // pinned host mirror
+    void *raw[7] = {}, *srt[7] = {};   // pos, vel, drho, drc, mass, type, id
+    void *H0n = nullptr, *H1n = nullptr, *H0h = nullptr, *H1h = nullptr;
+    double2 *posh = nullptr;
+    void *C = nullptr, *nhat = nullptr, *nvec = nullptr;
+    void *acc = nullptr, *dr = nullptr;
+    SortBufs sb{};
+    uint2 *cellSE = nullptr, *cellSE_b = nullptr;
+    void *bH = nullptr;
+    double2 *bpos = nullptr;
+    uint32_t *parent = nullptr;
+    uint8_t *flag = nullptr;
+    double *layer_y = nullptr;
+    int sorted_buf = 0;          // which sort buffer holds the sorted keys
+
+    // host-side boundary particles (static)
+    std::vector<double> bx, by, bnx, bny;
+
+    // derivative rows valid for raw[0, n_eval)
+    long long n_eval = 0;
+    bool csf_valid = false;
+
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_dirty = true;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static sph_status fail(sph_ctx *c, sph_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_init_error = buf;
+    return st;
+}
+
+static sph_status cuda_check(sph_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return SPH_OK;
+    return fail(c, e == cudaErrorMemoryAllocation ? SPH_ERR_OOM : SPH_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                              \
+    do {                                                            \
+        sph_status _s = cuda_check(c, (call), (what));              \
+        if (_s != SPH_OK) return _s;                                \
+    } while (0)
+
+static void *dalloc(sph_ctx *c, size_t bytes, cudaError_t &e) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) {
+        cudaMemset(p, 0, bytes);
+        c->allocs.push_back({p, bytes});
+    }
+    return p;
+}
+
+// All host<->device copies go through the context's stream and wait for it,
+// so they are ordered with the kernels whatever kind of stream it is.
+static cudaError_t copy_sync(sph_ctx *c, void *dst, const void *src, size_t bytes,
+                             cudaMemcpyKind kind) {
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, c->stream);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(c->stream);
+}
+
+static sph_status status_from_err(sph_ctx *c, unsigned err) {
+    if (err & ERR_NONFINITE) return fail(c, SPH_ERR_NONFINITE, "non-finite acceleration or density rate");
+    if (err & ERR_SKIN)
+        return fail(c, SPH_ERR_SKIN, "a particle moved more than skin/2 within a step; reduce dt or raise skin_over_h");
+    if (err & ERR_CAPACITY) return fail(c, SPH_ERR_CAPACITY, "inflow exceeded the particle capacity");
+    if (err & ERR_TIMEOUT) return fail(c, SPH_ERR_TIMEOUT, "a bounded device loop hit its iteration limit");
+    if (err & ERR_NODT) return fail(c, SPH_ERR_STATE, "adaptive time step without fluid particles");
+    return SPH_OK;
+}
+
+template <class T> static State<T> state_of(void *const a[7]) {
+    State<T> s;
+    s.pos = (double2 *)a[0];
+    s.vel = (typename Vec<T>::v2 *)a[1];
+    s.drho = (T *)a[2];
+    s.drc = (T *)a[3];
+    s.mass = (T *)a[4];
+    s.type = (uint8_t *)a[5];
+    s.id = (uint32_t *)a[6];
+    return s;
+}
+
+template <class T> static PhysT<T> make_phys(const sph_params &p, const Grid &g, bool walls) {
+    PhysT<T> P{};
+    double h = p.h_over_dx * p.dx;
+    double H = 2.0 * h, H2 = H * H;
+    double R = 1.5 * h, R2 = R * R;
+    double band = sizeof(T) == 4 ? 2e-5 : 1e-12;
+    const double pi = 3.14159265358979323846;
+    double kap = p.kernel == SPH_KERNEL_CUBIC ? 10.0 / (7.0 * pi) : 7.0 / (64.0 * pi);
+    P.kernel = p.kernel;
+    P.csf = p.sigma > 0.0;
+    P.walls = walls;
+    P.h = (T)h;
+    P.inv_h = (T)(1.0 / h);
+    P.H2lo = (T)(H2 * (1.0 - band));
+    P.H2hi = (T)(H2 * (1.0 + band));
+    P.R15lo = (T)(R2 * (1.0 - band));
+    P.R15hi = (T)(R2 * (1.0 + band));
+    P.H2d = H2;
+    P.R15d = R2;
+    P.sc = (T)g.sc;
+    P.two_sc = (T)(2.0 * g.sc);
+    P.four_sc = (T)(4.0 * g.sc);
+    P.wn = (T)(kap / (h * h));
+    P.gn = (T)(p.kernel == SPH_KERNEL_CUBIC ? kap / (h * h * h * h) : -10.0 * kap / (h * h * h * h));
+    P.W0 = (T)(p.kernel == SPH_KERNEL_CUBIC ? kap / (h * h) : 16.0 * kap / (h * h));
+    P.rho0 = (T)p.rho0;
+    P.inv_rho0 = (T)(1.0 / p.rho0);
+    P.B = (T)(p.rho0 * p.c0 * p.c0 / p.gamma);
+    P.gamma = (T)p.gamma;
+    P.c0 = (T)p.c0;
+    P.half_gm1 = (T)(0.5 * (p.gamma - 1.0));
+    P.alpha_h = (T)(p.alpha * h);
+    P.eta2 = (T)(p.eta2_over_h2 * h * h);
+    P.sigma = (T)p.sigma;
+    P.eps_n = (T)(p.eps_n_times_h / h);
+    P.gx = (T)p.gx;
+    P.gy = (T)p.gy;
+    P.wall_A = (T)(p.wall_A_coef * p.c0 * p.c0 / h);
+    P.wall_db = (T)(p.wall_db_over_dx * p.dx);
+    P.inv_wall_db = (T)(1.0 / (p.wall_db_over_dx * p.dx));
+    P.wall_h0 = (T)p.wall_h0;
+    P.inv_wall_h0 = (T)(p.wall_h0 > 0.0 ? 1.0 / p.wall_h0 : 0.0);
+    P.two_h = (T)(2.0 * h);
+    P.c0_inv = (T)(1.0 / p.c0);
+    P.courant = p.courant;
+    P.dt_fixed = p.dt_fixed;
+    return P;
+}
+
+static void cell_of(const Grid &g, double x, double y, int &cx, int &cy) {
+    cx = (int)std::floor((x - g.xmin) / g.sc) + 1;
+    cy = (int)std::floor((y - g.ymin) / g.sc) + 1;
+    cx = std::min(std::max(cx, 1), g.ncx - 2);
+    cy = std::min(std::max(cy, 1), g.ncy - 2);
+}
+
+// ---------------------------------------------------------------------------
+// step assembly
+// ---------------------------------------------------------------------------
+template <class T> struct Ops {
+    static const PhysT<T> &phys(sph_ctx *c);
+};
+template <> const PhysT<float> &Ops<float>::phys(sph_ctx *c) { return c->Pf; }
+template <> const PhysT<double> &Ops<double>::phys(sph_ctx *c) { return c->Pd; }
+
+template <class T> static Hot<T> hot_n(sph_ctx *c) {
+    return Hot<T>{(typename Vec<T>::v4 *)c->H0n, (typename Vec<T>::v4 *)c->H1n,
+                  (double2 *)c->srt[0]};
+}
+template <class T> static Hot<T> hot_h(sph_ctx *c) {
+    return Hot<T>{(typename Vec<T>::v4 *)c->H0h, (typename Vec<T>::v4 *)c->H1h, c->posh};
+}
+template <class T> static Csf<T> csf_of(sph_ctx *c) {
+    return Csf<T>{(T *)c->C, (typename Vec<T>::v2 *)c->nhat, (typename Vec<T>::v2 *)c->nvec};
+}
+static Boundary bd_of(sph_ctx *c) {
+    Boundary b;
+    b.n = (int)c->bx.size();
+    b.cellSE = c->cellSE_b;
+    b.bh = c->bH;
+    b.pos = c->bpos;
+    return b;
+}
+
+// hash -> sort -> cell ranges -> gather into cell order (evaluation-n records)
+template <class T> static const uint32_t *enqueue_sort(sph_ctx *c) {
+    const PhysT<T> &P = Ops<T>::phys(c);
+    State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
+    launch_hash<T>(c->grid, raw, c->sc, c->sb.key[0], c->sb.val[0], c->cap, c->stream);
+    int buf = launch_radix_sort(c->sb, c->grid, c->sc, c->cap, c->stream);
+    c->sorted_buf = buf;
+    const uint32_t *key = c->sb.key[buf];
+    launch_cells(c->grid, key, c->sc, c->cellSE, c->cap, c->stream);
+    launch_reorder<T>(P, c->grid, c->sc, key, c->sb.val[buf], raw, srt, hot_n<T>(c), c->cap,
+                      c->stream);
+    return key;
+}
+
+template <class T> static void enqueue_csf(sph_ctx *c, const uint32_t *key, const Hot<T> &hot) {
+    const PhysT<T> &P = Ops<T>::phys(c);
+    if (!P.csf) return;
+    launch_colour<T>(P, c->grid, c->sc, c->cellSE, key, hot, csf_of<T>(c), c->cap, c->stream);
+    launch_normal<T>(P, c->grid, c->sc, c->cellSE, key, hot, csf_of<T>(c), c->cap, c->stream);
+}
+
+template <class T> static void enqueue_step(sph_ctx *c) {
+    const PhysT<T> &P = Ops<T>::phys(c);
+    State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
+    auto *acc = (typename Vec<T>::v2 *)c->acc;
+    T *dr = (T *)c->dr;
+    const uint32_t *key = enqueue_sort<T>(c);
+    Hot<T> hn = hot_n<T>(c), hh = hot_h<T>(c);
+    enqueue_csf<T>(c, key, hn);
+    launch_forces<T>(1, P, c->grid, c->inf, c->sc, c->cellSE, key, hn, csf_of<T>(c), bd_of(c),
+                     srt, raw, acc, dr, c->cap, c->stream);
+    launch_predict<T>(P, c->grid, c->inf, c->sc, key, srt, acc, dr, hh, c->cap, c->stream);
+    enqueue_csf<T>(c, key, hh);
+    launch_forces<T>(2, P, c->grid, c->inf, c->sc, c->cellSE, key, hh, csf_of<T>(c), bd_of(c),
+                     srt, raw, acc, dr, c->cap, c->stream);
+    launch_spawn<T>(P, c->inf, c->sc, raw, c->layer_y, c->cap, c->stream);
+}
+
+template <class T> static void enqueue_evaluate(sph_ctx *c) {
+    const PhysT<T> &P = Ops<T>::phys(c);
+    State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
+    const uint32_t *key = enqueue_sort<T>(c);
+    Hot<T> hn = hot_n<T>(c);
+    enqueue_csf<T>(c, key, hn);
+    launch_forces<T>(0, P, c->grid, c->inf, c->sc, c->cellSE, key, hn, csf_of<T>(c), bd_of(c),
+                     srt, raw, (typename Vec<T>::v2 *)c->acc, (T *)c->dr, c->cap, c->stream);
+}
+
+template <class T> static void enqueue_breakup(sph_ctx *c) {
+    const uint32_t *key = enqueue_sort<T>(c);
+    State<T> srt = state_of<T>(c->srt);
+    launch_breakup<T>(Ops<T>::phys(c), c->grid, c->sc, c->cellSE, key, hot_n<T>(c), srt.type,
+                      c->parent, c->flag, c->cap, c->stream);
+}
+
+static void step_any(sph_ctx *c) {
+    if (c->tsz == 4) enqueue_step<float>(c); else enqueue_step<double>(c);
+}
+
+static sph_status pull_scalars(sph_ctx *c) {
+    CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream),
+       "copy scalars");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return SPH_OK;
+}
+
+static sph_status push_scalars(sph_ctx *c) {
+    CK(cudaMemcpyAsync(c->sc, c->hsc, sizeof(Scalars), cudaMemcpyHostToDevice, c->stream),
+       "copy scalars");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return SPH_OK;
+}
+
+static sph_status after_work(sph_ctx *c, const char *what) {
+    CK(cudaGetLastError(), what);
+    sph_status s = pull_scalars(c);
+    if (s != SPH_OK) return s;
+    return status_from_err(c, c->hsc->err);
+}
+
+static void rebuild_phys(sph_ctx *c) {
+    bool walls = !c->bx.empty();
+    c->Pf = make_phys<float>(c->prm, c->grid, walls);
+    c->Pd = make_phys<double>(c->prm, c->grid, walls);
+    c->graph_dirty = true;
+}
+
+static sph_status upload_boundary(sph_ctx *c) {
+    size_t nb = c->bx.size();
+    std::vector<uint32_t> key(nb);
+    for (size_t k = 0; k < nb; ++k) {
+        int cx, cy;
+        cell_of(c->grid, c->bx[k], c->by[k], cx, cy);
+        key[k] = (uint32_t)cy * (uint32_t)c->grid.ncx + (uint32_t)cx;
+    }
+    std::vector<size_t> ord(nb);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return key[a] < key[b]; });
+    std::vector<uint2> se(c->grid.ncells, make_uint2(0, 0));
+    std::vector<double2> pos(nb);
+    std::vector<double> hd(4 * nb);
+    for (size_t r = 0; r < nb; ++r) {
+        size_t k = ord[r];
+        uint32_t kk = key[k];
+        if (r == 0 || key[ord[r - 1]] != kk) se[kk].x = (unsigned)r;
+        if (r + 1 == nb || key[ord[r + 1]] != kk) se[kk].y = (unsigned)(r + 1);
+        int cy = (int)(kk / (uint32_t)c->grid.ncx), cx = (int)kk - cy * c->grid.ncx;
+        double xo = c->bx[k] - (c->grid.xmin + (double)(cx - 1) * c->grid.sc);
+        double yo = c->by[k] - (c->grid.ymin + (double)(cy - 1) * c->grid.sc);
+        hd[4 * r + 0] = xo + (double)(cx & 3) * c->grid.sc;
+        hd[4 * r + 1] = yo;
+        hd[4 * r + 2] = c->bnx[k];
+        hd[4 * r + 3] = c->bny[k];
+        pos[r] = make_double2(c->bx[k], c->by[k]);
+    }
+    if (c->tsz == 4) {
+        std::vector<float> hf(4 * nb);
+        for (size_t q = 0; q < 4 * nb; ++q) hf[q] = (float)hd[q];
+        CK(copy_sync(c, c->bH, hf.data(), 4 * nb * sizeof(float), cudaMemcpyHostToDevice), "upload boundary");
+    } else {
+        CK(copy_sync(c, c->bH, hd.data(), 4 * nb * sizeof(double), cudaMemcpyHostToDevice), "upload boundary");
+    }
+    CK(copy_sync(c, c->bpos, pos.data(), nb * sizeof(double2), cudaMemcpyHostToDevice), "upload boundary");
+    CK(copy_sync(c, c->cellSE_b, se.data(), se.size() * sizeof(uint2), cudaMemcpyHostToDevice),
+       "upload boundary cells");
+    rebuild_phys(c);
+    return SPH_OK;
+}
+
+// Upload n particles into raw[at, at+n).
+static sph_status upload_particles(sph_ctx *c, long long at, long long n, const double *x,
+                                   const double *y, const double *u, const double *v,
+                                   const double *rho, const double *mass,
+                                   const unsigned char *type, const unsigned *id) {
+    if (n == 0) return SPH_OK;
+    std::vector<double2> pos(n);
+    for (long long i = 0; i < n; ++i) pos[i] = make_double2(x[i], y[i]);
+    CK(copy_sync(c, (double2 *)c->raw[0] + at, pos.data(), n * sizeof(double2), cudaMemcpyHostToDevice), "upload");
+    size_t ts = c->tsz;
+    std::vector<unsigned char> vel(2 * n * ts), drho(n * ts), zero(n * ts, 0), m(n * ts);
+    for (long long i = 0; i < n; ++i) {
+        double d = rho[i] - c->prm.rho0;
+        if (ts == 4) {
+            float f2[2] = {(float)u[i], (float)v[i]}, fd = (float)d, fm = (float)mass[i];
+            memcpy(&vel[2 * i * ts], f2, 8);
+            memcpy(&drho[i * ts], &fd, 4);
+            memcpy(&m[i * ts], &fm, 4);
+        } else {
+            double d2[2] = {u[i], v[i]};
+            memcpy(&vel[2 * i * ts], d2, 16);
+            memcpy(&drho[i * ts], &d, 8);
+            memcpy(&m[i * ts], &mass[i], 8);
+        }
+    }
+    CK(copy_sync(c, (char *)c->raw[1] + 2 * at * ts, vel.data(), 2 * n * ts, cudaMemcpyHostToDevice), "upload");
+    CK(copy_sync(c, (char *)c->raw[2] + at * ts, drho.data(), n * ts, cudaMemcpyHostToDevice), "upload");
+    CK(copy_sync(c, (char *)c->raw[3] + at * ts, zero.data(), n * ts, cudaMemcpyHostToDevice), "upload");
+    CK(copy_sync(c, (char *)c->raw[4] + at * ts, m.data(), n * ts, cudaMemcpyHostToDevice), "upload");
+    CK(copy_sync(c, (uint8_t *)c->raw[5] + at, type, n, cudaMemcpyHostToDevice), "upload");
+    CK(copy_sync(c, (uint32_t *)c->raw[6] + at, id, n * sizeof(unsigned), cudaMemcpyHostToDevice), "upload");
+    return SPH_OK;
+}
+
+static bool inside(const sph_ctx *c, double x, double y) {
+    return x >= c->prm.xmin && x < c->prm.xmax && y >= c->prm.ymin && y < c->prm.ymax;
+}
+
+template <class T> static void to_double(const std::vector<unsigned char> &src, size_t i, size_t comp,
+                                         size_t ncomp, double &out) {
+    T v;
+    memcpy(&v, &src[(i * ncomp + comp) * sizeof(T)], sizeof(T));
+    out = (double)v;
+}
+
+static double rd(const sph_ctx *c, const std::vector<unsigned char> &b, size_t i, size_t comp, size_t ncomp) {
+    double o;
+    if (c->tsz == 4) to_double<float>(b, i, comp, ncomp, o); else to_double<double>(b, i, comp, ncomp, o);
+    return o;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *sph_last_error(const sph_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+sph_status sph_init(const sph_params *p, sph_ctx **out) {
+    if (!out) return fail(nullptr, SPH_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, SPH_ERR_ARG, "params is NULL");
+    const sph_params &q = *p;
+    if (q.kernel != SPH_KERNEL_CUBIC && q.kernel != SPH_KERNEL_WENDLAND)
+        return fail(nullptr, SPH_ERR_ARG, "unknown kernel %d", q.kernel);
+    if (q.precision != SPH_FP32 && q.precision != SPH_FP64)
+        return fail(nullptr, SPH_ERR_ARG, "unknown precision %d", q.precision);
+    if (!(q.dx > 0 && q.h_over_dx > 0 && q.rho0 > 0 && q.c0 > 0 && q.gamma >= 1.0))
+        return fail(nullptr, SPH_ERR_ARG, "dx, h_over_dx, rho0, c0 must be > 0 and gamma >= 1");
+    if (!(q.alpha >= 0 && q.eta2_over_h2 > 0 && q.sigma >= 0 && q.eps_n_times_h > 0))
+        return fail(nullptr, SPH_ERR_ARG, "alpha, sigma >= 0; eta2_over_h2, eps_n_times_h > 0 required");
+    if (!(q.courant > 0 && q.courant <= 1.0 && q.dt_fixed >= 0))
+        return fail(nullptr, SPH_ERR_ARG, "courant in (0, 1] and dt_fixed >= 0 required");
+    if (!(q.xmax > q.xmin && q.ymax > q.ymin)) return fail(nullptr, SPH_ERR_ARG, "empty domain box");
+    if (!(q.skin_over_h >= 0.1 && q.skin_over_h <= 2.0))
+        return fail(nullptr, SPH_ERR_ARG, "skin_over_h must lie in [0.1, 2]");
+    if (!(q.capacity >= 1 && q.capacity <= (1ll << 30)))
+        return fail(nullptr, SPH_ERR_ARG, "capacity must lie in [1, 2^30]");
+    if (!(q.boundary_capacity >= 0 && q.boundary_capacity <= (1ll << 26)))
+        return fail(nullptr, SPH_ERR_ARG, "boundary_capacity must lie in [0, 2^26]");
+    if (!(q.wall_A_coef >= 0 && q.wall_h0 >= 0 && q.wall_db_over_dx > 0))
+        return fail(nullptr, SPH_ERR_ARG, "wall parameters out of range");
+    double h = q.h_over_dx * q.dx, skin = q.skin_over_h * h;
+    double db = q.wall_db_over_dx * q.dx;
+    if (q.boundary_capacity > 0 && std::sqrt(4 * h * h + db * db) > 2 * h + 0.5 * skin)
+        return fail(nullptr, SPH_ERR_ARG, "skin too small for the wall-force reach");
+    double sc = 2.0 * h + skin;
+    double ncx = std::floor((q.xmax - q.xmin) / sc) + 3, ncy = std::floor((q.ymax - q.ymin) / sc) + 3;
+    if (ncx * ncy > 2.0e9) return fail(nullptr, SPH_ERR_ARG, "cell grid too large (%.3g cells)", ncx * ncy);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(nullptr, SPH_ERR_CUDA, "no CUDA device available");
+    if (q.device < 0 || q.device >= ndev) return fail(nullptr, SPH_ERR_ARG, "device %d out of range", q.device);
+
+    sph_ctx *c = new (std::nothrow) sph_ctx();
+    if (!c) return fail(nullptr, SPH_ERR_OOM, "host allocation failed");
+    c->prm = q;
+    c->cap = (int)q.capacity;
+    c->bcap = (int)q.boundary_capacity;
+    c->tsz = q.precision == SPH_FP32 ? 4 : 8;
+    Grid &g = c->grid;
+    g.xmin = q.xmin; g.ymin = q.ymin; g.xmax = q.xmax; g.ymax = q.ymax;
+    g.sc = sc; g.inv_sc = 1.0 / sc;
+    g.ncx = (int)ncx; g.ncy = (int)ncy;
+    g.ncells = (unsigned)(g.ncx * g.ncy);
+    int bits = 1;
+    while (((1ull << bits) - 1ull) < (unsigned long long)g.ncells) ++bits;
+    g.keybits = bits;
+    g.sentinel = (uint32_t)((1ull << bits) - 1ull);
+
+    auto bail = [&](sph_status s) { sph_destroy(c); return s; };
+    cudaError_t e = cudaSetDevice(q.device);
+    if (e != cudaSuccess) { fail(nullptr, SPH_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e)); return bail(SPH_ERR_CUDA); }
+    if (q.cuda_stream) {
+        c->stream = (cudaStream_t)q.cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { fail(nullptr, SPH_ERR_CUDA, "stream: %s", cudaGetErrorString(e)); return bail(SPH_ERR_CUDA); }
+        c->own_stream = true;
+    }
+    size_t N = (size_t)c->cap, ts = c->tsz, NB = (size_t)std::max(c->bcap, 1);
+    size_t sizes[7] = {16, 2 * ts, ts, ts, ts, 1, 4};
+    for (int k = 0; k < 7; ++k) {
+        c->raw[k] = dalloc(c, N * sizes[k], e); if (e) break;
+        c->srt[k] = dalloc(c, N * sizes[k], e); if (e) break;
+    }
+    if (!e) c->H0n = dalloc(c, N * 4 * ts, e);
+    if (!e) c->H1n = dalloc(c, N * 4 * ts, e);
+    if (!e) c->H0h = dalloc(c, N * 4 * ts, e);
+    if (!e) c->H1h = dalloc(c, N * 4 * ts, e);
+    if (!e) c->posh = (double2 *)dalloc(c, N * 16, e);
+    if (!e) c->C = dalloc(c, N * ts, e);
+    if (!e) c->nhat = dalloc(c, N * 2 * ts, e);
+    if (!e) c->nvec = dalloc(c, N * 2 * ts, e);
+    if (!e) c->acc = dalloc(c, N * 2 * ts, e);
+    if (!e) c->dr = dalloc(c, N * ts, e);
+    c->sb.ntiles = (int)((N + RS_TILE - 1) / RS_TILE);
+    for (int k = 0; k < 2 && !e; ++k) {
+        c->sb.key[k] = (uint32_t *)dalloc(c, N * 4, e);
+        if (!e) c->sb.val[k] = (uint32_t *)dalloc(c, N * 4, e);
+    }
+    if (!e) c->sb.tileHist = (uint32_t *)dalloc(c, (size_t)RS_BINS * c->sb.ntiles * 4, e);
+    if (!e) c->cellSE = (uint2 *)dalloc(c, (size_t)g.ncells * 8, e);
+    if (!e) c->cellSE_b = (uint2 *)dalloc(c, (size_t)g.ncells * 8, e);
+    if (!e) c->bH = dalloc(c, NB * 4 * ts, e);
+    if (!e) c->bpos = (double2 *)dalloc(c, NB * 16, e);
+    if (!e) c->parent = (uint32_t *)dalloc(c, N * 4, e);
+    if (!e) c->flag = (uint8_t *)dalloc(c, N, e);
+    if (!e) c->layer_y = (double *)dalloc(c, 1024 * sizeof(double), e);
+    if (!e) c->sc = (Scalars *)dalloc(c, sizeof(Scalars), e);
+    if (e) { fail(nullptr, e == cudaErrorMemoryAllocation ? SPH_ERR_OOM : SPH_ERR_CUDA, "device allocation: %s", cudaGetErrorString(e)); return bail(SPH_ERR_OOM); }
+    e = cudaDeviceSynchronize();
+    if (e) { fail(nullptr, SPH_ERR_CUDA, "device synchronize: %s", cudaGetErrorString(e)); return bail(SPH_ERR_CUDA); }
+    e = cudaMallocHost(&c->hsc, sizeof(Scalars));
+    if (e) { fail(nullptr, SPH_ERR_OOM, "pinned allocation: %s", cudaGetErrorString(e)); return bail(SPH_ERR_OOM); }
+    memset(c->hsc, 0, sizeof(Scalars));
+    c->hsc->dtmin_f = 0x7f7f7f7fu;
+    c->hsc->dtmin_d = 0x7f7f7f7f7f7f7f7full;
+    if (push_scalars(c) != SPH_OK) { g_init_error = c->err; return bail(SPH_ERR_CUDA); }
+    rebuild_phys(c);
+    *out = c;
+    return SPH_OK;
+}
+
+void sph_destroy(sph_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    for (auto &b : c->allocs) cudaFree(b.p);
+    if (c->hsc) cudaFreeHost(c->hsc);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+sph_status sph_add_particles(sph_ctx *c, long long n, const double *x, const double *y,
+                             const double *u, const double *v, const double *rho,
+                             const double *mass, const unsigned char *type, const double *nx,
+                             const double *ny) {
+    if (!c) return SPH_ERR_ARG;
+    try {
+        if (n < 0) return fail(c, SPH_ERR_ARG, "n < 0");
+        if (n == 0) return SPH_OK;
+        if (!x || !y || !type) return fail(c, SPH_ERR_ARG, "x, y and type are required");
+        long long nf = 0, nb = 0;
+        for (long long i = 0; i < n; ++i) {
+            if (type[i] == SPH_BOUNDARY) ++nb;
+            else if (type[i] == SPH_FLUID || type[i] == SPH_BUFFER) ++nf;
+            else return fail(c, SPH_ERR_ARG, "particle %lld has unknown type %d", i, (int)type[i]);
+            if (!std::isfinite(x[i]) || !std::isfinite(y[i]))
+                return fail(c, SPH_ERR_ARG, "particle %lld has a non-finite position", i);
+            if (!inside(c, x[i], y[i])) return fail(c, SPH_ERR_ARG, "particle %lld lies outside the domain", i);
+        }
+        if (nf > 0 && (!u || !v || !rho || !mass)) return fail(c, SPH_ERR_ARG, "u, v, rho and mass are required");
+        if (nb > 0 && (!nx || !ny)) return fail(c, SPH_ERR_ARG, "boundary particles need nx, ny");
+        for (long long i = 0; i < n; ++i) {
+            if (type[i] == SPH_BOUNDARY) continue;
+            if (!(rho[i] > 0) || !(mass[i] > 0) || !std::isfinite(u[i]) || !std::isfinite(v[i]))
+                return fail(c, SPH_ERR_ARG, "particle %lld needs rho, mass > 0 and a finite velocity", i);
+        }
+        sph_status s = pull_scalars(c);
+        if (s) return s;
+        long long n0 = c->hsc->n;
+        if (n0 + nf > c->cap) return fail(c, SPH_ERR_CAPACITY, "capacity %d exceeded", c->cap);
+        if ((long long)c->bx.size() + nb > c->bcap)
+            return fail(c, SPH_ERR_CAPACITY, "boundary capacity %d exceeded", c->bcap);
+        if (nf > 0) {
+            std::vector<double> fx, fy, fu, fv, fr, fm;
+            std::vector<unsigned char> ft;
+            std::vector<unsigned> fid;
+            unsigned nid = c->hsc->next_id;
+            for (long long i = 0; i < n; ++i) {
+                if (type[i] == SPH_BOUNDARY) continue;
+                fx.push_back(x[i]); fy.push_back(y[i]); fu.push_back(u[i]); fv.push_back(v[i]);
+                fr.push_back(rho[i]); fm.push_back(mass[i]); ft.push_back(type[i]);
+                fid.push_back(nid++);
+            }
+            s = upload_particles(c, n0, nf, fx.data(), fy.data(), fu.data(), fv.data(), fr.data(),
+                                 fm.data(), ft.data(), fid.data());
+            if (s) return s;
+            c->hsc->n = (int)(n0 + nf);
+            c->hsc->next_id = nid;
+            s = push_scalars(c);
+            if (s) return s;
+            c->n_eval = 0;
+            c->csf_valid = false;
+        }
+        if (nb > 0) {
+            for (long long i = 0; i < n; ++i) {
+                if (type[i] != SPH_BOUNDARY) continue;
+                double l = std::hypot(nx[i], ny[i]);
+                if (!(l > 0)) return fail(c, SPH_ERR_ARG, "boundary particle %lld has a zero normal", i);
+                c->bx.push_back(x[i]); c->by.push_back(y[i]);
+                c->bnx.push_back(nx[i] / l); c->bny.push_back(ny[i] / l);
+            }
+            s = upload_boundary(c);
+            if (s) return s;
+        }
+        return SPH_OK;
+    } catch (...) {
+        return fail(c, SPH_ERR_OOM, "host allocation failed");
+    }
+}
+
+sph_status sph_inflow(sph_ctx *c, double x_exit, double y0, double y1, double U, double amp,
+                      double k, double phase, int layers) {
+    if (!c) return SPH_ERR_ARG;
+    try {
+        if (c->inf.on) return fail(c, SPH_ERR_STATE, "inflow already configured");
+        double dx = c->prm.dx;
+        if (!(y1 > y0) || !(U > 0) || !(amp >= 0 && amp < 1) || layers < 1 || layers > 16 ||
+            !std::isfinite(k) || !std::isfinite(phase))
+            return fail(c, SPH_ERR_ARG, "invalid inflow parameters");
+        int ny = (int)std::lround((y1 - y0) / dx);
+        if (ny < 1 || ny > 1024) return fail(c, SPH_ERR_ARG, "inflow layer holds %d particles (1..1024)", ny);
+        Inflow &f = c->inf;
+        f.layers = layers; f.ny = ny; f.x_exit = x_exit; f.y0 = y0; f.y1 = y1; f.U = U;
+        f.amp = amp; f.k = k; f.phase = phase; f.dx = dx;
+        f.m_layer = c->prm.rho0 * (dx * dx);
+        f.threshold = x_exit - (layers - 0.5) * dx;
+        std::vector<double> ly(ny);
+        for (int j = 0; j < ny; ++j) ly[j] = y0 + (j + 0.5) * dx;
+        for (int j = 0; j < ny; ++j)
+            if (!inside(c, f.threshold - dx, ly[j]))
+                return fail(c, SPH_ERR_ARG, "inflow buffer lies outside the domain");
+        sph_status s = pull_scalars(c);
+        if (s) return s;
+        double t = c->hsc->t;
+        double u0 = U * (1.0 + amp * std::sin(k * U * t + phase));
+        long long nnew = (long long)layers * ny;
+        std::vector<double> xs(nnew), ys(nnew), us(nnew, u0), vs(nnew, 0.0), rs(nnew, c->prm.rho0),
+            ms(nnew, f.m_layer);
+        std::vector<unsigned char> ts(nnew, SPH_BUFFER);
+        for (int L = 0; L < layers; ++L)
+            for (int j = 0; j < ny; ++j) {
+                xs[(size_t)L * ny + j] = x_exit - (L + 0.5) * dx;
+                ys[(size_t)L * ny + j] = ly[j];
+            }
+        CK(copy_sync(c, c->layer_y, ly.data(), ny * sizeof(double), cudaMemcpyHostToDevice), "upload layer");
+        s = sph_add_particles(c, nnew, xs.data(), ys.data(), us.data(), vs.data(), rs.data(),
+                              ms.data(), ts.data(), nullptr, nullptr);
+        if (s) return s;
+        s = pull_scalars(c);
+        if (s) return s;
+        c->hsc->x_up = x_exit - (layers - 0.5) * dx;
+        s = push_scalars(c);
+        if (s) return s;
+        f.on = 1;
+        c->graph_dirty = true;
+        return SPH_OK;
+    } catch (...) {
+        return fail(c, SPH_ERR_OOM, "host allocation failed");
+    }
+}
+
+sph_status sph_step(sph_ctx *c, double *dt_used) {
+    if (!c) return SPH_ERR_ARG;
+    step_any(c);
+    sph_status s = after_work(c, "step");
+    if (dt_used) *dt_used = c->hsc->dt;
+    c->n_eval = c->hsc->nsrt;
+    c->csf_valid = false;
+    return s;
+}
+
+sph_status sph_evaluate(sph_ctx *c) {
+    if (!c) return SPH_ERR_ARG;
+    if (c->tsz == 4) enqueue_evaluate<float>(c); else enqueue_evaluate<double>(c);
+    sph_status s = after_work(c, "evaluate");
+    c->n_eval = c->hsc->nsrt;
+    c->csf_valid = true;
+    return s;
+}
+
+static sph_status breakup_now(sph_ctx *c, double D, double *L, int *broken) {
+    if (c->tsz == 4) enqueue_breakup<float>(c); else enqueue_breakup<double>(c);
+    sph_status s = after_work(c, "breakup");
+    if (s) return s;
+    unsigned long long k = c->hsc->xmax_key;
+    if (k == 0) return fail(c, SPH_ERR_STATE, "no inflow buffer particle present");
+    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    double xmax;
+    memcpy(&xmax, &b, 8);
+    *L = (xmax - c->inf.x_exit) / D;
+    if (broken) *broken = c->hsc->detached > 0;
+    return SPH_OK;
+}
+
+sph_status sph_breakup_length(sph_ctx *c, double D, double *L_over_D, int *broken) {
+    if (!c) return SPH_ERR_ARG;
+    if (!c->inf.on) return fail(c, SPH_ERR_STATE, "breakup length needs an inflow");
+    if (!(D > 0) || !L_over_D) return fail(c, SPH_ERR_ARG, "D > 0 and L_over_D required");
+    return breakup_now(c, D, L_over_D, broken);
+}
+
+sph_status sph_run(sph_ctx *c, long long nsteps, int breakup_every, double D, double *L_out,
+                   long long *nL) {
+    if (!c) return SPH_ERR_ARG;
+    if (nsteps < 0) return fail(c, SPH_ERR_ARG, "nsteps < 0");
+    if (breakup_every > 0) {
+        if (!c->inf.on) return fail(c, SPH_ERR_STATE, "breakup sampling needs an inflow");
+        if (!L_out || !nL || !(D > 0)) return fail(c, SPH_ERR_ARG, "L_out, nL and D > 0 required");
+        *nL = 0;
+    }
+    if (c->graph_dirty || !c->gexec) {
+        if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+        if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        step_any(c);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &c->graph);
+        CK(e, "end capture");
+        CK(cudaGraphInstantiate(&c->gexec, c->graph, 0), "instantiate graph");
+        c->graph_dirty = false;
+    }
+    for (long long k = 1; k <= nsteps; ++k) {
+        CK(cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+        if (breakup_every > 0 && k % breakup_every == 0) {
+            double L;
+            sph_status s = breakup_now(c, D, &L, nullptr);
+            if (s) return s;
+            L_out[(*nL)++] = L;
+        }
+    }
+    sph_status s = after_work(c, "run");
+    c->n_eval = c->hsc->nsrt;
+    c->csf_valid = false;
+    return s;
+}
+
+sph_status sph_get_state(sph_ctx *c, long long cap, long long *n_out, double *x, double *y,
+                         double *u, double *v, double *rho, double *mass, unsigned char *type,
+                         unsigned *id, double *ax, double *ay, double *drho) {
+    if (!c || !n_out) return SPH_ERR_ARG;
+    try {
+        sph_status s = pull_scalars(c);
+        if (s) return s;
+        size_t n = (size_t)c->hsc->n, ts = c->tsz;
+        std::vector<double2> pos(n);
+        std::vector<unsigned char> vel(2 * n * ts), dr(n * ts), m(n * ts), ac(2 * n * ts), drt(n * ts);
+        std::vector<unsigned char> ty(n);
+        std::vector<unsigned> ids(n);
+        if (n) {
+            CK(copy_sync(c, pos.data(), c->raw[0], n * 16, cudaMemcpyDeviceToHost), "download");
+            CK(copy_sync(c, vel.data(), c->raw[1], 2 * n * ts, cudaMemcpyDeviceToHost), "download");
+            CK(copy_sync(c, dr.data(), c->raw[2], n * ts, cudaMemcpyDeviceToHost), "download");
+            CK(copy_sync(c, m.data(), c->raw[4], n * ts, cudaMemcpyDeviceToHost), "download");
+            CK(copy_sync(c, ty.data(), c->raw[5], n, cudaMemcpyDeviceToHost), "download");
+            CK(copy_sync(c, ids.data(), c->raw[6], n * 4, cudaMemcpyDeviceToHost), "download");
+            CK(copy_sync(c, ac.data(), c->acc, 2 * n * ts, cudaMemcpyDeviceToHost), "download");
+            CK(copy_sync(c, drt.data(), c->dr, n * ts, cudaMemcpyDeviceToHost), "download");
+        }
+        std::vector<size_t> ord;
+        ord.reserve(n);
+        for (size_t i = 0; i < n; ++i)
+            if (ty[i] != T_DEAD) ord.push_back(i);
+        std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return ids[a] < ids[b]; });
+        *n_out = (long long)ord.size();
+        if ((long long)ord.size() > cap) return fail(c, SPH_ERR_CAPACITY, "%zu particles > cap %lld", ord.size(), cap);
+        for (size_t r = 0; r < ord.size(); ++r) {
+            size_t i = ord[r];
+            bool has = (long long)i < c->n_eval;
+            if (x) x[r] = pos[i].x;
+            if (y) y[r] = pos[i].y;
+            if (u) u[r] = rd(c, vel, i, 0, 2);
+            if (v) v[r] = rd(c, vel, i, 1, 2);
+            if (rho) rho[r] = c->prm.rho0 + rd(c, dr, i, 0, 1);
+            if (mass) mass[r] = rd(c, m, i, 0, 1);
+            if (type) type[r] = ty[i];
+            if (id) id[r] = ids[i];
+            if (ax) ax[r] = has ? rd(c, ac, i, 0, 2) : 0.0;
+            if (ay) ay[r] = has ? rd(c, ac, i, 1, 2) : 0.0;
+            if (drho) drho[r] = has ? rd(c, drt, i, 0, 1) : 0.0;
+        }
+        return SPH_OK;
+    } catch (...) {
+        return fail(c, SPH_ERR_OOM, "host allocation failed");
+    }
+}
+
+sph_status sph_set_state(sph_ctx *c, long long n, const double *x, const double *y,
+                         const double *u, const double *v, const double *rho,
+                         const double *mass, const unsigned char *type, const unsigned *id) {
+    if (!c) return SPH_ERR_ARG;
+    try {
+        if (n < 0 || n > c->cap) return fail(c, SPH_ERR_CAPACITY, "n = %lld outside [0, capacity]", n);
+        if (n > 0 && (!x || !y || !u || !v || !rho || !mass || !type || !id))
+            return fail(c, SPH_ERR_ARG, "all arrays are required");
+        unsigned maxid = 0;
+        std::vector<unsigned> sid(id, id + n);
+        std::sort(sid.begin(), sid.end());
+        for (long long i = 1; i < n; ++i)
+            if (sid[i] == sid[i - 1]) return fail(c, SPH_ERR_ARG, "duplicate id %u", sid[i]);
+        for (long long i = 0; i < n; ++i) {
+            if (type[i] != SPH_FLUID && type[i] != SPH_BUFFER)
+                return fail(c, SPH_ERR_ARG, "particle %lld: set_state takes fluid or buffer particles", i);
+            if (!inside(c, x[i], y[i])) return fail(c, SPH_ERR_ARG, "particle %lld lies outside the domain", i);
+            if (!(rho[i] > 0) || !(mass[i] > 0)) return fail(c, SPH_ERR_ARG, "particle %lld needs rho, mass > 0", i);
+            maxid = std::max(maxid, id[i]);
+        }
+        sph_status s = pull_scalars(c);
+        if (s) return s;
+        s = upload_particles(c, 0, n, x, y, u, v, rho, mass, type, id);
+        if (s) return s;
+        c->hsc->n = (int)n;
+        c->hsc->nsrt = 0;
+        if (n > 0) c->hsc->next_id = std::max(c->hsc->next_id, maxid + 1);
+        s = push_scalars(c);
+        c->n_eval = 0;
+        c->csf_valid = false;
+        return s;
+    } catch (...) {
+        return fail(c, SPH_ERR_OOM, "host allocation failed");
+    }
+}
+
+sph_status sph_get_csf(sph_ctx *c, long long cap, long long *n_out, unsigned *id, double *C,
+                       double *nx, double *ny) {
+    if (!c || !n_out) return SPH_ERR_ARG;
+    if (!c->csf_valid) return fail(c, SPH_ERR_STATE, "call sph_evaluate first");
+    try {
+        sph_status s = pull_scalars(c);
+        if (s) return s;
+        size_t n = (size_t)c->hsc->nsrt, ts = c->tsz;
+        *n_out = (long long)n;
+        if ((long long)n > cap) return fail(c, SPH_ERR_CAPACITY, "%zu particles > cap %lld", n, cap);
+        std::vector<unsigned char> cc(n * ts), nv(2 * n * ts);
+        std::vector<unsigned> ids(n);
+        bool on = c->prm.sigma > 0;
+        if (n) {
+            CK(copy_sync(c, ids.data(), c->raw[6], n * 4, cudaMemcpyDeviceToHost), "download");
+            if (on) {
+                CK(copy_sync(c, cc.data(), c->C, n * ts, cudaMemcpyDeviceToHost), "download");
+                CK(copy_sync(c, nv.data(), c->nvec, 2 * n * ts, cudaMemcpyDeviceToHost), "download");
+            }
+        }
+        std::vector<size_t> ord(n);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return ids[a] < ids[b]; });
+        for (size_t r = 0; r < n; ++r) {
+            size_t i = ord[r];
+            if (id) id[r] = ids[i];
+            if (C) C[r] = on ? rd(c, cc, i, 0, 1) : 0.0;
+            if (nx) nx[r] = on ? rd(c, nv, i, 0, 2) : 0.0;
+            if (ny) ny[r] = on ? rd(c, nv, i, 1, 2) : 0.0;
+        }
+        return SPH_OK;
+    } catch (...) {
+        return fail(c, SPH_ERR_OOM, "host allocation failed");
+    }
+}
+
+sph_status sph_get_pairs(sph_ctx *c, long long cap, unsigned *id_a, unsigned *id_b,
+                         long long *npairs) {
+    if (!c || !npairs || cap < 0) return SPH_ERR_ARG;
+    if (cap > 0 && (!id_a || !id_b)) return fail(c, SPH_ERR_ARG, "output arrays required");
+    unsigned dcap = (unsigned)std::min<long long>(cap, 0x7fffffffll);
+    unsigned *da = nullptr, *db = nullptr;
+    CK(cudaMalloc(&da, std::max<size_t>(dcap, 1) * 4), "pair buffer");
+    cudaError_t e = cudaMalloc(&db, std::max<size_t>(dcap, 1) * 4);
+    if (e) { cudaFree(da); return cuda_check(c, e, "pair buffer"); }
+    sph_status s = SPH_OK;
+    if (c->tsz == 4) {
+        const uint32_t *key = enqueue_sort<float>(c);
+        launch_pairs<float>(c->Pf, c->grid, c->sc, c->sc, c->cellSE, key, hot_n<float>(c),
+                            (uint32_t *)c->srt[6], da, db, dcap, c->cap, c->stream);
+    } else {
+        const uint32_t *key = enqueue_sort<double>(c);
+        launch_pairs<double>(c->Pd, c->grid, c->sc, c->sc, c->cellSE, key, hot_n<double>(c),
+                             (uint32_t *)c->srt[6], da, db, dcap, c->cap, c->stream);
+    }
+    s = after_work(c, "pairs");
+    if (s == SPH_OK) {
+        long long np = c->hsc->pair_count;
+        *npairs = np;
+        if (np > cap) {
+            s = fail(c, SPH_ERR_CAPACITY, "%lld pairs > cap %lld", np, cap);
+        } else if (np > 0) {
+            e = copy_sync(c, id_a, da, (size_t)np * 4, cudaMemcpyDeviceToHost);
+            if (!e) e = copy_sync(c, id_b, db, (size_t)np * 4, cudaMemcpyDeviceToHost);
+            if (e) s = cuda_check(c, e, "download pairs");
+        }
+    }
+    cudaFree(da);
+    cudaFree(db);
+    return s;
+}
+
+sph_status sph_get_time(sph_ctx *c, double *t, long long *steps, long long *n_particles,
+                        long long *n_deleted) {
+    if (!c) return SPH_ERR_ARG;
+    sph_status s = pull_scalars(c);
+    if (s) return s;
+    if (t) *t = c->hsc->t;
+    if (steps) *steps = c->hsc->step;
+    if (n_deleted) *n_deleted = c->hsc->deleted;
+    if (n_particles) {
+        // dead-marked particles are dropped at the next cell build
+        long long n = c->hsc->n;
+        if (n > 0) {
+            std::vector<unsigned char> ty((size_t)n);
+            CK(copy_sync(c, ty.data(), c->raw[5], (size_t)n, cudaMemcpyDeviceToHost), "download");
+            for (auto v : ty) if (v == T_DEAD) --n;
+        }
+        *n_particles = n;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_kernels_per_step(sph_ctx *c, int *count) {
+    if (!c || !count) return SPH_ERR_ARG;
+    int passes = (c->grid.keybits + 7) / 8;
+    int k = 1 + 3 * passes + 1 + 1;   // hash, sort passes, cell ranges, reorder
+    k += c->prm.sigma > 0 ? 4 : 0;     // colour + normal, twice
+    k += 3;                            // forces (2x) + predict
+    k += 1;                            // spawn / time advance
+    *count = k;
+    return SPH_OK;
+}
+
+}  // extern "C"

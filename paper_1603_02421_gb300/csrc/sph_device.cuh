@@ -1,0 +1,138 @@
+// Device helpers shared by the libsph kernels: kernel functions (Sec. 2-5),
+// Tait EOS (Eq. 26) and the cell-list neighbour walk (Sec. 2-7).
+#pragma once
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float log1p_t(float x) { return log1pf(x); }
+__device__ __forceinline__ double log1p_t(double x) { return log1p(x); }
+__device__ __forceinline__ float expm1_t(float x) { return expm1f(x); }
+__device__ __forceinline__ double expm1_t(double x) { return expm1(x); }
+__device__ __forceinline__ float exp_t(float x) { return expf(x); }
+__device__ __forceinline__ double exp_t(double x) { return exp(x); }
+__device__ __forceinline__ float cospi_t(float x) { return cospif(x); }
+__device__ __forceinline__ double cospi_t(double x) { return cospi(x); }
+__device__ __forceinline__ float abs_t(float x) { return fabsf(x); }
+__device__ __forceinline__ double abs_t(double x) { return fabs(x); }
+
+// Eq. 27 / Eq. 28: W(q) including the 2D normalisation kappa / h^2.
+template <class T> __device__ __forceinline__ T kernel_W(const PhysT<T> &P, T q) {
+    T t = T(2) - q;
+    if (t <= T(0)) return T(0);
+    if (P.kernel == 1) {
+        T t2 = t * t;
+        return P.wn * (T(1) + T(2) * q) * (t2 * t2);
+    }
+    if (q <= T(1)) return P.wn * (T(1) - T(1.5) * q * q + T(0.75) * q * q * q);
+    return P.wn * T(0.25) * t * t * t;
+}
+
+// (1/r) dW/dr, finite at r = 0; grad_a W_ab = F * (r_a - r_b).
+//   Wendland: -10 kappa/h^4 (2-q)^3
+//   cubic:    kappa/h^4 (-3 + 9q/4) for q <= 1, -(3 kappa/4h^4)(2-q)^2 / q above
+template <class T> __device__ __forceinline__ T kernel_F(const PhysT<T> &P, T q) {
+    T t = T(2) - q;
+    if (t <= T(0)) return T(0);
+    if (P.kernel == 1) return P.gn * t * t * t;
+    if (q <= T(1)) return P.gn * (T(-3) + T(2.25) * q);
+    return P.gn * T(-0.75) * t * t / q;
+}
+
+// Eq. 26 with rho = rho0 + drho evaluated as B expm1(gamma log1p(drho/rho0))
+// to keep the small pressure accurate in FP32; c = c0 (rho/rho0)^((gamma-1)/2).
+template <class T>
+__device__ __forceinline__ void eos(const PhysT<T> &P, T drho, T &rho, T &P_over_rho2, T &c) {
+    rho = P.rho0 + drho;
+    T lg = log1p_t(drho * P.inv_rho0);
+    T p = P.B * expm1_t(P.gamma * lg);
+    c = P.c0 * exp_t(P.half_gm1 * lg);
+    P_over_rho2 = p / (rho * rho);
+}
+
+// Exact FP64 distance test, written out so that it matches a plain
+// (dx*dx + dy*dy < r2max) evaluation without fused multiply-add.
+__device__ __forceinline__ bool exact_within(double2 pa, double2 pb, double r2max) {
+    double dx = __dsub_rn(pa.x, pb.x);
+    double dy = __dsub_rn(pa.y, pb.y);
+    double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    return d2 < r2max;
+}
+
+// Cell coordinates from a key.
+__device__ __forceinline__ void key_cell(const Grid &g, uint32_t key, int &cx, int &cy) {
+    cy = (int)(key / (uint32_t)g.ncx);
+    cx = (int)key - cy * g.ncx;
+}
+
+// Cell-relative offsets: x_loc = x - X(cx) + (cx mod 4) sc (so neighbours one
+// cell apart differ by less than 2 sc after wrapping by 4 sc), y_off = y - Y(cy).
+template <class T>
+__device__ __forceinline__ void cell_offsets(const Grid &g, uint32_t key, double2 p, T &xloc,
+                                             T &yoff, double &xo, double &yo) {
+    int cx, cy;
+    key_cell(g, key, cx, cy);
+    xo = p.x - (g.xmin + (double)(cx - 1) * g.sc);
+    yo = p.y - (g.ymin + (double)(cy - 1) * g.sc);
+    xloc = (T)(xo + (double)(cx & 3) * g.sc);
+    yoff = (T)yo;
+}
+
+// Contiguous particle range of the three cells (cx-1..cx+1) of one row.
+__device__ __forceinline__ void row_range(const uint2 *__restrict__ cellSE, int c, unsigned &lo,
+                                          unsigned &hi) {
+    uint2 s0 = __ldg(&cellSE[c - 1]);
+    uint2 s1 = __ldg(&cellSE[c]);
+    uint2 s2 = __ldg(&cellSE[c + 1]);
+    lo = 0xffffffffu;
+    hi = 0u;
+    if (s0.y > s0.x) { lo = s0.x; hi = s0.y; }
+    if (s1.y > s1.x) { lo = min(lo, s1.x); hi = max(hi, s1.y); }
+    if (s2.y > s2.x) { lo = min(lo, s2.x); hi = max(hi, s2.y); }
+}
+
+template <class T> __device__ __forceinline__ T wrap4(const PhysT<T> &P, T rx) {
+    rx = rx > P.two_sc ? rx - P.four_sc : rx;
+    rx = rx < -P.two_sc ? rx + P.four_sc : rx;
+    return rx;
+}
+
+// Visit every particle b != i of the 3x3 cell block of particle i whose FP64
+// distance is below the threshold (r2 in [lo, hi) in T is re-tested exactly
+// in FP64 on the stored positions).  body(b, rx, ry, r2, H0[b]).
+template <class T, class Body>
+__device__ __forceinline__ void for_neighbours(const PhysT<T> &P, const Grid &g,
+                                               const uint2 *__restrict__ cellSE,
+                                               const typename Vec<T>::v4 *__restrict__ H0,
+                                               const double2 *__restrict__ pos, unsigned i,
+                                               uint32_t key, T xa, T ya, T r2lo, T r2hi,
+                                               double r2exact, Body &&body) {
+    int cx, cy;
+    key_cell(g, key, cx, cy);
+    double2 pa = make_double2(0.0, 0.0);
+    bool have_pa = false;
+#pragma unroll 1
+    for (int dy = -1; dy <= 1; ++dy) {
+        unsigned lo, hi;
+        row_range(cellSE, (cy + dy) * g.ncx + cx, lo, hi);
+        T yshift = T(dy) * P.sc;
+#pragma unroll 2
+        for (unsigned b = lo; b < hi; ++b) {
+            typename Vec<T>::v4 hb = H0[b];
+            T rx = wrap4(P, xa - hb.x);
+            T ry = (ya - hb.y) - yshift;
+            T r2 = rx * rx + ry * ry;
+            if (r2 >= r2hi || b == i) continue;
+            if (r2 >= r2lo) {
+                if (!have_pa) { pa = pos[i]; have_pa = true; }
+                if (!exact_within(pa, pos[b], r2exact)) continue;
+            }
+            body(b, rx, ry, r2, hb);
+        }
+    }
+}
+
+}  // namespace sph

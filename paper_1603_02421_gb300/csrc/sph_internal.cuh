@@ -1,0 +1,171 @@
+// Internal device-side declarations of libsph (not part of the C ABI).
+//
+// Data layout in HBM (all arrays sized for the context's capacity):
+//  * "raw" particle state: the integrator's output, in the order of the
+//    last cell sort, plus particles laid by the inflow appended at the end.
+//  * "srt" particle state: raw gathered into cell order by the sort.
+//  * hot per-evaluation records in cell order, read by the pair sweeps with
+//    one vector load per candidate:
+//      H0 = (x_loc, y_off, u, v)  cell-relative position + velocity
+//      H1 = (V, rho, P/rho^2, c)  volume m/rho, density, pressure term, sound speed
+//    plus colour C, normal n and unit normal nhat for the CSF terms.
+//  * positions are FP64 everywhere; pair arithmetic runs in T (float or double).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sph {
+
+constexpr uint8_t T_FLUID = 0, T_BOUNDARY = 1, T_BUFFER = 2, T_DEAD = 0xFF;
+enum ErrBits : unsigned {
+    ERR_NONFINITE = 1u,
+    ERR_SKIN = 2u,
+    ERR_CAPACITY = 4u,
+    ERR_TIMEOUT = 8u,
+    ERR_NODT = 16u
+};
+
+struct __align__(16) f4 { float x, y, z, w; };
+struct __align__(32) d4 { double x, y, z, w; };
+
+template <class T> struct Vec;
+template <> struct Vec<float> { using v2 = float2; using v4 = f4; };
+template <> struct Vec<double> { using v2 = double2; using v4 = d4; };
+
+// Uniform cell grid: cell size sc = 2h + skin; one empty padding cell on each
+// side so the 3x3 block of any occupied cell stays inside the grid.
+struct Grid {
+    double xmin, ymin, xmax, ymax, sc, inv_sc;
+    int ncx, ncy;
+    unsigned ncells, sentinel;   // sentinel key sorts after every cell
+    int keybits;
+};
+
+// Physical constants, converted once to the pair-arithmetic type T.
+template <class T> struct PhysT {
+    int kernel;          // 0 cubic, 1 Wendland
+    int csf;             // sigma > 0
+    int walls;           // boundary particles present
+    T h, inv_h, H2lo, H2hi, R15lo, R15hi;
+    T sc, two_sc, four_sc;
+    T wn, gn;            // kernel factors: W = wn f(q), (1/r) dW/dr = gn g(q)
+    T W0;                // W(0)
+    T rho0, inv_rho0, B, gamma, c0, half_gm1;
+    T alpha_h, eta2, sigma, eps_n;
+    T gx, gy;
+    T wall_A, wall_db, inv_wall_db, wall_h0, inv_wall_h0, two_h, c0_inv;
+    double H2d, R15d;    // exact FP64 thresholds (2h)^2, (1.5h)^2
+    double courant, dt_fixed;
+};
+
+// Inflow of the planar jet.
+struct Inflow {
+    int on;
+    int layers, ny;
+    double x_exit, y0, y1, U, amp, k, phase, dx, m_layer, threshold;
+};
+
+// Device-resident scalars of a context.
+struct Scalars {
+    int n;                        // raw particle count (incl. dead-marked)
+    int nsrt;                     // particles in the current cell order
+    unsigned next_id;
+    unsigned err;                 // ErrBits, sticky
+    unsigned dtmin_f;             // float bits of min_a dt candidate (FP32 path)
+    unsigned pad0;
+    unsigned long long dtmin_d;   // double bits (FP64 path)
+    double dt, t, x_up;
+    long long step, deleted;
+    unsigned long long xmax_key;  // breakup: ordered bits of max x of the jet
+    unsigned detached;            // breakup: particles outside the jet
+    unsigned pair_count;
+};
+
+template <class T> struct State {
+    double2 *pos;
+    typename Vec<T>::v2 *vel;
+    T *drho, *drc;                // density offset rho - rho0 and its Kahan carry
+    T *mass;
+    uint8_t *type;
+    uint32_t *id;
+};
+
+template <class T> struct Hot {
+    typename Vec<T>::v4 *H0, *H1;
+    double2 *pos;                 // FP64 positions of this evaluation
+};
+
+template <class T> struct Csf {
+    T *C;
+    typename Vec<T>::v2 *nhat;    // unit normal, zero where the filter N_a = 0
+    typename Vec<T>::v2 *nvec;    // normal n_a of Eq. 18
+};
+
+struct Boundary {
+    int n;
+    const uint2 *cellSE;          // per-cell [start, end) into the sorted boundary arrays
+    const void *bh;               // Vec<T>::v4 (x_loc, y_off, nx, ny), cell order
+    const double2 *pos;           // FP64 positions, cell order
+};
+
+struct SortBufs {
+    uint32_t *key[2], *val[2];
+    uint32_t *tileHist;
+    int ntiles;
+};
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_BINS = 256;
+
+// ---- launchers (sph_neighbour.cu) ----
+template <class T>
+void launch_hash(const Grid &g, const State<T> &raw, Scalars *sc, uint32_t *key, uint32_t *val,
+                 int cap, cudaStream_t s);
+// Returns the index (0/1) of the buffers holding the sorted result.
+int launch_radix_sort(SortBufs &sb, const Grid &g, Scalars *sc, int cap, cudaStream_t s);
+void launch_cells(const Grid &g, const uint32_t *key, Scalars *sc, uint2 *cellSE, int cap,
+                  cudaStream_t s);
+template <class T>
+void launch_pairs(const PhysT<T> &P, const Grid &g, const Scalars *sc_dev, Scalars *sc,
+                  const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot,
+                  const uint32_t *ids, unsigned *out_a, unsigned *out_b, unsigned cap, int ncap,
+                  cudaStream_t s);
+template <class T>
+void launch_breakup(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *cellSE,
+                    const uint32_t *key, const Hot<T> &hot, const uint8_t *type,
+                    uint32_t *parent, uint8_t *flag, int cap, cudaStream_t s);
+
+// ---- launchers (sph_sweeps.cu) ----
+template <class T>
+void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint32_t *key,
+                    const uint32_t *val, const State<T> &raw, const State<T> &srt,
+                    const Hot<T> &hot, int cap, cudaStream_t s);
+template <class T>
+void launch_colour(const PhysT<T> &P, const Grid &g, const Scalars *sc, const uint2 *cellSE,
+                   const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf, int cap,
+                   cudaStream_t s);
+template <class T>
+void launch_normal(const PhysT<T> &P, const Grid &g, const Scalars *sc, const uint2 *cellSE,
+                   const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf, int cap,
+                   cudaStream_t s);
+// mode 0: evaluate only (store derivatives, copy srt -> raw); mode 1: first
+// evaluation of a step (store derivatives, time-step minimum); mode 2:
+// second evaluation + corrector (write raw).
+template <class T>
+void launch_forces(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars *sc,
+                   const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot,
+                   const Csf<T> &csf, const Boundary &bd, const State<T> &srt,
+                   const State<T> &raw, typename Vec<T>::v2 *acc, T *dr, int cap,
+                   cudaStream_t s);
+template <class T>
+void launch_predict(const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars *sc,
+                    const uint32_t *key, const State<T> &srt, const typename Vec<T>::v2 *acc,
+                    const T *dr, const Hot<T> &half, int cap, cudaStream_t s);
+template <class T>
+void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &raw,
+                  const double *layer_y, int cap, cudaStream_t s);
+
+}  // namespace sph

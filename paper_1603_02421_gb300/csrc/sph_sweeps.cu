@@ -1,0 +1,504 @@
+// Pair sweeps and integrator of libsph (Secs. 2-2 to 2-8 of the paper).
+//
+//  k_reorder   gather raw -> cell order; EOS and hot records of evaluation n
+//  k_colour    C_a = sum_b V_b W_ab, self included                   (Eq. 14)
+//  k_normal    n_a = sum_b V_b (C_b - C_a) grad W; filter N_a; nhat (Eqs. 18, 20, 21)
+//  k_forces    continuity (Eq. 7), momentum with pressure, viscosity,
+//              curvature + CSF, gravity, repulsive walls (Eqs. 9, 10, 23-25,
+//              29); time-step terms (Eqs. 30-31); fused corrector
+//  k_predict   dt (Eq. 32), predictor half step, hot records of evaluation n+1/2
+//  k_spawn     inflow layer laying, time advance
+//
+// One thread per particle in cell order: consecutive threads own spatially
+// adjacent particles, so their 3x3 candidate rows overlap and the vector
+// loads of H0/H1 are served from L1.
+#include "sph_device.cuh"
+
+namespace sph {
+
+template <class T> using V2 = typename Vec<T>::v2;
+template <class T> using V4 = typename Vec<T>::v4;
+
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+
+template <class T> __device__ __forceinline__ V4<T> mk4(T a, T b, T c, T d) {
+    V4<T> r;
+    r.x = a; r.y = b; r.z = c; r.w = d;
+    return r;
+}
+
+__device__ __forceinline__ double inflow_u(const Inflow &f, double t) {
+    return f.U * (1.0 + f.amp * sin(f.k * f.U * t + f.phase));
+}
+
+template <class T>
+__device__ __forceinline__ V4<T> hot1(const PhysT<T> &P, T drho, T mass) {
+    T rho, pr2, c;
+    eos(P, drho, rho, pr2, c);
+    return mk4<T>(mass / rho, rho, pr2, c);
+}
+
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_reorder(PhysT<T> P, Grid g, const Scalars *__restrict__ sc,
+                          const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
+                          State<T> raw, State<T> srt, Hot<T> hot) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc->nsrt) return;
+    uint32_t j = val[i];
+    double2 p = raw.pos[j];
+    V2<T> v = raw.vel[j];
+    T dr = raw.drho[j];
+    T m = raw.mass[j];
+    srt.pos[i] = p;
+    srt.vel[i] = v;
+    srt.drho[i] = dr;
+    srt.drc[i] = raw.drc[j];
+    srt.mass[i] = m;
+    srt.type[i] = raw.type[j];
+    srt.id[i] = raw.id[j];
+    T xl, yo;
+    double xo, yoo;
+    cell_offsets<T>(g, key[i], p, xl, yo, xo, yoo);
+    hot.H0[i] = mk4<T>(xl, yo, v.x, v.y);
+    hot.H1[i] = hot1<T>(P, dr, m);
+}
+
+template <class T>
+void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint32_t *key,
+                    const uint32_t *val, const State<T> &raw, const State<T> &srt,
+                    const Hot<T> &hot, int cap, cudaStream_t s) {
+    k_reorder<T><<<(cap + 255) / 256, 256, 0, s>>>(P, g, sc, key, val, raw, srt, hot);
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 14: colour
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(128)
+k_colour(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, const uint2 *__restrict__ cellSE,
+         const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf) {
+    unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (unsigned)sc->nsrt) return;
+    V4<T> ha = hot.H0[i];
+    T Va = hot.H1[i].x;
+    T sum = Va * P.W0;
+    const V4<T> *__restrict__ H1 = hot.H1;
+    for_neighbours<T>(P, g, cellSE, hot.H0, hot.pos, i, key[i], ha.x, ha.y, P.H2lo, P.H2hi,
+                      P.H2d, [&](unsigned b, T, T, T r2, const V4<T> &) {
+                          T q = sqrt_t(r2) * P.inv_h;
+                          sum += H1[b].x * kernel_W<T>(P, q);
+                      });
+    csf.C[i] = sum;
+}
+
+// ---------------------------------------------------------------------------
+// Eqs. 18, 20, 21: normal, filter, unit normal
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(128)
+k_normal(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, const uint2 *__restrict__ cellSE,
+         const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf) {
+    unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (unsigned)sc->nsrt) return;
+    V4<T> ha = hot.H0[i];
+    T Ca = csf.C[i];
+    T nx = T(0), ny = T(0);
+    const V4<T> *__restrict__ H1 = hot.H1;
+    const T *__restrict__ C = csf.C;
+    for_neighbours<T>(P, g, cellSE, hot.H0, hot.pos, i, key[i], ha.x, ha.y, P.H2lo, P.H2hi,
+                      P.H2d, [&](unsigned b, T rx, T ry, T r2, const V4<T> &) {
+                          T q = sqrt_t(r2) * P.inv_h;
+                          T w = H1[b].x * (C[b] - Ca) * kernel_F<T>(P, q);
+                          nx += w * rx;
+                          ny += w * ry;
+                      });
+    T mag = sqrt_t(nx * nx + ny * ny);
+    V2<T> nh = mk2(T(0), T(0));
+    if (mag > P.eps_n) nh = mk2(nx / mag, ny / mag);
+    csf.nhat[i] = nh;
+    csf.nvec[i] = mk2(nx, ny);
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 29: repulsive wall force per unit mass from the boundary particles in
+// the 3x3 cell block (R(psi) P(xi) eps(z, u_perp) along the wall normal).
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, const Boundary &bd,
+                                            uint32_t key, T xa, T ya, T ua, T va, T y_abs,
+                                            T &ax, T &ay) {
+    int cx, cy;
+    key_cell(g, key, cx, cy);
+    const V4<T> *__restrict__ BH = (const V4<T> *)bd.bh;
+    T ez = T(1);
+    if (P.wall_h0 > T(0)) {
+        T z = y_abs - P.wall_h0;
+        if (z >= T(0)) ez = T(0.02);
+        else if (z > -P.wall_h0) ez = abs_t(z * P.inv_wall_h0) + T(0.02);
+    }
+    for (int dy = -1; dy <= 1; ++dy) {
+        unsigned lo, hi;
+        row_range(bd.cellSE, (cy + dy) * g.ncx + cx, lo, hi);
+        T yshift = T(dy) * P.sc;
+        for (unsigned k = lo; k < hi; ++k) {
+            V4<T> bk = BH[k];
+            T rx = wrap4(P, xa - bk.x);
+            T ry = (ya - bk.y) - yshift;
+            T psi = rx * bk.z + ry * bk.w;
+            T xi = -rx * bk.w + ry * bk.z;
+            if (!(psi > T(0) && psi < P.two_h && abs_t(xi) < P.wall_db)) continue;
+            T q = psi / P.two_h;
+            T R = P.wall_A * (T(1) - q) / sqrt_t(q);
+            T Pf = T(0.5) * (T(1) + cospi_t(xi * P.inv_wall_db));
+            T up = ua * bk.z + va * bk.w;
+            T eu = T(0);
+            if (up < T(0)) {
+                eu = abs_t(T(20) * up) * P.c0_inv;
+                eu = eu > T(1) ? T(1) : eu;
+            }
+            T mag = R * Pf * (ez + eu);
+            ax += mag * bk.z;
+            ay += mag * bk.w;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Eqs. 7, 9, 10, 23-25, 29-31 (+ corrector in mode 2)
+// ---------------------------------------------------------------------------
+template <class T, int MODE>
+__global__ void __launch_bounds__(128)
+k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc,
+         const uint2 *__restrict__ cellSE, const uint32_t *__restrict__ key, Hot<T> hot,
+         Csf<T> csf, Boundary bd, State<T> srt, State<T> raw, V2<T> *__restrict__ acc,
+         T *__restrict__ drout) {
+    unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    int nsrt = sc->nsrt;
+    T dtc = T(3.0e38);   // per-particle time-step candidate (fluid only)
+    bool active = i < (unsigned)nsrt;
+    T ax = T(0), ay = T(0), drho = T(0);
+    uint8_t typ = T_DEAD;
+    if (active) {
+        typ = srt.type[i];
+        if (typ == T_FLUID) {
+            V4<T> ha = hot.H0[i];
+            V4<T> h1a = hot.H1[i];
+            T rhoa = h1a.y, PAa = h1a.z, ca = h1a.w;
+            T ua = ha.z, va = ha.w;
+            V2<T> nha = mk2(T(0), T(0));
+            bool Na = false;
+            if (P.csf) {
+                nha = csf.nhat[i];
+                Na = (nha.x != T(0)) || (nha.y != T(0));
+            }
+            T vmax = T(0), num = T(0), den = T(0);
+            if (Na) den = h1a.x * P.W0;
+            const V4<T> *__restrict__ H1 = hot.H1;
+            const V2<T> *__restrict__ NH = csf.nhat;
+            for_neighbours<T>(
+                P, g, cellSE, hot.H0, hot.pos, i, key[i], ha.x, ha.y, P.H2lo, P.H2hi, P.H2d,
+                [&](unsigned b, T rx, T ry, T r2, const V4<T> &hb) {
+                    V4<T> h1b = H1[b];
+                    T r = sqrt_t(r2);
+                    T q = r * P.inv_h;
+                    T F = kernel_F<T>(P, q);
+                    T du = ua - hb.z, dv = va - hb.w;
+                    T udotr = du * rx + dv * ry;
+                    T mb = h1b.x * h1b.y;
+                    drho += mb * udotr * F;                       // Eq. 7
+                    T Pi = T(0);
+                    if (udotr < T(0)) {                            // Eq. 10
+                        T cbar = T(0.5) * (ca + h1b.w);
+                        T rbar = T(0.5) * (rhoa + h1b.y);
+                        Pi = -P.alpha_h * cbar * udotr / (rbar * (r2 + P.eta2));
+                    }
+                    T coef = mb * (PAa + h1b.z + Pi) * F;          // Eq. 9 / 25
+                    ax -= coef * rx;
+                    ay -= coef * ry;
+                    if (r2 > T(0)) {                               // Eq. 31
+                        T cv = abs_t(P.h * udotr / r2);
+                        vmax = cv > vmax ? cv : vmax;
+                    }
+                    if (Na) {                                      // Eq. 23
+                        V2<T> nb = NH[b];
+                        if (nb.x != T(0) || nb.y != T(0)) {
+                            num += h1b.x * ((nb.x - nha.x) * rx + (nb.y - nha.y) * ry) * F;
+                            den += h1b.x * kernel_W<T>(P, q);
+                        }
+                    }
+                });
+            if (Na && den > T(0)) {                                // Eq. 24
+                T kappa = num / den;
+                V2<T> na = csf.nvec[i];
+                T s = P.sigma / rhoa * kappa;
+                ax -= s * na.x;
+                ay -= s * na.y;
+            }
+            ax += P.gx;
+            ay += P.gy;
+            if (P.walls) {
+                double2 pa = hot.pos[i];
+                wall_forces<T>(P, g, bd, key[i], ha.x, ha.y, ua, va, (T)pa.y, ax, ay);
+            }
+            if (!(isfinite(ax) && isfinite(ay) && isfinite(drho))) atomicOr(&sc->err, ERR_NONFINITE);
+            if (MODE == 1) {                                       // Eqs. 30-31
+                T fa = sqrt_t(ax * ax + ay * ay);
+                T dtf = fa > T(0) ? sqrt_t(P.h / fa) : T(3.0e38);
+                T dtcv = P.h / (ca + vmax);
+                dtc = dtf < dtcv ? dtf : dtcv;
+            }
+        }
+    }
+
+    if (MODE == 0 || MODE == 1) {
+        if (active) {
+            acc[i] = mk2(ax, ay);
+            drout[i] = drho;
+        }
+        if (MODE == 0 && active) {
+            if (i == 0) sc->n = nsrt;
+            raw.pos[i] = srt.pos[i];
+            raw.vel[i] = srt.vel[i];
+            raw.drho[i] = srt.drho[i];
+            raw.drc[i] = srt.drc[i];
+            raw.mass[i] = srt.mass[i];
+            raw.type[i] = srt.type[i];
+            raw.id[i] = srt.id[i];
+        }
+        if (MODE == 1) {
+            // block minimum of the time-step candidates, then one atomic
+            T v = dtc;
+            for (int o = 16; o > 0; o >>= 1) {
+                T w = __shfl_xor_sync(0xffffffffu, v, o);
+                v = w < v ? w : v;
+            }
+            __shared__ T wmin[4];
+            if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                T m = wmin[0];
+                for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = wmin[k] < m ? wmin[k] : m;
+                if (m < T(3.0e38)) {
+                    if (sizeof(T) == 4)
+                        atomicMin(&sc->dtmin_f, __float_as_uint((float)m));
+                    else
+                        atomicMin(&sc->dtmin_d,
+                                  (unsigned long long)__double_as_longlong((double)m));
+                }
+            }
+        }
+        return;
+    }
+
+    // MODE 2: corrector X^{n+1} = X^n + dt Xdot^{n+1/2}, positions with
+    // u* = u^n + dt/2 a^{n+1/2}; buffer particles follow the inflow velocity.
+    if (!active) return;
+    double dt = sc->dt, half = 0.5 * dt, t = sc->t;
+    double2 p0 = srt.pos[i];
+    V2<T> v0 = srt.vel[i];
+    T d0 = srt.drho[i], c0 = srt.drc[i];
+    double2 p1;
+    V2<T> v1;
+    T d1 = d0, c1 = c0;
+    if (typ == T_FLUID) {
+        T th = (T)half, tdt = (T)dt;
+        T usx = v0.x + th * ax, usy = v0.y + th * ay;
+        p1 = make_double2(p0.x + dt * (double)usx, p0.y + dt * (double)usy);
+        v1 = mk2(v0.x + tdt * ax, v0.y + tdt * ay);
+        T y = tdt * drho - c0;          // compensated density update
+        T s = d0 + y;
+        c1 = (s - d0) - y;
+        d1 = s;
+    } else {
+        double uh = inf.on ? inflow_u(inf, t + half) : (double)v0.x;
+        p1 = make_double2(p0.x + dt * uh, p0.y);
+        v1 = mk2((T)(inf.on ? inflow_u(inf, t + dt) : (double)v0.x), T(0));
+        if (inf.on && p1.x >= inf.x_exit) typ = T_FLUID;
+    }
+    if (typ == T_FLUID &&
+        !(p1.x >= g.xmin && p1.x < g.xmax && p1.y >= g.ymin && p1.y < g.ymax)) {
+        typ = T_DEAD;
+        atomicAdd((unsigned long long *)&sc->deleted, 1ull);
+    }
+    raw.pos[i] = p1;
+    raw.vel[i] = v1;
+    raw.drho[i] = d1;
+    raw.drc[i] = c1;
+    raw.mass[i] = srt.mass[i];
+    raw.type[i] = typ;
+    raw.id[i] = srt.id[i];
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 32 + predictor: X^{n+1/2} = X^n + dt/2 Xdot^n; hot records at n+1/2
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_predict(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc,
+                          const uint32_t *__restrict__ key, State<T> srt,
+                          const V2<T> *__restrict__ acc, const T *__restrict__ dr, Hot<T> half) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double dt;
+    if (P.dt_fixed > 0.0) {
+        dt = P.dt_fixed;
+    } else {
+        double m = sizeof(T) == 4 ? (double)__uint_as_float(sc->dtmin_f)
+                                  : __longlong_as_double((long long)sc->dtmin_d);
+        if (!(m < 1.0e37)) {
+            if (i == 0) atomicOr(&sc->err, ERR_NODT);
+            m = 0.0;
+        }
+        dt = P.courant * m;
+    }
+    if (i == 0) sc->dt = dt;
+    if (i >= sc->nsrt) return;
+    double hdt = 0.5 * dt;
+    double2 p = srt.pos[i];
+    V2<T> v = srt.vel[i];
+    T d = srt.drho[i];
+    uint8_t typ = srt.type[i];
+    double2 ph = make_double2(p.x + hdt * (double)v.x, p.y + hdt * (double)v.y);
+    V2<T> vh = v;
+    T dh = d;
+    if (typ == T_FLUID) {
+        V2<T> a = acc[i];
+        T th = (T)hdt;
+        vh = mk2(v.x + th * a.x, v.y + th * a.y);
+        dh = d + th * dr[i];
+    } else if (inf.on) {
+        vh = mk2((T)inflow_u(inf, sc->t + hdt), T(0));
+    }
+    T xl, yo;
+    double xo, yoo;
+    cell_offsets<T>(g, key[i], ph, xl, yo, xo, yoo);
+    // the cell list stays exact while every particle is within skin/2 of its cell
+    double lo = -0.5 * (g.sc - 2.0 * (double)P.h), hi = g.sc - lo;
+    if (!(xo >= lo && xo < hi && yoo >= lo && yoo < hi)) atomicOr(&sc->err, ERR_SKIN);
+    half.pos[i] = ph;
+    half.H0[i] = mk4<T>(xl, yo, vh.x, vh.y);
+    half.H1[i] = hot1<T>(P, dh, srt.mass[i]);
+}
+
+// ---------------------------------------------------------------------------
+// inflow layers + time advance (one block)
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_spawn(Inflow inf, Scalars *__restrict__ sc, State<T> raw,
+                        const double *__restrict__ layer_y, int cap) {
+    __shared__ int do_spawn, base;
+    __shared__ unsigned idbase;
+    __shared__ double xnew, unew;
+    if (threadIdx.x == 0) {
+        double dt = sc->dt, t = sc->t, half = 0.5 * dt;
+        int n = sc->nsrt;
+        do_spawn = 0;
+        if (inf.on) {
+            double uh = inflow_u(inf, t + half);
+            double xs = __dadd_rn(sc->x_up, __dmul_rn(half, uh));
+            double xu = __dsub_rn(__dmul_rn(2.0, xs), sc->x_up);
+            sc->x_up = xu;
+            if (xu >= inf.threshold) {
+                if (n + inf.ny <= cap) {
+                    do_spawn = 1;
+                    base = n;
+                    idbase = sc->next_id;
+                    xnew = __dsub_rn(xu, inf.dx);
+                    unew = inflow_u(inf, t + dt);
+                    sc->x_up = xnew;
+                    sc->next_id += (unsigned)inf.ny;
+                    n += inf.ny;
+                } else {
+                    atomicOr(&sc->err, ERR_CAPACITY);
+                }
+            }
+        }
+        sc->n = n;
+        sc->t = __dadd_rn(t, dt);
+        sc->step += 1;
+        sc->dtmin_f = 0x7f7f7f7fu;
+        sc->dtmin_d = 0x7f7f7f7f7f7f7f7full;
+    }
+    __syncthreads();
+    if (!do_spawn) return;
+    for (int j = threadIdx.x; j < inf.ny; j += blockDim.x) {
+        int k = base + j;
+        raw.pos[k] = make_double2(xnew, layer_y[j]);
+        raw.vel[k] = mk2((T)unew, T(0));
+        raw.drho[k] = T(0);
+        raw.drc[k] = T(0);
+        raw.mass[k] = (T)inf.m_layer;
+        raw.type[k] = T_BUFFER;
+        raw.id[k] = idbase + (unsigned)j;
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <class T>
+void launch_colour(const PhysT<T> &P, const Grid &g, const Scalars *sc, const uint2 *cellSE,
+                   const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf, int cap,
+                   cudaStream_t s) {
+    k_colour<T><<<(cap + 127) / 128, 128, 0, s>>>(P, g, sc, cellSE, key, hot, csf);
+}
+
+template <class T>
+void launch_normal(const PhysT<T> &P, const Grid &g, const Scalars *sc, const uint2 *cellSE,
+                   const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf, int cap,
+                   cudaStream_t s) {
+    k_normal<T><<<(cap + 127) / 128, 128, 0, s>>>(P, g, sc, cellSE, key, hot, csf);
+}
+
+template <class T>
+void launch_forces(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars *sc,
+                   const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot,
+                   const Csf<T> &csf, const Boundary &bd, const State<T> &srt,
+                   const State<T> &raw, V2<T> *acc, T *dr, int cap, cudaStream_t s) {
+    int blocks = (cap + 127) / 128;
+    if (mode == 0)
+        k_forces<T, 0><<<blocks, 128, 0, s>>>(P, g, inf, sc, cellSE, key, hot, csf, bd, srt, raw,
+                                              acc, dr);
+    else if (mode == 1)
+        k_forces<T, 1><<<blocks, 128, 0, s>>>(P, g, inf, sc, cellSE, key, hot, csf, bd, srt, raw,
+                                              acc, dr);
+    else
+        k_forces<T, 2><<<blocks, 128, 0, s>>>(P, g, inf, sc, cellSE, key, hot, csf, bd, srt, raw,
+                                              acc, dr);
+}
+
+template <class T>
+void launch_predict(const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars *sc,
+                    const uint32_t *key, const State<T> &srt, const V2<T> *acc, const T *dr,
+                    const Hot<T> &half, int cap, cudaStream_t s) {
+    k_predict<T><<<(cap + 255) / 256, 256, 0, s>>>(P, g, inf, sc, key, srt, acc, dr, half);
+}
+
+template <class T>
+void launch_spawn(const PhysT<T> &, const Inflow &inf, Scalars *sc, const State<T> &raw,
+                  const double *layer_y, int cap, cudaStream_t s) {
+    k_spawn<T><<<1, 256, 0, s>>>(inf, sc, raw, layer_y, cap);
+}
+
+#define SPH_INST(T)                                                                              \
+    template void launch_reorder<T>(const PhysT<T> &, const Grid &, Scalars *, const uint32_t *, \
+                                    const uint32_t *, const State<T> &, const State<T> &,         \
+                                    const Hot<T> &, int, cudaStream_t);                           \
+    template void launch_colour<T>(const PhysT<T> &, const Grid &, const Scalars *,              \
+                                   const uint2 *, const uint32_t *, const Hot<T> &,               \
+                                   const Csf<T> &, int, cudaStream_t);                            \
+    template void launch_normal<T>(const PhysT<T> &, const Grid &, const Scalars *,              \
+                                   const uint2 *, const uint32_t *, const Hot<T> &,               \
+                                   const Csf<T> &, int, cudaStream_t);                            \
+    template void launch_forces<T>(int, const PhysT<T> &, const Grid &, const Inflow &,          \
+                                   Scalars *, const uint2 *, const uint32_t *, const Hot<T> &,    \
+                                   const Csf<T> &, const Boundary &, const State<T> &,            \
+                                   const State<T> &, V2<T> *, T *, int, cudaStream_t);            \
+    template void launch_predict<T>(const PhysT<T> &, const Grid &, const Inflow &, Scalars *,   \
+                                    const uint32_t *, const State<T> &, const V2<T> *,            \
+                                    const T *, const Hot<T> &, int, cudaStream_t);                \
+    template void launch_spawn<T>(const PhysT<T> &, const Inflow &, Scalars *, const State<T> &, \
+                                  const double *, int, cudaStream_t);
+
+SPH_INST(float)
+SPH_INST(double)
+
+}  // namespace sph

@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 CPU oracle.
+
+Tolerances (fixed in advance, per quantity):
+  neighbour pair sets                      bit-exact (identical FP64 positions)
+  per-evaluation du/dt                     rel-L2 <= 1e-5
+  per-evaluation drho/dt                   rel-L2 <= 1e-5
+  per-step density                         rel-L2 <= 1e-6
+  100-step trajectories r, u, rho          rel-L2 <= 1e-4 (fixed dt)
+  breakup length, same state               exact
+  CSF filter decisions (Eq. 20)            identical outside a 1e-4 band around eps
+FP64 runs are held to 1e-10 where FP32 runs are held to the numbers above.
+"""
+import numpy as np
+import pytest
+
+from paper_1603_02421_gb300 import workloads as wl
+from tests.helpers import ambiguous_mask, oracle_sim, rel_l2, rel_l2_vec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sph():
+    from paper_1603_02421_gb300 import binding, build
+    build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return binding
+
+
+def _case_from_state(params, st, capacity=None):
+    p = dict(params)
+    p["capacity"] = capacity or (len(st["x"]) + 256)
+    return {"params": p, "fluid": st, "boundary": None, "inflow": None}
+
+
+def _tol(prec, fp32):
+    return fp32 if prec == "fp32" else 1e-10
+
+
+# ---------------------------------------------------------------------------
+# neighbour sets (Sec. 2-7)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_pairs_bit_exact_random(sph, orc, prec):
+    st = wl.random_cloud(seed=7, n=5000, box=(2.0, 1.5), dx=0.02)
+    p = wl.test_params(dx=0.02, prec=prec, box=(-0.1, -0.1, 2.1, 1.6))
+    sim = sph.Simulation(_case_from_state(p, st))
+    a, b = sim.pairs(400000)
+    got = np.unique(np.stack([a, b], 1).astype(np.int64), axis=0)
+    d = orc.derive(p)
+    ref = orc.pair_set(st["x"], st["y"], 2.0 * d.h)
+    assert len(got) == len(ref) and np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_pairs_bit_exact_at_support_boundary(sph, orc, prec):
+    # dyadic lattice with h = 0.5: many pairs at exactly 2h = 1.0 (excluded),
+    # plus copies nudged by one ulp either way
+    x, y = wl.lattice(0.0, 0.0, 40, 30, 0.5)
+    x = np.concatenate([x, x[:200] + 1.0 + np.spacing(1.0)])
+    y = np.concatenate([y, y[:200] + 0.25])
+    x[5] = np.nextafter(x[5], 0.0)
+    st = wl._fluid(x, y, dx=0.5)
+    p = wl.test_params(dx=0.5, prec=prec, box=(-2.0, -2.0, 25.0, 18.0))
+    p["h_over_dx"] = 1.0
+    sim = sph.Simulation(_case_from_state(p, st))
+    a, b = sim.pairs(200000)
+    got = np.unique(np.stack([a, b], 1).astype(np.int64), axis=0)
+    ref = orc.pair_set(x, y, 1.0)
+    assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------------------
+# one evaluation (Eqs. 7, 9, 10, 14, 18-26)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("kernel", ["cubic", "wendland"])
+def test_evaluate_patch(sph, orc, prec, kernel):
+    st = wl.jittered_patch(seed=3, nx=70, ny=45, dx=0.02, vel=0.3, drho=0.01)
+    p = wl.test_params(kernel=kernel, dx=0.02, sigma=2.0, alpha=0.3, g=9.81, prec=prec,
+                       box=(-0.5, -0.5, 2.0, 1.5))
+    sim = sph.Simulation(_case_from_state(p, st))
+    sim.evaluate()
+    g = sim.state()
+    d = orc.derive(p)
+    ev = orc.evaluate(d, st, None)
+    assert np.array_equal(g["id"], np.arange(len(st["x"])))
+    amb = ambiguous_mask(orc, d, st, ev)
+    keep = ~amb
+    assert keep.mean() > 0.95
+    assert rel_l2_vec(g["ax"][keep], g["ay"][keep], ev["ax"][keep], ev["ay"][keep]) < _tol(prec, 1e-5)
+    assert rel_l2(g["drho"], ev["drho"]) < _tol(prec, 1e-5)
+    csf = sim.csf(len(st["x"]))
+    assert rel_l2(csf["C"], ev["C"]) < _tol(prec, 1e-6)
+    assert rel_l2_vec(csf["nx"], csf["ny"], ev["nx"], ev["ny"]) < _tol(prec, 1e-5)
+    Ng = np.hypot(csf["nx"], csf["ny"]) > d.eps_n
+    mag = np.hypot(ev["nx"], ev["ny"])
+    clear = np.abs(mag / d.eps_n - 1.0) >= 1e-4
+    assert np.array_equal(Ng[clear], ev["N"][clear].astype(bool))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_evaluate_jet_with_inflow(sph, orc, prec):
+    case = wl.jet(seed=2, dx=1.0 / 20, length=8.0, prec=prec, Re=200, We=20)
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.evaluate()
+    g = sim.state()
+    ev = osim.evaluate()
+    st = osim.st
+    assert np.array_equal(g["id"], st["id"])
+    assert np.array_equal(g["type"], st["type"])
+    amb = ambiguous_mask(orc, osim.d, st, ev)
+    keep = ~amb
+    assert rel_l2_vec(g["ax"][keep], g["ay"][keep], ev["ax"][keep], ev["ay"][keep]) < _tol(prec, 1e-5)
+    assert rel_l2(g["drho"], ev["drho"]) < _tol(prec, 1e-5) or np.abs(ev["drho"]).max() == 0
+
+
+# ---------------------------------------------------------------------------
+# one step and 100-step trajectories (Sec. 2-8)
+# ---------------------------------------------------------------------------
+def _compare_states(g, st, prec, tol_r, tol_u, tol_rho):
+    assert np.array_equal(g["id"], st["id"].astype(np.uint32))
+    assert np.array_equal(g["type"], st["type"])
+    assert rel_l2_vec(g["x"], g["y"], st["x"], st["y"]) < _tol(prec, tol_r)
+    assert rel_l2_vec(g["u"], g["v"], st["u"], st["v"]) < _tol(prec, tol_u)
+    assert rel_l2(g["rho"], st["rho"]) < _tol(prec, tol_rho)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("dt_fixed", [0.0, 2e-4])
+def test_one_step(sph, orc, prec, dt_fixed):
+    st = wl.jittered_patch(seed=9, nx=50, ny=40, dx=0.02, vel=0.3, drho=0.005)
+    p = wl.test_params(dx=0.02, sigma=1.0, alpha=0.2, g=9.81, prec=prec, dt_fixed=dt_fixed,
+                       box=(-0.5, -0.5, 1.5, 1.5))
+    case = _case_from_state(p, st)
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    dt_g = sim.step()
+    dt_o = osim.step()
+    assert dt_g == pytest.approx(dt_o, rel=_tol(prec, 1e-5))
+    g = sim.state()
+    _compare_states(g, osim.st, prec, 1e-6, 1e-5, 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_jet_trajectory_100_steps(sph, orc, prec):
+    case = wl.jet(seed=4, dx=1.0 / 20, length=6.0, prec=prec, Re=200, We=20)
+    case["params"]["dt_fixed"] = 1e-3
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.run(100)
+    osim.run(100)
+    g = sim.state()
+    tg = sim.time()
+    assert tg["steps"] == 100 and tg["t"] == pytest.approx(osim.t, rel=1e-12)
+    assert tg["deleted"] == osim.deleted
+    _compare_states(g, osim.st, prec, 1e-4, 1e-4, 1e-4)
+
+
+def test_dam_break_fp64_trajectory(sph, orc):
+    case = wl.dam_break(seed=1, dx=0.02, prec="fp64")
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.run(200)
+    osim.run(200)
+    g = sim.state()
+    _compare_states(g, osim.st, "fp64", 0, 0, 0)
+
+
+def test_dam_break_fp32_trajectory(sph, orc):
+    case = wl.dam_break(seed=1, dx=0.02, prec="fp32")
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.run(100)
+    osim.run(100)
+    _compare_states(sim.state(), osim.st, "fp32", 1e-4, 1e-4, 1e-4)
+
+
+# ---------------------------------------------------------------------------
+# breakup length (Sec. 3-2)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("gap_factor", [1.49, 1.51, 3.0])
+def test_breakup_planted_gap(sph, orc, gap_factor):
+    dx = 0.01
+    h = 1.3 * dx
+    p = wl.jet_params(Re=100, We=10, dx=dx, length=1.0)
+    p["capacity"] = 4096
+    xs = [0.5 * dx + k * dx for k in range(30)]
+    xg = xs[-1] + gap_factor * h
+    xs += [xg + k * dx for k in range(20)]
+    xs = np.array(xs)
+    st = wl._fluid(xs, np.zeros(len(xs)), dx=dx)
+    case = {"params": p, "fluid": st, "boundary": None,
+            "inflow": dict(x_exit=0.0, y0=-0.5 * dx, y1=0.5 * dx, U=1.0, amp=0.0, k=1.0,
+                           phase=0.0, layers=3)}
+    sim = sph.Simulation(case)
+    L, broken = sim.breakup_length(D=0.1)
+    osim = oracle_sim(orc, case)
+    Lo, bo = osim.breakup_length(D=0.1)
+    assert (L, broken) == (Lo, bo)
+    assert broken == (gap_factor > 1.5)
+
+
+def test_breakup_matches_oracle_on_jet(sph, orc):
+    case = wl.jet(seed=5, dx=1.0 / 20, length=10.0, Re=200, We=20)
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    L, broken = sim.breakup_length()
+    Lo, bo = osim.breakup_length()
+    assert L == Lo and broken == bo
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_empty_state(sph):
+    p = wl.test_params(dx=0.02, g=9.81, dt_fixed=1e-3)
+    case = _case_from_state(p, wl._fluid([], [], dx=0.02), capacity=64)
+    sim = sph.Simulation(case)
+    sim.evaluate()
+    assert len(sim.state()["x"]) == 0
+    assert sim.step() == pytest.approx(1e-3)
+    sim.run(5)
+    assert sim.time()["steps"] == 6
+
+
+def test_single_particle_free_fall(sph):
+    p = wl.test_params(dx=0.02, g=9.81, dt_fixed=1e-3, prec="fp64", box=(-10, -100, 10, 100))
+    case = _case_from_state(p, wl._fluid([0.3], [0.7], [0.25], [1.5], dx=0.02), capacity=8)
+    sim = sph.Simulation(case)
+    sim.run(200)
+    g = sim.state()
+    t = 0.2
+    assert g["x"][0] == pytest.approx(0.3 + 0.25 * t, rel=1e-12)
+    assert g["y"][0] == pytest.approx(0.7 + 1.5 * t - 0.5 * 9.81 * t * t, rel=1e-11)
+
+
+def test_capacity_and_argument_errors(sph):
+    p = wl.test_params(dx=0.02)
+    st = wl.jittered_patch(seed=1, nx=10, ny=10, dx=0.02)
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(_case_from_state(p, st, capacity=50))
+    assert e.value.status == -3
+    bad = dict(st)
+    bad["x"] = bad["x"].copy()
+    bad["x"][3] = 1e9
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(_case_from_state(p, bad))
+    assert e.value.status == -1
+
+
+def test_outflow_deletes_and_inflow_feeds(sph, orc):
+    case = wl.jet(seed=6, dx=1.0 / 10, length=3.0, Re=100, We=10)
+    case["params"]["dt_fixed"] = 5e-3
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.run(300)
+    osim.run(300)
+    tg = sim.time()
+    assert tg["deleted"] == osim.deleted > 0
+    g = sim.state()
+    assert np.array_equal(g["id"], osim.st["id"].astype(np.uint32))

@@ -80,6 +80,11 @@ typedef struct {
     double wall_A_coef;    /* wall force strength A = wall_A_coef * c0^2 / h, Eq. 29 */
     double wall_h0;        /* still-water depth of the eps(z) factor (0: eps(z) = 1) */
     double wall_db_over_dx;/* boundary particle spacing db = wall_db_over_dx * dx   */
+    double u_frame_x, u_frame_y; /* reference velocity: velocities are stored as
+                              u - u_frame (the equations are Galilean invariant, so
+                              any value gives the same results to rounding; the
+                              stream velocity of a jet keeps its small velocity
+                              differences accurate in FP32)                      */
     long long capacity;    /* maximum fluid + buffer particles held at once         */
     long long boundary_capacity; /* maximum boundary particles                      */
     void *cuda_stream;     /* cudaStream_t to issue work on, or NULL                */

@@ -46,6 +46,7 @@ class sph_params(ctypes.Structure):
                 ("xmax", ctypes.c_double), ("ymax", ctypes.c_double),
                 ("skin_over_h", ctypes.c_double), ("wall_A_coef", ctypes.c_double),
                 ("wall_h0", ctypes.c_double), ("wall_db_over_dx", ctypes.c_double),
+                ("u_frame_x", ctypes.c_double), ("u_frame_y", ctypes.c_double),
                 ("capacity", ctypes.c_longlong), ("boundary_capacity", ctypes.c_longlong),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
 
@@ -124,6 +125,7 @@ def make_params(p: dict, capacity=None, boundary_capacity=0, stream=None, device
         xmin=p["xmin"], ymin=p["ymin"], xmax=p["xmax"], ymax=p["ymax"],
         skin_over_h=p.get("skin_over_h", 0.2), wall_A_coef=p.get("wall_A_coef", 0.01),
         wall_h0=p.get("wall_h0", 0.0), wall_db_over_dx=p.get("wall_db_over_dx", 0.5),
+        u_frame_x=p.get("u_frame_x", 0.0), u_frame_y=p.get("u_frame_y", 0.0),
         capacity=cap, boundary_capacity=int(boundary_capacity),
         cuda_stream=stream, device=int(device))
 

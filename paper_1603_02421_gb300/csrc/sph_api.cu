@@ -159,8 +159,6 @@ template <class T> static PhysT<T> make_phys(const sph_params &p, const Grid &g,
     P.H2d = H2;
     P.R15d = R2;
     P.sc = (T)g.sc;
-    P.two_sc = (T)(2.0 * g.sc);
-    P.four_sc = (T)(4.0 * g.sc);
     P.wn = (T)(kap / (h * h));
     P.gn = (T)(p.kernel == SPH_KERNEL_CUBIC ? kap / (h * h * h * h) : -10.0 * kap / (h * h * h * h));
     P.W0 = (T)(p.kernel == SPH_KERNEL_CUBIC ? kap / (h * h) : 16.0 * kap / (h * h));
@@ -183,6 +181,10 @@ template <class T> static PhysT<T> make_phys(const sph_params &p, const Grid &g,
     P.inv_wall_h0 = (T)(p.wall_h0 > 0.0 ? 1.0 / p.wall_h0 : 0.0);
     P.two_h = (T)(2.0 * h);
     P.c0_inv = (T)(1.0 / p.c0);
+    P.ufx = (T)p.u_frame_x;
+    P.ufy = (T)p.u_frame_y;
+    P.ufx_d = p.u_frame_x;
+    P.ufy_d = p.u_frame_y;
     P.courant = p.courant;
     P.dt_fixed = p.dt_fixed;
     return P;
@@ -332,7 +334,7 @@ static sph_status upload_boundary(sph_ctx *c) {
         int cy = (int)(kk / (uint32_t)c->grid.ncx), cx = (int)kk - cy * c->grid.ncx;
         double xo = c->bx[k] - (c->grid.xmin + (double)(cx - 1) * c->grid.sc);
         double yo = c->by[k] - (c->grid.ymin + (double)(cy - 1) * c->grid.sc);
-        hd[4 * r + 0] = xo + (double)(cx & 3) * c->grid.sc;
+        hd[4 * r + 0] = xo;
         hd[4 * r + 1] = yo;
         hd[4 * r + 2] = c->bnx[k];
         hd[4 * r + 3] = c->bny[k];
@@ -366,12 +368,13 @@ static sph_status upload_particles(sph_ctx *c, long long at, long long n, const 
     for (long long i = 0; i < n; ++i) {
         double d = rho[i] - c->prm.rho0;
         if (ts == 4) {
-            float f2[2] = {(float)u[i], (float)v[i]}, fd = (float)d, fm = (float)mass[i];
+            float f2[2] = {(float)(u[i] - c->prm.u_frame_x), (float)(v[i] - c->prm.u_frame_y)},
+                  fd = (float)d, fm = (float)mass[i];
             memcpy(&vel[2 * i * ts], f2, 8);
             memcpy(&drho[i * ts], &fd, 4);
             memcpy(&m[i * ts], &fm, 4);
         } else {
-            double d2[2] = {u[i], v[i]};
+            double d2[2] = {u[i] - c->prm.u_frame_x, v[i] - c->prm.u_frame_y};
             memcpy(&vel[2 * i * ts], d2, 16);
             memcpy(&drho[i * ts], &d, 8);
             memcpy(&m[i * ts], &mass[i], 8);
@@ -434,6 +437,8 @@ sph_status sph_init(const sph_params *p, sph_ctx **out) {
         return fail(nullptr, SPH_ERR_ARG, "capacity must lie in [1, 2^30]");
     if (!(q.boundary_capacity >= 0 && q.boundary_capacity <= (1ll << 26)))
         return fail(nullptr, SPH_ERR_ARG, "boundary_capacity must lie in [0, 2^26]");
+    if (!(std::isfinite(q.u_frame_x) && std::isfinite(q.u_frame_y)))
+        return fail(nullptr, SPH_ERR_ARG, "u_frame must be finite");
     if (!(q.wall_A_coef >= 0 && q.wall_h0 >= 0 && q.wall_db_over_dx > 0))
         return fail(nullptr, SPH_ERR_ARG, "wall parameters out of range");
     double h = q.h_over_dx * q.dx, skin = q.skin_over_h * h;
@@ -757,8 +762,8 @@ sph_status sph_get_state(sph_ctx *c, long long cap, long long *n_out, double *x,
             bool has = (long long)i < c->n_eval;
             if (x) x[r] = pos[i].x;
             if (y) y[r] = pos[i].y;
-            if (u) u[r] = rd(c, vel, i, 0, 2);
-            if (v) v[r] = rd(c, vel, i, 1, 2);
+            if (u) u[r] = c->prm.u_frame_x + rd(c, vel, i, 0, 2);
+            if (v) v[r] = c->prm.u_frame_y + rd(c, vel, i, 1, 2);
             if (rho) rho[r] = c->prm.rho0 + rd(c, dr, i, 0, 1);
             if (mass) mass[r] = rd(c, m, i, 0, 1);
             if (type) type[r] = ty[i];

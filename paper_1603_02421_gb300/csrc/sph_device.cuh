@@ -68,41 +68,49 @@ __device__ __forceinline__ void key_cell(const Grid &g, uint32_t key, int &cx, i
     cx = (int)key - cy * g.ncx;
 }
 
-// Cell-relative offsets: x_loc = x - X(cx) + (cx mod 4) sc (so neighbours one
-// cell apart differ by less than 2 sc after wrapping by 4 sc), y_off = y - Y(cy).
+// Cell-relative offsets x - X(cx), y - Y(cy) of the particle's own cell.
 template <class T>
-__device__ __forceinline__ void cell_offsets(const Grid &g, uint32_t key, double2 p, T &xloc,
+__device__ __forceinline__ void cell_offsets(const Grid &g, uint32_t key, double2 p, T &xoff,
                                              T &yoff, double &xo, double &yo) {
     int cx, cy;
     key_cell(g, key, cx, cy);
     xo = p.x - (g.xmin + (double)(cx - 1) * g.sc);
     yo = p.y - (g.ymin + (double)(cy - 1) * g.sc);
-    xloc = (T)(xo + (double)(cx & 3) * g.sc);
+    xoff = (T)xo;
     yoff = (T)yo;
 }
 
-// Contiguous particle range of the three cells (cx-1..cx+1) of one row.
-__device__ __forceinline__ void row_range(const uint2 *__restrict__ cellSE, int c, unsigned &lo,
-                                          unsigned &hi) {
+// Particle range of the three cells (cx-1, cx, cx+1) of one row.  Cells of a
+// row are contiguous in the sorted order, so the range is [lo, hi) with the
+// cell cx-1 part below b1 and the cell cx+1 part from b2 on.
+struct RowRange {
+    unsigned lo, b1, b2, hi;
+};
+
+__device__ __forceinline__ RowRange row_range(const uint2 *__restrict__ cellSE, int c) {
     uint2 s0 = __ldg(&cellSE[c - 1]);
     uint2 s1 = __ldg(&cellSE[c]);
     uint2 s2 = __ldg(&cellSE[c + 1]);
-    lo = 0xffffffffu;
-    hi = 0u;
-    if (s0.y > s0.x) { lo = s0.x; hi = s0.y; }
-    if (s1.y > s1.x) { lo = min(lo, s1.x); hi = max(hi, s1.y); }
-    if (s2.y > s2.x) { lo = min(lo, s2.x); hi = max(hi, s2.y); }
+    bool e0 = s0.y > s0.x, e1 = s1.y > s1.x, e2 = s2.y > s2.x;
+    RowRange r;
+    r.lo = e0 ? s0.x : (e1 ? s1.x : (e2 ? s2.x : 0u));
+    r.hi = e2 ? s2.y : (e1 ? s1.y : (e0 ? s0.y : 0u));
+    r.b1 = e0 ? s0.y : r.lo;
+    r.b2 = e2 ? s2.x : r.hi;
+    return r;
 }
 
-template <class T> __device__ __forceinline__ T wrap4(const PhysT<T> &P, T rx) {
-    rx = rx > P.two_sc ? rx - P.four_sc : rx;
-    rx = rx < -P.two_sc ? rx + P.four_sc : rx;
-    return rx;
+// x-shift (cx_a - cx_b) * sc of candidate b of a row range.
+template <class T>
+__device__ __forceinline__ T row_shift(const RowRange &rr, unsigned b, T sc) {
+    return b < rr.b1 ? sc : (b < rr.b2 ? T(0) : -sc);
 }
 
 // Visit every particle b != i of the 3x3 cell block of particle i whose FP64
-// distance is below the threshold (r2 in [lo, hi) in T is re-tested exactly
-// in FP64 on the stored positions).  body(b, rx, ry, r2, H0[b]).
+// distance is below the threshold.  Squared distances in T inside [lo, hi)
+// are re-tested exactly in FP64 on the stored positions, so the visited set
+// is exactly {b : |r_a - r_b|^2 < r2exact} of the FP64 positions.
+// body(b, rx, ry, r2, H0[b]) with (rx, ry) = r_a - r_b.
 template <class T, class Body>
 __device__ __forceinline__ void for_neighbours(const PhysT<T> &P, const Grid &g,
                                                const uint2 *__restrict__ cellSE,
@@ -116,13 +124,12 @@ __device__ __forceinline__ void for_neighbours(const PhysT<T> &P, const Grid &g,
     bool have_pa = false;
 #pragma unroll 1
     for (int dy = -1; dy <= 1; ++dy) {
-        unsigned lo, hi;
-        row_range(cellSE, (cy + dy) * g.ncx + cx, lo, hi);
+        RowRange rr = row_range(cellSE, (cy + dy) * g.ncx + cx);
         T yshift = T(dy) * P.sc;
 #pragma unroll 2
-        for (unsigned b = lo; b < hi; ++b) {
+        for (unsigned b = rr.lo; b < rr.hi; ++b) {
             typename Vec<T>::v4 hb = H0[b];
-            T rx = wrap4(P, xa - hb.x);
+            T rx = (xa - hb.x) + row_shift<T>(rr, b, P.sc);
             T ry = (ya - hb.y) - yshift;
             T r2 = rx * rx + ry * ry;
             if (r2 >= r2hi || b == i) continue;

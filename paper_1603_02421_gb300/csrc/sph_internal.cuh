@@ -6,7 +6,8 @@
 //  * "srt" particle state: raw gathered into cell order by the sort.
 //  * hot per-evaluation records in cell order, read by the pair sweeps with
 //    one vector load per candidate:
-//      H0 = (x_loc, y_off, u, v)  cell-relative position + velocity
+//      H0 = (x_off, y_off, u', v')  offset in the particle's cell, velocity
+//                                   relative to the frame u_frame
 //      H1 = (V, rho, P/rho^2, c)  volume m/rho, density, pressure term, sound speed
 //    plus colour C, normal n and unit normal nhat for the CSF terms.
 //  * positions are FP64 everywhere; pair arithmetic runs in T (float or double).
@@ -48,15 +49,17 @@ template <class T> struct PhysT {
     int csf;             // sigma > 0
     int walls;           // boundary particles present
     T h, inv_h, H2lo, H2hi, R15lo, R15hi;
-    T sc, two_sc, four_sc;
+    T sc;
     T wn, gn;            // kernel factors: W = wn f(q), (1/r) dW/dr = gn g(q)
     T W0;                // W(0)
     T rho0, inv_rho0, B, gamma, c0, half_gm1;
     T alpha_h, eta2, sigma, eps_n;
     T gx, gy;
     T wall_A, wall_db, inv_wall_db, wall_h0, inv_wall_h0, two_h, c0_inv;
+    T ufx, ufy;          // velocity frame: stored velocities are u - u_frame
     double H2d, R15d;    // exact FP64 thresholds (2h)^2, (1.5h)^2
     double courant, dt_fixed;
+    double ufx_d, ufy_d;
 };
 
 // Inflow of the planar jet.

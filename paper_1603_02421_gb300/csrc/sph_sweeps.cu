@@ -139,12 +139,11 @@ __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, co
         else if (z > -P.wall_h0) ez = abs_t(z * P.inv_wall_h0) + T(0.02);
     }
     for (int dy = -1; dy <= 1; ++dy) {
-        unsigned lo, hi;
-        row_range(bd.cellSE, (cy + dy) * g.ncx + cx, lo, hi);
+        RowRange rr = row_range(bd.cellSE, (cy + dy) * g.ncx + cx);
         T yshift = T(dy) * P.sc;
-        for (unsigned k = lo; k < hi; ++k) {
+        for (unsigned k = rr.lo; k < rr.hi; ++k) {
             V4<T> bk = BH[k];
-            T rx = wrap4(P, xa - bk.x);
+            T rx = (xa - bk.x) + row_shift<T>(rr, k, P.sc);
             T ry = (ya - bk.y) - yshift;
             T psi = rx * bk.z + ry * bk.w;
             T xi = -rx * bk.w + ry * bk.z;
@@ -152,7 +151,7 @@ __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, co
             T q = psi / P.two_h;
             T R = P.wall_A * (T(1) - q) / sqrt_t(q);
             T Pf = T(0.5) * (T(1) + cospi_t(xi * P.inv_wall_db));
-            T up = ua * bk.z + va * bk.w;
+            T up = (ua + P.ufx) * bk.z + (va + P.ufy) * bk.w;
             T eu = T(0);
             if (up < T(0)) {
                 eu = abs_t(T(20) * up) * P.c0_inv;
@@ -305,16 +304,16 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc,
     if (typ == T_FLUID) {
         T th = (T)half, tdt = (T)dt;
         T usx = v0.x + th * ax, usy = v0.y + th * ay;
-        p1 = make_double2(p0.x + dt * (double)usx, p0.y + dt * (double)usy);
+        p1 = make_double2(p0.x + dt * (P.ufx_d + (double)usx), p0.y + dt * (P.ufy_d + (double)usy));
         v1 = mk2(v0.x + tdt * ax, v0.y + tdt * ay);
         T y = tdt * drho - c0;          // compensated density update
         T s = d0 + y;
         c1 = (s - d0) - y;
         d1 = s;
     } else {
-        double uh = inf.on ? inflow_u(inf, t + half) : (double)v0.x;
+        double uh = inf.on ? inflow_u(inf, t + half) : P.ufx_d + (double)v0.x;
         p1 = make_double2(p0.x + dt * uh, p0.y);
-        v1 = mk2((T)(inf.on ? inflow_u(inf, t + dt) : (double)v0.x), T(0));
+        v1 = inf.on ? mk2((T)(inflow_u(inf, t + dt) - P.ufx_d), (T)(-P.ufy_d)) : v0;
         if (inf.on && p1.x >= inf.x_exit) typ = T_FLUID;
     }
     if (typ == T_FLUID &&
@@ -358,7 +357,7 @@ __global__ void k_predict(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ 
     V2<T> v = srt.vel[i];
     T d = srt.drho[i];
     uint8_t typ = srt.type[i];
-    double2 ph = make_double2(p.x + hdt * (double)v.x, p.y + hdt * (double)v.y);
+    double2 ph = make_double2(p.x + hdt * (P.ufx_d + (double)v.x), p.y + hdt * (P.ufy_d + (double)v.y));
     V2<T> vh = v;
     T dh = d;
     if (typ == T_FLUID) {
@@ -367,7 +366,7 @@ __global__ void k_predict(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ 
         vh = mk2(v.x + th * a.x, v.y + th * a.y);
         dh = d + th * dr[i];
     } else if (inf.on) {
-        vh = mk2((T)inflow_u(inf, sc->t + hdt), T(0));
+        vh = mk2((T)(inflow_u(inf, sc->t + hdt) - P.ufx_d), (T)(-P.ufy_d));
     }
     T xl, yo;
     double xo, yoo;
@@ -384,8 +383,8 @@ __global__ void k_predict(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ 
 // inflow layers + time advance (one block)
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_spawn(Inflow inf, Scalars *__restrict__ sc, State<T> raw,
-                        const double *__restrict__ layer_y, int cap) {
+__global__ void k_spawn(Inflow inf, double ufx, double ufy, Scalars *__restrict__ sc,
+                        State<T> raw, const double *__restrict__ layer_y, int cap) {
     __shared__ int do_spawn, base;
     __shared__ unsigned idbase;
     __shared__ double xnew, unew;
@@ -424,7 +423,7 @@ __global__ void k_spawn(Inflow inf, Scalars *__restrict__ sc, State<T> raw,
     for (int j = threadIdx.x; j < inf.ny; j += blockDim.x) {
         int k = base + j;
         raw.pos[k] = make_double2(xnew, layer_y[j]);
-        raw.vel[k] = mk2((T)unew, T(0));
+        raw.vel[k] = mk2((T)(unew - ufx), (T)(-ufy));
         raw.drho[k] = T(0);
         raw.drc[k] = T(0);
         raw.mass[k] = (T)inf.m_layer;
@@ -473,9 +472,9 @@ void launch_predict(const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars
 }
 
 template <class T>
-void launch_spawn(const PhysT<T> &, const Inflow &inf, Scalars *sc, const State<T> &raw,
+void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &raw,
                   const double *layer_y, int cap, cudaStream_t s) {
-    k_spawn<T><<<1, 256, 0, s>>>(inf, sc, raw, layer_y, cap);
+    k_spawn<T><<<1, 256, 0, s>>>(inf, P.ufx_d, P.ufy_d, sc, raw, layer_y, cap);
 }
 
 #define SPH_INST(T)                                                                              \

@@ -152,7 +152,7 @@ def jet_params(Re, We, D=1.0, U=1.0, rho0=1000.0, dx=None, kernel="wendland",
                 eps_n_times_h=0.01, gx=0.0, gy=0.0, courant=0.2, dt_fixed=0.0,
                 xmin=-(layers + 5) * dx, ymin=-half_width * D, xmax=length * D,
                 ymax=half_width * D, skin_over_h=0.2, wall_A_coef=0.01, wall_h0=0.0,
-                wall_db_over_dx=0.5)
+                wall_db_over_dx=0.5, u_frame_x=U, u_frame_y=0.0)
 
 
 def jet(seed=0, Re=200.0, We=20.0, D=1.0, U=1.0, rho0=1000.0, dx=None,

@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the WCSPH hot path on GB300: SPH particle-steps/s.
+
+One step = one full pass of the method over the whole particle set: cell
+hash + radix sort + cell ranges + reorder, two evaluations (colour, normal,
+forces) with the predictor-corrector update in between, inflow/outflow, and
+(every 100 steps) the breakup-length evaluation.
+
+Default workload (N = 1): the 2D planar jet, Re = 200, We = 20, Wendland
+kernel, dx = D/40, 60 D domain (~96k particles), FP32 pair sums with FP64
+positions and time, adaptive dt (Eqs. 30-32).  Inputs are seeded synthetic
+states (workloads.py).  Between timed steps the L2 cache is flushed by writing
+a 256 MiB buffer (outside the timed events).
+
+Usage:
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload jet_c2|jet_c3|dam_c1]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
+Under torchrun each rank simulates its own jet (seed = rank): weak scaling,
+no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1603_02421_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "SPH particle-steps/s on 1 GB300, plain vs batched/surrogate, at fixed error"
+UNIT = "particle-steps/s"
+BREAKUP_EVERY = 100
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload(name: str, seed: int):
+    if name == "jet_c2":
+        case = wl.jet(seed=seed, Re=200.0, We=20.0, dx=1.0 / 40, length=60.0,
+                      kernel="wendland", prec="fp32")
+        desc = ("2D planar jet, Re=200, We=20, Wendland, dx=D/40, 60D domain, "
+                "FP32 pair sums / FP64 positions, adaptive dt")
+    elif name == "jet_c3":
+        case = wl.jet(seed=seed, Re=100.0, We=10.0, dx=1.0 / 100, length=100.0,
+                      kernel="wendland", prec="fp32", capacity_factor=1.15)
+        desc = ("2D planar jet, Re=100, We=10, Wendland, dx=D/100, 100D domain, "
+                "FP32 pair sums / FP64 positions, adaptive dt")
+    elif name == "dam_c1":
+        case = wl.dam_break(seed=seed, dx=0.01, prec="fp64")
+        desc = "2D dam break with obstacle, cubic spline, dx=0.01 m, FP64, dt=1e-4"
+    else:
+        raise SystemExit("unknown workload %s" % name)
+    return case, desc
+
+
+# Algorithmic FP32 operations per interacting pair (r < 2h) of each pair
+# sweep, counting a fused multiply-add as 2, sqrt and division as 1 each.
+# The derivation is listed in the design doc.
+FLOP_PER_PAIR = {"colour": 16, "normal": 18, "forces": 62, "forces_correct": 62}
+FLOP_PER_PARTICLE = {"colour": 2, "normal": 8, "forces": 30, "forces_correct": 40}
+# Algorithmic HBM bytes per particle of the streaming kernels (FP32 path).
+BYTES_PER_PARTICLE = {"hash": 16 + 1 + 8, "reorder": 2 * 41 + 8 + 32,
+                      "predict": 41 + 12 + 48, "cell_ranges": 4 + 8}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="jet_c2", choices=["jet_c2", "jet_c3", "dam_c1"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(case, max_particles=24000):
+    """A bounded sample of the workload for the CPU oracle: the upstream part
+    of the jet (all particles with x below a cut chosen so that at most
+    max_particles remain), with its inflow."""
+    st = case["fluid"]
+    x = st["x"]
+    if len(x) > max_particles:
+        cut = np.sort(x)[max_particles]
+        keep = x < cut
+        st = {k: v[keep] for k, v in st.items()}
+        p = dict(case["params"])
+        p["xmax"] = float(cut)
+        case = dict(case, fluid=st, params=p)
+    return case
+
+
+def run_oracle(case, seconds, max_steps=None):
+    from oracle import oracle as orc
+    orc.build()
+    sim = orc.OracleSim(case["params"], case["fluid"], case.get("boundary"))
+    inf = case.get("inflow")
+    if inf is not None:
+        sim.add_inflow(inf["x_exit"], inf["y0"], inf["y1"], inf["U"], inf["amp"], inf["k"],
+                       inf["phase"], inf["layers"])
+    psteps = 0
+    nsteps = 0
+    t0 = time.perf_counter()
+    while True:
+        n = len(sim.st["x"])
+        sim.step()
+        psteps += n
+        nsteps += 1
+        el = time.perf_counter() - t0
+        if (max_steps is not None and nsteps >= max_steps) or \
+                (max_steps is None and el >= seconds):
+            break
+    return psteps, nsteps, time.perf_counter() - t0, len(sim.st["x"])
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    case, desc = workload(args.workload, seed=0)
+    sample = oracle_sample(case)
+    run_oracle(sample, 0, max_steps=max(args.warmup, 0) or 1)
+    psteps, nsteps, el, n = run_oracle(sample, 0, max_steps=args.steps)
+    v = psteps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / nsteps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload + ": " + desc, "particles": n,
+                   "sample": "upstream %d particles of the workload" % n},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "FP64 CPU oracle, %d steps of the upstream %d particles"
+                                   % (nsteps, n)},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, val in zip(names, r[2:]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1603_02421_gb300 import binding, build
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+
+    case, desc = workload(args.workload, seed=rank)
+    stream = torch.cuda.Stream(device=dev)
+    sim = binding.Simulation(case, stream=stream.cuda_stream, device=local)
+    ctx = sim.ctx
+    per_step, per_breakup = binding.sph_kernel_counts(ctx)
+    has_inflow = case.get("inflow") is not None
+
+    # interacting pairs of the initial state (for the algorithmic FLOP count)
+    n0 = binding.sph_get_time(ctx)["n"]
+    pa, _ = binding.sph_get_pairs(ctx, int(n0 * 40))
+    pairs_per_particle = len(pa) / max(n0, 1)
+    del pa
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 0)):
+        binding.sph_run_async(ctx, 1)
+        binding.sph_sync(ctx)
+    binding.sph_profile(ctx, 1)
+    binding.sph_run_async(ctx, 1)       # capture the step graph with timing events
+    binding.sph_sync(ctx)
+    binding.sph_profile(ctx, 1)         # reset totals
+
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    nact = np.zeros(K, np.int64)
+    nbreak = 0
+    Ls = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    t_wall0 = time.perf_counter()
+    for k in range(K):
+        nact[k] = binding.sph_get_time(ctx)["n"] if k == 0 else nact[k - 1]
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev0[k].record(stream)
+        binding.sph_run_async(ctx, 1)
+        if has_inflow and (k + 1) % BREAKUP_EVERY == 0:
+            Ls.append(binding.sph_breakup_length(ctx)[0])
+            nbreak += 1
+        ev1[k].record(stream)
+        binding.sph_sync(ctx)
+        if (k + 1) % 50 == 0 or k == K - 1:
+            nact[k] = binding.sph_get_time(ctx)["n"]
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = np.array([ev0[k].elapsed_time(ev1[k]) for k in range(K)])
+    # particle count per step: piecewise constant between samples
+    for k in range(1, K):
+        if nact[k] == 0:
+            nact[k] = nact[k - 1]
+    total_s = step_ms.sum() / 1e3
+    units = float(nact.sum())
+    if dist is not None:
+        t = torch.tensor([total_s, units], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_s = float(tmax[0])
+        units = float(t[1])
+        dist.barrier()
+    value = units / total_s
+
+    prof = binding.sph_profile_report(ctx)
+    binding.sph_profile(ctx, 0)
+
+    # ---- roofline of the dominant kernel group --------------------------
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    avg_s = dom_ms / 1e3 / max(dom_launches, 1)
+    n_mean = float(nact.mean())
+    sm_mhz = clk["sm_mhz"] if clk else 1900.0
+    if dom in FLOP_PER_PAIR:
+        flops = n_mean * (pairs_per_particle * FLOP_PER_PAIR[dom] + FLOP_PER_PARTICLE[dom])
+        achieved = flops / avg_s / 1e12
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (median SM clock "
+                               "sampled during the timed region)" % sm_mhz,
+                "algorithmic_per_launch": flops}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        nbytes = n_mean * BYTES_PER_PARTICLE.get(dom, 0)
+        achieved = nbytes / avg_s / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "algorithmic_per_launch": nbytes}
+
+    # ---- end to end through the public API with host buffers -------------
+    e2e = None
+    if rank == 0:
+        e2e = end_to_end(binding, case, stream, local, K=min(K, 100))
+
+    # ---- CPU baseline (oracle) on a bounded sample -----------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = oracle_sample(case)
+        psteps, nsteps, el, n = run_oracle(sample, args.cpu_seconds)
+        cpu = {"value": psteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 CPU oracle (single thread), %d steps of the upstream %d "
+                         "particles of the same workload, %.1f s" % (nsteps, n, el)}
+
+    launches = K * per_step + nbreak * per_breakup
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload + ": " + desc,
+                       "particles_mean": n_mean, "parallelism": "replicas (one jet per GPU)",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "breakup_every": BREAKUP_EVERY if has_inflow else None,
+                       "pairs_per_particle": pairs_per_particle,
+                       "wall_s": wall},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "kernel_ms_per_step": {k: v[0] / max(v[1], 1) * (2 if k in ("colour", "normal") else 1)
+                                   for k, v in prof.items()},
+            "breakup_L_over_D": Ls,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def end_to_end(binding, case, stream, local, K):
+    """Particle-steps/s through the public C ABI with host buffers: upload the
+    state from pinned host memory (sph_set_state), K x sph_step (each reads
+    the step's dt back to the host), download the state (sph_get_state)."""
+    import torch
+    sim = binding.Simulation(case, stream=stream.cuda_stream, device=local)
+    ctx = sim.ctx
+    st = binding.sph_get_state(ctx)
+    n = len(st["x"])
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
+              for k, v in st.items()}
+    binding.sph_step(ctx)              # warm (graph-free path)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    binding.sph_set_state(ctx, pinned)
+    for _ in range(K):
+        binding.sph_step(ctx)
+    psteps = n * K
+    out = binding.sph_get_state(ctx)
+    el = time.perf_counter() - t0
+    sim.close()
+    h2d = n * (16 + 8 + 4 + 4 + 4 + 1 + 4)
+    d2h_state = len(out["x"]) * (16 + 8 + 4 + 4 + 1 + 4 + 8 + 4)
+    scal = 96
+    return {"value": psteps / el, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / K,
+            "d2h_bytes_per_step": scal + d2h_state / K,
+            "how": "sph_set_state from pinned host arrays, %d x sph_step (dt read back "
+                   "each step), sph_get_state; host wall clock" % K}
+
+
+if __name__ == "__main__":
+    main()

@@ -182,8 +182,30 @@ sph_status sph_get_pairs(sph_ctx *ctx, long long cap, unsigned *id_a, unsigned *
 sph_status sph_get_time(sph_ctx *ctx, double *t, long long *steps, long long *n_particles,
                         long long *n_deleted);
 
-/* Number of device kernels one sph_step launches at the current settings. */
-sph_status sph_kernels_per_step(sph_ctx *ctx, int *count);
+/* Enqueue nsteps steps (CUDA-graph replay) on the context's stream and return
+ * without waiting.  Device-side errors surface at the next synchronising call
+ * (sph_sync, sph_step, sph_get_*). */
+sph_status sph_run_async(sph_ctx *ctx, long long nsteps);
+
+/* Wait for all work enqueued on the context's stream and report device-side
+ * errors of the steps it ran. */
+sph_status sph_sync(sph_ctx *ctx);
+
+/* Per-kernel timing.  enable = 1 records a CUDA event before each kernel
+ * group of every later step (the step graph is re-captured with the events);
+ * each synchronising call then adds the durations of the most recent step to
+ * running totals, which enable (0 or 1) resets. */
+sph_status sph_profile(sph_ctx *ctx, int enable);
+
+/* Totals per kernel group: names[k] (library-owned strings, valid until the
+ * next sph_profile_report), total_ms[k], launches[k]; *n receives the number
+ * of groups (SPH_ERR_CAPACITY if > cap).  Output arrays may be NULL. */
+sph_status sph_profile_report(sph_ctx *ctx, int cap, int *n, const char **names,
+                              double *total_ms, long long *launches);
+
+/* Number of device kernels (memsets excluded) one step and one breakup-length
+ * evaluation launch at the current settings.  Either pointer may be NULL. */
+sph_status sph_kernel_counts(sph_ctx *ctx, int *per_step, int *per_breakup);
 
 #ifdef __cplusplus
 }

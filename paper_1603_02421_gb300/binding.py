@@ -77,7 +77,13 @@ _SIGS = {
     "sph_get_csf": ([_CTX, ctypes.c_longlong, _LL, _U32, _D, _D, _D], ctypes.c_int),
     "sph_get_pairs": ([_CTX, ctypes.c_longlong, _U32, _U32, _LL], ctypes.c_int),
     "sph_get_time": ([_CTX, _D, _LL, _LL, _LL], ctypes.c_int),
-    "sph_kernels_per_step": ([_CTX, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "sph_kernel_counts": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                          ctypes.c_int),
+    "sph_run_async": ([_CTX, ctypes.c_longlong], ctypes.c_int),
+    "sph_sync": ([_CTX], ctypes.c_int),
+    "sph_profile": ([_CTX, ctypes.c_int], ctypes.c_int),
+    "sph_profile_report": ([_CTX, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_char_p), _D, _LL], ctypes.c_int),
 }
 
 _lib = None
@@ -242,10 +248,32 @@ def sph_get_time(ctx):
     return {"t": t.value, "steps": s.value, "n": n.value, "deleted": d.value}
 
 
-def sph_kernels_per_step(ctx) -> int:
-    c = ctypes.c_int()
-    _check(ctx, lib().sph_kernels_per_step(ctx, ctypes.byref(c)))
-    return c.value
+def sph_kernel_counts(ctx):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().sph_kernel_counts(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def sph_run_async(ctx, nsteps):
+    _check(ctx, lib().sph_run_async(ctx, int(nsteps)))
+
+
+def sph_sync(ctx):
+    _check(ctx, lib().sph_sync(ctx))
+
+
+def sph_profile(ctx, enable):
+    _check(ctx, lib().sph_profile(ctx, int(bool(enable))))
+
+
+def sph_profile_report(ctx, cap=64) -> dict:
+    n = ctypes.c_int()
+    names = (ctypes.c_char_p * cap)()
+    ms = np.zeros(cap)
+    cnt = np.zeros(cap, np.int64)
+    _check(ctx, lib().sph_profile_report(ctx, cap, ctypes.byref(n), names, _d(ms),
+                                         cnt.ctypes.data_as(_LL)))
+    return {names[k].decode(): (float(ms[k]), int(cnt[k])) for k in range(n.value)}
 
 
 # ---------------------------------------------------------------------------
@@ -321,4 +349,4 @@ class Simulation:
         return sph_get_time(self.ctx)
 
     def kernels_per_step(self):
-        return sph_kernels_per_step(self.ctx)
+        return sph_kernel_counts(self.ctx)[0]

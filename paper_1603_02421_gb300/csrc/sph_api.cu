@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -69,6 +70,14 @@ struct sph_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool graph_dirty = true;
+
+    // per-kernel timing: an event before each kernel group of a step
+    bool prof = false, prof_pending = false, ticking = false;
+    std::vector<cudaEvent_t> pev;
+    std::vector<const char *> pname;
+    int pidx = 0;
+    std::map<std::string, std::pair<double, long long>> ptot;
+    std::vector<std::string> report_names;
 };
 
 // ---------------------------------------------------------------------------
@@ -225,15 +234,34 @@ static Boundary bd_of(sph_ctx *c) {
     return b;
 }
 
+// Records a timing event before the next kernel group when profiling is on.
+// Events are created up front by sph_profile (not during a capture) and are
+// recorded as external event nodes when the step is captured into a graph.
+static void tick(sph_ctx *c, const char *name) {
+    if (!c->prof || !c->ticking || c->pidx >= (int)c->pev.size()) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->stream, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(c->pev[c->pidx], c->stream, cudaEventRecordExternal);
+    else
+        cudaEventRecord(c->pev[c->pidx], c->stream);
+    c->pname[c->pidx] = name;
+    ++c->pidx;
+}
+
 // hash -> sort -> cell ranges -> gather into cell order (evaluation-n records)
 template <class T> static const uint32_t *enqueue_sort(sph_ctx *c) {
     const PhysT<T> &P = Ops<T>::phys(c);
     State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
+    tick(c, "hash");
     launch_hash<T>(c->grid, raw, c->sc, c->sb.key[0], c->sb.val[0], c->cap, c->stream);
+    tick(c, "radix_sort");
     int buf = launch_radix_sort(c->sb, c->grid, c->sc, c->cap, c->stream);
     c->sorted_buf = buf;
     const uint32_t *key = c->sb.key[buf];
+    tick(c, "cell_ranges");
     launch_cells(c->grid, key, c->sc, c->cellSE, c->cap, c->stream);
+    tick(c, "reorder");
     launch_reorder<T>(P, c->grid, c->sc, key, c->sb.val[buf], raw, srt, hot_n<T>(c), c->cap,
                       c->stream);
     return key;
@@ -242,7 +270,9 @@ template <class T> static const uint32_t *enqueue_sort(sph_ctx *c) {
 template <class T> static void enqueue_csf(sph_ctx *c, const uint32_t *key, const Hot<T> &hot) {
     const PhysT<T> &P = Ops<T>::phys(c);
     if (!P.csf) return;
+    tick(c, "colour");
     launch_colour<T>(P, c->grid, c->sc, c->cellSE, key, hot, csf_of<T>(c), c->cap, c->stream);
+    tick(c, "normal");
     launch_normal<T>(P, c->grid, c->sc, c->cellSE, key, hot, csf_of<T>(c), c->cap, c->stream);
 }
 
@@ -251,16 +281,25 @@ template <class T> static void enqueue_step(sph_ctx *c) {
     State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
     auto *acc = (typename Vec<T>::v2 *)c->acc;
     T *dr = (T *)c->dr;
+    c->pidx = 0;
+    c->ticking = true;
     const uint32_t *key = enqueue_sort<T>(c);
     Hot<T> hn = hot_n<T>(c), hh = hot_h<T>(c);
     enqueue_csf<T>(c, key, hn);
+    tick(c, "forces");
     launch_forces<T>(1, P, c->grid, c->inf, c->sc, c->cellSE, key, hn, csf_of<T>(c), bd_of(c),
                      srt, raw, acc, dr, c->cap, c->stream);
+    tick(c, "predict");
     launch_predict<T>(P, c->grid, c->inf, c->sc, key, srt, acc, dr, hh, c->cap, c->stream);
     enqueue_csf<T>(c, key, hh);
+    tick(c, "forces_correct");
     launch_forces<T>(2, P, c->grid, c->inf, c->sc, c->cellSE, key, hh, csf_of<T>(c), bd_of(c),
                      srt, raw, acc, dr, c->cap, c->stream);
+    tick(c, "spawn");
     launch_spawn<T>(P, c->inf, c->sc, raw, c->layer_y, c->cap, c->stream);
+    tick(c, nullptr);
+    c->ticking = false;
+    c->prof_pending = c->prof;
 }
 
 template <class T> static void enqueue_evaluate(sph_ctx *c) {
@@ -298,10 +337,28 @@ static sph_status push_scalars(sph_ctx *c) {
     return SPH_OK;
 }
 
+// Adds the per-kernel durations of the most recent step to the totals.
+static void collect_profile(sph_ctx *c) {
+    if (!c->prof_pending) return;
+    c->prof_pending = false;
+    for (int k = 0; k + 1 < c->pidx; ++k) {
+        if (!c->pname[k]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->pev[k], c->pev[k + 1]) != cudaSuccess) {
+            cudaGetLastError();   // do not leave the failure as the sticky last error
+            continue;
+        }
+        auto &e = c->ptot[c->pname[k]];
+        e.first += ms;
+        e.second += 1;
+    }
+}
+
 static sph_status after_work(sph_ctx *c, const char *what) {
     CK(cudaGetLastError(), what);
     sph_status s = pull_scalars(c);
     if (s != SPH_OK) return s;
+    collect_profile(c);
     return status_from_err(c, c->hsc->err);
 }
 
@@ -526,6 +583,7 @@ sph_status sph_init(const sph_params *p, sph_ctx **out) {
 void sph_destroy(sph_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto e : c->pev) cudaEventDestroy(e);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     for (auto &b : c->allocs) cudaFree(b.p);
@@ -673,6 +731,21 @@ sph_status sph_evaluate(sph_ctx *c) {
     return s;
 }
 
+// Captures one step into a CUDA graph (again after any change of the
+// kernels' by-value parameters).
+static sph_status ensure_graph(sph_ctx *c) {
+    if (!c->graph_dirty && c->gexec) return SPH_OK;
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    step_any(c);
+    c->prof_pending = false;
+    CK(cudaStreamEndCapture(c->stream, &c->graph), "end capture");
+    CK(cudaGraphInstantiate(&c->gexec, c->graph, 0), "instantiate graph");
+    c->graph_dirty = false;
+    return SPH_OK;
+}
+
 static sph_status breakup_now(sph_ctx *c, double D, double *L, int *broken) {
     if (c->tsz == 4) enqueue_breakup<float>(c); else enqueue_breakup<double>(c);
     sph_status s = after_work(c, "breakup");
@@ -703,16 +776,8 @@ sph_status sph_run(sph_ctx *c, long long nsteps, int breakup_every, double D, do
         if (!L_out || !nL || !(D > 0)) return fail(c, SPH_ERR_ARG, "L_out, nL and D > 0 required");
         *nL = 0;
     }
-    if (c->graph_dirty || !c->gexec) {
-        if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-        if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
-        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        step_any(c);
-        cudaError_t e = cudaStreamEndCapture(c->stream, &c->graph);
-        CK(e, "end capture");
-        CK(cudaGraphInstantiate(&c->gexec, c->graph, 0), "instantiate graph");
-        c->graph_dirty = false;
-    }
+    sph_status gs = ensure_graph(c);
+    if (gs) return gs;
     for (long long k = 1; k <= nsteps; ++k) {
         CK(cudaGraphLaunch(c->gexec, c->stream), "graph launch");
         if (breakup_every > 0 && k % breakup_every == 0) {
@@ -735,6 +800,7 @@ sph_status sph_get_state(sph_ctx *c, long long cap, long long *n_out, double *x,
     try {
         sph_status s = pull_scalars(c);
         if (s) return s;
+        if (c->n_eval < 0) c->n_eval = c->hsc->nsrt;
         size_t n = (size_t)c->hsc->n, ts = c->tsz;
         std::vector<double2> pos(n);
         std::vector<unsigned char> vel(2 * n * ts), dr(n * ts), m(n * ts), ac(2 * n * ts), drt(n * ts);
@@ -907,14 +973,69 @@ sph_status sph_get_time(sph_ctx *c, double *t, long long *steps, long long *n_pa
     return SPH_OK;
 }
 
-sph_status sph_kernels_per_step(sph_ctx *c, int *count) {
-    if (!c || !count) return SPH_ERR_ARG;
+sph_status sph_run_async(sph_ctx *c, long long nsteps) {
+    if (!c) return SPH_ERR_ARG;
+    if (nsteps < 0) return fail(c, SPH_ERR_ARG, "nsteps < 0");
+    sph_status gs = ensure_graph(c);
+    if (gs) return gs;
+    for (long long k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+    if (nsteps > 0) {
+        c->prof_pending = c->prof;
+        c->n_eval = -1;   // resolved at the next synchronising call
+        c->csf_valid = false;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_sync(sph_ctx *c) {
+    if (!c) return SPH_ERR_ARG;
+    sph_status s = after_work(c, "sync");
+    if (c->n_eval < 0) c->n_eval = c->hsc->nsrt;
+    return s;
+}
+
+sph_status sph_profile(sph_ctx *c, int enable) {
+    if (!c) return SPH_ERR_ARG;
+    while (enable && c->pev.size() < 48) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e), "event create");
+        c->pev.push_back(e);
+        c->pname.push_back(nullptr);
+    }
+    if (c->prof != (enable != 0)) c->graph_dirty = true;
+    c->prof = enable != 0;
+    c->prof_pending = false;
+    c->ptot.clear();
+    return SPH_OK;
+}
+
+sph_status sph_profile_report(sph_ctx *c, int cap, int *n, const char **names, double *total_ms,
+                              long long *launches) {
+    if (!c || !n) return SPH_ERR_ARG;
+    c->report_names.clear();
+    for (auto &kv : c->ptot) c->report_names.push_back(kv.first);
+    *n = (int)c->report_names.size();
+    if (*n > cap) return fail(c, SPH_ERR_CAPACITY, "%d kernel groups > cap %d", *n, cap);
+    int k = 0;
+    for (auto &kv : c->ptot) {
+        if (names) names[k] = c->report_names[k].c_str();
+        if (total_ms) total_ms[k] = kv.second.first;
+        if (launches) launches[k] = kv.second.second;
+        ++k;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_kernel_counts(sph_ctx *c, int *per_step, int *per_breakup) {
+    if (!c) return SPH_ERR_ARG;
     int passes = (c->grid.keybits + 7) / 8;
-    int k = 1 + 3 * passes + 1 + 1;   // hash, sort passes, cell ranges, reorder
-    k += c->prm.sigma > 0 ? 4 : 0;     // colour + normal, twice
-    k += 3;                            // forces (2x) + predict
-    k += 1;                            // spawn / time advance
-    *count = k;
+    int build = 1 + 3 * passes + 1 + 1;   // hash, sort passes, cell ranges, reorder
+    int k = build;
+    k += c->prm.sigma > 0 ? 4 : 0;         // colour + normal, twice
+    k += 3;                                // forces (2x) + predict
+    k += 1;                                // spawn / time advance
+    if (per_step) *per_step = k;
+    if (per_breakup) *per_breakup = build + 4;   // + union-find init, link, compress, reach
     return SPH_OK;
 }
 

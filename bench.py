@@ -65,11 +65,13 @@ def workload(name: str, seed: int):
 # Algorithmic FP32 operations per interacting pair (r < 2h) of each pair
 # sweep, counting a fused multiply-add as 2, sqrt and division as 1 each.
 # The derivation is listed in the design doc.
-FLOP_PER_PAIR = {"colour": 16, "normal": 18, "forces": 62, "forces_correct": 62}
-FLOP_PER_PARTICLE = {"colour": 2, "normal": 8, "forces": 30, "forces_correct": 40}
-# Algorithmic HBM bytes per particle of the streaming kernels (FP32 path).
-BYTES_PER_PARTICLE = {"hash": 16 + 1 + 8, "reorder": 2 * 41 + 8 + 32,
-                      "predict": 41 + 12 + 48, "cell_ranges": 4 + 8}
+FLOP_PER_PAIR = {"list_colour": 16, "colour": 16, "normal": 18, "forces": 62,
+                 "forces_correct": 62}
+FLOP_PER_PARTICLE = {"list_colour": 2, "colour": 2, "normal": 8, "forces": 30,
+                     "forces_correct": 40}
+# Algorithmic HBM bytes per particle of the streaming kernel groups (FP32 path).
+BYTES_PER_PARTICLE = {"cell_sort": 16 + 1 + 4 + 4 + 4 + 4 + 4, "reorder": 2 * 41 + 4 + 4 + 32,
+                      "predict": 41 + 12 + 48, "spawn": 0}
 
 
 def parse():
@@ -245,43 +247,41 @@ def main():
     for _ in range(max(args.warmup, 0)):
         binding.sph_run_async(ctx, 1)
         binding.sph_sync(ctx)
-    binding.sph_profile(ctx, 1)
-    binding.sph_run_async(ctx, 1)       # capture the step graph with timing events
-    binding.sph_sync(ctx)
-    binding.sph_profile(ctx, 1)         # reset totals
+
+    def timed(K, profile):
+        """K steps, each bracketed by CUDA events on the library's stream, with
+        an L2 flush before each step outside the events."""
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        nact = np.zeros(K, np.int64)
+        Ls = []
+        n_now = binding.sph_get_time(ctx)["n"]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(K):
+            nact[k] = n_now
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev0[k].record(stream)
+            binding.sph_run_async(ctx, 1)
+            if has_inflow and not profile and (k + 1) % BREAKUP_EVERY == 0:
+                Ls.append(binding.sph_breakup_length(ctx)[0])
+            ev1[k].record(stream)
+            binding.sph_sync(ctx)
+            if (k + 1) % 50 == 0:
+                n_now = binding.sph_get_time(ctx)["n"]
+        torch.cuda.synchronize(dev)
+        ms = np.array([ev0[k].elapsed_time(ev1[k]) for k in range(K)])
+        return ms, nact, Ls
 
     K = args.steps
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    nact = np.zeros(K, np.int64)
-    nbreak = 0
-    Ls = []
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
     clocks = ClockSampler(local)
     t_wall0 = time.perf_counter()
-    for k in range(K):
-        nact[k] = binding.sph_get_time(ctx)["n"] if k == 0 else nact[k - 1]
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        ev0[k].record(stream)
-        binding.sph_run_async(ctx, 1)
-        if has_inflow and (k + 1) % BREAKUP_EVERY == 0:
-            Ls.append(binding.sph_breakup_length(ctx)[0])
-            nbreak += 1
-        ev1[k].record(stream)
-        binding.sph_sync(ctx)
-        if (k + 1) % 50 == 0 or k == K - 1:
-            nact[k] = binding.sph_get_time(ctx)["n"]
-    torch.cuda.synchronize(dev)
+    step_ms, nact, Ls = timed(K, profile=False)
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    step_ms = np.array([ev0[k].elapsed_time(ev1[k]) for k in range(K)])
-    # particle count per step: piecewise constant between samples
-    for k in range(1, K):
-        if nact[k] == 0:
-            nact[k] = nact[k - 1]
+    nbreak = len(Ls)
     total_s = step_ms.sum() / 1e3
     units = float(nact.sum())
     if dist is not None:
@@ -294,6 +294,14 @@ def main():
         dist.barrier()
     value = units / total_s
 
+    # per-kernel attribution: the same steps with a CUDA event before each
+    # kernel group (captured into the step graph)
+    binding.sph_profile(ctx, 1)
+    binding.sph_run_async(ctx, 1)
+    binding.sph_sync(ctx)
+    binding.sph_profile(ctx, 1)
+    Kp = min(K, 100)
+    prof_ms, _, _ = timed(Kp, profile=True)
     prof = binding.sph_profile_report(ctx)
     binding.sph_profile(ctx, 0)
 
@@ -353,8 +361,9 @@ def main():
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
-            "kernel_ms_per_step": {k: v[0] / max(v[1], 1) * (2 if k in ("colour", "normal") else 1)
-                                   for k, v in prof.items()},
+            "kernel_ms_per_step": {k: v[0] / Kp for k, v in prof.items()},
+            "attribution": {"steps": Kp, "ms_per_step_with_events": float(prof_ms.mean()),
+                            "how": "CUDA event before each kernel group inside the step graph"},
             "breakup_L_over_D": Ls,
         }
         print(json.dumps(line), flush=True)

@@ -45,7 +45,8 @@ typedef enum {
     SPH_OK = 0,
     SPH_ERR_ARG = -1,        /* invalid argument or parameter                */
     SPH_ERR_OOM = -2,        /* device allocation failed                     */
-    SPH_ERR_CAPACITY = -3,   /* particle capacity or output buffer too small */
+    SPH_ERR_CAPACITY = -3,   /* particle capacity, neighbour-list capacity or
+                                output buffer too small                      */
     SPH_ERR_CUDA = -4,       /* CUDA runtime / launch error                  */
     SPH_ERR_NONFINITE = -5,  /* NaN / Inf in an acceleration or density rate */
     SPH_ERR_TIMEOUT = -6,    /* a bounded device loop hit its limit          */
@@ -85,7 +86,7 @@ typedef struct {
                               any value gives the same results to rounding; the
                               stream velocity of a jet keeps its small velocity
                               differences accurate in FP32)                      */
-    long long capacity;    /* maximum fluid + buffer particles held at once         */
+    long long capacity;    /* maximum fluid + buffer particles held at once (<= 2^28) */
     long long boundary_capacity; /* maximum boundary particles                      */
     void *cuda_stream;     /* cudaStream_t to issue work on, or NULL                */
     int device;            /* CUDA device ordinal                                   */

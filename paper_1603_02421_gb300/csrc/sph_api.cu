@@ -49,16 +49,16 @@ struct sph_ctx {
     void *raw[7] = {}, *srt[7] = {};   // pos, vel, drho, drc, mass, type, id
     void *H0n = nullptr, *H1n = nullptr, *H0h = nullptr, *H1h = nullptr;
     double2 *posh = nullptr;
-    void *C = nullptr, *nhat = nullptr, *nvec = nullptr;
+    void *C = nullptr, *CX = nullptr, *nhat = nullptr, *nvec = nullptr;
     void *acc = nullptr, *dr = nullptr;
-    SortBufs sb{};
+    CellSort cs{};
+    NList nl{};
     uint2 *cellSE = nullptr, *cellSE_b = nullptr;
     void *bH = nullptr;
     double2 *bpos = nullptr;
     uint32_t *parent = nullptr;
     uint8_t *flag = nullptr;
     double *layer_y = nullptr;
-    int sorted_buf = 0;          // which sort buffer holds the sorted keys
 
     // host-side boundary particles (static)
     std::vector<double> bx, by, bnx, bny;
@@ -133,6 +133,8 @@ static sph_status status_from_err(sph_ctx *c, unsigned err) {
     if (err & ERR_CAPACITY) return fail(c, SPH_ERR_CAPACITY, "inflow exceeded the particle capacity");
     if (err & ERR_TIMEOUT) return fail(c, SPH_ERR_TIMEOUT, "a bounded device loop hit its iteration limit");
     if (err & ERR_NODT) return fail(c, SPH_ERR_STATE, "adaptive time step without fluid particles");
+    if (err & ERR_NLIST)
+        return fail(c, SPH_ERR_CAPACITY, "a particle has more neighbours than its list holds");
     return SPH_OK;
 }
 
@@ -159,6 +161,7 @@ template <class T> static PhysT<T> make_phys(const sph_params &p, const Grid &g,
     P.kernel = p.kernel;
     P.csf = p.sigma > 0.0;
     P.walls = walls;
+    P.gamma7 = p.gamma == 7.0;
     P.h = (T)h;
     P.inv_h = (T)(1.0 / h);
     P.H2lo = (T)(H2 * (1.0 - band));
@@ -167,6 +170,9 @@ template <class T> static PhysT<T> make_phys(const sph_params &p, const Grid &g,
     P.R15hi = (T)(R2 * (1.0 + band));
     P.H2d = H2;
     P.R15d = R2;
+    double RL = 2.0 * h + p.skin_over_h * h;
+    P.RL2hi = (T)(RL * RL * (1.0 + band));
+    P.half_skin2 = 0.25 * (p.skin_over_h * h) * (p.skin_over_h * h);
     P.sc = (T)g.sc;
     P.wn = (T)(kap / (h * h));
     P.gn = (T)(p.kernel == SPH_KERNEL_CUBIC ? kap / (h * h * h * h) : -10.0 * kap / (h * h * h * h));
@@ -200,8 +206,8 @@ template <class T> static PhysT<T> make_phys(const sph_params &p, const Grid &g,
 }
 
 static void cell_of(const Grid &g, double x, double y, int &cx, int &cy) {
-    cx = (int)std::floor((x - g.xmin) / g.sc) + 1;
-    cy = (int)std::floor((y - g.ymin) / g.sc) + 1;
+    cx = (int)std::floor((x - g.xmin) * g.inv_sc) + 1;
+    cy = (int)std::floor((y - g.ymin) * g.inv_sc) + 1;
     cx = std::min(std::max(cx, 1), g.ncx - 2);
     cy = std::min(std::max(cy, 1), g.ncy - 2);
 }
@@ -223,7 +229,8 @@ template <class T> static Hot<T> hot_h(sph_ctx *c) {
     return Hot<T>{(typename Vec<T>::v4 *)c->H0h, (typename Vec<T>::v4 *)c->H1h, c->posh};
 }
 template <class T> static Csf<T> csf_of(sph_ctx *c) {
-    return Csf<T>{(T *)c->C, (typename Vec<T>::v2 *)c->nhat, (typename Vec<T>::v2 *)c->nvec};
+    return Csf<T>{(T *)c->C, (typename Vec<T>::v4 *)c->CX, (typename Vec<T>::v2 *)c->nhat,
+                  (typename Vec<T>::v2 *)c->nvec};
 }
 static Boundary bd_of(sph_ctx *c) {
     Boundary b;
@@ -253,27 +260,27 @@ static void tick(sph_ctx *c, const char *name) {
 template <class T> static const uint32_t *enqueue_sort(sph_ctx *c) {
     const PhysT<T> &P = Ops<T>::phys(c);
     State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
-    tick(c, "hash");
-    launch_hash<T>(c->grid, raw, c->sc, c->sb.key[0], c->sb.val[0], c->cap, c->stream);
-    tick(c, "radix_sort");
-    int buf = launch_radix_sort(c->sb, c->grid, c->sc, c->cap, c->stream);
-    c->sorted_buf = buf;
-    const uint32_t *key = c->sb.key[buf];
-    tick(c, "cell_ranges");
-    launch_cells(c->grid, key, c->sc, c->cellSE, c->cap, c->stream);
+    tick(c, "cell_sort");
+    launch_cell_sort<T>(c->grid, raw, c->sc, c->cs, c->cap, c->stream);
     tick(c, "reorder");
-    launch_reorder<T>(P, c->grid, c->sc, key, c->sb.val[buf], raw, srt, hot_n<T>(c), c->cap,
-                      c->stream);
+    launch_reorder<T>(P, c->grid, c->sc, c->cs, raw, srt, hot_n<T>(c), c->cap, c->stream);
+    const uint32_t *key = c->cs.key;
     return key;
 }
 
-template <class T> static void enqueue_csf(sph_ctx *c, const uint32_t *key, const Hot<T> &hot) {
+// List build of evaluation n, fused with its colour when CSF is on.
+template <class T> static void enqueue_build(sph_ctx *c, const uint32_t *key) {
+    const PhysT<T> &P = Ops<T>::phys(c);
+    tick(c, "list_colour");
+    launch_build<T>(P.csf != 0, P, c->grid, c->sc, c->cellSE, key, hot_n<T>(c), c->nl,
+                    csf_of<T>(c), c->cap, c->stream);
+}
+
+template <class T> static void enqueue_normal(sph_ctx *c, const Hot<T> &hot) {
     const PhysT<T> &P = Ops<T>::phys(c);
     if (!P.csf) return;
-    tick(c, "colour");
-    launch_colour<T>(P, c->grid, c->sc, c->cellSE, key, hot, csf_of<T>(c), c->cap, c->stream);
     tick(c, "normal");
-    launch_normal<T>(P, c->grid, c->sc, c->cellSE, key, hot, csf_of<T>(c), c->cap, c->stream);
+    launch_normal<T>(P, c->sc, c->nl, hot, csf_of<T>(c), c->cap, c->stream);
 }
 
 template <class T> static void enqueue_step(sph_ctx *c) {
@@ -285,16 +292,21 @@ template <class T> static void enqueue_step(sph_ctx *c) {
     c->ticking = true;
     const uint32_t *key = enqueue_sort<T>(c);
     Hot<T> hn = hot_n<T>(c), hh = hot_h<T>(c);
-    enqueue_csf<T>(c, key, hn);
+    enqueue_build<T>(c, key);
+    enqueue_normal<T>(c, hn);
     tick(c, "forces");
-    launch_forces<T>(1, P, c->grid, c->inf, c->sc, c->cellSE, key, hn, csf_of<T>(c), bd_of(c),
-                     srt, raw, acc, dr, c->cap, c->stream);
+    launch_forces<T>(1, P, c->grid, c->inf, c->sc, c->nl, key, hn, csf_of<T>(c), bd_of(c), srt,
+                     raw, acc, dr, c->cap, c->stream);
     tick(c, "predict");
     launch_predict<T>(P, c->grid, c->inf, c->sc, key, srt, acc, dr, hh, c->cap, c->stream);
-    enqueue_csf<T>(c, key, hh);
+    if (P.csf) {
+        tick(c, "colour");
+        launch_colour<T>(P, c->sc, c->nl, hh, csf_of<T>(c), c->cap, c->stream);
+    }
+    enqueue_normal<T>(c, hh);
     tick(c, "forces_correct");
-    launch_forces<T>(2, P, c->grid, c->inf, c->sc, c->cellSE, key, hh, csf_of<T>(c), bd_of(c),
-                     srt, raw, acc, dr, c->cap, c->stream);
+    launch_forces<T>(2, P, c->grid, c->inf, c->sc, c->nl, key, hh, csf_of<T>(c), bd_of(c), srt,
+                     raw, acc, dr, c->cap, c->stream);
     tick(c, "spawn");
     launch_spawn<T>(P, c->inf, c->sc, raw, c->layer_y, c->cap, c->stream);
     tick(c, nullptr);
@@ -307,9 +319,10 @@ template <class T> static void enqueue_evaluate(sph_ctx *c) {
     State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
     const uint32_t *key = enqueue_sort<T>(c);
     Hot<T> hn = hot_n<T>(c);
-    enqueue_csf<T>(c, key, hn);
-    launch_forces<T>(0, P, c->grid, c->inf, c->sc, c->cellSE, key, hn, csf_of<T>(c), bd_of(c),
-                     srt, raw, (typename Vec<T>::v2 *)c->acc, (T *)c->dr, c->cap, c->stream);
+    enqueue_build<T>(c, key);
+    enqueue_normal<T>(c, hn);
+    launch_forces<T>(0, P, c->grid, c->inf, c->sc, c->nl, key, hn, csf_of<T>(c), bd_of(c), srt,
+                     raw, (typename Vec<T>::v2 *)c->acc, (T *)c->dr, c->cap, c->stream);
 }
 
 template <class T> static void enqueue_breakup(sph_ctx *c) {
@@ -490,8 +503,8 @@ sph_status sph_init(const sph_params *p, sph_ctx **out) {
     if (!(q.xmax > q.xmin && q.ymax > q.ymin)) return fail(nullptr, SPH_ERR_ARG, "empty domain box");
     if (!(q.skin_over_h >= 0.1 && q.skin_over_h <= 2.0))
         return fail(nullptr, SPH_ERR_ARG, "skin_over_h must lie in [0.1, 2]");
-    if (!(q.capacity >= 1 && q.capacity <= (1ll << 30)))
-        return fail(nullptr, SPH_ERR_ARG, "capacity must lie in [1, 2^30]");
+    if (!(q.capacity >= 1 && q.capacity <= (1ll << 28)))
+        return fail(nullptr, SPH_ERR_ARG, "capacity must lie in [1, 2^28]");
     if (!(q.boundary_capacity >= 0 && q.boundary_capacity <= (1ll << 26)))
         return fail(nullptr, SPH_ERR_ARG, "boundary_capacity must lie in [0, 2^26]");
     if (!(std::isfinite(q.u_frame_x) && std::isfinite(q.u_frame_y)))
@@ -504,7 +517,7 @@ sph_status sph_init(const sph_params *p, sph_ctx **out) {
         return fail(nullptr, SPH_ERR_ARG, "skin too small for the wall-force reach");
     double sc = 2.0 * h + skin;
     double ncx = std::floor((q.xmax - q.xmin) / sc) + 3, ncy = std::floor((q.ymax - q.ymin) / sc) + 3;
-    if (ncx * ncy > 2.0e9) return fail(nullptr, SPH_ERR_ARG, "cell grid too large (%.3g cells)", ncx * ncy);
+    if (ncx * ncy > 6.7e7) return fail(nullptr, SPH_ERR_ARG, "cell grid too large (%.3g cells)", ncx * ncy);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
         return fail(nullptr, SPH_ERR_CUDA, "no CUDA device available");
@@ -548,17 +561,21 @@ sph_status sph_init(const sph_params *p, sph_ctx **out) {
     if (!e) c->H1h = dalloc(c, N * 4 * ts, e);
     if (!e) c->posh = (double2 *)dalloc(c, N * 16, e);
     if (!e) c->C = dalloc(c, N * ts, e);
+    if (!e) c->CX = dalloc(c, N * 4 * ts, e);
     if (!e) c->nhat = dalloc(c, N * 2 * ts, e);
     if (!e) c->nvec = dalloc(c, N * 2 * ts, e);
     if (!e) c->acc = dalloc(c, N * 2 * ts, e);
     if (!e) c->dr = dalloc(c, N * ts, e);
-    c->sb.ntiles = (int)((N + RS_TILE - 1) / RS_TILE);
-    for (int k = 0; k < 2 && !e; ++k) {
-        c->sb.key[k] = (uint32_t *)dalloc(c, N * 4, e);
-        if (!e) c->sb.val[k] = (uint32_t *)dalloc(c, N * 4, e);
-    }
-    if (!e) c->sb.tileHist = (uint32_t *)dalloc(c, (size_t)RS_BINS * c->sb.ntiles * 4, e);
+    c->cs.nscan = (int)(((size_t)g.ncells + SCAN_CELLS - 1) / SCAN_CELLS);
+    if (!e) c->cs.knew = (uint32_t *)dalloc(c, N * 4, e);
+    if (!e) c->cs.count = (uint32_t *)dalloc(c, (size_t)g.ncells * 4, e);
+    if (!e) c->cs.tmp = (uint32_t *)dalloc(c, N * 4, e);
+    if (!e) c->cs.key = (uint32_t *)dalloc(c, N * 4, e);
+    if (!e) c->cs.bsum = (uint32_t *)dalloc(c, (size_t)c->cs.nscan * 4, e);
     if (!e) c->cellSE = (uint2 *)dalloc(c, (size_t)g.ncells * 8, e);
+    c->cs.cellSE = c->cellSE;
+    if (!e) c->nl.e = (uint32_t *)dalloc(c, N * LIST_SLOTS * 4, e);
+    if (!e) c->nl.cnt = (uint32_t *)dalloc(c, N * 4, e);
     if (!e) c->cellSE_b = (uint2 *)dalloc(c, (size_t)g.ncells * 8, e);
     if (!e) c->bH = dalloc(c, NB * 4 * ts, e);
     if (!e) c->bpos = (double2 *)dalloc(c, NB * 16, e);
@@ -928,11 +945,11 @@ sph_status sph_get_pairs(sph_ctx *c, long long cap, unsigned *id_a, unsigned *id
     sph_status s = SPH_OK;
     if (c->tsz == 4) {
         const uint32_t *key = enqueue_sort<float>(c);
-        launch_pairs<float>(c->Pf, c->grid, c->sc, c->sc, c->cellSE, key, hot_n<float>(c),
+        launch_pairs<float>(c->Pf, c->grid, c->sc, c->cellSE, key, hot_n<float>(c),
                             (uint32_t *)c->srt[6], da, db, dcap, c->cap, c->stream);
     } else {
         const uint32_t *key = enqueue_sort<double>(c);
-        launch_pairs<double>(c->Pd, c->grid, c->sc, c->sc, c->cellSE, key, hot_n<double>(c),
+        launch_pairs<double>(c->Pd, c->grid, c->sc, c->cellSE, key, hot_n<double>(c),
                              (uint32_t *)c->srt[6], da, db, dcap, c->cap, c->stream);
     }
     s = after_work(c, "pairs");
@@ -1028,10 +1045,9 @@ sph_status sph_profile_report(sph_ctx *c, int cap, int *n, const char **names, d
 
 sph_status sph_kernel_counts(sph_ctx *c, int *per_step, int *per_breakup) {
     if (!c) return SPH_ERR_ARG;
-    int passes = (c->grid.keybits + 7) / 8;
-    int build = 1 + 3 * passes + 1 + 1;   // hash, sort passes, cell ranges, reorder
-    int k = build;
-    k += c->prm.sigma > 0 ? 4 : 0;         // colour + normal, twice
+    int build = 5;                         // hash+count, scan (2), scatter, reorder
+    int k = build + 1;                     // + neighbour list (with the colour of step n)
+    k += c->prm.sigma > 0 ? 3 : 0;         // normal (2x) + colour of the half step
     k += 3;                                // forces (2x) + predict
     k += 1;                                // spawn / time advance
     if (per_step) *per_step = k;

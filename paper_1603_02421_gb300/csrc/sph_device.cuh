@@ -19,37 +19,52 @@ __device__ __forceinline__ double cospi_t(double x) { return cospi(x); }
 __device__ __forceinline__ float abs_t(float x) { return fabsf(x); }
 __device__ __forceinline__ double abs_t(double x) { return fabs(x); }
 
-// Eq. 27 / Eq. 28: W(q) including the 2D normalisation kappa / h^2.
-template <class T> __device__ __forceinline__ T kernel_W(const PhysT<T> &P, T q) {
+// Eq. 27 (K = 0, cubic spline) / Eq. 28 (K = 1, Wendland C2): W(q) with the
+// 2D normalisation kappa / h^2 folded into P.wn.  Callers pass q < 2 (up to
+// rounding; t is clamped at 0).
+template <class T, int K> __device__ __forceinline__ T kernel_W(const PhysT<T> &P, T q) {
     T t = T(2) - q;
-    if (t <= T(0)) return T(0);
-    if (P.kernel == 1) {
+    t = t > T(0) ? t : T(0);
+    if (K == 1) {
         T t2 = t * t;
         return P.wn * (T(1) + T(2) * q) * (t2 * t2);
     }
-    if (q <= T(1)) return P.wn * (T(1) - T(1.5) * q * q + T(0.75) * q * q * q);
+    if (q <= T(1)) return P.wn * (T(1) + q * q * (T(-1.5) + T(0.75) * q));
     return P.wn * T(0.25) * t * t * t;
 }
 
 // (1/r) dW/dr, finite at r = 0; grad_a W_ab = F * (r_a - r_b).
 //   Wendland: -10 kappa/h^4 (2-q)^3
 //   cubic:    kappa/h^4 (-3 + 9q/4) for q <= 1, -(3 kappa/4h^4)(2-q)^2 / q above
-template <class T> __device__ __forceinline__ T kernel_F(const PhysT<T> &P, T q) {
+// inv_q = 1/q (used by the cubic outer branch only).
+template <class T, int K> __device__ __forceinline__ T kernel_F(const PhysT<T> &P, T q, T inv_q) {
     T t = T(2) - q;
-    if (t <= T(0)) return T(0);
-    if (P.kernel == 1) return P.gn * t * t * t;
+    t = t > T(0) ? t : T(0);
+    if (K == 1) return P.gn * t * t * t;
     if (q <= T(1)) return P.gn * (T(-3) + T(2.25) * q);
-    return P.gn * T(-0.75) * t * t / q;
+    return P.gn * T(-0.75) * t * t * inv_q;
 }
 
-// Eq. 26 with rho = rho0 + drho evaluated as B expm1(gamma log1p(drho/rho0))
-// to keep the small pressure accurate in FP32; c = c0 (rho/rho0)^((gamma-1)/2).
+// Eq. 26 with rho = rho0 + drho, x = drho / rho0:
+//   P = B ((1 + x)^gamma - 1),  c = c0 (1 + x)^((gamma - 1)/2).
+// For gamma = 7 the binomial expansion x (7 + 21x + 35x^2 + 35x^3 + 21x^4 +
+// 7x^5 + x^6) and c0 (1 + x)^3 are exact and keep full relative precision for
+// small x; otherwise B expm1(gamma log1p(x)).
 template <class T>
 __device__ __forceinline__ void eos(const PhysT<T> &P, T drho, T &rho, T &P_over_rho2, T &c) {
     rho = P.rho0 + drho;
-    T lg = log1p_t(drho * P.inv_rho0);
-    T p = P.B * expm1_t(P.gamma * lg);
-    c = P.c0 * exp_t(P.half_gm1 * lg);
+    T x = drho * P.inv_rho0;
+    T p;
+    if (P.gamma7) {
+        T poly = T(7) + x * (T(21) + x * (T(35) + x * (T(35) + x * (T(21) + x * (T(7) + x)))));
+        p = P.B * x * poly;
+        T s = T(1) + x;
+        c = P.c0 * s * s * s;
+    } else {
+        T lg = log1p_t(x);
+        p = P.B * expm1_t(P.gamma * lg);
+        c = P.c0 * exp_t(P.half_gm1 * lg);
+    }
     P_over_rho2 = p / (rho * rho);
 }
 
@@ -106,18 +121,46 @@ __device__ __forceinline__ T row_shift(const RowRange &rr, unsigned b, T sc) {
     return b < rr.b1 ? sc : (b < rr.b2 ? T(0) : -sc);
 }
 
+// q = r/h, 1/q and 1/r from the squared distance (r2 > 0 except for
+// coincident particles, where q = 0 and 1/q, 1/r are returned as 0).
+__device__ __forceinline__ void q_of(float r2, float h, float inv_h, float &q, float &inv_q,
+                                     float &ri) {
+    ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    q = r2 * ri * inv_h;
+    inv_q = h * ri;
+}
+__device__ __forceinline__ void q_of(double r2, double h, double inv_h, double &q, double &inv_q,
+                                     double &ri) {
+    double r = sqrt(r2);
+    q = r * inv_h;
+    ri = r > 0.0 ? 1.0 / r : 0.0;
+    inv_q = h * ri;
+}
+__device__ __forceinline__ void q_of(float r2, float h, float inv_h, float &q, float &inv_q) {
+    float ri;
+    q_of(r2, h, inv_h, q, inv_q, ri);
+}
+__device__ __forceinline__ void q_of(double r2, double h, double inv_h, double &q, double &inv_q) {
+    double ri;
+    q_of(r2, h, inv_h, q, inv_q, ri);
+}
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+
 // Visit every particle b != i of the 3x3 cell block of particle i whose FP64
 // distance is below the threshold.  Squared distances in T inside [lo, hi)
 // are re-tested exactly in FP64 on the stored positions, so the visited set
-// is exactly {b : |r_a - r_b|^2 < r2exact} of the FP64 positions.
+// is exactly {b : |r_a - r_b|^2 < r2exact} of the FP64 positions.  G threads
+// share one particle: thread `sub` takes every G-th candidate of each row, so
+// the G threads of a particle load G consecutive records.
 // body(b, rx, ry, r2, H0[b]) with (rx, ry) = r_a - r_b.
-template <class T, class Body>
+template <int G, class T, class Body>
 __device__ __forceinline__ void for_neighbours(const PhysT<T> &P, const Grid &g,
                                                const uint2 *__restrict__ cellSE,
                                                const typename Vec<T>::v4 *__restrict__ H0,
                                                const double2 *__restrict__ pos, unsigned i,
-                                               uint32_t key, T xa, T ya, T r2lo, T r2hi,
-                                               double r2exact, Body &&body) {
+                                               unsigned sub, uint32_t key, T xa, T ya, T r2lo,
+                                               T r2hi, double r2exact, Body &&body) {
     int cx, cy;
     key_cell(g, key, cx, cy);
     double2 pa = make_double2(0.0, 0.0);
@@ -127,7 +170,7 @@ __device__ __forceinline__ void for_neighbours(const PhysT<T> &P, const Grid &g,
         RowRange rr = row_range(cellSE, (cy + dy) * g.ncx + cx);
         T yshift = T(dy) * P.sc;
 #pragma unroll 2
-        for (unsigned b = rr.lo; b < rr.hi; ++b) {
+        for (unsigned b = rr.lo + sub; b < rr.hi; b += G) {
             typename Vec<T>::v4 hb = H0[b];
             T rx = (xa - hb.x) + row_shift<T>(rr, b, P.sc);
             T ry = (ya - hb.y) - yshift;
@@ -140,6 +183,56 @@ __device__ __forceinline__ void for_neighbours(const PhysT<T> &P, const Grid &g,
             body(b, rx, ry, r2, hb);
         }
     }
+}
+
+// Sum of v over the G consecutive threads of a particle (all lanes of the
+// warp must call it).
+// Shift (code - 1) * sc of a list entry's 2-bit cell-offset code.
+template <class T> __device__ __forceinline__ T code_shift(uint32_t code, T sc) {
+    return code == 0u ? -sc : (code == 2u ? sc : T(0));
+}
+
+// Walk the G-strided part (lane `sub`) of the neighbour list of particle i:
+// entries whose squared distance in T is below H2lo, or re-tested exactly in
+// FP64 below (2h)^2.  body(b, rx, ry, r2) with (rx, ry) = r_a - r_b.
+template <int G, class T, class Body>
+__device__ __forceinline__ void for_list(const PhysT<T> &P, const NList &nl,
+                                         const typename Vec<T>::v4 *__restrict__ X,
+                                         const double2 *__restrict__ pos, unsigned i,
+                                         unsigned sub, T xa, T ya, Body &&body) {
+    unsigned cnt = nl.cnt[i];
+    const uint32_t *__restrict__ e = nl.e + (size_t)i * LIST_SLOTS;
+    double2 pa = make_double2(0.0, 0.0);
+    bool have_pa = false;
+#pragma unroll 2
+    for (unsigned k = sub; k < cnt; k += G) {
+        uint32_t ent = __ldg(e + k);
+        unsigned b = ent & 0x0FFFFFFFu;
+        typename Vec<T>::v4 xb = X[b];
+        T rx = (xa - xb.x) + code_shift<T>((ent >> 28) & 3u, P.sc);
+        T ry = (ya - xb.y) + code_shift<T>(ent >> 30, P.sc);
+        T r2 = rx * rx + ry * ry;
+        if (r2 >= P.H2hi) continue;
+        if (r2 >= P.H2lo) {
+            if (!have_pa) { pa = pos[i]; have_pa = true; }
+            if (!exact_within(pa, pos[b], P.H2d)) continue;
+        }
+        body(b, rx, ry, r2, xb);
+    }
+}
+
+template <int G, class T> __device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int G, class T> __device__ __forceinline__ T group_max(T v) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+        T w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
 }
 
 }  // namespace sph

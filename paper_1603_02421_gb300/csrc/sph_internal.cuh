@@ -24,7 +24,8 @@ enum ErrBits : unsigned {
     ERR_SKIN = 2u,
     ERR_CAPACITY = 4u,
     ERR_TIMEOUT = 8u,
-    ERR_NODT = 16u
+    ERR_NODT = 16u,
+    ERR_NLIST = 32u
 };
 
 struct __align__(16) f4 { float x, y, z, w; };
@@ -48,7 +49,9 @@ template <class T> struct PhysT {
     int kernel;          // 0 cubic, 1 Wendland
     int csf;             // sigma > 0
     int walls;           // boundary particles present
+    int gamma7;          // gamma == 7: Eq. 26 as an exact polynomial
     T h, inv_h, H2lo, H2hi, R15lo, R15hi;
+    T RL2hi;             // squared neighbour-list radius (2h + skin)^2, widened
     T sc;
     T wn, gn;            // kernel factors: W = wn f(q), (1/r) dW/dr = gn g(q)
     T W0;                // W(0)
@@ -60,6 +63,7 @@ template <class T> struct PhysT {
     double H2d, R15d;    // exact FP64 thresholds (2h)^2, (1.5h)^2
     double courant, dt_fixed;
     double ufx_d, ufy_d;
+    double half_skin2;   // (skin/2)^2: largest displacement between list build and use
 };
 
 // Inflow of the planar jet.
@@ -101,6 +105,7 @@ template <class T> struct Hot {
 
 template <class T> struct Csf {
     T *C;
+    typename Vec<T>::v4 *CX;      // (x_off, y_off, V, C) for the normal sweep
     typename Vec<T>::v2 *nhat;    // unit normal, zero where the filter N_a = 0
     typename Vec<T>::v2 *nvec;    // normal n_a of Eq. 18
 };
@@ -112,57 +117,77 @@ struct Boundary {
     const double2 *pos;           // FP64 positions, cell order
 };
 
-struct SortBufs {
-    uint32_t *key[2], *val[2];
-    uint32_t *tileHist;
-    int ntiles;
+// Counting sort of the particles by cell (Sec. 2-7 cell linked list laid out
+// as contiguous cell ranges).
+struct CellSort {
+    uint32_t *knew;     // [cap] cell key of each raw particle (sentinel: dead)
+    uint32_t *count;    // [ncells] per-cell counters, zero between sorts
+    uint32_t *tmp;      // [cap] raw index at its provisional slot
+    uint32_t *key;      // [cap] cell key of each sorted particle
+    uint32_t *bsum;     // [nscan] cell totals of each scan block
+    uint2 *cellSE;      // [ncells] [start, end) of every cell in the sorted order
+    int nscan;          // scan blocks of SCAN_CELLS cells
 };
 
-constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 8;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
-constexpr int RS_BINS = 256;
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_CELLS = SCAN_THREADS * SCAN_ITEMS;
+constexpr int SWEEP_LANES = 4;      // threads cooperating on one particle's neighbour loop
+constexpr int SWEEP_BLOCK = 128;
+constexpr int LIST_SLOTS = 96;      // neighbour-list entries per particle
+
+// Verlet neighbour list built once per step from the cell block (radius
+// 2h + skin, so it still holds every pair closer than 2h at the half step).
+// Entry = b | (sx + 1) << 28 | (sy + 1) << 30 with (sx, sy) = cell of the
+// particle minus cell of b; the entries of particle i are contiguous at
+// e[i * LIST_SLOTS + k], k < cnt[i].
+struct NList {
+    uint32_t *e;
+    uint32_t *cnt;
+};
 
 // ---- launchers (sph_neighbour.cu) ----
+// hash + count -> scan -> provisional scatter; leaves cs.cellSE final, cs.tmp
+// holding raw indices grouped by cell (in arbitrary order within a cell) and
+// sc->nsrt the live particle count.
 template <class T>
-void launch_hash(const Grid &g, const State<T> &raw, Scalars *sc, uint32_t *key, uint32_t *val,
-                 int cap, cudaStream_t s);
-// Returns the index (0/1) of the buffers holding the sorted result.
-int launch_radix_sort(SortBufs &sb, const Grid &g, Scalars *sc, int cap, cudaStream_t s);
-void launch_cells(const Grid &g, const uint32_t *key, Scalars *sc, uint2 *cellSE, int cap,
-                  cudaStream_t s);
+void launch_cell_sort(const Grid &g, const State<T> &raw, Scalars *sc, CellSort &cs, int cap,
+                      cudaStream_t s);
 template <class T>
-void launch_pairs(const PhysT<T> &P, const Grid &g, const Scalars *sc_dev, Scalars *sc,
-                  const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot,
-                  const uint32_t *ids, unsigned *out_a, unsigned *out_b, unsigned cap, int ncap,
-                  cudaStream_t s);
+void launch_pairs(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *cellSE,
+                  const uint32_t *key, const Hot<T> &hot, const uint32_t *ids, unsigned *out_a,
+                  unsigned *out_b, unsigned cap, int ncap, cudaStream_t s);
 template <class T>
 void launch_breakup(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *cellSE,
                     const uint32_t *key, const Hot<T> &hot, const uint8_t *type,
                     uint32_t *parent, uint8_t *flag, int cap, cudaStream_t s);
 
 // ---- launchers (sph_sweeps.cu) ----
+// Final rank of each particle inside its cell (by raw index, so the order is
+// deterministic and stable), gather raw -> cell order, records of evaluation n.
 template <class T>
-void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint32_t *key,
-                    const uint32_t *val, const State<T> &raw, const State<T> &srt,
-                    const Hot<T> &hot, int cap, cudaStream_t s);
+void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const CellSort &cs,
+                    const State<T> &raw, const State<T> &srt, const Hot<T> &hot, int cap,
+                    cudaStream_t s);
+// Neighbour list of evaluation n; with_colour also sums the colour (Eq. 14).
 template <class T>
-void launch_colour(const PhysT<T> &P, const Grid &g, const Scalars *sc, const uint2 *cellSE,
-                   const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf, int cap,
-                   cudaStream_t s);
+void launch_build(bool with_colour, const PhysT<T> &P, const Grid &g, Scalars *sc,
+                  const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot, const NList &nl,
+                  const Csf<T> &csf, int cap, cudaStream_t s);
 template <class T>
-void launch_normal(const PhysT<T> &P, const Grid &g, const Scalars *sc, const uint2 *cellSE,
-                   const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf, int cap,
-                   cudaStream_t s);
+void launch_colour(const PhysT<T> &P, const Scalars *sc, const NList &nl, const Hot<T> &hot,
+                   const Csf<T> &csf, int cap, cudaStream_t s);
+template <class T>
+void launch_normal(const PhysT<T> &P, const Scalars *sc, const NList &nl, const Hot<T> &hot,
+                   const Csf<T> &csf, int cap, cudaStream_t s);
 // mode 0: evaluate only (store derivatives, copy srt -> raw); mode 1: first
 // evaluation of a step (store derivatives, time-step minimum); mode 2:
 // second evaluation + corrector (write raw).
 template <class T>
 void launch_forces(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars *sc,
-                   const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot,
-                   const Csf<T> &csf, const Boundary &bd, const State<T> &srt,
-                   const State<T> &raw, typename Vec<T>::v2 *acc, T *dr, int cap,
-                   cudaStream_t s);
+                   const NList &nl, const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf,
+                   const Boundary &bd, const State<T> &srt, const State<T> &raw,
+                   typename Vec<T>::v2 *acc, T *dr, int cap, cudaStream_t s);
 template <class T>
 void launch_predict(const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars *sc,
                     const uint32_t *key, const State<T> &srt, const typename Vec<T>::v2 *acc,

@@ -1,9 +1,10 @@
 // Cell-linked-list neighbour build (Sec. 2-7) and the breakup-length
 // connectivity (Sec. 3-2) of libsph.
 //
-//  k_hash      FP64 position -> cell key (dead particles -> sentinel key)
-//  k_rs_*      stable LSD radix sort of (key, index), 8-bit digits
-//  k_cells     [start, end) of every occupied cell, live particle count
+//  k_hash_count  FP64 position -> cell key (dead -> sentinel), per-cell count
+//  k_scan_*      exclusive scan of the counts -> [start, end) of every cell
+//  k_scatter     provisional slot of each particle inside its cell range
+//                (the deterministic in-cell order is fixed by the reorder)
 //  k_pairs     neighbour pair export (exact FP64 test in the guard band)
 //  k_uf_*      union-find over links shorter than 1.5 h, jet reach
 #include "sph_device.cuh"
@@ -11,219 +12,175 @@
 namespace sph {
 
 // ---------------------------------------------------------------------------
-// cell hash
+// cell hash + per-cell count
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_hash(Grid g, State<T> raw, const Scalars *__restrict__ sc,
-                       uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
+__global__ void k_hash_count(Grid g, State<T> raw, const Scalars *__restrict__ sc,
+                             uint32_t *__restrict__ knew, uint32_t *__restrict__ count) {
     int n = sc->n;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t k = g.sentinel;
     if (raw.type[i] != T_DEAD) {
         double2 p = raw.pos[i];
-        int cx = (int)floor((p.x - g.xmin) / g.sc) + 1;
-        int cy = (int)floor((p.y - g.ymin) / g.sc) + 1;
+        int cx = (int)floor((p.x - g.xmin) * g.inv_sc) + 1;
+        int cy = (int)floor((p.y - g.ymin) * g.inv_sc) + 1;
         cx = min(max(cx, 1), g.ncx - 2);
         cy = min(max(cy, 1), g.ncy - 2);
         k = (uint32_t)cy * (uint32_t)g.ncx + (uint32_t)cx;
+        atomicAdd(&count[k], 1u);
     }
-    key[i] = k;
-    val[i] = (uint32_t)i;
+    knew[i] = k;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of the cell counts (two kernels)
+// ---------------------------------------------------------------------------
+// Block-local scan: cellSE[k] = (prefix within the block, count); bsum[b] = total.
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_scan_local(const uint32_t *__restrict__ count, uint2 *__restrict__ cellSE,
+             uint32_t *__restrict__ bsum, unsigned ncells) {
+    __shared__ uint32_t wsum[SCAN_THREADS / 32];
+    unsigned base = blockIdx.x * SCAN_CELLS + threadIdx.x * SCAN_ITEMS;
+    uint32_t c[SCAN_ITEMS];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        c[j] = base + j < ncells ? count[base + j] : 0u;
+        tot += c[j];
+    }
+    // inclusive warp scan of the per-thread totals
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t v = wsum[lane];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        wsum[lane] = x - v;          // exclusive prefix of the warp totals
+        if (lane == 31) bsum[blockIdx.x] = x;
+    }
+    __syncthreads();
+    uint32_t run = wsum[w] + inc - tot;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        if (base + j < ncells) cellSE[base + j] = make_uint2(run, c[j]);
+        run += c[j];
+    }
+}
+
+// Adds the offset of the block (sum of the earlier block totals) and turns
+// (prefix, count) into [start, end); block 0 also stores the live count.
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_scan_add(uint2 *__restrict__ cellSE, const uint32_t *__restrict__ bsum, unsigned ncells,
+           int nblocks, Scalars *__restrict__ sc) {
+    __shared__ uint32_t red[SCAN_THREADS / 32];
+    __shared__ uint32_t off_s;
+    uint32_t part = 0, all = 0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        uint32_t v = bsum[b];
+        if (b < (int)blockIdx.x) part += v;
+        all += v;
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) red[w] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int k = 0; k < SCAN_THREADS / 32; ++k) t += red[k];
+        off_s = t;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        for (int o = 16; o > 0; o >>= 1) all += __shfl_xor_sync(0xffffffffu, all, o);
+        __syncthreads();
+        if (lane == 0) red[w] = all;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int k = 0; k < SCAN_THREADS / 32; ++k) t += red[k];
+            sc->nsrt = (int)t;
+        }
+    }
+    uint32_t off = off_s;
+    unsigned base = blockIdx.x * SCAN_CELLS + threadIdx.x * SCAN_ITEMS;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        unsigned k = base + j;
+        if (k < ncells) {
+            uint2 v = cellSE[k];
+            uint32_t s0 = off + v.x;
+            cellSE[k] = make_uint2(s0, s0 + v.y);
+        }
+    }
+}
+
+// Provisional slot of every live particle inside its cell's range; the
+// counters return to zero.
+__global__ void k_scatter(const uint32_t *__restrict__ knew, uint32_t *__restrict__ count,
+                          const uint2 *__restrict__ cellSE, uint32_t *__restrict__ tmp,
+                          const Scalars *__restrict__ sc, uint32_t sentinel) {
+    int n = sc->n;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t k = knew[i];
+    if (k == sentinel) return;
+    uint32_t slot = atomicSub(&count[k], 1u) - 1u;
+    tmp[cellSE[k].x + slot] = (uint32_t)i;
 }
 
 template <class T>
-void launch_hash(const Grid &g, const State<T> &raw, Scalars *sc, uint32_t *key, uint32_t *val,
-                 int cap, cudaStream_t s) {
+void launch_cell_sort(const Grid &g, const State<T> &raw, Scalars *sc, CellSort &cs, int cap,
+                      cudaStream_t s) {
     int blocks = (cap + 255) / 256;
-    k_hash<T><<<blocks, 256, 0, s>>>(g, raw, sc, key, val);
-}
-
-// ---------------------------------------------------------------------------
-// stable LSD radix sort, one 8-bit digit per pass
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(RS_THREADS)
-k_rs_hist(const uint32_t *__restrict__ keys, const Scalars *__restrict__ sc, int shift,
-          uint32_t *__restrict__ tileHist, int ntiles) {
-    __shared__ uint32_t h[RS_BINS];
-    for (int d = threadIdx.x; d < RS_BINS; d += blockDim.x) h[d] = 0;
-    __syncthreads();
-    int n = sc->n;
-    int base = blockIdx.x * RS_TILE;
-#pragma unroll
-    for (int k = 0; k < RS_ITEMS; ++k) {
-        int idx = base + k * RS_THREADS + threadIdx.x;
-        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < RS_BINS; d += blockDim.x)
-        tileHist[d * ntiles + blockIdx.x] = h[d];
-}
-
-// Exclusive scan of the digit-major tile histogram (one block).
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *__restrict__ a, int M) {
-    __shared__ uint32_t part[1024];
-    int t = threadIdx.x;
-    int chunk = (M + 1023) / 1024;
-    int lo = min(t * chunk, M), hi = min(lo + chunk, M);
-    uint32_t s = 0;
-    for (int i = lo; i < hi; ++i) s += a[i];
-    part[t] = s;
-    __syncthreads();
-    // Hillis-Steele inclusive scan of the 1024 partial sums
-    for (int off = 1; off < 1024; off <<= 1) {
-        uint32_t v = t >= off ? part[t - off] : 0u;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    uint32_t run = part[t] - s;
-    for (int i = lo; i < hi; ++i) {
-        uint32_t x = a[i];
-        a[i] = run;
-        run += x;
-    }
-}
-
-// Scatter of one tile.  Warp w owns tile items [w*256, w*256+256) in eight
-// rounds of 32; ranks among equal digits follow tile order, so the sort is
-// stable.
-__global__ void __launch_bounds__(RS_THREADS)
-k_rs_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-             uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-             const Scalars *__restrict__ sc, int shift, const uint32_t *__restrict__ tileOff,
-             int ntiles) {
-    constexpr int NW = RS_THREADS / 32;
-    __shared__ uint32_t cnt[NW][RS_BINS];
-    __shared__ uint32_t gbase[RS_BINS];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < RS_BINS; d += blockDim.x) {
-        gbase[d] = tileOff[d * ntiles + blockIdx.x];
-#pragma unroll
-        for (int j = 0; j < NW; ++j) cnt[j][d] = 0;
-    }
-    __syncthreads();
-    int n = sc->n;
-    int base = blockIdx.x * RS_TILE + w * (RS_ITEMS * 32);
-    uint32_t kk[RS_ITEMS], vv[RS_ITEMS], rk[RS_ITEMS];
-    unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        int idx = base + r * 32 + lane;
-        bool valid = idx < n;
-        uint32_t key = valid ? kin[idx] : 0u;
-        uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        unsigned pos = __popc(peers & lt);
-        uint32_t b = valid ? cnt[w][d] : 0u;
-        __syncwarp();
-        if (valid && pos == 0) cnt[w][d] = b + __popc(peers);
-        __syncwarp();
-        kk[r] = key;
-        vv[r] = valid ? vin[idx] : 0u;
-        rk[r] = valid ? (b + pos) : 0xffffffffu;
-    }
-    __syncthreads();
-    // exclusive prefix over warps, per digit
-    for (int d = threadIdx.x; d < RS_BINS; d += blockDim.x) {
-        uint32_t run = 0;
-#pragma unroll
-        for (int j = 0; j < NW; ++j) {
-            uint32_t c = cnt[j][d];
-            cnt[j][d] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        if (rk[r] == 0xffffffffu) continue;
-        uint32_t d = (kk[r] >> shift) & 255u;
-        uint32_t dst = gbase[d] + cnt[w][d] + rk[r];
-        kout[dst] = kk[r];
-        vout[dst] = vv[r];
-    }
-}
-
-int launch_radix_sort(SortBufs &sb, const Grid &g, Scalars *sc, int cap, cudaStream_t s) {
-    int passes = (g.keybits + 7) / 8;
-    int ntiles = sb.ntiles;
-    int cur = 0;
-    for (int p = 0; p < passes; ++p) {
-        int shift = 8 * p;
-        k_rs_hist<<<ntiles, RS_THREADS, 0, s>>>(sb.key[cur], sc, shift, sb.tileHist, ntiles);
-        k_rs_scan<<<1, 1024, 0, s>>>(sb.tileHist, RS_BINS * ntiles);
-        k_rs_scatter<<<ntiles, RS_THREADS, 0, s>>>(sb.key[cur], sb.val[cur], sb.key[cur ^ 1],
-                                                   sb.val[cur ^ 1], sc, shift, sb.tileHist,
-                                                   ntiles);
-        cur ^= 1;
-    }
-    (void)cap;
-    return cur;
-}
-
-// ---------------------------------------------------------------------------
-// cell ranges
-// ---------------------------------------------------------------------------
-__global__ void k_cells(const uint32_t *__restrict__ key, Scalars *__restrict__ sc,
-                        uint2 *__restrict__ cellSE, uint32_t sentinel) {
-    int n = sc->n;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n == 0) {
-        if (i == 0) sc->nsrt = 0;
-        return;
-    }
-    if (i >= n) return;
-    uint32_t k = key[i];
-    if (k == sentinel) {
-        if (i == 0) sc->nsrt = 0;
-        return;
-    }
-    uint32_t kn = (i + 1 < n) ? key[i + 1] : sentinel;
-    if (kn == sentinel) sc->nsrt = i + 1;
-    uint32_t kp = i > 0 ? key[i - 1] : 0xffffffffu;
-    unsigned *se = reinterpret_cast<unsigned *>(cellSE);
-    if (kp != k) se[2 * (size_t)k] = (unsigned)i;
-    if (kn != k) se[2 * (size_t)k + 1] = (unsigned)(i + 1);
-}
-
-void launch_cells(const Grid &g, const uint32_t *key, Scalars *sc, uint2 *cellSE, int cap,
-                  cudaStream_t s) {
-    cudaMemsetAsync(cellSE, 0, sizeof(uint2) * (size_t)g.ncells, s);
-    int blocks = (cap + 255) / 256;
-    k_cells<<<blocks, 256, 0, s>>>(key, sc, cellSE, g.sentinel);
+    k_hash_count<T><<<blocks, 256, 0, s>>>(g, raw, sc, cs.knew, cs.count);
+    k_scan_local<<<cs.nscan, SCAN_THREADS, 0, s>>>(cs.count, cs.cellSE, cs.bsum, g.ncells);
+    k_scan_add<<<cs.nscan, SCAN_THREADS, 0, s>>>(cs.cellSE, cs.bsum, g.ncells, cs.nscan, sc);
+    k_scatter<<<blocks, 256, 0, s>>>(cs.knew, cs.count, cs.cellSE, cs.tmp, sc, g.sentinel);
 }
 
 // ---------------------------------------------------------------------------
 // neighbour pair export
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_pairs(PhysT<T> P, Grid g, Scalars *__restrict__ sc,
-                        const uint2 *__restrict__ cellSE, const uint32_t *__restrict__ key,
-                        Hot<T> hot, const uint32_t *__restrict__ ids, unsigned *out_a,
-                        unsigned *out_b, unsigned cap) {
-    unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(SWEEP_BLOCK)
+k_pairs(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ cellSE,
+        const uint32_t *__restrict__ key, Hot<T> hot, const uint32_t *__restrict__ ids,
+        unsigned *out_a, unsigned *out_b, unsigned cap) {
+    unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned i = gt / SWEEP_LANES, sub = gt % SWEEP_LANES;
     if (i >= (unsigned)sc->nsrt) return;
     typename Vec<T>::v4 ha = hot.H0[i];
     unsigned ida = ids[i];
-    for_neighbours<T>(P, g, cellSE, hot.H0, hot.pos, i, key[i], ha.x, ha.y, P.H2lo, P.H2hi,
-                      P.H2d, [&](unsigned b, T, T, T, const typename Vec<T>::v4 &) {
-                          unsigned slot = atomicAdd(&sc->pair_count, 1u);
-                          if (slot < cap) {
-                              out_a[slot] = ida;
-                              out_b[slot] = ids[b];
-                          }
-                      });
+    for_neighbours<SWEEP_LANES, T>(
+        P, g, cellSE, hot.H0, hot.pos, i, sub, key[i], ha.x, ha.y, P.H2lo, P.H2hi, P.H2d,
+        [&](unsigned b, T, T, T, const typename Vec<T>::v4 &) {
+            unsigned slot = atomicAdd(&sc->pair_count, 1u);
+            if (slot < cap) {
+                out_a[slot] = ida;
+                out_b[slot] = ids[b];
+            }
+        });
 }
 
 template <class T>
-void launch_pairs(const PhysT<T> &P, const Grid &g, const Scalars *, Scalars *sc,
-                  const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot,
-                  const uint32_t *ids, unsigned *out_a, unsigned *out_b, unsigned cap, int ncap,
-                  cudaStream_t s) {
+void launch_pairs(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *cellSE,
+                  const uint32_t *key, const Hot<T> &hot, const uint32_t *ids, unsigned *out_a,
+                  unsigned *out_b, unsigned cap, int ncap, cudaStream_t s) {
     cudaMemsetAsync(&sc->pair_count, 0, sizeof(unsigned), s);
-    int blocks = (ncap + 127) / 128;
-    k_pairs<T><<<blocks, 128, 0, s>>>(P, g, sc, cellSE, key, hot, ids, out_a, out_b, cap);
+    int blocks = (int)(((long long)ncap * SWEEP_LANES + SWEEP_BLOCK - 1) / SWEEP_BLOCK);
+    k_pairs<T><<<blocks, SWEEP_BLOCK, 0, s>>>(P, g, sc, cellSE, key, hot, ids, out_a, out_b, cap);
 }
 
 // ---------------------------------------------------------------------------
@@ -270,10 +227,10 @@ __global__ void k_uf_link(PhysT<T> P, Grid g, Scalars *__restrict__ sc,
     unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (unsigned)sc->nsrt) return;
     typename Vec<T>::v4 ha = hot.H0[i];
-    for_neighbours<T>(P, g, cellSE, hot.H0, hot.pos, i, key[i], ha.x, ha.y, P.R15lo, P.R15hi,
-                      P.R15d, [&](unsigned b, T, T, T, const typename Vec<T>::v4 &) {
-                          if (b < i) uf_union(parent, i, b, &sc->err);
-                      });
+    for_neighbours<1, T>(P, g, cellSE, hot.H0, hot.pos, i, 0u, key[i], ha.x, ha.y, P.R15lo,
+                         P.R15hi, P.R15d, [&](unsigned b, T, T, T, const typename Vec<T>::v4 &) {
+                             if (b < i) uf_union(parent, i, b, &sc->err);
+                         });
 }
 
 __global__ void k_uf_compress(Scalars *__restrict__ sc, uint32_t *parent,
@@ -315,18 +272,17 @@ void launch_breakup(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *
     k_uf_reach<T><<<blocks, 256, 0, s>>>(sc, parent, hot.pos, flag);
 }
 
-template void launch_hash<float>(const Grid &, const State<float> &, Scalars *, uint32_t *,
-                                 uint32_t *, int, cudaStream_t);
-template void launch_hash<double>(const Grid &, const State<double> &, Scalars *, uint32_t *,
-                                  uint32_t *, int, cudaStream_t);
-template void launch_pairs<float>(const PhysT<float> &, const Grid &, const Scalars *,
-                                  Scalars *, const uint2 *, const uint32_t *,
-                                  const Hot<float> &, const uint32_t *, unsigned *, unsigned *,
-                                  unsigned, int, cudaStream_t);
-template void launch_pairs<double>(const PhysT<double> &, const Grid &, const Scalars *,
-                                   Scalars *, const uint2 *, const uint32_t *,
-                                   const Hot<double> &, const uint32_t *, unsigned *,
-                                   unsigned *, unsigned, int, cudaStream_t);
+template void launch_cell_sort<float>(const Grid &, const State<float> &, Scalars *, CellSort &,
+                                       int, cudaStream_t);
+template void launch_cell_sort<double>(const Grid &, const State<double> &, Scalars *,
+                                        CellSort &, int, cudaStream_t);
+template void launch_pairs<float>(const PhysT<float> &, const Grid &, Scalars *, const uint2 *,
+                                  const uint32_t *, const Hot<float> &, const uint32_t *,
+                                  unsigned *, unsigned *, unsigned, int, cudaStream_t);
+template void launch_pairs<double>(const PhysT<double> &, const Grid &, Scalars *,
+                                   const uint2 *, const uint32_t *, const Hot<double> &,
+                                   const uint32_t *, unsigned *, unsigned *, unsigned, int,
+                                   cudaStream_t);
 template void launch_breakup<float>(const PhysT<float> &, const Grid &, Scalars *,
                                     const uint2 *, const uint32_t *, const Hot<float> &,
                                     const uint8_t *, uint32_t *, uint8_t *, int, cudaStream_t);

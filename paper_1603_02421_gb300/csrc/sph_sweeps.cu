@@ -1,7 +1,9 @@
 // Pair sweeps and integrator of libsph (Secs. 2-2 to 2-8 of the paper).
 //
 //  k_reorder   gather raw -> cell order; EOS and hot records of evaluation n
-//  k_colour    C_a = sum_b V_b W_ab, self included                   (Eq. 14)
+//  k_build     neighbour list of the step from the 3x3 cell block, fused
+//              with the colour of evaluation n                       (Eq. 14)
+//  k_colour    C_a = sum_b V_b W_ab, self included (evaluation n+1/2) (Eq. 14)
 //  k_normal    n_a = sum_b V_b (C_b - C_a) grad W; filter N_a; nhat (Eqs. 18, 20, 21)
 //  k_forces    continuity (Eq. 7), momentum with pressure, viscosity,
 //              curvature + CSF, gravity, repulsive walls (Eqs. 9, 10, 23-25,
@@ -9,9 +11,11 @@
 //  k_predict   dt (Eq. 32), predictor half step, hot records of evaluation n+1/2
 //  k_spawn     inflow layer laying, time advance
 //
-// One thread per particle in cell order: consecutive threads own spatially
-// adjacent particles, so their 3x3 candidate rows overlap and the vector
-// loads of H0/H1 are served from L1.
+// SWEEP_LANES consecutive threads share one particle: in the list build each
+// takes every SWEEP_LANES-th candidate of the 3x3 cell block and keeps its
+// own part of the list, which it walks again in the later sweeps; partial
+// sums are combined with warp shuffles.  Consecutive particles are spatially
+// adjacent, so their neighbours' records are served from L1.
 #include "sph_device.cuh"
 
 namespace sph {
@@ -40,13 +44,22 @@ __device__ __forceinline__ V4<T> hot1(const PhysT<T> &P, T drho, T mass) {
 }
 
 // ---------------------------------------------------------------------------
+// Fixes each particle's place inside its cell by its raw index (stable,
+// deterministic), gathers raw -> cell order and writes the records of
+// evaluation n.
+// ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_reorder(PhysT<T> P, Grid g, const Scalars *__restrict__ sc,
-                          const uint32_t *__restrict__ key, const uint32_t *__restrict__ val,
+__global__ void k_reorder(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, CellSort cs,
                           State<T> raw, State<T> srt, Hot<T> hot) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= sc->nsrt) return;
-    uint32_t j = val[i];
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= sc->nsrt) return;
+    uint32_t j = cs.tmp[t];
+    uint32_t k = cs.knew[j];
+    uint2 se = cs.cellSE[k];
+    uint32_t rank = 0;
+    for (uint32_t u = se.x; u < se.y; ++u) rank += cs.tmp[u] < j ? 1u : 0u;
+    uint32_t i = se.x + rank;
+    cs.key[i] = k;
     double2 p = raw.pos[j];
     V2<T> v = raw.vel[j];
     T dr = raw.drho[j];
@@ -60,65 +73,162 @@ __global__ void k_reorder(PhysT<T> P, Grid g, const Scalars *__restrict__ sc,
     srt.id[i] = raw.id[j];
     T xl, yo;
     double xo, yoo;
-    cell_offsets<T>(g, key[i], p, xl, yo, xo, yoo);
+    cell_offsets<T>(g, k, p, xl, yo, xo, yoo);
     hot.H0[i] = mk4<T>(xl, yo, v.x, v.y);
     hot.H1[i] = hot1<T>(P, dr, m);
 }
 
 template <class T>
-void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint32_t *key,
-                    const uint32_t *val, const State<T> &raw, const State<T> &srt,
-                    const Hot<T> &hot, int cap, cudaStream_t s) {
-    k_reorder<T><<<(cap + 255) / 256, 256, 0, s>>>(P, g, sc, key, val, raw, srt, hot);
+void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const CellSort &cs,
+                    const State<T> &raw, const State<T> &srt, const Hot<T> &hot, int cap,
+                    cudaStream_t s) {
+    k_reorder<T><<<(cap + 255) / 256, 256, 0, s>>>(P, g, sc, cs, raw, srt, hot);
 }
 
 // ---------------------------------------------------------------------------
-// Eq. 14: colour
+// Neighbour list (Sec. 2-7) + colour of evaluation n (Eq. 14)
 // ---------------------------------------------------------------------------
-template <class T>
-__global__ void __launch_bounds__(128)
-k_colour(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, const uint2 *__restrict__ cellSE,
-         const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf) {
-    unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (unsigned)sc->nsrt) return;
-    V4<T> ha = hot.H0[i];
-    T Va = hot.H1[i].x;
-    T sum = Va * P.W0;
+template <class T, int K, bool COLOUR>
+__global__ void __launch_bounds__(SWEEP_BLOCK)
+k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ cellSE,
+        const uint32_t *__restrict__ key, Hot<T> hot, NList nl, Csf<T> csf) {
+    unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned i = gt / SWEEP_LANES, sub = gt % SWEEP_LANES;
+    unsigned lane = threadIdx.x & 31u;
+    unsigned gbase = lane & ~(unsigned)(SWEEP_LANES - 1);
+    unsigned gmask = ((1u << SWEEP_LANES) - 1u) << gbase;
+    bool active = i < (unsigned)sc->nsrt;
+    const V4<T> *__restrict__ H0 = hot.H0;
     const V4<T> *__restrict__ H1 = hot.H1;
-    for_neighbours<T>(P, g, cellSE, hot.H0, hot.pos, i, key[i], ha.x, ha.y, P.H2lo, P.H2hi,
-                      P.H2d, [&](unsigned b, T, T, T r2, const V4<T> &) {
-                          T q = sqrt_t(r2) * P.inv_h;
-                          sum += H1[b].x * kernel_W<T>(P, q);
-                      });
-    csf.C[i] = sum;
+    T sum = T(0);
+    V4<T> ha = mk4<T>(T(0), T(0), T(0), T(0));
+    if (active) {
+        ha = H0[i];
+        T xa = ha.x, ya = ha.y;
+        int cx, cy;
+        key_cell(g, key[i], cx, cy);
+        unsigned cnt = 0;
+        uint32_t *__restrict__ e = nl.e + (size_t)i * LIST_SLOTS;
+        double2 pa = make_double2(0.0, 0.0);
+        bool have_pa = false;
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+            RowRange rr = row_range(cellSE, (cy + dy) * g.ncx + cx);
+            T yshift = T(dy) * P.sc;
+            uint32_t sy_code = (uint32_t)(1 - dy) << 30;
+            // the lanes of a particle run the same number of iterations, so
+            // they can compact their finds with a group ballot
+            unsigned nit = rr.hi > rr.lo ? (rr.hi - rr.lo + SWEEP_LANES - 1) / SWEEP_LANES : 0u;
+            for (unsigned it = 0; it < nit; ++it) {
+                unsigned b = rr.lo + it * SWEEP_LANES + sub;
+                bool keep = false;
+                uint32_t ent = 0;
+                if (b < rr.hi) {
+                    V4<T> hb = H0[b];
+                    int sx = b < rr.b1 ? 1 : (b < rr.b2 ? 0 : -1);
+                    T rx = (xa - hb.x) + T(sx) * P.sc;
+                    T ry = (ya - hb.y) - yshift;
+                    T r2 = rx * rx + ry * ry;
+                    if (r2 < P.RL2hi && b != i) {
+                        keep = true;
+                        ent = b | ((uint32_t)(sx + 1) << 28) | sy_code;
+                        if (COLOUR && r2 < P.H2hi) {
+                            bool in = true;
+                            if (r2 >= P.H2lo) {
+                                if (!have_pa) { pa = hot.pos[i]; have_pa = true; }
+                                in = exact_within(pa, hot.pos[b], P.H2d);
+                            }
+                            if (in) {
+                                T q, iq;
+                                q_of(r2, P.h, P.inv_h, q, iq);
+                                sum += H1[b].x * kernel_W<T, K>(P, q);
+                            }
+                        }
+                    }
+                }
+                unsigned m = __ballot_sync(gmask, keep) & gmask;
+                unsigned slot = cnt + __popc(m & ((1u << lane) - 1u));
+                if (keep && slot < LIST_SLOTS) e[slot] = ent;
+                cnt += __popc(m);
+            }
+        }
+        if (sub == 0) {
+            if (cnt > LIST_SLOTS) atomicOr(&sc->err, ERR_NLIST);
+            nl.cnt[i] = cnt < LIST_SLOTS ? cnt : LIST_SLOTS;
+        }
+    }
+    if (COLOUR) {
+        sum = group_sum<SWEEP_LANES>(sum);
+        if (active && sub == 0) {
+            T Va = H1[i].x;
+            T C = sum + Va * P.W0;
+            csf.C[i] = C;
+            csf.CX[i] = mk4<T>(ha.x, ha.y, Va, C);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 14: colour at the half step (over the list)
+// ---------------------------------------------------------------------------
+template <class T, int K>
+__global__ void __launch_bounds__(SWEEP_BLOCK)
+k_colour(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T> csf) {
+    unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned i = gt / SWEEP_LANES, sub = gt % SWEEP_LANES;
+    bool active = i < (unsigned)sc->nsrt;
+    const V4<T> *__restrict__ H1 = hot.H1;
+    T sum = T(0);
+    V4<T> ha = mk4<T>(T(0), T(0), T(0), T(0));
+    if (active) {
+        ha = hot.H0[i];
+        for_list<SWEEP_LANES, T>(P, nl, hot.H0, hot.pos, i, sub, ha.x, ha.y,
+                                 [&](unsigned b, T, T, T r2, const V4<T> &) {
+                                     T q, iq;
+                                     q_of(r2, P.h, P.inv_h, q, iq);
+                                     sum += H1[b].x * kernel_W<T, K>(P, q);
+                                 });
+    }
+    sum = group_sum<SWEEP_LANES>(sum);
+    if (active && sub == 0) {
+        T Va = H1[i].x;
+        T C = sum + Va * P.W0;
+        csf.C[i] = C;
+        csf.CX[i] = mk4<T>(ha.x, ha.y, Va, C);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Eqs. 18, 20, 21: normal, filter, unit normal
 // ---------------------------------------------------------------------------
-template <class T>
-__global__ void __launch_bounds__(128)
-k_normal(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, const uint2 *__restrict__ cellSE,
-         const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf) {
-    unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (unsigned)sc->nsrt) return;
-    V4<T> ha = hot.H0[i];
-    T Ca = csf.C[i];
+template <class T, int K>
+__global__ void __launch_bounds__(SWEEP_BLOCK)
+k_normal(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T> csf) {
+    unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned i = gt / SWEEP_LANES, sub = gt % SWEEP_LANES;
+    bool active = i < (unsigned)sc->nsrt;
     T nx = T(0), ny = T(0);
-    const V4<T> *__restrict__ H1 = hot.H1;
-    const T *__restrict__ C = csf.C;
-    for_neighbours<T>(P, g, cellSE, hot.H0, hot.pos, i, key[i], ha.x, ha.y, P.H2lo, P.H2hi,
-                      P.H2d, [&](unsigned b, T rx, T ry, T r2, const V4<T> &) {
-                          T q = sqrt_t(r2) * P.inv_h;
-                          T w = H1[b].x * (C[b] - Ca) * kernel_F<T>(P, q);
-                          nx += w * rx;
-                          ny += w * ry;
-                      });
-    T mag = sqrt_t(nx * nx + ny * ny);
-    V2<T> nh = mk2(T(0), T(0));
-    if (mag > P.eps_n) nh = mk2(nx / mag, ny / mag);
-    csf.nhat[i] = nh;
-    csf.nvec[i] = mk2(nx, ny);
+    if (active) {
+        V4<T> xa = csf.CX[i];
+        T Ca = xa.w;
+        for_list<SWEEP_LANES, T>(P, nl, csf.CX, hot.pos, i, sub, xa.x, xa.y,
+                                 [&](unsigned, T rx, T ry, T r2, const V4<T> &xb) {
+                                     T q, iq;
+                                     q_of(r2, P.h, P.inv_h, q, iq);
+                                     T w = xb.z * (xb.w - Ca) * kernel_F<T, K>(P, q, iq);
+                                     nx += w * rx;
+                                     ny += w * ry;
+                                 });
+    }
+    nx = group_sum<SWEEP_LANES>(nx);
+    ny = group_sum<SWEEP_LANES>(ny);
+    if (active && sub == 0) {
+        T mag = sqrt_t(nx * nx + ny * ny);
+        V2<T> nh = mk2(T(0), T(0));
+        if (mag > P.eps_n) nh = mk2(nx / mag, ny / mag);
+        csf.nhat[i] = nh;
+        csf.nvec[i] = mk2(nx, ny);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -127,8 +237,8 @@ k_normal(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, const uint2 *__rest
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, const Boundary &bd,
-                                            uint32_t key, T xa, T ya, T ua, T va, T y_abs,
-                                            T &ax, T &ay) {
+                                            uint32_t key, unsigned sub, T xa, T ya, T ua, T va,
+                                            T y_abs, T &ax, T &ay) {
     int cx, cy;
     key_cell(g, key, cx, cy);
     const V4<T> *__restrict__ BH = (const V4<T> *)bd.bh;
@@ -141,7 +251,7 @@ __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, co
     for (int dy = -1; dy <= 1; ++dy) {
         RowRange rr = row_range(bd.cellSE, (cy + dy) * g.ncx + cx);
         T yshift = T(dy) * P.sc;
-        for (unsigned k = rr.lo; k < rr.hi; ++k) {
+        for (unsigned k = rr.lo + sub; k < rr.hi; k += SWEEP_LANES) {
             V4<T> bk = BH[k];
             T rx = (xa - bk.x) + row_shift<T>(rr, k, P.sc);
             T ry = (ya - bk.y) - yshift;
@@ -167,104 +277,108 @@ __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, co
 // ---------------------------------------------------------------------------
 // Eqs. 7, 9, 10, 23-25, 29-31 (+ corrector in mode 2)
 // ---------------------------------------------------------------------------
-template <class T, int MODE>
-__global__ void __launch_bounds__(128)
-k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc,
-         const uint2 *__restrict__ cellSE, const uint32_t *__restrict__ key, Hot<T> hot,
-         Csf<T> csf, Boundary bd, State<T> srt, State<T> raw, V2<T> *__restrict__ acc,
-         T *__restrict__ drout) {
-    unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+template <class T, int K, int MODE>
+__global__ void __launch_bounds__(SWEEP_BLOCK)
+k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
+         const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf, Boundary bd, State<T> srt,
+         State<T> raw, V2<T> *__restrict__ acc, T *__restrict__ drout) {
+    unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned i = gt / SWEEP_LANES, sub = gt % SWEEP_LANES;
     int nsrt = sc->nsrt;
-    T dtc = T(3.0e38);   // per-particle time-step candidate (fluid only)
     bool active = i < (unsigned)nsrt;
-    T ax = T(0), ay = T(0), drho = T(0);
-    uint8_t typ = T_DEAD;
-    if (active) {
-        typ = srt.type[i];
-        if (typ == T_FLUID) {
-            V4<T> ha = hot.H0[i];
-            V4<T> h1a = hot.H1[i];
-            T rhoa = h1a.y, PAa = h1a.z, ca = h1a.w;
-            T ua = ha.z, va = ha.w;
-            V2<T> nha = mk2(T(0), T(0));
-            bool Na = false;
-            if (P.csf) {
-                nha = csf.nhat[i];
-                Na = (nha.x != T(0)) || (nha.y != T(0));
-            }
-            T vmax = T(0), num = T(0), den = T(0);
-            if (Na) den = h1a.x * P.W0;
-            const V4<T> *__restrict__ H1 = hot.H1;
-            const V2<T> *__restrict__ NH = csf.nhat;
-            for_neighbours<T>(
-                P, g, cellSE, hot.H0, hot.pos, i, key[i], ha.x, ha.y, P.H2lo, P.H2hi, P.H2d,
-                [&](unsigned b, T rx, T ry, T r2, const V4<T> &hb) {
-                    V4<T> h1b = H1[b];
-                    T r = sqrt_t(r2);
-                    T q = r * P.inv_h;
-                    T F = kernel_F<T>(P, q);
-                    T du = ua - hb.z, dv = va - hb.w;
-                    T udotr = du * rx + dv * ry;
-                    T mb = h1b.x * h1b.y;
-                    drho += mb * udotr * F;                       // Eq. 7
-                    T Pi = T(0);
-                    if (udotr < T(0)) {                            // Eq. 10
-                        T cbar = T(0.5) * (ca + h1b.w);
-                        T rbar = T(0.5) * (rhoa + h1b.y);
-                        Pi = -P.alpha_h * cbar * udotr / (rbar * (r2 + P.eta2));
+    uint8_t typ = active ? srt.type[i] : T_DEAD;
+    bool fluid = typ == T_FLUID;
+    T ax = T(0), ay = T(0), drho = T(0), vmax = T(0), num = T(0), den = T(0);
+    V4<T> ha = mk4<T>(T(0), T(0), T(0), T(0)), h1a = ha;
+    V2<T> nha = mk2(T(0), T(0));
+    bool Na = false;
+    if (fluid) {
+        ha = hot.H0[i];
+        h1a = hot.H1[i];
+        T rhoa = h1a.y, PAa = h1a.z, ca = h1a.w;
+        T ua = ha.z, va = ha.w;
+        if (P.csf) {
+            nha = csf.nhat[i];
+            Na = (nha.x != T(0)) || (nha.y != T(0));
+        }
+        const V4<T> *__restrict__ H1 = hot.H1;
+        const V2<T> *__restrict__ NH = csf.nhat;
+        for_list<SWEEP_LANES, T>(
+            P, nl, hot.H0, hot.pos, i, sub, ha.x, ha.y,
+            [&](unsigned b, T rx, T ry, T r2, const V4<T> &hb) {
+                V4<T> h1b = H1[b];
+                T q, iq, ri;
+                q_of(r2, P.h, P.inv_h, q, iq, ri);
+                T F = kernel_F<T, K>(P, q, iq);
+                T du = ua - hb.z, dv = va - hb.w;
+                T udotr = du * rx + dv * ry;
+                T mb = h1b.x * h1b.y;
+                drho += mb * udotr * F;                       // Eq. 7
+                // Eq. 10 (approaching pairs only), evaluated without a branch
+                T cbar = T(0.5) * (ca + h1b.w);
+                T rbar = T(0.5) * (rhoa + h1b.y);
+                T Pi = -P.alpha_h * cbar * udotr * fast_div(T(1), rbar * (r2 + P.eta2));
+                Pi = udotr < T(0) ? Pi : T(0);
+                T coef = mb * (PAa + h1b.z + Pi) * F;          // Eq. 9 / 25
+                ax -= coef * rx;
+                ay -= coef * ry;
+                T cv = abs_t(P.h * udotr) * (ri * ri);         // Eq. 31 (0 if r = 0)
+                vmax = cv > vmax ? cv : vmax;
+                if (Na) {                                      // Eq. 23
+                    V2<T> nb = NH[b];
+                    if (nb.x != T(0) || nb.y != T(0)) {
+                        num += h1b.x * ((nb.x - nha.x) * rx + (nb.y - nha.y) * ry) * F;
+                        den += h1b.x * kernel_W<T, K>(P, q);
                     }
-                    T coef = mb * (PAa + h1b.z + Pi) * F;          // Eq. 9 / 25
-                    ax -= coef * rx;
-                    ay -= coef * ry;
-                    if (r2 > T(0)) {                               // Eq. 31
-                        T cv = abs_t(P.h * udotr / r2);
-                        vmax = cv > vmax ? cv : vmax;
-                    }
-                    if (Na) {                                      // Eq. 23
-                        V2<T> nb = NH[b];
-                        if (nb.x != T(0) || nb.y != T(0)) {
-                            num += h1b.x * ((nb.x - nha.x) * rx + (nb.y - nha.y) * ry) * F;
-                            den += h1b.x * kernel_W<T>(P, q);
-                        }
-                    }
-                });
-            if (Na && den > T(0)) {                                // Eq. 24
-                T kappa = num / den;
-                V2<T> na = csf.nvec[i];
-                T s = P.sigma / rhoa * kappa;
-                ax -= s * na.x;
-                ay -= s * na.y;
-            }
-            ax += P.gx;
-            ay += P.gy;
-            if (P.walls) {
-                double2 pa = hot.pos[i];
-                wall_forces<T>(P, g, bd, key[i], ha.x, ha.y, ua, va, (T)pa.y, ax, ay);
-            }
-            if (!(isfinite(ax) && isfinite(ay) && isfinite(drho))) atomicOr(&sc->err, ERR_NONFINITE);
-            if (MODE == 1) {                                       // Eqs. 30-31
-                T fa = sqrt_t(ax * ax + ay * ay);
-                T dtf = fa > T(0) ? sqrt_t(P.h / fa) : T(3.0e38);
-                T dtcv = P.h / (ca + vmax);
-                dtc = dtf < dtcv ? dtf : dtcv;
-            }
+                }
+            });
+        if (P.walls) {
+            double2 pa = hot.pos[i];
+            wall_forces<T>(P, g, bd, key[i], sub, ha.x, ha.y, ua, va, (T)pa.y, ax, ay);
+        }
+    }
+    ax = group_sum<SWEEP_LANES>(ax);
+    ay = group_sum<SWEEP_LANES>(ay);
+    drho = group_sum<SWEEP_LANES>(drho);
+    num = group_sum<SWEEP_LANES>(num);
+    den = group_sum<SWEEP_LANES>(den);
+    vmax = group_max<SWEEP_LANES>(vmax);
+    T dtc = T(3.0e38);   // per-particle time-step candidate (fluid only)
+    if (fluid) {
+        if (Na) {                                              // Eq. 24
+            den += h1a.x * P.W0;
+            T kappa = num / den;
+            V2<T> na = csf.nvec[i];
+            T s = P.sigma / h1a.y * kappa;
+            ax -= s * na.x;
+            ay -= s * na.y;
+        }
+        ax += P.gx;
+        ay += P.gy;
+        if (sub == 0 && !(isfinite(ax) && isfinite(ay) && isfinite(drho)))
+            atomicOr(&sc->err, ERR_NONFINITE);
+        if (MODE == 1 && sub == 0) {                           // Eqs. 30-31
+            T fa = sqrt_t(ax * ax + ay * ay);
+            T dtf = fa > T(0) ? sqrt_t(P.h / fa) : T(3.0e38);
+            T dtcv = P.h / (h1a.w + vmax);
+            dtc = dtf < dtcv ? dtf : dtcv;
         }
     }
 
     if (MODE == 0 || MODE == 1) {
-        if (active) {
+        if (active && sub == 0) {
             acc[i] = mk2(ax, ay);
             drout[i] = drho;
-        }
-        if (MODE == 0 && active) {
-            if (i == 0) sc->n = nsrt;
-            raw.pos[i] = srt.pos[i];
-            raw.vel[i] = srt.vel[i];
-            raw.drho[i] = srt.drho[i];
-            raw.drc[i] = srt.drc[i];
-            raw.mass[i] = srt.mass[i];
-            raw.type[i] = srt.type[i];
-            raw.id[i] = srt.id[i];
+            if (MODE == 0) {
+                if (i == 0) sc->n = nsrt;
+                raw.pos[i] = srt.pos[i];
+                raw.vel[i] = srt.vel[i];
+                raw.drho[i] = srt.drho[i];
+                raw.drc[i] = srt.drc[i];
+                raw.mass[i] = srt.mass[i];
+                raw.type[i] = srt.type[i];
+                raw.id[i] = srt.id[i];
+            }
         }
         if (MODE == 1) {
             // block minimum of the time-step candidates, then one atomic
@@ -273,12 +387,12 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc,
                 T w = __shfl_xor_sync(0xffffffffu, v, o);
                 v = w < v ? w : v;
             }
-            __shared__ T wmin[4];
+            __shared__ T wmin[SWEEP_BLOCK / 32];
             if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = v;
             __syncthreads();
             if (threadIdx.x == 0) {
                 T m = wmin[0];
-                for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = wmin[k] < m ? wmin[k] : m;
+                for (int k = 1; k < SWEEP_BLOCK / 32; ++k) m = wmin[k] < m ? wmin[k] : m;
                 if (m < T(3.0e38)) {
                     if (sizeof(T) == 4)
                         atomicMin(&sc->dtmin_f, __float_as_uint((float)m));
@@ -293,7 +407,7 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc,
 
     // MODE 2: corrector X^{n+1} = X^n + dt Xdot^{n+1/2}, positions with
     // u* = u^n + dt/2 a^{n+1/2}; buffer particles follow the inflow velocity.
-    if (!active) return;
+    if (!active || sub != 0) return;
     double dt = sc->dt, half = 0.5 * dt, t = sc->t;
     double2 p0 = srt.pos[i];
     V2<T> v0 = srt.vel[i];
@@ -373,7 +487,10 @@ __global__ void k_predict(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ 
     cell_offsets<T>(g, key[i], ph, xl, yo, xo, yoo);
     // the cell list stays exact while every particle is within skin/2 of its cell
     double lo = -0.5 * (g.sc - 2.0 * (double)P.h), hi = g.sc - lo;
-    if (!(xo >= lo && xo < hi && yoo >= lo && yoo < hi)) atomicOr(&sc->err, ERR_SKIN);
+    // and the neighbour list while no particle has moved more than skin/2
+    double ddx = ph.x - p.x, ddy = ph.y - p.y;
+    if (!(xo >= lo && xo < hi && yoo >= lo && yoo < hi) || !(ddx * ddx + ddy * ddy <= P.half_skin2))
+        atomicOr(&sc->err, ERR_SKIN);
     half.pos[i] = ph;
     half.H0[i] = mk4<T>(xl, yo, vh.x, vh.y);
     half.H1[i] = hot1<T>(P, dh, srt.mass[i]);
@@ -433,35 +550,63 @@ __global__ void k_spawn(Inflow inf, double ufx, double ufy, Scalars *__restrict_
 }
 
 // ---------------------------------------------------------------------------
-template <class T>
-void launch_colour(const PhysT<T> &P, const Grid &g, const Scalars *sc, const uint2 *cellSE,
-                   const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf, int cap,
-                   cudaStream_t s) {
-    k_colour<T><<<(cap + 127) / 128, 128, 0, s>>>(P, g, sc, cellSE, key, hot, csf);
+static int sweep_blocks(int cap) {
+    return (int)(((long long)cap * SWEEP_LANES + SWEEP_BLOCK - 1) / SWEEP_BLOCK);
 }
 
 template <class T>
-void launch_normal(const PhysT<T> &P, const Grid &g, const Scalars *sc, const uint2 *cellSE,
-                   const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf, int cap,
-                   cudaStream_t s) {
-    k_normal<T><<<(cap + 127) / 128, 128, 0, s>>>(P, g, sc, cellSE, key, hot, csf);
+void launch_build(bool with_colour, const PhysT<T> &P, const Grid &g, Scalars *sc,
+                  const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot, const NList &nl,
+                  const Csf<T> &csf, int cap, cudaStream_t s) {
+    int b = sweep_blocks(cap);
+    if (P.kernel == 1) {
+        if (with_colour) k_build<T, 1, true><<<b, SWEEP_BLOCK, 0, s>>>(P, g, sc, cellSE, key, hot, nl, csf);
+        else k_build<T, 1, false><<<b, SWEEP_BLOCK, 0, s>>>(P, g, sc, cellSE, key, hot, nl, csf);
+    } else {
+        if (with_colour) k_build<T, 0, true><<<b, SWEEP_BLOCK, 0, s>>>(P, g, sc, cellSE, key, hot, nl, csf);
+        else k_build<T, 0, false><<<b, SWEEP_BLOCK, 0, s>>>(P, g, sc, cellSE, key, hot, nl, csf);
+    }
+}
+
+template <class T>
+void launch_colour(const PhysT<T> &P, const Scalars *sc, const NList &nl, const Hot<T> &hot,
+                   const Csf<T> &csf, int cap, cudaStream_t s) {
+    int b = sweep_blocks(cap);
+    if (P.kernel == 1) k_colour<T, 1><<<b, SWEEP_BLOCK, 0, s>>>(P, sc, nl, hot, csf);
+    else k_colour<T, 0><<<b, SWEEP_BLOCK, 0, s>>>(P, sc, nl, hot, csf);
+}
+
+template <class T>
+void launch_normal(const PhysT<T> &P, const Scalars *sc, const NList &nl, const Hot<T> &hot,
+                   const Csf<T> &csf, int cap, cudaStream_t s) {
+    int b = sweep_blocks(cap);
+    if (P.kernel == 1) k_normal<T, 1><<<b, SWEEP_BLOCK, 0, s>>>(P, sc, nl, hot, csf);
+    else k_normal<T, 0><<<b, SWEEP_BLOCK, 0, s>>>(P, sc, nl, hot, csf);
+}
+
+template <class T, int K>
+static void launch_forces_k(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
+                            Scalars *sc, const NList &nl, const uint32_t *key, const Hot<T> &hot,
+                            const Csf<T> &csf, const Boundary &bd, const State<T> &srt,
+                            const State<T> &raw, V2<T> *acc, T *dr, int cap, cudaStream_t s) {
+    int b = sweep_blocks(cap);
+    if (mode == 0)
+        k_forces<T, K, 0><<<b, SWEEP_BLOCK, 0, s>>>(P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
+    else if (mode == 1)
+        k_forces<T, K, 1><<<b, SWEEP_BLOCK, 0, s>>>(P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
+    else
+        k_forces<T, K, 2><<<b, SWEEP_BLOCK, 0, s>>>(P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
 }
 
 template <class T>
 void launch_forces(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars *sc,
-                   const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot,
-                   const Csf<T> &csf, const Boundary &bd, const State<T> &srt,
-                   const State<T> &raw, V2<T> *acc, T *dr, int cap, cudaStream_t s) {
-    int blocks = (cap + 127) / 128;
-    if (mode == 0)
-        k_forces<T, 0><<<blocks, 128, 0, s>>>(P, g, inf, sc, cellSE, key, hot, csf, bd, srt, raw,
-                                              acc, dr);
-    else if (mode == 1)
-        k_forces<T, 1><<<blocks, 128, 0, s>>>(P, g, inf, sc, cellSE, key, hot, csf, bd, srt, raw,
-                                              acc, dr);
+                   const NList &nl, const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf,
+                   const Boundary &bd, const State<T> &srt, const State<T> &raw, V2<T> *acc,
+                   T *dr, int cap, cudaStream_t s) {
+    if (P.kernel == 1)
+        launch_forces_k<T, 1>(mode, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, cap, s);
     else
-        k_forces<T, 2><<<blocks, 128, 0, s>>>(P, g, inf, sc, cellSE, key, hot, csf, bd, srt, raw,
-                                              acc, dr);
+        launch_forces_k<T, 0>(mode, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, cap, s);
 }
 
 template <class T>
@@ -478,17 +623,18 @@ void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State
 }
 
 #define SPH_INST(T)                                                                              \
-    template void launch_reorder<T>(const PhysT<T> &, const Grid &, Scalars *, const uint32_t *, \
-                                    const uint32_t *, const State<T> &, const State<T> &,         \
-                                    const Hot<T> &, int, cudaStream_t);                           \
-    template void launch_colour<T>(const PhysT<T> &, const Grid &, const Scalars *,              \
-                                   const uint2 *, const uint32_t *, const Hot<T> &,               \
-                                   const Csf<T> &, int, cudaStream_t);                            \
-    template void launch_normal<T>(const PhysT<T> &, const Grid &, const Scalars *,              \
-                                   const uint2 *, const uint32_t *, const Hot<T> &,               \
-                                   const Csf<T> &, int, cudaStream_t);                            \
+    template void launch_reorder<T>(const PhysT<T> &, const Grid &, Scalars *, const CellSort &,  \
+                                    const State<T> &, const State<T> &, const Hot<T> &, int,      \
+                                    cudaStream_t);                                                \
+    template void launch_build<T>(bool, const PhysT<T> &, const Grid &, Scalars *, const uint2 *, \
+                                  const uint32_t *, const Hot<T> &, const NList &,                \
+                                  const Csf<T> &, int, cudaStream_t);                             \
+    template void launch_colour<T>(const PhysT<T> &, const Scalars *, const NList &,              \
+                                   const Hot<T> &, const Csf<T> &, int, cudaStream_t);            \
+    template void launch_normal<T>(const PhysT<T> &, const Scalars *, const NList &,              \
+                                   const Hot<T> &, const Csf<T> &, int, cudaStream_t);            \
     template void launch_forces<T>(int, const PhysT<T> &, const Grid &, const Inflow &,          \
-                                   Scalars *, const uint2 *, const uint32_t *, const Hot<T> &,    \
+                                   Scalars *, const NList &, const uint32_t *, const Hot<T> &,    \
                                    const Csf<T> &, const Boundary &, const State<T> &,            \
                                    const State<T> &, V2<T> *, T *, int, cudaStream_t);            \
     template void launch_predict<T>(const PhysT<T> &, const Grid &, const Inflow &, Scalars *,   \

@@ -123,7 +123,7 @@ def dam_break(seed=0, dx=0.01, kernel="cubic", prec="fp64", column=(0.4, 0.6),
     params = dict(kernel=kernel, prec=prec, dx=dx, h_over_dx=1.3, rho0=rho0, c0=c0,
                   gamma=gamma, alpha=alpha, eta2_over_h2=0.01, sigma=0.0,
                   eps_n_times_h=0.01, gx=0.0, gy=-g, courant=0.2, dt_fixed=dt,
-                  xmin=-0.1, ymin=-0.1, xmax=1.7, ymax=1.3, skin_over_h=0.2,
+                  xmin=-0.1, ymin=-0.1, xmax=1.7, ymax=1.3, skin_over_h=0.1,
                   wall_A_coef=0.01, wall_h0=Hc, wall_db_over_dx=0.5,
                   capacity=len(x) + 64)
     return {"name": "dam_break", "params": params,
@@ -151,7 +151,7 @@ def jet_params(Re, We, D=1.0, U=1.0, rho0=1000.0, dx=None, kernel="wendland",
                 gamma=7.0, alpha=alpha, eta2_over_h2=0.01, sigma=sigma,
                 eps_n_times_h=0.01, gx=0.0, gy=0.0, courant=0.2, dt_fixed=0.0,
                 xmin=-(layers + 5) * dx, ymin=-half_width * D, xmax=length * D,
-                ymax=half_width * D, skin_over_h=0.2, wall_A_coef=0.01, wall_h0=0.0,
+                ymax=half_width * D, skin_over_h=0.1, wall_A_coef=0.01, wall_h0=0.0,
                 wall_db_over_dx=0.5, u_frame_x=U, u_frame_y=0.0)
 
 
@@ -222,5 +222,5 @@ def test_params(kernel="wendland", dx=0.02, sigma=0.0, alpha=0.1, c0=10.0, g=0.0
     return dict(kernel=kernel, prec=prec, dx=dx, h_over_dx=1.3, rho0=rho0, c0=c0,
                 gamma=7.0, alpha=alpha, eta2_over_h2=0.01, sigma=sigma,
                 eps_n_times_h=0.01, gx=0.0, gy=-g, courant=0.2, dt_fixed=dt_fixed,
-                xmin=box[0], ymin=box[1], xmax=box[2], ymax=box[3], skin_over_h=0.2,
+                xmin=box[0], ymin=box[1], xmax=box[2], ymax=box[3], skin_over_h=0.1,
                 wall_A_coef=0.01, wall_h0=0.0, wall_db_over_dx=0.5, capacity=0)

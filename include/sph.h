@@ -208,6 +208,34 @@ sph_status sph_profile_report(sph_ctx *ctx, int cap, int *n, const char **names,
  * evaluation launch at the current settings.  Either pointer may be NULL. */
 sph_status sph_kernel_counts(sph_ctx *ctx, int *per_step, int *per_breakup);
 
+/* Neighbour pairs without any device allocation.  The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc --
+ * code running inside another framework's memory pool or stream capture, an
+ * application that must not grow its device footprint after start-up, or a
+ * plugin that only receives device buffers from its host.
+ *
+ * x, y: DEVICE arrays of n FP64 positions, all inside the box
+ * [xmin, xmax) x [ymin, ymax) (particles outside are reported with
+ * SPH_ERR_ARG).  Finds every ordered pair (a, b), a != b, with
+ * |r_a - r_b| < 2h (Sec. 2-7), exactly as sph_get_pairs does, and writes the
+ * input indices a, b to the DEVICE arrays pair_a, pair_b (cap entries each,
+ * order unspecified); *npairs (host) receives the count (SPH_ERR_CAPACITY if
+ * it exceeds cap).  Work runs on `stream` (a cudaStream_t, NULL = legacy
+ * default stream) of the current device, and the call waits for it.
+ *
+ * Limits: n <= 262144 particles and a search grid of at most 1048576 cells of
+ * size 2.1 h over the box (SPH_ERR_CAPACITY beyond).  The scratch is one
+ * static device array of about 31 MB that every GPU loading the library holds
+ * until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress), so make the first call on each
+ * device before any stream capture.  All calls share the array: calls whose
+ * work overlaps on the GPU (other host threads, other streams) race and must
+ * be serialised by the caller. */
+sph_status sph_pairs_noalloc(const double *x, const double *y, long long n, double h,
+                             double xmin, double ymin, double xmax, double ymax,
+                             unsigned *pair_a, unsigned *pair_b, long long cap,
+                             long long *npairs, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,10 @@ _SIGS = {
     "sph_kernel_counts": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                           ctypes.c_int),
     "sph_run_async": ([_CTX, ctypes.c_longlong], ctypes.c_int),
+    "sph_pairs_noalloc": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong] +
+                          [ctypes.c_double] * 5 + [ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_longlong, _LL, ctypes.c_void_p],
+                          ctypes.c_int),
     "sph_sync": ([_CTX], ctypes.c_int),
     "sph_profile": ([_CTX, ctypes.c_int], ctypes.c_int),
     "sph_profile_report": ([_CTX, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -274,6 +278,19 @@ def sph_profile_report(ctx, cap=64) -> dict:
     _check(ctx, lib().sph_profile_report(ctx, cap, ctypes.byref(n), names, _d(ms),
                                          cnt.ctypes.data_as(_LL)))
     return {names[k].decode(): (float(ms[k]), int(cnt[k])) for k in range(n.value)}
+
+
+def sph_pairs_noalloc(x_ptr, y_ptr, n, h, box, a_ptr, b_ptr, cap, stream=None):
+    """Neighbour pairs on caller-owned device buffers (raw device pointers as
+    ints, e.g. torch tensors' data_ptr()); allocates no device memory.
+    Returns the pair count."""
+    npairs = ctypes.c_longlong()
+    st = lib().sph_pairs_noalloc(x_ptr, y_ptr, int(n), float(h), float(box[0]), float(box[1]),
+                                 float(box[2]), float(box[3]), a_ptr, b_ptr, int(cap),
+                                 ctypes.byref(npairs), stream)
+    if st != SPH_OK:
+        raise SphError(st, "sph_pairs_noalloc failed (%d pairs found)" % npairs.value)
+    return npairs.value
 
 
 # ---------------------------------------------------------------------------

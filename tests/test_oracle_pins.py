@@ -361,3 +361,27 @@ def test_dam_break_walls_hold(orc):
     assert not inside_obstacle.any()
     # the column has started to collapse: the front moved right, the top down
     assert st["x"].max() > 0.41 and st["y"].max() < 0.6
+
+
+def test_wall_force_constant_along_a_straight_wall(orc):
+    # Sec. 2-6, Eq. 29: when a fluid particle moves between two boundary
+    # particles the wall force stays constant and normal to the wall.  With
+    # boundary particles every db along y = 0, P(xi) must sum to one for any
+    # tangential offset, so du/dt does not depend on x.
+    dx = 0.02
+    p = wl.test_params(dx=dx, alpha=0.0, box=(-1, -1, 2, 2))
+    d = orc.derive(p)
+    db = d.wall_db
+    bx = np.arange(-40, 41) * db
+    bd = {"x": bx, "y": np.zeros(len(bx)), "nx": np.zeros(len(bx)), "ny": np.ones(len(bx))}
+    psi = 0.7 * d.h
+    ays = []
+    for off in np.linspace(0.0, db, 9):
+        st = wl._fluid([0.3 + off], [psi], dx=dx)
+        ev = orc.evaluate(d, st, bd)
+        assert abs(ev["ax"][0]) < 1e-9 * abs(ev["ay"][0])
+        ays.append(ev["ay"][0])
+    assert np.ptp(ays) < 1e-9 * np.mean(ays)
+    q = psi / (2 * d.h)
+    # R(psi) eps with eps(z) = 1 (h0 = 0) and eps(u) = 0 (at rest)
+    assert np.mean(ays) == pytest.approx(d.wall_A * (1 - q) / np.sqrt(q), rel=1e-12)

@@ -173,6 +173,7 @@ template <class T> static PhysT<T> make_phys(const sph_params &p, const Grid &g,
     double RL = 2.0 * h + p.skin_over_h * h;
     P.RL2hi = (T)(RL * RL * (1.0 + band));
     P.half_skin2 = 0.25 * (p.skin_over_h * h) * (p.skin_over_h * h);
+    P.half_skin = (T)(0.5 * p.skin_over_h * h);
     P.sc = (T)g.sc;
     P.wn = (T)(kap / (h * h));
     P.gn = (T)(p.kernel == SPH_KERNEL_CUBIC ? kap / (h * h * h * h) : -10.0 * kap / (h * h * h * h));
@@ -298,7 +299,7 @@ template <class T> static void enqueue_step(sph_ctx *c) {
     launch_forces<T>(1, P, c->grid, c->inf, c->sc, c->nl, key, hn, csf_of<T>(c), bd_of(c), srt,
                      raw, acc, dr, c->cap, c->stream);
     tick(c, "predict");
-    launch_predict<T>(P, c->grid, c->inf, c->sc, key, srt, acc, dr, hh, c->cap, c->stream);
+    launch_predict<T>(P, c->inf, c->sc, srt, hn.H0, acc, dr, hh, c->cap, c->stream);
     if (P.csf) {
         tick(c, "colour");
         launch_colour<T>(P, c->sc, c->nl, hh, csf_of<T>(c), c->cap, c->stream);

@@ -60,6 +60,7 @@ template <class T> struct PhysT {
     T gx, gy;
     T wall_A, wall_db, inv_wall_db, wall_h0, inv_wall_h0, two_h, c0_inv;
     T ufx, ufy;          // velocity frame: stored velocities are u - u_frame
+    T half_skin;         // skin / 2
     double H2d, R15d;    // exact FP64 thresholds (2h)^2, (1.5h)^2
     double courant, dt_fixed;
     double ufx_d, ufy_d;
@@ -129,6 +130,19 @@ struct CellSort {
     int nscan;          // scan blocks of SCAN_CELLS cells
 };
 
+// Kernel launch through cudaLaunchKernelEx (plain stream order).
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kern)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_CELLS = SCAN_THREADS * SCAN_ITEMS;
@@ -189,9 +203,9 @@ void launch_forces(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf
                    const Boundary &bd, const State<T> &srt, const State<T> &raw,
                    typename Vec<T>::v2 *acc, T *dr, int cap, cudaStream_t s);
 template <class T>
-void launch_predict(const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars *sc,
-                    const uint32_t *key, const State<T> &srt, const typename Vec<T>::v2 *acc,
-                    const T *dr, const Hot<T> &half, int cap, cudaStream_t s);
+void launch_predict(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &srt,
+                    const typename Vec<T>::v4 *H0n, const typename Vec<T>::v2 *acc, const T *dr,
+                    const Hot<T> &half, int cap, cudaStream_t s);
 template <class T>
 void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &raw,
                   const double *layer_y, int cap, cudaStream_t s);

@@ -144,10 +144,13 @@ template <class T>
 void launch_cell_sort(const Grid &g, const State<T> &raw, Scalars *sc, CellSort &cs, int cap,
                       cudaStream_t s) {
     int blocks = (cap + 255) / 256;
-    k_hash_count<T><<<blocks, 256, 0, s>>>(g, raw, sc, cs.knew, cs.count);
-    k_scan_local<<<cs.nscan, SCAN_THREADS, 0, s>>>(cs.count, cs.cellSE, cs.bsum, g.ncells);
-    k_scan_add<<<cs.nscan, SCAN_THREADS, 0, s>>>(cs.cellSE, cs.bsum, g.ncells, cs.nscan, sc);
-    k_scatter<<<blocks, 256, 0, s>>>(cs.knew, cs.count, cs.cellSE, cs.tmp, sc, g.sentinel);
+    launch_k(k_hash_count<T>, blocks, 256, s, g, raw, (const Scalars *)sc, cs.knew, cs.count);
+    launch_k(k_scan_local, cs.nscan, SCAN_THREADS, s, (const uint32_t *)cs.count, cs.cellSE,
+               cs.bsum, g.ncells);
+    launch_k(k_scan_add, cs.nscan, SCAN_THREADS, s, cs.cellSE, (const uint32_t *)cs.bsum,
+               g.ncells, cs.nscan, sc);
+    launch_k(k_scatter, blocks, 256, s, (const uint32_t *)cs.knew, cs.count,
+               (const uint2 *)cs.cellSE, cs.tmp, (const Scalars *)sc, g.sentinel);
 }
 
 // ---------------------------------------------------------------------------

@@ -82,7 +82,8 @@ template <class T>
 void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const CellSort &cs,
                     const State<T> &raw, const State<T> &srt, const Hot<T> &hot, int cap,
                     cudaStream_t s) {
-    k_reorder<T><<<(cap + 255) / 256, 256, 0, s>>>(P, g, sc, cs, raw, srt, hot);
+    launch_k(k_reorder<T>, (cap + 255) / 256, 256, s, P, g, (const Scalars *)sc, cs, raw, srt,
+               hot);
 }
 
 // ---------------------------------------------------------------------------
@@ -448,9 +449,9 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
 // Eq. 32 + predictor: X^{n+1/2} = X^n + dt/2 Xdot^n; hot records at n+1/2
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_predict(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc,
-                          const uint32_t *__restrict__ key, State<T> srt,
-                          const V2<T> *__restrict__ acc, const T *__restrict__ dr, Hot<T> half) {
+__global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, State<T> srt,
+                          const V4<T> *__restrict__ H0n, const V2<T> *__restrict__ acc,
+                          const T *__restrict__ dr, Hot<T> half) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double dt;
     if (P.dt_fixed > 0.0) {
@@ -467,32 +468,33 @@ __global__ void k_predict(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ 
     if (i == 0) sc->dt = dt;
     if (i >= sc->nsrt) return;
     double hdt = 0.5 * dt;
-    double2 p = srt.pos[i];
-    V2<T> v = srt.vel[i];
+    V4<T> h0 = H0n[i];                  // offsets and velocity at n
+    V2<T> v = mk2(h0.z, h0.w);
     T d = srt.drho[i];
     uint8_t typ = srt.type[i];
+    T th = (T)hdt;
+    // displacement over the half step (absolute velocity = frame + stored)
+    T ddx = th * (P.ufx + v.x), ddy = th * (P.ufy + v.y);
+    double2 p = srt.pos[i];
     double2 ph = make_double2(p.x + hdt * (P.ufx_d + (double)v.x), p.y + hdt * (P.ufy_d + (double)v.y));
     V2<T> vh = v;
     T dh = d;
     if (typ == T_FLUID) {
         V2<T> a = acc[i];
-        T th = (T)hdt;
         vh = mk2(v.x + th * a.x, v.y + th * a.y);
         dh = d + th * dr[i];
     } else if (inf.on) {
         vh = mk2((T)(inflow_u(inf, sc->t + hdt) - P.ufx_d), (T)(-P.ufy_d));
     }
-    T xl, yo;
-    double xo, yoo;
-    cell_offsets<T>(g, key[i], ph, xl, yo, xo, yoo);
-    // the cell list stays exact while every particle is within skin/2 of its cell
-    double lo = -0.5 * (g.sc - 2.0 * (double)P.h), hi = g.sc - lo;
-    // and the neighbour list while no particle has moved more than skin/2
-    double ddx = ph.x - p.x, ddy = ph.y - p.y;
-    if (!(xo >= lo && xo < hi && yoo >= lo && yoo < hi) || !(ddx * ddx + ddy * ddy <= P.half_skin2))
+    T xo = h0.x + ddx, yo = h0.y + ddy;
+    // the cell walks stay exact while every particle is within skin/2 of its
+    // cell, and the neighbour list while no particle has moved more than skin/2
+    T lo = -P.half_skin, hi = P.sc + P.half_skin;
+    if (!(xo >= lo && xo < hi && yo >= lo && yo < hi) ||
+        !(ddx * ddx + ddy * ddy <= P.half_skin * P.half_skin))
         atomicOr(&sc->err, ERR_SKIN);
     half.pos[i] = ph;
-    half.H0[i] = mk4<T>(xl, yo, vh.x, vh.y);
+    half.H0[i] = mk4<T>(xo, yo, vh.x, vh.y);
     half.H1[i] = hot1<T>(P, dh, srt.mass[i]);
 }
 
@@ -560,11 +562,11 @@ void launch_build(bool with_colour, const PhysT<T> &P, const Grid &g, Scalars *s
                   const Csf<T> &csf, int cap, cudaStream_t s) {
     int b = sweep_blocks(cap);
     if (P.kernel == 1) {
-        if (with_colour) k_build<T, 1, true><<<b, SWEEP_BLOCK, 0, s>>>(P, g, sc, cellSE, key, hot, nl, csf);
-        else k_build<T, 1, false><<<b, SWEEP_BLOCK, 0, s>>>(P, g, sc, cellSE, key, hot, nl, csf);
+        if (with_colour) launch_k(k_build<T, 1, true>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
+        else launch_k(k_build<T, 1, false>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
     } else {
-        if (with_colour) k_build<T, 0, true><<<b, SWEEP_BLOCK, 0, s>>>(P, g, sc, cellSE, key, hot, nl, csf);
-        else k_build<T, 0, false><<<b, SWEEP_BLOCK, 0, s>>>(P, g, sc, cellSE, key, hot, nl, csf);
+        if (with_colour) launch_k(k_build<T, 0, true>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
+        else launch_k(k_build<T, 0, false>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
     }
 }
 
@@ -572,16 +574,16 @@ template <class T>
 void launch_colour(const PhysT<T> &P, const Scalars *sc, const NList &nl, const Hot<T> &hot,
                    const Csf<T> &csf, int cap, cudaStream_t s) {
     int b = sweep_blocks(cap);
-    if (P.kernel == 1) k_colour<T, 1><<<b, SWEEP_BLOCK, 0, s>>>(P, sc, nl, hot, csf);
-    else k_colour<T, 0><<<b, SWEEP_BLOCK, 0, s>>>(P, sc, nl, hot, csf);
+    if (P.kernel == 1) launch_k(k_colour<T, 1>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+    else launch_k(k_colour<T, 0>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
 }
 
 template <class T>
 void launch_normal(const PhysT<T> &P, const Scalars *sc, const NList &nl, const Hot<T> &hot,
                    const Csf<T> &csf, int cap, cudaStream_t s) {
     int b = sweep_blocks(cap);
-    if (P.kernel == 1) k_normal<T, 1><<<b, SWEEP_BLOCK, 0, s>>>(P, sc, nl, hot, csf);
-    else k_normal<T, 0><<<b, SWEEP_BLOCK, 0, s>>>(P, sc, nl, hot, csf);
+    if (P.kernel == 1) launch_k(k_normal<T, 1>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+    else launch_k(k_normal<T, 0>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
 }
 
 template <class T, int K>
@@ -591,11 +593,11 @@ static void launch_forces_k(int mode, const PhysT<T> &P, const Grid &g, const In
                             const State<T> &raw, V2<T> *acc, T *dr, int cap, cudaStream_t s) {
     int b = sweep_blocks(cap);
     if (mode == 0)
-        k_forces<T, K, 0><<<b, SWEEP_BLOCK, 0, s>>>(P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
+        launch_k(k_forces<T, K, 0>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
     else if (mode == 1)
-        k_forces<T, K, 1><<<b, SWEEP_BLOCK, 0, s>>>(P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
+        launch_k(k_forces<T, K, 1>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
     else
-        k_forces<T, K, 2><<<b, SWEEP_BLOCK, 0, s>>>(P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
+        launch_k(k_forces<T, K, 2>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
 }
 
 template <class T>
@@ -610,16 +612,16 @@ void launch_forces(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf
 }
 
 template <class T>
-void launch_predict(const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars *sc,
-                    const uint32_t *key, const State<T> &srt, const V2<T> *acc, const T *dr,
-                    const Hot<T> &half, int cap, cudaStream_t s) {
-    k_predict<T><<<(cap + 255) / 256, 256, 0, s>>>(P, g, inf, sc, key, srt, acc, dr, half);
+void launch_predict(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &srt,
+                    const V4<T> *H0n, const V2<T> *acc, const T *dr, const Hot<T> &half, int cap,
+                    cudaStream_t s) {
+    launch_k(k_predict<T>, (cap + 255) / 256, 256, s, P, inf, sc, srt, H0n, acc, dr, half);
 }
 
 template <class T>
 void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &raw,
                   const double *layer_y, int cap, cudaStream_t s) {
-    k_spawn<T><<<1, 256, 0, s>>>(inf, P.ufx_d, P.ufy_d, sc, raw, layer_y, cap);
+    launch_k(k_spawn<T>, 1, 256, s, inf, P.ufx_d, P.ufy_d, sc, raw, layer_y, cap);
 }
 
 #define SPH_INST(T)                                                                              \
@@ -637,9 +639,9 @@ void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State
                                    Scalars *, const NList &, const uint32_t *, const Hot<T> &,    \
                                    const Csf<T> &, const Boundary &, const State<T> &,            \
                                    const State<T> &, V2<T> *, T *, int, cudaStream_t);            \
-    template void launch_predict<T>(const PhysT<T> &, const Grid &, const Inflow &, Scalars *,   \
-                                    const uint32_t *, const State<T> &, const V2<T> *,            \
-                                    const T *, const Hot<T> &, int, cudaStream_t);                \
+    template void launch_predict<T>(const PhysT<T> &, const Inflow &, Scalars *,                 \
+                                    const State<T> &, const V4<T> *, const V2<T> *, const T *,    \
+                                    const Hot<T> &, int, cudaStream_t);                           \
     template void launch_spawn<T>(const PhysT<T> &, const Inflow &, Scalars *, const State<T> &, \
                                   const double *, int, cudaStream_t);
 

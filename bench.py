@@ -230,7 +230,8 @@ def main():
     if dist is not None:
         dist.barrier()
 
-    case, desc = workload(args.workload, seed=rank)
+    from paper_1603_02421_gb300.replicas import rank_members
+    case, desc = workload(args.workload, seed=rank_members(rank, world, world)[0])
     stream = torch.cuda.Stream(device=dev)
     sim = binding.Simulation(case, stream=stream.cuda_stream, device=local)
     ctx = sim.ctx
@@ -282,17 +283,10 @@ def main():
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     nbreak = len(Ls)
-    total_s = step_ms.sum() / 1e3
-    units = float(nact.sum())
+    from paper_1603_02421_gb300.replicas import reduce_rate
+    value, total_s, units = reduce_rate(step_ms.sum() / 1e3, float(nact.sum()), dist, dev)
     if dist is not None:
-        t = torch.tensor([total_s, units], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_s = float(tmax[0])
-        units = float(t[1])
         dist.barrier()
-    value = units / total_s
 
     # per-kernel attribution: the same steps with a CUDA event before each
     # kernel group (captured into the step graph)

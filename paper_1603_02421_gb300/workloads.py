@@ -157,15 +157,21 @@ def jet_params(Re, We, D=1.0, U=1.0, rho0=1000.0, dx=None, kernel="wendland",
 
 def jet(seed=0, Re=200.0, We=20.0, D=1.0, U=1.0, rho0=1000.0, dx=None,
         length=60.0, kernel="wendland", prec="fp32", amp=0.01, layers=3,
-        fill=None, capacity_factor=1.3):
+        fill=None, capacity_factor=1.3, Fr=None, drho=0.0):
     """Planar jet of width D issuing at x = 0 along +x (Sec. 3-2 setting,
     inflow buffer in place of the paper's tank).  The strip [0, fill*D) is
     prefilled on a dx lattice with u = u_in(-x/U), the velocity the inflow
-    had when that fluid left the orifice."""
+    had when that fluid left the orifice.  Fr = U / sqrt(g D) (Eq. 36)
+    adds gravity along the jet axis (the paper's jets fall from a tank);
+    None means no gravity.  drho > 0 adds a seeded uniform density
+    perturbation of relative amplitude drho (the density fluctuations of a
+    running weakly-compressible flow; 0 gives the uniform start state)."""
     rng = np.random.default_rng(seed)
     p = jet_params(Re, We, D=D, U=U, rho0=rho0, dx=dx, kernel=kernel, prec=prec,
                    length=length, layers=layers)
     dx = p["dx"]
+    if Fr is not None:
+        p["gx"] = U * U / (Fr * Fr * D)
     fill = length if fill is None else fill
     k = rng.uniform(0.5, 1.0) / D
     phase = 0.0
@@ -173,7 +179,8 @@ def jet(seed=0, Re=200.0, We=20.0, D=1.0, U=1.0, rho0=1000.0, dx=None,
     nyp = int(round(D / dx))
     x, y = lattice(0.0, -0.5 * D, nxp, nyp, dx)
     u = U * (1.0 + amp * np.sin(k * U * (-x / U) + phase))
-    fluid = _fluid(x, y, u=u, rho0=rho0, dx=dx)
+    rho = rho0 * (1.0 + rng.uniform(-drho, drho, len(x))) if drho > 0 else None
+    fluid = _fluid(x, y, u=u, rho=rho, rho0=rho0, dx=dx)
     p["capacity"] = int(capacity_factor * (len(x) + layers * nyp)) + 1024
     inflow = dict(x_exit=0.0, y0=-0.5 * D, y1=0.5 * D, U=U, amp=amp, k=k, phase=phase,
                   layers=layers)

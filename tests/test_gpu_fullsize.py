@@ -1,0 +1,166 @@
+"""GPU parity at the configured workload sizes, in the launch configuration
+bench.py times (default tuning, CUDA-graph replay), plus the breakup-length
+statistic.
+
+* dam break with obstacle (dx = 0.01 m, ~2.4k fluid + wall particles, FP64)
+* planar jet, dx = D/40, 60 D (96k particles, FP32 pair sums)
+* planar jet, dx = D/100, 100 D (1.0M particles), FP32 and FP64 on the GPU
+  (single evaluations use the jet with a seeded +-0.3 % density perturbation,
+  the fluctuation level of a running weakly-compressible flow, so that the
+  state carries a pressure field; the uniform start state has none and its
+  acceleration is the surface-tension term alone)
+* breakup length: mean over samples (at fixed simulated times) after the
+  first breakup, 5 seeds, within 2 % of the oracle's 5-seed mean (long runs
+  are chaotic, so the comparison is statistical)
+
+Measured errors are appended as JSON lines to $SPH_REPORT when it is set.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1603_02421_gb300 import workloads as wl
+from tests.helpers import ambiguous_mask, oracle_sim, rel_l2, rel_l2_vec
+
+pytestmark = pytest.mark.gpu
+
+
+def report(**kw):
+    path = os.environ.get("SPH_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(kw) + "\n")
+
+
+@pytest.fixture(scope="module")
+def sph():
+    from paper_1603_02421_gb300 import binding, build
+    build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return binding
+
+
+def _traj_errors(g, st):
+    assert np.array_equal(g["id"], st["id"].astype(np.uint32))
+    return (rel_l2_vec(g["x"], g["y"], st["x"], st["y"]),
+            rel_l2_vec(g["u"], g["v"], st["u"], st["v"]),
+            rel_l2(g["rho"], st["rho"]))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_dam_break_full_size_100_steps(sph, orc, prec, tol):
+    case = wl.dam_break(seed=0, dx=0.01, prec=prec)
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.run(100)
+    osim.run(100)
+    er, eu, erho = _traj_errors(sim.state(), osim.st)
+    report(case="dam_break_c1", prec=prec, steps=100, r=er, u=eu, rho=erho)
+    assert er < tol and eu < tol and erho < tol
+
+
+def test_jet_c2_full_size_evaluation_and_step(sph, orc):
+    case = wl.jet(seed=0, Re=200, We=20, dx=1.0 / 40, length=60.0, prec="fp32", drho=0.003)
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.evaluate()
+    g = sim.state()
+    ev = osim.evaluate()
+    st = osim.st
+    keep = ~ambiguous_mask(orc, osim.d, st, ev)
+    ea = rel_l2_vec(g["ax"][keep], g["ay"][keep], ev["ax"][keep], ev["ay"][keep])
+    ed = rel_l2(g["drho"], ev["drho"]) if np.abs(ev["drho"]).max() > 0 else 0.0
+    sim.step()
+    osim.step()
+    er, eu, erho = _traj_errors(sim.state(), osim.st)
+    report(case="jet_c2", prec="fp32", accel=ea, drho_dt=ed, masked=int((~keep).sum()),
+           step_r=er, step_u=eu, step_rho=erho)
+    assert ea < 1e-5 and ed < 1e-5
+    assert erho < 1e-6 and eu < 1e-5 and er < 1e-6
+
+
+def test_jet_c2_full_size_100_steps(sph, orc):
+    case = wl.jet(seed=1, Re=200, We=20, dx=1.0 / 40, length=60.0, prec="fp32")
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.run(100)
+    osim.run(100)
+    er, eu, erho = _traj_errors(sim.state(), osim.st)
+    report(case="jet_c2", prec="fp32", steps=100, r=er, u=eu, rho=erho)
+    assert er < 1e-4 and eu < 1e-4 and erho < 1e-4
+
+
+def test_jet_c3_full_size_evaluation(sph, orc):
+    case = wl.jet(seed=0, Re=100, We=10, dx=1.0 / 100, length=100.0, prec="fp32",
+                  capacity_factor=1.15, drho=0.003)
+    osim = oracle_sim(orc, case)
+    ev = osim.evaluate()
+    st = osim.st
+    keep = ~ambiguous_mask(orc, osim.d, st, ev)
+    for prec, tol in (("fp32", 1e-5), ("fp64", 1e-10)):
+        sim = sph.Simulation(case, prec=prec)
+        sim.evaluate()
+        g = sim.state()
+        sim.close()
+        assert len(g["x"]) > 990000
+        ea = rel_l2_vec(g["ax"][keep], g["ay"][keep], ev["ax"][keep], ev["ay"][keep])
+        ed = rel_l2(g["drho"], ev["drho"]) if np.abs(ev["drho"]).max() > 0 else 0.0
+        report(case="jet_c3", prec=prec, accel=ea, drho_dt=ed, masked=int((~keep).sum()))
+        assert ea < tol and ed < tol
+
+
+def test_breakup_length_five_seed_mean(sph, orc):
+    # Gravity along the jet (Fr = 1, as for the paper's jets falling from a
+    # tank) makes the planar jet break within the run.  L is sampled at fixed
+    # simulated times (the adaptive step shrinks after breakup, so step
+    # counts do not line up); per seed the mean over samples after the first
+    # breakup, then the mean over 5 seeds.
+    times = [2.0 + 0.1 * k for k in range(15)]
+
+    def samples(sim, clock):
+        out = []
+        for tk in times:
+            while clock() < tk:
+                sim.step()
+            L, broken = sim.breakup_length()
+            if broken or out:
+                out.append(L)
+        assert out, "no breakup within the run"
+        return float(np.mean(out))
+
+    Lg, Lo = [], []
+    for seed in range(5):
+        case = wl.jet(seed=seed, Re=100, We=5, dx=1.0 / 10, length=12.0, amp=0.05, Fr=1.0)
+        g = sph.Simulation(case)
+        Lg.append(samples(g, lambda: g.time()["t"]))
+        g.close()
+        o = oracle_sim(orc, case)
+        Lo.append(samples(o, lambda: o.t))
+    mg, mo = float(np.mean(Lg)), float(np.mean(Lo))
+    report(case="breakup_5seeds", gpu=Lg, oracle=Lo, gpu_mean=mg, oracle_mean=mo,
+           rel=abs(mg - mo) / mo)
+    assert abs(mg - mo) <= 0.02 * mo
+
+
+@pytest.mark.parametrize("dx,length,label", [(1.0 / 40, 60.0, "jet_c2"),
+                                             (1.0 / 100, 100.0, "jet_c3")])
+def test_uniform_start_state_surface_tension_only(sph, orc, dx, length, label):
+    # The unperturbed strip: no pressure field, du/dt is the CSF term plus a
+    # tiny viscous term.  FP32 curvature on flat surfaces has a noise floor
+    # set by the FP32 cell offsets (~1e-7 h), which dominates this nearly
+    # zero field; the error is reported and held to 5e-5.
+    case = wl.jet(seed=0, Re=200, We=20, dx=dx, length=length, prec="fp32",
+                  capacity_factor=1.15)
+    osim = oracle_sim(orc, case)
+    ev = osim.evaluate()
+    keep = ~ambiguous_mask(orc, osim.d, osim.st, ev)
+    sim = sph.Simulation(case)
+    sim.evaluate()
+    g = sim.state()
+    ea = rel_l2_vec(g["ax"][keep], g["ay"][keep], ev["ax"][keep], ev["ay"][keep])
+    report(case=label + "_uniform_start", prec="fp32", accel=ea)
+    assert ea < 5e-5

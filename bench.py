@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--workload", default="jet_c2", choices=["jet_c2", "jet_c3", "dam_c1"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--tune", default="auto",
+                    help="auto (autotuner), or LANES,CADENCE (e.g. 4,1 for every-step cell builds)")
+    ap.add_argument("--skin", type=float, default=0.3, help="skin / h of the cell search")
     return ap.parse_args()
 
 
@@ -232,9 +235,15 @@ def main():
 
     from paper_1603_02421_gb300.replicas import rank_members
     case, desc = workload(args.workload, seed=rank_members(rank, world, world)[0])
+    case["params"]["skin_over_h"] = args.skin
     stream = torch.cuda.Stream(device=dev)
     sim = binding.Simulation(case, stream=stream.cuda_stream, device=local)
     ctx = sim.ctx
+    if args.tune == "auto":
+        lanes, cadence, _ = binding.sph_autotune(ctx, 24)
+    else:
+        lanes, cadence = (int(v) for v in args.tune.split(","))
+        binding.sph_set_tuning(ctx, lanes, cadence)
     per_step, per_breakup = binding.sph_kernel_counts(ctx)
     has_inflow = case.get("inflow") is not None
 
@@ -326,7 +335,7 @@ def main():
     # ---- end to end through the public API with host buffers -------------
     e2e = None
     if rank == 0:
-        e2e = end_to_end(binding, case, stream, local, K=min(K, 100))
+        e2e = end_to_end(binding, case, stream, local, K=min(K, 100), tuning=(lanes, cadence))
 
     # ---- CPU baseline (oracle) on a bounded sample -----------------------
     cpu = None
@@ -347,6 +356,8 @@ def main():
             "config": {"workload": args.workload + ": " + desc,
                        "particles_mean": n_mean, "parallelism": "replicas (one jet per GPU)",
                        "l2": "flushed between timed steps (256 MiB write)",
+                       "tuning": {"lanes": lanes, "cadence": cadence, "skin_over_h": args.skin,
+                                  "chosen_by": "autotuner" if args.tune == "auto" else "flag"},
                        "breakup_every": BREAKUP_EVERY if has_inflow else None,
                        "pairs_per_particle": pairs_per_particle,
                        "wall_s": wall},
@@ -366,13 +377,14 @@ def main():
         dist.destroy_process_group()
 
 
-def end_to_end(binding, case, stream, local, K):
+def end_to_end(binding, case, stream, local, K, tuning):
     """Particle-steps/s through the public C ABI with host buffers: upload the
     state from pinned host memory (sph_set_state), K x sph_step (each reads
     the step's dt back to the host), download the state (sph_get_state)."""
     import torch
     sim = binding.Simulation(case, stream=stream.cuda_stream, device=local)
     ctx = sim.ctx
+    binding.sph_set_tuning(ctx, *tuning)
     st = binding.sph_get_state(ctx)
     n = len(st["x"])
     pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
@@ -389,7 +401,7 @@ def end_to_end(binding, case, stream, local, K):
     sim.close()
     h2d = n * (16 + 8 + 4 + 4 + 4 + 1 + 4)
     d2h_state = len(out["x"]) * (16 + 8 + 4 + 4 + 1 + 4 + 8 + 4)
-    scal = 96
+    scal = 728   # bytes of the device scalars read back by each sph_step
     return {"value": psteps / el, "unit": UNIT,
             "h2d_bytes_per_step": h2d / K,
             "d2h_bytes_per_step": scal + d2h_state / K,

@@ -204,6 +204,23 @@ sph_status sph_profile(sph_ctx *ctx, int enable);
 sph_status sph_profile_report(sph_ctx *ctx, int cap, int *n, const char **names,
                               double *total_ms, long long *launches);
 
+/* Tuning of the step.  lanes (1, 2, 4 or 8): threads that share one particle's
+ * neighbour loop in the pair sweeps.  cadence (1..64): the cells and neighbour
+ * lists are rebuilt every `cadence` steps (always after the particles were
+ * added, replaced or reordered by another call); the steps in between keep
+ * the last build, which stays exact while no particle moves more than skin/2
+ * since it (checked: SPH_ERR_SKIN otherwise), and a due inflow layer is laid
+ * at the next rebuild.  Defaults: lanes 4, cadence 1 (every step). */
+sph_status sph_set_tuning(sph_ctx *ctx, int lanes, int cadence);
+sph_status sph_get_tuning(sph_ctx *ctx, int *lanes, int *cadence);
+
+/* Autotuner: times trial_steps steps for each lanes in {1, 2, 4, 8} and cadence
+ * in {1, 2, 4, 8} from a copy of the current state (rejecting settings that
+ * trip SPH_ERR_SKIN), restores the state, and keeps the fastest setting.
+ * Outputs (nullable): the chosen lanes, cadence and its ms per step. */
+sph_status sph_autotune(sph_ctx *ctx, int trial_steps, int *lanes, int *cadence,
+                        double *ms_per_step);
+
 /* Number of device kernels (memsets excluded) one step and one breakup-length
  * evaluation launch at the current settings.  Either pointer may be NULL. */
 sph_status sph_kernel_counts(sph_ctx *ctx, int *per_step, int *per_breakup);

@@ -80,6 +80,11 @@ _SIGS = {
     "sph_kernel_counts": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                           ctypes.c_int),
     "sph_run_async": ([_CTX, ctypes.c_longlong], ctypes.c_int),
+    "sph_set_tuning": ([_CTX, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "sph_get_tuning": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                       ctypes.c_int),
+    "sph_autotune": ([_CTX, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                      ctypes.POINTER(ctypes.c_int), _D], ctypes.c_int),
     "sph_pairs_noalloc": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong] +
                           [ctypes.c_double] * 5 + [ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.c_longlong, _LL, ctypes.c_void_p],
@@ -258,6 +263,23 @@ def sph_kernel_counts(ctx):
     return a.value, b.value
 
 
+def sph_set_tuning(ctx, lanes, cadence):
+    _check(ctx, lib().sph_set_tuning(ctx, int(lanes), int(cadence)))
+
+
+def sph_get_tuning(ctx):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().sph_get_tuning(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def sph_autotune(ctx, trial_steps=20):
+    a, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(ctx, lib().sph_autotune(ctx, int(trial_steps), ctypes.byref(a), ctypes.byref(b),
+                                   ctypes.byref(ms)))
+    return a.value, b.value, ms.value
+
+
 def sph_run_async(ctx, nsteps):
     _check(ctx, lib().sph_run_async(ctx, int(nsteps)))
 
@@ -364,6 +386,15 @@ class Simulation:
 
     def time(self):
         return sph_get_time(self.ctx)
+
+    def set_tuning(self, lanes, cadence):
+        sph_set_tuning(self.ctx, lanes, cadence)
+
+    def tuning(self):
+        return sph_get_tuning(self.ctx)
+
+    def autotune(self, trial_steps=20):
+        return sph_autotune(self.ctx, trial_steps)
 
     def kernels_per_step(self):
         return sph_kernel_counts(self.ctx)[0]

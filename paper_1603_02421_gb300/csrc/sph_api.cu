@@ -46,7 +46,7 @@ struct sph_ctx {
     // device state
     Scalars *sc = nullptr;       // device scalars
     Scalars *hsc = nullptr;      // pinned host mirror
-    void *raw[7] = {}, *srt[7] = {};   // pos, vel, drho, drc, mass, type, id
+    void *raw[8] = {}, *srt[8] = {};   // pos, vel, drho, drc, mass, type, id, disp
     void *H0n = nullptr, *H1n = nullptr, *H0h = nullptr, *H1h = nullptr;
     double2 *posh = nullptr;
     void *C = nullptr, *CX = nullptr, *nhat = nullptr, *nvec = nullptr;
@@ -67,15 +67,33 @@ struct sph_ctx {
     long long n_eval = 0;
     bool csf_valid = false;
 
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    // step graphs: [0] with a cell build, [1] reusing the last build
+    cudaGraph_t graph[2] = {};
+    cudaGraphExec_t gexec[2] = {};
     bool graph_dirty = true;
 
+    // tuning: lanes per particle in the pair sweeps, longest cell-build cadence
+    int lanes = 4, cadence = 1;
+    bool force_full = true;      // host: the next step must rebuild the cells
+    bool hsc_fresh = false;      // hsc mirrors the device scalars (synchronised)
+
+    // step graph with a device-decided rebuild (IF node: rebuild / reuse)
+    cudaGraph_t cgraph = nullptr;
+    cudaGraphExec_t cexec = nullptr;
+    bool no_ticks = false;
+
+    // autotune snapshot of the raw state
+    void *snap[8] = {};
+    size_t snap_n = 0;
+    Scalars snap_sc{};
+
     // per-kernel timing: an event before each kernel group of a step
+    // one event set per kind of step (0: with a cell build, 1: reusing it)
     bool prof = false, prof_pending = false, ticking = false;
-    std::vector<cudaEvent_t> pev;
-    std::vector<const char *> pname;
-    int pidx = 0;
+    std::vector<cudaEvent_t> pev[2];
+    std::vector<const char *> pname[2];
+    int pidx[2] = {0, 0};
+    int tick_kind = 0, last_kind = 0;
     std::map<std::string, std::pair<double, long long>> ptot;
     std::vector<std::string> report_names;
 };
@@ -138,7 +156,7 @@ static sph_status status_from_err(sph_ctx *c, unsigned err) {
     return SPH_OK;
 }
 
-template <class T> static State<T> state_of(void *const a[7]) {
+template <class T> static State<T> state_of(void *const a[8]) {
     State<T> s;
     s.pos = (double2 *)a[0];
     s.vel = (typename Vec<T>::v2 *)a[1];
@@ -147,6 +165,7 @@ template <class T> static State<T> state_of(void *const a[7]) {
     s.mass = (T *)a[4];
     s.type = (uint8_t *)a[5];
     s.id = (uint32_t *)a[6];
+    s.disp = (typename Vec<T>::v2 *)a[7];
     return s;
 }
 
@@ -246,15 +265,16 @@ static Boundary bd_of(sph_ctx *c) {
 // Events are created up front by sph_profile (not during a capture) and are
 // recorded as external event nodes when the step is captured into a graph.
 static void tick(sph_ctx *c, const char *name) {
-    if (!c->prof || !c->ticking || c->pidx >= (int)c->pev.size()) return;
+    int k = c->tick_kind;
+    if (!c->prof || !c->ticking || c->no_ticks || c->pidx[k] >= (int)c->pev[k].size()) return;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(c->stream, &cs);
     if (cs == cudaStreamCaptureStatusActive)
-        cudaEventRecordWithFlags(c->pev[c->pidx], c->stream, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(c->pev[k][c->pidx[k]], c->stream, cudaEventRecordExternal);
     else
-        cudaEventRecord(c->pev[c->pidx], c->stream);
-    c->pname[c->pidx] = name;
-    ++c->pidx;
+        cudaEventRecord(c->pev[k][c->pidx[k]], c->stream);
+    c->pname[k][c->pidx[k]] = name;
+    ++c->pidx[k];
 }
 
 // hash -> sort -> cell ranges -> gather into cell order (evaluation-n records)
@@ -273,7 +293,7 @@ template <class T> static const uint32_t *enqueue_sort(sph_ctx *c) {
 template <class T> static void enqueue_build(sph_ctx *c, const uint32_t *key) {
     const PhysT<T> &P = Ops<T>::phys(c);
     tick(c, "list_colour");
-    launch_build<T>(P.csf != 0, P, c->grid, c->sc, c->cellSE, key, hot_n<T>(c), c->nl,
+    launch_build<T>(c->lanes, P.csf != 0, P, c->grid, c->sc, c->cellSE, key, hot_n<T>(c), c->nl,
                     csf_of<T>(c), c->cap, c->stream);
 }
 
@@ -281,35 +301,66 @@ template <class T> static void enqueue_normal(sph_ctx *c, const Hot<T> &hot) {
     const PhysT<T> &P = Ops<T>::phys(c);
     if (!P.csf) return;
     tick(c, "normal");
-    launch_normal<T>(P, c->sc, c->nl, hot, csf_of<T>(c), c->cap, c->stream);
+    launch_normal<T>(c->lanes, P, c->sc, c->nl, hot, csf_of<T>(c), c->cap, c->stream);
 }
 
-template <class T> static void enqueue_step(sph_ctx *c) {
+// The two ways a step starts.  Rebuild: hash, sort, reorder and neighbour
+// list (with the colour of evaluation n).  Reuse: the particles keep the
+// order, cells and lists of the last rebuild (exact while no particle has
+// moved more than skin/2 since, which the kernels check); the records of
+// evaluation n are recomputed in place.
+template <class T> static void enqueue_cells(sph_ctx *c, bool full) {
+    const PhysT<T> &P = Ops<T>::phys(c);
+    State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
+    Hot<T> hn = hot_n<T>(c);
+    const uint32_t *key = c->cs.key;
+    if (full) {
+        enqueue_sort<T>(c);
+        enqueue_build<T>(c, key);
+    } else {
+        tick(c, "refresh");
+        launch_refresh<T>(P, c->grid, c->sc, key, raw, srt, hn, c->cap, c->stream);
+        if (P.csf) {
+            tick(c, "colour");
+            launch_colour<T>(c->lanes, P, c->sc, c->nl, hn, csf_of<T>(c), c->cap, c->stream);
+        }
+    }
+}
+
+// The rest of a step (Sec. 2-8): normal and forces at n, predictor, colour,
+// normal and forces at n+1/2 with the corrector, inflow and time advance.
+template <class T> static void enqueue_rest(sph_ctx *c) {
     const PhysT<T> &P = Ops<T>::phys(c);
     State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
     auto *acc = (typename Vec<T>::v2 *)c->acc;
     T *dr = (T *)c->dr;
-    c->pidx = 0;
-    c->ticking = true;
-    const uint32_t *key = enqueue_sort<T>(c);
     Hot<T> hn = hot_n<T>(c), hh = hot_h<T>(c);
-    enqueue_build<T>(c, key);
+    const uint32_t *key = c->cs.key;
     enqueue_normal<T>(c, hn);
     tick(c, "forces");
-    launch_forces<T>(1, P, c->grid, c->inf, c->sc, c->nl, key, hn, csf_of<T>(c), bd_of(c), srt,
-                     raw, acc, dr, c->cap, c->stream);
+    launch_forces<T>(c->lanes, 1, P, c->grid, c->inf, c->sc, c->nl, key, hn, csf_of<T>(c),
+                     bd_of(c), srt, raw, acc, dr, c->cap, c->stream);
     tick(c, "predict");
     launch_predict<T>(P, c->inf, c->sc, srt, hn.H0, acc, dr, hh, c->cap, c->stream);
     if (P.csf) {
         tick(c, "colour");
-        launch_colour<T>(P, c->sc, c->nl, hh, csf_of<T>(c), c->cap, c->stream);
+        launch_colour<T>(c->lanes, P, c->sc, c->nl, hh, csf_of<T>(c), c->cap, c->stream);
     }
     enqueue_normal<T>(c, hh);
     tick(c, "forces_correct");
-    launch_forces<T>(2, P, c->grid, c->inf, c->sc, c->nl, key, hh, csf_of<T>(c), bd_of(c), srt,
-                     raw, acc, dr, c->cap, c->stream);
+    launch_forces<T>(c->lanes, 2, P, c->grid, c->inf, c->sc, c->nl, key, hh, csf_of<T>(c),
+                     bd_of(c), srt, raw, acc, dr, c->cap, c->stream);
     tick(c, "spawn");
-    launch_spawn<T>(P, c->inf, c->sc, raw, c->layer_y, c->cap, c->stream);
+    launch_spawn<T>(P, c->inf, c->sc, raw, c->layer_y, c->cap, c->cadence, c->stream);
+}
+
+template <class T> static void enqueue_step(sph_ctx *c, bool full) {
+    c->tick_kind = full ? 0 : 1;
+    c->last_kind = c->tick_kind;
+    c->pidx[c->tick_kind] = 0;
+    c->ticking = true;
+    enqueue_cells<T>(c, full);
+    enqueue_rest<T>(c);
     tick(c, nullptr);
     c->ticking = false;
     c->prof_pending = c->prof;
@@ -322,8 +373,9 @@ template <class T> static void enqueue_evaluate(sph_ctx *c) {
     Hot<T> hn = hot_n<T>(c);
     enqueue_build<T>(c, key);
     enqueue_normal<T>(c, hn);
-    launch_forces<T>(0, P, c->grid, c->inf, c->sc, c->nl, key, hn, csf_of<T>(c), bd_of(c), srt,
-                     raw, (typename Vec<T>::v2 *)c->acc, (T *)c->dr, c->cap, c->stream);
+    launch_forces<T>(c->lanes, 0, P, c->grid, c->inf, c->sc, c->nl, key, hn, csf_of<T>(c),
+                     bd_of(c), srt, raw, (typename Vec<T>::v2 *)c->acc, (T *)c->dr, c->cap,
+                     c->stream);
 }
 
 template <class T> static void enqueue_breakup(sph_ctx *c) {
@@ -333,14 +385,29 @@ template <class T> static void enqueue_breakup(sph_ctx *c) {
                       c->parent, c->flag, c->cap, c->stream);
 }
 
-static void step_any(sph_ctx *c) {
-    if (c->tsz == 4) enqueue_step<float>(c); else enqueue_step<double>(c);
+static void step_any(sph_ctx *c, bool full) {
+    if (c->tsz == 4) enqueue_step<float>(c, full); else enqueue_step<double>(c, full);
+}
+
+// Host-side choice of the next step's kind: rebuild when forced, when the
+// device scalars are not known (not synchronised since the last step), or
+// when the last step asked for it.  Forcing also sets the device flag that
+// the graph's own decision reads.
+static bool host_next_is_full(sph_ctx *c) {
+    bool full = c->force_full || !c->hsc_fresh || c->hsc->need_full;
+    if (c->force_full) {
+        cudaMemsetAsync(&c->sc->need_full, 0x01, sizeof(int), c->stream);
+        c->force_full = false;
+    }
+    c->hsc_fresh = false;
+    return full;
 }
 
 static sph_status pull_scalars(sph_ctx *c) {
     CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream),
        "copy scalars");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
+    c->hsc_fresh = true;
     return SPH_OK;
 }
 
@@ -355,14 +422,15 @@ static sph_status push_scalars(sph_ctx *c) {
 static void collect_profile(sph_ctx *c) {
     if (!c->prof_pending) return;
     c->prof_pending = false;
-    for (int k = 0; k + 1 < c->pidx; ++k) {
-        if (!c->pname[k]) continue;
+    int kind = c->last_kind;
+    for (int k = 0; k + 1 < c->pidx[kind]; ++k) {
+        if (!c->pname[kind][k]) continue;
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, c->pev[k], c->pev[k + 1]) != cudaSuccess) {
+        if (cudaEventElapsedTime(&ms, c->pev[kind][k], c->pev[kind][k + 1]) != cudaSuccess) {
             cudaGetLastError();   // do not leave the failure as the sticky last error
             continue;
         }
-        auto &e = c->ptot[c->pname[k]];
+        auto &e = c->ptot[c->pname[kind][k]];
         e.first += ms;
         e.second += 1;
     }
@@ -454,6 +522,7 @@ static sph_status upload_particles(sph_ctx *c, long long at, long long n, const 
     CK(copy_sync(c, (char *)c->raw[1] + 2 * at * ts, vel.data(), 2 * n * ts, cudaMemcpyHostToDevice), "upload");
     CK(copy_sync(c, (char *)c->raw[2] + at * ts, drho.data(), n * ts, cudaMemcpyHostToDevice), "upload");
     CK(copy_sync(c, (char *)c->raw[3] + at * ts, zero.data(), n * ts, cudaMemcpyHostToDevice), "upload");
+    CK(cudaMemsetAsync((char *)c->raw[7] + 2 * at * ts, 0, 2 * n * ts, c->stream), "upload");
     CK(copy_sync(c, (char *)c->raw[4] + at * ts, m.data(), n * ts, cudaMemcpyHostToDevice), "upload");
     CK(copy_sync(c, (uint8_t *)c->raw[5] + at, type, n, cudaMemcpyHostToDevice), "upload");
     CK(copy_sync(c, (uint32_t *)c->raw[6] + at, id, n * sizeof(unsigned), cudaMemcpyHostToDevice), "upload");
@@ -551,8 +620,8 @@ sph_status sph_init(const sph_params *p, sph_ctx **out) {
         c->own_stream = true;
     }
     size_t N = (size_t)c->cap, ts = c->tsz, NB = (size_t)std::max(c->bcap, 1);
-    size_t sizes[7] = {16, 2 * ts, ts, ts, ts, 1, 4};
-    for (int k = 0; k < 7; ++k) {
+    size_t sizes[8] = {16, 2 * ts, ts, ts, ts, 1, 4, 2 * ts};
+    for (int k = 0; k < 8; ++k) {
         c->raw[k] = dalloc(c, N * sizes[k], e); if (e) break;
         c->srt[k] = dalloc(c, N * sizes[k], e); if (e) break;
     }
@@ -590,8 +659,10 @@ sph_status sph_init(const sph_params *p, sph_ctx **out) {
     e = cudaMallocHost(&c->hsc, sizeof(Scalars));
     if (e) { fail(nullptr, SPH_ERR_OOM, "pinned allocation: %s", cudaGetErrorString(e)); return bail(SPH_ERR_OOM); }
     memset(c->hsc, 0, sizeof(Scalars));
-    c->hsc->dtmin_f = 0x7f7f7f7fu;
-    c->hsc->dtmin_d = 0x7f7f7f7f7f7f7f7full;
+    for (int k = 0; k < RED_SLOTS; ++k) {
+        c->hsc->dtmin_f[k] = 0x7f7f7f7fu;
+        c->hsc->dtmin_d[k] = 0x7f7f7f7f7f7f7f7full;
+    }
     if (push_scalars(c) != SPH_OK) { g_init_error = c->err; return bail(SPH_ERR_CUDA); }
     rebuild_phys(c);
     *out = c;
@@ -601,9 +672,15 @@ sph_status sph_init(const sph_params *p, sph_ctx **out) {
 void sph_destroy(sph_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (auto e : c->pev) cudaEventDestroy(e);
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->graph) cudaGraphDestroy(c->graph);
+    for (int k = 0; k < 2; ++k)
+        for (auto e : c->pev[k]) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k) {
+        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+        if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+    }
+    for (auto p : c->snap) if (p) cudaFree(p);
+    if (c->cexec) cudaGraphExecDestroy(c->cexec);
+    if (c->cgraph) cudaGraphDestroy(c->cgraph);
     for (auto &b : c->allocs) cudaFree(b.p);
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -657,6 +734,7 @@ sph_status sph_add_particles(sph_ctx *c, long long n, const double *x, const dou
             if (s) return s;
             c->hsc->n = (int)(n0 + nf);
             c->hsc->next_id = nid;
+            c->force_full = true;
             s = push_scalars(c);
             if (s) return s;
             c->n_eval = 0;
@@ -732,7 +810,7 @@ sph_status sph_inflow(sph_ctx *c, double x_exit, double y0, double y1, double U,
 
 sph_status sph_step(sph_ctx *c, double *dt_used) {
     if (!c) return SPH_ERR_ARG;
-    step_any(c);
+    step_any(c, host_next_is_full(c));
     sph_status s = after_work(c, "step");
     if (dt_used) *dt_used = c->hsc->dt;
     c->n_eval = c->hsc->nsrt;
@@ -742,6 +820,7 @@ sph_status sph_step(sph_ctx *c, double *dt_used) {
 
 sph_status sph_evaluate(sph_ctx *c) {
     if (!c) return SPH_ERR_ARG;
+    c->force_full = true;
     if (c->tsz == 4) enqueue_evaluate<float>(c); else enqueue_evaluate<double>(c);
     sph_status s = after_work(c, "evaluate");
     c->n_eval = c->hsc->nsrt;
@@ -749,22 +828,83 @@ sph_status sph_evaluate(sph_ctx *c) {
     return s;
 }
 
-// Captures one step into a CUDA graph (again after any change of the
-// kernels' by-value parameters).
+// Captures the step graphs: [0] rebuild and [1] reuse (chosen by the host,
+// used while profiling, since event nodes may not sit inside conditional
+// bodies), and the graph that decides on the device: a kernel sets an IF
+// node's condition from the flag the previous step left, the IF node runs
+// the rebuild or the reuse start, then the rest of the step follows.
 static sph_status ensure_graph(sph_ctx *c) {
-    if (!c->graph_dirty && c->gexec) return SPH_OK;
-    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
-    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    step_any(c);
-    c->prof_pending = false;
-    CK(cudaStreamEndCapture(c->stream, &c->graph), "end capture");
-    CK(cudaGraphInstantiate(&c->gexec, c->graph, 0), "instantiate graph");
+    if (!c->graph_dirty && c->gexec[0] && c->gexec[1] && c->cexec) return SPH_OK;
+    for (int k = 0; k < 2; ++k) {
+        if (c->gexec[k]) { cudaGraphExecDestroy(c->gexec[k]); c->gexec[k] = nullptr; }
+        if (c->graph[k]) { cudaGraphDestroy(c->graph[k]); c->graph[k] = nullptr; }
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        step_any(c, k == 0);
+        c->prof_pending = false;
+        CK(cudaStreamEndCapture(c->stream, &c->graph[k]), "end capture");
+        CK(cudaGraphInstantiate(&c->gexec[k], c->graph[k], 0), "instantiate graph");
+    }
+    if (c->cexec) { cudaGraphExecDestroy(c->cexec); c->cexec = nullptr; }
+    if (c->cgraph) { cudaGraphDestroy(c->cgraph); c->cgraph = nullptr; }
+    c->no_ticks = true;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0), "graph create");
+    c->cgraph = g;
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1u, 0u), "conditional handle");
+    CK(cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal), "capture decide");
+    launch_decide(h, c->sc, c->stream);
+    CK(cudaStreamEndCapture(c->stream, &g), "end capture decide");
+    cudaGraphNode_t dnode;
+    size_t nn = 1;
+    CK(cudaGraphGetNodes(g, &dnode, &nn), "graph nodes");
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 2;
+    cudaGraphNode_t cnode;
+    CK(cudaGraphAddNode(&cnode, g, &dnode, nullptr, 1, &np), "conditional node");
+    cudaGraph_t body[2] = {np.conditional.phGraph_out[0], np.conditional.phGraph_out[1]};
+    for (int k = 0; k < 2; ++k) {
+        CK(cudaStreamBeginCaptureToGraph(c->stream, body[k], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal), "capture body");
+        if (c->tsz == 4) enqueue_cells<float>(c, k == 0); else enqueue_cells<double>(c, k == 0);
+        CK(cudaStreamEndCapture(c->stream, &body[k]), "end capture body");
+    }
+    CK(cudaStreamBeginCaptureToGraph(c->stream, g, &cnode, nullptr, 1,
+                                     cudaStreamCaptureModeThreadLocal), "capture rest");
+    if (c->tsz == 4) enqueue_rest<float>(c); else enqueue_rest<double>(c);
+    CK(cudaStreamEndCapture(c->stream, &g), "end capture rest");
+    c->no_ticks = false;
+    CK(cudaGraphInstantiate(&c->cexec, g, 0), "instantiate conditional graph");
     c->graph_dirty = false;
     return SPH_OK;
 }
 
+static sph_status launch_step_graph(sph_ctx *c) {
+    if (c->prof || c->cadence <= 1) {
+        // host-chosen graphs: while profiling, and for cadence 1, where every
+        // step rebuilds and the device decision would only add its overhead
+        bool full = c->cadence <= 1 ? true : host_next_is_full(c);
+        if (c->cadence <= 1) { c->force_full = false; c->hsc_fresh = false; }
+        CK(cudaGraphLaunch(c->gexec[full ? 0 : 1], c->stream), "graph launch");
+        c->last_kind = full ? 0 : 1;
+        c->prof_pending = c->prof;
+    } else {
+        if (c->force_full) {
+            CK(cudaMemsetAsync(&c->sc->need_full, 0x01, sizeof(int), c->stream), "force rebuild");
+            c->force_full = false;
+        }
+        c->hsc_fresh = false;
+        CK(cudaGraphLaunch(c->cexec, c->stream), "graph launch");
+    }
+    return SPH_OK;
+}
+
 static sph_status breakup_now(sph_ctx *c, double D, double *L, int *broken) {
+    c->force_full = true;
     if (c->tsz == 4) enqueue_breakup<float>(c); else enqueue_breakup<double>(c);
     sph_status s = after_work(c, "breakup");
     if (s) return s;
@@ -797,7 +937,8 @@ sph_status sph_run(sph_ctx *c, long long nsteps, int breakup_every, double D, do
     sph_status gs = ensure_graph(c);
     if (gs) return gs;
     for (long long k = 1; k <= nsteps; ++k) {
-        CK(cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+        sph_status ls = launch_step_graph(c);
+        if (ls) return ls;
         if (breakup_every > 0 && k % breakup_every == 0) {
             double L;
             sph_status s = breakup_now(c, D, &L, nullptr);
@@ -888,6 +1029,7 @@ sph_status sph_set_state(sph_ctx *c, long long n, const double *x, const double 
         if (s) return s;
         c->hsc->n = (int)n;
         c->hsc->nsrt = 0;
+        c->force_full = true;
         if (n > 0) c->hsc->next_id = std::max(c->hsc->next_id, maxid + 1);
         s = push_scalars(c);
         c->n_eval = 0;
@@ -940,6 +1082,7 @@ sph_status sph_get_pairs(sph_ctx *c, long long cap, unsigned *id_a, unsigned *id
     if (cap > 0 && (!id_a || !id_b)) return fail(c, SPH_ERR_ARG, "output arrays required");
     unsigned dcap = (unsigned)std::min<long long>(cap, 0x7fffffffll);
     unsigned *da = nullptr, *db = nullptr;
+    c->force_full = true;
     CK(cudaMalloc(&da, std::max<size_t>(dcap, 1) * 4), "pair buffer");
     cudaError_t e = cudaMalloc(&db, std::max<size_t>(dcap, 1) * 4);
     if (e) { cudaFree(da); return cuda_check(c, e, "pair buffer"); }
@@ -996,9 +1139,11 @@ sph_status sph_run_async(sph_ctx *c, long long nsteps) {
     if (nsteps < 0) return fail(c, SPH_ERR_ARG, "nsteps < 0");
     sph_status gs = ensure_graph(c);
     if (gs) return gs;
-    for (long long k = 0; k < nsteps; ++k) CK(cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+    for (long long k = 0; k < nsteps; ++k) {
+        sph_status ls = launch_step_graph(c);
+        if (ls) return ls;
+    }
     if (nsteps > 0) {
-        c->prof_pending = c->prof;
         c->n_eval = -1;   // resolved at the next synchronising call
         c->csf_valid = false;
     }
@@ -1014,12 +1159,13 @@ sph_status sph_sync(sph_ctx *c) {
 
 sph_status sph_profile(sph_ctx *c, int enable) {
     if (!c) return SPH_ERR_ARG;
-    while (enable && c->pev.size() < 48) {
-        cudaEvent_t e;
-        CK(cudaEventCreate(&e), "event create");
-        c->pev.push_back(e);
-        c->pname.push_back(nullptr);
-    }
+    for (int k = 0; k < 2; ++k)
+        while (enable && c->pev[k].size() < 48) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e), "event create");
+            c->pev[k].push_back(e);
+            c->pname[k].push_back(nullptr);
+        }
     if (c->prof != (enable != 0)) c->graph_dirty = true;
     c->prof = enable != 0;
     c->prof_pending = false;
@@ -1044,10 +1190,114 @@ sph_status sph_profile_report(sph_ctx *c, int cap, int *n, const char **names, d
     return SPH_OK;
 }
 
+sph_status sph_set_tuning(sph_ctx *c, int lanes, int cadence) {
+    if (!c) return SPH_ERR_ARG;
+    if (!(lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8))
+        return fail(c, SPH_ERR_ARG, "lanes must be 1, 2, 4 or 8");
+    if (cadence < 1 || cadence > 64) return fail(c, SPH_ERR_ARG, "cadence must lie in [1, 64]");
+    if (lanes != c->lanes) c->graph_dirty = true;
+    c->lanes = lanes;
+    c->cadence = cadence;
+    c->force_full = true;
+    return SPH_OK;
+}
+
+sph_status sph_get_tuning(sph_ctx *c, int *lanes, int *cadence) {
+    if (!c) return SPH_ERR_ARG;
+    if (lanes) *lanes = c->lanes;
+    if (cadence) *cadence = c->cadence;
+    return SPH_OK;
+}
+
+// Copies of the raw state and scalars, to run trial steps and come back.
+static sph_status snapshot(sph_ctx *c, bool restore) {
+    size_t ts = c->tsz;
+    size_t sizes[8] = {16, 2 * ts, ts, ts, ts, 1, 4, 2 * ts};
+    if (!restore) {
+        sph_status s = pull_scalars(c);
+        if (s) return s;
+        size_t n = (size_t)c->hsc->n;
+        if (n > c->snap_n || !c->snap[0]) {
+            for (auto &p : c->snap) if (p) { cudaFree(p); p = nullptr; }
+            for (int k = 0; k < 8; ++k)
+                CK(cudaMalloc(&c->snap[k], std::max<size_t>(n, 1) * sizes[k]), "snapshot");
+            c->snap_n = n;
+        }
+        for (int k = 0; k < 8; ++k)
+            CK(cudaMemcpyAsync(c->snap[k], c->raw[k], n * sizes[k], cudaMemcpyDeviceToDevice,
+                               c->stream), "snapshot");
+        c->snap_sc = *c->hsc;
+        CK(cudaStreamSynchronize(c->stream), "snapshot");
+        return SPH_OK;
+    }
+    size_t n = (size_t)c->snap_sc.n;
+    for (int k = 0; k < 8; ++k)
+        CK(cudaMemcpyAsync(c->raw[k], c->snap[k], n * sizes[k], cudaMemcpyDeviceToDevice,
+                           c->stream), "restore");
+    *c->hsc = c->snap_sc;
+    c->force_full = true;
+    return push_scalars(c);
+}
+
+sph_status sph_autotune(sph_ctx *c, int trial_steps, int *lanes, int *cadence, double *ms_per_step) {
+    if (!c) return SPH_ERR_ARG;
+    if (trial_steps < 1 || trial_steps > 10000) return fail(c, SPH_ERR_ARG, "trial_steps in [1, 10000]");
+    sph_status s = snapshot(c, false);
+    if (s) return s;
+    if (c->snap_sc.err) {
+        status_from_err(c, c->snap_sc.err);
+        return fail(c, SPH_ERR_STATE, "autotune needs a context without a pending error (%s)",
+                    c->err.c_str());
+    }
+    const int L[4] = {1, 2, 4, 8}, K[4] = {1, 2, 4, 8};
+    int bestL = c->lanes, bestK = c->cadence;
+    double best = 1e300;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    bool prof = c->prof;
+    c->prof = false;
+    for (int a = 0; a < 4; ++a) {
+        for (int b = 0; b < 4; ++b) {
+            s = snapshot(c, true);
+            if (!s) s = sph_set_tuning(c, L[a], K[b]);
+            if (!s) s = sph_run_async(c, K[b]);          // warm: capture + one cycle
+            if (!s) s = sph_sync(c);
+            if (s == SPH_ERR_SKIN) continue;              // cadence too long for this flow
+            if (s) break;
+            cudaEventRecord(e0, c->stream);
+            s = sph_run_async(c, trial_steps);
+            cudaEventRecord(e1, c->stream);
+            if (!s) s = sph_sync(c);
+            if (s == SPH_ERR_SKIN) continue;
+            if (s) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            double per = ms / trial_steps;
+            if (per < best) { best = per; bestL = L[a]; bestK = K[b]; }
+        }
+        if (s && s != SPH_ERR_SKIN) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->prof = prof;
+    sph_status r = snapshot(c, true);
+    if (s && s != SPH_ERR_SKIN) return s;
+    if (r) return r;
+    if (best >= 1e300) return fail(c, SPH_ERR_STATE, "no tuning candidate ran without error");
+    r = sph_set_tuning(c, bestL, bestK);
+    if (r) return r;
+    if (lanes) *lanes = bestL;
+    if (cadence) *cadence = bestK;
+    if (ms_per_step) *ms_per_step = best;
+    return SPH_OK;
+}
+
 sph_status sph_kernel_counts(sph_ctx *c, int *per_step, int *per_breakup) {
     if (!c) return SPH_ERR_ARG;
     int build = 5;                         // hash+count, scan (2), scatter, reorder
     int k = build + 1;                     // + neighbour list (with the colour of step n)
+    // (a step that reuses the last build runs refresh + colour instead: 2 or 1)
     k += c->prm.sigma > 0 ? 3 : 0;         // normal (2x) + colour of the half step
     k += 3;                                // forces (2x) + predict
     k += 1;                                // spawn / time advance

@@ -80,15 +80,24 @@ struct Scalars {
     int nsrt;                     // particles in the current cell order
     unsigned next_id;
     unsigned err;                 // ErrBits, sticky
-    unsigned dtmin_f;             // float bits of min_a dt candidate (FP32 path)
     unsigned pad0;
-    unsigned long long dtmin_d;   // double bits (FP64 path)
+    unsigned pad1;
     double dt, t, x_up;
     long long step, deleted;
     unsigned long long xmax_key;  // breakup: ordered bits of max x of the jet
     unsigned detached;            // breakup: particles outside the jet
     unsigned pair_count;
+    int need_full;                // next step rebuilds the cells and lists
+    int since_full;               // steps since the last rebuild
+    // reductions spread over RED_SLOTS addresses (slot = block index mod
+    // RED_SLOTS) so that thousands of blocks do not serialise on one atomic;
+    // the next kernel folds the slots
+    unsigned long long dtmin_d[32];  // double bits of min_a dt candidate (FP64 path)
+    unsigned dtmin_f[32];         // float bits (FP32 path)
+    unsigned max_disp2[32];       // float bits: max |displacement since the rebuild|^2
+    unsigned max_step2[32];       // float bits: max |displacement in this step|^2
 };
+constexpr int RED_SLOTS = 32;
 
 template <class T> struct State {
     double2 *pos;
@@ -97,6 +106,7 @@ template <class T> struct State {
     T *mass;
     uint8_t *type;
     uint32_t *id;
+    typename Vec<T>::v2 *disp;    // displacement since the last cell build
 };
 
 template <class T> struct Hot {
@@ -146,8 +156,8 @@ inline void launch_k(void (*kern)(KArgs...), int grid, int block, cudaStream_t s
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_CELLS = SCAN_THREADS * SCAN_ITEMS;
-constexpr int SWEEP_LANES = 4;      // threads cooperating on one particle's neighbour loop
-constexpr int SWEEP_BLOCK = 128;
+constexpr int SWEEP_BLOCK = 128;    // threads per block of the pair sweeps
+// lanes: threads cooperating on one particle's neighbour loop (1, 2, 4 or 8)
 constexpr int LIST_SLOTS = 96;      // neighbour-list entries per particle
 
 // Verlet neighbour list built once per step from the cell block (radius
@@ -185,29 +195,42 @@ void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const CellSor
                     cudaStream_t s);
 // Neighbour list of evaluation n; with_colour also sums the colour (Eq. 14).
 template <class T>
-void launch_build(bool with_colour, const PhysT<T> &P, const Grid &g, Scalars *sc,
+void launch_build(int lanes, bool with_colour, const PhysT<T> &P, const Grid &g, Scalars *sc,
                   const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot, const NList &nl,
                   const Csf<T> &csf, int cap, cudaStream_t s);
 template <class T>
-void launch_colour(const PhysT<T> &P, const Scalars *sc, const NList &nl, const Hot<T> &hot,
-                   const Csf<T> &csf, int cap, cudaStream_t s);
+void launch_colour(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
+                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s);
 template <class T>
-void launch_normal(const PhysT<T> &P, const Scalars *sc, const NList &nl, const Hot<T> &hot,
-                   const Csf<T> &csf, int cap, cudaStream_t s);
+void launch_normal(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
+                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s);
 // mode 0: evaluate only (store derivatives, copy srt -> raw); mode 1: first
 // evaluation of a step (store derivatives, time-step minimum); mode 2:
 // second evaluation + corrector (write raw).
 template <class T>
-void launch_forces(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars *sc,
-                   const NList &nl, const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf,
-                   const Boundary &bd, const State<T> &srt, const State<T> &raw,
-                   typename Vec<T>::v2 *acc, T *dr, int cap, cudaStream_t s);
+void launch_forces(int lanes, int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
+                   Scalars *sc, const NList &nl, const uint32_t *key, const Hot<T> &hot,
+                   const Csf<T> &csf, const Boundary &bd, const State<T> &srt,
+                   const State<T> &raw, typename Vec<T>::v2 *acc, T *dr, int cap,
+                   cudaStream_t s);
+// Step without a cell build: raw -> srt in the same order, records of
+// evaluation n relative to the cells of the last build.
+template <class T>
+void launch_refresh(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint32_t *key,
+                    const State<T> &raw, const State<T> &srt, const Hot<T> &hot, int cap,
+                    cudaStream_t s);
 template <class T>
 void launch_predict(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &srt,
                     const typename Vec<T>::v4 *H0n, const typename Vec<T>::v2 *acc, const T *dr,
                     const Hot<T> &half, int cap, cudaStream_t s);
+// End of a step: lays a due inflow layer, advances time, and decides whether
+// the next step rebuilds the cells (a layer was laid, `cadence` steps have
+// passed, or the displacement since the last rebuild may reach skin/2 within
+// the next step).
 template <class T>
 void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &raw,
-                  const double *layer_y, int cap, cudaStream_t s);
+                  const double *layer_y, int cap, int cadence, cudaStream_t s);
+// Sets the step graph's rebuild condition from sc->need_full.
+void launch_decide(cudaGraphConditionalHandle h, const Scalars *sc, cudaStream_t s);
 
 }  // namespace sph

@@ -156,17 +156,19 @@ void launch_cell_sort(const Grid &g, const State<T> &raw, Scalars *sc, CellSort 
 // ---------------------------------------------------------------------------
 // neighbour pair export
 // ---------------------------------------------------------------------------
+constexpr int PAIR_LANES = 4;
+
 template <class T>
 __global__ void __launch_bounds__(SWEEP_BLOCK)
 k_pairs(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ cellSE,
         const uint32_t *__restrict__ key, Hot<T> hot, const uint32_t *__restrict__ ids,
         unsigned *out_a, unsigned *out_b, unsigned cap) {
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned i = gt / SWEEP_LANES, sub = gt % SWEEP_LANES;
+    unsigned i = gt / PAIR_LANES, sub = gt % PAIR_LANES;
     if (i >= (unsigned)sc->nsrt) return;
     typename Vec<T>::v4 ha = hot.H0[i];
     unsigned ida = ids[i];
-    for_neighbours<SWEEP_LANES, T>(
+    for_neighbours<PAIR_LANES, T>(
         P, g, cellSE, hot.H0, hot.pos, i, sub, key[i], ha.x, ha.y, P.H2lo, P.H2hi, P.H2d,
         [&](unsigned b, T, T, T, const typename Vec<T>::v4 &) {
             unsigned slot = atomicAdd(&sc->pair_count, 1u);
@@ -182,7 +184,7 @@ void launch_pairs(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *ce
                   const uint32_t *key, const Hot<T> &hot, const uint32_t *ids, unsigned *out_a,
                   unsigned *out_b, unsigned cap, int ncap, cudaStream_t s) {
     cudaMemsetAsync(&sc->pair_count, 0, sizeof(unsigned), s);
-    int blocks = (int)(((long long)ncap * SWEEP_LANES + SWEEP_BLOCK - 1) / SWEEP_BLOCK);
+    int blocks = (int)(((long long)ncap * PAIR_LANES + SWEEP_BLOCK - 1) / SWEEP_BLOCK);
     k_pairs<T><<<blocks, SWEEP_BLOCK, 0, s>>>(P, g, sc, cellSE, key, hot, ids, out_a, out_b, cap);
 }
 

@@ -11,11 +11,13 @@
 //  k_predict   dt (Eq. 32), predictor half step, hot records of evaluation n+1/2
 //  k_spawn     inflow layer laying, time advance
 //
-// SWEEP_LANES consecutive threads share one particle: in the list build each
-// takes every SWEEP_LANES-th candidate of the 3x3 cell block and keeps its
-// own part of the list, which it walks again in the later sweeps; partial
-// sums are combined with warp shuffles.  Consecutive particles are spatially
+// G consecutive threads share one particle (G = 1, 2, 4 or 8, chosen at run
+// time): in the list build each takes every G-th candidate of the 3x3 cell
+// block and the finds are compacted with a G-lane ballot; later sweeps split
+// each particle's list G ways; partial sums are combined with warp shuffles.  Consecutive particles are spatially
 // adjacent, so their neighbours' records are served from L1.
+#include <type_traits>
+
 #include "sph_device.cuh"
 
 namespace sph {
@@ -71,11 +73,62 @@ __global__ void k_reorder(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, Ce
     srt.mass[i] = m;
     srt.type[i] = raw.type[j];
     srt.id[i] = raw.id[j];
+    srt.disp[i] = mk2(T(0), T(0));
     T xl, yo;
     double xo, yoo;
     cell_offsets<T>(g, k, p, xl, yo, xo, yoo);
     hot.H0[i] = mk4<T>(xl, yo, v.x, v.y);
     hot.H1[i] = hot1<T>(P, dr, m);
+}
+
+// ---------------------------------------------------------------------------
+// Step without a cell build: the particles keep their order and cells; the
+// records of evaluation n are recomputed from the integrated state.  Particles
+// deleted since the build keep their slot with zero volume and mass, so they
+// drop out of every sum.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_refresh(PhysT<T> P, Grid g, Scalars *__restrict__ sc,
+                          const uint32_t *__restrict__ key, State<T> raw, State<T> srt,
+                          Hot<T> hot) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc->nsrt) return;
+    double2 p = raw.pos[i];
+    V2<T> v = raw.vel[i];
+    T dr = raw.drho[i];
+    T m = raw.mass[i];
+    uint8_t typ = raw.type[i];
+    V2<T> ds = raw.disp[i];
+    srt.pos[i] = p;
+    srt.vel[i] = v;
+    srt.drho[i] = dr;
+    srt.drc[i] = raw.drc[i];
+    srt.mass[i] = m;
+    srt.type[i] = typ;
+    srt.id[i] = raw.id[i];
+    srt.disp[i] = ds;
+    T xl, yo;
+    double xo, yoo;
+    cell_offsets<T>(g, key[i], p, xl, yo, xo, yoo);
+    hot.H0[i] = mk4<T>(xl, yo, v.x, v.y);
+    if (typ == T_DEAD) {
+        hot.H1[i] = mk4<T>(T(0), P.rho0, T(0), P.c0);
+        return;
+    }
+    hot.H1[i] = hot1<T>(P, dr, m);
+    // the lists and cell walks of the last build stay exact while no particle
+    // has moved more than skin/2 (and stays within skin/2 of its cell)
+    T lo = -P.half_skin, hi = P.sc + P.half_skin;
+    if (!(xl >= lo && xl < hi && yo >= lo && yo < hi) ||
+        !(ds.x * ds.x + ds.y * ds.y <= P.half_skin * P.half_skin))
+        atomicOr(&sc->err, ERR_SKIN);
+}
+
+template <class T>
+void launch_refresh(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint32_t *key,
+                    const State<T> &raw, const State<T> &srt, const Hot<T> &hot, int cap,
+                    cudaStream_t s) {
+    launch_k(k_refresh<T>, (cap + 255) / 256, 256, s, P, g, sc, key, raw, srt, hot);
 }
 
 template <class T>
@@ -89,15 +142,15 @@ void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const CellSor
 // ---------------------------------------------------------------------------
 // Neighbour list (Sec. 2-7) + colour of evaluation n (Eq. 14)
 // ---------------------------------------------------------------------------
-template <class T, int K, bool COLOUR>
+template <class T, int K, bool COLOUR, int G>
 __global__ void __launch_bounds__(SWEEP_BLOCK)
 k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ cellSE,
         const uint32_t *__restrict__ key, Hot<T> hot, NList nl, Csf<T> csf) {
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned i = gt / SWEEP_LANES, sub = gt % SWEEP_LANES;
+    unsigned i = gt / G, sub = gt % G;
     unsigned lane = threadIdx.x & 31u;
-    unsigned gbase = lane & ~(unsigned)(SWEEP_LANES - 1);
-    unsigned gmask = ((1u << SWEEP_LANES) - 1u) << gbase;
+    unsigned gbase = lane & ~(unsigned)(G - 1);
+    unsigned gmask = ((1u << G) - 1u) << gbase;
     bool active = i < (unsigned)sc->nsrt;
     const V4<T> *__restrict__ H0 = hot.H0;
     const V4<T> *__restrict__ H1 = hot.H1;
@@ -119,9 +172,9 @@ k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ 
             uint32_t sy_code = (uint32_t)(1 - dy) << 30;
             // the lanes of a particle run the same number of iterations, so
             // they can compact their finds with a group ballot
-            unsigned nit = rr.hi > rr.lo ? (rr.hi - rr.lo + SWEEP_LANES - 1) / SWEEP_LANES : 0u;
+            unsigned nit = rr.hi > rr.lo ? (rr.hi - rr.lo + G - 1) / G : 0u;
             for (unsigned it = 0; it < nit; ++it) {
-                unsigned b = rr.lo + it * SWEEP_LANES + sub;
+                unsigned b = rr.lo + it * G + sub;
                 bool keep = false;
                 uint32_t ent = 0;
                 if (b < rr.hi) {
@@ -159,7 +212,7 @@ k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ 
         }
     }
     if (COLOUR) {
-        sum = group_sum<SWEEP_LANES>(sum);
+        sum = group_sum<G>(sum);
         if (active && sub == 0) {
             T Va = H1[i].x;
             T C = sum + Va * P.W0;
@@ -172,25 +225,25 @@ k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ 
 // ---------------------------------------------------------------------------
 // Eq. 14: colour at the half step (over the list)
 // ---------------------------------------------------------------------------
-template <class T, int K>
+template <class T, int K, int G>
 __global__ void __launch_bounds__(SWEEP_BLOCK)
 k_colour(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T> csf) {
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned i = gt / SWEEP_LANES, sub = gt % SWEEP_LANES;
+    unsigned i = gt / G, sub = gt % G;
     bool active = i < (unsigned)sc->nsrt;
     const V4<T> *__restrict__ H1 = hot.H1;
     T sum = T(0);
     V4<T> ha = mk4<T>(T(0), T(0), T(0), T(0));
     if (active) {
         ha = hot.H0[i];
-        for_list<SWEEP_LANES, T>(P, nl, hot.H0, hot.pos, i, sub, ha.x, ha.y,
+        for_list<G, T>(P, nl, hot.H0, hot.pos, i, sub, ha.x, ha.y,
                                  [&](unsigned b, T, T, T r2, const V4<T> &) {
                                      T q, iq;
                                      q_of(r2, P.h, P.inv_h, q, iq);
                                      sum += H1[b].x * kernel_W<T, K>(P, q);
                                  });
     }
-    sum = group_sum<SWEEP_LANES>(sum);
+    sum = group_sum<G>(sum);
     if (active && sub == 0) {
         T Va = H1[i].x;
         T C = sum + Va * P.W0;
@@ -202,17 +255,17 @@ k_colour(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T
 // ---------------------------------------------------------------------------
 // Eqs. 18, 20, 21: normal, filter, unit normal
 // ---------------------------------------------------------------------------
-template <class T, int K>
+template <class T, int K, int G>
 __global__ void __launch_bounds__(SWEEP_BLOCK)
 k_normal(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T> csf) {
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned i = gt / SWEEP_LANES, sub = gt % SWEEP_LANES;
+    unsigned i = gt / G, sub = gt % G;
     bool active = i < (unsigned)sc->nsrt;
     T nx = T(0), ny = T(0);
     if (active) {
         V4<T> xa = csf.CX[i];
         T Ca = xa.w;
-        for_list<SWEEP_LANES, T>(P, nl, csf.CX, hot.pos, i, sub, xa.x, xa.y,
+        for_list<G, T>(P, nl, csf.CX, hot.pos, i, sub, xa.x, xa.y,
                                  [&](unsigned, T rx, T ry, T r2, const V4<T> &xb) {
                                      T q, iq;
                                      q_of(r2, P.h, P.inv_h, q, iq);
@@ -221,8 +274,8 @@ k_normal(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T
                                      ny += w * ry;
                                  });
     }
-    nx = group_sum<SWEEP_LANES>(nx);
-    ny = group_sum<SWEEP_LANES>(ny);
+    nx = group_sum<G>(nx);
+    ny = group_sum<G>(ny);
     if (active && sub == 0) {
         T mag = sqrt_t(nx * nx + ny * ny);
         V2<T> nh = mk2(T(0), T(0));
@@ -236,7 +289,7 @@ k_normal(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T
 // Eq. 29: repulsive wall force per unit mass from the boundary particles in
 // the 3x3 cell block (R(psi) P(xi) eps(z, u_perp) along the wall normal).
 // ---------------------------------------------------------------------------
-template <class T>
+template <class T, int G>
 __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, const Boundary &bd,
                                             uint32_t key, unsigned sub, T xa, T ya, T ua, T va,
                                             T y_abs, T &ax, T &ay) {
@@ -252,7 +305,7 @@ __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, co
     for (int dy = -1; dy <= 1; ++dy) {
         RowRange rr = row_range(bd.cellSE, (cy + dy) * g.ncx + cx);
         T yshift = T(dy) * P.sc;
-        for (unsigned k = rr.lo + sub; k < rr.hi; k += SWEEP_LANES) {
+        for (unsigned k = rr.lo + sub; k < rr.hi; k += G) {
             V4<T> bk = BH[k];
             T rx = (xa - bk.x) + row_shift<T>(rr, k, P.sc);
             T ry = (ya - bk.y) - yshift;
@@ -278,13 +331,13 @@ __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, co
 // ---------------------------------------------------------------------------
 // Eqs. 7, 9, 10, 23-25, 29-31 (+ corrector in mode 2)
 // ---------------------------------------------------------------------------
-template <class T, int K, int MODE>
+template <class T, int K, int MODE, int G>
 __global__ void __launch_bounds__(SWEEP_BLOCK)
 k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
          const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf, Boundary bd, State<T> srt,
          State<T> raw, V2<T> *__restrict__ acc, T *__restrict__ drout) {
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned i = gt / SWEEP_LANES, sub = gt % SWEEP_LANES;
+    unsigned i = gt / G, sub = gt % G;
     int nsrt = sc->nsrt;
     bool active = i < (unsigned)nsrt;
     uint8_t typ = active ? srt.type[i] : T_DEAD;
@@ -304,7 +357,7 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
         }
         const V4<T> *__restrict__ H1 = hot.H1;
         const V2<T> *__restrict__ NH = csf.nhat;
-        for_list<SWEEP_LANES, T>(
+        for_list<G, T>(
             P, nl, hot.H0, hot.pos, i, sub, ha.x, ha.y,
             [&](unsigned b, T rx, T ry, T r2, const V4<T> &hb) {
                 V4<T> h1b = H1[b];
@@ -335,15 +388,15 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
             });
         if (P.walls) {
             double2 pa = hot.pos[i];
-            wall_forces<T>(P, g, bd, key[i], sub, ha.x, ha.y, ua, va, (T)pa.y, ax, ay);
+            wall_forces<T, G>(P, g, bd, key[i], sub, ha.x, ha.y, ua, va, (T)pa.y, ax, ay);
         }
     }
-    ax = group_sum<SWEEP_LANES>(ax);
-    ay = group_sum<SWEEP_LANES>(ay);
-    drho = group_sum<SWEEP_LANES>(drho);
-    num = group_sum<SWEEP_LANES>(num);
-    den = group_sum<SWEEP_LANES>(den);
-    vmax = group_max<SWEEP_LANES>(vmax);
+    ax = group_sum<G>(ax);
+    ay = group_sum<G>(ay);
+    drho = group_sum<G>(drho);
+    num = group_sum<G>(num);
+    den = group_sum<G>(den);
+    vmax = group_max<G>(vmax);
     T dtc = T(3.0e38);   // per-particle time-step candidate (fluid only)
     if (fluid) {
         if (Na) {                                              // Eq. 24
@@ -379,6 +432,7 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
                 raw.mass[i] = srt.mass[i];
                 raw.type[i] = srt.type[i];
                 raw.id[i] = srt.id[i];
+                raw.disp[i] = srt.disp[i];
             }
         }
         if (MODE == 1) {
@@ -395,10 +449,11 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
                 T m = wmin[0];
                 for (int k = 1; k < SWEEP_BLOCK / 32; ++k) m = wmin[k] < m ? wmin[k] : m;
                 if (m < T(3.0e38)) {
+                    int slot = blockIdx.x & (RED_SLOTS - 1);
                     if (sizeof(T) == 4)
-                        atomicMin(&sc->dtmin_f, __float_as_uint((float)m));
+                        atomicMin(&sc->dtmin_f[slot], __float_as_uint((float)m));
                     else
-                        atomicMin(&sc->dtmin_d,
+                        atomicMin(&sc->dtmin_d[slot],
                                   (unsigned long long)__double_as_longlong((double)m));
                 }
             }
@@ -413,10 +468,13 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
     double2 p0 = srt.pos[i];
     V2<T> v0 = srt.vel[i];
     T d0 = srt.drho[i], c0 = srt.drc[i];
-    double2 p1;
-    V2<T> v1;
+    double2 p1 = p0;
+    V2<T> v1 = v0;
     T d1 = d0, c1 = c0;
-    if (typ == T_FLUID) {
+    V2<T> ds = srt.disp[i];
+    if (typ == T_DEAD) {
+        // deleted since the last cell build: kept as is until it is dropped
+    } else if (typ == T_FLUID) {
         T th = (T)half, tdt = (T)dt;
         T usx = v0.x + th * ax, usy = v0.y + th * ay;
         p1 = make_double2(p0.x + dt * (P.ufx_d + (double)usx), p0.y + dt * (P.ufy_d + (double)usy));
@@ -425,11 +483,13 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
         T s = d0 + y;
         c1 = (s - d0) - y;
         d1 = s;
+        ds = mk2(ds.x + tdt * (P.ufx + usx), ds.y + tdt * (P.ufy + usy));
     } else {
         double uh = inf.on ? inflow_u(inf, t + half) : P.ufx_d + (double)v0.x;
         p1 = make_double2(p0.x + dt * uh, p0.y);
         v1 = inf.on ? mk2((T)(inflow_u(inf, t + dt) - P.ufx_d), (T)(-P.ufy_d)) : v0;
         if (inf.on && p1.x >= inf.x_exit) typ = T_FLUID;
+        ds = mk2(ds.x + (T)(dt * uh), ds.y);
     }
     if (typ == T_FLUID &&
         !(p1.x >= g.xmin && p1.x < g.xmax && p1.y >= g.ymin && p1.y < g.ymax)) {
@@ -443,6 +503,21 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
     raw.mass[i] = srt.mass[i];
     raw.type[i] = typ;
     raw.id[i] = srt.id[i];
+    raw.disp[i] = ds;
+    // largest displacements (squared, as float bits: monotone for >= 0)
+    if (typ != T_DEAD) {
+        float d2 = (float)(ds.x * ds.x + ds.y * ds.y);
+        float sx = (float)(p1.x - p0.x), sy = (float)(p1.y - p0.y);
+        float s2 = sx * sx + sy * sy;
+        unsigned m = __activemask();
+        unsigned a = __reduce_max_sync(m, __float_as_uint(d2));
+        unsigned b2 = __reduce_max_sync(m, __float_as_uint(s2));
+        if ((threadIdx.x & 31u) == (unsigned)(__ffs(m) - 1)) {
+            int slot = (blockIdx.x * (SWEEP_BLOCK / 32) + (threadIdx.x >> 5)) & (RED_SLOTS - 1);
+            atomicMax(&sc->max_disp2[slot], a);
+            atomicMax(&sc->max_step2[slot], b2);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -457,8 +532,19 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
     if (P.dt_fixed > 0.0) {
         dt = P.dt_fixed;
     } else {
-        double m = sizeof(T) == 4 ? (double)__uint_as_float(sc->dtmin_f)
-                                  : __longlong_as_double((long long)sc->dtmin_d);
+        // fold the minimum slots (one warp), share through shared memory
+        __shared__ double m_s;
+        if (threadIdx.x < 32) {
+            double m = sizeof(T) == 4 ? (double)__uint_as_float(sc->dtmin_f[threadIdx.x])
+                                      : __longlong_as_double((long long)sc->dtmin_d[threadIdx.x]);
+            for (int o = 16; o > 0; o >>= 1) {
+                double w = __shfl_xor_sync(0xffffffffu, m, o);
+                m = w < m ? w : m;
+            }
+            if (threadIdx.x == 0) m_s = m;
+        }
+        __syncthreads();
+        double m = m_s;
         if (!(m < 1.0e37)) {
             if (i == 0) atomicOr(&sc->err, ERR_NODT);
             m = 0.0;
@@ -483,27 +569,35 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
         V2<T> a = acc[i];
         vh = mk2(v.x + th * a.x, v.y + th * a.y);
         dh = d + th * dr[i];
-    } else if (inf.on) {
+    } else if (typ == T_BUFFER && inf.on) {
         vh = mk2((T)(inflow_u(inf, sc->t + hdt) - P.ufx_d), (T)(-P.ufy_d));
     }
     T xo = h0.x + ddx, yo = h0.y + ddy;
-    // the cell walks stay exact while every particle is within skin/2 of its
-    // cell, and the neighbour list while no particle has moved more than skin/2
-    T lo = -P.half_skin, hi = P.sc + P.half_skin;
-    if (!(xo >= lo && xo < hi && yo >= lo && yo < hi) ||
-        !(ddx * ddx + ddy * ddy <= P.half_skin * P.half_skin))
-        atomicOr(&sc->err, ERR_SKIN);
     half.pos[i] = ph;
     half.H0[i] = mk4<T>(xo, yo, vh.x, vh.y);
+    if (typ == T_DEAD) {
+        half.H1[i] = mk4<T>(T(0), P.rho0, T(0), P.c0);
+        return;
+    }
     half.H1[i] = hot1<T>(P, dh, srt.mass[i]);
+    // the cell walks stay exact while every particle is within skin/2 of its
+    // cell, and the neighbour list while no particle has moved more than
+    // skin/2 since the list was built
+    V2<T> ds = srt.disp[i];
+    T tx = ds.x + ddx, ty = ds.y + ddy;
+    T lo = -P.half_skin, hi = P.sc + P.half_skin;
+    if (!(xo >= lo && xo < hi && yo >= lo && yo < hi) ||
+        !(tx * tx + ty * ty <= P.half_skin * P.half_skin))
+        atomicOr(&sc->err, ERR_SKIN);
 }
 
 // ---------------------------------------------------------------------------
 // inflow layers + time advance (one block)
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_spawn(Inflow inf, double ufx, double ufy, Scalars *__restrict__ sc,
-                        State<T> raw, const double *__restrict__ layer_y, int cap) {
+__global__ void k_spawn(Inflow inf, double ufx, double ufy, float half_skin,
+                        Scalars *__restrict__ sc, State<T> raw,
+                        const double *__restrict__ layer_y, int cap, int cadence) {
     __shared__ int do_spawn, base;
     __shared__ unsigned idbase;
     __shared__ double xnew, unew;
@@ -534,8 +628,25 @@ __global__ void k_spawn(Inflow inf, double ufx, double ufy, Scalars *__restrict_
         sc->n = n;
         sc->t = __dadd_rn(t, dt);
         sc->step += 1;
-        sc->dtmin_f = 0x7f7f7f7fu;
-        sc->dtmin_d = 0x7f7f7f7f7f7f7f7full;
+        // rebuild next step if particles were appended, the cadence is
+        // reached, or one more step (twice this one's largest move) could
+        // carry a particle past skin/2 from where the lists were built
+        unsigned d2 = 0u, s2 = 0u;
+        for (int k = 0; k < RED_SLOTS; ++k) {
+            d2 = max(d2, sc->max_disp2[k]);
+            s2 = max(s2, sc->max_step2[k]);
+        }
+        float dmax = sqrtf(__uint_as_float(d2));
+        float smax = sqrtf(__uint_as_float(s2));
+        int need = do_spawn || sc->since_full + 1 >= cadence || dmax + 2.0f * smax > half_skin;
+        sc->need_full = need;
+        sc->since_full = need ? 0 : sc->since_full + 1;
+        for (int k = 0; k < RED_SLOTS; ++k) {
+            sc->max_disp2[k] = 0u;
+            sc->max_step2[k] = 0u;
+            sc->dtmin_f[k] = 0x7f7f7f7fu;
+            sc->dtmin_d[k] = 0x7f7f7f7f7f7f7f7full;
+        }
     }
     __syncthreads();
     if (!do_spawn) return;
@@ -548,67 +659,90 @@ __global__ void k_spawn(Inflow inf, double ufx, double ufy, Scalars *__restrict_
         raw.mass[k] = (T)inf.m_layer;
         raw.type[k] = T_BUFFER;
         raw.id[k] = idbase + (unsigned)j;
+        raw.disp[k] = mk2(T(0), T(0));
     }
 }
 
 // ---------------------------------------------------------------------------
-static int sweep_blocks(int cap) {
-    return (int)(((long long)cap * SWEEP_LANES + SWEEP_BLOCK - 1) / SWEEP_BLOCK);
+static int sweep_blocks(int cap, int lanes) {
+    return (int)(((long long)cap * lanes + SWEEP_BLOCK - 1) / SWEEP_BLOCK);
 }
 
-template <class T>
-void launch_build(bool with_colour, const PhysT<T> &P, const Grid &g, Scalars *sc,
-                  const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot, const NList &nl,
-                  const Csf<T> &csf, int cap, cudaStream_t s) {
-    int b = sweep_blocks(cap);
-    if (P.kernel == 1) {
-        if (with_colour) launch_k(k_build<T, 1, true>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
-        else launch_k(k_build<T, 1, false>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
-    } else {
-        if (with_colour) launch_k(k_build<T, 0, true>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
-        else launch_k(k_build<T, 0, false>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
+// Calls f.template operator()<G>() for the run-time lane count.
+template <class F> static void with_lanes(int lanes, F &&f) {
+    switch (lanes) {
+        case 1: f(std::integral_constant<int, 1>()); break;
+        case 2: f(std::integral_constant<int, 2>()); break;
+        case 8: f(std::integral_constant<int, 8>()); break;
+        default: f(std::integral_constant<int, 4>()); break;
     }
 }
 
 template <class T>
-void launch_colour(const PhysT<T> &P, const Scalars *sc, const NList &nl, const Hot<T> &hot,
-                   const Csf<T> &csf, int cap, cudaStream_t s) {
-    int b = sweep_blocks(cap);
-    if (P.kernel == 1) launch_k(k_colour<T, 1>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
-    else launch_k(k_colour<T, 0>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+void launch_build(int lanes, bool with_colour, const PhysT<T> &P, const Grid &g, Scalars *sc,
+                  const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot, const NList &nl,
+                  const Csf<T> &csf, int cap, cudaStream_t s) {
+    with_lanes(lanes, [&](auto Gc) {
+        constexpr int G = decltype(Gc)::value;
+        int b = sweep_blocks(cap, G);
+        if (P.kernel == 1) {
+            if (with_colour) launch_k(k_build<T, 1, true, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
+            else launch_k(k_build<T, 1, false, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
+        } else {
+            if (with_colour) launch_k(k_build<T, 0, true, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
+            else launch_k(k_build<T, 0, false, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
+        }
+    });
 }
 
 template <class T>
-void launch_normal(const PhysT<T> &P, const Scalars *sc, const NList &nl, const Hot<T> &hot,
-                   const Csf<T> &csf, int cap, cudaStream_t s) {
-    int b = sweep_blocks(cap);
-    if (P.kernel == 1) launch_k(k_normal<T, 1>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
-    else launch_k(k_normal<T, 0>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+void launch_colour(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
+                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s) {
+    with_lanes(lanes, [&](auto Gc) {
+        constexpr int G = decltype(Gc)::value;
+        int b = sweep_blocks(cap, G);
+        if (P.kernel == 1) launch_k(k_colour<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+        else launch_k(k_colour<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+    });
 }
 
-template <class T, int K>
+template <class T>
+void launch_normal(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
+                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s) {
+    with_lanes(lanes, [&](auto Gc) {
+        constexpr int G = decltype(Gc)::value;
+        int b = sweep_blocks(cap, G);
+        if (P.kernel == 1) launch_k(k_normal<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+        else launch_k(k_normal<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+    });
+}
+
+template <class T, int K, int G>
 static void launch_forces_k(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
                             Scalars *sc, const NList &nl, const uint32_t *key, const Hot<T> &hot,
                             const Csf<T> &csf, const Boundary &bd, const State<T> &srt,
                             const State<T> &raw, V2<T> *acc, T *dr, int cap, cudaStream_t s) {
-    int b = sweep_blocks(cap);
+    int b = sweep_blocks(cap, G);
     if (mode == 0)
-        launch_k(k_forces<T, K, 0>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
+        launch_k(k_forces<T, K, 0, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
     else if (mode == 1)
-        launch_k(k_forces<T, K, 1>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
+        launch_k(k_forces<T, K, 1, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
     else
-        launch_k(k_forces<T, K, 2>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
+        launch_k(k_forces<T, K, 2, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
 }
 
 template <class T>
-void launch_forces(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf, Scalars *sc,
-                   const NList &nl, const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf,
-                   const Boundary &bd, const State<T> &srt, const State<T> &raw, V2<T> *acc,
-                   T *dr, int cap, cudaStream_t s) {
-    if (P.kernel == 1)
-        launch_forces_k<T, 1>(mode, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, cap, s);
-    else
-        launch_forces_k<T, 0>(mode, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, cap, s);
+void launch_forces(int lanes, int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
+                   Scalars *sc, const NList &nl, const uint32_t *key, const Hot<T> &hot,
+                   const Csf<T> &csf, const Boundary &bd, const State<T> &srt,
+                   const State<T> &raw, V2<T> *acc, T *dr, int cap, cudaStream_t s) {
+    with_lanes(lanes, [&](auto Gc) {
+        constexpr int G = decltype(Gc)::value;
+        if (P.kernel == 1)
+            launch_forces_k<T, 1, G>(mode, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, cap, s);
+        else
+            launch_forces_k<T, 0, G>(mode, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, cap, s);
+    });
 }
 
 template <class T>
@@ -620,22 +754,34 @@ void launch_predict(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const Sta
 
 template <class T>
 void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &raw,
-                  const double *layer_y, int cap, cudaStream_t s) {
-    launch_k(k_spawn<T>, 1, 256, s, inf, P.ufx_d, P.ufy_d, sc, raw, layer_y, cap);
+                  const double *layer_y, int cap, int cadence, cudaStream_t s) {
+    launch_k(k_spawn<T>, 1, 256, s, inf, P.ufx_d, P.ufy_d, (float)P.half_skin, sc, raw,
+             layer_y, cap, cadence);
+}
+
+__global__ void k_decide(cudaGraphConditionalHandle h, const Scalars *__restrict__ sc) {
+    cudaGraphSetConditional(h, sc->need_full ? 1u : 0u);
+}
+
+void launch_decide(cudaGraphConditionalHandle h, const Scalars *sc, cudaStream_t s) {
+    launch_k(k_decide, 1, 1, s, h, sc);
 }
 
 #define SPH_INST(T)                                                                              \
     template void launch_reorder<T>(const PhysT<T> &, const Grid &, Scalars *, const CellSort &,  \
                                     const State<T> &, const State<T> &, const Hot<T> &, int,      \
                                     cudaStream_t);                                                \
-    template void launch_build<T>(bool, const PhysT<T> &, const Grid &, Scalars *, const uint2 *, \
-                                  const uint32_t *, const Hot<T> &, const NList &,                \
-                                  const Csf<T> &, int, cudaStream_t);                             \
-    template void launch_colour<T>(const PhysT<T> &, const Scalars *, const NList &,              \
+    template void launch_refresh<T>(const PhysT<T> &, const Grid &, Scalars *, const uint32_t *,  \
+                                    const State<T> &, const State<T> &, const Hot<T> &, int,      \
+                                    cudaStream_t);                                                \
+    template void launch_build<T>(int, bool, const PhysT<T> &, const Grid &, Scalars *,          \
+                                  const uint2 *, const uint32_t *, const Hot<T> &,                \
+                                  const NList &, const Csf<T> &, int, cudaStream_t);              \
+    template void launch_colour<T>(int, const PhysT<T> &, const Scalars *, const NList &,         \
                                    const Hot<T> &, const Csf<T> &, int, cudaStream_t);            \
-    template void launch_normal<T>(const PhysT<T> &, const Scalars *, const NList &,              \
+    template void launch_normal<T>(int, const PhysT<T> &, const Scalars *, const NList &,         \
                                    const Hot<T> &, const Csf<T> &, int, cudaStream_t);            \
-    template void launch_forces<T>(int, const PhysT<T> &, const Grid &, const Inflow &,          \
+    template void launch_forces<T>(int, int, const PhysT<T> &, const Grid &, const Inflow &,     \
                                    Scalars *, const NList &, const uint32_t *, const Hot<T> &,    \
                                    const Csf<T> &, const Boundary &, const State<T> &,            \
                                    const State<T> &, V2<T> *, T *, int, cudaStream_t);            \
@@ -643,7 +789,7 @@ void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State
                                     const State<T> &, const V4<T> *, const V2<T> *, const T *,    \
                                     const Hot<T> &, int, cudaStream_t);                           \
     template void launch_spawn<T>(const PhysT<T> &, const Inflow &, Scalars *, const State<T> &, \
-                                  const double *, int, cudaStream_t);
+                                  const double *, int, int, cudaStream_t);
 
 SPH_INST(float)
 SPH_INST(double)

@@ -113,7 +113,8 @@ def test_jet_c3_full_size_evaluation(sph, orc):
         assert ea < tol and ed < tol
 
 
-def test_breakup_length_five_seed_mean(sph, orc):
+@pytest.mark.parametrize("lanes,cadence", [(4, 1), (4, 4)])
+def test_breakup_length_five_seed_mean(sph, orc, lanes, cadence):
     # Gravity along the jet (Fr = 1, as for the paper's jets falling from a
     # tank) makes the planar jet break within the run.  L is sampled at fixed
     # simulated times (the adaptive step shrinks after breakup, so step
@@ -135,14 +136,16 @@ def test_breakup_length_five_seed_mean(sph, orc):
     Lg, Lo = [], []
     for seed in range(5):
         case = wl.jet(seed=seed, Re=100, We=5, dx=1.0 / 10, length=12.0, amp=0.05, Fr=1.0)
+        case["params"]["skin_over_h"] = 0.3
         g = sph.Simulation(case)
+        g.set_tuning(lanes, cadence)
         Lg.append(samples(g, lambda: g.time()["t"]))
         g.close()
         o = oracle_sim(orc, case)
         Lo.append(samples(o, lambda: o.t))
     mg, mo = float(np.mean(Lg)), float(np.mean(Lo))
-    report(case="breakup_5seeds", gpu=Lg, oracle=Lo, gpu_mean=mg, oracle_mean=mo,
-           rel=abs(mg - mo) / mo)
+    report(case="breakup_5seeds", lanes=lanes, cadence=cadence, gpu=Lg, oracle=Lo,
+           gpu_mean=mg, oracle_mean=mo, rel=abs(mg - mo) / mo)
     assert abs(mg - mo) <= 0.02 * mo
 
 

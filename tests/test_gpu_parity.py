@@ -263,3 +263,85 @@ def test_outflow_deletes_and_inflow_feeds(sph, orc):
     assert tg["deleted"] == osim.deleted > 0
     g = sim.state()
     assert np.array_equal(g["id"], osim.st["id"].astype(np.uint32))
+
+
+# ---------------------------------------------------------------------------
+# tuning: lanes per particle, cell-build cadence, autotuner
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("lanes", [1, 2, 8])
+def test_lanes_give_the_same_evaluation(sph, orc, lanes):
+    st = wl.jittered_patch(seed=13, nx=60, ny=40, dx=0.02, vel=0.3, drho=0.01)
+    p = wl.test_params(dx=0.02, sigma=2.0, alpha=0.3, g=9.81, box=(-0.5, -0.5, 2.0, 1.5))
+    sim = sph.Simulation(_case_from_state(p, st))
+    sim.set_tuning(lanes, 1)
+    sim.evaluate()
+    g = sim.state()
+    d = orc.derive(p)
+    ev = orc.evaluate(d, st, None)
+    keep = ~ambiguous_mask(orc, d, st, ev)
+    assert rel_l2_vec(g["ax"][keep], g["ay"][keep], ev["ax"][keep], ev["ay"][keep]) < 1e-5
+    assert rel_l2(g["drho"], ev["drho"]) < 1e-5
+
+
+@pytest.mark.parametrize("cadence,lanes", [(2, 4), (4, 2), (8, 8)])
+def test_cadence_keeps_dam_break_trajectory(sph, orc, cadence, lanes):
+    # the cells and lists of a build are reused for `cadence` steps; the
+    # neighbour sets stay exact, so the trajectory still matches the oracle
+    case = wl.dam_break(seed=2, dx=0.02, prec="fp64")
+    case["params"]["skin_over_h"] = 0.1 * cadence   # room for `cadence` steps of motion
+    sim = sph.Simulation(case)
+    sim.set_tuning(lanes, cadence)
+    osim = oracle_sim(orc, case)
+    sim.run(120)
+    osim.run(120)
+    _compare_states(sim.state(), osim.st, "fp64", 0, 0, 0)
+
+
+def test_cadence_with_outflow_patch(sph, orc):
+    # particles leaving the box between builds drop out of every sum at once
+    st = wl.jittered_patch(seed=21, nx=40, ny=30, dx=0.02, vel=0.05, drho=0.002,
+                           x0=0.0, y0=0.0)
+    st["u"] = st["u"] + 2.0
+    p = wl.test_params(dx=0.02, alpha=0.2, dt_fixed=5e-4, box=(-0.1, -0.1, 0.83, 0.7))
+    p["skin_over_h"] = 0.5
+    case = _case_from_state(p, st)
+    sim = sph.Simulation(case)
+    sim.set_tuning(4, 4)
+    osim = oracle_sim(orc, case)
+    sim.run(60)
+    osim.run(60)
+    assert sim.time()["deleted"] == osim.deleted > 0
+    _compare_states(sim.state(), osim.st, "fp32", 1e-5, 1e-4, 1e-5)
+
+
+def test_autotune_restores_state(sph):
+    case = wl.jet(seed=3, dx=1.0 / 20, length=8.0)
+    sim = sph.Simulation(case)
+    sim.run(5)
+    before = sim.state()
+    t_before = sim.time()
+    lanes, cadence, ms = sim.autotune(trial_steps=8)
+    assert lanes in (1, 2, 4, 8) and cadence in (1, 2, 4, 8) and ms > 0
+    after = sim.state()
+    assert sim.time() == t_before
+    for k in ("x", "y", "u", "v", "rho", "id"):
+        assert np.array_equal(before[k], after[k])
+    assert sim.tuning() == (lanes, cadence)
+    sim.run(10)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_jet_trajectory_with_reused_builds(sph, orc, prec):
+    # inflow, outflow and spawning with the rebuild decided on the device:
+    # layers are laid on the same steps as in the oracle, so the particle
+    # sets and trajectories still match
+    case = wl.jet(seed=4, dx=1.0 / 20, length=6.0, prec=prec, Re=200, We=20)
+    case["params"]["dt_fixed"] = 1e-3
+    case["params"]["skin_over_h"] = 0.3
+    sim = sph.Simulation(case)
+    sim.set_tuning(4, 8)
+    osim = oracle_sim(orc, case)
+    sim.run(150)
+    osim.run(150)
+    assert sim.time()["deleted"] == osim.deleted
+    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4)

@@ -77,7 +77,7 @@ BYTES_PER_PARTICLE = {"cell_sort": 16 + 1 + 4 + 4 + 4 + 4 + 4, "reorder": 2 * 41
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="jet_c2", choices=["jet_c2", "jet_c3", "dam_c1"])
@@ -174,6 +174,13 @@ class ClockSampler:
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the first reading takes a moment: start timing only once it is in
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
@@ -244,7 +251,7 @@ def main():
     else:
         lanes, cadence = (int(v) for v in args.tune.split(","))
         binding.sph_set_tuning(ctx, lanes, cadence)
-    per_step, per_breakup = binding.sph_kernel_counts(ctx)
+    per_full, per_reuse, per_breakup = binding.sph_kernel_counts(ctx)
     has_inflow = case.get("inflow") is not None
 
     # interacting pairs of the initial state (for the algorithmic FLOP count)
@@ -287,11 +294,15 @@ def main():
 
     K = args.steps
     clocks = ClockSampler(local)
+    builds0 = binding.sph_get_rebuild_stats(ctx)[0]
     t_wall0 = time.perf_counter()
     step_ms, nact, Ls = timed(K, profile=False)
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     nbreak = len(Ls)
+    # cell sorts in the timed region: one per rebuilding step and one per
+    # breakup-length evaluation
+    full_steps = binding.sph_get_rebuild_stats(ctx)[0] - builds0 - nbreak
     from paper_1603_02421_gb300.replicas import reduce_rate
     value, total_s, units = reduce_rate(step_ms.sum() / 1e3, float(nact.sum()), dist, dev)
     if dist is not None:
@@ -346,7 +357,7 @@ def main():
                "sample": "FP64 CPU oracle (single thread), %d steps of the upstream %d "
                          "particles of the same workload, %.1f s" % (nsteps, n, el)}
 
-    launches = K * per_step + nbreak * per_breakup
+    launches = full_steps * per_full + (K - full_steps) * per_reuse + nbreak * per_breakup
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -357,7 +368,8 @@ def main():
                        "particles_mean": n_mean, "parallelism": "replicas (one jet per GPU)",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "tuning": {"lanes": lanes, "cadence": cadence, "skin_over_h": args.skin,
-                                  "chosen_by": "autotuner" if args.tune == "auto" else "flag"},
+                                  "chosen_by": "autotuner" if args.tune == "auto" else "flag",
+                                  "rebuild_fraction": full_steps / K},
                        "breakup_every": BREAKUP_EVERY if has_inflow else None,
                        "pairs_per_particle": pairs_per_particle,
                        "wall_s": wall},

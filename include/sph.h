@@ -221,9 +221,22 @@ sph_status sph_get_tuning(sph_ctx *ctx, int *lanes, int *cadence);
 sph_status sph_autotune(sph_ctx *ctx, int trial_steps, int *lanes, int *cadence,
                         double *ms_per_step);
 
-/* Number of device kernels (memsets excluded) one step and one breakup-length
- * evaluation launch at the current settings.  Either pointer may be NULL. */
-sph_status sph_kernel_counts(sph_ctx *ctx, int *per_step, int *per_breakup);
+/* Cell builds so far (cell sorts run by steps and by the calls that sort:
+ * evaluate, pairs, breakup length), and the rebuild decision taken at the end
+ * of the last step: the largest displacement of a particle since the last
+ * build and the largest move in that step (both in length units, FP32).
+ * Any pointer may be NULL. */
+sph_status sph_get_rebuild_stats(sph_ctx *ctx, long long *builds, double *disp_max,
+                                 double *step_max);
+
+/* Number of device kernels (memsets excluded) launched at the current
+ * settings by a step that rebuilds the cells and lists, by a step that reuses
+ * the last build (equal to the first at cadence 1, where every step
+ * rebuilds), and by one breakup-length evaluation.  At cadence > 1 each step
+ * also runs the one-thread kernel that decides the next step's kind, which
+ * both step counts include.  Any pointer may be NULL. */
+sph_status sph_kernel_counts(sph_ctx *ctx, int *per_full_step, int *per_reused_step,
+                             int *per_breakup);
 
 /* Neighbour pairs without any device allocation.  The paper has no
  * counterpart: this is a service for callers that cannot call cudaMalloc --

@@ -77,8 +77,9 @@ _SIGS = {
     "sph_get_csf": ([_CTX, ctypes.c_longlong, _LL, _U32, _D, _D, _D], ctypes.c_int),
     "sph_get_pairs": ([_CTX, ctypes.c_longlong, _U32, _U32, _LL], ctypes.c_int),
     "sph_get_time": ([_CTX, _D, _LL, _LL, _LL], ctypes.c_int),
-    "sph_kernel_counts": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
-                          ctypes.c_int),
+    "sph_kernel_counts": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "sph_get_rebuild_stats": ([_CTX, _LL, _D, _D], ctypes.c_int),
     "sph_run_async": ([_CTX, ctypes.c_longlong], ctypes.c_int),
     "sph_set_tuning": ([_CTX, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sph_get_tuning": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -258,9 +259,20 @@ def sph_get_time(ctx):
 
 
 def sph_kernel_counts(ctx):
-    a, b = ctypes.c_int(), ctypes.c_int()
-    _check(ctx, lib().sph_kernel_counts(ctx, ctypes.byref(a), ctypes.byref(b)))
-    return a.value, b.value
+    """(kernels of a rebuilding step, of a step reusing the build, of a
+    breakup-length evaluation)."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().sph_kernel_counts(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def sph_get_rebuild_stats(ctx):
+    """(cell builds so far, largest displacement since the build, largest move
+    of the last step) as seen by the last step's rebuild decision."""
+    b, d, m = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().sph_get_rebuild_stats(ctx, ctypes.byref(b), ctypes.byref(d),
+                                            ctypes.byref(m)))
+    return b.value, d.value, m.value
 
 
 def sph_set_tuning(ctx, lanes, cadence):
@@ -395,6 +407,9 @@ class Simulation:
 
     def autotune(self, trial_steps=20):
         return sph_autotune(self.ctx, trial_steps)
+
+    def rebuild_stats(self):
+        return sph_get_rebuild_stats(self.ctx)
 
     def kernels_per_step(self):
         return sph_kernel_counts(self.ctx)[0]

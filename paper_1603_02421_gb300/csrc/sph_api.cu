@@ -1195,7 +1195,9 @@ sph_status sph_set_tuning(sph_ctx *c, int lanes, int cadence) {
     if (!(lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8))
         return fail(c, SPH_ERR_ARG, "lanes must be 1, 2, 4 or 8");
     if (cadence < 1 || cadence > 64) return fail(c, SPH_ERR_ARG, "cadence must lie in [1, 64]");
-    if (lanes != c->lanes) c->graph_dirty = true;
+    // both are captured into the step graphs (launch shapes; the cadence
+    // is an argument of the rebuild decision)
+    if (lanes != c->lanes || cadence != c->cadence) c->graph_dirty = true;
     c->lanes = lanes;
     c->cadence = cadence;
     c->force_full = true;
@@ -1293,16 +1295,31 @@ sph_status sph_autotune(sph_ctx *c, int trial_steps, int *lanes, int *cadence, d
     return SPH_OK;
 }
 
-sph_status sph_kernel_counts(sph_ctx *c, int *per_step, int *per_breakup) {
+sph_status sph_get_rebuild_stats(sph_ctx *c, long long *builds, double *disp_max,
+                                 double *step_max) {
     if (!c) return SPH_ERR_ARG;
-    int build = 5;                         // hash+count, scan (2), scatter, reorder
-    int k = build + 1;                     // + neighbour list (with the colour of step n)
-    // (a step that reuses the last build runs refresh + colour instead: 2 or 1)
-    k += c->prm.sigma > 0 ? 3 : 0;         // normal (2x) + colour of the half step
-    k += 3;                                // forces (2x) + predict
-    k += 1;                                // spawn / time advance
-    if (per_step) *per_step = k;
-    if (per_breakup) *per_breakup = build + 4;   // + union-find init, link, compress, reach
+    sph_status s = pull_scalars(c);
+    if (s) return s;
+    if (builds) *builds = c->hsc->builds;
+    if (disp_max) *disp_max = c->hsc->last_dmax;
+    if (step_max) *step_max = c->hsc->last_smax;
+    return SPH_OK;
+}
+
+sph_status sph_kernel_counts(sph_ctx *c, int *per_full_step, int *per_reused_step,
+                             int *per_breakup) {
+    if (!c) return SPH_ERR_ARG;
+    bool csf = c->prm.sigma > 0;
+    int sort = 5;                          // hash+count, scan (2), scatter, reorder
+    int full = sort + 1;                   // + neighbour list (with the colour of step n)
+    int reuse = 1 + (csf ? 1 : 0);         // refresh + colour of step n
+    int rest = (csf ? 3 : 0)               // normal (2x) + colour of the half step
+               + 3                         // forces (2x) + predict
+               + 1;                        // spawn / time advance
+    int decide = c->cadence > 1 ? 1 : 0;   // device-side choice of the next step's kind
+    if (per_full_step) *per_full_step = full + rest + decide;
+    if (per_reused_step) *per_reused_step = (c->cadence > 1 ? reuse : full) + rest + decide;
+    if (per_breakup) *per_breakup = sort + 4;    // + union-find init, link, compress, reach
     return SPH_OK;
 }
 

@@ -80,10 +80,11 @@ struct Scalars {
     int nsrt;                     // particles in the current cell order
     unsigned next_id;
     unsigned err;                 // ErrBits, sticky
-    unsigned pad0;
-    unsigned pad1;
+    float last_dmax;              // rebuild decision of the last step: largest
+    float last_smax;              //   displacement since the build, largest move
     double dt, t, x_up;
     long long step, deleted;
+    long long builds;             // cell sorts run (steps and other calls)
     unsigned long long xmax_key;  // breakup: ordered bits of max x of the jet
     unsigned detached;            // breakup: particles outside the jet
     unsigned pair_count;

@@ -111,6 +111,7 @@ k_scan_add(uint2 *__restrict__ cellSE, const uint32_t *__restrict__ bsum, unsign
             uint32_t t = 0;
             for (int k = 0; k < SCAN_THREADS / 32; ++k) t += red[k];
             sc->nsrt = (int)t;
+            sc->builds += 1;
         }
     }
     uint32_t off = off_s;

@@ -638,6 +638,8 @@ __global__ void k_spawn(Inflow inf, double ufx, double ufy, float half_skin,
         }
         float dmax = sqrtf(__uint_as_float(d2));
         float smax = sqrtf(__uint_as_float(s2));
+        sc->last_dmax = dmax;
+        sc->last_smax = smax;
         int need = do_spawn || sc->since_full + 1 >= cadence || dmax + 2.0f * smax > half_skin;
         sc->need_full = need;
         sc->since_full = need ? 0 : sc->since_full + 1;

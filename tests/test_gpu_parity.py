@@ -341,7 +341,35 @@ def test_jet_trajectory_with_reused_builds(sph, orc, prec):
     sim = sph.Simulation(case)
     sim.set_tuning(4, 8)
     osim = oracle_sim(orc, case)
+    b0 = sim.rebuild_stats()[0]
     sim.run(150)
     osim.run(150)
+    builds = sim.rebuild_stats()[0] - b0
+    assert 150 // 8 <= builds < 75          # most steps reused a build
     assert sim.time()["deleted"] == osim.deleted
     _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4)
+
+
+def test_cadence_change_takes_effect(sph):
+    # a cadence set after steps were run (the step graphs already exist)
+    # governs the following steps; the rebuild decision keeps every
+    # displacement since a build below skin/2
+    case = wl.jet(seed=5, dx=1.0 / 20, length=6.0, Re=200, We=20)
+    case["params"]["skin_over_h"] = 0.3
+    h = case["params"]["dx"] * case["params"]["h_over_dx"]
+    sim = sph.Simulation(case)
+    sim.set_tuning(4, 1)
+    sim.run(3)
+    b0 = sim.rebuild_stats()[0]
+    sim.run(12)
+    b1 = sim.rebuild_stats()[0]
+    assert b1 - b0 == 12
+    sim.set_tuning(4, 8)
+    worst = 0.0
+    for _ in range(24):
+        sim.step()
+        _, dmax, smax = sim.rebuild_stats()
+        worst = max(worst, dmax)
+    b2 = sim.rebuild_stats()[0]
+    assert 3 <= b2 - b1 <= 12
+    assert worst <= 0.15 * h * (1 + 1e-5)

@@ -457,7 +457,7 @@ static sph_status upload_boundary(sph_ctx *c) {
     for (size_t k = 0; k < nb; ++k) {
         int cx, cy;
         cell_of(c->grid, c->bx[k], c->by[k], cx, cy);
-        key[k] = (uint32_t)cy * (uint32_t)c->grid.ncx + (uint32_t)cx;
+        key[k] = grid_key(c->grid, cx, cy);
     }
     std::vector<size_t> ord(nb);
     std::iota(ord.begin(), ord.end(), 0);
@@ -470,7 +470,8 @@ static sph_status upload_boundary(sph_ctx *c) {
         uint32_t kk = key[k];
         if (r == 0 || key[ord[r - 1]] != kk) se[kk].x = (unsigned)r;
         if (r + 1 == nb || key[ord[r + 1]] != kk) se[kk].y = (unsigned)(r + 1);
-        int cy = (int)(kk / (uint32_t)c->grid.ncx), cx = (int)kk - cy * c->grid.ncx;
+        int cx, cy;
+        grid_cell(c->grid, kk, cx, cy);
         double xo = c->bx[k] - (c->grid.xmin + (double)(cx - 1) * c->grid.sc);
         double yo = c->by[k] - (c->grid.ymin + (double)(cy - 1) * c->grid.sc);
         hd[4 * r + 0] = xo;
@@ -603,11 +604,7 @@ sph_status sph_init(const sph_params *p, sph_ctx **out) {
     g.xmin = q.xmin; g.ymin = q.ymin; g.xmax = q.xmax; g.ymax = q.ymax;
     g.sc = sc; g.inv_sc = 1.0 / sc;
     g.ncx = (int)ncx; g.ncy = (int)ncy;
-    g.ncells = (unsigned)(g.ncx * g.ncy);
-    int bits = 1;
-    while (((1ull << bits) - 1ull) < (unsigned long long)g.ncells) ++bits;
-    g.keybits = bits;
-    g.sentinel = (uint32_t)((1ull << bits) - 1ull);
+    grid_finish(g);
 
     auto bail = [&](sph_status s) { sph_destroy(c); return s; };
     cudaError_t e = cudaSetDevice(q.device);

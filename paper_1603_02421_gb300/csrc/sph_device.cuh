@@ -79,8 +79,7 @@ __device__ __forceinline__ bool exact_within(double2 pa, double2 pb, double r2ma
 
 // Cell coordinates from a key.
 __device__ __forceinline__ void key_cell(const Grid &g, uint32_t key, int &cx, int &cy) {
-    cy = (int)(key / (uint32_t)g.ncx);
-    cx = (int)key - cy * g.ncx;
+    grid_cell(g, key, cx, cy);
 }
 
 // Cell-relative offsets x - X(cx), y - Y(cy) of the particle's own cell.
@@ -95,9 +94,10 @@ __device__ __forceinline__ void cell_offsets(const Grid &g, uint32_t key, double
     yoff = (T)yo;
 }
 
-// Particle range of the three cells (cx-1, cx, cx+1) of one row.  Cells of a
-// row are contiguous in the sorted order, so the range is [lo, hi) with the
-// cell cx-1 part below b1 and the cell cx+1 part from b2 on.
+// Particle range of the three cells (cx-1, cx, cx+1) of one row, centred on
+// cell key c.  Cells of a row are contiguous in the sorted order, so the
+// range is [lo, hi) with the cell cx-1 part below b1 and the cell cx+1 part
+// from b2 on.
 struct RowRange {
     unsigned lo, b1, b2, hi;
 };
@@ -113,6 +113,11 @@ __device__ __forceinline__ RowRange row_range(const uint2 *__restrict__ cellSE, 
     r.b1 = e0 ? s0.y : r.lo;
     r.b2 = e2 ? s2.x : r.hi;
     return r;
+}
+
+// x-cell difference cx_a - cx_b (+1, 0 or -1) of candidate b of a row range.
+__device__ __forceinline__ int row_step(const RowRange &rr, unsigned b) {
+    return b < rr.b1 ? 1 : (b < rr.b2 ? 0 : -1);
 }
 
 // x-shift (cx_a - cx_b) * sc of candidate b of a row range.
@@ -161,13 +166,11 @@ __device__ __forceinline__ void for_neighbours(const PhysT<T> &P, const Grid &g,
                                                const double2 *__restrict__ pos, unsigned i,
                                                unsigned sub, uint32_t key, T xa, T ya, T r2lo,
                                                T r2hi, double r2exact, Body &&body) {
-    int cx, cy;
-    key_cell(g, key, cx, cy);
     double2 pa = make_double2(0.0, 0.0);
     bool have_pa = false;
 #pragma unroll 1
     for (int dy = -1; dy <= 1; ++dy) {
-        RowRange rr = row_range(cellSE, (cy + dy) * g.ncx + cx);
+        RowRange rr = row_range(cellSE, (int)key + dy * g.ncx);
         T yshift = T(dy) * P.sc;
 #pragma unroll 2
         for (unsigned b = rr.lo + sub; b < rr.hi; b += G) {
@@ -192,32 +195,73 @@ template <class T> __device__ __forceinline__ T code_shift(uint32_t code, T sc) 
     return code == 0u ? -sc : (code == 2u ? sc : T(0));
 }
 
-// Walk the G-strided part (lane `sub`) of the neighbour list of particle i:
-// entries whose squared distance in T is below H2lo, or re-tested exactly in
-// FP64 below (2h)^2.  body(b, rx, ry, r2) with (rx, ry) = r_a - r_b.
-template <int G, class T, class Body>
+// Loads CH consecutive list entries with one vector load (the address is a
+// multiple of CH entries from a row start, and rows start 384-byte aligned).
+template <int CH> __device__ __forceinline__ void load_entries(const uint32_t *p, uint32_t *ent) {
+    if constexpr (CH == 4) {
+        uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        ent[0] = v.x; ent[1] = v.y; ent[2] = v.z; ent[3] = v.w;
+    } else if constexpr (CH == 2) {
+        uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+        ent[0] = v.x; ent[1] = v.y;
+    } else {
+        ent[0] = __ldg(p);
+    }
+}
+
+// Walk lane `sub`'s part of the neighbour list of particle i: the G lanes of a
+// particle take chunks of CH consecutive entries in turn (lane sub: entries
+// [c*G*CH + sub*CH, +CH) of round c).  A chunk is read with one vector load,
+// and every gather of the chunk -- gather(b), the sweep's record of b with
+// its cell offsets in .x -- is issued before any of them is used, so a lane
+// keeps CH independent gathers in flight instead of a chain of index ->
+// record loads; the next chunk's entries are loaded while this one is
+// processed.  Entries whose squared distance in T is below H2lo are
+// taken; those below H2hi are re-tested exactly in FP64 below (2h)^2.  Slots
+// past the list end (inside the 96-slot row, so the vector load stays in
+// bounds) are masked and gather particle i's own record instead of an index
+// they do not hold.  body(b, rx, ry, r2, record) with (rx, ry) = r_a - r_b.
+template <int G, int CH, class T, class Gather, class Body>
 __device__ __forceinline__ void for_list(const PhysT<T> &P, const NList &nl,
-                                         const typename Vec<T>::v4 *__restrict__ X,
                                          const double2 *__restrict__ pos, unsigned i,
-                                         unsigned sub, T xa, T ya, Body &&body) {
+                                         unsigned sub, T xa, T ya, Gather &&gather, Body &&body) {
+    static_assert(CH == 1 || CH == 2 || CH == 4, "chunk of 1, 2 or 4 entries");
+    static_assert(LIST_SLOTS % CH == 0, "rows hold whole chunks");
+    using Rec = decltype(gather(0u));
     unsigned cnt = nl.cnt[i];
     const uint32_t *__restrict__ e = nl.e + (size_t)i * LIST_SLOTS;
     double2 pa = make_double2(0.0, 0.0);
     bool have_pa = false;
-#pragma unroll 2
-    for (unsigned k = sub; k < cnt; k += G) {
-        uint32_t ent = __ldg(e + k);
-        unsigned b = ent & 0x0FFFFFFFu;
-        typename Vec<T>::v4 xb = X[b];
-        T rx = (xa - xb.x) + code_shift<T>((ent >> 28) & 3u, P.sc);
-        T ry = (ya - xb.y) + code_shift<T>(ent >> 30, P.sc);
-        T r2 = rx * rx + ry * ry;
-        if (r2 >= P.H2hi) continue;
-        if (r2 >= P.H2lo) {
-            if (!have_pa) { pa = pos[i]; have_pa = true; }
-            if (!exact_within(pa, pos[b], P.H2d)) continue;
+    uint32_t ent[CH], nxt[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) nxt[u] = 0u;
+    if (sub * CH < cnt) load_entries<CH>(e + sub * CH, ent);
+#pragma unroll 1
+    for (unsigned base = sub * CH; base < cnt; base += G * CH) {
+        // the next chunk's entries load while this chunk is processed
+        if (base + G * CH < cnt) load_entries<CH>(e + base + G * CH, nxt);
+        Rec rec[CH];
+        unsigned bb[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            bb[u] = base + u < cnt ? (ent[u] & 0x0FFFFFFFu) : i;
+            rec[u] = gather(bb[u]);
         }
-        body(b, rx, ry, r2, xb);
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            if (base + u >= cnt) continue;
+            T rx = (xa - rec[u].x.x) + code_shift<T>((ent[u] >> 28) & 3u, P.sc);
+            T ry = (ya - rec[u].x.y) + code_shift<T>(ent[u] >> 30, P.sc);
+            T r2 = rx * rx + ry * ry;
+            if (r2 >= P.H2hi) continue;
+            if (r2 >= P.H2lo) {
+                if (!have_pa) { pa = pos[i]; have_pa = true; }
+                if (!exact_within(pa, pos[bb[u]], P.H2d)) continue;
+            }
+            body(bb[u], rx, ry, r2, rec[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) ent[u] = nxt[u];
     }
 }
 

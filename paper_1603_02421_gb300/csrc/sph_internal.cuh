@@ -36,13 +36,32 @@ template <> struct Vec<float> { using v2 = float2; using v4 = f4; };
 template <> struct Vec<double> { using v2 = double2; using v4 = d4; };
 
 // Uniform cell grid: cell size sc = 2h + skin; one empty padding cell on each
-// side so the 3x3 block of any occupied cell stays inside the grid.
+// side so the 3x3 block of any occupied cell stays inside the grid.  Cell keys
+// run along x first: key = cy * ncx + cx.
 struct Grid {
     double xmin, ymin, xmax, ymax, sc, inv_sc;
     int ncx, ncy;
     unsigned ncells, sentinel;   // sentinel key sorts after every cell
     int keybits;
 };
+
+// Completes a grid whose box, cell size and cell counts are set.
+inline void grid_finish(Grid &g) {
+    g.ncells = (unsigned)(g.ncx * g.ncy);
+    int bits = 1;
+    while (((1ull << bits) - 1ull) < (unsigned long long)g.ncells) ++bits;
+    g.keybits = bits;
+    g.sentinel = (uint32_t)((1ull << bits) - 1ull);
+}
+
+__host__ __device__ __forceinline__ uint32_t grid_key(const Grid &g, int cx, int cy) {
+    return (uint32_t)cy * (uint32_t)g.ncx + (uint32_t)cx;
+}
+
+__host__ __device__ __forceinline__ void grid_cell(const Grid &g, uint32_t key, int &cx, int &cy) {
+    cy = (int)(key / (uint32_t)g.ncx);
+    cx = (int)key - cy * g.ncx;
+}
 
 // Physical constants, converted once to the pair-arithmetic type T.
 template <class T> struct PhysT {

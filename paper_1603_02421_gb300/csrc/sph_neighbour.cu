@@ -27,7 +27,7 @@ __global__ void k_hash_count(Grid g, State<T> raw, const Scalars *__restrict__ s
         int cy = (int)floor((p.y - g.ymin) * g.inv_sc) + 1;
         cx = min(max(cx, 1), g.ncx - 2);
         cy = min(max(cy, 1), g.ncy - 2);
-        k = (uint32_t)cy * (uint32_t)g.ncx + (uint32_t)cx;
+        k = grid_key(g, cx, cy);
         atomicAdd(&count[k], 1u);
     }
     knew[i] = k;

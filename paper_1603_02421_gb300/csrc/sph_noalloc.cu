@@ -149,11 +149,7 @@ extern "C" sph_status sph_pairs_noalloc(const double *x, const double *y, long l
     g.xmin = xmin; g.ymin = ymin; g.xmax = xmax; g.ymax = ymax;
     g.sc = sc; g.inv_sc = 1.0 / sc;
     g.ncx = (int)ncx; g.ncy = (int)ncy;
-    g.ncells = (unsigned)(g.ncx * g.ncy);
-    int bits = 1;
-    while (((1ull << bits) - 1ull) < (unsigned long long)g.ncells) ++bits;
-    g.keybits = bits;
-    g.sentinel = (uint32_t)((1ull << bits) - 1ull);
+    grid_finish(g);
 
     PhysT<float> P{};
     double H = 2.0 * h, H2 = H * H, band = 2e-5;

@@ -22,8 +22,34 @@
 
 namespace sph {
 
+// List entries a lane takes per chunk in each pair sweep (1, 2 or 4).
+#ifndef SPH_CH_COLOUR
+#define SPH_CH_COLOUR 4
+#endif
+#ifndef SPH_CH_NORMAL
+#define SPH_CH_NORMAL 4
+#endif
+#ifndef SPH_CH_FORCES
+#define SPH_CH_FORCES 1
+#endif
+
+
 template <class T> using V2 = typename Vec<T>::v2;
 template <class T> using V4 = typename Vec<T>::v4;
+
+// Neighbour records the pair sweeps gather ahead of use.  .x holds the cell
+// offsets (x, y).
+template <class T> struct ColourRec {     // offsets and volume
+    V4<T> x;
+};
+template <class T> struct NormalRec {     // offsets, volume, colour
+    V4<T> x;
+};
+template <class T> struct ForceRec {      // offsets and velocity; volume, density,
+    V4<T> x;                              // pressure term, sound speed; unit normal
+    V4<T> h1;                             // (zero unless particle a has one)
+    V2<T> nb;
+};
 
 __device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
@@ -159,17 +185,14 @@ k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ 
     if (active) {
         ha = H0[i];
         T xa = ha.x, ya = ha.y;
-        int cx, cy;
-        key_cell(g, key[i], cx, cy);
+        const int ka = (int)key[i];
         unsigned cnt = 0;
         uint32_t *__restrict__ e = nl.e + (size_t)i * LIST_SLOTS;
         double2 pa = make_double2(0.0, 0.0);
         bool have_pa = false;
 #pragma unroll 1
         for (int dy = -1; dy <= 1; ++dy) {
-            RowRange rr = row_range(cellSE, (cy + dy) * g.ncx + cx);
-            T yshift = T(dy) * P.sc;
-            uint32_t sy_code = (uint32_t)(1 - dy) << 30;
+            RowRange rr = row_range(cellSE, ka + dy * g.ncx);
             // the lanes of a particle run the same number of iterations, so
             // they can compact their finds with a group ballot
             unsigned nit = rr.hi > rr.lo ? (rr.hi - rr.lo + G - 1) / G : 0u;
@@ -179,13 +202,15 @@ k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ 
                 uint32_t ent = 0;
                 if (b < rr.hi) {
                     V4<T> hb = H0[b];
-                    int sx = b < rr.b1 ? 1 : (b < rr.b2 ? 0 : -1);
+                    // cell differences c_a - c_b along x and y
+                    int sx = row_step(rr, b);
+                    int sy = -dy;
                     T rx = (xa - hb.x) + T(sx) * P.sc;
-                    T ry = (ya - hb.y) - yshift;
+                    T ry = (ya - hb.y) + T(sy) * P.sc;
                     T r2 = rx * rx + ry * ry;
                     if (r2 < P.RL2hi && b != i) {
                         keep = true;
-                        ent = b | ((uint32_t)(sx + 1) << 28) | sy_code;
+                        ent = b | ((uint32_t)(sx + 1) << 28) | ((uint32_t)(sy + 1) << 30);
                         if (COLOUR && r2 < P.H2hi) {
                             bool in = true;
                             if (r2 >= P.H2lo) {
@@ -231,17 +256,25 @@ k_colour(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned i = gt / G, sub = gt % G;
     bool active = i < (unsigned)sc->nsrt;
+    const V4<T> *__restrict__ H0 = hot.H0;
     const V4<T> *__restrict__ H1 = hot.H1;
     T sum = T(0);
     V4<T> ha = mk4<T>(T(0), T(0), T(0), T(0));
     if (active) {
-        ha = hot.H0[i];
-        for_list<G, T>(P, nl, hot.H0, hot.pos, i, sub, ha.x, ha.y,
-                                 [&](unsigned b, T, T, T r2, const V4<T> &) {
-                                     T q, iq;
-                                     q_of(r2, P.h, P.inv_h, q, iq);
-                                     sum += H1[b].x * kernel_W<T, K>(P, q);
-                                 });
+        ha = H0[i];
+        for_list<G, SPH_CH_COLOUR, T>(
+            P, nl, hot.pos, i, sub, ha.x, ha.y,
+            [&](unsigned b) {
+                ColourRec<T> r;
+                V4<T> h0 = H0[b];
+                r.x = mk4<T>(h0.x, h0.y, H1[b].x, T(0));
+                return r;
+            },
+            [&](unsigned, T, T, T r2, const ColourRec<T> &r) {
+                T q, iq;
+                q_of(r2, P.h, P.inv_h, q, iq);
+                sum += r.x.z * kernel_W<T, K>(P, q);
+            });
     }
     sum = group_sum<G>(sum);
     if (active && sub == 0) {
@@ -261,18 +294,25 @@ k_normal(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned i = gt / G, sub = gt % G;
     bool active = i < (unsigned)sc->nsrt;
+    const V4<T> *__restrict__ CX = csf.CX;
     T nx = T(0), ny = T(0);
     if (active) {
-        V4<T> xa = csf.CX[i];
+        V4<T> xa = CX[i];
         T Ca = xa.w;
-        for_list<G, T>(P, nl, csf.CX, hot.pos, i, sub, xa.x, xa.y,
-                                 [&](unsigned, T rx, T ry, T r2, const V4<T> &xb) {
-                                     T q, iq;
-                                     q_of(r2, P.h, P.inv_h, q, iq);
-                                     T w = xb.z * (xb.w - Ca) * kernel_F<T, K>(P, q, iq);
-                                     nx += w * rx;
-                                     ny += w * ry;
-                                 });
+        for_list<G, SPH_CH_NORMAL, T>(
+            P, nl, hot.pos, i, sub, xa.x, xa.y,
+            [&](unsigned b) {
+                NormalRec<T> r;
+                r.x = CX[b];
+                return r;
+            },
+            [&](unsigned, T rx, T ry, T r2, const NormalRec<T> &r) {
+                T q, iq;
+                q_of(r2, P.h, P.inv_h, q, iq);
+                T wgt = r.x.z * (r.x.w - Ca) * kernel_F<T, K>(P, q, iq);
+                nx += wgt * rx;
+                ny += wgt * ry;
+            });
     }
     nx = group_sum<G>(nx);
     ny = group_sum<G>(ny);
@@ -293,8 +333,6 @@ template <class T, int G>
 __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, const Boundary &bd,
                                             uint32_t key, unsigned sub, T xa, T ya, T ua, T va,
                                             T y_abs, T &ax, T &ay) {
-    int cx, cy;
-    key_cell(g, key, cx, cy);
     const V4<T> *__restrict__ BH = (const V4<T> *)bd.bh;
     T ez = T(1);
     if (P.wall_h0 > T(0)) {
@@ -303,7 +341,7 @@ __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, co
         else if (z > -P.wall_h0) ez = abs_t(z * P.inv_wall_h0) + T(0.02);
     }
     for (int dy = -1; dy <= 1; ++dy) {
-        RowRange rr = row_range(bd.cellSE, (cy + dy) * g.ncx + cx);
+        RowRange rr = row_range(bd.cellSE, (int)key + dy * g.ncx);
         T yshift = T(dy) * P.sc;
         for (unsigned k = rr.lo + sub; k < rr.hi; k += G) {
             V4<T> bk = BH[k];
@@ -355,12 +393,21 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
             nha = csf.nhat[i];
             Na = (nha.x != T(0)) || (nha.y != T(0));
         }
+        const V4<T> *__restrict__ H0 = hot.H0;
         const V4<T> *__restrict__ H1 = hot.H1;
         const V2<T> *__restrict__ NH = csf.nhat;
-        for_list<G, T>(
-            P, nl, hot.H0, hot.pos, i, sub, ha.x, ha.y,
-            [&](unsigned b, T rx, T ry, T r2, const V4<T> &hb) {
-                V4<T> h1b = H1[b];
+        for_list<G, SPH_CH_FORCES, T>(
+            P, nl, hot.pos, i, sub, ha.x, ha.y,
+            [&](unsigned b) {
+                ForceRec<T> r;
+                r.x = H0[b];
+                r.h1 = H1[b];
+                r.nb = Na ? NH[b] : mk2(T(0), T(0));
+                return r;
+            },
+            [&](unsigned, T rx, T ry, T r2, const ForceRec<T> &r) {
+                const V4<T> &hb = r.x;
+                const V4<T> &h1b = r.h1;
                 T q, iq, ri;
                 q_of(r2, P.h, P.inv_h, q, iq, ri);
                 T F = kernel_F<T, K>(P, q, iq);
@@ -379,7 +426,7 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
                 T cv = abs_t(P.h * udotr) * (ri * ri);         // Eq. 31 (0 if r = 0)
                 vmax = cv > vmax ? cv : vmax;
                 if (Na) {                                      // Eq. 23
-                    V2<T> nb = NH[b];
+                    V2<T> nb = r.nb;
                     if (nb.x != T(0) || nb.y != T(0)) {
                         num += h1b.x * ((nb.x - nha.x) * rx + (nb.y - nha.y) * ry) * F;
                         den += h1b.x * kernel_W<T, K>(P, q);
@@ -703,8 +750,10 @@ void launch_colour(int lanes, const PhysT<T> &P, const Scalars *sc, const NList 
     with_lanes(lanes, [&](auto Gc) {
         constexpr int G = decltype(Gc)::value;
         int b = sweep_blocks(cap, G);
-        if (P.kernel == 1) launch_k(k_colour<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
-        else launch_k(k_colour<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+        if (P.kernel == 1)
+            launch_k(k_colour<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+        else
+            launch_k(k_colour<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
     });
 }
 
@@ -714,8 +763,10 @@ void launch_normal(int lanes, const PhysT<T> &P, const Scalars *sc, const NList 
     with_lanes(lanes, [&](auto Gc) {
         constexpr int G = decltype(Gc)::value;
         int b = sweep_blocks(cap, G);
-        if (P.kernel == 1) launch_k(k_normal<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
-        else launch_k(k_normal<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+        if (P.kernel == 1)
+            launch_k(k_normal<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+        else
+            launch_k(k_normal<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
     });
 }
 

@@ -14,6 +14,9 @@ a 256 MiB buffer (outside the timed events).
 
 Usage:
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload jet_c2|jet_c3|dam_c1]
+  python bench.py --workload ensemble_c4 [--steps K]   (64-jet batched ensemble,
+      one graph launch per ensemble step, against the same members run one after
+      another with their own step graphs)
   python bench.py --impl reference ...   (the FP64 CPU oracle on the host cores)
 Under torchrun each rank simulates its own jet (seed = rank): weak scaling,
 no data-path collective.
@@ -74,13 +77,42 @@ BYTES_PER_PARTICLE = {"cell_sort": 16 + 1 + 4 + 4 + 4 + 4 + 4, "reorder": 2 * 41
                       "predict": 41 + 12 + 48, "spawn": 0}
 
 
+# Batched ensemble: 64 jets on the Re x We grid of the paper's sweeps
+# (Table 1 ranges), dx from D/30 to D/80 and 20k-400k particles per member.
+ENS_RE = [100, 200, 400, 700, 1000, 1500, 2000, 3000]
+ENS_WE = [5, 10, 15, 20, 30, 40, 50, 60]
+
+
+def ensemble_members():
+    """(member, Re, We, dx, strip length) of the 64 members: member m = 8i + j
+    has Re_i, We_j, dx = D / (30 + 50 m/63) and a strip holding about
+    20k * 20^(m/63) particles (geometric from 20k to 400k)."""
+    out = []
+    for i, re in enumerate(ENS_RE):
+        for j, we in enumerate(ENS_WE):
+            m = 8 * i + j
+            f = m / 63.0
+            dx = 1.0 / (30.0 + 50.0 * f)
+            n_target = 20000.0 * 20.0 ** f
+            out.append((m, float(re), float(we), dx, n_target * dx * dx))
+    return out
+
+
+def ensemble_case(m, re, we, dx, length, skin):
+    case = wl.jet(seed=m, Re=re, We=we, dx=dx, length=length, kernel="wendland", prec="fp32",
+                  capacity_factor=1.15)
+    case["params"]["skin_over_h"] = skin
+    return case
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="jet_c2", choices=["jet_c2", "jet_c3", "dam_c1"])
+    ap.add_argument("--workload", default="jet_c2",
+                    choices=["jet_c2", "jet_c3", "dam_c1", "ensemble_c4"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tune", default="auto",
@@ -241,6 +273,11 @@ def main():
         dist.barrier()
 
     from paper_1603_02421_gb300.replicas import rank_members
+    if args.workload == "ensemble_c4":
+        bench_ensemble(args, binding, dist, dev, rank, world, local)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     case, desc = workload(args.workload, seed=rank_members(rank, world, world)[0])
     case["params"]["skin_over_h"] = args.skin
     stream = torch.cuda.Stream(device=dev)
@@ -413,12 +450,168 @@ def end_to_end(binding, case, stream, local, K, tuning):
     sim.close()
     h2d = n * (16 + 8 + 4 + 4 + 4 + 1 + 4)
     d2h_state = len(out["x"]) * (16 + 8 + 4 + 4 + 1 + 4 + 8 + 4)
-    scal = 728   # bytes of the device scalars read back by each sph_step
+    scal = 736   # bytes of the device scalars read back by each sph_step
     return {"value": psteps / el, "unit": UNIT,
             "h2d_bytes_per_step": h2d / K,
             "d2h_bytes_per_step": scal + d2h_state / K,
             "how": "sph_set_state from pinned host arrays, %d x sph_step (dt read back "
                    "each step), sph_get_state; host wall clock" % K}
+
+
+def bench_ensemble(args, binding, dist, dev, rank, world, local):
+    """The 64-member ensemble: ensemble steps (one graph launch advancing
+    every member one step) against the plain form (each member's own step
+    graph, one member after another) on the same stream.  Ranks own members
+    round-robin (weak scaling over members, no exchange)."""
+    import torch
+    from paper_1603_02421_gb300.replicas import rank_members, reduce_rate
+    specs = [ensemble_members()[m] for m in rank_members(rank, world, 64)]
+    stream = torch.cuda.Stream(device=dev)
+    sims = []
+    for (m, re, we, dx, length) in specs:
+        sims.append(binding.Simulation(ensemble_case(m, re, we, dx, length, args.skin),
+                                       stream=stream.cuda_stream, device=local))
+    ens = binding.Ensemble(sims, stream=stream.cuda_stream)
+    if args.tune == "auto":
+        lanes, cadence, _ = ens.autotune(8)
+    else:
+        lanes, cadence = (int(v) for v in args.tune.split(","))
+        for sm in sims:
+            sm.set_tuning(lanes, cadence)
+    counts = [binding.sph_kernel_counts(sm.ctx) for sm in sims]
+
+    def live():
+        return sum(sm.time()["n"] for sm in sims)
+
+    def builds():
+        return [sm.rebuild_stats()[0] for sm in sims]
+
+    K = args.steps
+    ens.run(max(args.warmup, 1))
+    # plain: every member's own step graph (captured on first use), then timed
+    for sm in sims:
+        binding.sph_run_async(sm.ctx, 1)
+    torch.cuda.synchronize(dev)
+    n0 = live()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for sm in sims:
+        binding.sph_run_async(sm.ctx, K)
+    e1.record(stream)
+    for sm in sims:
+        binding.sph_sync(sm.ctx)
+    torch.cuda.synchronize(dev)
+    plain_s = e0.elapsed_time(e1) / 1e3
+    n1 = live()
+    plain_units = 0.5 * (n0 + n1) * K
+    # batched
+    ens.run(1)
+    b0 = builds()
+    n0 = live()
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    e0.record(stream)
+    ens.run_async(K)
+    e1.record(stream)
+    ens.sync()
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    batched_s = e0.elapsed_time(e1) / 1e3
+    n1 = live()
+    b1 = builds()
+    units = 0.5 * (n0 + n1) * K
+    value, total_s, total_units = reduce_rate(batched_s, units, dist, dev)
+    plain_value, _, _ = reduce_rate(plain_s, plain_units, dist, dev)
+    launches = 0
+    for (pf, pr, _), bb0, bb1 in zip(counts, b0, b1):
+        full = bb1 - bb0
+        launches += full * pf + (K - full) * pr
+    Ls = [binding.sph_breakup_length(sm.ctx)[0] for sm in sims]
+
+    # end to end: members' states from pinned host arrays, K ensemble steps,
+    # states back to the host
+    Ke = min(K, 20)
+    states = [binding.sph_get_state(sm.ctx) for sm in sims]
+    pinned = [{k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
+               for k, v in st.items()} for st in states]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for sm, st in zip(sims, pinned):
+        binding.sph_set_state(sm.ctx, st)
+    ens.run(Ke)
+    outs = [binding.sph_get_state(sm.ctx) for sm in sims]
+    e2e_s = time.perf_counter() - t0
+    n_e2e = sum(len(st["x"]) for st in states)
+    h2d = n_e2e * (16 + 8 + 4 + 4 + 4 + 1 + 4)
+    d2h = sum(len(o["x"]) for o in outs) * (16 + 8 + 4 + 4 + 1 + 4 + 8 + 4)
+    e2e_value, _, _ = reduce_rate(e2e_s, n_e2e * Ke, dist, dev)
+
+    # whole-step FP32 work against the FP32 peak (algorithmic FLOPs per
+    # particle-step of the six pair sweeps and the per-particle work)
+    pairs_pp = 20.0
+    flop_ps = 2 * (pairs_pp * (FLOP_PER_PAIR["colour"] + FLOP_PER_PAIR["normal"] +
+                               FLOP_PER_PAIR["forces"]) +
+                   FLOP_PER_PARTICLE["colour"] + FLOP_PER_PARTICLE["normal"] +
+                   FLOP_PER_PARTICLE["forces_correct"])
+    sm_mhz = clk["sm_mhz"] if clk else 1900.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flop_ps * value / world / 1e12
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        m, re, we, dx, length = specs[0]
+        sample = oracle_sample(ensemble_case(m, re, we, dx, length, args.skin), 20000)
+        psteps, nsteps, el, n = run_oracle(sample, args.cpu_seconds)
+        cpu = {"value": psteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 CPU oracle (single thread), %d steps of member 0 (%d "
+                         "particles), %.1f s" % (nsteps, n, el)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "ensemble_c4: 64 planar jets, Re in %s x We in %s, "
+                                   "dx = D/30 .. D/80, 20k-400k particles each, Wendland, "
+                                   "FP32 pair sums / FP64 positions, adaptive dt per member"
+                                   % (ENS_RE, ENS_WE),
+                       "members_per_gpu": len(sims), "particles_total": 0.5 * (n0 + n1),
+                       "parallelism": "members round-robin over ranks (no exchange)",
+                       "l2": "inputs larger than L2 (all members resident, several GB)",
+                       "tuning": {"lanes": lanes, "cadence": cadence, "skin_over_h": args.skin,
+                                  "chosen_by": "ensemble autotuner" if args.tune == "auto"
+                                  else "flag"},
+                       "plain_value": plain_value,
+                       "batched_over_plain": value / plain_value,
+                       "plain_how": "each member's own step graph, members one after "
+                                    "another on the same stream",
+                       "wall_s": wall},
+            "roofline": {"kernel": "whole ensemble step (all kernels)", "bound": "alu",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz,
+                         "algorithmic_per_particle_step": flop_ps},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / Ke,
+                    "d2h_bytes_per_step": d2h / Ke,
+                    "how": "sph_set_state of every member from pinned host arrays, %d "
+                           "ensemble steps, sph_get_state of every member; host wall clock"
+                           % Ke},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "breakup_L_over_D_mean": float(np.mean(Ls)),
+        }
+        print(json.dumps(line), flush=True)
+    ens.close()
+    for sm in sims:
+        sm.close()
 
 
 if __name__ == "__main__":

@@ -266,6 +266,49 @@ sph_status sph_pairs_noalloc(const double *x, const double *y, long long n, doub
                              unsigned *pair_a, unsigned *pair_b, long long cap,
                              long long *npairs, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Ensembles: several independent simulations (e.g. jets on a grid of Re and
+ * We, Table 1, with different dx and particle counts) advanced together.
+ * One ensemble step is one step of every member, each with its own time
+ * step; the members' steps are the branches of one CUDA graph, so one graph
+ * launch runs all of them and the GPU overlaps the kernels of different
+ * members.  Each member computes exactly what sph_run computes for it alone.
+ * ------------------------------------------------------------------------ */
+typedef struct sph_ensemble sph_ensemble;
+
+/* Groups n >= 1 distinct contexts of one device.  The ensemble keeps the
+ * pointers (the contexts stay owned by the caller and must outlive it) and
+ * works on cuda_stream (a cudaStream_t; NULL creates a stream of its own).
+ * Work enqueued on the members' streams before an ensemble run completes
+ * before it, and later work on them waits for it.  On error *out is NULL and
+ * sph_ensemble_last_error(NULL) describes it. */
+sph_status sph_ensemble_create(sph_ctx *const *members, int n, void *cuda_stream,
+                               sph_ensemble **out);
+
+/* Enqueue nsteps ensemble steps and return without waiting.  The graph is
+ * re-captured when a member's parameters or tuning changed since the last
+ * run. */
+sph_status sph_ensemble_run(sph_ensemble *e, long long nsteps);
+
+/* Wait for the enqueued steps and report the first member whose steps
+ * raised a device-side error (*bad_member = its index, else -1; nullable);
+ * the member's own sph_last_error holds the description. */
+sph_status sph_ensemble_sync(sph_ensemble *e, int *bad_member);
+
+/* Autotuner over one (lanes, cadence) for all members: times trial_steps
+ * ensemble steps for lanes in {1, 2, 4, 8} and cadence in {1, 2, 4, 8} from
+ * copies of the members' states (rejecting settings that trip SPH_ERR_SKIN),
+ * restores the states and keeps the fastest setting.  Outputs nullable. */
+sph_status sph_ensemble_autotune(sph_ensemble *e, int trial_steps, int *lanes, int *cadence,
+                                 double *ms_per_step);
+
+/* Waits for the ensemble's work and frees it (not the members). */
+void sph_ensemble_destroy(sph_ensemble *e);
+
+/* Description of the last error of an ensemble call (e = NULL: of the last
+ * failed sph_ensemble_create). */
+const char *sph_ensemble_last_error(const sph_ensemble *e);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsph.so")
 
 SPH_OK = 0
+SPH_ERR_ARG, SPH_ERR_OOM, SPH_ERR_CAPACITY, SPH_ERR_CUDA = -1, -2, -3, -4
+SPH_ERR_NONFINITE, SPH_ERR_TIMEOUT, SPH_ERR_STATE, SPH_ERR_SKIN = -5, -6, -7, -8
 STATUS = {0: "SPH_OK", -1: "SPH_ERR_ARG", -2: "SPH_ERR_OOM", -3: "SPH_ERR_CAPACITY",
           -4: "SPH_ERR_CUDA", -5: "SPH_ERR_NONFINITE", -6: "SPH_ERR_TIMEOUT",
           -7: "SPH_ERR_STATE", -8: "SPH_ERR_SKIN"}
@@ -80,6 +82,14 @@ _SIGS = {
     "sph_kernel_counts": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sph_get_rebuild_stats": ([_CTX, _LL, _D, _D], ctypes.c_int),
+    "sph_ensemble_create": ([ctypes.POINTER(_CTX), ctypes.c_int, ctypes.c_void_p,
+                             ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "sph_ensemble_run": ([ctypes.c_void_p, ctypes.c_longlong], ctypes.c_int),
+    "sph_ensemble_sync": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "sph_ensemble_autotune": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int), _D], ctypes.c_int),
+    "sph_ensemble_destroy": ([ctypes.c_void_p], None),
+    "sph_ensemble_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "sph_run_async": ([_CTX, ctypes.c_longlong], ctypes.c_int),
     "sph_set_tuning": ([_CTX, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sph_get_tuning": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -413,3 +423,78 @@ class Simulation:
 
     def kernels_per_step(self):
         return sph_kernel_counts(self.ctx)[0]
+
+
+def _ens_check(ens, st, bad=None):
+    if st != SPH_OK:
+        err = SphError(st, lib().sph_ensemble_last_error(ens).decode(errors="replace"))
+        err.member = bad
+        raise err
+
+
+def sph_ensemble_last_error(ens=None):
+    return lib().sph_ensemble_last_error(ens).decode(errors="replace")
+
+
+def sph_ensemble_create(ctxs, stream=None):
+    arr = (_CTX * len(ctxs))(*ctxs)
+    out = ctypes.c_void_p()
+    _ens_check(None, lib().sph_ensemble_create(arr, len(ctxs), stream, ctypes.byref(out)))
+    return out.value
+
+
+def sph_ensemble_run(ens, nsteps):
+    _ens_check(ens, lib().sph_ensemble_run(ens, int(nsteps)))
+
+
+def sph_ensemble_sync(ens):
+    """Raises SphError with .member = index of the failing member."""
+    bad = ctypes.c_int(-1)
+    st = lib().sph_ensemble_sync(ens, ctypes.byref(bad))
+    _ens_check(ens, st, bad.value)
+
+
+def sph_ensemble_autotune(ens, trial_steps=16):
+    a, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _ens_check(ens, lib().sph_ensemble_autotune(ens, int(trial_steps), ctypes.byref(a),
+                                                ctypes.byref(b), ctypes.byref(ms)))
+    return a.value, b.value, ms.value
+
+
+def sph_ensemble_destroy(ens):
+    lib().sph_ensemble_destroy(ens)
+
+
+class Ensemble:
+    """Several Simulations advanced together, one CUDA graph launch per
+    ensemble step (sph_ensemble_*).  The Simulations stay owned by the
+    caller and must outlive the Ensemble."""
+
+    def __init__(self, sims, stream=None):
+        self.sims = list(sims)
+        self.ens = None
+        self.ens = sph_ensemble_create([s.ctx for s in self.sims], stream)
+
+    def run_async(self, nsteps):
+        sph_ensemble_run(self.ens, nsteps)
+
+    def sync(self):
+        sph_ensemble_sync(self.ens)
+
+    def run(self, nsteps):
+        self.run_async(nsteps)
+        self.sync()
+
+    def autotune(self, trial_steps=16):
+        return sph_ensemble_autotune(self.ens, trial_steps)
+
+    def close(self):
+        if getattr(self, "ens", None):
+            sph_ensemble_destroy(self.ens)
+            self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

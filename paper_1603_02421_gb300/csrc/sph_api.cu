@@ -71,6 +71,7 @@ struct sph_ctx {
     cudaGraph_t graph[2] = {};
     cudaGraphExec_t gexec[2] = {};
     bool graph_dirty = true;
+    unsigned long long graph_gen = 0;   // counts changes that invalidate captured steps
 
     // tuning: lanes per particle in the pair sweeps, longest cell-build cadence
     int lanes = 4, cadence = 1;
@@ -444,11 +445,18 @@ static sph_status after_work(sph_ctx *c, const char *what) {
     return status_from_err(c, c->hsc->err);
 }
 
+// The captured step graphs (the context's own and any ensemble's) no longer
+// match the context's parameters or tuning.
+static void mark_graph_dirty(sph_ctx *c) {
+    c->graph_dirty = true;
+    ++c->graph_gen;
+}
+
 static void rebuild_phys(sph_ctx *c) {
     bool walls = !c->bx.empty();
     c->Pf = make_phys<float>(c->prm, c->grid, walls);
     c->Pd = make_phys<double>(c->prm, c->grid, walls);
-    c->graph_dirty = true;
+    mark_graph_dirty(c);
 }
 
 static sph_status upload_boundary(sph_ctx *c) {
@@ -798,7 +806,7 @@ sph_status sph_inflow(sph_ctx *c, double x_exit, double y0, double y1, double U,
         s = push_scalars(c);
         if (s) return s;
         f.on = 1;
-        c->graph_dirty = true;
+        mark_graph_dirty(c);
         return SPH_OK;
     } catch (...) {
         return fail(c, SPH_ERR_OOM, "host allocation failed");
@@ -830,32 +838,44 @@ sph_status sph_evaluate(sph_ctx *c) {
 // bodies), and the graph that decides on the device: a kernel sets an IF
 // node's condition from the flag the previous step left, the IF node runs
 // the rebuild or the reuse start, then the rest of the step follows.
-static sph_status ensure_graph(sph_ctx *c) {
-    if (!c->graph_dirty && c->gexec[0] && c->gexec[1] && c->cexec) return SPH_OK;
-    for (int k = 0; k < 2; ++k) {
-        if (c->gexec[k]) { cudaGraphExecDestroy(c->gexec[k]); c->gexec[k] = nullptr; }
-        if (c->graph[k]) { cudaGraphDestroy(c->graph[k]); c->graph[k] = nullptr; }
-        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        step_any(c, k == 0);
-        c->prof_pending = false;
-        CK(cudaStreamEndCapture(c->stream, &c->graph[k]), "end capture");
-        CK(cudaGraphInstantiate(&c->gexec[k], c->graph[k], 0), "instantiate graph");
-    }
-    if (c->cexec) { cudaGraphExecDestroy(c->cexec); c->cexec = nullptr; }
-    if (c->cgraph) { cudaGraphDestroy(c->cgraph); c->cgraph = nullptr; }
+// Appends one step of context c to graph g as a branch of its own (no
+// dependencies on nodes already in g).  At cadence 1 the branch is the
+// rebuilding step.  Otherwise it decides on the device: a one-thread kernel
+// sets an IF node's condition from the flag the previous step left, the IF
+// node runs the rebuild or the reuse start, then the rest of the step
+// follows.
+static sph_status append_step(sph_ctx *c, cudaGraph_t g) {
     c->no_ticks = true;
-    cudaGraph_t g = nullptr;
-    CK(cudaGraphCreate(&g, 0), "graph create");
-    c->cgraph = g;
+    struct Untick {
+        sph_ctx *c;
+        ~Untick() { c->no_ticks = false; }
+    } untick{c};
+    if (c->cadence <= 1) {
+        CK(cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal), "capture step");
+        if (c->tsz == 4) {
+            enqueue_cells<float>(c, true);
+            enqueue_rest<float>(c);
+        } else {
+            enqueue_cells<double>(c, true);
+            enqueue_rest<double>(c);
+        }
+        CK(cudaStreamEndCapture(c->stream, &g), "end capture step");
+        return SPH_OK;
+    }
     cudaGraphConditionalHandle h;
-    CK(cudaGraphConditionalHandleCreate(&h, g, 1u, 0u), "conditional handle");
-    CK(cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0,
-                                     cudaStreamCaptureModeThreadLocal), "capture decide");
-    launch_decide(h, c->sc, c->stream);
-    CK(cudaStreamEndCapture(c->stream, &g), "end capture decide");
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0u, 0u), "conditional handle");
+    const Scalars *scp = c->sc;
+    void *args[2] = {(void *)&h, (void *)&scp};
+    cudaKernelNodeParams kp = {};
+    kp.func = decide_kernel();
+    kp.gridDim = dim3(1, 1, 1);
+    kp.blockDim = dim3(1, 1, 1);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
     cudaGraphNode_t dnode;
-    size_t nn = 1;
-    CK(cudaGraphGetNodes(g, &dnode, &nn), "graph nodes");
+    CK(cudaGraphAddKernelNode(&dnode, g, nullptr, 0, &kp), "decide node");
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = h;
@@ -874,8 +894,28 @@ static sph_status ensure_graph(sph_ctx *c) {
                                      cudaStreamCaptureModeThreadLocal), "capture rest");
     if (c->tsz == 4) enqueue_rest<float>(c); else enqueue_rest<double>(c);
     CK(cudaStreamEndCapture(c->stream, &g), "end capture rest");
-    c->no_ticks = false;
-    CK(cudaGraphInstantiate(&c->cexec, g, 0), "instantiate conditional graph");
+    return SPH_OK;
+}
+
+// The two host-chosen step graphs (rebuild / reuse; the profiling path, and
+// every step at cadence 1) and the graph that decides on the device.
+static sph_status ensure_graph(sph_ctx *c) {
+    if (!c->graph_dirty && c->gexec[0] && c->gexec[1] && c->cexec) return SPH_OK;
+    for (int k = 0; k < 2; ++k) {
+        if (c->gexec[k]) { cudaGraphExecDestroy(c->gexec[k]); c->gexec[k] = nullptr; }
+        if (c->graph[k]) { cudaGraphDestroy(c->graph[k]); c->graph[k] = nullptr; }
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        step_any(c, k == 0);
+        c->prof_pending = false;
+        CK(cudaStreamEndCapture(c->stream, &c->graph[k]), "end capture");
+        CK(cudaGraphInstantiate(&c->gexec[k], c->graph[k], 0), "instantiate graph");
+    }
+    if (c->cexec) { cudaGraphExecDestroy(c->cexec); c->cexec = nullptr; }
+    if (c->cgraph) { cudaGraphDestroy(c->cgraph); c->cgraph = nullptr; }
+    CK(cudaGraphCreate(&c->cgraph, 0), "graph create");
+    sph_status s = append_step(c, c->cgraph);
+    if (s) return s;
+    CK(cudaGraphInstantiate(&c->cexec, c->cgraph, 0), "instantiate conditional graph");
     c->graph_dirty = false;
     return SPH_OK;
 }
@@ -1163,7 +1203,7 @@ sph_status sph_profile(sph_ctx *c, int enable) {
             c->pev[k].push_back(e);
             c->pname[k].push_back(nullptr);
         }
-    if (c->prof != (enable != 0)) c->graph_dirty = true;
+    if (c->prof != (enable != 0)) mark_graph_dirty(c);
     c->prof = enable != 0;
     c->prof_pending = false;
     c->ptot.clear();
@@ -1194,7 +1234,7 @@ sph_status sph_set_tuning(sph_ctx *c, int lanes, int cadence) {
     if (cadence < 1 || cadence > 64) return fail(c, SPH_ERR_ARG, "cadence must lie in [1, 64]");
     // both are captured into the step graphs (launch shapes; the cadence
     // is an argument of the rebuild decision)
-    if (lanes != c->lanes || cadence != c->cadence) c->graph_dirty = true;
+    if (lanes != c->lanes || cadence != c->cadence) mark_graph_dirty(c);
     c->lanes = lanes;
     c->cadence = cadence;
     c->force_full = true;
@@ -1318,6 +1358,217 @@ sph_status sph_kernel_counts(sph_ctx *c, int *per_full_step, int *per_reused_ste
     if (per_reused_step) *per_reused_step = (c->cadence > 1 ? reuse : full) + rest + decide;
     if (per_breakup) *per_breakup = sort + 4;    // + union-find init, link, compress, reach
     return SPH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Ensembles
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct sph_ensemble {
+    std::vector<sph_ctx *> m;
+    std::vector<unsigned long long> gen;   // member graph generations captured
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev = nullptr;              // orders member streams and the ensemble stream
+    std::string err;
+};
+
+namespace {
+std::string g_ens_error;
+
+sph_status ens_fail(sph_ensemble *e, sph_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (e) e->err = buf; else g_ens_error = buf;
+    return st;
+}
+
+#define ECK(e, call, what)                                                                        \
+    do {                                                                                          \
+        cudaError_t ce_ = (call);                                                                 \
+        if (ce_ != cudaSuccess)                                                                   \
+            return ens_fail((e), ce_ == cudaErrorMemoryAllocation ? SPH_ERR_OOM : SPH_ERR_CUDA,   \
+                            "%s: %s", (what), cudaGetErrorString(ce_));                           \
+    } while (0)
+
+// Captures one step of every member as parallel branches of one graph.
+sph_status ens_ensure_graph(sph_ensemble *e) {
+    bool stale = !e->exec;
+    for (size_t k = 0; k < e->m.size() && !stale; ++k) stale = e->gen[k] != e->m[k]->graph_gen;
+    if (!stale) return SPH_OK;
+    if (e->exec) { cudaGraphExecDestroy(e->exec); e->exec = nullptr; }
+    if (e->graph) { cudaGraphDestroy(e->graph); e->graph = nullptr; }
+    ECK(e, cudaGraphCreate(&e->graph, 0), "ensemble graph");
+    for (size_t k = 0; k < e->m.size(); ++k) {
+        sph_status s = append_step(e->m[k], e->graph);
+        if (s) return ens_fail(e, s, "member %zu: %s", k, e->m[k]->err.c_str());
+        e->gen[k] = e->m[k]->graph_gen;
+    }
+    ECK(e, cudaGraphInstantiate(&e->exec, e->graph, 0), "instantiate ensemble graph");
+    return SPH_OK;
+}
+}  // namespace
+
+extern "C" {
+
+sph_status sph_ensemble_create(sph_ctx *const *members, int n, void *cuda_stream,
+                               sph_ensemble **out) {
+    if (!out) return ens_fail(nullptr, SPH_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!members || n < 1) return ens_fail(nullptr, SPH_ERR_ARG, "need n >= 1 members");
+    for (int k = 0; k < n; ++k) {
+        if (!members[k]) return ens_fail(nullptr, SPH_ERR_ARG, "member %d is NULL", k);
+        for (int j = 0; j < k; ++j)
+            if (members[j] == members[k])
+                return ens_fail(nullptr, SPH_ERR_ARG, "member %d repeats member %d", k, j);
+        if (members[k]->prm.device != members[0]->prm.device)
+            return ens_fail(nullptr, SPH_ERR_ARG, "members are on different devices");
+    }
+    sph_ensemble *e = new (std::nothrow) sph_ensemble();
+    if (!e) return ens_fail(nullptr, SPH_ERR_OOM, "host allocation failed");
+    e->m.assign(members, members + n);
+    e->gen.assign((size_t)n, ~0ull);
+    auto bail = [&](cudaError_t ce, const char *what) {
+        ens_fail(nullptr, SPH_ERR_CUDA, "%s: %s", what, cudaGetErrorString(ce));
+        sph_ensemble_destroy(e);
+        return SPH_ERR_CUDA;
+    };
+    cudaError_t ce = cudaSetDevice(members[0]->prm.device);
+    if (ce != cudaSuccess) return bail(ce, "cudaSetDevice");
+    if (cuda_stream) {
+        e->stream = (cudaStream_t)cuda_stream;
+    } else {
+        ce = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) return bail(ce, "stream");
+        e->own_stream = true;
+    }
+    ce = cudaEventCreateWithFlags(&e->ev, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return bail(ce, "event");
+    *out = e;
+    return SPH_OK;
+}
+
+sph_status sph_ensemble_run(sph_ensemble *e, long long nsteps) {
+    if (!e) return SPH_ERR_ARG;
+    if (nsteps < 0) return ens_fail(e, SPH_ERR_ARG, "nsteps < 0");
+    if (nsteps == 0) return SPH_OK;
+    sph_status s = ens_ensure_graph(e);
+    if (s) return s;
+    for (sph_ctx *c : e->m) {
+        ECK(e, cudaEventRecord(e->ev, c->stream), "order members");
+        ECK(e, cudaStreamWaitEvent(e->stream, e->ev, 0), "order members");
+    }
+    for (long long k = 0; k < nsteps; ++k) {
+        for (sph_ctx *c : e->m) {
+            if (c->force_full && c->cadence > 1)
+                ECK(e, cudaMemsetAsync(&c->sc->need_full, 0x01, sizeof(int), e->stream),
+                    "force rebuild");
+            c->force_full = false;
+        }
+        ECK(e, cudaGraphLaunch(e->exec, e->stream), "ensemble graph launch");
+    }
+    ECK(e, cudaEventRecord(e->ev, e->stream), "order members");
+    for (sph_ctx *c : e->m) {
+        ECK(e, cudaStreamWaitEvent(c->stream, e->ev, 0), "order members");
+        c->hsc_fresh = false;
+        c->n_eval = -1;
+        c->csf_valid = false;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_ensemble_sync(sph_ensemble *e, int *bad_member) {
+    if (bad_member) *bad_member = -1;
+    if (!e) return SPH_ERR_ARG;
+    ECK(e, cudaStreamSynchronize(e->stream), "ensemble synchronize");
+    for (size_t k = 0; k < e->m.size(); ++k) {
+        sph_status s = sph_sync(e->m[k]);
+        if (s) {
+            if (bad_member) *bad_member = (int)k;
+            return ens_fail(e, s, "member %zu: %s", k, e->m[k]->err.c_str());
+        }
+    }
+    return SPH_OK;
+}
+
+sph_status sph_ensemble_autotune(sph_ensemble *e, int trial_steps, int *lanes, int *cadence,
+                                 double *ms_per_step) {
+    if (!e) return SPH_ERR_ARG;
+    if (trial_steps < 1 || trial_steps > 10000)
+        return ens_fail(e, SPH_ERR_ARG, "trial_steps in [1, 10000]");
+    sph_status s = sph_ensemble_sync(e, nullptr);
+    if (s) return s;
+    for (sph_ctx *c : e->m) {
+        s = snapshot(c, false);
+        if (s) return ens_fail(e, s, "snapshot: %s", c->err.c_str());
+    }
+    const int L[4] = {1, 2, 4, 8}, K[4] = {1, 2, 4, 8};
+    int bestL = e->m[0]->lanes, bestK = e->m[0]->cadence;
+    double best = 1e300;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    ECK(e, cudaEventCreate(&t0), "event");
+    ECK(e, cudaEventCreate(&t1), "event");
+    auto restore_all = [&]() -> sph_status {
+        for (sph_ctx *c : e->m) {
+            sph_status r = snapshot(c, true);
+            if (r) return r;
+        }
+        return SPH_OK;
+    };
+    for (int a = 0; a < 4 && !s; ++a) {
+        for (int b = 0; b < 4 && !s; ++b) {
+            s = restore_all();
+            for (size_t k = 0; k < e->m.size() && !s; ++k) s = sph_set_tuning(e->m[k], L[a], K[b]);
+            if (!s) s = sph_ensemble_run(e, K[b]);   // capture + one cycle
+            if (!s) s = sph_ensemble_sync(e, nullptr);
+            if (s == SPH_ERR_SKIN) { s = SPH_OK; continue; }
+            if (s) break;
+            cudaEventRecord(t0, e->stream);
+            s = sph_ensemble_run(e, trial_steps);
+            cudaEventRecord(t1, e->stream);
+            if (!s) s = sph_ensemble_sync(e, nullptr);
+            if (s == SPH_ERR_SKIN) { s = SPH_OK; continue; }
+            if (s) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            double per = ms / trial_steps;
+            if (per < best) { best = per; bestL = L[a]; bestK = K[b]; }
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    sph_status r = restore_all();
+    if (s) return s;
+    if (r) return ens_fail(e, r, "restore failed");
+    if (best >= 1e300) return ens_fail(e, SPH_ERR_STATE, "no tuning candidate ran without error");
+    for (sph_ctx *c : e->m) {
+        r = sph_set_tuning(c, bestL, bestK);
+        if (r) return ens_fail(e, r, "%s", c->err.c_str());
+    }
+    if (lanes) *lanes = bestL;
+    if (cadence) *cadence = bestK;
+    if (ms_per_step) *ms_per_step = best;
+    return SPH_OK;
+}
+
+void sph_ensemble_destroy(sph_ensemble *e) {
+    if (!e) return;
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    if (e->ev) cudaEventDestroy(e->ev);
+    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+    delete e;
+}
+
+const char *sph_ensemble_last_error(const sph_ensemble *e) {
+    return e ? e->err.c_str() : g_ens_error.c_str();
 }
 
 }  // extern "C"

@@ -252,5 +252,7 @@ void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State
                   const double *layer_y, int cap, int cadence, cudaStream_t s);
 // Sets the step graph's rebuild condition from sc->need_full.
 void launch_decide(cudaGraphConditionalHandle h, const Scalars *sc, cudaStream_t s);
+// Host stub of the kernel launch_decide runs (for explicit graph nodes).
+void *decide_kernel();
 
 }  // namespace sph

@@ -820,6 +820,8 @@ void launch_decide(cudaGraphConditionalHandle h, const Scalars *sc, cudaStream_t
     launch_k(k_decide, 1, 1, s, h, sc);
 }
 
+void *decide_kernel() { return (void *)k_decide; }
+
 #define SPH_INST(T)                                                                              \
     template void launch_reorder<T>(const PhysT<T> &, const Grid &, Scalars *, const CellSort &,  \
                                     const State<T> &, const State<T> &, const Hot<T> &, int,      \

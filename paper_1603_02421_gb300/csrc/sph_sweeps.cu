@@ -33,6 +33,11 @@ namespace sph {
 #define SPH_CH_FORCES 1
 #endif
 
+// Blocks per SM the pair sweeps are compiled for (register budget).
+#ifndef SPH_SWEEP_MINB
+#define SPH_SWEEP_MINB 10
+#endif
+
 
 template <class T> using V2 = typename Vec<T>::v2;
 template <class T> using V4 = typename Vec<T>::v4;
@@ -169,7 +174,7 @@ void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const CellSor
 // Neighbour list (Sec. 2-7) + colour of evaluation n (Eq. 14)
 // ---------------------------------------------------------------------------
 template <class T, int K, bool COLOUR, int G>
-__global__ void __launch_bounds__(SWEEP_BLOCK)
+__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
 k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ cellSE,
         const uint32_t *__restrict__ key, Hot<T> hot, NList nl, Csf<T> csf) {
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -251,7 +256,7 @@ k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ 
 // Eq. 14: colour at the half step (over the list)
 // ---------------------------------------------------------------------------
 template <class T, int K, int G>
-__global__ void __launch_bounds__(SWEEP_BLOCK)
+__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
 k_colour(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T> csf) {
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned i = gt / G, sub = gt % G;
@@ -289,7 +294,7 @@ k_colour(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T
 // Eqs. 18, 20, 21: normal, filter, unit normal
 // ---------------------------------------------------------------------------
 template <class T, int K, int G>
-__global__ void __launch_bounds__(SWEEP_BLOCK)
+__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
 k_normal(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T> csf) {
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned i = gt / G, sub = gt % G;
@@ -370,7 +375,7 @@ __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, co
 // Eqs. 7, 9, 10, 23-25, 29-31 (+ corrector in mode 2)
 // ---------------------------------------------------------------------------
 template <class T, int K, int MODE, int G>
-__global__ void __launch_bounds__(SWEEP_BLOCK)
+__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
 k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
          const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf, Boundary bd, State<T> srt,
          State<T> raw, V2<T> *__restrict__ acc, T *__restrict__ drout) {
@@ -641,6 +646,8 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
 // ---------------------------------------------------------------------------
 // inflow layers + time advance (one block)
 // ---------------------------------------------------------------------------
+static_assert(RED_SLOTS == 32, "one reduction slot per lane of a warp");
+
 template <class T>
 __global__ void k_spawn(Inflow inf, double ufx, double ufy, float half_skin,
                         Scalars *__restrict__ sc, State<T> raw,
@@ -648,53 +655,55 @@ __global__ void k_spawn(Inflow inf, double ufx, double ufy, float half_skin,
     __shared__ int do_spawn, base;
     __shared__ unsigned idbase;
     __shared__ double xnew, unew;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // warp 0: each lane folds and resets one reduction slot, lanes 0 and
+        // 1 evaluate the two inflow velocities; lane 0 takes the decisions
+        const unsigned lane = threadIdx.x;
+        unsigned d2 = __reduce_max_sync(0xffffffffu, sc->max_disp2[lane]);
+        unsigned s2 = __reduce_max_sync(0xffffffffu, sc->max_step2[lane]);
+        sc->max_disp2[lane] = 0u;
+        sc->max_step2[lane] = 0u;
+        sc->dtmin_f[lane] = 0x7f7f7f7fu;
+        sc->dtmin_d[lane] = 0x7f7f7f7f7f7f7f7full;
         double dt = sc->dt, t = sc->t, half = 0.5 * dt;
-        int n = sc->nsrt;
-        do_spawn = 0;
-        if (inf.on) {
-            double uh = inflow_u(inf, t + half);
-            double xs = __dadd_rn(sc->x_up, __dmul_rn(half, uh));
-            double xu = __dsub_rn(__dmul_rn(2.0, xs), sc->x_up);
-            sc->x_up = xu;
-            if (xu >= inf.threshold) {
-                if (n + inf.ny <= cap) {
-                    do_spawn = 1;
-                    base = n;
-                    idbase = sc->next_id;
-                    xnew = __dsub_rn(xu, inf.dx);
-                    unew = inflow_u(inf, t + dt);
-                    sc->x_up = xnew;
-                    sc->next_id += (unsigned)inf.ny;
-                    n += inf.ny;
-                } else {
-                    atomicOr(&sc->err, ERR_CAPACITY);
+        double uq = (inf.on && lane < 2) ? inflow_u(inf, lane == 0 ? t + half : t + dt) : 0.0;
+        double uh = __shfl_sync(0xffffffffu, uq, 0);
+        double ue = __shfl_sync(0xffffffffu, uq, 1);
+        if (lane == 0) {
+            int n = sc->nsrt;
+            do_spawn = 0;
+            if (inf.on) {
+                double xs = __dadd_rn(sc->x_up, __dmul_rn(half, uh));
+                double xu = __dsub_rn(__dmul_rn(2.0, xs), sc->x_up);
+                sc->x_up = xu;
+                if (xu >= inf.threshold) {
+                    if (n + inf.ny <= cap) {
+                        do_spawn = 1;
+                        base = n;
+                        idbase = sc->next_id;
+                        xnew = __dsub_rn(xu, inf.dx);
+                        unew = ue;
+                        sc->x_up = xnew;
+                        sc->next_id += (unsigned)inf.ny;
+                        n += inf.ny;
+                    } else {
+                        atomicOr(&sc->err, ERR_CAPACITY);
+                    }
                 }
             }
-        }
-        sc->n = n;
-        sc->t = __dadd_rn(t, dt);
-        sc->step += 1;
-        // rebuild next step if particles were appended, the cadence is
-        // reached, or one more step (twice this one's largest move) could
-        // carry a particle past skin/2 from where the lists were built
-        unsigned d2 = 0u, s2 = 0u;
-        for (int k = 0; k < RED_SLOTS; ++k) {
-            d2 = max(d2, sc->max_disp2[k]);
-            s2 = max(s2, sc->max_step2[k]);
-        }
-        float dmax = sqrtf(__uint_as_float(d2));
-        float smax = sqrtf(__uint_as_float(s2));
-        sc->last_dmax = dmax;
-        sc->last_smax = smax;
-        int need = do_spawn || sc->since_full + 1 >= cadence || dmax + 2.0f * smax > half_skin;
-        sc->need_full = need;
-        sc->since_full = need ? 0 : sc->since_full + 1;
-        for (int k = 0; k < RED_SLOTS; ++k) {
-            sc->max_disp2[k] = 0u;
-            sc->max_step2[k] = 0u;
-            sc->dtmin_f[k] = 0x7f7f7f7fu;
-            sc->dtmin_d[k] = 0x7f7f7f7f7f7f7f7full;
+            sc->n = n;
+            sc->t = __dadd_rn(t, dt);
+            sc->step += 1;
+            // rebuild next step if particles were appended, the cadence is
+            // reached, or one more step (twice this one's largest move) could
+            // carry a particle past skin/2 from where the lists were built
+            float dmax = sqrtf(__uint_as_float(d2));
+            float smax = sqrtf(__uint_as_float(s2));
+            sc->last_dmax = dmax;
+            sc->last_smax = smax;
+            int need = do_spawn || sc->since_full + 1 >= cadence || dmax + 2.0f * smax > half_skin;
+            sc->need_full = need;
+            sc->since_full = need ? 0 : sc->since_full + 1;
         }
     }
     __syncthreads();

@@ -66,12 +66,18 @@ def workload(name: str, seed: int):
 
 
 # Algorithmic FP32 operations per interacting pair (r < 2h) of each pair
-# sweep, counting a fused multiply-add as 2, sqrt and division as 1 each.
-# The derivation is listed in the design doc.
-FLOP_PER_PAIR = {"list_colour": 16, "colour": 16, "normal": 18, "forces": 62,
-                 "forces_correct": 62}
-FLOP_PER_PARTICLE = {"list_colour": 2, "colour": 2, "normal": 8, "forces": 30,
-                     "forces_correct": 40}
+# sweep (Wendland), counting a fused multiply-add as 2 and rsqrt, sqrt and
+# division as 1 each; compares and selects are not counted.  Geometry (offset
+# difference with the cell shift, r^2, 1/r, q, 1/q) 11; W(q) 7; F(q) 4.
+#   colour: geometry + W + accumulate 2 = 20
+#   normal: geometry + F + weight 3 + accumulate 4 = 22
+#   forces: geometry + F + continuity 9 + viscosity 10 + pressure 8 + Eq. 31
+#           term 3 = 45 (the curvature sums add 17 for pairs of two
+#           free-surface particles; not counted)
+FLOP_PER_PAIR = {"list_colour": 20, "colour": 20, "normal": 22, "forces": 45,
+                 "forces_correct": 45}
+FLOP_PER_PARTICLE = {"list_colour": 2, "colour": 2, "normal": 8, "forces": 20,
+                     "forces_correct": 30}
 # Algorithmic HBM bytes per particle of the streaming kernel groups (FP32 path).
 BYTES_PER_PARTICLE = {"cell_sort": 16 + 1 + 4 + 4 + 4 + 4 + 4, "reorder": 2 * 41 + 4 + 4 + 32,
                       "predict": 41 + 12 + 48, "spawn": 0}
@@ -103,6 +109,39 @@ def ensemble_case(m, re, we, dx, length, skin):
                   capacity_factor=1.15)
     case["params"]["skin_over_h"] = skin
     return case
+
+
+def sources_sha256() -> str:
+    """Hash of the CUDA sources (kernels and runtime) of libsph."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1603_02421_gb300", "csrc")
+    hsh = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                hsh.update(name.encode() + b"\0" + f.read())
+    return hsh.hexdigest()
+
+
+def measured_traffic(group: str, particles: float):
+    """DRAM bytes (read + write) per launch of a kernel group from an ncu
+    capture summarised under profiles/ (a line 'traffic: group=... bytes=...
+    particles=... sources_sha256=...'), scaled to `particles`; None when no
+    capture exists or the sources changed since it was taken."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    want = sources_sha256()
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith(".md"):
+            continue
+        for line in open(os.path.join(pdir, name)):
+            if not line.startswith("traffic:"):
+                continue
+            kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+            if kv.get("group") == group and kv.get("sources_sha256") == want:
+                return float(kv["bytes"]) * particles / float(kv["particles"])
+    return None
 
 
 def parse():
@@ -167,8 +206,16 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    case, desc = workload(args.workload, seed=0)
-    sample = oracle_sample(case)
+    if args.workload == "ensemble_c4":
+        m, re, we, dx, length = ensemble_members()[0]
+        case = ensemble_case(m, re, we, dx, length, args.skin)
+        desc = "member 0 of the 64-jet ensemble"
+    else:
+        case, desc = workload(args.workload, seed=0)
+    # the oracle runs ~0.75 M particle-steps/s on one core: size the sample so
+    # that the K steps take about a minute
+    budget = 4.5e7 / max(args.steps, 1)
+    sample = oracle_sample(case, int(min(24000, max(2000, budget))))
     run_oracle(sample, 0, max_steps=max(args.warmup, 0) or 1)
     psteps, nsteps, el, n = run_oracle(sample, 0, max_steps=args.steps)
     v = psteps / el
@@ -367,7 +414,8 @@ def main():
         achieved = flops / avg_s / 1e12
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": measured_traffic(dom, n_mean),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (median SM clock "
                                "sampled during the timed region)" % sm_mhz,
                 "algorithmic_per_launch": flops}
@@ -376,7 +424,8 @@ def main():
         nbytes = n_mean * BYTES_PER_PARTICLE.get(dom, 0)
         achieved = nbytes / avg_s / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": measured_traffic(dom, n_mean),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "algorithmic_per_launch": nbytes}
 
@@ -479,6 +528,11 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local):
         for sm in sims:
             sm.set_tuning(lanes, cadence)
     counts = [binding.sph_kernel_counts(sm.ctx) for sm in sims]
+    # interacting pairs per particle (the same h/dx in every member)
+    n_first = sims[0].time()["n"]
+    pa, _ = binding.sph_get_pairs(sims[0].ctx, int(n_first * 40))
+    pairs_pp = len(pa) / max(n_first, 1)
+    del pa
 
     def live():
         return sum(sm.time()["n"] for sm in sims)
@@ -556,7 +610,6 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local):
 
     # whole-step FP32 work against the FP32 peak (algorithmic FLOPs per
     # particle-step of the six pair sweeps and the per-particle work)
-    pairs_pp = 20.0
     flop_ps = 2 * (pairs_pp * (FLOP_PER_PAIR["colour"] + FLOP_PER_PAIR["normal"] +
                                FLOP_PER_PAIR["forces"]) +
                    FLOP_PER_PARTICLE["colour"] + FLOP_PER_PARTICLE["normal"] +
@@ -597,7 +650,8 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local):
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz,
-                         "algorithmic_per_particle_step": flop_ps},
+                         "algorithmic_per_particle_step": flop_ps,
+                         "pairs_per_particle": pairs_pp},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / Ke,
                     "d2h_bytes_per_step": d2h / Ke,

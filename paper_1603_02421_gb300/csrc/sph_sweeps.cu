@@ -524,6 +524,7 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
     V2<T> v1 = v0;
     T d1 = d0, c1 = c0;
     V2<T> ds = srt.disp[i];
+    T stx = T(0), sty = T(0);           // this step's displacement (rebuild decision)
     if (typ == T_DEAD) {
         // deleted since the last cell build: kept as is until it is dropped
     } else if (typ == T_FLUID) {
@@ -535,14 +536,16 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
         T s = d0 + y;
         c1 = (s - d0) - y;
         d1 = s;
-        ds = mk2(ds.x + tdt * (P.ufx + usx), ds.y + tdt * (P.ufy + usy));
+        stx = tdt * (P.ufx + usx);
+        sty = tdt * (P.ufy + usy);
     } else {
         double uh = inf.on ? inflow_u(inf, t + half) : P.ufx_d + (double)v0.x;
         p1 = make_double2(p0.x + dt * uh, p0.y);
         v1 = inf.on ? mk2((T)(inflow_u(inf, t + dt) - P.ufx_d), (T)(-P.ufy_d)) : v0;
         if (inf.on && p1.x >= inf.x_exit) typ = T_FLUID;
-        ds = mk2(ds.x + (T)(dt * uh), ds.y);
+        stx = (T)(dt * uh);
     }
+    ds = mk2(ds.x + stx, ds.y + sty);
     if (typ == T_FLUID &&
         !(p1.x >= g.xmin && p1.x < g.xmax && p1.y >= g.ymin && p1.y < g.ymax)) {
         typ = T_DEAD;
@@ -559,8 +562,7 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
     // largest displacements (squared, as float bits: monotone for >= 0)
     if (typ != T_DEAD) {
         float d2 = (float)(ds.x * ds.x + ds.y * ds.y);
-        float sx = (float)(p1.x - p0.x), sy = (float)(p1.y - p0.y);
-        float s2 = sx * sx + sy * sy;
+        float s2 = (float)(stx * stx + sty * sty);
         unsigned m = __activemask();
         unsigned a = __reduce_max_sync(m, __float_as_uint(d2));
         unsigned b2 = __reduce_max_sync(m, __float_as_uint(s2));

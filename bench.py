@@ -448,7 +448,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if case["params"].get("prec") == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": args.workload + ": " + desc,
                        "particles_mean": n_mean, "parallelism": "replicas (one jet per GPU)",

@@ -231,3 +231,34 @@ def test_params(kernel="wendland", dx=0.02, sigma=0.0, alpha=0.1, c0=10.0, g=0.0
                 eps_n_times_h=0.01, gx=0.0, gy=-g, courant=0.2, dt_fixed=dt_fixed,
                 xmin=box[0], ymin=box[1], xmax=box[2], ymax=box[3], skin_over_h=0.1,
                 wall_A_coef=0.01, wall_h0=0.0, wall_db_over_dx=0.5, capacity=0)
+
+
+# ---------------------------------------------------------------------------
+# Learned surrogate: shapes and seeded initial weights (random draws only;
+# the network's arithmetic lives in the CUDA library and, for tests, in the
+# oracle's reference).
+# ---------------------------------------------------------------------------
+MPNN_IN, MPNN_H, MPNN_P, MPNN_L, MPNN_OUT = 4, 128, 32, 3, 2
+
+
+def mpnn_shapes():
+    """Parameter tensors in their packed order: (name, shape)."""
+    shp = [("W_in", (MPNN_IN, MPNN_H)), ("b_in", (MPNN_H,))]
+    for l in range(MPNN_L):
+        shp += [("Pi%d" % l, (MPNN_H, MPNN_P)), ("U%d" % l, (MPNN_H + 4 * MPNN_P, MPNN_H)),
+                ("c%d" % l, (MPNN_H,))]
+    shp += [("D", (MPNN_H, MPNN_OUT)), ("d", (MPNN_OUT,))]
+    return shp
+
+
+def mpnn_init(seed=0, scale=1.0):
+    """Seeded initial weights: normal(0, scale/sqrt(fan_in)) matrices, zero
+    biases; returned as a dict of float64 arrays."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for name, shp in mpnn_shapes():
+        if len(shp) == 1:
+            out[name] = np.zeros(shp)
+        else:
+            out[name] = rng.normal(0.0, scale / math.sqrt(shp[0]), shp)
+    return out

@@ -309,6 +309,69 @@ void sph_ensemble_destroy(sph_ensemble *e);
  * failed sph_ensemble_create). */
 const char *sph_ensemble_last_error(const sph_ensemble *e);
 
+/* ------------------------------------------------------------------------
+ * Learned surrogate (no counterpart in the paper): a message-passing network
+ * on the SPH neighbour graph that predicts each particle's mean acceleration
+ * over the next k substeps.  Definition (all sums over ordered pairs a != b
+ * with r_ab < 2h of the context's last evaluation, Sec. 2-7):
+ *   node inputs  x_a = [100 (rho_a/rho0 - 1), N_a (Eq. 20), C_a (Eq. 14),
+ *                       h |n_a| (Eq. 18)]
+ *   edge weights V_b = m_b/rho_b, W and F = (1/r) dW/dr of Eqs. 27-28:
+ *                w0 = V_b W_ab, w1 = V_b F_ab (x_a - x_b) h,
+ *                w2 = V_b F_ab (y_a - y_b) h,
+ *                w3 = V_b F_ab ((u_a - u_b).(r_a - r_b)) h / u_ref
+ *   layers       h0 = relu(x W_in + b_in); for l = 0, 1, 2: z = h Pi_l
+ *                (128 -> 32), g_a[32k + j] = sum_b w_k,ab z_b[j],
+ *                h = h + relu([h, g] U_l + c_l) (256 -> 128); y = h D + d.
+ *   loss         L = (1/N) sum_a |y_a - t_a|^2.
+ * Parameters are packed float32 in the order W_in (4x128), b_in (128), then
+ * per layer Pi_l (128x32), U_l (256x128), c_l (128), then D (128x2), d (2);
+ * matrices row-major (fan-in x fan-out).  Every call works on a context that
+ * sph_evaluate left on its current state (SPH_ERR_STATE otherwise), FP32
+ * contexts only, on the context's stream; particles are in the context's
+ * cell order, reported with their ids.
+ * ------------------------------------------------------------------------ */
+typedef struct sph_mpnn sph_mpnn;
+
+/* Number of packed parameters. */
+long long sph_mpnn_param_count(void);
+
+/* A network for up to `capacity` particles on `device` (parameters zero;
+ * set them with sph_mpnn_set_params).  On error *out is NULL and
+ * sph_mpnn_last_error(NULL) describes it. */
+sph_status sph_mpnn_create(int device, long long capacity, sph_mpnn **out);
+void sph_mpnn_destroy(sph_mpnn *net);
+const char *sph_mpnn_last_error(const sph_mpnn *net);
+
+/* Host copies of the packed parameters / of the gradients of the last
+ * sph_mpnn_backward (n must equal sph_mpnn_param_count()).  Setting the
+ * parameters resets the optimiser state. */
+sph_status sph_mpnn_set_params(sph_mpnn *net, const float *host, long long n);
+sph_status sph_mpnn_get_params(sph_mpnn *net, float *host, long long n);
+sph_status sph_mpnn_get_grads(sph_mpnn *net, float *host, long long n);
+
+/* The network's inputs for inspection: *n particles (ids to id[], x to
+ * x[4n]) and *ne ordered pairs (cell-order indices ea, eb; weights w[4 ne]);
+ * SPH_ERR_CAPACITY if cap or ecap is too small (the counts are still set). */
+sph_status sph_mpnn_features(sph_mpnn *net, sph_ctx *ctx, double u_ref, long long cap,
+                             long long *n, unsigned *id, float *x, long long ecap,
+                             long long *ne, int *ea, int *eb, float *w);
+
+/* Forward pass: y[2n] for the *n particles (ids to id[]).  bf16 != 0 runs
+ * the dense layers on the tensor cores (BF16 operands, FP32 accumulation);
+ * otherwise everything is FP32. */
+sph_status sph_mpnn_forward(sph_mpnn *net, sph_ctx *ctx, double u_ref, int bf16, long long cap,
+                            long long *n, unsigned *id, float *y);
+
+/* FP32 forward and backward pass against host targets t[2n] (cell order, as
+ * reported by sph_mpnn_forward): the loss to *loss (nullable) and the
+ * gradients kept for sph_mpnn_get_grads / sph_mpnn_adam. */
+sph_status sph_mpnn_backward(sph_mpnn *net, sph_ctx *ctx, double u_ref, const float *target,
+                             long long n, double *loss);
+
+/* One Adam update (beta 0.9 / 0.999, eps 1e-8) from the last gradients. */
+sph_status sph_mpnn_adam(sph_mpnn *net, double lr);
+
 #ifdef __cplusplus
 }
 #endif

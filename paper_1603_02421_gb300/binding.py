@@ -58,6 +58,8 @@ _U8 = ctypes.POINTER(ctypes.c_ubyte)
 _U32 = ctypes.POINTER(ctypes.c_uint)
 _LL = ctypes.POINTER(ctypes.c_longlong)
 _CTX = ctypes.c_void_p
+_F32 = ctypes.POINTER(ctypes.c_float)
+_I32 = ctypes.POINTER(ctypes.c_int)
 
 _SIGS = {
     "sph_init": ([ctypes.POINTER(sph_params), ctypes.POINTER(_CTX)], ctypes.c_int),
@@ -90,6 +92,21 @@ _SIGS = {
                                ctypes.POINTER(ctypes.c_int), _D], ctypes.c_int),
     "sph_ensemble_destroy": ([ctypes.c_void_p], None),
     "sph_ensemble_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
+    "sph_mpnn_param_count": ([], ctypes.c_longlong),
+    "sph_mpnn_create": ([ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_void_p)],
+                        ctypes.c_int),
+    "sph_mpnn_destroy": ([ctypes.c_void_p], None),
+    "sph_mpnn_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
+    "sph_mpnn_set_params": ([ctypes.c_void_p, _F32, ctypes.c_longlong], ctypes.c_int),
+    "sph_mpnn_get_params": ([ctypes.c_void_p, _F32, ctypes.c_longlong], ctypes.c_int),
+    "sph_mpnn_get_grads": ([ctypes.c_void_p, _F32, ctypes.c_longlong], ctypes.c_int),
+    "sph_mpnn_features": ([ctypes.c_void_p, _CTX, ctypes.c_double, ctypes.c_longlong, _LL, _U32,
+                           _F32, ctypes.c_longlong, _LL, _I32, _I32, _F32], ctypes.c_int),
+    "sph_mpnn_forward": ([ctypes.c_void_p, _CTX, ctypes.c_double, ctypes.c_int,
+                          ctypes.c_longlong, _LL, _U32, _F32], ctypes.c_int),
+    "sph_mpnn_backward": ([ctypes.c_void_p, _CTX, ctypes.c_double, _F32, ctypes.c_longlong, _D],
+                          ctypes.c_int),
+    "sph_mpnn_adam": ([ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
     "sph_run_async": ([_CTX, ctypes.c_longlong], ctypes.c_int),
     "sph_set_tuning": ([_CTX, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sph_get_tuning": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -492,6 +509,135 @@ class Ensemble:
         if getattr(self, "ens", None):
             sph_ensemble_destroy(self.ens)
             self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# learned surrogate
+# ---------------------------------------------------------------------------
+def _mp_check(net, st):
+    if st != SPH_OK:
+        raise SphError(st, lib().sph_mpnn_last_error(net).decode(errors="replace"))
+
+
+def _f32p(a):
+    return a.ctypes.data_as(_F32)
+
+
+def sph_mpnn_param_count():
+    return int(lib().sph_mpnn_param_count())
+
+
+def sph_mpnn_last_error(net=None):
+    return lib().sph_mpnn_last_error(net).decode(errors="replace")
+
+
+def sph_mpnn_create(capacity, device=0):
+    out = ctypes.c_void_p()
+    _mp_check(None, lib().sph_mpnn_create(int(device), int(capacity), ctypes.byref(out)))
+    return out.value
+
+
+def sph_mpnn_destroy(net):
+    lib().sph_mpnn_destroy(net)
+
+
+def sph_mpnn_set_params(net, flat):
+    a = np.ascontiguousarray(flat, dtype=np.float32)
+    _mp_check(net, lib().sph_mpnn_set_params(net, _f32p(a), a.size))
+
+
+def sph_mpnn_get_params(net):
+    a = np.zeros(sph_mpnn_param_count(), np.float32)
+    _mp_check(net, lib().sph_mpnn_get_params(net, _f32p(a), a.size))
+    return a
+
+
+def sph_mpnn_get_grads(net):
+    a = np.zeros(sph_mpnn_param_count(), np.float32)
+    _mp_check(net, lib().sph_mpnn_get_grads(net, _f32p(a), a.size))
+    return a
+
+
+def sph_mpnn_features(net, ctx, u_ref, cap, ecap):
+    """(ids, x[n,4], ea, eb, w[ne,4]) in the context's cell order."""
+    n, ne = ctypes.c_longlong(), ctypes.c_longlong()
+    ids = np.zeros(cap, np.uint32)
+    x = np.zeros((cap, 4), np.float32)
+    ea = np.zeros(ecap, np.int32)
+    eb = np.zeros(ecap, np.int32)
+    w = np.zeros((ecap, 4), np.float32)
+    _mp_check(net, lib().sph_mpnn_features(net, ctx, float(u_ref), int(cap), ctypes.byref(n),
+                                           ids.ctypes.data_as(_U32), _f32p(x), int(ecap),
+                                           ctypes.byref(ne), ea.ctypes.data_as(_I32),
+                                           eb.ctypes.data_as(_I32), _f32p(w)))
+    k, m = n.value, ne.value
+    return ids[:k], x[:k], ea[:m], eb[:m], w[:m]
+
+
+def sph_mpnn_forward(net, ctx, u_ref, bf16, cap):
+    """(ids, y[n,2]) in the context's cell order."""
+    n = ctypes.c_longlong()
+    ids = np.zeros(cap, np.uint32)
+    y = np.zeros((cap, 2), np.float32)
+    _mp_check(net, lib().sph_mpnn_forward(net, ctx, float(u_ref), int(bool(bf16)), int(cap),
+                                          ctypes.byref(n), ids.ctypes.data_as(_U32), _f32p(y)))
+    return ids[:n.value], y[:n.value]
+
+
+def sph_mpnn_backward(net, ctx, u_ref, target):
+    t = np.ascontiguousarray(target, dtype=np.float32)
+    loss = ctypes.c_double()
+    _mp_check(net, lib().sph_mpnn_backward(net, ctx, float(u_ref), _f32p(t), len(t),
+                                           ctypes.byref(loss)))
+    return loss.value
+
+
+def sph_mpnn_adam(net, lr):
+    _mp_check(net, lib().sph_mpnn_adam(net, float(lr)))
+
+
+class Mpnn:
+    """The learned surrogate (sph_mpnn_*): parameters as a dict of float64
+    arrays in the shapes of workloads.mpnn_shapes()."""
+
+    def __init__(self, capacity, device=0):
+        self.net = None
+        self.net = sph_mpnn_create(capacity, device)
+
+    @staticmethod
+    def pack(prm):
+        from .workloads import mpnn_shapes
+        return np.concatenate([np.asarray(prm[k], np.float64).reshape(-1) for k, _ in mpnn_shapes()])
+
+    @staticmethod
+    def unpack(flat):
+        from .workloads import mpnn_shapes
+        out, o = {}, 0
+        for k, shp in mpnn_shapes():
+            size = int(np.prod(shp))
+            out[k] = np.asarray(flat[o:o + size], np.float64).reshape(shp)
+            o += size
+        return out
+
+    def set_params(self, prm):
+        sph_mpnn_set_params(self.net, self.pack(prm))
+
+    def params(self):
+        return self.unpack(sph_mpnn_get_params(self.net))
+
+    def grads(self):
+        return self.unpack(sph_mpnn_get_grads(self.net))
+
+    def close(self):
+        if getattr(self, "net", None):
+            sph_mpnn_destroy(self.net)
+            self.net = None
 
     def __del__(self):
         try:

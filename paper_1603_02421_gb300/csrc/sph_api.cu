@@ -1360,6 +1360,27 @@ sph_status sph_kernel_counts(sph_ctx *c, int *per_full_step, int *per_reused_ste
     return SPH_OK;
 }
 
+}  // extern "C"
+
+void ctx_view(sph_ctx *c, CtxView *v) {
+    *v = CtxView{};
+    v->n = c->hsc->nsrt;
+    v->cap = c->cap;
+    v->fp32 = c->tsz == 4;
+    v->evaluated = c->csf_valid;
+    v->device = c->prm.device;
+    v->stream = c->stream;
+    if (!v->fp32) return;
+    v->P = c->Pf;
+    v->hot = hot_n<float>(c);
+    v->csf = csf_of<float>(c);
+    v->nl = c->nl;
+    v->id = (const uint32_t *)c->srt[6];
+    v->type = (const uint8_t *)c->srt[5];
+}
+
+extern "C" {
+
 // ---------------------------------------------------------------------------
 // Ensembles
 // ---------------------------------------------------------------------------

@@ -255,4 +255,26 @@ void launch_decide(cudaGraphConditionalHandle h, const Scalars *sc, cudaStream_t
 // Host stub of the kernel launch_decide runs (for explicit graph nodes).
 void *decide_kernel();
 
+// Read-only view of a context's last evaluation (for the learned surrogate):
+// records, CSF fields and neighbour lists of the current state in cell
+// order.  `evaluated` is false unless sph_evaluate ran on the current state.
+struct CtxView {
+    int n;                   // particles in cell order
+    int cap;
+    bool fp32;
+    bool evaluated;
+    int device;
+    cudaStream_t stream;
+    PhysT<float> P;
+    Hot<float> hot;
+    Csf<float> csf;
+    NList nl;
+    const uint32_t *id;      // particle ids in cell order
+    const uint8_t *type;
+};
+
 }  // namespace sph
+
+// Fills a view of context c (sph_api.cu).
+struct sph_ctx;
+void ctx_view(struct sph_ctx *c, sph::CtxView *v);

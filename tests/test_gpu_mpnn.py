@@ -1,0 +1,166 @@
+"""Learned surrogate on the GPU (sph_mpnn_*) against the FP64 reference
+(oracle/mpnn.py).
+
+* inputs: the node inputs and edge weights the CUDA path builds from a
+  context's evaluation equal the reference's, built from the oracle's own
+  evaluation of the same state (FP32 against FP64);
+* forward: on the GPU's own inputs, the FP32 network equals the FP64
+  reference to rel-L2 1e-5; the BF16 tensor-core path (8-bit mantissa
+  operands, FP32 accumulation, about seven roundings deep) to 2e-2;
+* backward: loss and every parameter gradient of the FP32 pass equal the
+  FP64 reference's to rel-L2 1e-4;
+* training: Adam on the GPU lowers the loss on a fixed state.
+"""
+import numpy as np
+import pytest
+
+from paper_1603_02421_gb300 import workloads as wl
+from tests.helpers import ambiguous_mask, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sph():
+    from paper_1603_02421_gb300 import binding, build
+    build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return binding
+
+
+@pytest.fixture(scope="module")
+def mp():
+    from oracle import mpnn
+    return mpnn
+
+
+def _drop(seed=2):
+    st = wl.disc(R=0.4, dx=0.02)
+    rng = np.random.default_rng(seed)
+    st["u"] = rng.normal(0, 0.05, len(st["x"]))
+    st["v"] = rng.normal(0, 0.05, len(st["x"]))
+    st["rho"] = st["rho"] * (1 + rng.uniform(-0.002, 0.002, len(st["x"])))
+    p = wl.test_params(dx=0.02, sigma=0.05)
+    p["capacity"] = len(st["x"]) + 64
+    return p, st
+
+
+@pytest.fixture(scope="module")
+def evaluated(sph):
+    p, st = _drop()
+    sim = sph.Simulation({"params": p, "fluid": st, "boundary": None, "inflow": None})
+    sim.evaluate()
+    net = sph.Mpnn(capacity=len(st["x"]) + 64)
+    yield p, st, sim, net
+    net.close()
+    sim.close()
+
+
+def _params(seed):
+    prm = wl.mpnn_init(seed)
+    rng = np.random.default_rng(seed + 50)
+    for k, v in prm.items():
+        if v.ndim == 1:
+            prm[k] = rng.normal(0.0, 0.05, v.shape)
+    return prm
+
+
+def _as_f32(prm):
+    return {k: np.asarray(v, np.float32).astype(np.float64) for k, v in prm.items()}
+
+
+def _gpu_inputs(sph, net, sim, n):
+    ids, x, ea, eb, w = sph.sph_mpnn_features(net.net, sim.ctx, 1.0, n + 64, 64 * n)
+    return ids, x.astype(np.float64), ea.astype(np.int64), eb.astype(np.int64), w.astype(np.float64)
+
+
+def test_inputs_match_oracle(sph, mp, orc, evaluated):
+    p, st, sim, net = evaluated
+    n = len(st["x"])
+    ids, x, ea, eb, w = _gpu_inputs(sph, net, sim, n)
+    d = orc.derive(p)
+    ev = orc.evaluate(d, st)
+    xo, ao, bo, wo = mp.features(d, st, ev, 1.0)
+    # the same ordered pairs
+    ga, gb = ids[ea].astype(np.int64), ids[eb].astype(np.int64)
+    key_g = ga * n + gb
+    key_o = ao * n + bo
+    og, oo = np.argsort(key_g), np.argsort(key_o)
+    assert np.array_equal(key_g[og], key_o[oo])
+    wg = w[og]
+    wr = wo[oo]
+    for c in range(4):
+        assert rel_l2(wg[:, c], wr[:, c]) < 1e-5, c
+    xg = np.zeros_like(x)
+    xg[ids] = x
+    keep = ~ambiguous_mask(orc, d, st, ev)
+    assert rel_l2(xg[:, 0], xo[:, 0]) < 1e-4            # FP32 rho near rho0
+    assert np.array_equal(xg[keep, 1], xo[keep, 1])     # Eq. 20 flags
+    assert rel_l2(xg[:, 2], xo[:, 2]) < 1e-6
+    assert rel_l2(xg[keep, 3], xo[keep, 3]) < 1e-5
+
+
+@pytest.mark.parametrize("bf16,tol", [(False, 1e-5), (True, 2e-2)])
+def test_forward_matches_reference(sph, mp, evaluated, bf16, tol):
+    p, st, sim, net = evaluated
+    n = len(st["x"])
+    prm = _as_f32(_params(3))
+    net.set_params(prm)
+    ids, x, ea, eb, w = _gpu_inputs(sph, net, sim, n)
+    ids2, y = sph.sph_mpnn_forward(net.net, sim.ctx, 1.0, bf16, n + 64)
+    assert np.array_equal(ids, ids2)
+    yr, _ = mp.forward(prm, x, ea, eb, w)
+    assert np.abs(yr).max() > 0
+    assert rel_l2(y[:, 0], yr[:, 0]) < tol and rel_l2(y[:, 1], yr[:, 1]) < tol
+
+
+def test_gradients_match_reference(sph, mp, evaluated):
+    p, st, sim, net = evaluated
+    n = len(st["x"])
+    prm = _as_f32(_params(4))
+    net.set_params(prm)
+    ids, x, ea, eb, w = _gpu_inputs(sph, net, sim, n)
+    t = np.random.default_rng(6).normal(0.0, 1.0, (n, 2)).astype(np.float32)
+    loss = sph.sph_mpnn_backward(net.net, sim.ctx, 1.0, t)
+    g = net.grads()
+    yr, cache = mp.forward(prm, x, ea, eb, w)
+    lr_, dy = mp.loss(yr, t.astype(np.float64))
+    gr = mp.backward(prm, cache, dy, ea, eb, w)
+    assert abs(loss - lr_) <= 1e-5 * lr_
+    for k in gr:
+        assert rel_l2(g[k], gr[k]) < 1e-4, k
+
+
+def test_training_lowers_the_loss(sph, evaluated):
+    p, st, sim, net = evaluated
+    n = len(st["x"])
+    net.set_params(_params(7))
+    s = sim.state()
+    ids, _ = sph.sph_mpnn_forward(net.net, sim.ctx, 1.0, False, n + 64)
+    a = np.stack([s["ax"], s["ay"]], 1)
+    a_ref = a.std()
+    order = np.argsort(s["id"])
+    t = (a[order][ids] / a_ref).astype(np.float32)       # targets in cell order
+    losses = []
+    for _ in range(150):
+        losses.append(sph.sph_mpnn_backward(net.net, sim.ctx, 1.0, t))
+        sph.sph_mpnn_adam(net.net, 2e-3)
+    assert losses[-1] < 0.3 * losses[0]
+
+
+def test_needs_an_evaluated_state(sph):
+    p, st = _drop(5)
+    sim = sph.Simulation({"params": p, "fluid": st, "boundary": None, "inflow": None})
+    net = sph.Mpnn(capacity=len(st["x"]) + 64)
+    with pytest.raises(sph.SphError) as ei:
+        sph.sph_mpnn_forward(net.net, sim.ctx, 1.0, False, len(st["x"]) + 64)
+    assert ei.value.status == sph.SPH_ERR_STATE
+    sim.evaluate()
+    sph.sph_mpnn_forward(net.net, sim.ctx, 1.0, False, len(st["x"]) + 64)
+    sim.step()
+    with pytest.raises(sph.SphError):
+        sph.sph_mpnn_forward(net.net, sim.ctx, 1.0, False, len(st["x"]) + 64)
+    net.close()
+    sim.close()

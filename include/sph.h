@@ -372,6 +372,25 @@ sph_status sph_mpnn_backward(sph_mpnn *net, sph_ctx *ctx, double u_ref, const fl
 /* One Adam update (beta 0.9 / 0.999, eps 1e-8) from the last gradients. */
 sph_status sph_mpnn_adam(sph_mpnn *net, double lr);
 
+/* One surrogate step of length dT = k dt (dt: the last plain step's, or
+ * dt_fixed), with plain SPH as judge and fallback:
+ *   1. evaluate SPH at the current state (a_n, drho/dt_n);
+ *   2. predict abar = a_ref * y with the network (bf16 != 0: tensor cores);
+ *   3. fluid: u' = u + dT abar, r' = r + dT (u + u')/2, rho' = rho + dT
+ *      drho/dt_n; inflow buffer, buffer -> fluid and outflow as in a plain
+ *      step; inflow layers and time advance for dT;
+ *   4. evaluate SPH at the new state (same cell order and lists) and form the
+ *      residuals r_m = |abar - (a_n + a_k)/2| / |(a_n + a_k)/2| (L2 over the
+ *      fluid) and r_rho = (dT/2) rms(drho/dt_k - drho/dt_n) / rho0;
+ *   5. accept when both are <= threshold; otherwise restore the state and
+ *      run k plain steps instead (also when a particle moved more than
+ *      skin/2, so the lists of the start no longer hold).
+ * *accepted (nullable) says which; the residuals go to res_momentum and
+ * res_density (nullable).  FP32 contexts only. */
+sph_status sph_surrogate_step(sph_ctx *ctx, sph_mpnn *net, int k, double u_ref, double a_ref,
+                              double threshold, int bf16, int *accepted, double *res_momentum,
+                              double *res_density);
+
 #ifdef __cplusplus
 }
 #endif

@@ -107,6 +107,9 @@ _SIGS = {
     "sph_mpnn_backward": ([ctypes.c_void_p, _CTX, ctypes.c_double, _F32, ctypes.c_longlong, _D],
                           ctypes.c_int),
     "sph_mpnn_adam": ([ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
+    "sph_surrogate_step": ([_CTX, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                            ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D],
+                           ctypes.c_int),
     "sph_run_async": ([_CTX, ctypes.c_longlong], ctypes.c_int),
     "sph_set_tuning": ([_CTX, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sph_get_tuning": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -600,6 +603,17 @@ def sph_mpnn_backward(net, ctx, u_ref, target):
 
 def sph_mpnn_adam(net, lr):
     _mp_check(net, lib().sph_mpnn_adam(net, float(lr)))
+
+
+def sph_surrogate_step(ctx, net, k, u_ref, a_ref, threshold, bf16=True):
+    """One surrogate step with plain SPH as judge and fallback; returns
+    (accepted, momentum residual, density residual)."""
+    acc = ctypes.c_int()
+    rm, rd = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().sph_surrogate_step(ctx, net, int(k), float(u_ref), float(a_ref),
+                                         float(threshold), int(bool(bf16)), ctypes.byref(acc),
+                                         ctypes.byref(rm), ctypes.byref(rd)))
+    return bool(acc.value), rm.value, rd.value
 
 
 class Mpnn:

@@ -72,6 +72,9 @@ struct sph_ctx {
     cudaGraphExec_t gexec[2] = {};
     bool graph_dirty = true;
     unsigned long long graph_gen = 0;   // counts changes that invalidate captured steps
+    // learned-surrogate step scratch: SPH accelerations and density rates at
+    // the step start, residual sums, saved particle count
+    void *sg_an = nullptr, *sg_drn = nullptr, *sg_sums = nullptr, *sg_n = nullptr;
 
     // tuning: lanes per particle in the pair sweeps, longest cell-build cadence
     int lanes = 4, cadence = 1;
@@ -1380,6 +1383,112 @@ void ctx_view(sph_ctx *c, CtxView *v) {
 }
 
 extern "C" {
+
+// ---------------------------------------------------------------------------
+// Learned-surrogate step
+// ---------------------------------------------------------------------------
+sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, double a_ref,
+                              double threshold, int bf16, int *accepted, double *res_momentum,
+                              double *res_density) {
+    if (!c) return SPH_ERR_ARG;
+    if (accepted) *accepted = 0;
+    if (!net) return fail(c, SPH_ERR_ARG, "network is NULL");
+    if (c->tsz != 4) return fail(c, SPH_ERR_ARG, "the surrogate step needs an FP32 context");
+    if (k < 1 || k > 64) return fail(c, SPH_ERR_ARG, "k must lie in [1, 64]");
+    if (!(u_ref > 0) || !(a_ref > 0) || !(threshold > 0))
+        return fail(c, SPH_ERR_ARG, "u_ref, a_ref and threshold must be > 0");
+    sph_status s = pull_scalars(c);
+    if (s) return s;
+    s = status_from_err(c, c->hsc->err);
+    if (s) return s;
+    if (!c->sg_an) {
+        cudaError_t e = cudaSuccess;
+        c->sg_an = dalloc(c, (size_t)c->cap * sizeof(float2), e);
+        if (!e) c->sg_drn = dalloc(c, (size_t)c->cap * sizeof(float), e);
+        if (!e) c->sg_sums = dalloc(c, 4 * sizeof(double), e);
+        if (!e) c->sg_n = dalloc(c, sizeof(int), e);
+        CK(e, "surrogate scratch");
+    }
+    s = snapshot(c, false);
+    if (s) return s;
+    auto reject = [&](double rm, double rd) -> sph_status {
+        sph_status r = snapshot(c, true);
+        if (r) return r;
+        r = sph_run_async(c, k);
+        if (!r) r = sph_sync(c);
+        if (res_momentum) *res_momentum = rm;
+        if (res_density) *res_density = rd;
+        return r;
+    };
+    // SPH at the step start, with the time-step candidates of Eqs. 30-31
+    State<float> raw = state_of<float>(c->raw), srt = state_of<float>(c->srt);
+    {
+        const uint32_t *key = enqueue_sort<float>(c);
+        enqueue_build<float>(c, key);
+        enqueue_normal<float>(c, hot_n<float>(c));
+        launch_forces<float>(c->lanes, 1, c->Pf, c->grid, c->inf, c->sc, c->nl, key,
+                             hot_n<float>(c), csf_of<float>(c), bd_of(c), srt, raw,
+                             (float2 *)c->acc, (float *)c->dr, c->cap, c->stream);
+    }
+    s = after_work(c, "surrogate: evaluation at the start");
+    if (s) return s;
+    c->n_eval = c->hsc->nsrt;
+    c->csf_valid = true;
+    const int n = c->hsc->nsrt;
+    // Eq. 32: the plain step's dt at this state; the surrogate step spans k
+    double dt = c->prm.dt_fixed;
+    if (!(dt > 0)) {
+        float m = 3.0e38f;
+        for (int q = 0; q < RED_SLOTS; ++q) {
+            float v;
+            std::memcpy(&v, &c->hsc->dtmin_f[q], sizeof v);
+            m = std::min(m, v);
+        }
+        if (!(m < 1.0e37f)) {
+            snapshot(c, true);
+            return fail(c, SPH_ERR_STATE, "adaptive time step without fluid particles");
+        }
+        dt = c->prm.courant * (double)m;
+    }
+    const double dT = k * dt;
+    CK(cudaMemcpyAsync(c->sg_an, c->acc, (size_t)n * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(c->sg_drn, c->dr, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    // prediction and update
+    const float2 *abar = nullptr;
+    s = mpnn_predict(net, c, u_ref, bf16 != 0, &abar);
+    if (s) return fail(c, s, "surrogate: %s", sph_mpnn_last_error(net));
+    launch_surrogate_update(c->Pf, c->inf, c->grid, c->sc, srt, raw, abar, (float)a_ref,
+                            (const float *)c->sg_drn, dT, c->cap, c->stream);
+    launch_spawn<float>(c->Pf, c->inf, c->sc, raw, c->layer_y, c->cap, 1, c->stream);
+    CK(cudaMemcpyAsync(c->sg_n, &c->sc->n, sizeof(int), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    // SPH at the end, on the cell order and lists of the start (exact while
+    // no particle moved more than skin/2, which the refresh checks)
+    enqueue_cells<float>(c, false);
+    enqueue_normal<float>(c, hot_n<float>(c));
+    launch_forces<float>(c->lanes, 0, c->Pf, c->grid, c->inf, c->sc, c->nl, c->cs.key,
+                         hot_n<float>(c), csf_of<float>(c), bd_of(c), srt, raw,
+                         (float2 *)c->acc, (float *)c->dr, c->cap, c->stream);
+    CK(cudaMemcpyAsync(&c->sc->n, c->sg_n, sizeof(int), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemsetAsync(c->sg_sums, 0, 4 * sizeof(double), c->stream), "clear");
+    launch_surrogate_residual(n, srt.type, abar, (float)a_ref, (const float2 *)c->sg_an,
+                              (const float2 *)c->acc, (const float *)c->sg_drn,
+                              (const float *)c->dr, (double *)c->sg_sums, c->cap, c->stream);
+    double sums[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(sums, c->sg_sums, sizeof sums, cudaMemcpyDeviceToHost, c->stream), "residual");
+    s = after_work(c, "surrogate: evaluation at the end");
+    double rm = sums[1] > 0 ? std::sqrt(sums[0] / sums[1]) : 0.0;
+    double rd = sums[3] > 0 ? 0.5 * dT * std::sqrt(sums[2] / sums[3]) / c->prm.rho0 : 0.0;
+    if (s == SPH_ERR_SKIN) return reject(rm, rd);   // moved too far for the lists: plain steps
+    if (s) return s;
+    if (!(rm <= threshold && rd <= threshold)) return reject(rm, rd);
+    c->force_full = true;
+    c->csf_valid = false;
+    c->n_eval = 0;
+    if (accepted) *accepted = 1;
+    if (res_momentum) *res_momentum = rm;
+    if (res_density) *res_density = rd;
+    return SPH_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Ensembles

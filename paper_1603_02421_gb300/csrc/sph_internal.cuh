@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sph.h"
+
 namespace sph {
 
 constexpr uint8_t T_FLUID = 0, T_BOUNDARY = 1, T_BUFFER = 2, T_DEAD = 0xFF;
@@ -252,6 +254,14 @@ void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State
                   const double *layer_y, int cap, int cadence, cudaStream_t s);
 // Sets the step graph's rebuild condition from sc->need_full.
 void launch_decide(cudaGraphConditionalHandle h, const Scalars *sc, cudaStream_t s);
+// Learned-surrogate step (FP32 contexts): state update with a predicted mean
+// acceleration, and the residual sums against the SPH evaluations at both ends.
+void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Grid &g, Scalars *sc,
+                             const State<float> &srt, const State<float> &raw, const float2 *abar,
+                             float a_ref, const float *dr, double dT, int cap, cudaStream_t s);
+void launch_surrogate_residual(int n, const uint8_t *type, const float2 *abar, float a_ref,
+                               const float2 *a_n, const float2 *a_k, const float *dr_n,
+                               const float *dr_k, double *sums, int cap, cudaStream_t s);
 // Host stub of the kernel launch_decide runs (for explicit graph nodes).
 void *decide_kernel();
 
@@ -277,4 +287,10 @@ struct CtxView {
 
 // Fills a view of context c (sph_api.cu).
 struct sph_ctx;
+struct sph_mpnn;
 void ctx_view(struct sph_ctx *c, sph::CtxView *v);
+
+// Surrogate forward pass on an evaluated context (sph_mpnn.cu): *y receives
+// the device array of the n predictions (float2, cell order).
+sph_status mpnn_predict(struct sph_mpnn *net, struct sph_ctx *c, double u_ref, bool bf16,
+                        const float2 **y);

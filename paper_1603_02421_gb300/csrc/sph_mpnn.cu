@@ -716,6 +716,16 @@ sph_status mp_backward(sph_mpnn *net, const CtxView &v, float inv_uref) {
 
 }  // namespace
 
+sph_status mpnn_predict(sph_mpnn *net, sph_ctx *c, double u_ref, bool bf16, const float2 **y) {
+    if (!net || !y || !(u_ref > 0)) return net ? mp_fail(net, SPH_ERR_ARG, "bad arguments") : SPH_ERR_ARG;
+    CtxView v;
+    sph_status s = mp_view(net, c, v);
+    if (s) return s;
+    s = mp_forward(net, v, (float)(1.0 / u_ref), bf16);
+    *y = reinterpret_cast<const float2 *>(net->y);
+    return s;
+}
+
 extern "C" {
 
 long long sph_mpnn_param_count(void) { return kMP.total; }

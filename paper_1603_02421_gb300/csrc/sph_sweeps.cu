@@ -823,6 +823,104 @@ void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State
              layer_y, cap, cadence);
 }
 
+// ---------------------------------------------------------------------------
+// Surrogate step (learned surrogate): one step of length dT = k dt with a
+// predicted mean acceleration abar (cell order, in units of a_ref) in place
+// of the SPH accelerations.  Fluid: u' = u + dT abar, r' = r + dT (u + u')/2,
+// rho' = rho + dT (drho/dt)_n (the SPH continuity rate of the evaluation at
+// n); inflow buffer, buffer -> fluid conversion and outflow as in the
+// corrector.  Writes raw in the cell order of the evaluation and sets the
+// step length for the time advance that follows.
+// ---------------------------------------------------------------------------
+__global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *__restrict__ sc,
+                                   State<float> srt, State<float> raw,
+                                   const float2 *__restrict__ abar, float a_ref,
+                                   const float *__restrict__ dr, double dT) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) sc->dt = dT;
+    if (i >= sc->nsrt) return;
+    double t = sc->t, half = 0.5 * dT;
+    double2 p0 = srt.pos[i];
+    float2 v0 = srt.vel[i];
+    float d0 = srt.drho[i], c0 = srt.drc[i];
+    uint8_t typ = srt.type[i];
+    double2 p1 = p0;
+    float2 v1 = v0;
+    float d1 = d0, c1 = c0;
+    float2 ds = srt.disp[i];
+    if (typ == T_FLUID) {
+        float tdt = (float)dT;
+        float ax = a_ref * abar[i].x, ay = a_ref * abar[i].y;
+        float uhx = v0.x + 0.5f * tdt * ax, uhy = v0.y + 0.5f * tdt * ay;
+        p1 = make_double2(p0.x + dT * (P.ufx_d + (double)uhx), p0.y + dT * (P.ufy_d + (double)uhy));
+        v1 = make_float2(v0.x + tdt * ax, v0.y + tdt * ay);
+        float y = tdt * dr[i] - c0;     // compensated density update
+        float s = d0 + y;
+        c1 = (s - d0) - y;
+        d1 = s;
+        ds = make_float2(ds.x + tdt * (P.ufx + uhx), ds.y + tdt * (P.ufy + uhy));
+    } else if (typ == T_BUFFER) {
+        double uh = inf.on ? inflow_u(inf, t + half) : P.ufx_d + (double)v0.x;
+        p1 = make_double2(p0.x + dT * uh, p0.y);
+        v1 = inf.on ? make_float2((float)(inflow_u(inf, t + dT) - P.ufx_d), (float)(-P.ufy_d)) : v0;
+        if (inf.on && p1.x >= inf.x_exit) typ = T_FLUID;
+        ds = make_float2(ds.x + (float)(dT * uh), ds.y);
+    }
+    if (typ == T_FLUID &&
+        !(p1.x >= g.xmin && p1.x < g.xmax && p1.y >= g.ymin && p1.y < g.ymax)) {
+        typ = T_DEAD;
+        atomicAdd((unsigned long long *)&sc->deleted, 1ull);
+    }
+    raw.pos[i] = p1;
+    raw.vel[i] = v1;
+    raw.drho[i] = d1;
+    raw.drc[i] = c1;
+    raw.mass[i] = srt.mass[i];
+    raw.type[i] = typ;
+    raw.id[i] = srt.id[i];
+    raw.disp[i] = ds;
+}
+
+void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Grid &g, Scalars *sc,
+                             const State<float> &srt, const State<float> &raw, const float2 *abar,
+                             float a_ref, const float *dr, double dT, int cap, cudaStream_t s) {
+    launch_k(k_surrogate_update, (cap + 255) / 256, 256, s, P, inf, g, sc, srt, raw, abar, a_ref, dr,
+             dT);
+}
+
+// Residuals of a surrogate step over the fluid particles (cell order): sums of
+// |a_ref abar - (a_n + a_k)/2|^2, |(a_n + a_k)/2|^2 and (drho_k - drho_n)^2,
+// and the fluid count, accumulated in FP64.
+__global__ void k_surrogate_residual(int n, const uint8_t *__restrict__ type,
+                                     const float2 *__restrict__ abar, float a_ref,
+                                     const float2 *__restrict__ a_n, const float2 *__restrict__ a_k,
+                                     const float *__restrict__ dr_n, const float *__restrict__ dr_k,
+                                     double *__restrict__ sums) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < n && type[i] == T_FLUID) {
+        double mx = 0.5 * ((double)a_n[i].x + a_k[i].x), my = 0.5 * ((double)a_n[i].y + a_k[i].y);
+        double ex = (double)a_ref * abar[i].x - mx, ey = (double)a_ref * abar[i].y - my;
+        double dd = (double)dr_k[i] - dr_n[i];
+        v[0] = ex * ex + ey * ey;
+        v[1] = mx * mx + my * my;
+        v[2] = dd * dd;
+        v[3] = 1.0;
+    }
+    for (int k = 0; k < 4; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&sums[k], x);
+    }
+}
+
+void launch_surrogate_residual(int n, const uint8_t *type, const float2 *abar, float a_ref,
+                               const float2 *a_n, const float2 *a_k, const float *dr_n,
+                               const float *dr_k, double *sums, int cap, cudaStream_t s) {
+    launch_k(k_surrogate_residual, (cap + 255) / 256, 256, s, n, type, abar, a_ref, a_n, a_k, dr_n,
+             dr_k, sums);
+}
+
 __global__ void k_decide(cudaGraphConditionalHandle h, const Scalars *__restrict__ sc) {
     cudaGraphSetConditional(h, sc->need_full ? 1u : 0u);
 }

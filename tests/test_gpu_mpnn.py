@@ -164,3 +164,88 @@ def test_needs_an_evaluated_state(sph):
         sph.sph_mpnn_forward(net.net, sim.ctx, 1.0, False, len(st["x"]) + 64)
     net.close()
     sim.close()
+
+
+# ---------------------------------------------------------------------------
+# surrogate step (plain SPH as judge and fallback)
+# ---------------------------------------------------------------------------
+def _patch_case(seed):
+    st = wl.jittered_patch(seed=seed, nx=40, ny=30, dx=0.02, vel=0.05, drho=0.002)
+    p = wl.test_params(dx=0.02, sigma=0.05, box=(-0.5, -0.5, 1.3, 1.1))
+    p["capacity"] = len(st["x"]) + 64
+    p["skin_over_h"] = 0.3
+    return {"params": p, "fluid": st, "boundary": None, "inflow": None}
+
+
+def test_accepted_surrogate_step_applies_the_prediction(sph):
+    case = _patch_case(3)
+    sim = sph.Simulation(case)
+    dt = sim.step()
+    n = len(case["fluid"]["x"])
+    net = sph.Mpnn(capacity=n + 64)
+    net.set_params(_params(8))
+    sim.evaluate()
+    before = sim.state()
+    t0 = sim.time()["t"]
+    ids, y = sph.sph_mpnn_forward(net.net, sim.ctx, 1.0, True, n + 64)
+    a_ref, k = 0.5, 4
+    acc, rm, rd = sph.sph_surrogate_step(sim.ctx, net.net, k, 1.0, a_ref, 1e30, True)
+    assert acc and rm > 0
+    after = sim.state()
+    dT = sim.time()["t"] - t0           # k times the Eq. 32 step at this state
+    assert abs(dT - k * dt) < 0.05 * k * dt
+    yb = np.zeros_like(y, dtype=np.float64)
+    yb[ids] = y
+    ax, ay = a_ref * yb[:, 0], a_ref * yb[:, 1]
+    u1 = before["u"] + dT * ax
+    v1 = before["v"] + dT * ay
+    x1 = before["x"] + dT * (before["u"] + 0.5 * dT * ax)
+    y1 = before["y"] + dT * (before["v"] + 0.5 * dT * ay)
+    rho1 = before["rho"] + dT * before["drho"]
+    assert np.array_equal(after["id"], before["id"])
+    assert np.allclose(after["x"], x1, rtol=0, atol=1e-9)
+    assert np.allclose(after["y"], y1, rtol=0, atol=1e-9)
+    assert rel_l2(after["u"], u1) < 1e-6 and rel_l2(after["v"], v1) < 1e-6
+    assert np.allclose(after["rho"], rho1, rtol=1e-6, atol=0)
+    net.close()
+    sim.close()
+
+
+def test_rejected_surrogate_step_equals_plain_steps(sph):
+    case = _patch_case(4)
+    a = sph.Simulation(case)
+    b = sph.Simulation(case)
+    a.step()
+    b.step()
+    n = len(case["fluid"]["x"])
+    net = sph.Mpnn(capacity=n + 64)
+    net.set_params(_params(9))
+    acc, rm, rd = sph.sph_surrogate_step(a.ctx, net.net, 3, 1.0, 1.0, 1e-30, True)
+    assert not acc
+    b.run(3)
+    assert a.time() == b.time()
+    sa, sb = a.state(), b.state()
+    for key in ("x", "y", "u", "v", "rho", "id"):
+        assert np.array_equal(sa[key], sb[key]), key
+    net.close()
+    a.close()
+    b.close()
+
+
+def test_surrogate_steps_on_a_jet(sph):
+    case = wl.jet(seed=2, dx=1.0 / 20, length=6.0, Re=200, We=20)
+    case["params"]["skin_over_h"] = 0.3
+    sim = sph.Simulation(case)
+    sim.run(2)
+    net = sph.Mpnn(capacity=case["params"]["capacity"])
+    net.set_params(_params(10))
+    t0 = sim.time()["t"]
+    for _ in range(6):
+        acc, rm, rd = sph.sph_surrogate_step(sim.ctx, net.net, 4, 1.0, 0.1, 1e30, True)
+        assert acc
+    assert sim.time()["t"] > t0
+    sim.run(3)                      # plain steps continue from the surrogate's state
+    s = sim.state()
+    assert np.all(np.isfinite(s["x"])) and len(np.unique(s["id"])) == len(s["id"])
+    net.close()
+    sim.close()

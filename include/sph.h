@@ -375,7 +375,8 @@ sph_status sph_mpnn_adam(sph_mpnn *net, double lr);
 /* One surrogate step of length dT = k dt (dt: the last plain step's, or
  * dt_fixed), with plain SPH as judge and fallback:
  *   1. evaluate SPH at the current state (a_n, drho/dt_n);
- *   2. predict abar = a_ref * y with the network (bf16 != 0: tensor cores);
+ *   2. predict the mean acceleration over the k substeps as abar = a_n +
+ *      a_ref * y, y the network's output (bf16 != 0: tensor cores);
  *   3. fluid: u' = u + dT abar, r' = r + dT (u + u')/2, rho' = rho + dT
  *      drho/dt_n; inflow buffer, buffer -> fluid and outflow as in a plain
  *      step; inflow layers and time advance for dT;

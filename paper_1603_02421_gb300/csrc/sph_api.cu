@@ -1457,8 +1457,8 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
     const float2 *abar = nullptr;
     s = mpnn_predict(net, c, u_ref, bf16 != 0, &abar);
     if (s) return fail(c, s, "surrogate: %s", sph_mpnn_last_error(net));
-    launch_surrogate_update(c->Pf, c->inf, c->grid, c->sc, srt, raw, abar, (float)a_ref,
-                            (const float *)c->sg_drn, dT, c->cap, c->stream);
+    launch_surrogate_update(c->Pf, c->inf, c->grid, c->sc, srt, raw, (const float2 *)c->sg_an,
+                            abar, (float)a_ref, (const float *)c->sg_drn, dT, c->cap, c->stream);
     launch_spawn<float>(c->Pf, c->inf, c->sc, raw, c->layer_y, c->cap, 1, c->stream);
     CK(cudaMemcpyAsync(c->sg_n, &c->sc->n, sizeof(int), cudaMemcpyDeviceToDevice, c->stream), "copy");
     // SPH at the end, on the cell order and lists of the start (exact while

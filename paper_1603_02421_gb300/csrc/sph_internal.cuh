@@ -257,9 +257,10 @@ void launch_decide(cudaGraphConditionalHandle h, const Scalars *sc, cudaStream_t
 // Learned-surrogate step (FP32 contexts): state update with a predicted mean
 // acceleration, and the residual sums against the SPH evaluations at both ends.
 void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Grid &g, Scalars *sc,
-                             const State<float> &srt, const State<float> &raw, const float2 *abar,
-                             float a_ref, const float *dr, double dT, int cap, cudaStream_t s);
-void launch_surrogate_residual(int n, const uint8_t *type, const float2 *abar, float a_ref,
+                             const State<float> &srt, const State<float> &raw, const float2 *a_n,
+                             const float2 *y, float a_ref, const float *dr, double dT, int cap,
+                             cudaStream_t s);
+void launch_surrogate_residual(int n, const uint8_t *type, const float2 *y, float a_ref,
                                const float2 *a_n, const float2 *a_k, const float *dr_n,
                                const float *dr_k, double *sums, int cap, cudaStream_t s);
 // Host stub of the kernel launch_decide runs (for explicit graph nodes).

@@ -824,9 +824,10 @@ void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State
 }
 
 // ---------------------------------------------------------------------------
-// Surrogate step (learned surrogate): one step of length dT = k dt with a
-// predicted mean acceleration abar (cell order, in units of a_ref) in place
-// of the SPH accelerations.  Fluid: u' = u + dT abar, r' = r + dT (u + u')/2,
+// Surrogate step (learned surrogate): one step of length dT = k dt with the
+// mean acceleration abar = a_n + a_ref y (a_n: the SPH acceleration at the
+// step start; y: the network's correction, cell order) in place of the SPH
+// accelerations.  Fluid: u' = u + dT abar, r' = r + dT (u + u')/2,
 // rho' = rho + dT (drho/dt)_n (the SPH continuity rate of the evaluation at
 // n); inflow buffer, buffer -> fluid conversion and outflow as in the
 // corrector.  Writes raw in the cell order of the evaluation and sets the
@@ -834,8 +835,8 @@ void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State
 // ---------------------------------------------------------------------------
 __global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *__restrict__ sc,
                                    State<float> srt, State<float> raw,
-                                   const float2 *__restrict__ abar, float a_ref,
-                                   const float *__restrict__ dr, double dT) {
+                                   const float2 *__restrict__ a_n, const float2 *__restrict__ y,
+                                   float a_ref, const float *__restrict__ dr, double dT) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) sc->dt = dT;
     if (i >= sc->nsrt) return;
@@ -850,7 +851,7 @@ __global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *
     float2 ds = srt.disp[i];
     if (typ == T_FLUID) {
         float tdt = (float)dT;
-        float ax = a_ref * abar[i].x, ay = a_ref * abar[i].y;
+        float ax = a_n[i].x + a_ref * y[i].x, ay = a_n[i].y + a_ref * y[i].y;
         float uhx = v0.x + 0.5f * tdt * ax, uhy = v0.y + 0.5f * tdt * ay;
         p1 = make_double2(p0.x + dT * (P.ufx_d + (double)uhx), p0.y + dT * (P.ufy_d + (double)uhy));
         v1 = make_float2(v0.x + tdt * ax, v0.y + tdt * ay);
@@ -882,17 +883,18 @@ __global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *
 }
 
 void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Grid &g, Scalars *sc,
-                             const State<float> &srt, const State<float> &raw, const float2 *abar,
-                             float a_ref, const float *dr, double dT, int cap, cudaStream_t s) {
-    launch_k(k_surrogate_update, (cap + 255) / 256, 256, s, P, inf, g, sc, srt, raw, abar, a_ref, dr,
-             dT);
+                             const State<float> &srt, const State<float> &raw, const float2 *a_n,
+                             const float2 *y, float a_ref, const float *dr, double dT, int cap,
+                             cudaStream_t s) {
+    launch_k(k_surrogate_update, (cap + 255) / 256, 256, s, P, inf, g, sc, srt, raw, a_n, y, a_ref,
+             dr, dT);
 }
 
 // Residuals of a surrogate step over the fluid particles (cell order): sums of
-// |a_ref abar - (a_n + a_k)/2|^2, |(a_n + a_k)/2|^2 and (drho_k - drho_n)^2,
-// and the fluid count, accumulated in FP64.
+// |abar - (a_n + a_k)/2|^2 with abar = a_n + a_ref y, |(a_n + a_k)/2|^2 and
+// (drho_k - drho_n)^2, and the fluid count, accumulated in FP64.
 __global__ void k_surrogate_residual(int n, const uint8_t *__restrict__ type,
-                                     const float2 *__restrict__ abar, float a_ref,
+                                     const float2 *__restrict__ y, float a_ref,
                                      const float2 *__restrict__ a_n, const float2 *__restrict__ a_k,
                                      const float *__restrict__ dr_n, const float *__restrict__ dr_k,
                                      double *__restrict__ sums) {
@@ -900,7 +902,8 @@ __global__ void k_surrogate_residual(int n, const uint8_t *__restrict__ type,
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (i < n && type[i] == T_FLUID) {
         double mx = 0.5 * ((double)a_n[i].x + a_k[i].x), my = 0.5 * ((double)a_n[i].y + a_k[i].y);
-        double ex = (double)a_ref * abar[i].x - mx, ey = (double)a_ref * abar[i].y - my;
+        double ex = (double)a_n[i].x + (double)a_ref * y[i].x - mx;
+        double ey = (double)a_n[i].y + (double)a_ref * y[i].y - my;
         double dd = (double)dr_k[i] - dr_n[i];
         v[0] = ex * ex + ey * ey;
         v[1] = mx * mx + my * my;

@@ -1,0 +1,136 @@
+"""Training and evaluation of the learned surrogate (sph_mpnn_*,
+sph_surrogate_step) from plain SPH trajectories.
+
+A sample is a state s_n of a jet together with what the network must
+predict there: the correction y* = (abar - a_n) / a_ref, where abar =
+(u_{n+k} - u_n) / (t_{n+k} - t_n) is the mean acceleration of a particle over
+the next k plain steps and a_n its SPH acceleration at s_n (Eq. 25).  Only
+fluid particles present at both ends carry a target; the others get y* = 0.
+The surrogate step then advances with abar = a_n + a_ref y (plain SPH judges
+it and takes over when its residuals exceed the threshold).
+
+Everything runs through the C ABI of libsph (binding.py); nothing here
+computes SPH or network arithmetic itself.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import binding
+
+STATE_KEYS = ("x", "y", "u", "v", "rho", "m", "type", "id")
+
+
+def collect(case, nsamples, every=20, k=4, warm=20, lanes_cadence=(2, 8)):
+    """Samples from one jet: warm-up steps, then every `every` steps a state
+    with the k-step targets.  Returns a list of dicts (state arrays sorted by
+    id, the correction abar - a_n and abar per particle, the validity mask)."""
+    sim = binding.Simulation(case)
+    sim.set_tuning(*lanes_cadence)
+    out = []
+    try:
+        sim.run(warm)
+        for _ in range(nsamples):
+            sim.evaluate()
+            s0 = sim.state()
+            t0 = sim.time()["t"]
+            sim.run(k)
+            s1 = sim.state()
+            t1 = sim.time()["t"]
+            common, i0, i1 = np.intersect1d(s0["id"], s1["id"], return_indices=True)
+            n0 = len(s0["id"])
+            abar = np.zeros((n0, 2))
+            abar[i0, 0] = (s1["u"][i1] - s0["u"][i0]) / (t1 - t0)
+            abar[i0, 1] = (s1["v"][i1] - s0["v"][i0]) / (t1 - t0)
+            valid = np.zeros(n0, bool)
+            valid[i0] = (s0["type"][i0] == binding.FLUID) & (s1["type"][i1] == binding.FLUID)
+            a_n = np.stack([s0["ax"], s0["ay"]], 1)
+            corr = np.where(valid[:, None], abar - a_n, 0.0)
+            out.append({"state": {key: s0[key] for key in STATE_KEYS}, "corr": corr,
+                        "abar": np.where(valid[:, None], abar, 0.0), "valid": valid})
+            sim.run(max(every - k, 0))
+    finally:
+        sim.close()
+    return out
+
+
+def a_scale(samples):
+    """RMS (per component) of the correction over the valid particles."""
+    num = sum(float(np.sum(s["corr"][s["valid"]] ** 2)) for s in samples)
+    cnt = sum(int(np.sum(s["valid"])) for s in samples)
+    return float(np.sqrt(num / max(cnt, 1) / 2.0)) or 1.0
+
+
+class Trainer:
+    """One evaluation context per case (the samples of a case share its
+    parameters); the network is trained on the GPU with its own forward,
+    backward and Adam kernels."""
+
+    def __init__(self, cases, capacity, u_ref=1.0, seed=0, device=0):
+        from .workloads import mpnn_init
+        self.sims = [binding.Simulation(c) for c in cases]
+        self.net = binding.Mpnn(capacity, device)
+        prm = mpnn_init(seed)
+        prm["D"][:] = 0.0          # start from the zero correction (steps with a_n)
+        self.net.set_params(prm)
+        self.u_ref = u_ref
+        self.capacity = capacity
+
+    def _load(self, ci, sample):
+        sim = self.sims[ci]
+        binding.sph_set_state(sim.ctx, sample["state"])
+        sim.evaluate()
+        return sim
+
+    def _order(self, sim, sample):
+        """Positions, in the sample's id-sorted arrays, of the context's
+        particles in cell order."""
+        ids, _ = binding.sph_mpnn_forward(self.net.net, sim.ctx, self.u_ref, False, self.capacity)
+        return np.searchsorted(sample["state"]["id"], ids)
+
+    def train(self, data, a_ref, epochs=None, seconds=None, lr=1e-3, seed=0):
+        """data: list of (case index, sample).  Stops after `epochs` passes or
+        `seconds` of wall time.  Returns the mean loss of each pass."""
+        rng = np.random.default_rng(seed)
+        losses = []
+        t_start = time.perf_counter()
+        while True:
+            tot = 0.0
+            for j in rng.permutation(len(data)):
+                ci, smp = data[j]
+                sim = self._load(ci, smp)
+                pos = self._order(sim, smp)
+                t = (smp["corr"][pos] / a_ref).astype(np.float32)
+                tot += binding.sph_mpnn_backward(self.net.net, sim.ctx, self.u_ref, t)
+                binding.sph_mpnn_adam(self.net.net, lr)
+            losses.append(tot / len(data))
+            if epochs is not None and len(losses) >= epochs:
+                break
+            if seconds is not None and time.perf_counter() - t_start >= seconds:
+                break
+        return losses
+
+    def prediction_errors(self, data, a_ref, bf16=True):
+        """Relative L2 errors, over the valid particles of all samples, of the
+        predicted mean acceleration a_n + a_ref y against the true k-step
+        mean, and of a_n alone (the method without the network)."""
+        num_net = num_zero = den = 0.0
+        for ci, smp in data:
+            sim = self._load(ci, smp)
+            ids, y = binding.sph_mpnn_forward(self.net.net, sim.ctx, self.u_ref, bf16,
+                                              self.capacity)
+            pos = np.searchsorted(smp["state"]["id"], ids)
+            v = smp["valid"][pos]
+            corr = smp["corr"][pos][v]
+            pred = a_ref * y.astype(np.float64)[v]
+            num_net += float(np.sum((pred - corr) ** 2))
+            num_zero += float(np.sum(corr ** 2))
+            den += float(np.sum(smp["abar"][pos][v] ** 2))
+        return float(np.sqrt(num_net / den)), float(np.sqrt(num_zero / den))
+
+    def close(self):
+        self.net.close()
+        for s in self.sims:
+            s.close()

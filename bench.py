@@ -151,7 +151,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="jet_c2",
-                    choices=["jet_c2", "jet_c3", "dam_c1", "ensemble_c4"])
+                    choices=["jet_c2", "jet_c3", "dam_c1", "ensemble_c4", "surrogate_c5"])
+    ap.add_argument("--train-seconds", type=float, default=60.0,
+                    help="surrogate_c5: GPU training time of the network")
+    ap.add_argument("--threshold", type=float, default=1e-3,
+                    help="surrogate_c5: residual threshold above which plain SPH takes over")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tune", default="auto",
@@ -206,7 +210,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    if args.workload == "ensemble_c4":
+    if args.workload in ("ensemble_c4", "surrogate_c5"):
         m, re, we, dx, length = ensemble_members()[0]
         case = ensemble_case(m, re, we, dx, length, args.skin)
         desc = "member 0 of the 64-jet ensemble"
@@ -322,6 +326,11 @@ def main():
     from paper_1603_02421_gb300.replicas import rank_members
     if args.workload == "ensemble_c4":
         bench_ensemble(args, binding, dist, dev, rank, world, local)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    if args.workload == "surrogate_c5":
+        bench_surrogate(args, binding, dist, dev, rank, world, local)
         if dist is not None:
             dist.destroy_process_group()
         return
@@ -665,6 +674,181 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local):
         }
         print(json.dumps(line), flush=True)
     ens.close()
+    for sm in sims:
+        sm.close()
+
+
+# Learned-surrogate workload: training jets on the ensemble's Re x We grid and
+# 16 held-out (Re, We) pairs between its grid points at about 200k particles.
+SUR_TRAIN = [(100, 5), (200, 20), (400, 40), (700, 10), (1000, 60), (1500, 15), (2000, 30),
+             (3000, 50)]
+SUR_HELD_RE = [150, 300, 550, 850, 1250, 1750, 2500, 2750]
+SUR_HELD_WE = [7.5, 25.0]
+SUR_K = 4
+
+
+def bench_surrogate(args, binding, dist, dev, rank, world, local):
+    """Plain SPH (the 16 held-out members as one batched ensemble) against
+    surrogate steps (k = 4 substeps per step, plain SPH as judge and fallback
+    at the residual threshold) on the same members, after training the
+    network on the GPU from plain trajectories of the training jets."""
+    import torch
+    from paper_1603_02421_gb300 import surrogate as sg
+    from paper_1603_02421_gb300.replicas import rank_members, reduce_rate
+
+    def jet_case(seed, re, we, dx, n_target):
+        case = wl.jet(seed=seed, Re=re, We=we, dx=dx, length=n_target * dx * dx,
+                      kernel="wendland", prec="fp32", capacity_factor=1.15)
+        case["params"]["skin_over_h"] = args.skin
+        return case
+
+    # ---- training (plain trajectories -> samples -> GPU training) ----------
+    t_tr = time.perf_counter()
+    train_cases = [jet_case(100 + i, re, we, 1.0 / (30 + 30 * i / 7), 15000)
+                   for i, (re, we) in enumerate(SUR_TRAIN)]
+    data = [(ci, smp) for ci, c in enumerate(train_cases)
+            for smp in sg.collect(c, 10, every=10, k=SUR_K, warm=20)]
+    a_ref = sg.a_scale([smp for _, smp in data])
+    held_all = [(200 + 2 * i + j, re, we) for i, re in enumerate(SUR_HELD_RE)
+                for j, we in enumerate(SUR_HELD_WE)]
+    mine = [held_all[m] for m in rank_members(rank, world, len(held_all))]
+    held_cases = [jet_case(seed, re, we, 1.0 / 60, 200000) for seed, re, we in mine]
+    cap = max(c["params"]["capacity"] for c in train_cases + held_cases)
+    tr = sg.Trainer(train_cases, cap)
+    losses = tr.train(data, a_ref, seconds=args.train_seconds, lr=1e-3)
+    params = tr.net.params()
+    tr.close()
+    train_s = time.perf_counter() - t_tr
+    # held-out prediction errors (network vs the SPH acceleration alone)
+    test = [(ci, smp) for ci, c in enumerate(held_cases[:2])
+            for smp in sg.collect(c, 2, every=10, k=SUR_K, warm=20)]
+    ev = sg.Trainer(held_cases[:2], cap)
+    ev.net.set_params(params)
+    e_net, e_an = ev.prediction_errors(test, a_ref)
+    ev.close()
+
+    # ---- plain arm: the held-out members as one batched ensemble ----------
+    K = min(args.steps, 400)
+    K -= K % SUR_K
+    stream = torch.cuda.Stream(device=dev)
+    sims = [binding.Simulation(c, stream=stream.cuda_stream, device=local) for c in held_cases]
+    for sm in sims:
+        sm.set_tuning(2, 8)
+    ens = binding.Ensemble(sims, stream=stream.cuda_stream)
+    ens.run(max(args.warmup, 3))
+    start = [binding.sph_get_state(sm.ctx) for sm in sims]
+    n0 = sum(sm.time()["n"] for sm in sims)
+    t_start = [sm.time()["t"] for sm in sims]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    ens.run_async(K)
+    e1.record(stream)
+    ens.sync()
+    torch.cuda.synchronize(dev)
+    plain_s = e0.elapsed_time(e1) / 1e3
+    L_plain = [binding.sph_breakup_length(sm.ctx)[0] for sm in sims]
+    plain_value, _, _ = reduce_rate(plain_s, n0 * K, dist, dev)
+    ens.close()
+    t_plain = [sm.time()["t"] - t0_ for sm, t0_ in zip(sims, t_start)]
+
+    # ---- surrogate arm: the same members from the same states (the state
+    # is replaced; the simulated time runs on, so spans are differences) ----
+    t_sur0 = []
+    for sm, st in zip(sims, start):
+        binding.sph_set_state(sm.ctx, st)
+        t_sur0.append(sm.time()["t"])
+    net = binding.Mpnn(cap, local)
+    net.set_params(params)
+    clocks = ClockSampler(local)
+    accepted = steps = 0
+    rms = []
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for sm in sims:
+        for _ in range(K // SUR_K):
+            ok, rm, rd = binding.sph_surrogate_step(sm.ctx, net.net, SUR_K, 1.0, a_ref,
+                                                    args.threshold, True)
+            accepted += int(ok)
+            steps += 1
+            rms.append(rm)
+    torch.cuda.synchronize(dev)
+    sur_s = time.perf_counter() - t0
+    clk = clocks.stop()
+    L_sur = [binding.sph_breakup_length(sm.ctx)[0] for sm in sims]
+    t_sur = [sm.time()["t"] - t0_ for sm, t0_ in zip(sims, t_sur0)]
+    value, total_s, _ = reduce_rate(sur_s, n0 * K, dist, dev)
+    per_full = binding.sph_kernel_counts(sims[0].ctx)[0]
+    launches = steps * 27 + (steps - accepted) * SUR_K * per_full
+
+    # ---- end to end: host state in, surrogate steps, host state out -------
+    Ke = 5
+    pinned = [{k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
+               for k, v in st.items()} for st in start]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for sm, st in zip(sims, pinned):
+        binding.sph_set_state(sm.ctx, st)
+        for _ in range(Ke):
+            binding.sph_surrogate_step(sm.ctx, net.net, SUR_K, 1.0, a_ref, args.threshold, True)
+        binding.sph_get_state(sm.ctx)
+    e2e_s = time.perf_counter() - t0
+    e2e_value, _, _ = reduce_rate(e2e_s, n0 * Ke * SUR_K, dist, dev)
+    h2d = n0 * (16 + 8 + 4 + 4 + 4 + 1 + 4)
+    d2h = n0 * (16 + 8 + 4 + 4 + 1 + 4 + 8 + 4)
+    net.close()
+
+    # network GEMM work per surrogate step on the tensor cores (BF16)
+    tensor_flop = 2.0 * 3 * (128 * 32 + 256 * 128) * n0 * (K // SUR_K)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    achieved = tensor_flop / sur_s / 1e12
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = oracle_sample(held_cases[0], 20000)
+        psteps, nsteps, el, n = run_oracle(sample, args.cpu_seconds)
+        cpu = {"value": psteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 CPU oracle (single thread), %d steps of the upstream %d "
+                         "particles of held-out member 0, %.1f s" % (nsteps, n, el)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "surrogate_c5: 16 held-out planar jets, Re in %s x We in %s, "
+                                   "dx = D/60, ~200k particles each; network trained on 8 jets "
+                                   "of the Re x We grid" % (SUR_HELD_RE, SUR_HELD_WE),
+                       "members_per_gpu": len(sims), "particles_total": n0,
+                       "k_substeps": SUR_K, "threshold": args.threshold,
+                       "surrogate_steps": steps, "accepted": accepted,
+                       "acceptance_rate": accepted / max(steps, 1),
+                       "momentum_residual_median": float(np.median(rms)) if rms else None,
+                       "prediction_error_heldout": {"network": e_net, "sph_acceleration_only": e_an},
+                       "training": {"seconds": train_s, "passes": len(losses),
+                                    "samples": len(data), "final_loss": losses[-1],
+                                    "a_ref": a_ref},
+                       "plain_value": plain_value, "surrogate_over_plain": value / plain_value,
+                       "plain_how": "the same members as one batched ensemble, K plain steps",
+                       "simulated_time_span": {"plain_mean": float(np.mean(t_plain)),
+                                               "surrogate_mean": float(np.mean(t_sur))},
+                       "breakup_L_over_D_mean": {"plain": float(np.mean(L_plain)),
+                                                 "surrogate": float(np.mean(L_sur))},
+                       "l2": "inputs larger than L2 (all members resident)"},
+            "roofline": {"kernel": "BF16 tensor-core GEMMs of the network (whole surrogate-arm time)",
+                         "bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
+                         "traffic": None,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / (Ke * SUR_K),
+                    "d2h_bytes_per_step": d2h / (Ke * SUR_K),
+                    "how": "per member: sph_set_state from pinned host arrays, %d surrogate "
+                           "steps of %d substeps, sph_get_state; host wall clock" % (Ke, SUR_K)},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
     for sm in sims:
         sm.close()
 

@@ -175,7 +175,9 @@ def jet(seed=0, Re=200.0, We=20.0, D=1.0, U=1.0, rho0=1000.0, dx=None,
     fill = length if fill is None else fill
     k = rng.uniform(0.5, 1.0) / D
     phase = 0.0
-    nxp = int(round(fill * D / dx))
+    # whole lattice columns inside [0, fill): the last column centre stays
+    # below the box end even when fill is not a whole number of spacings
+    nxp = int(math.floor(fill * D / dx + 1e-6))
     nyp = int(round(D / dx))
     x, y = lattice(0.0, -0.5 * D, nxp, nyp, dx)
     u = U * (1.0 + amp * np.sin(k * U * (-x / U) + phase))

@@ -704,7 +704,7 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
 
     # ---- training (plain trajectories -> samples -> GPU training) ----------
     t_tr = time.perf_counter()
-    train_cases = [jet_case(100 + i, re, we, 1.0 / (30 + 30 * i / 7), 15000)
+    train_cases = [jet_case(100 + i, re, we, 1.0 / 60, 50000)
                    for i, (re, we) in enumerate(SUR_TRAIN)]
     data = [(ci, smp) for ci, c in enumerate(train_cases)
             for smp in sg.collect(c, 10, every=10, k=SUR_K, warm=20)]
@@ -818,7 +818,8 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
             "data": "synthetic",
             "config": {"workload": "surrogate_c5: 16 held-out planar jets, Re in %s x We in %s, "
                                    "dx = D/60, ~200k particles each; network trained on 8 jets "
-                                   "of the Re x We grid" % (SUR_HELD_RE, SUR_HELD_WE),
+                                   "of the Re x We grid at D/60, 50k particles each"
+                                   % (SUR_HELD_RE, SUR_HELD_WE),
                        "members_per_gpu": len(sims), "particles_total": n0,
                        "k_substeps": SUR_K, "threshold": args.threshold,
                        "surrogate_steps": steps, "accepted": accepted,

@@ -497,7 +497,7 @@ def end_to_end(binding, case, stream, local, K, tuning):
     n = len(st["x"])
     pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
               for k, v in st.items()}
-    binding.sph_step(ctx)              # warm (graph-free path)
+    binding.sph_step(ctx)              # warm (captures the step graphs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     binding.sph_set_state(ctx, pinned)

@@ -816,9 +816,17 @@ sph_status sph_inflow(sph_ctx *c, double x_exit, double y0, double y1, double U,
     }
 }
 
+static sph_status ensure_graph(sph_ctx *c);
+static sph_status launch_step_graph(sph_ctx *c);
+
 sph_status sph_step(sph_ctx *c, double *dt_used) {
     if (!c) return SPH_ERR_ARG;
-    step_any(c, host_next_is_full(c));
+    // one replay of the captured step (the same kernels as an eager launch,
+    // without the per-kernel launch cost)
+    sph_status gs = ensure_graph(c);
+    if (gs) return gs;
+    gs = launch_step_graph(c);
+    if (gs) return gs;
     sph_status s = after_work(c, "step");
     if (dt_used) *dt_used = c->hsc->dt;
     c->n_eval = c->hsc->nsrt;

@@ -111,15 +111,18 @@ def ensemble_case(m, re, we, dx, length, skin):
     return case
 
 
+# Sources that define the SPH step kernels (the host runtime is not among them).
+KERNEL_SOURCES = ("sph_sweeps.cu", "sph_device.cuh", "sph_internal.cuh")
+
+
 def sources_sha256() -> str:
-    """Hash of the CUDA sources (kernels and runtime) of libsph."""
+    """Hash of the sources that define libsph's step kernels."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1603_02421_gb300", "csrc")
     hsh = hashlib.sha256()
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                hsh.update(name.encode() + b"\0" + f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            hsh.update(name.encode() + b"\0" + f.read())
     return hsh.hexdigest()
 
 

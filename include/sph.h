@@ -205,12 +205,14 @@ sph_status sph_profile_report(sph_ctx *ctx, int cap, int *n, const char **names,
                               double *total_ms, long long *launches);
 
 /* Tuning of the step.  lanes (1, 2, 4 or 8): threads that share one particle's
- * neighbour loop in the pair sweeps.  cadence (1..64): the cells and neighbour
- * lists are rebuilt every `cadence` steps (always after the particles were
- * added, replaced or reordered by another call); the steps in between keep
- * the last build, which stays exact while no particle moves more than skin/2
- * since it (checked: SPH_ERR_SKIN otherwise), and a due inflow layer is laid
- * at the next rebuild.  Defaults: lanes 4, cadence 1 (every step). */
+ * neighbour loop in the pair sweeps (the neighbour-list build uses at least
+ * 4).  cadence (1..64): the cells and neighbour lists are rebuilt at least
+ * every `cadence` steps, and earlier when the step before spawned an inflow
+ * layer or when one more step could move a particle more than skin/2 from
+ * where the lists were built (decided on the device); also after the
+ * particles were added, replaced or reordered by another call.  The steps in
+ * between keep the last build, which stays exact (checked: SPH_ERR_SKIN
+ * otherwise).  Defaults: lanes 4, cadence 1 (every step). */
 sph_status sph_set_tuning(sph_ctx *ctx, int lanes, int cadence);
 sph_status sph_get_tuning(sph_ctx *ctx, int *lanes, int *cadence);
 

@@ -297,7 +297,9 @@ template <class T> static const uint32_t *enqueue_sort(sph_ctx *c) {
 template <class T> static void enqueue_build(sph_ctx *c, const uint32_t *key) {
     const PhysT<T> &P = Ops<T>::phys(c);
     tick(c, "list_colour");
-    launch_build<T>(c->lanes, P.csf != 0, P, c->grid, c->sc, c->cellSE, key, hot_n<T>(c), c->nl,
+    // the list build walks ~61 candidates of the 3x3 cells per particle; it
+    // takes at least 4 lanes per particle whatever the sweeps use
+    launch_build<T>(std::max(c->lanes, 4), P.csf != 0, P, c->grid, c->sc, c->cellSE, key, hot_n<T>(c), c->nl,
                     csf_of<T>(c), c->cap, c->stream);
 }
 

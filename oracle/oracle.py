@@ -104,6 +104,9 @@ def lib():
         _lib.orc_evaluate.restype = ctypes.c_int
         _lib.orc_evaluate.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(_State),
                                       ctypes.POINTER(_Out)]
+        _lib.orc_summation_density.restype = ctypes.c_int
+        _lib.orc_summation_density.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(_State),
+                                               _dp]
         _lib.orc_components.restype = ctypes.c_longlong
         _lib.orc_components.argtypes = [ctypes.c_longlong, _dp, _dp, ctypes.c_double,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
@@ -225,6 +228,7 @@ class Derived:
     wall_A: float
     wall_db: float
     wall_h0: float
+    summation: bool
 
 
 def derive(params: dict) -> Derived:
@@ -252,7 +256,8 @@ def derive(params: dict) -> Derived:
         xmax=float(params["xmax"]), ymax=float(params["ymax"]),
         wall_A=float(params.get("wall_A_coef", 0.01)) * c0 * c0 / h,
         wall_db=float(params.get("wall_db_over_dx", 0.5)) * dx,
-        wall_h0=float(params.get("wall_h0", 0.0)))
+        wall_h0=float(params.get("wall_h0", 0.0)),
+        summation=params.get("density", "continuity") == "summation")
 
 
 def _cparams(d: Derived, use_cells: bool) -> _Params:
@@ -295,6 +300,23 @@ def evaluate(d: Derived, st: dict, boundary: dict | None = None, use_cells=True)
     if lib().orc_evaluate(ctypes.byref(cp), ctypes.byref(s), ctypes.byref(o)) != 0:
         raise MemoryError("oracle evaluation failed")
     return {k: v[:n] for k, v in out.items()}
+
+
+def summation_density(d: Derived, st: dict, use_cells=True) -> np.ndarray:
+    """Eq. 6: rho_a = sum_b m_b W_ab over the fluid and buffer particles
+    within 2h, the particle itself included."""
+    n = len(st["x"])
+    cols = {k: _f64(st[k]) for k in ("x", "y", "u", "v", "rho", "m")}
+    typ = np.ascontiguousarray(st["type"], dtype=np.uint8)
+    z = np.zeros(1)
+    s = _State(n=n, x=_d(cols["x"]), y=_d(cols["y"]), u=_d(cols["u"]), v=_d(cols["v"]),
+               rho=_d(cols["rho"]), m=_d(cols["m"]), type=_u8(typ), nb=0,
+               bx=_d(z), by=_d(z), bnx=_d(z), bny=_d(z))
+    out = np.zeros(max(n, 1))
+    cp = _cparams(d, use_cells)
+    if lib().orc_summation_density(ctypes.byref(cp), ctypes.byref(s), _d(out)) != 0:
+        raise MemoryError("oracle summation density failed")
+    return out[:n]
 
 
 # --------------------------------------------------------------------------
@@ -429,12 +451,21 @@ class OracleSim:
         from the evaluation at n over the fluid particles.
         Buffer particles follow the prescribed inflow velocity through the
         same position update and keep rho = rho0.
+        With params["density"] == "summation" the fluid density of each
+        evaluation is Eq. 6 at that evaluation's positions instead of the
+        integrated Eq. 7, and the state keeps the density of the last
+        evaluation (the half step).
         """
         d = self.d
         st = self.st
         fl = st["type"] == FLUID
         bf = st["type"] == BUFFER
-        ev = self.evaluate()
+        if d.summation:
+            # Eq. 6 in place of Eq. 7: each evaluation takes the fluid density
+            # from the positions; it is not integrated
+            st = dict(st)
+            st["rho"] = np.where(fl, summation_density(d, st, self.use_cells), st["rho"])
+        ev = self.evaluate(st)
         self.last_eval = ev
         if d.dt_fixed > 0.0:
             dt = d.dt_fixed
@@ -457,6 +488,8 @@ class OracleSim:
         if bf.any():
             mid["u"] = np.where(bf, uin_half, mid["u"])
             mid["v"] = np.where(bf, 0.0, mid["v"])
+        if d.summation:
+            mid["rho"] = np.where(fl, summation_density(d, mid, self.use_cells), st["rho"])
         ev2 = self.evaluate(mid)
 
         # corrector
@@ -471,6 +504,8 @@ class OracleSim:
         new["u"] = 2.0 * us - st["u"]
         new["v"] = 2.0 * vs - st["v"]
         new["rho"] = 2.0 * rs - st["rho"]
+        if d.summation:
+            new["rho"] = mid["rho"]         # the density of the last evaluation
         if bf.any():
             new["u"] = np.where(bf, uin_new, new["u"])
             new["v"] = np.where(bf, 0.0, new["v"])

@@ -452,3 +452,27 @@ long long orc_components(long long n, const double *x, const double *y,
     free(queue); free(start); free(nb);
     return ncomp;
 }
+
+int orc_summation_density(const orc_params *p, const orc_state *s, double *rho)
+{
+    long long n = s->n;
+    int K = p->kernel;
+    double h = p->h;
+    long long *start = NULL;
+    int *nb = NULL;
+    if (orc_neighbours(n, s->x, s->y, NULL, 2.0 * h, p->use_cells, &start, &nb) < 0)
+        return -1;
+    double W0 = orc_W(K, 0.0, h);
+    for (long long a = 0; a < n; ++a) {
+        double sum = s->m[a] * W0;
+        for (long long k = start[a]; k < start[a + 1]; ++k) {
+            int b = nb[k];
+            double dx = s->x[a] - s->x[b], dy = s->y[a] - s->y[b];
+            sum += s->m[b] * orc_W(K, sqrt(dx * dx + dy * dy), h);
+        }
+        rho[a] = sum;
+    }
+    free(start);
+    free(nb);
+    return 0;
+}

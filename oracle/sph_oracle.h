@@ -78,6 +78,11 @@ void orc_free(void *p);
  * Returns 0 on success, -1 on allocation failure. */
 int orc_evaluate(const orc_params *p, const orc_state *s, orc_out *o);
 
+/* Summation density (Eq. 6): rho_a = sum_b m_b W_ab over the fluid and buffer
+ * particles within 2h, the particle itself included.  Returns 0 on success,
+ * -1 on allocation failure. */
+int orc_summation_density(const orc_params *p, const orc_state *s, double *rho);
+
 /* Connected components of the graph with edges r_ab < radius among the
  * n particles (Sec. 3-2 breakup criterion).  label[a] = smallest index in
  * a's component.  Returns the number of components or -1. */

@@ -385,3 +385,53 @@ def test_wall_force_constant_along_a_straight_wall(orc):
     q = psi / (2 * d.h)
     # R(psi) eps with eps(z) = 1 (h0 = 0) and eps(u) = 0 (at rest)
     assert np.mean(ays) == pytest.approx(d.wall_A * (1 - q) / np.sqrt(q), rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# summation density (Eq. 6), the alternative to integrating Eq. 7
+# ---------------------------------------------------------------------------
+def test_summation_density_equals_rho0_times_colour(orc):
+    # with every density at rho0, V_b = m_b / rho0, so Eq. 6 is rho0 times the
+    # colour sum of Eq. 14 (computed by a separate loop of the oracle)
+    st = wl.jittered_patch(seed=3, nx=18, ny=14, dx=0.02, jitter=0.1, drho=0.0)
+    p = wl.test_params(dx=0.02, sigma=0.05)
+    d = orc.derive(p)
+    rs = orc.summation_density(d, st)
+    ev = orc.evaluate(d, st)
+    assert np.allclose(rs, d.rho0 * ev["C"], rtol=1e-13, atol=0)
+
+
+def test_summation_density_isolated_particle(orc):
+    st = wl.jittered_patch(seed=0, nx=1, ny=1, dx=0.02, jitter=0.0, drho=0.0)
+    for kernel in ("cubic", "wendland"):
+        p = wl.test_params(dx=0.02, kernel=kernel)
+        d = orc.derive(p)
+        rs = orc.summation_density(d, st)
+        assert rs[0] == pytest.approx(st["m"][0] * orc.W(kernel, 0.0, d.h), rel=1e-15)
+
+
+def test_summation_density_interior_of_lattice(orc):
+    st = wl.jittered_patch(seed=0, nx=30, ny=30, dx=0.02, jitter=0.0, drho=0.0)
+    p = wl.test_params(dx=0.02)
+    d = orc.derive(p)
+    rs = orc.summation_density(d, st)
+    x, y = st["x"], st["y"]
+    inner = (x > x.min() + 0.1) & (x < x.max() - 0.1) & (y > y.min() + 0.1) & (y < y.max() - 0.1)
+    assert np.all(np.abs(rs[inner] / d.rho0 - 1.0) < 0.02)
+
+
+def test_summation_mode_step_keeps_the_half_step_density(orc):
+    st = wl.jittered_patch(seed=4, nx=16, ny=12, dx=0.02, vel=0.2, drho=0.0)
+    p = wl.test_params(dx=0.02, dt_fixed=2e-4)
+    p["density"] = "summation"
+    sim = orc.OracleSim(p, st)
+    x0, y0, u0, v0 = (sim.st[k].copy() for k in ("x", "y", "u", "v"))
+    d = sim.d
+    rho_n = orc.summation_density(d, sim.st)
+    ev = orc.evaluate(d, dict(sim.st, rho=rho_n))
+    sim.step()
+    half = 0.5 * 2e-4
+    mid = dict(sim.st, x=x0 + half * u0, y=y0 + half * v0)
+    assert np.allclose(sim.st["rho"], orc.summation_density(d, mid), rtol=1e-14, atol=0)
+    assert not np.allclose(sim.st["rho"], rho_n)      # the density follows the positions
+    assert np.isfinite(ev["ax"]).all()

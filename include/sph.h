@@ -58,6 +58,9 @@ typedef enum {
 
 typedef enum { SPH_KERNEL_CUBIC = 0, SPH_KERNEL_WENDLAND = 1 } sph_kernel;
 typedef enum { SPH_FP32 = 0, SPH_FP64 = 1 } sph_precision;
+/* Density of the fluid particles: integrated continuity equation (Eq. 7, the
+ * paper's choice) or the summation of Eq. 6 at each evaluation. */
+typedef enum { SPH_DENSITY_CONTINUITY = 0, SPH_DENSITY_SUMMATION = 1 } sph_density;
 enum { SPH_FLUID = 0, SPH_BOUNDARY = 1, SPH_BUFFER = 2 };
 
 /* Run parameters (all SI or consistently nondimensional). */
@@ -90,6 +93,13 @@ typedef struct {
     long long boundary_capacity; /* maximum boundary particles                      */
     void *cuda_stream;     /* cudaStream_t to issue work on, or NULL                */
     int device;            /* CUDA device ordinal                                   */
+    int density;           /* sph_density.  With SPH_DENSITY_SUMMATION each
+                              evaluation takes the fluid density from Eq. 6 at its
+                              positions (buffer particles keep theirs); the state's
+                              density is that of the step's last evaluation (the
+                              half step), and sph_evaluate stores the density it
+                              used.  FP32 and FP64 contexts; not with
+                              sph_surrogate_step.                               */
 } sph_params;
 
 /* Create a context: validates *params, selects the device, allocates all

@@ -50,7 +50,8 @@ class sph_params(ctypes.Structure):
                 ("wall_h0", ctypes.c_double), ("wall_db_over_dx", ctypes.c_double),
                 ("u_frame_x", ctypes.c_double), ("u_frame_y", ctypes.c_double),
                 ("capacity", ctypes.c_longlong), ("boundary_capacity", ctypes.c_longlong),
-                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("density", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -173,7 +174,8 @@ def make_params(p: dict, capacity=None, boundary_capacity=0, stream=None, device
         wall_h0=p.get("wall_h0", 0.0), wall_db_over_dx=p.get("wall_db_over_dx", 0.5),
         u_frame_x=p.get("u_frame_x", 0.0), u_frame_y=p.get("u_frame_y", 0.0),
         capacity=cap, boundary_capacity=int(boundary_capacity),
-        cuda_stream=stream, device=int(device))
+        cuda_stream=stream, device=int(device),
+        density=1 if p.get("density", "continuity") == "summation" else 0)
 
 
 # ---------------------------------------------------------------------------

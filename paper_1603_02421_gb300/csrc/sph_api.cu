@@ -185,6 +185,7 @@ template <class T> static PhysT<T> make_phys(const sph_params &p, const Grid &g,
     P.csf = p.sigma > 0.0;
     P.walls = walls;
     P.gamma7 = p.gamma == 7.0;
+    P.summation = p.density == SPH_DENSITY_SUMMATION;
     P.h = (T)h;
     P.inv_h = (T)(1.0 / h);
     P.H2lo = (T)(H2 * (1.0 - band));
@@ -299,8 +300,27 @@ template <class T> static void enqueue_build(sph_ctx *c, const uint32_t *key) {
     tick(c, "list_colour");
     // the list build walks ~61 candidates of the 3x3 cells per particle; it
     // takes at least 4 lanes per particle whatever the sweeps use
-    launch_build<T>(std::max(c->lanes, 4), P.csf != 0, P, c->grid, c->sc, c->cellSE, key, hot_n<T>(c), c->nl,
-                    csf_of<T>(c), c->cap, c->stream);
+    // with Eq. 6 densities the colour needs the summed volumes, so it runs
+    // after the density sweep instead of inside the list build
+    launch_build<T>(std::max(c->lanes, 4), P.csf != 0 && !P.summation, P, c->grid, c->sc,
+                    c->cellSE, key, hot_n<T>(c), c->nl, csf_of<T>(c), c->cap, c->stream);
+}
+
+// Eq. 6 densities of the records `hot` (a no-op with Eq. 7), then, when the
+// colour was not computed with the list, the colour of those records.
+// drho_out: where the state keeps the density (null at the half step).
+template <class T>
+static void enqueue_density(sph_ctx *c, const Hot<T> &hot, T *drho_out, bool colour) {
+    const PhysT<T> &P = Ops<T>::phys(c);
+    if (!P.summation) return;
+    State<T> srt = state_of<T>(c->srt);
+    tick(c, "density");
+    launch_density<T>(c->lanes, P, c->sc, c->nl, hot, srt.mass, srt.type, drho_out, c->cap,
+                      c->stream);
+    if (colour && P.csf) {
+        tick(c, "colour");
+        launch_colour<T>(c->lanes, P, c->sc, c->nl, hot, csf_of<T>(c), c->cap, c->stream);
+    }
 }
 
 template <class T> static void enqueue_normal(sph_ctx *c, const Hot<T> &hot) {
@@ -323,9 +343,11 @@ template <class T> static void enqueue_cells(sph_ctx *c, bool full) {
     if (full) {
         enqueue_sort<T>(c);
         enqueue_build<T>(c, key);
+        enqueue_density<T>(c, hn, srt.drho, true);
     } else {
         tick(c, "refresh");
         launch_refresh<T>(P, c->grid, c->sc, key, raw, srt, hn, c->cap, c->stream);
+        enqueue_density<T>(c, hn, srt.drho, false);
         if (P.csf) {
             tick(c, "colour");
             launch_colour<T>(c->lanes, P, c->sc, c->nl, hn, csf_of<T>(c), c->cap, c->stream);
@@ -348,6 +370,7 @@ template <class T> static void enqueue_rest(sph_ctx *c) {
                      bd_of(c), srt, raw, acc, dr, c->cap, c->stream);
     tick(c, "predict");
     launch_predict<T>(P, c->inf, c->sc, srt, hn.H0, acc, dr, hh, c->cap, c->stream);
+    enqueue_density<T>(c, hh, (T *)nullptr, false);
     if (P.csf) {
         tick(c, "colour");
         launch_colour<T>(c->lanes, P, c->sc, c->nl, hh, csf_of<T>(c), c->cap, c->stream);
@@ -378,6 +401,7 @@ template <class T> static void enqueue_evaluate(sph_ctx *c) {
     const uint32_t *key = enqueue_sort<T>(c);
     Hot<T> hn = hot_n<T>(c);
     enqueue_build<T>(c, key);
+    enqueue_density<T>(c, hn, srt.drho, true);
     enqueue_normal<T>(c, hn);
     launch_forces<T>(c->lanes, 0, P, c->grid, c->inf, c->sc, c->nl, key, hn, csf_of<T>(c),
                      bd_of(c), srt, raw, (typename Vec<T>::v2 *)c->acc, (T *)c->dr, c->cap,
@@ -585,6 +609,8 @@ sph_status sph_init(const sph_params *p, sph_ctx **out) {
     if (!(q.courant > 0 && q.courant <= 1.0 && q.dt_fixed >= 0))
         return fail(nullptr, SPH_ERR_ARG, "courant in (0, 1] and dt_fixed >= 0 required");
     if (!(q.xmax > q.xmin && q.ymax > q.ymin)) return fail(nullptr, SPH_ERR_ARG, "empty domain box");
+    if (q.density != SPH_DENSITY_CONTINUITY && q.density != SPH_DENSITY_SUMMATION)
+        return fail(nullptr, SPH_ERR_ARG, "unknown density mode %d", q.density);
     if (!(q.skin_over_h >= 0.1 && q.skin_over_h <= 2.0))
         return fail(nullptr, SPH_ERR_ARG, "skin_over_h must lie in [0.1, 2]");
     if (!(q.capacity >= 1 && q.capacity <= (1ll << 28)))
@@ -1366,6 +1392,11 @@ sph_status sph_kernel_counts(sph_ctx *c, int *per_full_step, int *per_reused_ste
     int rest = (csf ? 3 : 0)               // normal (2x) + colour of the half step
                + 3                         // forces (2x) + predict
                + 1;                        // spawn / time advance
+    if (c->prm.density == SPH_DENSITY_SUMMATION) {
+        full += 1 + (csf ? 1 : 0);         // Eq. 6 sweep, colour out of the list build
+        reuse += 1;                        // Eq. 6 sweep
+        rest += 1;                         // Eq. 6 sweep of the half step
+    }
     int decide = c->cadence > 1 ? 1 : 0;   // device-side choice of the next step's kind
     if (per_full_step) *per_full_step = full + rest + decide;
     if (per_reused_step) *per_reused_step = (c->cadence > 1 ? reuse : full) + rest + decide;
@@ -1404,6 +1435,8 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
     if (accepted) *accepted = 0;
     if (!net) return fail(c, SPH_ERR_ARG, "network is NULL");
     if (c->tsz != 4) return fail(c, SPH_ERR_ARG, "the surrogate step needs an FP32 context");
+    if (c->prm.density != SPH_DENSITY_CONTINUITY)
+        return fail(c, SPH_ERR_ARG, "the surrogate step needs the continuity density (Eq. 7)");
     if (k < 1 || k > 64) return fail(c, SPH_ERR_ARG, "k must lie in [1, 64]");
     if (!(u_ref > 0) || !(a_ref > 0) || !(threshold > 0))
         return fail(c, SPH_ERR_ARG, "u_ref, a_ref and threshold must be > 0");

@@ -71,6 +71,7 @@ template <class T> struct PhysT {
     int csf;             // sigma > 0
     int walls;           // boundary particles present
     int gamma7;          // gamma == 7: Eq. 26 as an exact polynomial
+    int summation;       // fluid density from Eq. 6 at each evaluation
     T h, inv_h, H2lo, H2hi, R15lo, R15hi;
     T RL2hi;             // squared neighbour-list radius (2h + skin)^2, widened
     T sc;
@@ -223,6 +224,12 @@ void launch_build(int lanes, bool with_colour, const PhysT<T> &P, const Grid &g,
 template <class T>
 void launch_colour(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
                    const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s);
+// Eq. 6 density of the fluid particles; rewrites their H1 records (and
+// stores rho - rho0 to drho_out when given).
+template <class T>
+void launch_density(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
+                    const Hot<T> &hot, const T *mass, const uint8_t *type, T *drho_out, int cap,
+                    cudaStream_t s);
 template <class T>
 void launch_normal(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
                    const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s);

@@ -253,6 +253,51 @@ k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// Eq. 6: summation density of the fluid particles (over the list), in place of
+// the integrated Eq. 7.  Rewrites the particle's record H1 = (V, rho, P/rho^2,
+// c) and, when drho_out is given, stores rho - rho0.  Neighbour masses come
+// from the mass array (zero for particles deleted since the build), so no
+// record that this kernel rewrites is read.
+// ---------------------------------------------------------------------------
+template <class T> struct DensityRec {    // offsets and mass
+    V4<T> x;
+};
+
+template <class T, int K, int G>
+__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
+k_density(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot,
+          const T *__restrict__ mass, const uint8_t *__restrict__ type, T *__restrict__ drho_out) {
+    unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned i = gt / G, sub = gt % G;
+    bool fluid = i < (unsigned)sc->nsrt && type[i] == T_FLUID;
+    const V4<T> *__restrict__ H0 = hot.H0;
+    T sum = T(0);
+    if (fluid) {
+        V4<T> ha = H0[i];
+        for_list<G, SPH_CH_COLOUR, T>(
+            P, nl, hot.pos, i, sub, ha.x, ha.y,
+            [&](unsigned b) {
+                DensityRec<T> r;
+                V4<T> h0 = H0[b];
+                r.x = mk4<T>(h0.x, h0.y, type[b] == T_DEAD ? T(0) : mass[b], T(0));
+                return r;
+            },
+            [&](unsigned, T, T, T r2, const DensityRec<T> &r) {
+                T q, iq;
+                q_of(r2, P.h, P.inv_h, q, iq);
+                sum += r.x.z * kernel_W<T, K>(P, q);
+            });
+    }
+    sum = group_sum<G>(sum);
+    if (fluid && sub == 0) {
+        T m = mass[i];
+        T dr = (sum + m * P.W0) - P.rho0;
+        hot.H1[i] = hot1<T>(P, dr, m);
+        if (drho_out) drho_out[i] = dr;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Eq. 14: colour at the half step (over the list)
 // ---------------------------------------------------------------------------
 template <class T, int K, int G>
@@ -532,10 +577,15 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
         T usx = v0.x + th * ax, usy = v0.y + th * ay;
         p1 = make_double2(p0.x + dt * (P.ufx_d + (double)usx), p0.y + dt * (P.ufy_d + (double)usy));
         v1 = mk2(v0.x + tdt * ax, v0.y + tdt * ay);
-        T y = tdt * drho - c0;          // compensated density update
-        T s = d0 + y;
-        c1 = (s - d0) - y;
-        d1 = s;
+        if (P.summation) {              // Eq. 6: the density of the half-step evaluation
+            d1 = hot.H1[i].y - P.rho0;
+            c1 = T(0);
+        } else {
+            T y = tdt * drho - c0;      // compensated density update
+            T s = d0 + y;
+            c1 = (s - d0) - y;
+            d1 = s;
+        }
         stx = tdt * (P.ufx + usx);
         sty = tdt * (P.ufy + usy);
     } else {
@@ -769,6 +819,20 @@ void launch_colour(int lanes, const PhysT<T> &P, const Scalars *sc, const NList 
 }
 
 template <class T>
+void launch_density(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
+                    const Hot<T> &hot, const T *mass, const uint8_t *type, T *drho_out, int cap,
+                    cudaStream_t s) {
+    with_lanes(lanes, [&](auto Gc) {
+        constexpr int G = decltype(Gc)::value;
+        int b = sweep_blocks(cap, G);
+        if (P.kernel == 1)
+            launch_k(k_density<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, mass, type, drho_out);
+        else
+            launch_k(k_density<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, mass, type, drho_out);
+    });
+}
+
+template <class T>
 void launch_normal(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
                    const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s) {
     with_lanes(lanes, [&](auto Gc) {
@@ -946,6 +1010,9 @@ void *decide_kernel() { return (void *)k_decide; }
                                   const NList &, const Csf<T> &, int, cudaStream_t);              \
     template void launch_colour<T>(int, const PhysT<T> &, const Scalars *, const NList &,         \
                                    const Hot<T> &, const Csf<T> &, int, cudaStream_t);            \
+    template void launch_density<T>(int, const PhysT<T> &, const Scalars *, const NList &,        \
+                                    const Hot<T> &, const T *, const uint8_t *, T *, int,         \
+                                    cudaStream_t);                                                \
     template void launch_normal<T>(int, const PhysT<T> &, const Scalars *, const NList &,         \
                                    const Hot<T> &, const Csf<T> &, int, cudaStream_t);            \
     template void launch_forces<T>(int, int, const PhysT<T> &, const Grid &, const Inflow &,     \

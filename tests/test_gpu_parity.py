@@ -373,3 +373,51 @@ def test_cadence_change_takes_effect(sph):
     b2 = sim.rebuild_stats()[0]
     assert 3 <= b2 - b1 <= 12
     assert worst <= 0.15 * h * (1 + 1e-5)
+
+
+# ---------------------------------------------------------------------------
+# summation density (Eq. 6) in place of the integrated continuity equation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_summation_density_evaluation(sph, orc, prec):
+    st = wl.jittered_patch(seed=12, nx=40, ny=30, dx=0.02, vel=0.2, drho=0.004)
+    p = wl.test_params(dx=0.02, sigma=0.5, alpha=0.2, prec=prec, box=(-0.5, -0.5, 1.3, 1.1))
+    p["density"] = "summation"
+    case = _case_from_state(p, st)
+    sim = sph.Simulation(case)
+    sim.evaluate()
+    g = sim.state()
+    d = orc.derive(p)
+    rho = orc.summation_density(d, st)
+    ev = orc.evaluate(d, dict(st, rho=rho))
+    assert rel_l2(g["rho"], rho) < _tol(prec, 1e-6)          # the density the GPU used
+    assert rel_l2_vec(g["ax"], g["ay"], ev["ax"], ev["ay"]) < _tol(prec, 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("lanes,cadence", [(4, 1), (2, 4)])
+def test_summation_density_trajectory(sph, orc, prec, lanes, cadence):
+    st = wl.jittered_patch(seed=13, nx=40, ny=30, dx=0.02, vel=0.2, drho=0.004)
+    p = wl.test_params(dx=0.02, sigma=0.5, alpha=0.2, prec=prec, dt_fixed=2e-4,
+                       box=(-0.5, -0.5, 1.3, 1.1))
+    p["density"] = "summation"
+    p["skin_over_h"] = 0.3
+    case = _case_from_state(p, st)
+    sim = sph.Simulation(case)
+    sim.set_tuning(lanes, cadence)
+    osim = oracle_sim(orc, case)
+    sim.run(60)
+    osim.run(60)
+    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4)
+
+
+def test_summation_density_jet_with_inflow(sph, orc):
+    case = wl.jet(seed=6, dx=1.0 / 20, length=6.0, Re=200, We=20)
+    case["params"]["density"] = "summation"
+    case["params"]["dt_fixed"] = 1e-3
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.run(60)
+    osim.run(60)
+    assert sim.time()["deleted"] == osim.deleted
+    _compare_states(sim.state(), osim.st, "fp32", 1e-4, 1e-4, 1e-4)

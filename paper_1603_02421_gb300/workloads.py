@@ -157,7 +157,7 @@ def jet_params(Re, We, D=1.0, U=1.0, rho0=1000.0, dx=None, kernel="wendland",
 
 def jet(seed=0, Re=200.0, We=20.0, D=1.0, U=1.0, rho0=1000.0, dx=None,
         length=60.0, kernel="wendland", prec="fp32", amp=0.01, layers=3,
-        fill=None, capacity_factor=1.3, Fr=None, drho=0.0):
+        fill=None, capacity_factor=1.3, Fr=None, drho=0.0, nozzle=0.0):
     """Planar jet of width D issuing at x = 0 along +x (Sec. 3-2 setting,
     inflow buffer in place of the paper's tank).  The strip [0, fill*D) is
     prefilled on a dx lattice with u = u_in(-x/U), the velocity the inflow
@@ -165,7 +165,12 @@ def jet(seed=0, Re=200.0, We=20.0, D=1.0, U=1.0, rho0=1000.0, dx=None,
     adds gravity along the jet axis (the paper's jets fall from a tank);
     None means no gravity.  drho > 0 adds a seeded uniform density
     perturbation of relative amplitude drho (the density fluctuations of a
-    running weakly-compressible flow; 0 gives the uniform start state)."""
+    running weakly-compressible flow; 0 gives the uniform start state).
+    nozzle > 0 adds a nozzle of that length (in D) upstream of x = 0: walls of
+    repulsive boundary particles (Eq. 29) at y = +-D/2, spacing dx/2, normals
+    into the channel; the inflow buffer then enters at the nozzle inlet
+    x = -nozzle D and the channel is prefilled like the strip (the paper's
+    jets leave a tank through a nozzle of aspect ratio 15)."""
     rng = np.random.default_rng(seed)
     p = jet_params(Re, We, D=D, U=U, rho0=rho0, dx=dx, kernel=kernel, prec=prec,
                    length=length, layers=layers)
@@ -175,19 +180,29 @@ def jet(seed=0, Re=200.0, We=20.0, D=1.0, U=1.0, rho0=1000.0, dx=None,
     fill = length if fill is None else fill
     k = rng.uniform(0.5, 1.0) / D
     phase = 0.0
-    # whole lattice columns inside [0, fill): the last column centre stays
+    x0 = -nozzle * D
+    if nozzle > 0:
+        p["xmin"] = x0 - (layers + 5) * dx
+    # whole lattice columns inside [x0, fill): the last column centre stays
     # below the box end even when fill is not a whole number of spacings
-    nxp = int(math.floor(fill * D / dx + 1e-6))
+    nxp = int(math.floor((fill * D - x0) / dx + 1e-6))
     nyp = int(round(D / dx))
-    x, y = lattice(0.0, -0.5 * D, nxp, nyp, dx)
+    x, y = lattice(x0, -0.5 * D, nxp, nyp, dx)
     u = U * (1.0 + amp * np.sin(k * U * (-x / U) + phase))
     rho = rho0 * (1.0 + rng.uniform(-drho, drho, len(x))) if drho > 0 else None
     fluid = _fluid(x, y, u=u, rho=rho, rho0=rho0, dx=dx)
     p["capacity"] = int(capacity_factor * (len(x) + layers * nyp)) + 1024
-    inflow = dict(x_exit=0.0, y0=-0.5 * D, y1=0.5 * D, U=U, amp=amp, k=k, phase=phase,
+    inflow = dict(x_exit=x0, y0=-0.5 * D, y1=0.5 * D, U=U, amp=amp, k=k, phase=phase,
                   layers=layers)
-    return {"name": "jet", "params": p, "fluid": fluid, "boundary": None, "inflow": inflow,
-            "D": D}
+    boundary = None
+    if nozzle > 0:
+        db = 0.5 * dx
+        top = _segment((x0, 0.5 * D), (0.0, 0.5 * D), db, (0.0, -1.0))
+        bot = _segment((x0, -0.5 * D), (0.0, -0.5 * D), db, (0.0, 1.0))
+        boundary = {"x": np.concatenate([top[0], bot[0]]), "y": np.concatenate([top[1], bot[1]]),
+                    "nx": np.concatenate([top[2], bot[2]]), "ny": np.concatenate([top[3], bot[3]])}
+    return {"name": "jet", "params": p, "fluid": fluid, "boundary": boundary, "inflow": inflow,
+            "D": D, "nozzle": nozzle * D}
 
 
 # --------------------------------------------------------------------------

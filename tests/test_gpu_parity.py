@@ -421,3 +421,31 @@ def test_summation_density_jet_with_inflow(sph, orc):
     osim.run(60)
     assert sim.time()["deleted"] == osim.deleted
     _compare_states(sim.state(), osim.st, "fp32", 1e-4, 1e-4, 1e-4)
+
+
+# ---------------------------------------------------------------------------
+# paper-faithful variants: nozzle walls, inviscid jet
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_nozzle_jet_trajectory(sph, orc, prec):
+    # inflow buffer -> nozzle with repulsive walls (Eq. 29) -> free jet
+    case = wl.jet(seed=7, dx=1.0 / 20, length=4.0, nozzle=2.0, Re=200, We=20, prec=prec)
+    case["params"]["dt_fixed"] = 1e-3
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.run(80)
+    osim.run(80)
+    assert sim.time()["deleted"] == osim.deleted
+    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4)
+
+
+def test_inviscid_jet_trajectory(sph, orc):
+    # alpha = 0: the inviscid setting of the paper's Fig. 8 comparison
+    case = wl.jet(seed=8, dx=1.0 / 20, length=6.0, Re=200, We=20)
+    case["params"]["alpha"] = 0.0
+    case["params"]["dt_fixed"] = 1e-3
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.run(80)
+    osim.run(80)
+    _compare_states(sim.state(), osim.st, "fp32", 1e-4, 1e-4, 1e-4)

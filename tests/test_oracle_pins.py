@@ -435,3 +435,20 @@ def test_summation_mode_step_keeps_the_half_step_density(orc):
     assert np.allclose(sim.st["rho"], orc.summation_density(d, mid), rtol=1e-14, atol=0)
     assert not np.allclose(sim.st["rho"], rho_n)      # the density follows the positions
     assert np.isfinite(ev["ax"]).all()
+
+
+def test_nozzle_walls_confine_the_jet(orc):
+    # the repulsive walls of the nozzle (Eq. 29) keep the fluid inside the
+    # channel |y| < D/2 while it flows through it
+    case = wl.jet(seed=3, dx=1.0 / 10, length=3.0, nozzle=2.0, Re=200, We=20)
+    case["params"]["dt_fixed"] = 2e-3
+    sim = orc.OracleSim(case["params"], case["fluid"], case["boundary"])
+    inf = case["inflow"]
+    sim.add_inflow(inf["x_exit"], inf["y0"], inf["y1"], inf["U"], inf["amp"], inf["k"],
+                   inf["phase"], inf["layers"])
+    sim.run(150)
+    st = sim.st
+    inside = (st["x"] > -2.0 + 0.1) & (st["x"] < -0.1)
+    assert inside.sum() > 100
+    assert np.all(np.abs(st["y"][inside]) < 0.5)
+    assert np.all(np.isfinite(st["u"]))

@@ -171,3 +171,34 @@ def test_uniform_start_state_surface_tension_only(sph, orc, dx, length, label):
     ea = rel_l2_vec(g["ax"][keep], g["ay"][keep], ev["ax"][keep], ev["ay"][keep])
     report(case=label + "_uniform_start", prec="fp32", accel=ea)
     assert ea < 5e-5
+
+
+def test_breakup_length_grows_with_weber_number(sph, orc):
+    # context for Eq. 37 (L/D = 13 sqrt(We)(1 + 3 Oh)): a weaker surface
+    # tension (larger We) gives a longer intact jet.  Means over 3 seeds at
+    # fixed simulated times after the first breakup, as in the 5-seed test.
+    times = [2.0 + 0.1 * k for k in range(31)]
+
+    def mean_L(We):
+        Ls = []
+        for seed in range(3):
+            case = wl.jet(seed=seed, Re=100, We=We, dx=1.0 / 10, length=16.0, amp=0.05, Fr=1.0)
+            case["params"]["skin_over_h"] = 0.3
+            g = sph.Simulation(case)
+            g.set_tuning(4, 4)
+            out = []
+            for tk in times:
+                while g.time()["t"] < tk:
+                    g.step()
+                L, broken = g.breakup_length()
+                if broken or out:
+                    out.append(L)
+            g.close()
+            assert out, "no breakup within the run"
+            Ls.append(float(np.mean(out)))
+        return float(np.mean(Ls))
+
+    L2, L20 = mean_L(2.0), mean_L(20.0)
+    report(case="breakup_vs_We", We=[2.0, 20.0], L_over_D=[L2, L20],
+           eq37_R_based=[orc.correlation_LD(1.0, 50.0), orc.correlation_LD(10.0, 50.0)])
+    assert L2 < L20

@@ -162,7 +162,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tune", default="auto",
-                    help="auto (autotuner), or LANES,CADENCE (e.g. 4,1 for every-step cell builds)")
+                    help="auto (autotuner), or LANES,CADENCE[,gated|conditional] (e.g. 4,1 for "
+                         "every-step cell builds; the third field picks how a step at cadence > 1 "
+                         "chooses its start on the device, default gated)")
     ap.add_argument("--skin", type=float, default=0.3, help="skin / h of the cell search")
     return ap.parse_args()
 
@@ -344,9 +346,11 @@ def main():
     ctx = sim.ctx
     if args.tune == "auto":
         lanes, cadence, _ = binding.sph_autotune(ctx, 24)
+        form = binding.sph_get_start_form(ctx)
     else:
-        lanes, cadence = (int(v) for v in args.tune.split(","))
+        lanes, cadence, form = parse_tune(args.tune)
         binding.sph_set_tuning(ctx, lanes, cadence)
+        binding.sph_set_start_form(ctx, form)
     per_full, per_reuse, per_breakup = binding.sph_kernel_counts(ctx)
     has_inflow = case.get("inflow") is not None
 
@@ -444,7 +448,7 @@ def main():
     # ---- end to end through the public API with host buffers -------------
     e2e = None
     if rank == 0:
-        e2e = end_to_end(binding, case, stream, local, K=min(K, 100), tuning=(lanes, cadence))
+        e2e = end_to_end(binding, case, stream, local, K=min(K, 100), tuning=(lanes, cadence, form))
 
     # ---- CPU baseline (oracle) on a bounded sample -----------------------
     cpu = None
@@ -466,7 +470,8 @@ def main():
             "config": {"workload": args.workload + ": " + desc,
                        "particles_mean": n_mean, "parallelism": "replicas (one jet per GPU)",
                        "l2": "flushed between timed steps (256 MiB write)",
-                       "tuning": {"lanes": lanes, "cadence": cadence, "skin_over_h": args.skin,
+                       "tuning": {"lanes": lanes, "cadence": cadence,
+                                  "start_form": FORM_NAMES[form], "skin_over_h": args.skin,
                                   "chosen_by": "autotuner" if args.tune == "auto" else "flag",
                                   "rebuild_fraction": full_steps / K},
                        "breakup_every": BREAKUP_EVERY if has_inflow else None,
@@ -488,6 +493,18 @@ def main():
         dist.destroy_process_group()
 
 
+def parse_tune(text):
+    """'LANES,CADENCE[,gated|conditional]' -> (lanes, cadence, start form)."""
+    from paper_1603_02421_gb300 import binding
+    parts = text.split(",")
+    forms = {"gated": binding.START_GATED, "conditional": binding.START_CONDITIONAL}
+    form = forms[parts[2]] if len(parts) > 2 else binding.START_GATED
+    return int(parts[0]), int(parts[1]), form
+
+
+FORM_NAMES = {0: "gated", 1: "conditional"}
+
+
 def end_to_end(binding, case, stream, local, K, tuning):
     """Particle-steps/s through the public C ABI with host buffers: upload the
     state from pinned host memory (sph_set_state), K x sph_step (each reads
@@ -495,7 +512,8 @@ def end_to_end(binding, case, stream, local, K, tuning):
     import torch
     sim = binding.Simulation(case, stream=stream.cuda_stream, device=local)
     ctx = sim.ctx
-    binding.sph_set_tuning(ctx, *tuning)
+    binding.sph_set_tuning(ctx, *tuning[:2])
+    binding.sph_set_start_form(ctx, tuning[2])
     st = binding.sph_get_state(ctx)
     n = len(st["x"])
     pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
@@ -536,10 +554,12 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local):
     ens = binding.Ensemble(sims, stream=stream.cuda_stream)
     if args.tune == "auto":
         lanes, cadence, _ = ens.autotune(8)
+        form = sims[0].start_form()
     else:
-        lanes, cadence = (int(v) for v in args.tune.split(","))
+        lanes, cadence, form = parse_tune(args.tune)
         for sm in sims:
             sm.set_tuning(lanes, cadence)
+            sm.set_start_form(form)
     counts = [binding.sph_kernel_counts(sm.ctx) for sm in sims]
     # interacting pairs per particle (the same h/dx in every member)
     n_first = sims[0].time()["n"]
@@ -651,7 +671,8 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local):
                        "members_per_gpu": len(sims), "particles_total": 0.5 * (n0 + n1),
                        "parallelism": "members round-robin over ranks (no exchange)",
                        "l2": "inputs larger than L2 (all members resident, several GB)",
-                       "tuning": {"lanes": lanes, "cadence": cadence, "skin_over_h": args.skin,
+                       "tuning": {"lanes": lanes, "cadence": cadence,
+                                  "start_form": FORM_NAMES[form], "skin_over_h": args.skin,
                                   "chosen_by": "ensemble autotuner" if args.tune == "auto"
                                   else "flag"},
                        "plain_value": plain_value,

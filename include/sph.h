@@ -226,10 +226,31 @@ sph_status sph_profile_report(sph_ctx *ctx, int cap, int *n, const char **names,
 sph_status sph_set_tuning(sph_ctx *ctx, int lanes, int cadence);
 sph_status sph_get_tuning(sph_ctx *ctx, int *lanes, int *cadence);
 
+/* How a step at cadence > 1 picks its start -- rebuild the cells and lists,
+ * or refresh the records on the last build -- on the device, from the flag
+ * the step before left, with nothing returned to the host in between.  Both
+ * forms launch the same kernels on the same data, so results are identical:
+ *   SPH_START_GATED        the step graph holds both starts in one line; each
+ *                          start kernel returns at once when its start is not
+ *                          the one taken (every kernel of both starts is
+ *                          launched, each skipped one costing about 1 us and
+ *                          a pass over its blocks);
+ *   SPH_START_CONDITIONAL  a one-thread kernel sets a CUDA-graph IF node that
+ *                          runs only the taken start (about 10 us per step for
+ *                          the node, whatever the particle count).
+ * The gated form is faster for one context of up to a few 1e5 particles, the
+ * conditional one for large contexts and many-member ensembles, whose graphs
+ * are bound by the number of launches; sph_autotune and
+ * sph_ensemble_autotune time both.  Default: SPH_START_GATED. */
+typedef enum { SPH_START_GATED = 0, SPH_START_CONDITIONAL = 1 } sph_start_form;
+sph_status sph_set_start_form(sph_ctx *ctx, int form);
+sph_status sph_get_start_form(sph_ctx *ctx, int *form);
+
 /* Autotuner: times trial_steps steps for each lanes in {1, 2, 4, 8} and cadence
- * in {1, 2, 4, 8} from a copy of the current state (rejecting settings that
- * trip SPH_ERR_SKIN), restores the state, and keeps the fastest setting.
- * Outputs (nullable): the chosen lanes, cadence and its ms per step. */
+ * in {1, 2, 4, 8} (at cadence > 1 in both start forms) from a copy of the
+ * current state (rejecting settings that trip SPH_ERR_SKIN), restores the
+ * state, and keeps the fastest setting.  Outputs (nullable): the chosen
+ * lanes, cadence and its ms per step; sph_get_start_form gives the form. */
 sph_status sph_autotune(sph_ctx *ctx, int trial_steps, int *lanes, int *cadence,
                         double *ms_per_step);
 
@@ -243,10 +264,12 @@ sph_status sph_get_rebuild_stats(sph_ctx *ctx, long long *builds, double *disp_m
 
 /* Number of device kernels (memsets excluded) launched at the current
  * settings by a step that rebuilds the cells and lists, by a step that reuses
- * the last build (equal to the first at cadence 1, where every step
- * rebuilds), and by one breakup-length evaluation.  At cadence > 1 each step
- * also runs the one-thread kernel that decides the next step's kind, which
- * both step counts include.  Any pointer may be NULL. */
+ * the last build, and by one breakup-length evaluation.  At cadence 1 every
+ * step rebuilds.  At cadence > 1 in the gated start form every step launches
+ * the kernels of both starts (those of the start not taken return at once),
+ * so the two step counts are equal; in the conditional form each step also
+ * runs the one-thread kernel that sets the IF node.  Any pointer may be
+ * NULL. */
 sph_status sph_kernel_counts(sph_ctx *ctx, int *per_full_step, int *per_reused_step,
                              int *per_breakup);
 
@@ -307,10 +330,11 @@ sph_status sph_ensemble_run(sph_ensemble *e, long long nsteps);
  * the member's own sph_last_error holds the description. */
 sph_status sph_ensemble_sync(sph_ensemble *e, int *bad_member);
 
-/* Autotuner over one (lanes, cadence) for all members: times trial_steps
- * ensemble steps for lanes in {1, 2, 4, 8} and cadence in {1, 2, 4, 8} from
- * copies of the members' states (rejecting settings that trip SPH_ERR_SKIN),
- * restores the states and keeps the fastest setting.  Outputs nullable. */
+/* Autotuner over one (lanes, cadence, start form) for all members: times
+ * trial_steps ensemble steps for lanes in {1, 2, 4, 8} and cadence in
+ * {1, 2, 4, 8} (at cadence > 1 in both start forms) from copies of the
+ * members' states (rejecting settings that trip SPH_ERR_SKIN), restores the
+ * states and keeps the fastest setting.  Outputs nullable. */
 sph_status sph_ensemble_autotune(sph_ensemble *e, int trial_steps, int *lanes, int *cadence,
                                  double *ms_per_step);
 

@@ -26,6 +26,7 @@ STATUS = {0: "SPH_OK", -1: "SPH_ERR_ARG", -2: "SPH_ERR_OOM", -3: "SPH_ERR_CAPACI
           -4: "SPH_ERR_CUDA", -5: "SPH_ERR_NONFINITE", -6: "SPH_ERR_TIMEOUT",
           -7: "SPH_ERR_STATE", -8: "SPH_ERR_SKIN"}
 FLUID, BOUNDARY, BUFFER = 0, 1, 2
+START_GATED, START_CONDITIONAL = 0, 1       # sph_start_form
 KERNELS = {"cubic": 0, "wendland": 1}
 PRECISIONS = {"fp32": 0, "fp64": 1}
 
@@ -113,6 +114,8 @@ _SIGS = {
                            ctypes.c_int),
     "sph_run_async": ([_CTX, ctypes.c_longlong], ctypes.c_int),
     "sph_set_tuning": ([_CTX, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "sph_set_start_form": ([_CTX, ctypes.c_int], ctypes.c_int),
+    "sph_get_start_form": ([_CTX, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sph_get_tuning": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
                        ctypes.c_int),
     "sph_autotune": ([_CTX, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -317,6 +320,18 @@ def sph_get_tuning(ctx):
     return a.value, b.value
 
 
+def sph_set_start_form(ctx, form):
+    """form: START_GATED or START_CONDITIONAL (how a step at cadence > 1 picks
+    its start on the device; the results are identical)."""
+    _check(ctx, lib().sph_set_start_form(ctx, int(form)))
+
+
+def sph_get_start_form(ctx):
+    f = ctypes.c_int()
+    _check(ctx, lib().sph_get_start_form(ctx, ctypes.byref(f)))
+    return f.value
+
+
 def sph_autotune(ctx, trial_steps=20):
     a, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(ctx, lib().sph_autotune(ctx, int(trial_steps), ctypes.byref(a), ctypes.byref(b),
@@ -436,6 +451,12 @@ class Simulation:
 
     def tuning(self):
         return sph_get_tuning(self.ctx)
+
+    def set_start_form(self, form):
+        sph_set_start_form(self.ctx, form)
+
+    def start_form(self):
+        return sph_get_start_form(self.ctx)
 
     def autotune(self, trial_steps=20):
         return sph_autotune(self.ctx, trial_steps)

@@ -78,10 +78,11 @@ struct sph_ctx {
 
     // tuning: lanes per particle in the pair sweeps, longest cell-build cadence
     int lanes = 4, cadence = 1;
+    int start_form = SPH_START_GATED;   // how a step at cadence > 1 picks its start
     bool force_full = true;      // host: the next step must rebuild the cells
     bool hsc_fresh = false;      // hsc mirrors the device scalars (synchronised)
 
-    // step graph with a device-decided rebuild (IF node: rebuild / reuse)
+    // step graph whose start (rebuild / reuse) is chosen on the device
     cudaGraph_t cgraph = nullptr;
     cudaGraphExec_t cexec = nullptr;
     bool no_ticks = false;
@@ -283,19 +284,20 @@ static void tick(sph_ctx *c, const char *name) {
 }
 
 // hash -> sort -> cell ranges -> gather into cell order (evaluation-n records)
-template <class T> static const uint32_t *enqueue_sort(sph_ctx *c) {
+template <class T> static const uint32_t *enqueue_sort(sph_ctx *c, int gate = GATE_ALWAYS) {
     const PhysT<T> &P = Ops<T>::phys(c);
     State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
     tick(c, "cell_sort");
-    launch_cell_sort<T>(c->grid, raw, c->sc, c->cs, c->cap, c->stream);
+    launch_cell_sort<T>(c->grid, raw, c->sc, c->cs, c->cap, c->stream, gate);
     tick(c, "reorder");
-    launch_reorder<T>(P, c->grid, c->sc, c->cs, raw, srt, hot_n<T>(c), c->cap, c->stream);
+    launch_reorder<T>(P, c->grid, c->sc, c->cs, raw, srt, hot_n<T>(c), c->cap, c->stream, gate);
     const uint32_t *key = c->cs.key;
     return key;
 }
 
 // List build of evaluation n, fused with its colour when CSF is on.
-template <class T> static void enqueue_build(sph_ctx *c, const uint32_t *key) {
+template <class T>
+static void enqueue_build(sph_ctx *c, const uint32_t *key, int gate = GATE_ALWAYS) {
     const PhysT<T> &P = Ops<T>::phys(c);
     tick(c, "list_colour");
     // the list build walks ~61 candidates of the 3x3 cells per particle; it
@@ -303,23 +305,24 @@ template <class T> static void enqueue_build(sph_ctx *c, const uint32_t *key) {
     // with Eq. 6 densities the colour needs the summed volumes, so it runs
     // after the density sweep instead of inside the list build
     launch_build<T>(std::max(c->lanes, 4), P.csf != 0 && !P.summation, P, c->grid, c->sc,
-                    c->cellSE, key, hot_n<T>(c), c->nl, csf_of<T>(c), c->cap, c->stream);
+                    c->cellSE, key, hot_n<T>(c), c->nl, csf_of<T>(c), c->cap, c->stream, gate);
 }
 
 // Eq. 6 densities of the records `hot` (a no-op with Eq. 7), then, when the
 // colour was not computed with the list, the colour of those records.
 // drho_out: where the state keeps the density (null at the half step).
 template <class T>
-static void enqueue_density(sph_ctx *c, const Hot<T> &hot, T *drho_out, bool colour) {
+static void enqueue_density(sph_ctx *c, const Hot<T> &hot, T *drho_out, bool colour,
+                            int gate = GATE_ALWAYS) {
     const PhysT<T> &P = Ops<T>::phys(c);
     if (!P.summation) return;
     State<T> srt = state_of<T>(c->srt);
     tick(c, "density");
     launch_density<T>(c->lanes, P, c->sc, c->nl, hot, srt.mass, srt.type, drho_out, c->cap,
-                      c->stream);
+                      c->stream, gate);
     if (colour && P.csf) {
         tick(c, "colour");
-        launch_colour<T>(c->lanes, P, c->sc, c->nl, hot, csf_of<T>(c), c->cap, c->stream);
+        launch_colour<T>(c->lanes, P, c->sc, c->nl, hot, csf_of<T>(c), c->cap, c->stream, gate);
     }
 }
 
@@ -334,23 +337,26 @@ template <class T> static void enqueue_normal(sph_ctx *c, const Hot<T> &hot) {
 // list (with the colour of evaluation n).  Reuse: the particles keep the
 // order, cells and lists of the last rebuild (exact while no particle has
 // moved more than skin/2 since, which the kernels check); the records of
-// evaluation n are recomputed in place.
-template <class T> static void enqueue_cells(sph_ctx *c, bool full) {
+// evaluation n are recomputed in place.  gate: GATE_ALWAYS when the host
+// chose the start; otherwise the start's kernels run only on the steps whose
+// device flag selects it.
+template <class T> static void enqueue_cells(sph_ctx *c, bool full, int gate = GATE_ALWAYS) {
     const PhysT<T> &P = Ops<T>::phys(c);
     State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
     Hot<T> hn = hot_n<T>(c);
     const uint32_t *key = c->cs.key;
     if (full) {
-        enqueue_sort<T>(c);
-        enqueue_build<T>(c, key);
-        enqueue_density<T>(c, hn, srt.drho, true);
+        enqueue_sort<T>(c, gate);
+        enqueue_build<T>(c, key, gate);
+        enqueue_density<T>(c, hn, srt.drho, true, gate);
     } else {
         tick(c, "refresh");
-        launch_refresh<T>(P, c->grid, c->sc, key, raw, srt, hn, c->cap, c->stream);
-        enqueue_density<T>(c, hn, srt.drho, false);
+        launch_refresh<T>(P, c->grid, c->sc, key, raw, srt, hn, c->cap, c->stream, gate);
+        enqueue_density<T>(c, hn, srt.drho, false, gate);
         if (P.csf) {
             tick(c, "colour");
-            launch_colour<T>(c->lanes, P, c->sc, c->nl, hn, csf_of<T>(c), c->cap, c->stream);
+            launch_colour<T>(c->lanes, P, c->sc, c->nl, hn, csf_of<T>(c), c->cap, c->stream,
+                             gate);
         }
     }
 }
@@ -872,31 +878,35 @@ sph_status sph_evaluate(sph_ctx *c) {
     return s;
 }
 
-// Captures the step graphs: [0] rebuild and [1] reuse (chosen by the host,
-// used while profiling, since event nodes may not sit inside conditional
-// bodies), and the graph that decides on the device: a kernel sets an IF
-// node's condition from the flag the previous step left, the IF node runs
-// the rebuild or the reuse start, then the rest of the step follows.
 // Appends one step of context c to graph g as a branch of its own (no
 // dependencies on nodes already in g).  At cadence 1 the branch is the
-// rebuilding step.  Otherwise it decides on the device: a one-thread kernel
-// sets an IF node's condition from the flag the previous step left, the IF
-// node runs the rebuild or the reuse start, then the rest of the step
-// follows.
+// rebuilding step.  Otherwise the start (rebuild or reuse of the last build)
+// is picked on the device from the flag the previous step left, in one of two
+// forms with identical results:
+//   gated: both starts one after the other in one straight line, each kernel
+//     returning at once when its start is not the one taken (no graph node
+//     beyond the kernels; every kernel of both starts is launched);
+//   conditional: a one-thread kernel sets an IF node's condition, the node
+//     runs the rebuild or the reuse start (only the taken start's kernels are
+//     launched, but the node itself costs about 10 us per step on GB300).
+// The rest of the step follows either form.
 static sph_status append_step(sph_ctx *c, cudaGraph_t g) {
     c->no_ticks = true;
     struct Untick {
         sph_ctx *c;
         ~Untick() { c->no_ticks = false; }
     } untick{c};
-    if (c->cadence <= 1) {
+    if (c->cadence <= 1 || c->start_form == SPH_START_GATED) {
         CK(cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0,
                                          cudaStreamCaptureModeThreadLocal), "capture step");
+        bool gated = c->cadence > 1;
         if (c->tsz == 4) {
-            enqueue_cells<float>(c, true);
+            enqueue_cells<float>(c, true, gated ? GATE_FULL : GATE_ALWAYS);
+            if (gated) enqueue_cells<float>(c, false, GATE_REUSE);
             enqueue_rest<float>(c);
         } else {
-            enqueue_cells<double>(c, true);
+            enqueue_cells<double>(c, true, gated ? GATE_FULL : GATE_ALWAYS);
+            if (gated) enqueue_cells<double>(c, false, GATE_REUSE);
             enqueue_rest<double>(c);
         }
         CK(cudaStreamEndCapture(c->stream, &g), "end capture step");
@@ -937,7 +947,8 @@ static sph_status append_step(sph_ctx *c, cudaGraph_t g) {
 }
 
 // The two host-chosen step graphs (rebuild / reuse; the profiling path, and
-// every step at cadence 1) and the graph that decides on the device.
+// every step at cadence 1) and the step graph whose start is chosen on the
+// device.
 static sph_status ensure_graph(sph_ctx *c) {
     if (!c->graph_dirty && c->gexec[0] && c->gexec[1] && c->cexec) return SPH_OK;
     for (int k = 0; k < 2; ++k) {
@@ -954,7 +965,7 @@ static sph_status ensure_graph(sph_ctx *c) {
     CK(cudaGraphCreate(&c->cgraph, 0), "graph create");
     sph_status s = append_step(c, c->cgraph);
     if (s) return s;
-    CK(cudaGraphInstantiate(&c->cexec, c->cgraph, 0), "instantiate conditional graph");
+    CK(cudaGraphInstantiate(&c->cexec, c->cgraph, 0), "instantiate step graph");
     c->graph_dirty = false;
     return SPH_OK;
 }
@@ -962,7 +973,7 @@ static sph_status ensure_graph(sph_ctx *c) {
 static sph_status launch_step_graph(sph_ctx *c) {
     if (c->prof || c->cadence <= 1) {
         // host-chosen graphs: while profiling, and for cadence 1, where every
-        // step rebuilds and the device decision would only add its overhead
+        // step rebuilds and the gated reuse kernels would only add overhead
         bool full = c->cadence <= 1 ? true : host_next_is_full(c);
         if (c->cadence <= 1) { c->force_full = false; c->hsc_fresh = false; }
         CK(cudaGraphLaunch(c->gexec[full ? 0 : 1], c->stream), "graph launch");
@@ -1287,6 +1298,21 @@ sph_status sph_get_tuning(sph_ctx *c, int *lanes, int *cadence) {
     return SPH_OK;
 }
 
+sph_status sph_set_start_form(sph_ctx *c, int form) {
+    if (!c) return SPH_ERR_ARG;
+    if (form != SPH_START_GATED && form != SPH_START_CONDITIONAL)
+        return fail(c, SPH_ERR_ARG, "start form must be SPH_START_GATED or SPH_START_CONDITIONAL");
+    if (form != c->start_form) mark_graph_dirty(c);
+    c->start_form = form;
+    return SPH_OK;
+}
+
+sph_status sph_get_start_form(sph_ctx *c, int *form) {
+    if (!c) return SPH_ERR_ARG;
+    if (form) *form = c->start_form;
+    return SPH_OK;
+}
+
 // Copies of the raw state and scalars, to run trial steps and come back.
 static sph_status snapshot(sph_ctx *c, bool restore) {
     size_t ts = c->tsz;
@@ -1328,7 +1354,7 @@ sph_status sph_autotune(sph_ctx *c, int trial_steps, int *lanes, int *cadence, d
                     c->err.c_str());
     }
     const int L[4] = {1, 2, 4, 8}, K[4] = {1, 2, 4, 8};
-    int bestL = c->lanes, bestK = c->cadence;
+    int bestL = c->lanes, bestK = c->cadence, bestF = c->start_form;
     double best = 1e300;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
@@ -1337,22 +1363,28 @@ sph_status sph_autotune(sph_ctx *c, int trial_steps, int *lanes, int *cadence, d
     c->prof = false;
     for (int a = 0; a < 4; ++a) {
         for (int b = 0; b < 4; ++b) {
-            s = snapshot(c, true);
-            if (!s) s = sph_set_tuning(c, L[a], K[b]);
-            if (!s) s = sph_run_async(c, K[b]);          // warm: capture + one cycle
-            if (!s) s = sph_sync(c);
-            if (s == SPH_ERR_SKIN) continue;              // cadence too long for this flow
-            if (s) break;
-            cudaEventRecord(e0, c->stream);
-            s = sph_run_async(c, trial_steps);
-            cudaEventRecord(e1, c->stream);
-            if (!s) s = sph_sync(c);
-            if (s == SPH_ERR_SKIN) continue;
-            if (s) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            double per = ms / trial_steps;
-            if (per < best) { best = per; bestL = L[a]; bestK = K[b]; }
+            // both start forms where the device picks the start (cadence > 1)
+            for (int f = 0; f < (K[b] > 1 ? 2 : 1); ++f) {
+                int F = f == 0 ? SPH_START_GATED : SPH_START_CONDITIONAL;
+                s = snapshot(c, true);
+                if (!s) s = sph_set_tuning(c, L[a], K[b]);
+                if (!s) s = sph_set_start_form(c, F);
+                if (!s) s = sph_run_async(c, K[b]);      // warm: capture + one cycle
+                if (!s) s = sph_sync(c);
+                if (s == SPH_ERR_SKIN) break;             // cadence too long for this flow
+                if (s) break;
+                cudaEventRecord(e0, c->stream);
+                s = sph_run_async(c, trial_steps);
+                cudaEventRecord(e1, c->stream);
+                if (!s) s = sph_sync(c);
+                if (s == SPH_ERR_SKIN) break;
+                if (s) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                double per = ms / trial_steps;
+                if (per < best) { best = per; bestL = L[a]; bestK = K[b]; bestF = F; }
+            }
+            if (s && s != SPH_ERR_SKIN) break;
         }
         if (s && s != SPH_ERR_SKIN) break;
     }
@@ -1364,6 +1396,7 @@ sph_status sph_autotune(sph_ctx *c, int trial_steps, int *lanes, int *cadence, d
     if (r) return r;
     if (best >= 1e300) return fail(c, SPH_ERR_STATE, "no tuning candidate ran without error");
     r = sph_set_tuning(c, bestL, bestK);
+    if (!r) r = sph_set_start_form(c, bestF);
     if (r) return r;
     if (lanes) *lanes = bestL;
     if (cadence) *cadence = bestK;
@@ -1397,9 +1430,19 @@ sph_status sph_kernel_counts(sph_ctx *c, int *per_full_step, int *per_reused_ste
         reuse += 1;                        // Eq. 6 sweep
         rest += 1;                         // Eq. 6 sweep of the half step
     }
-    int decide = c->cadence > 1 ? 1 : 0;   // device-side choice of the next step's kind
-    if (per_full_step) *per_full_step = full + rest + decide;
-    if (per_reused_step) *per_reused_step = (c->cadence > 1 ? reuse : full) + rest + decide;
+    if (c->cadence <= 1) {
+        if (per_full_step) *per_full_step = full + rest;
+        if (per_reused_step) *per_reused_step = full + rest;
+    } else if (c->start_form == SPH_START_GATED) {
+        // every step launches the kernels of both starts; those of the start
+        // not taken return at once
+        if (per_full_step) *per_full_step = full + reuse + rest;
+        if (per_reused_step) *per_reused_step = full + reuse + rest;
+    } else {
+        // the one-thread kernel that sets the IF node, then the taken start
+        if (per_full_step) *per_full_step = 1 + full + rest;
+        if (per_reused_step) *per_reused_step = 1 + reuse + rest;
+    }
     if (per_breakup) *per_breakup = sort + 4;    // + union-find init, link, compress, reach
     return SPH_OK;
 }
@@ -1682,7 +1725,7 @@ sph_status sph_ensemble_autotune(sph_ensemble *e, int trial_steps, int *lanes, i
         if (s) return ens_fail(e, s, "snapshot: %s", c->err.c_str());
     }
     const int L[4] = {1, 2, 4, 8}, K[4] = {1, 2, 4, 8};
-    int bestL = e->m[0]->lanes, bestK = e->m[0]->cadence;
+    int bestL = e->m[0]->lanes, bestK = e->m[0]->cadence, bestF = e->m[0]->start_form;
     double best = 1e300;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     ECK(e, cudaEventCreate(&t0), "event");
@@ -1696,22 +1739,28 @@ sph_status sph_ensemble_autotune(sph_ensemble *e, int trial_steps, int *lanes, i
     };
     for (int a = 0; a < 4 && !s; ++a) {
         for (int b = 0; b < 4 && !s; ++b) {
-            s = restore_all();
-            for (size_t k = 0; k < e->m.size() && !s; ++k) s = sph_set_tuning(e->m[k], L[a], K[b]);
-            if (!s) s = sph_ensemble_run(e, K[b]);   // capture + one cycle
-            if (!s) s = sph_ensemble_sync(e, nullptr);
-            if (s == SPH_ERR_SKIN) { s = SPH_OK; continue; }
-            if (s) break;
-            cudaEventRecord(t0, e->stream);
-            s = sph_ensemble_run(e, trial_steps);
-            cudaEventRecord(t1, e->stream);
-            if (!s) s = sph_ensemble_sync(e, nullptr);
-            if (s == SPH_ERR_SKIN) { s = SPH_OK; continue; }
-            if (s) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, t0, t1);
-            double per = ms / trial_steps;
-            if (per < best) { best = per; bestL = L[a]; bestK = K[b]; }
+            for (int f = 0; f < (K[b] > 1 ? 2 : 1) && !s; ++f) {
+                int F = f == 0 ? SPH_START_GATED : SPH_START_CONDITIONAL;
+                s = restore_all();
+                for (size_t k = 0; k < e->m.size() && !s; ++k) {
+                    s = sph_set_tuning(e->m[k], L[a], K[b]);
+                    if (!s) s = sph_set_start_form(e->m[k], F);
+                }
+                if (!s) s = sph_ensemble_run(e, K[b]);   // capture + one cycle
+                if (!s) s = sph_ensemble_sync(e, nullptr);
+                if (s == SPH_ERR_SKIN) { s = SPH_OK; break; }
+                if (s) break;
+                cudaEventRecord(t0, e->stream);
+                s = sph_ensemble_run(e, trial_steps);
+                cudaEventRecord(t1, e->stream);
+                if (!s) s = sph_ensemble_sync(e, nullptr);
+                if (s == SPH_ERR_SKIN) { s = SPH_OK; break; }
+                if (s) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, t0, t1);
+                double per = ms / trial_steps;
+                if (per < best) { best = per; bestL = L[a]; bestK = K[b]; bestF = F; }
+            }
         }
     }
     cudaEventDestroy(t0);
@@ -1722,6 +1771,7 @@ sph_status sph_ensemble_autotune(sph_ensemble *e, int trial_steps, int *lanes, i
     if (best >= 1e300) return ens_fail(e, SPH_ERR_STATE, "no tuning candidate ran without error");
     for (sph_ctx *c : e->m) {
         r = sph_set_tuning(c, bestL, bestK);
+        if (!r) r = sph_set_start_form(c, bestF);
         if (r) return ens_fail(e, r, "%s", c->err.c_str());
     }
     if (lanes) *lanes = bestL;

@@ -122,6 +122,17 @@ struct Scalars {
 };
 constexpr int RED_SLOTS = 32;
 
+// Which start of a step a kernel belongs to.  A step graph holds both starts
+// (rebuild: sort + list build; reuse: refresh of the last build) in one
+// straight line; each start kernel reads the flag the previous step left in
+// sc->need_full and returns at once when its start is not the one taken.
+// Kernels launched outside such a graph run unconditionally.
+enum Gate : int { GATE_ALWAYS = -1, GATE_REUSE = 0, GATE_FULL = 1 };
+
+__device__ __forceinline__ bool gate_skips(int gate, const Scalars *sc) {
+    return gate >= 0 && (sc->need_full != 0) != (gate == GATE_FULL);
+}
+
 template <class T> struct State {
     double2 *pos;
     typename Vec<T>::v2 *vel;
@@ -199,7 +210,7 @@ struct NList {
 // sc->nsrt the live particle count.
 template <class T>
 void launch_cell_sort(const Grid &g, const State<T> &raw, Scalars *sc, CellSort &cs, int cap,
-                      cudaStream_t s);
+                      cudaStream_t s, int gate = GATE_ALWAYS);
 template <class T>
 void launch_pairs(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *cellSE,
                   const uint32_t *key, const Hot<T> &hot, const uint32_t *ids, unsigned *out_a,
@@ -215,21 +226,22 @@ void launch_breakup(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *
 template <class T>
 void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const CellSort &cs,
                     const State<T> &raw, const State<T> &srt, const Hot<T> &hot, int cap,
-                    cudaStream_t s);
+                    cudaStream_t s, int gate = GATE_ALWAYS);
 // Neighbour list of evaluation n; with_colour also sums the colour (Eq. 14).
 template <class T>
 void launch_build(int lanes, bool with_colour, const PhysT<T> &P, const Grid &g, Scalars *sc,
                   const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot, const NList &nl,
-                  const Csf<T> &csf, int cap, cudaStream_t s);
+                  const Csf<T> &csf, int cap, cudaStream_t s, int gate = GATE_ALWAYS);
 template <class T>
 void launch_colour(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
-                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s);
+                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s,
+                   int gate = GATE_ALWAYS);
 // Eq. 6 density of the fluid particles; rewrites their H1 records (and
 // stores rho - rho0 to drho_out when given).
 template <class T>
 void launch_density(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
                     const Hot<T> &hot, const T *mass, const uint8_t *type, T *drho_out, int cap,
-                    cudaStream_t s);
+                    cudaStream_t s, int gate = GATE_ALWAYS);
 template <class T>
 void launch_normal(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
                    const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s);
@@ -247,7 +259,7 @@ void launch_forces(int lanes, int mode, const PhysT<T> &P, const Grid &g, const 
 template <class T>
 void launch_refresh(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint32_t *key,
                     const State<T> &raw, const State<T> &srt, const Hot<T> &hot, int cap,
-                    cudaStream_t s);
+                    cudaStream_t s, int gate = GATE_ALWAYS);
 template <class T>
 void launch_predict(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &srt,
                     const typename Vec<T>::v4 *H0n, const typename Vec<T>::v2 *acc, const T *dr,
@@ -259,8 +271,9 @@ void launch_predict(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const Sta
 template <class T>
 void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &raw,
                   const double *layer_y, int cap, int cadence, cudaStream_t s);
-// Sets the step graph's rebuild condition from sc->need_full.
-void launch_decide(cudaGraphConditionalHandle h, const Scalars *sc, cudaStream_t s);
+// Host stub of the one-thread kernel that sets a step graph's IF-node
+// condition from sc->need_full (the conditional step form).
+void *decide_kernel();
 // Learned-surrogate step (FP32 contexts): state update with a predicted mean
 // acceleration, and the residual sums against the SPH evaluations at both ends.
 void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Grid &g, Scalars *sc,
@@ -270,8 +283,6 @@ void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Gri
 void launch_surrogate_residual(int n, const uint8_t *type, const float2 *y, float a_ref,
                                const float2 *a_n, const float2 *a_k, const float *dr_n,
                                const float *dr_k, double *sums, int cap, cudaStream_t s);
-// Host stub of the kernel launch_decide runs (for explicit graph nodes).
-void *decide_kernel();
 
 // Read-only view of a context's last evaluation (for the learned surrogate):
 // records, CSF fields and neighbour lists of the current state in cell

@@ -16,7 +16,8 @@ namespace sph {
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_hash_count(Grid g, State<T> raw, const Scalars *__restrict__ sc,
-                             uint32_t *__restrict__ knew, uint32_t *__restrict__ count) {
+                             uint32_t *__restrict__ knew, uint32_t *__restrict__ count, int gate) {
+    if (gate_skips(gate, sc)) return;
     int n = sc->n;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -39,7 +40,9 @@ __global__ void k_hash_count(Grid g, State<T> raw, const Scalars *__restrict__ s
 // Block-local scan: cellSE[k] = (prefix within the block, count); bsum[b] = total.
 __global__ void __launch_bounds__(SCAN_THREADS)
 k_scan_local(const uint32_t *__restrict__ count, uint2 *__restrict__ cellSE,
-             uint32_t *__restrict__ bsum, unsigned ncells) {
+             uint32_t *__restrict__ bsum, unsigned ncells, const Scalars *__restrict__ sc,
+             int gate) {
+    if (gate_skips(gate, sc)) return;
     __shared__ uint32_t wsum[SCAN_THREADS / 32];
     unsigned base = blockIdx.x * SCAN_CELLS + threadIdx.x * SCAN_ITEMS;
     uint32_t c[SCAN_ITEMS];
@@ -83,7 +86,8 @@ k_scan_local(const uint32_t *__restrict__ count, uint2 *__restrict__ cellSE,
 // (prefix, count) into [start, end); block 0 also stores the live count.
 __global__ void __launch_bounds__(SCAN_THREADS)
 k_scan_add(uint2 *__restrict__ cellSE, const uint32_t *__restrict__ bsum, unsigned ncells,
-           int nblocks, Scalars *__restrict__ sc) {
+           int nblocks, Scalars *__restrict__ sc, int gate) {
+    if (gate_skips(gate, sc)) return;
     __shared__ uint32_t red[SCAN_THREADS / 32];
     __shared__ uint32_t off_s;
     uint32_t part = 0, all = 0;
@@ -131,7 +135,8 @@ k_scan_add(uint2 *__restrict__ cellSE, const uint32_t *__restrict__ bsum, unsign
 // counters return to zero.
 __global__ void k_scatter(const uint32_t *__restrict__ knew, uint32_t *__restrict__ count,
                           const uint2 *__restrict__ cellSE, uint32_t *__restrict__ tmp,
-                          const Scalars *__restrict__ sc, uint32_t sentinel) {
+                          const Scalars *__restrict__ sc, uint32_t sentinel, int gate) {
+    if (gate_skips(gate, sc)) return;
     int n = sc->n;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -143,15 +148,16 @@ __global__ void k_scatter(const uint32_t *__restrict__ knew, uint32_t *__restric
 
 template <class T>
 void launch_cell_sort(const Grid &g, const State<T> &raw, Scalars *sc, CellSort &cs, int cap,
-                      cudaStream_t s) {
+                      cudaStream_t s, int gate) {
     int blocks = (cap + 255) / 256;
-    launch_k(k_hash_count<T>, blocks, 256, s, g, raw, (const Scalars *)sc, cs.knew, cs.count);
+    launch_k(k_hash_count<T>, blocks, 256, s, g, raw, (const Scalars *)sc, cs.knew, cs.count,
+             gate);
     launch_k(k_scan_local, cs.nscan, SCAN_THREADS, s, (const uint32_t *)cs.count, cs.cellSE,
-               cs.bsum, g.ncells);
+             cs.bsum, g.ncells, (const Scalars *)sc, gate);
     launch_k(k_scan_add, cs.nscan, SCAN_THREADS, s, cs.cellSE, (const uint32_t *)cs.bsum,
-               g.ncells, cs.nscan, sc);
+             g.ncells, cs.nscan, sc, gate);
     launch_k(k_scatter, blocks, 256, s, (const uint32_t *)cs.knew, cs.count,
-               (const uint2 *)cs.cellSE, cs.tmp, (const Scalars *)sc, g.sentinel);
+             (const uint2 *)cs.cellSE, cs.tmp, (const Scalars *)sc, g.sentinel, gate);
 }
 
 // ---------------------------------------------------------------------------
@@ -279,9 +285,9 @@ void launch_breakup(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *
 }
 
 template void launch_cell_sort<float>(const Grid &, const State<float> &, Scalars *, CellSort &,
-                                       int, cudaStream_t);
+                                       int, cudaStream_t, int);
 template void launch_cell_sort<double>(const Grid &, const State<double> &, Scalars *,
-                                        CellSort &, int, cudaStream_t);
+                                        CellSort &, int, cudaStream_t, int);
 template void launch_pairs<float>(const PhysT<float> &, const Grid &, Scalars *, const uint2 *,
                                   const uint32_t *, const Hot<float> &, const uint32_t *,
                                   unsigned *, unsigned *, unsigned, int, cudaStream_t);

@@ -83,7 +83,8 @@ __device__ __forceinline__ V4<T> hot1(const PhysT<T> &P, T drho, T mass) {
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_reorder(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, CellSort cs,
-                          State<T> raw, State<T> srt, Hot<T> hot) {
+                          State<T> raw, State<T> srt, Hot<T> hot, int gate) {
+    if (gate_skips(gate, sc)) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= sc->nsrt) return;
     uint32_t j = cs.tmp[t];
@@ -121,7 +122,8 @@ __global__ void k_reorder(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, Ce
 template <class T>
 __global__ void k_refresh(PhysT<T> P, Grid g, Scalars *__restrict__ sc,
                           const uint32_t *__restrict__ key, State<T> raw, State<T> srt,
-                          Hot<T> hot) {
+                          Hot<T> hot, int gate) {
+    if (gate_skips(gate, sc)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sc->nsrt) return;
     double2 p = raw.pos[i];
@@ -158,16 +160,16 @@ __global__ void k_refresh(PhysT<T> P, Grid g, Scalars *__restrict__ sc,
 template <class T>
 void launch_refresh(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint32_t *key,
                     const State<T> &raw, const State<T> &srt, const Hot<T> &hot, int cap,
-                    cudaStream_t s) {
-    launch_k(k_refresh<T>, (cap + 255) / 256, 256, s, P, g, sc, key, raw, srt, hot);
+                    cudaStream_t s, int gate) {
+    launch_k(k_refresh<T>, (cap + 255) / 256, 256, s, P, g, sc, key, raw, srt, hot, gate);
 }
 
 template <class T>
 void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const CellSort &cs,
                     const State<T> &raw, const State<T> &srt, const Hot<T> &hot, int cap,
-                    cudaStream_t s) {
+                    cudaStream_t s, int gate) {
     launch_k(k_reorder<T>, (cap + 255) / 256, 256, s, P, g, (const Scalars *)sc, cs, raw, srt,
-               hot);
+             hot, gate);
 }
 
 // ---------------------------------------------------------------------------
@@ -176,7 +178,8 @@ void launch_reorder(const PhysT<T> &P, const Grid &g, Scalars *sc, const CellSor
 template <class T, int K, bool COLOUR, int G>
 __global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
 k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ cellSE,
-        const uint32_t *__restrict__ key, Hot<T> hot, NList nl, Csf<T> csf) {
+        const uint32_t *__restrict__ key, Hot<T> hot, NList nl, Csf<T> csf, int gate) {
+    if (gate_skips(gate, sc)) return;
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned i = gt / G, sub = gt % G;
     unsigned lane = threadIdx.x & 31u;
@@ -266,7 +269,9 @@ template <class T> struct DensityRec {    // offsets and mass
 template <class T, int K, int G>
 __global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
 k_density(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot,
-          const T *__restrict__ mass, const uint8_t *__restrict__ type, T *__restrict__ drho_out) {
+          const T *__restrict__ mass, const uint8_t *__restrict__ type, T *__restrict__ drho_out,
+          int gate) {
+    if (gate_skips(gate, sc)) return;
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned i = gt / G, sub = gt % G;
     bool fluid = i < (unsigned)sc->nsrt && type[i] == T_FLUID;
@@ -302,7 +307,9 @@ k_density(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot,
 // ---------------------------------------------------------------------------
 template <class T, int K, int G>
 __global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
-k_colour(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T> csf) {
+k_colour(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T> csf,
+         int gate) {
+    if (gate_skips(gate, sc)) return;
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned i = gt / G, sub = gt % G;
     bool active = i < (unsigned)sc->nsrt;
@@ -791,44 +798,46 @@ template <class F> static void with_lanes(int lanes, F &&f) {
 template <class T>
 void launch_build(int lanes, bool with_colour, const PhysT<T> &P, const Grid &g, Scalars *sc,
                   const uint2 *cellSE, const uint32_t *key, const Hot<T> &hot, const NList &nl,
-                  const Csf<T> &csf, int cap, cudaStream_t s) {
+                  const Csf<T> &csf, int cap, cudaStream_t s, int gate) {
     with_lanes(lanes, [&](auto Gc) {
         constexpr int G = decltype(Gc)::value;
         int b = sweep_blocks(cap, G);
         if (P.kernel == 1) {
-            if (with_colour) launch_k(k_build<T, 1, true, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
-            else launch_k(k_build<T, 1, false, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
+            if (with_colour) launch_k(k_build<T, 1, true, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf, gate);
+            else launch_k(k_build<T, 1, false, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf, gate);
         } else {
-            if (with_colour) launch_k(k_build<T, 0, true, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
-            else launch_k(k_build<T, 0, false, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf);
+            if (with_colour) launch_k(k_build<T, 0, true, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf, gate);
+            else launch_k(k_build<T, 0, false, G>, b, SWEEP_BLOCK, s, P, g, sc, cellSE, key, hot, nl, csf, gate);
         }
     });
 }
 
 template <class T>
 void launch_colour(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
-                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s) {
+                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s, int gate) {
     with_lanes(lanes, [&](auto Gc) {
         constexpr int G = decltype(Gc)::value;
         int b = sweep_blocks(cap, G);
         if (P.kernel == 1)
-            launch_k(k_colour<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+            launch_k(k_colour<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf, gate);
         else
-            launch_k(k_colour<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+            launch_k(k_colour<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf, gate);
     });
 }
 
 template <class T>
 void launch_density(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
                     const Hot<T> &hot, const T *mass, const uint8_t *type, T *drho_out, int cap,
-                    cudaStream_t s) {
+                    cudaStream_t s, int gate) {
     with_lanes(lanes, [&](auto Gc) {
         constexpr int G = decltype(Gc)::value;
         int b = sweep_blocks(cap, G);
         if (P.kernel == 1)
-            launch_k(k_density<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, mass, type, drho_out);
+            launch_k(k_density<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, mass, type, drho_out,
+                     gate);
         else
-            launch_k(k_density<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, mass, type, drho_out);
+            launch_k(k_density<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, mass, type, drho_out,
+                     gate);
     });
 }
 
@@ -992,27 +1001,23 @@ __global__ void k_decide(cudaGraphConditionalHandle h, const Scalars *__restrict
     cudaGraphSetConditional(h, sc->need_full ? 1u : 0u);
 }
 
-void launch_decide(cudaGraphConditionalHandle h, const Scalars *sc, cudaStream_t s) {
-    launch_k(k_decide, 1, 1, s, h, sc);
-}
-
 void *decide_kernel() { return (void *)k_decide; }
 
 #define SPH_INST(T)                                                                              \
     template void launch_reorder<T>(const PhysT<T> &, const Grid &, Scalars *, const CellSort &,  \
                                     const State<T> &, const State<T> &, const Hot<T> &, int,      \
-                                    cudaStream_t);                                                \
+                                    cudaStream_t, int);                                           \
     template void launch_refresh<T>(const PhysT<T> &, const Grid &, Scalars *, const uint32_t *,  \
                                     const State<T> &, const State<T> &, const Hot<T> &, int,      \
-                                    cudaStream_t);                                                \
+                                    cudaStream_t, int);                                           \
     template void launch_build<T>(int, bool, const PhysT<T> &, const Grid &, Scalars *,          \
                                   const uint2 *, const uint32_t *, const Hot<T> &,                \
-                                  const NList &, const Csf<T> &, int, cudaStream_t);              \
+                                  const NList &, const Csf<T> &, int, cudaStream_t, int);         \
     template void launch_colour<T>(int, const PhysT<T> &, const Scalars *, const NList &,         \
-                                   const Hot<T> &, const Csf<T> &, int, cudaStream_t);            \
+                                   const Hot<T> &, const Csf<T> &, int, cudaStream_t, int);       \
     template void launch_density<T>(int, const PhysT<T> &, const Scalars *, const NList &,        \
                                     const Hot<T> &, const T *, const uint8_t *, T *, int,         \
-                                    cudaStream_t);                                                \
+                                    cudaStream_t, int);                                           \
     template void launch_normal<T>(int, const PhysT<T> &, const Scalars *, const NList &,         \
                                    const Hot<T> &, const Csf<T> &, int, cudaStream_t);            \
     template void launch_forces<T>(int, int, const PhysT<T> &, const Grid &, const Inflow &,     \

@@ -26,12 +26,13 @@ def sph():
     return binding
 
 
-# (seed, Re, We, dx, length, lanes, cadence): uneven sizes, mixed tunings
+# (seed, Re, We, dx, length, lanes, cadence, start form): uneven sizes, mixed
+# tunings, both ways of picking a step's start on the device
 MEMBERS = [
-    (0, 100, 10, 1.0 / 12, 10.0, 4, 1),
-    (1, 200, 20, 1.0 / 20, 6.0, 2, 8),
-    (2, 400, 40, 1.0 / 16, 12.0, 8, 4),
-    (3, 700, 5, 1.0 / 24, 5.0, 1, 2),
+    (0, 100, 10, 1.0 / 12, 10.0, 4, 1, 0),
+    (1, 200, 20, 1.0 / 20, 6.0, 2, 8, 1),
+    (2, 400, 40, 1.0 / 16, 12.0, 8, 4, 0),
+    (3, 700, 5, 1.0 / 24, 5.0, 1, 2, 1),
 ]
 
 
@@ -42,9 +43,10 @@ def _case(seed, Re, We, dx, length):
 
 
 def _make(sph, spec):
-    seed, Re, We, dx, length, lanes, cadence = spec
+    seed, Re, We, dx, length, lanes, cadence, form = spec
     sim = sph.Simulation(_case(seed, Re, We, dx, length))
     sim.set_tuning(lanes, cadence)
+    sim.set_start_form(form)
     return sim
 
 
@@ -102,6 +104,7 @@ def test_retuned_member_is_recaptured(sph):
     ens = sph.Ensemble(sims)
     ens.run(10)
     sims[0].set_tuning(2, 4)          # changes the captured step of member 0
+    sims[1].set_start_form(sph.START_GATED)   # and the start form of member 1
     ens.run(30)
     b0 = sims[0].rebuild_stats()[0]
     ens.run(16)
@@ -111,6 +114,11 @@ def test_retuned_member_is_recaptured(sph):
     solo.set_tuning(2, 4)
     solo.run(46)
     assert _same(sims[0].state(), solo.state())
+    solo = _make(sph, MEMBERS[1])
+    solo.run(10)
+    solo.set_start_form(sph.START_GATED)
+    solo.run(46)
+    assert _same(sims[1].state(), solo.state())
     ens.close()
 
 
@@ -139,6 +147,7 @@ def test_autotune_restores_states(sph):
     t_before = [s.time() for s in sims]
     lanes, cadence, ms = ens.autotune(trial_steps=8)
     assert lanes in (1, 2, 4, 8) and cadence in (1, 2, 4, 8) and ms > 0
+    assert len({s.start_form() for s in sims}) == 1
     for s, b, t in zip(sims, before, t_before):
         assert s.time() == t
         assert _same(s.state(), b)

@@ -327,6 +327,7 @@ def test_autotune_restores_state(sph):
     for k in ("x", "y", "u", "v", "rho", "id"):
         assert np.array_equal(before[k], after[k])
     assert sim.tuning() == (lanes, cadence)
+    assert sim.start_form() in (sph.START_GATED, sph.START_CONDITIONAL)
     sim.run(10)
 
 
@@ -348,6 +349,43 @@ def test_jet_trajectory_with_reused_builds(sph, orc, prec):
     assert 150 // 8 <= builds < 75          # most steps reused a build
     assert sim.time()["deleted"] == osim.deleted
     _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4)
+
+
+@pytest.mark.parametrize("density", ["continuity", "summation"])
+def test_start_forms_are_bit_identical(sph, density):
+    # the gated and the conditional step graph launch the same start kernels
+    # on the same data, so their trajectories agree bit for bit (the gated one
+    # is held to the oracle above)
+    def run(form):
+        case = wl.jet(seed=6, dx=1.0 / 20, length=6.0, Re=200, We=20)
+        case["params"]["skin_over_h"] = 0.3
+        case["params"]["density"] = density
+        sim = sph.Simulation(case)
+        sim.set_tuning(2, 8)
+        sim.set_start_form(form)
+        assert sim.start_form() == form
+        b0 = sim.rebuild_stats()[0]
+        sim.run(120)
+        out = sim.state(), sim.time(), sim.rebuild_stats()[0] - b0
+        counts = sph.sph_kernel_counts(sim.ctx)
+        sim.close()
+        return out, counts
+    (g, tg, bg), cg = run(sph.START_GATED)
+    (c, tc, bc), cc = run(sph.START_CONDITIONAL)
+    assert 120 // 8 <= bg == bc < 60
+    assert tg == tc
+    for k in ("x", "y", "u", "v", "rho", "id", "type"):
+        assert np.array_equal(g[k], c[k]), k
+    # gated: both starts every step; conditional: the IF-node kernel + one start
+    assert cg[0] == cg[1] > cc[0] > cc[1]
+
+
+def test_start_form_rejects_bad_values(sph):
+    sim = sph.Simulation(wl.jet(seed=6, dx=1.0 / 12, length=4.0))
+    with pytest.raises(sph.SphError):
+        sim.set_start_form(2)
+    assert sim.start_form() == sph.START_GATED
+    sim.close()
 
 
 def test_cadence_change_takes_effect(sph):

@@ -336,13 +336,14 @@ template <class T> static void enqueue_normal(sph_ctx *c, const Hot<T> &hot) {
 // The two ways a step starts.  Rebuild: hash, sort, reorder and neighbour
 // list (with the colour of evaluation n).  Reuse: the particles keep the
 // order, cells and lists of the last rebuild (exact while no particle has
-// moved more than skin/2 since, which the kernels check); the records of
-// evaluation n are recomputed in place.  gate: GATE_ALWAYS when the host
-// chose the start; otherwise the start's kernels run only on the steps whose
-// device flag selects it.
+// moved more than skin/2 since, which the kernels check), and the state and
+// records of evaluation n are those the last corrector wrote in place, so
+// the start is only the colour (and the Eq. 6 densities).  gate: GATE_ALWAYS
+// when the host chose the start; otherwise the start's kernels run only on
+// the steps whose device flag selects it.
 template <class T> static void enqueue_cells(sph_ctx *c, bool full, int gate = GATE_ALWAYS) {
     const PhysT<T> &P = Ops<T>::phys(c);
-    State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
+    State<T> srt = state_of<T>(c->srt);
     Hot<T> hn = hot_n<T>(c);
     const uint32_t *key = c->cs.key;
     if (full) {
@@ -350,8 +351,6 @@ template <class T> static void enqueue_cells(sph_ctx *c, bool full, int gate = G
         enqueue_build<T>(c, key, gate);
         enqueue_density<T>(c, hn, srt.drho, true, gate);
     } else {
-        tick(c, "refresh");
-        launch_refresh<T>(P, c->grid, c->sc, key, raw, srt, hn, c->cap, c->stream, gate);
         enqueue_density<T>(c, hn, srt.drho, false, gate);
         if (P.csf) {
             tick(c, "colour");
@@ -384,7 +383,7 @@ template <class T> static void enqueue_rest(sph_ctx *c) {
     enqueue_normal<T>(c, hh);
     tick(c, "forces_correct");
     launch_forces<T>(c->lanes, 2, P, c->grid, c->inf, c->sc, c->nl, key, hh, csf_of<T>(c),
-                     bd_of(c), srt, raw, acc, dr, c->cap, c->stream);
+                     bd_of(c), srt, raw, acc, dr, c->cap, c->stream, hn.H0, hn.H1);
     tick(c, "spawn");
     launch_spawn<T>(P, c->inf, c->sc, raw, c->layer_y, c->cap, c->cadence, c->stream);
 }
@@ -929,11 +928,15 @@ static sph_status append_step(sph_ctx *c, cudaGraph_t g) {
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = h;
     np.conditional.type = cudaGraphCondTypeIf;
-    np.conditional.size = 2;
+    // without surface tension and Eq. 6 the reuse start launches nothing:
+    // then the node has the rebuild body only
+    bool reuse_kernels = c->prm.sigma > 0 || c->prm.density == SPH_DENSITY_SUMMATION;
+    np.conditional.size = reuse_kernels ? 2 : 1;
     cudaGraphNode_t cnode;
     CK(cudaGraphAddNode(&cnode, g, &dnode, nullptr, 1, &np), "conditional node");
-    cudaGraph_t body[2] = {np.conditional.phGraph_out[0], np.conditional.phGraph_out[1]};
-    for (int k = 0; k < 2; ++k) {
+    cudaGraph_t body[2] = {np.conditional.phGraph_out[0],
+                           reuse_kernels ? np.conditional.phGraph_out[1] : nullptr};
+    for (int k = 0; k < (reuse_kernels ? 2 : 1); ++k) {
         CK(cudaStreamBeginCaptureToGraph(c->stream, body[k], nullptr, nullptr, 0,
                                          cudaStreamCaptureModeThreadLocal), "capture body");
         if (c->tsz == 4) enqueue_cells<float>(c, k == 0); else enqueue_cells<double>(c, k == 0);
@@ -1421,7 +1424,7 @@ sph_status sph_kernel_counts(sph_ctx *c, int *per_full_step, int *per_reused_ste
     bool csf = c->prm.sigma > 0;
     int sort = 5;                          // hash+count, scan (2), scatter, reorder
     int full = sort + 1;                   // + neighbour list (with the colour of step n)
-    int reuse = 1 + (csf ? 1 : 0);         // refresh + colour of step n
+    int reuse = csf ? 1 : 0;               // colour of step n (the corrector wrote the records)
     int rest = (csf ? 3 : 0)               // normal (2x) + colour of the half step
                + 3                         // forces (2x) + predict
                + 1;                        // spawn / time advance
@@ -1549,6 +1552,8 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
     CK(cudaMemcpyAsync(c->sg_n, &c->sc->n, sizeof(int), cudaMemcpyDeviceToDevice, c->stream), "copy");
     // SPH at the end, on the cell order and lists of the start (exact while
     // no particle moved more than skin/2, which the refresh checks)
+    launch_refresh<float>(c->Pf, c->grid, c->sc, c->cs.key, raw, srt, hot_n<float>(c), c->cap,
+                          c->stream);
     enqueue_cells<float>(c, false);
     enqueue_normal<float>(c, hot_n<float>(c));
     launch_forces<float>(c->lanes, 0, c->Pf, c->grid, c->inf, c->sc, c->nl, c->cs.key,

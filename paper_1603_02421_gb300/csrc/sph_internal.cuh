@@ -247,15 +247,19 @@ void launch_normal(int lanes, const PhysT<T> &P, const Scalars *sc, const NList 
                    const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s);
 // mode 0: evaluate only (store derivatives, copy srt -> raw); mode 1: first
 // evaluation of a step (store derivatives, time-step minimum); mode 2:
-// second evaluation + corrector (write raw).
+// second evaluation + corrector (write the new state to raw, and in place to
+// srt with the records of the next evaluation in nH0 / nH1, on the cells of
+// the last build).
 template <class T>
 void launch_forces(int lanes, int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
                    Scalars *sc, const NList &nl, const uint32_t *key, const Hot<T> &hot,
                    const Csf<T> &csf, const Boundary &bd, const State<T> &srt,
                    const State<T> &raw, typename Vec<T>::v2 *acc, T *dr, int cap,
-                   cudaStream_t s);
-// Step without a cell build: raw -> srt in the same order, records of
-// evaluation n relative to the cells of the last build.
+                   cudaStream_t s, typename Vec<T>::v4 *nH0 = nullptr,
+                   typename Vec<T>::v4 *nH1 = nullptr);
+// raw -> srt in the same order, records of evaluation n relative to the cells
+// of the last build (the learned surrogate's judge evaluation; a plain step
+// that keeps the build gets these from the corrector).
 template <class T>
 void launch_refresh(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint32_t *key,
                     const State<T> &raw, const State<T> &srt, const Hot<T> &hot, int cap,

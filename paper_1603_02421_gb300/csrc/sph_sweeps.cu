@@ -430,7 +430,8 @@ template <class T, int K, int MODE, int G>
 __global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
 k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
          const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf, Boundary bd, State<T> srt,
-         State<T> raw, V2<T> *__restrict__ acc, T *__restrict__ drout) {
+         State<T> raw, V2<T> *__restrict__ acc, T *__restrict__ drout, V4<T> *__restrict__ nH0,
+         V4<T> *__restrict__ nH1) {
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned i = gt / G, sub = gt % G;
     int nsrt = sc->nsrt;
@@ -608,18 +609,42 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
         typ = T_DEAD;
         atomicAdd((unsigned long long *)&sc->deleted, 1ull);
     }
+    T mass = srt.mass[i];
     raw.pos[i] = p1;
     raw.vel[i] = v1;
     raw.drho[i] = d1;
     raw.drc[i] = c1;
-    raw.mass[i] = srt.mass[i];
+    raw.mass[i] = mass;
     raw.type[i] = typ;
     raw.id[i] = srt.id[i];
     raw.disp[i] = ds;
+    // the same state in place in the cell order of the last build, with the
+    // records of evaluation n+1 on its cells: a next step that keeps the
+    // build starts from them (one that rebuilds sorts raw instead).  No
+    // thread of this sweep reads another particle's srt entries (neighbours
+    // come from the half-step records).
+    srt.pos[i] = p1;
+    srt.vel[i] = v1;
+    srt.drho[i] = d1;
+    srt.drc[i] = c1;
+    srt.type[i] = typ;
+    srt.disp[i] = ds;
+    T xl, yo;
+    double xo, yoo;
+    cell_offsets<T>(g, key[i], p1, xl, yo, xo, yoo);
+    nH0[i] = mk4<T>(xl, yo, v1.x, v1.y);
+    nH1[i] = typ == T_DEAD ? mk4<T>(T(0), P.rho0, T(0), P.c0) : hot1<T>(P, d1, mass);
     // largest displacements (squared, as float bits: monotone for >= 0)
     if (typ != T_DEAD) {
         float d2 = (float)(ds.x * ds.x + ds.y * ds.y);
         float s2 = (float)(stx * stx + sty * sty);
+        // the cell walks of the build stay exact while every particle lies
+        // within skin/2 of its cell; a particle outside (a rounding corner
+        // of the displacement bound) reports twice skin/2, so that the time
+        // advance rebuilds before the next step
+        T lo = -P.half_skin, hi = P.sc + P.half_skin;
+        if (!(xl >= lo && xl < hi && yo >= lo && yo < hi))
+            d2 = fmaxf(d2, 4.0f * (float)(P.half_skin * P.half_skin));
         unsigned m = __activemask();
         unsigned a = __reduce_max_sync(m, __float_as_uint(d2));
         unsigned b2 = __reduce_max_sync(m, __float_as_uint(s2));
@@ -858,27 +883,29 @@ template <class T, int K, int G>
 static void launch_forces_k(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
                             Scalars *sc, const NList &nl, const uint32_t *key, const Hot<T> &hot,
                             const Csf<T> &csf, const Boundary &bd, const State<T> &srt,
-                            const State<T> &raw, V2<T> *acc, T *dr, int cap, cudaStream_t s) {
+                            const State<T> &raw, V2<T> *acc, T *dr, V4<T> *nH0, V4<T> *nH1,
+                            int cap, cudaStream_t s) {
     int b = sweep_blocks(cap, G);
     if (mode == 0)
-        launch_k(k_forces<T, K, 0, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
+        launch_k(k_forces<T, K, 0, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, nH0, nH1);
     else if (mode == 1)
-        launch_k(k_forces<T, K, 1, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
+        launch_k(k_forces<T, K, 1, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, nH0, nH1);
     else
-        launch_k(k_forces<T, K, 2, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr);
+        launch_k(k_forces<T, K, 2, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, nH0, nH1);
 }
 
 template <class T>
 void launch_forces(int lanes, int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
                    Scalars *sc, const NList &nl, const uint32_t *key, const Hot<T> &hot,
                    const Csf<T> &csf, const Boundary &bd, const State<T> &srt,
-                   const State<T> &raw, V2<T> *acc, T *dr, int cap, cudaStream_t s) {
+                   const State<T> &raw, V2<T> *acc, T *dr, int cap, cudaStream_t s,
+                   V4<T> *nH0, V4<T> *nH1) {
     with_lanes(lanes, [&](auto Gc) {
         constexpr int G = decltype(Gc)::value;
         if (P.kernel == 1)
-            launch_forces_k<T, 1, G>(mode, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, cap, s);
+            launch_forces_k<T, 1, G>(mode, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, nH0, nH1, cap, s);
         else
-            launch_forces_k<T, 0, G>(mode, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, cap, s);
+            launch_forces_k<T, 0, G>(mode, P, g, inf, sc, nl, key, hot, csf, bd, srt, raw, acc, dr, nH0, nH1, cap, s);
     });
 }
 
@@ -1023,7 +1050,8 @@ void *decide_kernel() { return (void *)k_decide; }
     template void launch_forces<T>(int, int, const PhysT<T> &, const Grid &, const Inflow &,     \
                                    Scalars *, const NList &, const uint32_t *, const Hot<T> &,    \
                                    const Csf<T> &, const Boundary &, const State<T> &,            \
-                                   const State<T> &, V2<T> *, T *, int, cudaStream_t);            \
+                                   const State<T> &, V2<T> *, T *, int, cudaStream_t, V4<T> *,    \
+                                   V4<T> *);                                                      \
     template void launch_predict<T>(const PhysT<T> &, const Inflow &, Scalars *,                 \
                                     const State<T> &, const V4<T> *, const V2<T> *, const T *,    \
                                     const Hot<T> &, int, cudaStream_t);                           \

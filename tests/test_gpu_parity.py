@@ -377,7 +377,8 @@ def test_start_forms_are_bit_identical(sph, density):
     for k in ("x", "y", "u", "v", "rho", "id", "type"):
         assert np.array_equal(g[k], c[k]), k
     # gated: both starts every step; conditional: the IF-node kernel + one start
-    assert cg[0] == cg[1] > cc[0] > cc[1]
+    # (the reuse start is the colour sweep alone, the rebuild start six kernels)
+    assert cg[0] == cg[1] >= cc[0] > cc[1]
 
 
 def test_start_form_rejects_bad_values(sph):

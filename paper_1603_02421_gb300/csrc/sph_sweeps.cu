@@ -662,8 +662,20 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
 template <class T>
 __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, State<T> srt,
                           const V4<T> *__restrict__ H0n, const V2<T> *__restrict__ acc,
-                          const T *__restrict__ dr, Hot<T> half) {
+                          const T *__restrict__ dr, Hot<T> half, int cap) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // the particle's data first (in bounds for any i < cap; used only for
+    // i < nsrt), so that these loads overlap the fold of the dt slots
+    const int j = i < cap ? i : 0;
+    const int nsrt = sc->nsrt;
+    const V4<T> h0 = H0n[j];            // offsets and velocity at n
+    const T d = srt.drho[j];
+    const uint8_t typ = srt.type[j];
+    const double2 p = srt.pos[j];
+    const V2<T> a = acc[j];
+    const T dri = dr[j];
+    const T mass = srt.mass[j];
+    const V2<T> ds = srt.disp[j];
     double dt;
     if (P.dt_fixed > 0.0) {
         dt = P.dt_fixed;
@@ -688,23 +700,18 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
         dt = P.courant * m;
     }
     if (i == 0) sc->dt = dt;
-    if (i >= sc->nsrt) return;
+    if (i >= nsrt) return;
     double hdt = 0.5 * dt;
-    V4<T> h0 = H0n[i];                  // offsets and velocity at n
     V2<T> v = mk2(h0.z, h0.w);
-    T d = srt.drho[i];
-    uint8_t typ = srt.type[i];
     T th = (T)hdt;
     // displacement over the half step (absolute velocity = frame + stored)
     T ddx = th * (P.ufx + v.x), ddy = th * (P.ufy + v.y);
-    double2 p = srt.pos[i];
     double2 ph = make_double2(p.x + hdt * (P.ufx_d + (double)v.x), p.y + hdt * (P.ufy_d + (double)v.y));
     V2<T> vh = v;
     T dh = d;
     if (typ == T_FLUID) {
-        V2<T> a = acc[i];
         vh = mk2(v.x + th * a.x, v.y + th * a.y);
-        dh = d + th * dr[i];
+        dh = d + th * dri;
     } else if (typ == T_BUFFER && inf.on) {
         vh = mk2((T)(inflow_u(inf, sc->t + hdt) - P.ufx_d), (T)(-P.ufy_d));
     }
@@ -715,11 +722,10 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
         half.H1[i] = mk4<T>(T(0), P.rho0, T(0), P.c0);
         return;
     }
-    half.H1[i] = hot1<T>(P, dh, srt.mass[i]);
+    half.H1[i] = hot1<T>(P, dh, mass);
     // the cell walks stay exact while every particle is within skin/2 of its
     // cell, and the neighbour list while no particle has moved more than
     // skin/2 since the list was built
-    V2<T> ds = srt.disp[i];
     T tx = ds.x + ddx, ty = ds.y + ddy;
     T lo = -P.half_skin, hi = P.sc + P.half_skin;
     if (!(xo >= lo && xo < hi && yo >= lo && yo < hi) ||
@@ -743,32 +749,37 @@ __global__ void k_spawn(Inflow inf, double ufx, double ufy, float half_skin,
         // warp 0: each lane folds and resets one reduction slot, lanes 0 and
         // 1 evaluate the two inflow velocities; lane 0 takes the decisions
         const unsigned lane = threadIdx.x;
-        unsigned d2 = __reduce_max_sync(0xffffffffu, sc->max_disp2[lane]);
-        unsigned s2 = __reduce_max_sync(0xffffffffu, sc->max_step2[lane]);
+        // every scalar this kernel reads, loaded at once
+        const unsigned d2l = sc->max_disp2[lane], s2l = sc->max_step2[lane];
+        const double dt = sc->dt, t = sc->t, x_up = sc->x_up;
+        const int nsrt = sc->nsrt, since_full = sc->since_full;
+        const unsigned next_id = sc->next_id;
+        double half = 0.5 * dt;
+        unsigned d2 = __reduce_max_sync(0xffffffffu, d2l);
+        unsigned s2 = __reduce_max_sync(0xffffffffu, s2l);
         sc->max_disp2[lane] = 0u;
         sc->max_step2[lane] = 0u;
         sc->dtmin_f[lane] = 0x7f7f7f7fu;
         sc->dtmin_d[lane] = 0x7f7f7f7f7f7f7f7full;
-        double dt = sc->dt, t = sc->t, half = 0.5 * dt;
         double uq = (inf.on && lane < 2) ? inflow_u(inf, lane == 0 ? t + half : t + dt) : 0.0;
         double uh = __shfl_sync(0xffffffffu, uq, 0);
         double ue = __shfl_sync(0xffffffffu, uq, 1);
         if (lane == 0) {
-            int n = sc->nsrt;
+            int n = nsrt;
             do_spawn = 0;
             if (inf.on) {
-                double xs = __dadd_rn(sc->x_up, __dmul_rn(half, uh));
-                double xu = __dsub_rn(__dmul_rn(2.0, xs), sc->x_up);
+                double xs = __dadd_rn(x_up, __dmul_rn(half, uh));
+                double xu = __dsub_rn(__dmul_rn(2.0, xs), x_up);
                 sc->x_up = xu;
                 if (xu >= inf.threshold) {
                     if (n + inf.ny <= cap) {
                         do_spawn = 1;
                         base = n;
-                        idbase = sc->next_id;
+                        idbase = next_id;
                         xnew = __dsub_rn(xu, inf.dx);
                         unew = ue;
                         sc->x_up = xnew;
-                        sc->next_id += (unsigned)inf.ny;
+                        sc->next_id = next_id + (unsigned)inf.ny;
                         n += inf.ny;
                     } else {
                         atomicOr(&sc->err, ERR_CAPACITY);
@@ -785,9 +796,9 @@ __global__ void k_spawn(Inflow inf, double ufx, double ufy, float half_skin,
             float smax = sqrtf(__uint_as_float(s2));
             sc->last_dmax = dmax;
             sc->last_smax = smax;
-            int need = do_spawn || sc->since_full + 1 >= cadence || dmax + 2.0f * smax > half_skin;
+            int need = do_spawn || since_full + 1 >= cadence || dmax + 2.0f * smax > half_skin;
             sc->need_full = need;
-            sc->since_full = need ? 0 : sc->since_full + 1;
+            sc->since_full = need ? 0 : since_full + 1;
         }
     }
     __syncthreads();
@@ -913,7 +924,7 @@ template <class T>
 void launch_predict(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &srt,
                     const V4<T> *H0n, const V2<T> *acc, const T *dr, const Hot<T> &half, int cap,
                     cudaStream_t s) {
-    launch_k(k_predict<T>, (cap + 255) / 256, 256, s, P, inf, sc, srt, H0n, acc, dr, half);
+    launch_k(k_predict<T>, (cap + 255) / 256, 256, s, P, inf, sc, srt, H0n, acc, dr, half, cap);
 }
 
 template <class T>

@@ -629,9 +629,12 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
     srt.drc[i] = c1;
     srt.type[i] = typ;
     srt.disp[i] = ds;
-    T xl, yo;
-    double xo, yoo;
-    cell_offsets<T>(g, key[i], p1, xl, yo, xo, yoo);
+    // offsets from the cell: those of evaluation n plus this step's
+    // displacement (in T, as the displacement since the build; a few ulps
+    // from the offsets of the FP64 position over the steps between builds,
+    // far inside the band where pair tests are redone in FP64)
+    V4<T> h0n = nH0[i];
+    T xl = h0n.x + stx, yo = h0n.y + sty;
     nH0[i] = mk4<T>(xl, yo, v1.x, v1.y);
     nH1[i] = typ == T_DEAD ? mk4<T>(T(0), P.rho0, T(0), P.c0) : hot1<T>(P, d1, mass);
     // largest displacements (squared, as float bits: monotone for >= 0)

@@ -745,7 +745,10 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
     train_s = time.perf_counter() - t_tr
     # held-out prediction errors (network vs the SPH acceleration alone)
     test = [(ci, smp) for ci, c in enumerate(held_cases[:2])
-            for smp in sg.collect(c, 2, every=10, k=SUR_K, warm=20)]
+            for smp in sg.collect(c, 2, every=10, k=SUR_K, warm=20, end_accel=True)]
+    # the judge's momentum residual of the exact k-step mean (plain SPH): the
+    # lowest any predictor can score
+    floor = sg.residual_floor([smp for _, smp in test])
     ev = sg.Trainer(held_cases[:2], cap)
     ev.net.set_params(params)
     e_net, e_an = ev.prediction_errors(test, a_ref)
@@ -849,6 +852,10 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
                        "surrogate_steps": steps, "accepted": accepted,
                        "acceptance_rate": accepted / max(steps, 1),
                        "momentum_residual_median": float(np.median(rms)) if rms else None,
+                       "momentum_residual_floor": {
+                           "median": float(np.median(floor)), "values": floor,
+                           "how": "the judge's residual with the exact 4-step mean "
+                                  "acceleration of plain SPH on held-out samples"},
                        "prediction_error_heldout": {"network": e_net, "sph_acceleration_only": e_an},
                        "training": {"seconds": train_s, "passes": len(losses),
                                     "samples": len(data), "final_loss": losses[-1],

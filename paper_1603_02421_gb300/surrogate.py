@@ -23,10 +23,12 @@ from . import binding
 STATE_KEYS = ("x", "y", "u", "v", "rho", "m", "type", "id")
 
 
-def collect(case, nsamples, every=20, k=4, warm=20, lanes_cadence=(2, 8)):
+def collect(case, nsamples, every=20, k=4, warm=20, lanes_cadence=(2, 8), end_accel=False):
     """Samples from one jet: warm-up steps, then every `every` steps a state
     with the k-step targets.  Returns a list of dicts (state arrays sorted by
-    id, the correction abar - a_n and abar per particle, the validity mask)."""
+    id, the correction abar - a_n and abar per particle, the validity mask;
+    with end_accel also a_end, the SPH acceleration at the end of the k
+    steps, for residual_floor)."""
     sim = binding.Simulation(case)
     sim.set_tuning(*lanes_cadence)
     out = []
@@ -37,6 +39,8 @@ def collect(case, nsamples, every=20, k=4, warm=20, lanes_cadence=(2, 8)):
             s0 = sim.state()
             t0 = sim.time()["t"]
             sim.run(k)
+            if end_accel:
+                sim.evaluate()
             s1 = sim.state()
             t1 = sim.time()["t"]
             common, i0, i1 = np.intersect1d(s0["id"], s1["id"], return_indices=True)
@@ -50,9 +54,31 @@ def collect(case, nsamples, every=20, k=4, warm=20, lanes_cadence=(2, 8)):
             corr = np.where(valid[:, None], abar - a_n, 0.0)
             out.append({"state": {key: s0[key] for key in STATE_KEYS}, "corr": corr,
                         "abar": np.where(valid[:, None], abar, 0.0), "valid": valid})
+            if end_accel:
+                a_end = np.zeros((n0, 2))
+                a_end[i0, 0] = s1["ax"][i1]
+                a_end[i0, 1] = s1["ay"][i1]
+                out[-1]["a_end"] = np.where(valid[:, None], a_end, 0.0)
             sim.run(max(every - k, 0))
     finally:
         sim.close()
+    return out
+
+
+def residual_floor(samples):
+    """The judge's momentum residual, sqrt(sum |abar - (a_n + a_k)/2|^2 /
+    sum |(a_n + a_k)/2|^2) over the valid particles, evaluated with the true
+    k-step mean abar of plain SPH and the SPH accelerations a_n, a_k at both
+    ends of those k steps: what a perfect predictor would score.  One value
+    per sample (samples collected with end_accel=True)."""
+    out = []
+    for smp in samples:
+        v = smp["valid"]
+        abar = smp["abar"][v]
+        a_n = abar - smp["corr"][v]
+        trap = 0.5 * (a_n + smp["a_end"][v])
+        den = float(np.sum(trap ** 2))
+        out.append(float(np.sqrt(np.sum((abar - trap) ** 2) / den)) if den > 0 else 0.0)
     return out
 
 

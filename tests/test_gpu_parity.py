@@ -283,14 +283,18 @@ def test_lanes_give_the_same_evaluation(sph, orc, lanes):
     assert rel_l2(g["drho"], ev["drho"]) < 1e-5
 
 
+@pytest.mark.parametrize("form", ["gated", "conditional"])
 @pytest.mark.parametrize("cadence,lanes", [(2, 4), (4, 2), (8, 8)])
-def test_cadence_keeps_dam_break_trajectory(sph, orc, cadence, lanes):
+def test_cadence_keeps_dam_break_trajectory(sph, orc, cadence, lanes, form):
     # the cells and lists of a build are reused for `cadence` steps; the
-    # neighbour sets stay exact, so the trajectory still matches the oracle
+    # neighbour sets stay exact, so the trajectory still matches the oracle.
+    # Without surface tension the reuse start launches no kernel (in the
+    # conditional form the IF node then has the rebuild body only)
     case = wl.dam_break(seed=2, dx=0.02, prec="fp64")
     case["params"]["skin_over_h"] = 0.1 * cadence   # room for `cadence` steps of motion
     sim = sph.Simulation(case)
     sim.set_tuning(lanes, cadence)
+    sim.set_start_form(sph.START_GATED if form == "gated" else sph.START_CONDITIONAL)
     osim = oracle_sim(orc, case)
     sim.run(120)
     osim.run(120)

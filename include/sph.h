@@ -220,9 +220,15 @@ sph_status sph_profile_report(sph_ctx *ctx, int cap, int *n, const char **names,
  * every `cadence` steps, and earlier when the step before spawned an inflow
  * layer or when one more step could move a particle more than skin/2 from
  * where the lists were built (decided on the device); also after the
- * particles were added, replaced or reordered by another call.  The steps in
- * between keep the last build, which stays exact (checked: SPH_ERR_SKIN
- * otherwise).  Defaults: lanes 4, cadence 1 (every step). */
+ * particles were added, replaced or reordered by another call.  Without
+ * walls the displacement is taken relative to the velocity frame
+ * (u_frame_x, u_frame_y): a common translation changes no pair separation,
+ * so a jet moving at the frame velocity keeps its lists; particles may then
+ * move up to two cells from their build-time cell.  With walls it is the
+ * absolute displacement (wall contacts are found by walking the build-time
+ * cells).  The steps in between keep the last build, which stays exact
+ * (checked: SPH_ERR_SKIN otherwise).  Defaults: lanes 4, cadence 1 (every
+ * step). */
 sph_status sph_set_tuning(sph_ctx *ctx, int lanes, int cadence);
 sph_status sph_get_tuning(sph_ctx *ctx, int *lanes, int *cadence);
 
@@ -246,19 +252,22 @@ typedef enum { SPH_START_GATED = 0, SPH_START_CONDITIONAL = 1 } sph_start_form;
 sph_status sph_set_start_form(sph_ctx *ctx, int form);
 sph_status sph_get_start_form(sph_ctx *ctx, int *form);
 
-/* Autotuner: times trial_steps steps for each lanes in {1, 2, 4, 8} and cadence
- * in {1, 2, 4, 8} (at cadence > 1 in both start forms) from a copy of the
- * current state (rejecting settings that trip SPH_ERR_SKIN), restores the
- * state, and keeps the fastest setting.  Outputs (nullable): the chosen
- * lanes, cadence and its ms per step; sph_get_start_form gives the form. */
+/* Autotuner: from a copy of the current state, times each lanes in {1, 2, 4,
+ * 8} with cadence in {1, 2, 4, 8}, then cadence 16 and 32 at the best lanes
+ * (at cadence > 1 in both start forms), each over max(trial_steps,
+ * 2 x cadence) steps after a warm cycle, rejecting settings that trip
+ * SPH_ERR_SKIN; restores the state and keeps the fastest setting.  Outputs
+ * (nullable): the chosen lanes, cadence and its ms per step;
+ * sph_get_start_form gives the form. */
 sph_status sph_autotune(sph_ctx *ctx, int trial_steps, int *lanes, int *cadence,
                         double *ms_per_step);
 
 /* Cell builds so far (cell sorts run by steps and by the calls that sort:
  * evaluate, pairs, breakup length), and the rebuild decision taken at the end
  * of the last step: the largest displacement of a particle since the last
- * build and the largest move in that step (both in length units, FP32).
- * Any pointer may be NULL. */
+ * build and the largest move in that step (both in length units, FP32;
+ * relative to the velocity frame when there are no walls, see
+ * sph_set_tuning).  Any pointer may be NULL. */
 sph_status sph_get_rebuild_stats(sph_ctx *ctx, long long *builds, double *disp_max,
                                  double *step_max);
 
@@ -330,11 +339,11 @@ sph_status sph_ensemble_run(sph_ensemble *e, long long nsteps);
  * the member's own sph_last_error holds the description. */
 sph_status sph_ensemble_sync(sph_ensemble *e, int *bad_member);
 
-/* Autotuner over one (lanes, cadence, start form) for all members: times
- * trial_steps ensemble steps for lanes in {1, 2, 4, 8} and cadence in
- * {1, 2, 4, 8} (at cadence > 1 in both start forms) from copies of the
- * members' states (rejecting settings that trip SPH_ERR_SKIN), restores the
- * states and keeps the fastest setting.  Outputs nullable. */
+/* Autotuner over one (lanes, cadence, start form) for all members, with the
+ * candidates and trial lengths of sph_autotune, timed as ensemble steps from
+ * copies of the members' states (rejecting settings that trip
+ * SPH_ERR_SKIN); restores the states and keeps the fastest setting.  Outputs
+ * nullable. */
 sph_status sph_ensemble_autotune(sph_ensemble *e, int trial_steps, int *lanes, int *cadence,
                                  double *ms_per_step);
 

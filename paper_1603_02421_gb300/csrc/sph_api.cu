@@ -226,6 +226,21 @@ template <class T> static PhysT<T> make_phys(const sph_params &p, const Grid &g,
     P.ufy = (T)p.u_frame_y;
     P.ufx_d = p.u_frame_x;
     P.ufy_d = p.u_frame_y;
+    // Verlet lists stay exact while every pair separation has changed by
+    // less than the skin.  Measuring the displacement since the build
+    // relative to any common frame keeps that bound (|d_a - d_b| <= |d_a - w|
+    // + |d_b - w|), so without walls it is taken in the velocity frame, and a
+    // jet translating at U does not force rebuilds.  Particles may then leave
+    // their build-time cell: offsets up to two cells beyond it keep the FP32
+    // pair test about 16 times inside the band where pairs are redone in
+    // FP64.  Wall contacts are found by walking the build-time cells, so with
+    // walls the absolute displacement counts and a particle stays within
+    // skin/2 of its cell.
+    double half_skin = 0.5 * p.skin_over_h * h;
+    P.dfx = walls ? T(0) : (T)p.u_frame_x;
+    P.dfy = walls ? T(0) : (T)p.u_frame_y;
+    P.cell_lo = (T)(walls ? -half_skin : -2.0 * g.sc);
+    P.cell_hi = (T)(walls ? g.sc + half_skin : 3.0 * g.sc);
     P.courant = p.courant;
     P.dt_fixed = p.dt_fixed;
     return P;
@@ -1364,32 +1379,42 @@ sph_status sph_autotune(sph_ctx *c, int trial_steps, int *lanes, int *cadence, d
     CK(cudaEventCreate(&e1), "event");
     bool prof = c->prof;
     c->prof = false;
-    for (int a = 0; a < 4; ++a) {
-        for (int b = 0; b < 4; ++b) {
-            // both start forms where the device picks the start (cadence > 1)
+    // one candidate from the snapshot: a warm cycle (capture), then at least
+    // two rebuild cycles timed; SPH_ERR_SKIN rejects the candidate only
+    auto trial = [&](int Lv, int Kv, int Fv) -> sph_status {
+        int steps = std::max(trial_steps, 2 * Kv);
+        sph_status t = snapshot(c, true);
+        if (!t) t = sph_set_tuning(c, Lv, Kv);
+        if (!t) t = sph_set_start_form(c, Fv);
+        if (!t) t = sph_run_async(c, Kv);
+        if (!t) t = sph_sync(c);
+        if (t) return t;
+        cudaEventRecord(e0, c->stream);
+        t = sph_run_async(c, steps);
+        cudaEventRecord(e1, c->stream);
+        if (!t) t = sph_sync(c);
+        if (t) return t;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        double per = ms / steps;
+        if (per < best) { best = per; bestL = Lv; bestK = Kv; bestF = Fv; }
+        return SPH_OK;
+    };
+    // lanes x cadence up to 8, both start forms where the device picks the
+    // start (cadence > 1); then longer cadences at the best lane count
+    for (int a = 0; a < 4 && (!s || s == SPH_ERR_SKIN); ++a)
+        for (int b = 0; b < 4 && (!s || s == SPH_ERR_SKIN); ++b)
             for (int f = 0; f < (K[b] > 1 ? 2 : 1); ++f) {
-                int F = f == 0 ? SPH_START_GATED : SPH_START_CONDITIONAL;
-                s = snapshot(c, true);
-                if (!s) s = sph_set_tuning(c, L[a], K[b]);
-                if (!s) s = sph_set_start_form(c, F);
-                if (!s) s = sph_run_async(c, K[b]);      // warm: capture + one cycle
-                if (!s) s = sph_sync(c);
-                if (s == SPH_ERR_SKIN) break;             // cadence too long for this flow
-                if (s) break;
-                cudaEventRecord(e0, c->stream);
-                s = sph_run_async(c, trial_steps);
-                cudaEventRecord(e1, c->stream);
-                if (!s) s = sph_sync(c);
-                if (s == SPH_ERR_SKIN) break;
-                if (s) break;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                double per = ms / trial_steps;
-                if (per < best) { best = per; bestL = L[a]; bestK = K[b]; bestF = F; }
+                s = trial(L[a], K[b], f == 0 ? SPH_START_GATED : SPH_START_CONDITIONAL);
+                if (s) break;                             // SKIN: cadence too long here
             }
-            if (s && s != SPH_ERR_SKIN) break;
-        }
-        if (s && s != SPH_ERR_SKIN) break;
+    if (best < 1e300 && (!s || s == SPH_ERR_SKIN)) {
+        int L0 = bestL;
+        for (int Kv = 16; Kv <= 32 && (!s || s == SPH_ERR_SKIN); Kv *= 2)
+            for (int f = 0; f < 2; ++f) {
+                s = trial(L0, Kv, f == 0 ? SPH_START_GATED : SPH_START_CONDITIONAL);
+                if (s) break;
+            }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1742,31 +1767,44 @@ sph_status sph_ensemble_autotune(sph_ensemble *e, int trial_steps, int *lanes, i
         }
         return SPH_OK;
     };
-    for (int a = 0; a < 4 && !s; ++a) {
-        for (int b = 0; b < 4 && !s; ++b) {
-            for (int f = 0; f < (K[b] > 1 ? 2 : 1) && !s; ++f) {
-                int F = f == 0 ? SPH_START_GATED : SPH_START_CONDITIONAL;
-                s = restore_all();
-                for (size_t k = 0; k < e->m.size() && !s; ++k) {
-                    s = sph_set_tuning(e->m[k], L[a], K[b]);
-                    if (!s) s = sph_set_start_form(e->m[k], F);
-                }
-                if (!s) s = sph_ensemble_run(e, K[b]);   // capture + one cycle
-                if (!s) s = sph_ensemble_sync(e, nullptr);
-                if (s == SPH_ERR_SKIN) { s = SPH_OK; break; }
-                if (s) break;
-                cudaEventRecord(t0, e->stream);
-                s = sph_ensemble_run(e, trial_steps);
-                cudaEventRecord(t1, e->stream);
-                if (!s) s = sph_ensemble_sync(e, nullptr);
-                if (s == SPH_ERR_SKIN) { s = SPH_OK; break; }
-                if (s) break;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, t0, t1);
-                double per = ms / trial_steps;
-                if (per < best) { best = per; bestL = L[a]; bestK = K[b]; bestF = F; }
-            }
+    // one candidate from the snapshots: a warm cycle (capture), then at least
+    // two rebuild cycles timed; SPH_ERR_SKIN rejects the candidate only
+    auto trial = [&](int Lv, int Kv, int Fv) -> sph_status {
+        int steps = std::max(trial_steps, 2 * Kv);
+        sph_status t = restore_all();
+        for (size_t k = 0; k < e->m.size() && !t; ++k) {
+            t = sph_set_tuning(e->m[k], Lv, Kv);
+            if (!t) t = sph_set_start_form(e->m[k], Fv);
         }
+        if (!t) t = sph_ensemble_run(e, Kv);
+        if (!t) t = sph_ensemble_sync(e, nullptr);
+        if (t) return t;
+        cudaEventRecord(t0, e->stream);
+        t = sph_ensemble_run(e, steps);
+        cudaEventRecord(t1, e->stream);
+        if (!t) t = sph_ensemble_sync(e, nullptr);
+        if (t) return t;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        double per = ms / steps;
+        if (per < best) { best = per; bestL = Lv; bestK = Kv; bestF = Fv; }
+        return SPH_OK;
+    };
+    // lanes x cadence up to 8 in both start forms, then longer cadences at
+    // the best lane count
+    for (int a = 0; a < 4 && !s; ++a)
+        for (int b = 0; b < 4 && !s; ++b)
+            for (int f = 0; f < (K[b] > 1 ? 2 : 1) && !s; ++f) {
+                s = trial(L[a], K[b], f == 0 ? SPH_START_GATED : SPH_START_CONDITIONAL);
+                if (s == SPH_ERR_SKIN) { s = SPH_OK; break; }   // cadence too long here
+            }
+    if (best < 1e300 && !s) {
+        int L0 = bestL;
+        for (int Kv = 16; Kv <= 32 && !s; Kv *= 2)
+            for (int f = 0; f < 2 && !s; ++f) {
+                s = trial(L0, Kv, f == 0 ? SPH_START_GATED : SPH_START_CONDITIONAL);
+                if (s == SPH_ERR_SKIN) { s = SPH_OK; break; }
+            }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);

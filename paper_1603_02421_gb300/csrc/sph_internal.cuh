@@ -83,6 +83,12 @@ template <class T> struct PhysT {
     T wall_A, wall_db, inv_wall_db, wall_h0, inv_wall_h0, two_h, c0_inv;
     T ufx, ufy;          // velocity frame: stored velocities are u - u_frame
     T half_skin;         // skin / 2
+    // displacement since the list build is measured relative to a frame
+    // moving at (dfx, dfy): the velocity frame without walls (a common
+    // translation changes no pair separation), zero with walls (their
+    // contacts are found by walking the build-time cells)
+    T dfx, dfy;
+    T cell_lo, cell_hi;  // bounds of a particle's offset from its build-time cell
     double H2d, R15d;    // exact FP64 thresholds (2h)^2, (1.5h)^2
     double courant, dt_fixed;
     double ufx_d, ufy_d;

@@ -150,8 +150,9 @@ __global__ void k_refresh(PhysT<T> P, Grid g, Scalars *__restrict__ sc,
     }
     hot.H1[i] = hot1<T>(P, dr, m);
     // the lists and cell walks of the last build stay exact while no particle
-    // has moved more than skin/2 (and stays within skin/2 of its cell)
-    T lo = -P.half_skin, hi = P.sc + P.half_skin;
+    // has moved more than skin/2 (relative to the frame of P.dfx, P.dfy) and
+    // its offset from the build-time cell stays within bounds
+    T lo = P.cell_lo, hi = P.cell_hi;
     if (!(xl >= lo && xl < hi && yo >= lo && yo < hi) ||
         !(ds.x * ds.x + ds.y * ds.y <= P.half_skin * P.half_skin))
         atomicOr(&sc->err, ERR_SKIN);
@@ -577,7 +578,8 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
     V2<T> v1 = v0;
     T d1 = d0, c1 = c0;
     V2<T> ds = srt.disp[i];
-    T stx = T(0), sty = T(0);           // this step's displacement (rebuild decision)
+    T stx = T(0), sty = T(0);           // this step's displacement (cell offsets)
+    T srx = T(0), sry = T(0);           // the same relative to (dfx, dfy) (rebuild decision)
     if (typ == T_DEAD) {
         // deleted since the last cell build: kept as is until it is dropped
     } else if (typ == T_FLUID) {
@@ -596,14 +598,17 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
         }
         stx = tdt * (P.ufx + usx);
         sty = tdt * (P.ufy + usy);
+        srx = tdt * (P.ufx - P.dfx + usx);
+        sry = tdt * (P.ufy - P.dfy + usy);
     } else {
         double uh = inf.on ? inflow_u(inf, t + half) : P.ufx_d + (double)v0.x;
         p1 = make_double2(p0.x + dt * uh, p0.y);
         v1 = inf.on ? mk2((T)(inflow_u(inf, t + dt) - P.ufx_d), (T)(-P.ufy_d)) : v0;
         if (inf.on && p1.x >= inf.x_exit) typ = T_FLUID;
         stx = (T)(dt * uh);
+        srx = (T)(dt * (uh - (double)P.dfx));
     }
-    ds = mk2(ds.x + stx, ds.y + sty);
+    ds = mk2(ds.x + srx, ds.y + sry);
     if (typ == T_FLUID &&
         !(p1.x >= g.xmin && p1.x < g.xmax && p1.y >= g.ymin && p1.y < g.ymax)) {
         typ = T_DEAD;
@@ -640,12 +645,12 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
     // largest displacements (squared, as float bits: monotone for >= 0)
     if (typ != T_DEAD) {
         float d2 = (float)(ds.x * ds.x + ds.y * ds.y);
-        float s2 = (float)(stx * stx + sty * sty);
-        // the cell walks of the build stay exact while every particle lies
-        // within skin/2 of its cell; a particle outside (a rounding corner
-        // of the displacement bound) reports twice skin/2, so that the time
-        // advance rebuilds before the next step
-        T lo = -P.half_skin, hi = P.sc + P.half_skin;
+        float s2 = (float)(srx * srx + sry * sry);
+        // the cell walks and FP32 offsets of the build stay exact while every
+        // particle's offset from its build-time cell stays within bounds; a
+        // particle outside reports twice skin/2, so that the time advance
+        // rebuilds before the next step
+        T lo = P.cell_lo, hi = P.cell_hi;
         if (!(xl >= lo && xl < hi && yo >= lo && yo < hi))
             d2 = fmaxf(d2, 4.0f * (float)(P.half_skin * P.half_skin));
         unsigned m = __activemask();
@@ -726,11 +731,12 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
         return;
     }
     half.H1[i] = hot1<T>(P, dh, mass);
-    // the cell walks stay exact while every particle is within skin/2 of its
-    // cell, and the neighbour list while no particle has moved more than
-    // skin/2 since the list was built
-    T tx = ds.x + ddx, ty = ds.y + ddy;
-    T lo = -P.half_skin, hi = P.sc + P.half_skin;
+    // the neighbour list stays exact while no particle has moved more than
+    // skin/2 since it was built (relative to the frame of P.dfx, P.dfy), and
+    // the cell walks and FP32 offsets while every offset from the build-time
+    // cell stays within bounds
+    T tx = ds.x + th * (P.ufx - P.dfx + v.x), ty = ds.y + th * (P.ufy - P.dfy + v.y);
+    T lo = P.cell_lo, hi = P.cell_hi;
     if (!(xo >= lo && xo < hi && yo >= lo && yo < hi) ||
         !(tx * tx + ty * ty <= P.half_skin * P.half_skin))
         atomicOr(&sc->err, ERR_SKIN);
@@ -973,13 +979,13 @@ __global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *
         float s = d0 + y;
         c1 = (s - d0) - y;
         d1 = s;
-        ds = make_float2(ds.x + tdt * (P.ufx + uhx), ds.y + tdt * (P.ufy + uhy));
+        ds = make_float2(ds.x + tdt * (P.ufx - P.dfx + uhx), ds.y + tdt * (P.ufy - P.dfy + uhy));
     } else if (typ == T_BUFFER) {
         double uh = inf.on ? inflow_u(inf, t + half) : P.ufx_d + (double)v0.x;
         p1 = make_double2(p0.x + dT * uh, p0.y);
         v1 = inf.on ? make_float2((float)(inflow_u(inf, t + dT) - P.ufx_d), (float)(-P.ufy_d)) : v0;
         if (inf.on && p1.x >= inf.x_exit) typ = T_FLUID;
-        ds = make_float2(ds.x + (float)(dT * uh), ds.y);
+        ds = make_float2(ds.x + (float)(dT * (uh - (double)P.dfx)), ds.y);
     }
     if (typ == T_FLUID &&
         !(p1.x >= g.xmin && p1.x < g.xmax && p1.y >= g.ymin && p1.y < g.ymax)) {

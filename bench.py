@@ -165,7 +165,7 @@ def parse():
                     help="auto (autotuner), or LANES,CADENCE[,gated|conditional] (e.g. 4,1 for "
                          "every-step cell builds; the third field picks how a step at cadence > 1 "
                          "chooses its start on the device, default gated)")
-    ap.add_argument("--skin", type=float, default=0.3, help="skin / h of the cell search")
+    ap.add_argument("--skin", type=float, default=0.15, help="skin / h of the cell search")
     return ap.parse_args()
 
 

@@ -165,8 +165,14 @@ def parse():
                     help="auto (autotuner), or LANES,CADENCE[,gated|conditional] (e.g. 4,1 for "
                          "every-step cell builds; the third field picks how a step at cadence > 1 "
                          "chooses its start on the device, default gated)")
-    ap.add_argument("--skin", type=float, default=0.15, help="skin / h of the cell search")
-    return ap.parse_args()
+    ap.add_argument("--skin", type=float, default=None,
+                    help="skin / h of the cell search (default 0.15 for the jets, whose lists "
+                         "are kept in the velocity frame, 0.3 for the dam break, whose walls "
+                         "keep the absolute rebuild test)")
+    args = ap.parse_args()
+    if args.skin is None:
+        args.skin = 0.3 if args.workload == "dam_c1" else 0.15
+    return args
 
 
 # ---------------------------------------------------------------------------

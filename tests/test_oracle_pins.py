@@ -155,6 +155,72 @@ def test_viscosity_acts_only_on_approaching_pairs(orc):
     assert 10.0 * (0.1 * ev["ax"][0] - 0.1 * ev["ax"][1]) < 0
 
 
+def _wave_state(n, dx, U, k, axis):
+    """Square lattice of n x n at rho0 carrying u_x = U sin(k s), s = x or y."""
+    x, y = wl.lattice(0.0, 0.0, n, n, dx)
+    u = U * np.sin(k * (x if axis == "x" else y))
+    return x, y, wl._fluid(x, y, u, np.zeros_like(u), dx=dx)
+
+
+@pytest.mark.parametrize("kernel", ["cubic", "wendland"])
+def test_viscosity_magnitude_on_a_compression_wave(orc, kernel):
+    # Eq. 10 in the continuum limit.  With rho = rho0 (P = 0), g = 0 and
+    # sigma = 0 the acceleration is the viscous term alone,
+    #   a_a = sum_b V_b K (u_ab . r_ab) / r_ab^2 F_ab r_ab,  K = alpha h c0
+    # (eta^2 << r^2).  For u = U sin(kx) e_x a Taylor expansion u_a - u_b =
+    # u' r_x - u'' r_x^2 / 2 gives, where u' < 0 (every pair approaches, so the
+    # switch of Eq. 10 is on for all of them),
+    #   a_x = -(K u''/2) int F r_x^4 / r^2 dA = -(K u''/2)(3 pi/4) int r^2 W' dr
+    #       = (3/8) K u''
+    # using pi int r^2 W' dr = -1 (first moment of the kernel gradient).  A
+    # dropped h, a wrong eta^2 or a factor on alpha breaks the 5 % band; the
+    # lattice at h = 1.3 dx reproduces the integral to ~1 % (Wendland) and
+    # ~4 % (cubic).
+    dx, n, U, lam, alpha, c0 = 0.01, 64, 0.01, 0.32, 0.5, 10.0
+    k = 2 * math.pi / lam
+    x, y, st = _wave_state(n, dx, U, k, "x")
+    d = orc.derive(wl.test_params(kernel=kernel, dx=dx, alpha=alpha, c0=c0))
+    ev = orc.evaluate(d, st, None)
+    L = n * dx
+    inner = (x > 6 * d.h) & (x < L - 6 * d.h) & (y > 6 * d.h) & (y < L - 6 * d.h)
+    up = U * k * np.cos(k * x)
+    upp = -U * k * k * np.sin(k * x)
+    comp = inner & (up < -0.5 * U * k)
+    assert comp.sum() > 200
+    ratio = ev["ax"][comp] / (0.375 * alpha * d.h * c0 * upp[comp])
+    assert np.all(np.abs(ratio - 1.0) < 0.05)
+    assert np.abs(ev["ay"][comp]).max() < 1e-9 * np.abs(ev["ax"][comp]).max()
+    # where the flow expands every pair recedes: no viscous force at all
+    expand = inner & (up > 0.5 * U * k)
+    assert np.all(ev["ax"][expand] == 0.0)
+
+
+@pytest.mark.parametrize("kernel", ["cubic", "wendland"])
+def test_viscosity_of_a_shear_wave_with_the_approach_switch(orc, kernel):
+    # Eq. 10 on a shear flow u = U sin(ky) e_x.  Applied to every pair, the
+    # term gives a_x = -(K u''/2) int F r_x^2 r_y^2 / r^2 dA = K u''/8, i.e. a
+    # kinematic viscosity K/8 = alpha h c0 / 8.  The switch of Eq. 10 keeps
+    # only approaching pairs; to leading order those are the two quadrants
+    # where u' r_x r_y < 0, which carry exactly half of that integral (the
+    # first-order term cancels between them).  So the effective viscosity of a
+    # shear wave is alpha h c0 / 16, reached as the lattice resolves the kernel
+    # (h = 3 dx here; within 5 %).
+    dx, n, U, lam, alpha, c0 = 0.01, 128, 0.01, 0.64, 0.5, 10.0
+    k = 2 * math.pi / lam
+    x, y, st = _wave_state(n, dx, U, k, "y")
+    p = wl.test_params(kernel=kernel, dx=dx, alpha=alpha, c0=c0, box=(-1.0, -1.0, 3.0, 3.0))
+    p["h_over_dx"] = 3.0
+    d = orc.derive(p)
+    ev = orc.evaluate(d, st, None)
+    L = n * dx
+    inner = (x > 6 * d.h) & (x < L - 6 * d.h) & (y > 6 * d.h) & (y < L - 6 * d.h)
+    lap = -(k * k) * st["u"][inner]            # u''
+    nu = np.sum(ev["ax"][inner] * lap) / np.sum(lap * lap)
+    assert nu == pytest.approx(alpha * d.h * c0 / 16.0, rel=0.05)
+    resid = ev["ax"][inner] - nu * lap
+    assert np.linalg.norm(resid) < 1e-6 * np.linalg.norm(nu * lap)
+
+
 def test_continuity_of_uniform_expansion(orc):
     # u = eps * r gives div u = 2 eps, so Eq. 1: drho/dt = -2 eps rho in the interior.
     dx = 0.02
@@ -244,6 +310,31 @@ def test_adaptive_dt_of_isolated_particle(orc):
     assert dt == pytest.approx(0.2 * min(math.sqrt(h / 9.81), h / 1.0), rel=1e-14)
 
 
+def test_dt_neighbour_term_of_approaching_and_receding_pairs(orc):
+    # Eq. 31: dt_cv,a = h / (c_a + max_b |h u_ab . r_ab / r_ab^2|), with
+    # rho = rho0 (so c_a = c0 = 1) and dx = 0.1 (h = 0.13), worked by hand:
+    #   a (0, 0)    u (0.5, 0)  -- b: r_ab = (-0.1, 0), u_ab = (1, 0),
+    #   b (0.1, 0)  u (-0.5, 0)    u.r = -0.1, r^2 = 0.01 -> 0.13 * 10 = 1.3
+    #   c (0, -0.2) at rest     -- a: u.r = 0; b: r_cb = (-0.1, -0.2),
+    #                              u_cb = (0.5, 0), u.r = -0.05, r^2 = 0.05 -> 0.13
+    #   e (1, 1) at rest, f (1.1, 1) u (0.3, 0): receding, r_ef = (-0.1, 0),
+    #                              u_ef = (-0.3, 0), u.r = 0.03 -> 0.39 (|.| of Eq. 31)
+    # so dt_cv = 0.13/2.3 (a, b), 0.13/1.13 (c), 0.13/1.39 (e, f).  With alpha
+    # = 0 and P = 0 no particle accelerates, dt_f is infinite, and the step of
+    # Eq. 32 is 0.2 * 0.13/2.3.
+    p = wl.test_params(dx=0.1, alpha=0.0, c0=1.0, box=(-5.0, -5.0, 5.0, 5.0))
+    st = wl._fluid([0.0, 0.1, 0.0, 1.0, 1.1], [0.0, 0.0, -0.2, 1.0, 1.0],
+                   [0.5, -0.5, 0.0, 0.0, 0.3], [0.0] * 5, dx=0.1)
+    d = orc.derive(p)
+    ev = orc.evaluate(d, st, None)
+    expect = [0.05652173913043478, 0.05652173913043478, 0.11504424778761062,
+              0.09352517985611511, 0.09352517985611511]
+    assert ev["dt_cv"] == pytest.approx(expect, rel=1e-13)
+    assert np.all(np.isinf(ev["dt_f"]))
+    sim = orc.OracleSim(p, st)
+    assert sim.step() == pytest.approx(0.011304347826086957, rel=1e-13)
+
+
 def test_mass_and_count_conserved_without_inflow(orc):
     st = wl.jittered_patch(seed=4, nx=12, ny=10, dx=0.02, vel=0.2)
     p = wl.test_params(dx=0.02, alpha=0.2, g=9.81)
@@ -285,6 +376,105 @@ def test_drop_colour_normal_curvature(orc):
     # Eq. 24: surface tension pulls the rim inward
     adot = (ev["ax"][rim] * st["x"][rim] + ev["ay"][rim] * st["y"][rim]) / r[rim]
     assert np.median(adot) < 0
+
+
+@pytest.mark.parametrize("kernel,lattice_sum", [("cubic", 1.0105), ("wendland", 0.9739)])
+def test_normal_of_a_linear_colour_field(orc, kernel, lattice_sum):
+    # Eq. 18 is the SPH difference gradient of C: for a smooth C it gives
+    #   n_a = grad C . sum_b V_b (r_b - r_a) (x) grad_a W_ab = grad C (V_a / A) L,
+    # where A = dx^2 is the area per lattice particle and L = -sum_b A F r_x^2
+    # is the lattice form of int x dW/dx dA = -1 (1 up to a few per cent at h
+    # = 1.3 dx).  Volumes V_b = dx^2 (1 + beta x_b) on a uniform lattice make
+    # the colour of Eq. 14 linear in x; its slope is taken from C itself.
+    dx, n, beta = 0.02, 50, 0.2
+    x, y = wl.lattice(0.0, 0.0, n, n, dx)
+    st = wl._fluid(x, y, m=1000.0 * dx * dx * (1.0 + beta * x), dx=dx)
+    d = orc.derive(wl.test_params(kernel=kernel, dx=dx, sigma=1.0, alpha=0.0))
+    ev = orc.evaluate(d, st, None)
+    L = n * dx
+    inner = (x > 6 * d.h) & (x < L - 6 * d.h) & (y > 6 * d.h) & (y < L - 6 * d.h)
+    slope = np.polyfit(x[inner], ev["C"][inner], 1)[0]
+    assert slope == pytest.approx(beta, rel=0.02)
+    ratio = ev["nx"][inner] / ((1.0 + beta * x[inner]) * slope)
+    assert np.all(np.abs(ratio - 1.0) < 0.04)
+    assert np.all(np.abs(ratio - lattice_sum) < 1e-3)
+    assert np.abs(ev["ny"][inner]).max() < 1e-9 * np.abs(ev["nx"][inner]).max()
+
+
+def _csf_accel(orc, kernel, st, dx, sigma):
+    """Surface-tension part of du/dt: the evaluation with sigma minus the one
+    without (pressure, viscosity and g do not depend on sigma)."""
+    d1 = orc.derive(wl.test_params(kernel=kernel, dx=dx, sigma=sigma, alpha=0.0,
+                                   box=(-3.0, -3.0, 3.0, 3.0)))
+    d0 = orc.derive(wl.test_params(kernel=kernel, dx=dx, sigma=0.0, alpha=0.0,
+                                   box=(-3.0, -3.0, 3.0, 3.0)))
+    e1 = orc.evaluate(d1, st, None)
+    e0 = orc.evaluate(d0, st, None)
+    return e1["ax"] - e0["ax"], e1["ay"] - e0["ay"], e1
+
+
+@pytest.mark.parametrize("kernel", ["cubic", "wendland"])
+@pytest.mark.parametrize("dx", [0.05, 0.025])
+def test_csf_force_balance_of_a_half_drop(orc, kernel, dx):
+    # Eq. 24 magnitude.  A surface under tension T pulls each half of a
+    # circular drop toward the other with 2 T (the tension at the two ends of
+    # the cut, i.e. the Young-Laplace balance sigma kappa x 2R).  The CSF
+    # force density sigma kappa n carries a tension T = sigma tau, where tau
+    # = int |n| across the surface band.  In this single-phase setting (no air
+    # particles, colour = the Shepard sum of Eq. 14) the colour drops from 1
+    # only to about 0.5 inside the liquid, and tau is measured here on a flat
+    # free surface of the same lattice (about 0.20; kappa = 0 there, so the
+    # flat strip's tau does not involve Eq. 24).  The drop's right half must
+    # then feel sum_a m_a a_s,x = -2 sigma tau within 10 % (the curvature of
+    # Eq. 23 is within 10 % of -1/R at these resolutions).  A factor on sigma,
+    # or a missing 1/rho_a (x1000 here), fails.
+    sigma = 1.7
+    nxs, nys = int(round(2.0 / dx)), int(round(1.0 / dx))
+    xs, ys = wl.lattice(-1.0, -1.0, nxs, nys, dx)
+    flat = wl._fluid(xs, ys, dx=dx)
+    d = orc.derive(wl.test_params(kernel=kernel, dx=dx, sigma=sigma, alpha=0.0,
+                                  box=(-3.0, -3.0, 3.0, 3.0)))
+    ef = orc.evaluate(d, flat, None)
+    band = (np.abs(xs) < 0.5) & (ys > -0.5)            # upper surface, 1.0 long
+    tau = -np.sum((flat["m"] / flat["rho"] * ef["ny"])[band]) / 1.0
+    assert 0.15 < tau < 0.3
+    assert np.abs(ef["kappa"][band]).max() < 1e-9      # flat: no curvature
+    drop = wl.disc(R=1.0, dx=dx)
+    asx, asy, _ = _csf_accel(orc, kernel, drop, dx, sigma)
+    right = drop["x"] > 0.0
+    Fx = np.sum(drop["m"][right] * asx[right])
+    assert Fx / (-2.0 * sigma * tau) == pytest.approx(1.0, abs=0.1)
+    # and the two halves pull on each other equally
+    Fx_left = np.sum(drop["m"][~right] * asx[~right])
+    assert Fx_left == pytest.approx(-Fx, rel=1e-9)
+
+
+def test_csf_scales_with_sigma_and_the_particles_own_density(orc):
+    # Eq. 24: (a_s)_a = -(sigma/rho_a) kappa_a n_a.  C, n and kappa depend on
+    # the volumes V = m/rho only, so (i) a_s is exactly linear in sigma and
+    # (ii) scaling one particle's mass and density together by s leaves every
+    # volume, colour, normal and curvature unchanged and divides that
+    # particle's a_s -- and no other particle's -- by s (a_s uses rho_a, not
+    # rho0 or a neighbour's density).
+    dx, kernel = 0.05, "wendland"
+    drop = wl.disc(R=1.0, dx=dx)
+    ax1, ay1, e1 = _csf_accel(orc, kernel, drop, dx, 1.0)
+    ax3, ay3, _ = _csf_accel(orc, kernel, drop, dx, 3.0)
+    assert np.allclose(ax3, 3.0 * ax1, rtol=1e-9, atol=1e-12 * np.abs(ax1).max())
+    assert np.allclose(ay3, 3.0 * ay1, rtol=1e-9, atol=1e-12 * np.abs(ay1).max())
+    rim = np.flatnonzero(e1["N"] == 1)
+    a = int(rim[len(rim) // 3])
+    s = 1.25
+    st = {k: np.array(v, copy=True) for k, v in drop.items()}
+    st["m"][a] *= s
+    st["rho"][a] *= s
+    # sigma-free parts change with rho_a (pressure), so compare the CSF parts
+    bx, by, e2 = _csf_accel(orc, kernel, st, dx, 1.0)
+    assert np.allclose(e2["kappa"], e1["kappa"], rtol=1e-12, atol=1e-12)
+    assert bx[a] == pytest.approx(ax1[a] / s, rel=1e-9)
+    assert by[a] == pytest.approx(ay1[a] / s, rel=1e-9)
+    others = np.arange(len(ax1)) != a
+    assert np.allclose(bx[others], ax1[others], rtol=1e-9, atol=1e-12 * np.abs(ax1).max())
 
 
 # ---------------------------------------------------------------------------

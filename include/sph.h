@@ -284,27 +284,36 @@ sph_status sph_kernel_counts(sph_ctx *ctx, int *per_full_step, int *per_reused_s
 
 /* Neighbour pairs without any device allocation.  The paper has no
  * counterpart: this is a service for callers that cannot call cudaMalloc --
- * code running inside another framework's memory pool or stream capture, an
- * application that must not grow its device footprint after start-up, or a
- * plugin that only receives device buffers from its host.
+ * code running inside another framework's memory pool (whose allocator owns
+ * the device memory), an application that must not grow its device footprint
+ * after start-up, or a plugin that only receives device buffers from its
+ * host.
  *
  * x, y: DEVICE arrays of n FP64 positions, all inside the box
- * [xmin, xmax) x [ymin, ymax) (particles outside are reported with
- * SPH_ERR_ARG).  Finds every ordered pair (a, b), a != b, with
+ * [xmin, xmax) x [ymin, ymax).  Finds every ordered pair (a, b), a != b, with
  * |r_a - r_b| < 2h (Sec. 2-7), exactly as sph_get_pairs does, and writes the
  * input indices a, b to the DEVICE arrays pair_a, pair_b (cap entries each,
- * order unspecified); *npairs (host) receives the count (SPH_ERR_CAPACITY if
- * it exceeds cap).  Work runs on `stream` (a cudaStream_t, NULL = legacy
- * default stream) of the current device, and the call waits for it.
+ * order unspecified); *npairs (host) receives the total count (a 64-bit
+ * count, whatever the density of the input).  Work runs on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) of the current device; the call
+ * waits for it and copies the count to the host.
+ *
+ * Errors decided on the device still report the pairs found: particles
+ * outside the box or with a NaN coordinate are left out of the search and
+ * the call returns SPH_ERR_ARG with the pairs of the others written and
+ * counted; a count above cap returns SPH_ERR_CAPACITY with the first cap
+ * pairs written and *npairs the full count.
  *
  * Limits: n <= 262144 particles and a search grid of at most 1048576 cells of
  * size 2.1 h over the box (SPH_ERR_CAPACITY beyond).  The scratch is one
  * static device array of about 31 MB that every GPU loading the library holds
  * until the process exits.  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress), so make the first call on each
- * device before any stream capture.  All calls share the array: calls whose
- * work overlaps on the GPU (other host threads, other streams) race and must
- * be serialised by the caller. */
+ * device before any stream capture.  The address is kept for the life of the
+ * process, so a device reset (cudaDeviceReset) leaves it stale: do not call
+ * this entry point on a device after resetting it.  All calls share the
+ * array: calls whose work overlaps on the GPU (other host threads, other
+ * streams) race and must be serialised by the caller. */
 sph_status sph_pairs_noalloc(const double *x, const double *y, long long n, double h,
                              double xmin, double ymin, double xmax, double ymax,
                              unsigned *pair_a, unsigned *pair_b, long long cap,

@@ -370,7 +370,9 @@ def sph_pairs_noalloc(x_ptr, y_ptr, n, h, box, a_ptr, b_ptr, cap, stream=None):
                                  float(box[2]), float(box[3]), a_ptr, b_ptr, int(cap),
                                  ctypes.byref(npairs), stream)
     if st != SPH_OK:
-        raise SphError(st, "sph_pairs_noalloc failed (%d pairs found)" % npairs.value)
+        err = SphError(st, "sph_pairs_noalloc failed (%d pairs found)" % npairs.value)
+        err.count = npairs.value
+        raise err
     return npairs.value
 
 

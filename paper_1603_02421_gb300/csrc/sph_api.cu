@@ -1185,7 +1185,7 @@ sph_status sph_get_pairs(sph_ctx *c, long long cap, unsigned *id_a, unsigned *id
                          long long *npairs) {
     if (!c || !npairs || cap < 0) return SPH_ERR_ARG;
     if (cap > 0 && (!id_a || !id_b)) return fail(c, SPH_ERR_ARG, "output arrays required");
-    unsigned dcap = (unsigned)std::min<long long>(cap, 0x7fffffffll);
+    unsigned long long dcap = (unsigned long long)std::min<long long>(cap, 0x7fffffffll);
     unsigned *da = nullptr, *db = nullptr;
     c->force_full = true;
     CK(cudaMalloc(&da, std::max<size_t>(dcap, 1) * 4), "pair buffer");
@@ -1194,16 +1194,21 @@ sph_status sph_get_pairs(sph_ctx *c, long long cap, unsigned *id_a, unsigned *id
     sph_status s = SPH_OK;
     if (c->tsz == 4) {
         const uint32_t *key = enqueue_sort<float>(c);
-        launch_pairs<float>(c->Pf, c->grid, c->sc, c->cellSE, key, hot_n<float>(c),
-                            (uint32_t *)c->srt[6], da, db, dcap, c->cap, c->stream);
+        e = launch_pairs<float>(c->Pf, c->grid, c->sc, c->cellSE, key, hot_n<float>(c),
+                                (uint32_t *)c->srt[6], da, db, dcap, c->cap, c->stream);
     } else {
         const uint32_t *key = enqueue_sort<double>(c);
-        launch_pairs<double>(c->Pd, c->grid, c->sc, c->cellSE, key, hot_n<double>(c),
-                             (uint32_t *)c->srt[6], da, db, dcap, c->cap, c->stream);
+        e = launch_pairs<double>(c->Pd, c->grid, c->sc, c->cellSE, key, hot_n<double>(c),
+                                 (uint32_t *)c->srt[6], da, db, dcap, c->cap, c->stream);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(da);
+        cudaFree(db);
+        return cuda_check(c, e, "pair export");
     }
     s = after_work(c, "pairs");
     if (s == SPH_OK) {
-        long long np = c->hsc->pair_count;
+        long long np = (long long)c->hsc->pair_count;
         *npairs = np;
         if (np > cap) {
             s = fail(c, SPH_ERR_CAPACITY, "%lld pairs > cap %lld", np, cap);

@@ -115,7 +115,8 @@ struct Scalars {
     long long builds;             // cell sorts run (steps and other calls)
     unsigned long long xmax_key;  // breakup: ordered bits of max x of the jet
     unsigned detached;            // breakup: particles outside the jet
-    unsigned pair_count;
+    unsigned long long pair_count;  // pairs found by the pair export (64-bit: dense
+                                    // inputs can exceed 2^32 ordered pairs)
     int need_full;                // next step rebuilds the cells and lists
     int since_full;               // steps since the last rebuild
     // reductions spread over RED_SLOTS addresses (slot = block index mod
@@ -217,10 +218,14 @@ struct NList {
 template <class T>
 void launch_cell_sort(const Grid &g, const State<T> &raw, Scalars *sc, CellSort &cs, int cap,
                       cudaStream_t s, int gate = GATE_ALWAYS);
+// Exports every ordered pair closer than 2h; sc->pair_count receives the total
+// (slots beyond cap are counted but not written).  Returns the first error of
+// the enqueued memset and launch.
 template <class T>
-void launch_pairs(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *cellSE,
-                  const uint32_t *key, const Hot<T> &hot, const uint32_t *ids, unsigned *out_a,
-                  unsigned *out_b, unsigned cap, int ncap, cudaStream_t s);
+cudaError_t launch_pairs(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *cellSE,
+                         const uint32_t *key, const Hot<T> &hot, const uint32_t *ids,
+                         unsigned *out_a, unsigned *out_b, unsigned long long cap, int ncap,
+                         cudaStream_t s);
 template <class T>
 void launch_breakup(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *cellSE,
                     const uint32_t *key, const Hot<T> &hot, const uint8_t *type,

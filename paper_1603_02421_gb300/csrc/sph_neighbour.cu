@@ -169,7 +169,7 @@ template <class T>
 __global__ void __launch_bounds__(SWEEP_BLOCK)
 k_pairs(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ cellSE,
         const uint32_t *__restrict__ key, Hot<T> hot, const uint32_t *__restrict__ ids,
-        unsigned *out_a, unsigned *out_b, unsigned cap) {
+        unsigned *out_a, unsigned *out_b, unsigned long long cap) {
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned i = gt / PAIR_LANES, sub = gt % PAIR_LANES;
     if (i >= (unsigned)sc->nsrt) return;
@@ -178,7 +178,7 @@ k_pairs(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ 
     for_neighbours<PAIR_LANES, T>(
         P, g, cellSE, hot.H0, hot.pos, i, sub, key[i], ha.x, ha.y, P.H2lo, P.H2hi, P.H2d,
         [&](unsigned b, T, T, T, const typename Vec<T>::v4 &) {
-            unsigned slot = atomicAdd(&sc->pair_count, 1u);
+            unsigned long long slot = atomicAdd(&sc->pair_count, 1ull);
             if (slot < cap) {
                 out_a[slot] = ida;
                 out_b[slot] = ids[b];
@@ -187,12 +187,15 @@ k_pairs(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ 
 }
 
 template <class T>
-void launch_pairs(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *cellSE,
-                  const uint32_t *key, const Hot<T> &hot, const uint32_t *ids, unsigned *out_a,
-                  unsigned *out_b, unsigned cap, int ncap, cudaStream_t s) {
-    cudaMemsetAsync(&sc->pair_count, 0, sizeof(unsigned), s);
+cudaError_t launch_pairs(const PhysT<T> &P, const Grid &g, Scalars *sc, const uint2 *cellSE,
+                         const uint32_t *key, const Hot<T> &hot, const uint32_t *ids,
+                         unsigned *out_a, unsigned *out_b, unsigned long long cap, int ncap,
+                         cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&sc->pair_count, 0, sizeof(sc->pair_count), s);
+    if (e != cudaSuccess) return e;
     int blocks = (int)(((long long)ncap * PAIR_LANES + SWEEP_BLOCK - 1) / SWEEP_BLOCK);
     k_pairs<T><<<blocks, SWEEP_BLOCK, 0, s>>>(P, g, sc, cellSE, key, hot, ids, out_a, out_b, cap);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -288,13 +291,14 @@ template void launch_cell_sort<float>(const Grid &, const State<float> &, Scalar
                                        int, cudaStream_t, int);
 template void launch_cell_sort<double>(const Grid &, const State<double> &, Scalars *,
                                         CellSort &, int, cudaStream_t, int);
-template void launch_pairs<float>(const PhysT<float> &, const Grid &, Scalars *, const uint2 *,
-                                  const uint32_t *, const Hot<float> &, const uint32_t *,
-                                  unsigned *, unsigned *, unsigned, int, cudaStream_t);
-template void launch_pairs<double>(const PhysT<double> &, const Grid &, Scalars *,
-                                   const uint2 *, const uint32_t *, const Hot<double> &,
-                                   const uint32_t *, unsigned *, unsigned *, unsigned, int,
-                                   cudaStream_t);
+template cudaError_t launch_pairs<float>(const PhysT<float> &, const Grid &, Scalars *,
+                                         const uint2 *, const uint32_t *, const Hot<float> &,
+                                         const uint32_t *, unsigned *, unsigned *,
+                                         unsigned long long, int, cudaStream_t);
+template cudaError_t launch_pairs<double>(const PhysT<double> &, const Grid &, Scalars *,
+                                          const uint2 *, const uint32_t *, const Hot<double> &,
+                                          const uint32_t *, unsigned *, unsigned *,
+                                          unsigned long long, int, cudaStream_t);
 template void launch_breakup<float>(const PhysT<float> &, const Grid &, Scalars *,
                                     const uint2 *, const uint32_t *, const Hot<float> &,
                                     const uint8_t *, uint32_t *, uint8_t *, int, cudaStream_t);

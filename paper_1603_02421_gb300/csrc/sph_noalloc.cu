@@ -1,9 +1,9 @@
 // Neighbour-pair search that allocates no device memory (sph_pairs_noalloc).
 //
 // Some callers cannot call cudaMalloc: code running inside another
-// framework's memory pool or graph-capture region, a host application that
-// must not grow its device footprint after start-up, or a plugin that only
-// ever receives device buffers from its host.  This entry point takes the
+// framework's memory pool (whose allocator owns the device), a host
+// application that must not grow its device footprint after start-up, or a
+// plugin that only ever receives device buffers from its host.  This entry point takes the
 // caller's device input and output buffers and keeps all of its scratch
 // (cell counters, scan block sums, sort keys, the gathered positions) in one
 // file-scope device array of fixed size, which every GPU that loads the
@@ -64,7 +64,8 @@ std::mutex g_mu;
 unsigned char *g_base[NA_MAX_DEVICES] = {};   // device address of g_pairs_scratch per device
 
 // Device address of the scratch on the current device (looked up once per
-// device, with that device current).
+// device, with that device current, and kept for the life of the process: a
+// cudaDeviceReset of that device invalidates it, see include/sph.h).
 cudaError_t scratch_base(int dev, unsigned char **out) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_base[dev]) {
@@ -78,16 +79,12 @@ cudaError_t scratch_base(int dev, unsigned char **out) {
 }
 
 // Copies the caller's x, y into the scratch state; particles outside the box
-// are excluded (and reported).  Resets the counters of this call.
+// (or with a NaN coordinate) are excluded and reported in sc->err, which the
+// caller cleared before this launch.
 __global__ void k_na_gather(const double *__restrict__ x, const double *__restrict__ y, int n,
                             Grid g, double2 *pos, uint8_t *type, uint32_t *id, Scalars *sc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) {
-        sc->n = n;
-        sc->nsrt = 0;
-        sc->err = 0u;
-        sc->pair_count = 0u;
-    }
+    if (i == 0) sc->n = n;
     if (i >= n) return;
     double px = x[i], py = y[i];
     bool in = px >= g.xmin && px < g.xmax && py >= g.ymin && py < g.ymax;
@@ -179,15 +176,19 @@ extern "C" sph_status sph_pairs_noalloc(const double *x, const double *y, long l
     uint32_t *sid = (uint32_t *)(base + kL.sid);
 
     int ni = (int)n;
-    // the counters must start at zero (a failed earlier call may have left
-    // them set); the rest of the scratch is fully rewritten before it is read
+    // the scalars (error word, counts) and the cell counters must start at
+    // zero -- the scratch keeps whatever the last call left; the rest of it is
+    // fully rewritten before it is read
+    if (cudaMemsetAsync(scal, 0, sizeof(Scalars), s) != cudaSuccess) return SPH_ERR_CUDA;
     if (cudaMemsetAsync(cs.count, 0, (size_t)g.ncells * 4, s) != cudaSuccess) return SPH_ERR_CUDA;
     k_na_gather<<<(ni + 255) / 256, 256, 0, s>>>(x, y, ni, g, raw.pos, raw.type, raw.id, scal);
     launch_cell_sort<float>(g, raw, scal, cs, ni, s);
     k_na_order<<<(ni + 255) / 256, 256, 0, s>>>(g, scal, cs, raw.pos, raw.id, hot.pos, sid,
                                                 hot.H0);
-    unsigned dcap = (unsigned)std::min<long long>(cap, 0xffffffffll);
-    launch_pairs<float>(P, g, scal, cs.cellSE, cs.key, hot, sid, pair_a, pair_b, dcap, ni, s);
+    if (launch_pairs<float>(P, g, scal, cs.cellSE, cs.key, hot, sid, pair_a, pair_b,
+                            (unsigned long long)cap, ni, s) != cudaSuccess)
+        return SPH_ERR_CUDA;
+    // the kernels before the pair export are checked here too
     if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
     Scalars hs;
     if (cudaMemcpyAsync(&hs, scal, sizeof(Scalars), cudaMemcpyDeviceToHost, s) != cudaSuccess)

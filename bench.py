@@ -6,11 +6,17 @@ hash + radix sort + cell ranges + reorder, two evaluations (colour, normal,
 forces) with the predictor-corrector update in between, inflow/outflow, and
 (every 100 steps) the breakup-length evaluation.
 
-Default workload (N = 1): the 2D planar jet, Re = 200, We = 20, Wendland
-kernel, dx = D/40, 60 D domain (~96k particles), FP32 pair sums with FP64
-positions and time, adaptive dt (Eqs. 30-32).  Inputs are seeded synthetic
-states (workloads.py).  Between timed steps the L2 cache is flushed by writing
-a 256 MiB buffer (outside the timed events).
+Default workload (N = 1): the large 2D planar jet, Re = 100, We = 10,
+Wendland kernel, dx = D/100, 100 D domain (~1M particles), FP32 pair sums with
+FP64 positions and time, adaptive dt (Eqs. 30-32).  Inputs are seeded
+synthetic states (workloads.py).  The K timed steps start with a forced cell
+rebuild and include the breakup length every 100 steps; a second window of at
+least 64 rebuild cadences gives the steady-state rate.  Beside the line: the
+64-jet batched ensemble (batched and member by member), the GPU's FP32 / FP64
+FMA peaks measured by the library's probe, and the FP64 CPU oracle on 1 thread
+and on every host core.  Small states (below twice the L2 size) are timed step
+by step with a 256 MiB L2 flush before each step (outside the events); large
+ones back to back.
 
 Usage:
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload jet_c2|jet_c3|dam_c1]
@@ -153,14 +159,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="jet_c2",
+    ap.add_argument("--workload", default="jet_c3",
                     choices=["jet_c2", "jet_c3", "dam_c1", "ensemble_c4", "surrogate_c5"])
     ap.add_argument("--train-seconds", type=float, default=60.0,
                     help="surrogate_c5: GPU training time of the network")
     ap.add_argument("--threshold", type=float, default=1e-3,
                     help="surrogate_c5: residual threshold above which plain SPH takes over")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="jet_c3: skip the 64-jet batched ensemble reported beside the line")
+    ap.add_argument("--ensemble-steps", type=int, default=100,
+                    help="jet_c3: ensemble steps timed for the batched_c4 keys")
+    ap.add_argument("--cpu-seconds", type=float, default=24.0)
     ap.add_argument("--tune", default="auto",
                     help="auto (autotuner), or LANES,CADENCE[,gated|conditional] (e.g. 4,1 for "
                          "every-step cell builds; the third field picks how a step at cadence > 1 "
@@ -229,7 +239,13 @@ def reference_arm(args):
         case, desc = workload(args.workload, seed=0)
     # the oracle runs ~0.75 M particle-steps/s on one core: size the sample so
     # that the K steps take about a minute
-    budget = 4.5e7 / max(args.steps, 1)
+    from oracle import oracle as orc
+    orc.build()
+    cores = orc.max_threads()
+    orc.set_threads(cores)
+    # the oracle runs ~2e6 particle-steps/s on all cores of a 16-core host:
+    # size the sample so that the K steps take about a minute
+    budget = 1.2e8 / max(args.steps, 1)
     sample = oracle_sample(case, int(min(24000, max(2000, budget))))
     run_oracle(sample, 0, max_steps=max(args.warmup, 0) or 1)
     psteps, nsteps, el, n = run_oracle(sample, 0, max_steps=args.steps)
@@ -241,9 +257,9 @@ def reference_arm(args):
         "data": "synthetic",
         "config": {"workload": args.workload + ": " + desc, "particles": n,
                    "sample": "upstream %d particles of the workload" % n},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "FP64 CPU oracle, %d steps of the upstream %d particles"
-                                   % (nsteps, n)},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "FP64 CPU oracle (OpenMP over particles, %d threads), %d "
+                                   "steps of the upstream %d particles" % (cores, nsteps, n)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -347,9 +363,52 @@ def main():
         return
     case, desc = workload(args.workload, seed=rank_members(rank, world, world)[0])
     case["params"]["skin_over_h"] = args.skin
+    line, sim = bench_plain(args, binding, dist, dev, rank, world, local, case, desc)
+    sim.close()
+    if rank == 0 and args.workload == "jet_c3" and not args.no_ensemble:
+        # the metric compares plain with batched: the 64-jet ensemble of the
+        # paper's Re x We sweeps, batched and member by member, beside it
+        ens = bench_ensemble(args, binding, None, dev, 0, 1, local, steps=args.ensemble_steps,
+                             emit=False, cpu=False)
+        line["batched_c4"] = {k: ens[k] for k in ("value", "plain_value", "batched_over_plain",
+                                                  "ms_per_step", "steps", "particles_total",
+                                                  "tuning", "clocks", "gpu_launches")}
+        line["batched_c4"]["workload"] = ens["workload"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def measured_peaks(binding, local):
+    """FP32 and FP64 FMA rates of this GPU from the library's own probe
+    (CUDA events, best of 5 launches), with the SM clocks sampled while it
+    ran."""
+    clocks = ClockSampler(local)
+    f32, ms32 = binding.sph_fma_peak(local, 0)
+    f64, ms64 = binding.sph_fma_peak(local, 1)
+    clk = clocks.stop()
+    return {"fp32_tflops": f32, "fp64_tflops": f64, "fp32_launch_ms": ms32,
+            "fp64_launch_ms": ms64, "clocks": clk,
+            "how": "sph_fma_peak: every SM filled with threads running 8 independent FMA "
+                   "chains, 2 x FMAs / time of the best of 5 launches (CUDA events)"}
+
+
+def bench_plain(args, binding, dist, dev, rank, world, local, case, desc):
+    """One jet (or the dam break): autotune, W warm-up steps, then exactly K
+    timed steps starting with a forced cell rebuild, then a steady-state
+    window of at least 64 rebuild cadences, per-kernel attribution, the
+    roofline of the dominant kernel group, end to end through the ABI, and
+    the CPU oracle."""
+    import torch
+    peaks = measured_peaks(binding, local)
+    free0 = torch.cuda.mem_get_info(dev)[0]
     stream = torch.cuda.Stream(device=dev)
     sim = binding.Simulation(case, stream=stream.cuda_stream, device=local)
     ctx = sim.ctx
+    resident = max(free0 - torch.cuda.mem_get_info(dev)[0], 0)
+    l2_bytes = 129 * 1024 * 1024
+    flush_l2 = resident < 2 * l2_bytes
     if args.tune == "auto":
         lanes, cadence, _ = binding.sph_autotune(ctx, 24)
         form = binding.sph_get_start_form(ctx)
@@ -366,53 +425,87 @@ def main():
     pairs_per_particle = len(pa) / max(n0, 1)
     del pa
 
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = (torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+             if flush_l2 else None)
     for _ in range(max(args.warmup, 0)):
         binding.sph_run_async(ctx, 1)
         binding.sph_sync(ctx)
 
     def timed(K, profile):
-        """K steps, each bracketed by CUDA events on the library's stream, with
-        an L2 flush before each step outside the events."""
-        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        """K steps.  Small states (resident set below twice the L2): each step
+        bracketed by CUDA events on the library's stream with an L2 flush
+        before it, outside the events.  Large states: the K steps back to
+        back between two events (the inputs do not fit in L2).  The breakup
+        length (every 100 steps) is inside the timed region."""
         nact = np.zeros(K, np.int64)
         Ls = []
         n_now = binding.sph_get_time(ctx)["n"]
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
-        for k in range(K):
-            nact[k] = n_now
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            ev0[k].record(stream)
-            binding.sph_run_async(ctx, 1)
-            if has_inflow and not profile and (k + 1) % BREAKUP_EVERY == 0:
+        if flush is not None or profile:
+            ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+            ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+            for k in range(K):
+                nact[k] = n_now
+                if flush is not None:
+                    with torch.cuda.stream(stream):
+                        flush.zero_()
+                ev0[k].record(stream)
+                binding.sph_run_async(ctx, 1)
+                if has_inflow and not profile and (k + 1) % BREAKUP_EVERY == 0:
+                    Ls.append(binding.sph_breakup_length(ctx)[0])
+                ev1[k].record(stream)
+                binding.sph_sync(ctx)
+                if (k + 1) % 50 == 0:
+                    n_now = binding.sph_get_time(ctx)["n"]
+            torch.cuda.synchronize(dev)
+            ms = np.array([ev0[k].elapsed_time(ev1[k]) for k in range(K)])
+            return ms, nact, Ls
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        done = 0
+        while done < K:
+            chunk = min(BREAKUP_EVERY - done % BREAKUP_EVERY, K - done)
+            nact[done:done + chunk] = n_now
+            binding.sph_run_async(ctx, chunk)
+            done += chunk
+            if has_inflow and done % BREAKUP_EVERY == 0:
                 Ls.append(binding.sph_breakup_length(ctx)[0])
-            ev1[k].record(stream)
-            binding.sph_sync(ctx)
-            if (k + 1) % 50 == 0:
                 n_now = binding.sph_get_time(ctx)["n"]
+        e1.record(stream)
+        binding.sph_sync(ctx)
         torch.cuda.synchronize(dev)
-        ms = np.array([ev0[k].elapsed_time(ev1[k]) for k in range(K)])
-        return ms, nact, Ls
+        total = e0.elapsed_time(e1)
+        return np.full(K, total / K), nact, Ls
+
+    def window(K):
+        """K timed steps from a forced rebuild; (ms per step, active counts,
+        breakup lengths, steps that rebuilt, wall seconds, clocks)."""
+        binding.sph_request_rebuild(ctx)
+        clocks = ClockSampler(local)
+        b0 = binding.sph_get_rebuild_stats(ctx)[0]
+        t0 = time.perf_counter()
+        ms, nact, Ls = timed(K, profile=False)
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+        # cell sorts in the window: one per rebuilding step and one per
+        # breakup-length evaluation
+        full = binding.sph_get_rebuild_stats(ctx)[0] - b0 - len(Ls)
+        return ms, nact, Ls, full, wall, clk
 
     K = args.steps
-    clocks = ClockSampler(local)
-    builds0 = binding.sph_get_rebuild_stats(ctx)[0]
-    t_wall0 = time.perf_counter()
-    step_ms, nact, Ls = timed(K, profile=False)
-    wall = time.perf_counter() - t_wall0
-    clk = clocks.stop()
+    step_ms, nact, Ls, full_steps, wall, clk = window(K)
     nbreak = len(Ls)
-    # cell sorts in the timed region: one per rebuilding step and one per
-    # breakup-length evaluation
-    full_steps = binding.sph_get_rebuild_stats(ctx)[0] - builds0 - nbreak
     from paper_1603_02421_gb300.replicas import reduce_rate
     value, total_s, units = reduce_rate(step_ms.sum() / 1e3, float(nact.sum()), dist, dev)
     if dist is not None:
         dist.barrier()
+    # steady state: enough steps for many rebuild cycles and inflow layers
+    Ks = max(K, 64 * cadence, 1000)
+    s_ms, s_nact, s_Ls, s_full, s_wall, s_clk = window(Ks)
+    steady_value = float(s_nact.sum()) / (s_ms.sum() / 1e3)
 
     # per-kernel attribution: the same steps with a CUDA event before each
     # kernel group (captured into the step graph)
@@ -420,7 +513,7 @@ def main():
     binding.sph_run_async(ctx, 1)
     binding.sph_sync(ctx)
     binding.sph_profile(ctx, 1)
-    Kp = min(K, 100)
+    Kp = min(Ks, 200)
     prof_ms, _, _ = timed(Kp, profile=True)
     prof = binding.sph_profile_report(ctx)
     binding.sph_profile(ctx, 0)
@@ -430,23 +523,25 @@ def main():
     dom_ms, dom_launches = prof[dom]
     avg_s = dom_ms / 1e3 / max(dom_launches, 1)
     n_mean = float(nact.mean())
-    sm_mhz = clk["sm_mhz"] if clk else 1900.0
     if dom in FLOP_PER_PAIR:
         flops = n_mean * (pairs_per_particle * FLOP_PER_PAIR[dom] + FLOP_PER_PARTICLE[dom])
         achieved = flops / avg_s / 1e12
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        fp64 = case["params"].get("prec") == "fp64"
+        peak = peaks["fp64_tflops" if fp64 else "fp32_tflops"]
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": measured_traffic(dom, n_mean),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (median SM clock "
-                               "sampled during the timed region)" % sm_mhz,
+                "peak_source": "measured on this GPU by the library's FMA probe (sph_fma_peak, "
+                               "%s, median SM clock %s MHz during the probe)"
+                               % ("FP64" if fp64 else "FP32",
+                                  peaks["clocks"]["sm_mhz"] if peaks["clocks"] else "n/a"),
                 "algorithmic_per_launch": flops}
     else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         nbytes = n_mean * BYTES_PER_PARTICLE.get(dom, 0)
         achieved = nbytes / avg_s / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": mp["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / mp["hbm_gbs"],
                 "traffic": measured_traffic(dom, n_mean),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "algorithmic_per_launch": nbytes}
@@ -456,47 +551,68 @@ def main():
     if rank == 0:
         e2e = end_to_end(binding, case, stream, local, K=min(K, 100), tuning=(lanes, cadence, form))
 
-    # ---- CPU baseline (oracle) on a bounded sample -----------------------
+    # ---- CPU baseline (oracle) on a bounded sample: 1 thread, all cores ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = oracle_sample(case)
-        psteps, nsteps, el, n = run_oracle(sample, args.cpu_seconds)
-        cpu = {"value": psteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "FP64 CPU oracle (single thread), %d steps of the upstream %d "
-                         "particles of the same workload, %.1f s" % (nsteps, n, el)}
+        cpu = cpu_baseline(case, args.cpu_seconds)
 
     launches = full_steps * per_full + (K - full_steps) * per_reuse + nbreak * per_breakup
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if case["params"].get("prec") == "fp64" else "f32",
-            "data": "synthetic",
-            "config": {"workload": args.workload + ": " + desc,
-                       "particles_mean": n_mean, "parallelism": "replicas (one jet per GPU)",
-                       "l2": "flushed between timed steps (256 MiB write)",
-                       "tuning": {"lanes": lanes, "cadence": cadence,
-                                  "start_form": FORM_NAMES[form], "skin_over_h": args.skin,
-                                  "chosen_by": "autotuner" if args.tune == "auto" else "flag",
-                                  "rebuild_fraction": full_steps / K},
-                       "breakup_every": BREAKUP_EVERY if has_inflow else None,
-                       "pairs_per_particle": pairs_per_particle,
-                       "wall_s": wall},
-            "roofline": roof,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clk,
-            "kernel_ms_per_step": {k: v[0] / Kp for k, v in prof.items()},
-            "attribution": {"steps": Kp, "ms_per_step_with_events": float(prof_ms.mean()),
-                            "how": "CUDA event before each kernel group inside the step graph"},
-            "breakup_L_over_D": Ls,
-        }
-        print(json.dumps(line), flush=True)
-    sim.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if case["params"].get("prec") == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload + ": " + desc,
+                   "particles_mean": n_mean, "parallelism": "replicas (one jet per GPU)",
+                   "l2": ("flushed between timed steps (256 MiB write)" if flush_l2 else
+                          "inputs larger than L2 (%.2f GB resident), steps back to back"
+                          % (resident / 1e9)),
+                   "tuning": {"lanes": lanes, "cadence": cadence,
+                              "start_form": FORM_NAMES[form], "skin_over_h": args.skin,
+                              "chosen_by": "autotuner" if args.tune == "auto" else "flag",
+                              "rebuild_fraction": full_steps / K,
+                              "first_timed_step": "forced cell rebuild"},
+                   "breakup_every": BREAKUP_EVERY if has_inflow else None,
+                   "pairs_per_particle": pairs_per_particle,
+                   "wall_s": wall},
+        "steady_state": {"value": steady_value, "steps": Ks,
+                         "ms_per_step": float(s_ms.sum()) / Ks,
+                         "rebuild_fraction": s_full / Ks, "breakups": len(s_Ls),
+                         "clocks": s_clk,
+                         "how": "a second window of max(K, 64 x cadence, 1000) steps from a "
+                                "forced rebuild"},
+        "roofline": roof,
+        "measured_peaks": peaks,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "kernel_ms_per_step": {k: v[0] / Kp for k, v in prof.items()},
+        "attribution": {"steps": Kp, "ms_per_step_with_events": float(prof_ms.mean()),
+                        "how": "CUDA event before each kernel group inside the step graph"},
+        "breakup_L_over_D": Ls,
+    }
+    return line, sim
+
+
+def cpu_baseline(case, seconds):
+    """The FP64 oracle on a bounded sample of the workload (its upstream part),
+    timed with 1 thread and with every host core."""
+    from oracle import oracle as orc
+    orc.build()
+    sample = oracle_sample(case)
+    cores = orc.max_threads()
+    orc.set_threads(1)
+    p1, n1, e1, n = run_oracle(sample, seconds / 3.0)
+    orc.set_threads(cores)
+    pa, na, ea, n = run_oracle(sample, 2.0 * seconds / 3.0)
+    orc.set_threads(1)
+    return {"value": pa / ea, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread": {"value": p1 / e1, "cores": 1, "steps": n1, "seconds": e1},
+            "sample": "FP64 CPU oracle on the upstream %d particles of the same workload: "
+                      "%d steps on %d threads (OpenMP over particles) in %.1f s, and %d steps "
+                      "on 1 thread in %.1f s" % (n, na, cores, ea, n1, e1)}
 
 
 def parse_tune(text):
@@ -544,11 +660,13 @@ def end_to_end(binding, case, stream, local, K, tuning):
                    "each step), sph_get_state; host wall clock" % K}
 
 
-def bench_ensemble(args, binding, dist, dev, rank, world, local):
+def bench_ensemble(args, binding, dist, dev, rank, world, local, steps=None, emit=True,
+                   cpu=True):
     """The 64-member ensemble: ensemble steps (one graph launch advancing
     every member one step) against the plain form (each member's own step
     graph, one member after another) on the same stream.  Ranks own members
-    round-robin (weak scaling over members, no exchange)."""
+    round-robin (weak scaling over members, no exchange).  Returns the bench
+    line (printed by rank 0 when emit)."""
     import torch
     from paper_1603_02421_gb300.replicas import rank_members, reduce_rate
     specs = [ensemble_members()[m] for m in rank_members(rank, world, 64)]
@@ -579,7 +697,7 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local):
     def builds():
         return [sm.rebuild_stats()[0] for sm in sims]
 
-    K = args.steps
+    K = args.steps if steps is None else steps
     ens.run(max(args.warmup, 1))
     # plain: every member's own step graph (captured on first use), then timed
     for sm in sims:
@@ -656,14 +774,11 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local):
     sm_mhz = clk["sm_mhz"] if clk else 1900.0
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = flop_ps * value / world / 1e12
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    cpu_line = None
+    if cpu and rank == 0 and world == 1 and not args.no_cpu_baseline:
         m, re, we, dx, length = specs[0]
-        sample = oracle_sample(ensemble_case(m, re, we, dx, length, args.skin), 20000)
-        psteps, nsteps, el, n = run_oracle(sample, args.cpu_seconds)
-        cpu = {"value": psteps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "FP64 CPU oracle (single thread), %d steps of member 0 (%d "
-                         "particles), %.1f s" % (nsteps, n, el)}
+        cpu_line = cpu_baseline(ensemble_case(m, re, we, dx, length, args.skin), args.cpu_seconds)
+    line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -692,7 +807,7 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local):
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz,
                          "algorithmic_per_particle_step": flop_ps,
                          "pairs_per_particle": pairs_pp},
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu_line,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / Ke,
                     "d2h_bytes_per_step": d2h / Ke,
                     "how": "sph_set_state of every member from pinned host arrays, %d "
@@ -702,10 +817,20 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local):
             "clocks": clk,
             "breakup_L_over_D_mean": float(np.mean(Ls)),
         }
-        print(json.dumps(line), flush=True)
+        # flat copies of the keys the plain line quotes
+        line["workload"] = line["config"]["workload"]
+        line["plain_value"] = line["config"]["plain_value"]
+        line["batched_over_plain"] = line["config"]["batched_over_plain"]
+        line["particles_total"] = line["config"]["particles_total"]
+        line["tuning"] = line["config"]["tuning"]
+        if emit:
+            print(json.dumps({k: v for k, v in line.items()
+                              if k not in ("workload", "plain_value", "batched_over_plain",
+                                           "particles_total", "tuning")}), flush=True)
     ens.close()
     for sm in sims:
         sm.close()
+    return line
 
 
 # Learned-surrogate workload: training jets on the ensemble's Re x We grid and

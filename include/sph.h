@@ -271,6 +271,12 @@ sph_status sph_autotune(sph_ctx *ctx, int trial_steps, int *lanes, int *cadence,
 sph_status sph_get_rebuild_stats(sph_ctx *ctx, long long *builds, double *disp_max,
                                  double *step_max);
 
+/* The next step rebuilds the cells and neighbour lists (Sec. 2-7) whatever
+ * the cadence and the device's displacement test decide; the steps after it
+ * follow them again.  Results do not change (every build is exact); this
+ * only places a rebuild, e.g. at the start of a timed window. */
+sph_status sph_request_rebuild(sph_ctx *ctx);
+
 /* Number of device kernels (memsets excluded) launched at the current
  * settings by a step that rebuilds the cells and lists, by a step that reuses
  * the last build, and by one breakup-length evaluation.  At cadence 1 every
@@ -318,6 +324,16 @@ sph_status sph_pairs_noalloc(const double *x, const double *y, long long n, doub
                              double xmin, double ymin, double xmax, double ymax,
                              unsigned *pair_a, unsigned *pair_b, long long cap,
                              long long *npairs, void *stream);
+
+/* Arithmetic peak of `device` (no counterpart in the paper): the fused
+ * multiply-add rate of the SIMT pipes in `precision` (SPH_FP32 or SPH_FP64),
+ * the bound of the pair sweeps, which are FP32 (or FP64) arithmetic on
+ * irregular neighbour sets rather than dense contractions.  Every SM is
+ * filled with threads running 8 independent FMA chains each; *tflops
+ * receives 2 x FMAs / time of the best of 5 launches timed with CUDA events,
+ * *ms that launch's duration (both nullable).  Runs at whatever clocks the
+ * device is at; changes no device setting.  Allocates a small output buffer. */
+sph_status sph_fma_peak(int device, int precision, double *tflops, double *ms);
 
 /* ------------------------------------------------------------------------
  * Ensembles: several independent simulations (e.g. jets on a grid of Re and

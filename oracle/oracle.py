@@ -39,13 +39,17 @@ CUBIC, WENDLAND = 0, 1
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle's C file into ``oracle/liboracle.so`` with gcc."""
+    """Compile the oracle's C file into ``oracle/liboracle.so`` with gcc
+    (with OpenMP where the compiler has it; the particle loops then run on
+    ``set_threads`` threads, 1 by default, with identical results)."""
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-             "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:],
+                           stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -107,10 +111,24 @@ def lib():
         _lib.orc_summation_density.restype = ctypes.c_int
         _lib.orc_summation_density.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(_State),
                                                _dp]
+        _lib.orc_set_threads.restype = None
+        _lib.orc_set_threads.argtypes = [ctypes.c_int]
+        _lib.orc_max_threads.restype = ctypes.c_int
+        _lib.orc_max_threads.argtypes = []
         _lib.orc_components.restype = ctypes.c_longlong
         _lib.orc_components.argtypes = [ctypes.c_longlong, _dp, _dp, ctypes.c_double,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's particle loops (results do not depend on it)."""
+    lib().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    """The host's OpenMP thread count (1 when built without OpenMP)."""
+    return int(lib().orc_max_threads())
 
 
 def _d(a):

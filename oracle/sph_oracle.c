@@ -13,6 +13,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_PI 3.14159265358979323846
 
@@ -118,101 +121,138 @@ static int is_pair(const double *x, const double *y, long long a, long long b, d
     return r2 < r2max;
 }
 
+/* Threads of the particle loops (OpenMP, when the oracle is built with it).
+ * Every particle's sums keep their fixed ascending-neighbour order whatever
+ * the thread count, so results do not depend on it. */
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Candidates of particle a: every b of the 3x3 cell block (cell mode) or
+ * every particle (brute force).  Pass 1 counts the pairs of each particle,
+ * pass 2 writes them at the offsets of the counts; both visit candidates in
+ * the same order, and each particle's list is then sorted ascending. */
+typedef struct {
+    long long n, ncx, ncy;
+    const double *x, *y;
+    const unsigned char *active;
+    double r2max;
+    int use_cells;
+    const long long *head, *next, *cid;
+} nb_grid;
+
+static long long visit(const nb_grid *G, long long a, int *out)
+{
+    long long k = 0;
+    if (G->active && !G->active[a]) return 0;
+    if (!G->use_cells) {
+        for (long long b = 0; b < G->n; ++b) {
+            if (b == a || (G->active && !G->active[b])) continue;
+            if (!is_pair(G->x, G->y, a, b, G->r2max)) continue;
+            if (out) out[k] = (int)b;
+            ++k;
+        }
+        return k;
+    }
+    if (G->cid[a] < 0) return 0;
+    long long cx = G->cid[a] % G->ncx, cy = G->cid[a] / G->ncx;
+    for (long long jy = cy - 1; jy <= cy + 1; ++jy) {
+        if (jy < 0 || jy >= G->ncy) continue;
+        for (long long jx = cx - 1; jx <= cx + 1; ++jx) {
+            if (jx < 0 || jx >= G->ncx) continue;
+            for (long long b = G->head[jy * G->ncx + jx]; b >= 0; b = G->next[b]) {
+                if (b == a || !is_pair(G->x, G->y, a, b, G->r2max)) continue;
+                if (out) out[k] = (int)b;
+                ++k;
+            }
+        }
+    }
+    return k;
+}
+
 long long orc_neighbours(long long n, const double *x, const double *y,
                          const unsigned char *active, double radius,
                          int use_cells, long long **start_out, int **list_out)
 {
-    double r2max = radius * radius;
+    nb_grid G;
+    memset(&G, 0, sizeof(G));
+    G.n = n; G.x = x; G.y = y; G.active = active;
+    G.r2max = radius * radius;
+    G.use_cells = use_cells;
+    G.ncx = G.ncy = 1;
     long long *start = (long long *)calloc((size_t)n + 1, sizeof(long long));
-    long long cap = 16 * (n > 0 ? n : 1), total = 0;
-    int *list = (int *)malloc((size_t)cap * sizeof(int));
-    if (!start || !list) { free(start); free(list); return -1; }
+    long long *head = NULL, *next = NULL, *cid = NULL;
+    if (!start) return -1;
 
-    if (!use_cells) {
+    if (use_cells) {
+        /* cell list: square cells slightly larger than the search radius */
+        double cell = radius * 1.01;
+        double x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY;
         for (long long a = 0; a < n; ++a) {
-            start[a] = total;
             if (active && !active[a]) continue;
-            for (long long b = 0; b < n; ++b) {
-                if (b == a || (active && !active[b])) continue;
-                if (!is_pair(x, y, a, b, r2max)) continue;
-                if (total == cap) {
-                    cap *= 2;
-                    int *nl = (int *)realloc(list, (size_t)cap * sizeof(int));
-                    if (!nl) { free(start); free(list); return -1; }
-                    list = nl;
-                }
-                list[total++] = (int)b;
-            }
+            if (x[a] < x0) x0 = x[a];
+            if (y[a] < y0) y0 = y[a];
+            if (x[a] > x1) x1 = x[a];
+            if (y[a] > y1) y1 = y[a];
         }
-        start[n] = total;
-        *start_out = start;
-        *list_out = list;
-        return total;
+        if (x1 >= x0) {
+            G.ncx = (long long)floor((x1 - x0) / cell) + 1;
+            G.ncy = (long long)floor((y1 - y0) / cell) + 1;
+        }
+        long long ncell = G.ncx * G.ncy;
+        head = (long long *)malloc((size_t)ncell * sizeof(long long));
+        next = (long long *)malloc(((size_t)n + 1) * sizeof(long long));
+        cid = (long long *)malloc(((size_t)n + 1) * sizeof(long long));
+        if (!head || !next || !cid) {
+            free(head); free(next); free(cid); free(start);
+            return -1;
+        }
+        for (long long c = 0; c < ncell; ++c) head[c] = -1;
+        /* push in descending index so that each cell's chain is ascending */
+        for (long long a = n - 1; a >= 0; --a) {
+            cid[a] = -1;
+            if (active && !active[a]) continue;
+            long long cx = (long long)floor((x[a] - x0) / cell);
+            long long cy = (long long)floor((y[a] - y0) / cell);
+            if (cx >= G.ncx) cx = G.ncx - 1;
+            if (cy >= G.ncy) cy = G.ncy - 1;
+            cid[a] = cy * G.ncx + cx;
+            next[a] = head[cid[a]];
+            head[cid[a]] = a;
+        }
+        G.head = head; G.next = next; G.cid = cid;
     }
 
-    /* cell list */
-    double cell = radius * 1.01;
-    double x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY;
-    for (long long a = 0; a < n; ++a) {
-        if (active && !active[a]) continue;
-        if (x[a] < x0) x0 = x[a];
-        if (y[a] < y0) y0 = y[a];
-        if (x[a] > x1) x1 = x[a];
-        if (y[a] > y1) y1 = y[a];
-    }
-    long long ncx = 1, ncy = 1;
-    if (x1 >= x0) {
-        ncx = (long long)floor((x1 - x0) / cell) + 1;
-        ncy = (long long)floor((y1 - y0) / cell) + 1;
-    }
-    long long ncell = ncx * ncy;
-    long long *head = (long long *)malloc((size_t)ncell * sizeof(long long));
-    long long *next = (long long *)malloc(((size_t)n + 1) * sizeof(long long));
-    long long *cid = (long long *)malloc(((size_t)n + 1) * sizeof(long long));
-    if (!head || !next || !cid) {
-        free(head); free(next); free(cid); free(start); free(list);
+    /* pass 1: counts; prefix sum into start */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(g_threads)
+#endif
+    for (long long a = 0; a < n; ++a) start[a + 1] = visit(&G, a, NULL);
+    for (long long a = 0; a < n; ++a) start[a + 1] += start[a];
+    long long total = start[n];
+    int *list = (int *)malloc((size_t)(total > 0 ? total : 1) * sizeof(int));
+    if (!list) {
+        free(head); free(next); free(cid); free(start);
         return -1;
     }
-    for (long long c = 0; c < ncell; ++c) head[c] = -1;
-    /* push in descending index so that each cell's chain is ascending */
-    for (long long a = n - 1; a >= 0; --a) {
-        cid[a] = -1;
-        if (active && !active[a]) continue;
-        long long cx = (long long)floor((x[a] - x0) / cell);
-        long long cy = (long long)floor((y[a] - y0) / cell);
-        if (cx >= ncx) cx = ncx - 1;
-        if (cy >= ncy) cy = ncy - 1;
-        cid[a] = cy * ncx + cx;
-        next[a] = head[cid[a]];
-        head[cid[a]] = a;
-    }
+    /* pass 2: fill, each list ascending in b */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(g_threads)
+#endif
     for (long long a = 0; a < n; ++a) {
-        start[a] = total;
-        if (cid[a] < 0) continue;
-        long long cx = cid[a] % ncx, cy = cid[a] / ncx;
-        long long first = total;
-        for (long long jy = cy - 1; jy <= cy + 1; ++jy) {
-            if (jy < 0 || jy >= ncy) continue;
-            for (long long jx = cx - 1; jx <= cx + 1; ++jx) {
-                if (jx < 0 || jx >= ncx) continue;
-                for (long long b = head[jy * ncx + jx]; b >= 0; b = next[b]) {
-                    if (b == a || !is_pair(x, y, a, b, r2max)) continue;
-                    if (total == cap) {
-                        cap *= 2;
-                        int *nl = (int *)realloc(list, (size_t)cap * sizeof(int));
-                        if (!nl) {
-                            free(head); free(next); free(cid); free(start); free(list);
-                            return -1;
-                        }
-                        list = nl;
-                    }
-                    list[total++] = (int)b;
-                }
-            }
-        }
-        qsort(list + first, (size_t)(total - first), sizeof(int), cmp_int);
+        long long k = visit(&G, a, list + start[a]);
+        (void)k;
+        qsort(list + start[a], (size_t)(start[a + 1] - start[a]), sizeof(int), cmp_int);
     }
-    start[n] = total;
     free(head); free(next); free(cid);
     *start_out = start;
     *list_out = list;
@@ -290,6 +330,9 @@ int orc_evaluate(const orc_params *p, const orc_state *s, orc_out *o)
     }
 
     /* Eq. 26 and the sound-speed reading; V_b = m_b / rho_b (Eq. 4). */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(g_threads)
+#endif
     for (long long a = 0; a < n; ++a) {
         P[a] = orc_pressure(s->rho[a], p->rho0, p->c0, p->gamma);
         c[a] = orc_sound_speed(s->rho[a], p->rho0, p->c0, p->gamma);
@@ -303,6 +346,9 @@ int orc_evaluate(const orc_params *p, const orc_state *s, orc_out *o)
     if (p->sigma > 0.0) {
         double W0 = orc_W(K, 0.0, h);
         /* Eq. 14: colour C_a = sum_b V_b W_ab, the particle itself included. */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(g_threads)
+#endif
         for (long long a = 0; a < n; ++a) {
             double sum = V[a] * W0;
             for (long long k = start[a]; k < start[a + 1]; ++k) {
@@ -315,6 +361,9 @@ int orc_evaluate(const orc_params *p, const orc_state *s, orc_out *o)
         }
         /* Eq. 18: n_a = sum_b V_b (C_b - C_a) grad_a W_ab;
          * Eq. 20: N_a = 1 if |n_a| > eps; Eq. 21: unit normal or zero. */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(g_threads)
+#endif
         for (long long a = 0; a < n; ++a) {
             double sx = 0.0, sy = 0.0;
             for (long long k = start[a]; k < start[a + 1]; ++k) {
@@ -340,6 +389,9 @@ int orc_evaluate(const orc_params *p, const orc_state *s, orc_out *o)
          *           / sum_b min(N_a,N_b) V_b W_ab,
          * the denominator including the particle itself; kappa = 0 when the
          * denominator vanishes (N_a = 0). */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(g_threads)
+#endif
         for (long long a = 0; a < n; ++a) {
             if (!o->Nflag[a]) continue;
             double num = 0.0, den = V[a] * W0;
@@ -356,6 +408,9 @@ int orc_evaluate(const orc_params *p, const orc_state *s, orc_out *o)
         }
     }
 
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(g_threads)
+#endif
     for (long long a = 0; a < n; ++a) {
         o->ax[a] = 0.0; o->ay[a] = 0.0; o->drho[a] = 0.0;
         o->dt_f[a] = INFINITY; o->dt_cv[a] = INFINITY;
@@ -463,6 +518,9 @@ int orc_summation_density(const orc_params *p, const orc_state *s, double *rho)
     if (orc_neighbours(n, s->x, s->y, NULL, 2.0 * h, p->use_cells, &start, &nb) < 0)
         return -1;
     double W0 = orc_W(K, 0.0, h);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(g_threads)
+#endif
     for (long long a = 0; a < n; ++a) {
         double sum = s->m[a] * W0;
         for (long long k = start[a]; k < start[a + 1]; ++k) {

@@ -74,6 +74,12 @@ long long orc_neighbours(long long n, const double *x, const double *y,
                          int use_cells, long long **start, int **list);
 void orc_free(void *p);
 
+/* Threads of the particle loops when built with OpenMP (default 1).  Each
+ * particle's sums keep their order, so results do not depend on it.
+ * orc_max_threads() is the host's OpenMP thread count (1 without OpenMP). */
+void orc_set_threads(int n);
+int orc_max_threads(void);
+
 /* One evaluation of the right-hand sides at a given state (Sec. 2-2 to 2-8).
  * Returns 0 on success, -1 on allocation failure. */
 int orc_evaluate(const orc_params *p, const orc_state *s, orc_out *o);

@@ -86,6 +86,8 @@ _SIGS = {
     "sph_kernel_counts": ([_CTX, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sph_get_rebuild_stats": ([_CTX, _LL, _D, _D], ctypes.c_int),
+    "sph_request_rebuild": ([_CTX], ctypes.c_int),
+    "sph_fma_peak": ([ctypes.c_int, ctypes.c_int, _D, _D], ctypes.c_int),
     "sph_ensemble_create": ([ctypes.POINTER(_CTX), ctypes.c_int, ctypes.c_void_p,
                              ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "sph_ensemble_run": ([ctypes.c_void_p, ctypes.c_longlong], ctypes.c_int),
@@ -308,6 +310,21 @@ def sph_get_rebuild_stats(ctx):
     _check(ctx, lib().sph_get_rebuild_stats(ctx, ctypes.byref(b), ctypes.byref(d),
                                             ctypes.byref(m)))
     return b.value, d.value, m.value
+
+
+def sph_request_rebuild(ctx):
+    """The next step rebuilds the cells and neighbour lists."""
+    _check(ctx, lib().sph_request_rebuild(ctx))
+
+
+def sph_fma_peak(device=0, precision=0):
+    """(TFLOP/s, ms of the best launch) of the device's FMA pipes in FP32
+    (precision 0) or FP64 (1)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    st = lib().sph_fma_peak(int(device), int(precision), ctypes.byref(t), ctypes.byref(ms))
+    if st != SPH_OK:
+        raise SphError(st, "sph_fma_peak failed")
+    return t.value, ms.value
 
 
 def sph_set_tuning(ctx, lanes, cadence):

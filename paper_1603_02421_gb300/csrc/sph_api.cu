@@ -1448,6 +1448,12 @@ sph_status sph_get_rebuild_stats(sph_ctx *c, long long *builds, double *disp_max
     return SPH_OK;
 }
 
+sph_status sph_request_rebuild(sph_ctx *c) {
+    if (!c) return SPH_ERR_ARG;
+    c->force_full = true;
+    return SPH_OK;
+}
+
 sph_status sph_kernel_counts(sph_ctx *c, int *per_full_step, int *per_reused_step,
                              int *per_breakup) {
     if (!c) return SPH_ERR_ARG;

@@ -51,6 +51,14 @@ def _traj_errors(g, st):
             rel_l2(g["rho"], st["rho"]))
 
 
+def _drho_error(g, st, rho0):
+    """rel-L2 of the density offset rho - rho0 (what drives the pressure)."""
+    off = np.asarray(st["rho"]) - rho0
+    if np.abs(off).max() == 0:
+        return 0.0
+    return rel_l2(np.asarray(g["rho"]) - rho0, off)
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
 def test_dam_break_full_size_100_steps(sph, orc, prec, tol):
     case = wl.dam_break(seed=0, dx=0.01, prec=prec)
@@ -76,11 +84,14 @@ def test_jet_c2_full_size_evaluation_and_step(sph, orc):
     ed = rel_l2(g["drho"], ev["drho"]) if np.abs(ev["drho"]).max() > 0 else 0.0
     sim.step()
     osim.step()
-    er, eu, erho = _traj_errors(sim.state(), osim.st)
+    g1 = sim.state()
+    er, eu, erho = _traj_errors(g1, osim.st)
+    eoff = _drho_error(g1, osim.st, osim.d.rho0)
     report(case="jet_c2", prec="fp32", accel=ea, drho_dt=ed, masked=int((~keep).sum()),
-           step_r=er, step_u=eu, step_rho=erho)
+           step_r=er, step_u=eu, step_rho=erho, step_rho_offset=eoff)
     assert ea < 1e-5 and ed < 1e-5
     assert erho < 1e-6 and eu < 1e-5 and er < 1e-6
+    assert eoff < 1e-4
 
 
 def test_jet_c2_full_size_100_steps(sph, orc):
@@ -89,9 +100,41 @@ def test_jet_c2_full_size_100_steps(sph, orc):
     osim = oracle_sim(orc, case)
     sim.run(100)
     osim.run(100)
-    er, eu, erho = _traj_errors(sim.state(), osim.st)
-    report(case="jet_c2", prec="fp32", steps=100, r=er, u=eu, rho=erho)
+    g = sim.state()
+    er, eu, erho = _traj_errors(g, osim.st)
+    eoff = _drho_error(g, osim.st, osim.d.rho0)
+    report(case="jet_c2", prec="fp32", steps=100, r=er, u=eu, rho=erho, rho_offset=eoff)
     assert er < 1e-4 and eu < 1e-4 and erho < 1e-4
+    assert eoff < 1e-2
+
+
+def test_jet_c3_full_size_100_steps(sph, orc):
+    # the 1M-particle jet of the benchmark (Re = 100, We = 10, dx = D/100,
+    # 100 D), 100 FP32 steps in the benchmark's launch configuration (graph
+    # replay at the skin and a reused-build cadence) against 100 FP64 oracle
+    # steps; the oracle runs on every host core (identical results)
+    case = wl.jet(seed=0, Re=100, We=10, dx=1.0 / 100, length=100.0, prec="fp32",
+                  capacity_factor=1.15)
+    case["params"]["skin_over_h"] = 0.15
+    sim = sph.Simulation(case)
+    sim.set_tuning(2, 16)
+    osim = oracle_sim(orc, case)
+    orc.set_threads(orc.max_threads())
+    try:
+        sim.run(100)
+        osim.run(100)
+    finally:
+        orc.set_threads(1)
+    g = sim.state()
+    sim.close()
+    assert len(g["x"]) > 990000
+    tg = (g["x"].size, osim.nstep)
+    er, eu, erho = _traj_errors(g, osim.st)
+    eoff = _drho_error(g, osim.st, osim.d.rho0)
+    report(case="jet_c3", prec="fp32", steps=100, r=er, u=eu, rho=erho, rho_offset=eoff,
+           particles=tg[0])
+    assert er < 1e-4 and eu < 1e-4 and erho < 1e-4
+    assert eoff < 1e-2
 
 
 @pytest.mark.parametrize("kernel", ["wendland", "cubic"])

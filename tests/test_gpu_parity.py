@@ -114,6 +114,8 @@ def test_evaluate_jet_with_inflow(sph, orc, prec):
     assert np.array_equal(g["type"], st["type"])
     amb = ambiguous_mask(orc, osim.d, st, ev)
     keep = ~amb
+    # the filter band of Eq. 20 may mask a few surface particles, not the jet
+    assert keep.mean() > 0.95
     assert rel_l2_vec(g["ax"][keep], g["ay"][keep], ev["ax"][keep], ev["ay"][keep]) < _tol(prec, 1e-5)
     assert rel_l2(g["drho"], ev["drho"]) < _tol(prec, 1e-5) or np.abs(ev["drho"]).max() == 0
 
@@ -121,12 +123,23 @@ def test_evaluate_jet_with_inflow(sph, orc, prec):
 # ---------------------------------------------------------------------------
 # one step and 100-step trajectories (Sec. 2-8)
 # ---------------------------------------------------------------------------
-def _compare_states(g, st, prec, tol_r, tol_u, tol_rho):
+def _compare_states(g, st, prec, tol_r, tol_u, tol_rho, rho0=None, tol_drho=None):
+    """Positions, velocities and densities against the oracle's state.  The
+    density is near rho0 everywhere, so its rel-L2 says little about the
+    density variation that drives the pressure; when rho0 is given, the
+    offset rho - rho0 is compared as well (rel-L2 <= tol_drho, default 100
+    tol_rho: an error of tol_rho in rho is ~1000 tol_rho of a 0.1 % offset)."""
     assert np.array_equal(g["id"], st["id"].astype(np.uint32))
     assert np.array_equal(g["type"], st["type"])
     assert rel_l2_vec(g["x"], g["y"], st["x"], st["y"]) < _tol(prec, tol_r)
     assert rel_l2_vec(g["u"], g["v"], st["u"], st["v"]) < _tol(prec, tol_u)
     assert rel_l2(g["rho"], st["rho"]) < _tol(prec, tol_rho)
+    if rho0 is not None:
+        off_o = np.asarray(st["rho"]) - rho0
+        if np.abs(off_o).max() > 0:
+            err = rel_l2(np.asarray(g["rho"]) - rho0, off_o)
+            tol = 100.0 * tol_rho if tol_drho is None else tol_drho
+            assert err < _tol(prec, tol), "rho - rho0 rel-L2 %.3g" % err
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -142,7 +155,7 @@ def test_one_step(sph, orc, prec, dt_fixed):
     dt_o = osim.step()
     assert dt_g == pytest.approx(dt_o, rel=_tol(prec, 1e-5))
     g = sim.state()
-    _compare_states(g, osim.st, prec, 1e-6, 1e-5, 1e-6)
+    _compare_states(g, osim.st, prec, 1e-6, 1e-5, 1e-6, rho0=osim.d.rho0, tol_drho=1e-5)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -157,7 +170,7 @@ def test_jet_trajectory_100_steps(sph, orc, prec):
     tg = sim.time()
     assert tg["steps"] == 100 and tg["t"] == pytest.approx(osim.t, rel=1e-12)
     assert tg["deleted"] == osim.deleted
-    _compare_states(g, osim.st, prec, 1e-4, 1e-4, 1e-4)
+    _compare_states(g, osim.st, prec, 1e-4, 1e-4, 1e-4, rho0=osim.d.rho0, tol_drho=1e-3)
 
 
 def test_dam_break_fp64_trajectory(sph, orc):
@@ -167,7 +180,7 @@ def test_dam_break_fp64_trajectory(sph, orc):
     sim.run(200)
     osim.run(200)
     g = sim.state()
-    _compare_states(g, osim.st, "fp64", 0, 0, 0)
+    _compare_states(g, osim.st, "fp64", 0, 0, 0, rho0=osim.d.rho0)
 
 
 def test_dam_break_fp32_trajectory(sph, orc):
@@ -176,7 +189,7 @@ def test_dam_break_fp32_trajectory(sph, orc):
     osim = oracle_sim(orc, case)
     sim.run(100)
     osim.run(100)
-    _compare_states(sim.state(), osim.st, "fp32", 1e-4, 1e-4, 1e-4)
+    _compare_states(sim.state(), osim.st, "fp32", 1e-4, 1e-4, 1e-4, rho0=osim.d.rho0)
 
 
 # ---------------------------------------------------------------------------
@@ -298,7 +311,7 @@ def test_cadence_keeps_dam_break_trajectory(sph, orc, cadence, lanes, form):
     osim = oracle_sim(orc, case)
     sim.run(120)
     osim.run(120)
-    _compare_states(sim.state(), osim.st, "fp64", 0, 0, 0)
+    _compare_states(sim.state(), osim.st, "fp64", 0, 0, 0, rho0=osim.d.rho0)
 
 
 def test_cadence_with_outflow_patch(sph, orc):
@@ -315,7 +328,7 @@ def test_cadence_with_outflow_patch(sph, orc):
     sim.run(60)
     osim.run(60)
     assert sim.time()["deleted"] == osim.deleted > 0
-    _compare_states(sim.state(), osim.st, "fp32", 1e-5, 1e-4, 1e-5)
+    _compare_states(sim.state(), osim.st, "fp32", 1e-5, 1e-4, 1e-5, rho0=osim.d.rho0)
 
 
 def test_autotune_restores_state(sph):
@@ -352,7 +365,7 @@ def test_jet_trajectory_with_reused_builds(sph, orc, prec):
     builds = sim.rebuild_stats()[0] - b0
     assert 150 // 8 <= builds < 75          # most steps reused a build
     assert sim.time()["deleted"] == osim.deleted
-    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4)
+    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4, rho0=osim.d.rho0)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -382,7 +395,7 @@ def test_jet_keeps_its_lists_in_the_velocity_frame(sph, orc, prec):
     assert builds <= 10, builds
     assert worst <= 0.15 * h * (1 + 1e-5)
     assert sim.time()["deleted"] == osim.deleted
-    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4)
+    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4, rho0=osim.d.rho0)
 
 
 @pytest.mark.parametrize("density", ["continuity", "summation"])
@@ -481,7 +494,7 @@ def test_summation_density_trajectory(sph, orc, prec, lanes, cadence):
     osim = oracle_sim(orc, case)
     sim.run(60)
     osim.run(60)
-    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4)
+    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4, rho0=osim.d.rho0)
 
 
 def test_summation_density_jet_with_inflow(sph, orc):
@@ -493,7 +506,7 @@ def test_summation_density_jet_with_inflow(sph, orc):
     sim.run(60)
     osim.run(60)
     assert sim.time()["deleted"] == osim.deleted
-    _compare_states(sim.state(), osim.st, "fp32", 1e-4, 1e-4, 1e-4)
+    _compare_states(sim.state(), osim.st, "fp32", 1e-4, 1e-4, 1e-4, rho0=osim.d.rho0)
 
 
 # ---------------------------------------------------------------------------
@@ -509,7 +522,7 @@ def test_nozzle_jet_trajectory(sph, orc, prec):
     sim.run(80)
     osim.run(80)
     assert sim.time()["deleted"] == osim.deleted
-    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4)
+    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4, rho0=osim.d.rho0)
 
 
 def test_inviscid_jet_trajectory(sph, orc):
@@ -521,4 +534,4 @@ def test_inviscid_jet_trajectory(sph, orc):
     osim = oracle_sim(orc, case)
     sim.run(80)
     osim.run(80)
-    _compare_states(sim.state(), osim.st, "fp32", 1e-4, 1e-4, 1e-4)
+    _compare_states(sim.state(), osim.st, "fp32", 1e-4, 1e-4, 1e-4, rho0=osim.d.rho0)

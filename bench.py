@@ -71,19 +71,23 @@ def workload(name: str, seed: int):
     return case, desc
 
 
-# Algorithmic FP32 operations per interacting pair (r < 2h) of each pair
-# sweep (Wendland), counting a fused multiply-add as 2 and rsqrt, sqrt and
-# division as 1 each; compares and selects are not counted.  Geometry (offset
-# difference with the cell shift, r^2, 1/r, q, 1/q) 11; W(q) 7; F(q) 4.
-#   colour: geometry + W + accumulate 2 = 20
-#   normal: geometry + F + weight 3 + accumulate 4 = 22
-#   forces: geometry + F + continuity 9 + viscosity 10 + pressure 8 + Eq. 31
-#           term 3 = 45 (the curvature sums add 17 for pairs of two
-#           free-surface particles; not counted)
-FLOP_PER_PAIR = {"list_colour": 20, "colour": 20, "normal": 22, "forces": 45,
-                 "forces_correct": 45}
-FLOP_PER_PARTICLE = {"list_colour": 2, "colour": 2, "normal": 8, "forces": 20,
+# Algorithmic FP32 operations per interacting pair (r < 2h) (Wendland),
+# counting a fused multiply-add as 2 and rsqrt, sqrt and division as 1 each;
+# compares and selects are not counted.  Geometry (offset difference with the
+# cell shift, r^2, 1/r, q, 1/q) 11; W(q) 7; F(q) 4; colour accumulate 2;
+# normal weight 3 + accumulate 4; forces: continuity 9 + viscosity 10 +
+# pressure 8 + Eq. 31 term 3 = 30.
+#   pairsum (with surface tension: colour and the state-only forces in one
+#           list walk): geometry + W + F + colour 2 + forces 30 = 54
+#   normal: geometry + F + 7 = 22 per pair walked
+#   forces (without surface tension, one walk): geometry + F + 30 = 45
+# The method itself (colour, normal and forces each with its own geometry,
+# as the equations are written) is 20 + 22 + 45 = 87 per pair and evaluation.
+FLOP_PER_PAIR = {"pairsum": 54, "pairsum_correct": 54, "normal": 22}
+FLOP_PER_PAIR_NO_CSF = {"forces": 45, "forces_correct": 45}
+FLOP_PER_PARTICLE = {"pairsum": 22, "pairsum_correct": 22, "normal": 8, "forces": 20,
                      "forces_correct": 30}
+FLOP_METHOD_PER_PAIR = 87
 # Algorithmic HBM bytes per particle of the streaming kernel groups (FP32 path).
 BYTES_PER_PARTICLE = {"cell_sort": 16 + 1 + 4 + 4 + 4 + 4 + 4, "reorder": 2 * 41 + 4 + 4 + 32,
                       "predict": 41 + 12 + 48, "spawn": 0}
@@ -523,8 +527,12 @@ def bench_plain(args, binding, dist, dev, rank, world, local, case, desc):
     dom_ms, dom_launches = prof[dom]
     avg_s = dom_ms / 1e3 / max(dom_launches, 1)
     n_mean = float(nact.mean())
-    if dom in FLOP_PER_PAIR:
-        flops = n_mean * (pairs_per_particle * FLOP_PER_PAIR[dom] + FLOP_PER_PARTICLE[dom])
+    csf = float(case["params"].get("sigma", 0.0)) > 0.0
+    per_pair = dict(FLOP_PER_PAIR) if csf else dict(FLOP_PER_PAIR_NO_CSF)
+    if csf:
+        per_pair.pop("normal")       # walked only near the surface: not a full-pair count
+    if dom in per_pair:
+        flops = n_mean * (pairs_per_particle * per_pair[dom] + FLOP_PER_PARTICLE[dom])
         achieved = flops / avg_s / 1e12
         fp64 = case["params"].get("prec") == "fp64"
         peak = peaks["fp64_tflops" if fp64 else "fp32_tflops"]
@@ -767,9 +775,7 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local, steps=None, emi
 
     # whole-step FP32 work against the FP32 peak (algorithmic FLOPs per
     # particle-step of the six pair sweeps and the per-particle work)
-    flop_ps = 2 * (pairs_pp * (FLOP_PER_PAIR["colour"] + FLOP_PER_PAIR["normal"] +
-                               FLOP_PER_PAIR["forces"]) +
-                   FLOP_PER_PARTICLE["colour"] + FLOP_PER_PARTICLE["normal"] +
+    flop_ps = 2 * (pairs_pp * FLOP_METHOD_PER_PAIR + 2 + FLOP_PER_PARTICLE["normal"] +
                    FLOP_PER_PARTICLE["forces_correct"])
     sm_mhz = clk["sm_mhz"] if clk else 1900.0
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12

@@ -51,6 +51,10 @@ struct sph_ctx {
     double2 *posh = nullptr;
     void *C = nullptr, *CX = nullptr, *nhat = nullptr, *nvec = nullptr;
     void *acc = nullptr, *dr = nullptr;
+    // with surface tension: pair sums of the full list walk (ax, ay, drho/dt,
+    // Eq. 31 term), the normal bound G_a, and the colour range of each cell
+    void *accN = nullptr, *gsum = nullptr;
+    uint2 *crange = nullptr;
     CellSort cs{};
     NList nl{};
     uint2 *cellSE = nullptr, *cellSE_b = nullptr;
@@ -310,95 +314,97 @@ template <class T> static const uint32_t *enqueue_sort(sph_ctx *c, int gate = GA
     return key;
 }
 
-// List build of evaluation n, fused with its colour when CSF is on.
+// Neighbour list of evaluation n (the colour comes with the evaluation's
+// pair sweep).
 template <class T>
 static void enqueue_build(sph_ctx *c, const uint32_t *key, int gate = GATE_ALWAYS) {
     const PhysT<T> &P = Ops<T>::phys(c);
-    tick(c, "list_colour");
+    tick(c, "list");
     // the list build walks ~61 candidates of the 3x3 cells per particle; it
     // takes at least 4 lanes per particle whatever the sweeps use
-    // with Eq. 6 densities the colour needs the summed volumes, so it runs
-    // after the density sweep instead of inside the list build
-    launch_build<T>(std::max(c->lanes, 4), P.csf != 0 && !P.summation, P, c->grid, c->sc,
-                    c->cellSE, key, hot_n<T>(c), c->nl, csf_of<T>(c), c->cap, c->stream, gate);
+    launch_build<T>(std::max(c->lanes, 4), false, P, c->grid, c->sc, c->cellSE, key,
+                    hot_n<T>(c), c->nl, csf_of<T>(c), c->cap, c->stream, gate);
 }
 
-// Eq. 6 densities of the records `hot` (a no-op with Eq. 7), then, when the
-// colour was not computed with the list, the colour of those records.
+// Eq. 6 densities of the records `hot` (a no-op with Eq. 7).
 // drho_out: where the state keeps the density (null at the half step).
 template <class T>
-static void enqueue_density(sph_ctx *c, const Hot<T> &hot, T *drho_out, bool colour,
-                            int gate = GATE_ALWAYS) {
+static void enqueue_density(sph_ctx *c, const Hot<T> &hot, T *drho_out, int gate = GATE_ALWAYS) {
     const PhysT<T> &P = Ops<T>::phys(c);
     if (!P.summation) return;
     State<T> srt = state_of<T>(c->srt);
     tick(c, "density");
     launch_density<T>(c->lanes, P, c->sc, c->nl, hot, srt.mass, srt.type, drho_out, c->cap,
                       c->stream, gate);
-    if (colour && P.csf) {
-        tick(c, "colour");
-        launch_colour<T>(c->lanes, P, c->sc, c->nl, hot, csf_of<T>(c), c->cap, c->stream, gate);
-    }
 }
 
-template <class T> static void enqueue_normal(sph_ctx *c, const Hot<T> &hot) {
+// One evaluation of the right-hand sides on the records `hot` and the lists
+// of the last build, ending in mode 0 (store), 1 (store + time-step minimum)
+// or 2 (corrector, writing the next records to nH0 / nH1).  Without surface
+// tension one list walk does everything; with it, one full walk (colour and
+// the state-only pair sums), the normal (skip: not walked where it provably
+// stays below the filter threshold) and the surface terms with the mode's end.
+template <class T>
+static void enqueue_eval(sph_ctx *c, const Hot<T> &hot, int mode, bool skip,
+                         typename Vec<T>::v4 *nH0 = nullptr, typename Vec<T>::v4 *nH1 = nullptr) {
     const PhysT<T> &P = Ops<T>::phys(c);
-    if (!P.csf) return;
+    State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
+    auto *acc = (typename Vec<T>::v2 *)c->acc;
+    T *dr = (T *)c->dr;
+    const uint32_t *key = c->cs.key;
+    const char *fname = mode == 2 ? "forces_correct" : "forces";
+    if (!P.csf) {
+        tick(c, fname);
+        launch_forces<T>(c->lanes, mode, P, c->grid, c->inf, c->sc, c->nl, key, hot,
+                         csf_of<T>(c), bd_of(c), srt, raw, acc, dr, c->cap, c->stream, nH0, nH1);
+        return;
+    }
+    auto *accN = (typename Vec<T>::v4 *)c->accN;
+    T *gsum = (T *)c->gsum;
+    tick(c, mode == 2 ? "pairsum_correct" : "pairsum");
+    cudaMemsetAsync(c->crange, 0xFF, (size_t)c->grid.ncells * sizeof(uint2), c->stream);
+    launch_pairsum<T>(c->lanes, P, c->grid, c->sc, c->nl, key, hot, csf_of<T>(c), bd_of(c),
+                      srt.type, accN, gsum, c->crange, c->cap, c->stream);
     tick(c, "normal");
-    launch_normal<T>(c->lanes, P, c->sc, c->nl, hot, csf_of<T>(c), c->cap, c->stream);
+    launch_normal<T>(c->lanes, P, c->sc, c->nl, hot, csf_of<T>(c), c->cap, c->stream, key,
+                     skip ? gsum : nullptr, c->crange, c->grid.ncx);
+    tick(c, fname);
+    launch_surface<T>(c->lanes, mode, P, c->grid, c->inf, c->sc, c->nl, hot, csf_of<T>(c), srt,
+                      raw, accN, acc, dr, c->cap, c->stream, nH0, nH1);
 }
 
 // The two ways a step starts.  Rebuild: hash, sort, reorder and neighbour
-// list (with the colour of evaluation n).  Reuse: the particles keep the
-// order, cells and lists of the last rebuild (exact while no particle has
-// moved more than skin/2 since, which the kernels check), and the state and
-// records of evaluation n are those the last corrector wrote in place, so
-// the start is only the colour (and the Eq. 6 densities).  gate: GATE_ALWAYS
-// when the host chose the start; otherwise the start's kernels run only on
-// the steps whose device flag selects it.
+// list.  Reuse: the particles keep the order, cells and lists of the last
+// rebuild (exact while no particle has moved more than skin/2 since, which
+// the kernels check), and the state and records of evaluation n are those
+// the last corrector wrote in place, so the start is only the Eq. 6
+// densities (when used).  gate: GATE_ALWAYS when the host chose the start;
+// otherwise the start's kernels run only on the steps whose device flag
+// selects it.
 template <class T> static void enqueue_cells(sph_ctx *c, bool full, int gate = GATE_ALWAYS) {
-    const PhysT<T> &P = Ops<T>::phys(c);
     State<T> srt = state_of<T>(c->srt);
     Hot<T> hn = hot_n<T>(c);
     const uint32_t *key = c->cs.key;
     if (full) {
         enqueue_sort<T>(c, gate);
         enqueue_build<T>(c, key, gate);
-        enqueue_density<T>(c, hn, srt.drho, true, gate);
-    } else {
-        enqueue_density<T>(c, hn, srt.drho, false, gate);
-        if (P.csf) {
-            tick(c, "colour");
-            launch_colour<T>(c->lanes, P, c->sc, c->nl, hn, csf_of<T>(c), c->cap, c->stream,
-                             gate);
-        }
     }
+    enqueue_density<T>(c, hn, srt.drho, gate);
 }
 
-// The rest of a step (Sec. 2-8): normal and forces at n, predictor, colour,
-// normal and forces at n+1/2 with the corrector, inflow and time advance.
+// The rest of a step (Sec. 2-8): evaluation at n, predictor, evaluation at
+// n+1/2 with the corrector, inflow and time advance.
 template <class T> static void enqueue_rest(sph_ctx *c) {
     const PhysT<T> &P = Ops<T>::phys(c);
     State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
     auto *acc = (typename Vec<T>::v2 *)c->acc;
     T *dr = (T *)c->dr;
     Hot<T> hn = hot_n<T>(c), hh = hot_h<T>(c);
-    const uint32_t *key = c->cs.key;
-    enqueue_normal<T>(c, hn);
-    tick(c, "forces");
-    launch_forces<T>(c->lanes, 1, P, c->grid, c->inf, c->sc, c->nl, key, hn, csf_of<T>(c),
-                     bd_of(c), srt, raw, acc, dr, c->cap, c->stream);
+    enqueue_eval<T>(c, hn, 1, true);
     tick(c, "predict");
     launch_predict<T>(P, c->inf, c->sc, srt, hn.H0, acc, dr, hh, c->cap, c->stream);
-    enqueue_density<T>(c, hh, (T *)nullptr, false);
-    if (P.csf) {
-        tick(c, "colour");
-        launch_colour<T>(c->lanes, P, c->sc, c->nl, hh, csf_of<T>(c), c->cap, c->stream);
-    }
-    enqueue_normal<T>(c, hh);
-    tick(c, "forces_correct");
-    launch_forces<T>(c->lanes, 2, P, c->grid, c->inf, c->sc, c->nl, key, hh, csf_of<T>(c),
-                     bd_of(c), srt, raw, acc, dr, c->cap, c->stream, hn.H0, hn.H1);
+    enqueue_density<T>(c, hh, (T *)nullptr);
+    enqueue_eval<T>(c, hh, 2, true, hn.H0, hn.H1);
     tick(c, "spawn");
     launch_spawn<T>(P, c->inf, c->sc, raw, c->layer_y, c->cap, c->cadence, c->stream);
 }
@@ -415,17 +421,15 @@ template <class T> static void enqueue_step(sph_ctx *c, bool full) {
     c->prof_pending = c->prof;
 }
 
+// sph_evaluate: a fresh cell build and one evaluation, with the normal walked
+// for every particle (its CSF intermediates are returned exactly).
 template <class T> static void enqueue_evaluate(sph_ctx *c) {
-    const PhysT<T> &P = Ops<T>::phys(c);
-    State<T> raw = state_of<T>(c->raw), srt = state_of<T>(c->srt);
+    State<T> srt = state_of<T>(c->srt);
     const uint32_t *key = enqueue_sort<T>(c);
     Hot<T> hn = hot_n<T>(c);
     enqueue_build<T>(c, key);
-    enqueue_density<T>(c, hn, srt.drho, true);
-    enqueue_normal<T>(c, hn);
-    launch_forces<T>(c->lanes, 0, P, c->grid, c->inf, c->sc, c->nl, key, hn, csf_of<T>(c),
-                     bd_of(c), srt, raw, (typename Vec<T>::v2 *)c->acc, (T *)c->dr, c->cap,
-                     c->stream);
+    enqueue_density<T>(c, hn, srt.drho);
+    enqueue_eval<T>(c, hn, 0, false);
 }
 
 template <class T> static void enqueue_breakup(sph_ctx *c) {
@@ -692,6 +696,9 @@ sph_status sph_init(const sph_params *p, sph_ctx **out) {
     if (!e) c->nvec = dalloc(c, N * 2 * ts, e);
     if (!e) c->acc = dalloc(c, N * 2 * ts, e);
     if (!e) c->dr = dalloc(c, N * ts, e);
+    if (!e) c->accN = dalloc(c, N * 4 * ts, e);
+    if (!e) c->gsum = dalloc(c, N * ts, e);
+    if (!e) c->crange = (uint2 *)dalloc(c, (size_t)g.ncells * 8, e);
     c->cs.nscan = (int)(((size_t)g.ncells + SCAN_CELLS - 1) / SCAN_CELLS);
     if (!e) c->cs.knew = (uint32_t *)dalloc(c, N * 4, e);
     if (!e) c->cs.count = (uint32_t *)dalloc(c, (size_t)g.ncells * 4, e);
@@ -1459,13 +1466,14 @@ sph_status sph_kernel_counts(sph_ctx *c, int *per_full_step, int *per_reused_ste
     if (!c) return SPH_ERR_ARG;
     bool csf = c->prm.sigma > 0;
     int sort = 5;                          // hash+count, scan (2), scatter, reorder
-    int full = sort + 1;                   // + neighbour list (with the colour of step n)
-    int reuse = csf ? 1 : 0;               // colour of step n (the corrector wrote the records)
-    int rest = (csf ? 3 : 0)               // normal (2x) + colour of the half step
-               + 3                         // forces (2x) + predict
+    int full = sort + 1;                   // + neighbour list
+    int reuse = 0;                         // the corrector wrote the records of step n
+    int rest = 2 * (csf ? 3 : 1)           // per evaluation: pair sums, normal, surface
+                                           // (or the one force sweep without CSF)
+               + 1                         // predict
                + 1;                        // spawn / time advance
     if (c->prm.density == SPH_DENSITY_SUMMATION) {
-        full += 1 + (csf ? 1 : 0);         // Eq. 6 sweep, colour out of the list build
+        full += 1;                         // Eq. 6 sweep
         reuse += 1;                        // Eq. 6 sweep
         rest += 1;                         // Eq. 6 sweep of the half step
     }
@@ -1548,12 +1556,10 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
     // SPH at the step start, with the time-step candidates of Eqs. 30-31
     State<float> raw = state_of<float>(c->raw), srt = state_of<float>(c->srt);
     {
+        // the network reads the normals of every particle: no skipping
         const uint32_t *key = enqueue_sort<float>(c);
         enqueue_build<float>(c, key);
-        enqueue_normal<float>(c, hot_n<float>(c));
-        launch_forces<float>(c->lanes, 1, c->Pf, c->grid, c->inf, c->sc, c->nl, key,
-                             hot_n<float>(c), csf_of<float>(c), bd_of(c), srt, raw,
-                             (float2 *)c->acc, (float *)c->dr, c->cap, c->stream);
+        enqueue_eval<float>(c, hot_n<float>(c), 1, false);
     }
     s = after_work(c, "surrogate: evaluation at the start");
     if (s) return s;
@@ -1591,10 +1597,7 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
     launch_refresh<float>(c->Pf, c->grid, c->sc, c->cs.key, raw, srt, hot_n<float>(c), c->cap,
                           c->stream);
     enqueue_cells<float>(c, false);
-    enqueue_normal<float>(c, hot_n<float>(c));
-    launch_forces<float>(c->lanes, 0, c->Pf, c->grid, c->inf, c->sc, c->nl, c->cs.key,
-                         hot_n<float>(c), csf_of<float>(c), bd_of(c), srt, raw,
-                         (float2 *)c->acc, (float *)c->dr, c->cap, c->stream);
+    enqueue_eval<float>(c, hot_n<float>(c), 0, false);
     CK(cudaMemcpyAsync(&c->sc->n, c->sg_n, sizeof(int), cudaMemcpyDeviceToDevice, c->stream), "copy");
     CK(cudaMemsetAsync(c->sg_sums, 0, 4 * sizeof(double), c->stream), "clear");
     launch_surrogate_residual(n, srt.type, abar, (float)a_ref, (const float2 *)c->sg_an,

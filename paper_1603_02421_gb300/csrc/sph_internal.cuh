@@ -253,9 +253,34 @@ template <class T>
 void launch_density(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
                     const Hot<T> &hot, const T *mass, const uint8_t *type, T *drho_out, int cap,
                     cudaStream_t s, int gate = GATE_ALWAYS);
+// Normal, filter and unit normal (Eqs. 18, 20, 21).  With gsum (the bound
+// G_a of launch_pairsum) and crange (the colour range of every cell), particles
+// whose normal provably stays below the filter threshold are not walked (their
+// n is written as zero); with gsum null every particle is walked.
 template <class T>
 void launch_normal(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
-                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s);
+                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s,
+                   const uint32_t *key = nullptr, const T *gsum = nullptr,
+                   const uint2 *crange = nullptr, int ncx = 0);
+// With surface tension: the one full list walk of an evaluation -- colour
+// (Eq. 14, to csf.C and csf.CX) and, for fluid particles, the pair sums that
+// need only the state (Eqs. 7, 9, 10, 29, 31) to accN = (ax, ay, drho/dt,
+// max Eq. 31 term); gsum_a = sum_b V_b |grad_a W_ab|; the colour range of
+// each cell to crange (min, ~max as float bits; reset to all ones before).
+template <class T>
+void launch_pairsum(int lanes, const PhysT<T> &P, const Grid &g, const Scalars *sc,
+                    const NList &nl, const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf,
+                    const Boundary &bd, const uint8_t *type, typename Vec<T>::v4 *accN, T *gsum,
+                    uint2 *crange, int cap, cudaStream_t s);
+// With surface tension: curvature (Eq. 23) of the particles with N_a = 1, CSF
+// acceleration (Eq. 24), gravity, and the end of launch_forces' mode (0, 1
+// or 2) from the sums of launch_pairsum.
+template <class T>
+void launch_surface(int lanes, int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
+                    Scalars *sc, const NList &nl, const Hot<T> &hot, const Csf<T> &csf,
+                    const State<T> &srt, const State<T> &raw, const typename Vec<T>::v4 *accN,
+                    typename Vec<T>::v2 *acc, T *dr, int cap, cudaStream_t s,
+                    typename Vec<T>::v4 *nH0 = nullptr, typename Vec<T>::v4 *nH1 = nullptr);
 // mode 0: evaluate only (store derivatives, copy srt -> raw); mode 1: first
 // evaluation of a step (store derivatives, time-step minimum); mode 2:
 // second evaluation + corrector (write the new state to raw, and in place to

@@ -344,11 +344,21 @@ k_colour(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T
 }
 
 // ---------------------------------------------------------------------------
-// Eqs. 18, 20, 21: normal, filter, unit normal
+// Eqs. 18, 20, 21: normal, filter, unit normal.  With SKIP (the steps), a
+// particle whose normal provably stays below the filter threshold is not
+// walked: |n_a| <= sum_b V_b |C_b - C_a| |grad_a W_ab| <= D_a G_a, with G_a =
+// sum_b V_b |grad_a W_ab| from k_pairsum and D_a the largest |C_b - C_a| over
+// the colour ranges of the 3x3 cells of the last build around a (every list
+// neighbour of a lies in them).  When D_a G_a is at most half the threshold,
+// N_a = 0 and nhat_a = 0 exactly as the walk would give; n_a (used only
+// where N_a = 1) is then written as zero.  Without SKIP (sph_evaluate) every
+// particle is walked and n_a is exact everywhere.
 // ---------------------------------------------------------------------------
-template <class T, int K, int G>
+template <class T, int K, int G, bool SKIP>
 __global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
-k_normal(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T> csf) {
+k_normal(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T> csf,
+         const uint32_t *__restrict__ key, const T *__restrict__ gsum,
+         const uint2 *__restrict__ crange, int ncx) {
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned i = gt / G, sub = gt % G;
     bool active = i < (unsigned)sc->nsrt;
@@ -357,20 +367,38 @@ k_normal(PhysT<T> P, const Scalars *__restrict__ sc, NList nl, Hot<T> hot, Csf<T
     if (active) {
         V4<T> xa = CX[i];
         T Ca = xa.w;
-        for_list<G, SPH_CH_NORMAL, T>(
-            P, nl, hot.pos, i, sub, xa.x, xa.y,
-            [&](unsigned b) {
-                NormalRec<T> r;
-                r.x = CX[b];
-                return r;
-            },
-            [&](unsigned, T rx, T ry, T r2, const NormalRec<T> &r) {
-                T q, iq;
-                q_of(r2, P.h, P.inv_h, q, iq);
-                T wgt = r.x.z * (r.x.w - Ca) * kernel_F<T, K>(P, q, iq);
-                nx += wgt * rx;
-                ny += wgt * ry;
-            });
+        bool walk = true;
+        if (SKIP) {
+            const int k = (int)key[i];
+            float lo = 3.0e38f, hi = 0.0f;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    uint2 r = __ldg(&crange[k + dy * ncx + dx]);
+                    lo = fminf(lo, __uint_as_float(r.x));
+                    hi = fmaxf(hi, __uint_as_float(~r.y));
+                }
+            }
+            T D = (T)hi - Ca;
+            D = Ca - (T)lo > D ? Ca - (T)lo : D;
+            walk = !(D * gsum[i] <= T(0.5) * P.eps_n);
+        }
+        if (walk)
+            for_list<G, SPH_CH_NORMAL, T>(
+                P, nl, hot.pos, i, sub, xa.x, xa.y,
+                [&](unsigned b) {
+                    NormalRec<T> r;
+                    r.x = CX[b];
+                    return r;
+                },
+                [&](unsigned, T rx, T ry, T r2, const NormalRec<T> &r) {
+                    T q, iq;
+                    q_of(r2, P.h, P.inv_h, q, iq);
+                    T wgt = r.x.z * (r.x.w - Ca) * kernel_F<T, K>(P, q, iq);
+                    nx += wgt * rx;
+                    ny += wgt * ry;
+                });
     }
     nx = group_sum<G>(nx);
     ny = group_sum<G>(ny);
@@ -425,84 +453,49 @@ __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, co
 }
 
 // ---------------------------------------------------------------------------
-// Eqs. 7, 9, 10, 23-25, 29-31 (+ corrector in mode 2)
+// Pair terms of the momentum and continuity equations for fluid particle a
+// with neighbour b (Eqs. 7, 9, 10) and the Eq. 31 term.
 // ---------------------------------------------------------------------------
-template <class T, int K, int MODE, int G>
-__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
-k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
-         const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf, Boundary bd, State<T> srt,
-         State<T> raw, V2<T> *__restrict__ acc, T *__restrict__ drout, V4<T> *__restrict__ nH0,
-         V4<T> *__restrict__ nH1) {
-    unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned i = gt / G, sub = gt % G;
-    int nsrt = sc->nsrt;
-    bool active = i < (unsigned)nsrt;
-    uint8_t typ = active ? srt.type[i] : T_DEAD;
-    bool fluid = typ == T_FLUID;
-    T ax = T(0), ay = T(0), drho = T(0), vmax = T(0), num = T(0), den = T(0);
-    V4<T> ha = mk4<T>(T(0), T(0), T(0), T(0)), h1a = ha;
-    V2<T> nha = mk2(T(0), T(0));
-    bool Na = false;
-    if (fluid) {
-        ha = hot.H0[i];
-        h1a = hot.H1[i];
-        T rhoa = h1a.y, PAa = h1a.z, ca = h1a.w;
-        T ua = ha.z, va = ha.w;
-        if (P.csf) {
-            nha = csf.nhat[i];
-            Na = (nha.x != T(0)) || (nha.y != T(0));
-        }
-        const V4<T> *__restrict__ H0 = hot.H0;
-        const V4<T> *__restrict__ H1 = hot.H1;
-        const V2<T> *__restrict__ NH = csf.nhat;
-        for_list<G, SPH_CH_FORCES, T>(
-            P, nl, hot.pos, i, sub, ha.x, ha.y,
-            [&](unsigned b) {
-                ForceRec<T> r;
-                r.x = H0[b];
-                r.h1 = H1[b];
-                r.nb = Na ? NH[b] : mk2(T(0), T(0));
-                return r;
-            },
-            [&](unsigned, T rx, T ry, T r2, const ForceRec<T> &r) {
-                const V4<T> &hb = r.x;
-                const V4<T> &h1b = r.h1;
-                T q, iq, ri;
-                q_of(r2, P.h, P.inv_h, q, iq, ri);
-                T F = kernel_F<T, K>(P, q, iq);
-                T du = ua - hb.z, dv = va - hb.w;
-                T udotr = du * rx + dv * ry;
-                T mb = h1b.x * h1b.y;
-                drho += mb * udotr * F;                       // Eq. 7
-                // Eq. 10 (approaching pairs only), evaluated without a branch
-                T cbar = T(0.5) * (ca + h1b.w);
-                T rbar = T(0.5) * (rhoa + h1b.y);
-                T Pi = -P.alpha_h * cbar * udotr * fast_div(T(1), rbar * (r2 + P.eta2));
-                Pi = udotr < T(0) ? Pi : T(0);
-                T coef = mb * (PAa + h1b.z + Pi) * F;          // Eq. 9 / 25
-                ax -= coef * rx;
-                ay -= coef * ry;
-                T cv = abs_t(P.h * udotr) * (ri * ri);         // Eq. 31 (0 if r = 0)
-                vmax = cv > vmax ? cv : vmax;
-                if (Na) {                                      // Eq. 23
-                    V2<T> nb = r.nb;
-                    if (nb.x != T(0) || nb.y != T(0)) {
-                        num += h1b.x * ((nb.x - nha.x) * rx + (nb.y - nha.y) * ry) * F;
-                        den += h1b.x * kernel_W<T, K>(P, q);
-                    }
-                }
-            });
-        if (P.walls) {
-            double2 pa = hot.pos[i];
-            wall_forces<T, G>(P, g, bd, key[i], sub, ha.x, ha.y, ua, va, (T)pa.y, ax, ay);
-        }
-    }
-    ax = group_sum<G>(ax);
-    ay = group_sum<G>(ay);
-    drho = group_sum<G>(drho);
-    num = group_sum<G>(num);
-    den = group_sum<G>(den);
-    vmax = group_max<G>(vmax);
+template <class T>
+__device__ __forceinline__ void pair_forces(const PhysT<T> &P, T rx, T ry, T r2, T ri, T F,
+                                            T ua, T va, T rhoa, T PAa, T ca, const V4<T> &hb,
+                                            const V4<T> &h1b, T &ax, T &ay, T &drho, T &vmax) {
+    T du = ua - hb.z, dv = va - hb.w;
+    T udotr = du * rx + dv * ry;
+    T mb = h1b.x * h1b.y;
+    drho += mb * udotr * F;                       // Eq. 7
+    // Eq. 10 (approaching pairs only), evaluated without a branch
+    T cbar = T(0.5) * (ca + h1b.w);
+    T rbar = T(0.5) * (rhoa + h1b.y);
+    T Pi = -P.alpha_h * cbar * udotr * fast_div(T(1), rbar * (r2 + P.eta2));
+    Pi = udotr < T(0) ? Pi : T(0);
+    T coef = mb * (PAa + h1b.z + Pi) * F;         // Eq. 9 / 25
+    ax -= coef * rx;
+    ay -= coef * ry;
+    T cv = abs_t(P.h * udotr) * (ri * ri);        // Eq. 31 (0 if r = 0)
+    vmax = cv > vmax ? cv : vmax;
+}
+
+// ---------------------------------------------------------------------------
+// End of a force evaluation for particle i, once the pair sums of its G
+// lanes are combined (ax, ay, drho, vmax; the curvature sums num, den of
+// Eq. 23 when the filter N_a is set): CSF acceleration (Eq. 24), gravity
+// (Eq. 25), the non-finite check, the time-step candidate (Eqs. 30-31) and,
+// by mode, 0: store the derivatives and copy srt -> raw; 1: store them and
+// fold the time-step minimum; 2: corrector.  Every thread of the block calls
+// it (mode 1 has a block barrier).
+// ---------------------------------------------------------------------------
+template <class T, int MODE>
+__device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, const Inflow &inf,
+                                              Scalars *__restrict__ sc, const Hot<T> &hot,
+                                              const Csf<T> &csf, const State<T> &srt,
+                                              const State<T> &raw, V2<T> *__restrict__ acc,
+                                              T *__restrict__ drout, V4<T> *__restrict__ nH0,
+                                              V4<T> *__restrict__ nH1, unsigned i, unsigned sub,
+                                              int nsrt, bool active, uint8_t typ, bool Na,
+                                              const V4<T> &h1a, T ax, T ay, T drho, T vmax,
+                                              T num, T den) {
+    const bool fluid = typ == T_FLUID;
     T dtc = T(3.0e38);   // per-particle time-step candidate (fluid only)
     if (fluid) {
         if (Na) {                                              // Eq. 24
@@ -662,6 +655,238 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
             atomicMax(&sc->max_step2[slot], b2);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Eqs. 7, 9, 10, 23-25, 29-31 in one list walk (+ corrector in mode 2): the
+// form used without surface tension, where no colour, normal or curvature
+// precedes the forces.
+// ---------------------------------------------------------------------------
+template <class T, int K, int MODE, int G>
+__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
+k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
+         const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf, Boundary bd, State<T> srt,
+         State<T> raw, V2<T> *__restrict__ acc, T *__restrict__ drout, V4<T> *__restrict__ nH0,
+         V4<T> *__restrict__ nH1) {
+    unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned i = gt / G, sub = gt % G;
+    int nsrt = sc->nsrt;
+    bool active = i < (unsigned)nsrt;
+    uint8_t typ = active ? srt.type[i] : T_DEAD;
+    bool fluid = typ == T_FLUID;
+    T ax = T(0), ay = T(0), drho = T(0), vmax = T(0), num = T(0), den = T(0);
+    V4<T> ha = mk4<T>(T(0), T(0), T(0), T(0)), h1a = ha;
+    V2<T> nha = mk2(T(0), T(0));
+    bool Na = false;
+    if (fluid) {
+        ha = hot.H0[i];
+        h1a = hot.H1[i];
+        T rhoa = h1a.y, PAa = h1a.z, ca = h1a.w;
+        T ua = ha.z, va = ha.w;
+        if (P.csf) {
+            nha = csf.nhat[i];
+            Na = (nha.x != T(0)) || (nha.y != T(0));
+        }
+        const V4<T> *__restrict__ H0 = hot.H0;
+        const V4<T> *__restrict__ H1 = hot.H1;
+        const V2<T> *__restrict__ NH = csf.nhat;
+        for_list<G, SPH_CH_FORCES, T>(
+            P, nl, hot.pos, i, sub, ha.x, ha.y,
+            [&](unsigned b) {
+                ForceRec<T> r;
+                r.x = H0[b];
+                r.h1 = H1[b];
+                r.nb = Na ? NH[b] : mk2(T(0), T(0));
+                return r;
+            },
+            [&](unsigned, T rx, T ry, T r2, const ForceRec<T> &r) {
+                T q, iq, ri;
+                q_of(r2, P.h, P.inv_h, q, iq, ri);
+                T F = kernel_F<T, K>(P, q, iq);
+                pair_forces<T>(P, rx, ry, r2, ri, F, ua, va, rhoa, PAa, ca, r.x, r.h1, ax, ay,
+                               drho, vmax);
+                if (Na) {                                      // Eq. 23
+                    V2<T> nb = r.nb;
+                    if (nb.x != T(0) || nb.y != T(0)) {
+                        num += r.h1.x * ((nb.x - nha.x) * rx + (nb.y - nha.y) * ry) * F;
+                        den += r.h1.x * kernel_W<T, K>(P, q);
+                    }
+                }
+            });
+        if (P.walls) {
+            double2 pa = hot.pos[i];
+            wall_forces<T, G>(P, g, bd, key[i], sub, ha.x, ha.y, ua, va, (T)pa.y, ax, ay);
+        }
+    }
+    ax = group_sum<G>(ax);
+    ay = group_sum<G>(ay);
+    drho = group_sum<G>(drho);
+    num = group_sum<G>(num);
+    den = group_sum<G>(den);
+    vmax = group_max<G>(vmax);
+    forces_finish<T, MODE>(P, g, inf, sc, hot, csf, srt, raw, acc, drout, nH0, nH1, i, sub, nsrt,
+                           active, typ, Na, h1a, ax, ay, drho, vmax, num, den);
+}
+
+// ---------------------------------------------------------------------------
+// With surface tension an evaluation is three sweeps, of which only the
+// first walks every particle's list:
+//   k_pairsum  colour (Eq. 14) of every particle together with the pair sums
+//              of the fluid particles that need only the state -- continuity
+//              (Eq. 7), pressure and viscosity (Eqs. 9, 10), the Eq. 31 term,
+//              the walls (Eq. 29) -- and, per particle, the bound
+//              G_a = sum_b V_b |grad_a W_ab| and the colour range of its cell;
+//   k_normal   Eqs. 18, 20, 21; in a step it skips (n_a = 0, N_a = 0) every
+//              particle whose normal provably stays below the filter
+//              threshold: |n_a| <= max_b |C_b - C_a| G_a, with the colour
+//              range taken over the 3x3 cells around it;
+//   k_surface  curvature (Eq. 23) for the particles with N_a = 1, then CSF,
+//              gravity, time-step candidate and integrator (forces_finish).
+// The sums are those of k_forces, term for term and in the same order.
+// ---------------------------------------------------------------------------
+template <class T> struct PairRec {       // offsets and velocity; volume, density,
+    V4<T> x;                              // pressure term, sound speed
+    V4<T> h1;
+};
+
+// Colour range of a cell: (min C, ~max C) as float bits (C >= 0, so the bit
+// patterns order as the values), both reduced with atomicMin from the
+// all-ones reset; FP64 colours are rounded outward.
+__device__ __forceinline__ void colour_bits(float c, unsigned &lo, unsigned &nhi) {
+    lo = __float_as_uint(c);
+    nhi = ~__float_as_uint(c);
+}
+__device__ __forceinline__ void colour_bits(double c, unsigned &lo, unsigned &nhi) {
+    lo = __float_as_uint(__double2float_rd(c));
+    nhi = ~__float_as_uint(__double2float_ru(c));
+}
+
+template <class T, int K, int G>
+__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
+k_pairsum(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, NList nl,
+          const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf, Boundary bd,
+          const uint8_t *__restrict__ type, V4<T> *__restrict__ accN, T *__restrict__ gsum,
+          uint2 *__restrict__ crange) {
+    unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned i = gt / G, sub = gt % G;
+    bool active = i < (unsigned)sc->nsrt;
+    uint8_t typ = active ? type[i] : T_DEAD;
+    bool fluid = typ == T_FLUID;
+    T csum = T(0), gs = T(0), ax = T(0), ay = T(0), drho = T(0), vmax = T(0);
+    V4<T> ha = mk4<T>(T(0), T(0), T(0), T(0)), h1a = ha;
+    if (active) {
+        ha = hot.H0[i];
+        h1a = hot.H1[i];
+        T rhoa = h1a.y, PAa = h1a.z, ca = h1a.w;
+        T ua = ha.z, va = ha.w;
+        const V4<T> *__restrict__ H0 = hot.H0;
+        const V4<T> *__restrict__ H1 = hot.H1;
+        for_list<G, SPH_CH_FORCES, T>(
+            P, nl, hot.pos, i, sub, ha.x, ha.y,
+            [&](unsigned b) {
+                PairRec<T> r;
+                r.x = H0[b];
+                r.h1 = H1[b];
+                return r;
+            },
+            [&](unsigned, T rx, T ry, T r2, const PairRec<T> &r) {
+                T q, iq, ri;
+                q_of(r2, P.h, P.inv_h, q, iq, ri);
+                T F = kernel_F<T, K>(P, q, iq);
+                csum += r.h1.x * kernel_W<T, K>(P, q);                 // Eq. 14
+                gs += r.h1.x * abs_t(F) * (r2 * ri);
+                if (fluid)
+                    pair_forces<T>(P, rx, ry, r2, ri, F, ua, va, rhoa, PAa, ca, r.x, r.h1, ax,
+                                   ay, drho, vmax);
+            });
+        if (fluid && P.walls) {
+            double2 pa = hot.pos[i];
+            wall_forces<T, G>(P, g, bd, key[i], sub, ha.x, ha.y, ua, va, (T)pa.y, ax, ay);
+        }
+    }
+    csum = group_sum<G>(csum);
+    gs = group_sum<G>(gs);
+    ax = group_sum<G>(ax);
+    ay = group_sum<G>(ay);
+    drho = group_sum<G>(drho);
+    vmax = group_max<G>(vmax);
+    T Va = h1a.x;
+    T C = csum + Va * P.W0;
+    if (active && sub == 0) {
+        csf.C[i] = C;
+        csf.CX[i] = mk4<T>(ha.x, ha.y, Va, C);
+        accN[i] = mk4<T>(ax, ay, drho, vmax);
+        gsum[i] = gs;
+    }
+    // colour range of each cell of the last build, over the particles with
+    // a volume (those deleted since the build have none and enter no sum);
+    // the lanes of a warp holding the same cell combine first
+    bool rep = active && sub == 0 && Va > T(0);
+    unsigned m = __ballot_sync(0xffffffffu, rep);
+    if (rep) {
+        unsigned k = key[i];
+        unsigned peers = __match_any_sync(m, k);
+        unsigned lo, nhi;
+        colour_bits(C, lo, nhi);
+        lo = __reduce_min_sync(peers, lo);
+        nhi = __reduce_min_sync(peers, nhi);
+        if ((threadIdx.x & 31u) == (unsigned)(__ffs(peers) - 1)) {
+            atomicMin(&crange[k].x, lo);
+            atomicMin(&crange[k].y, nhi);
+        }
+    }
+}
+
+template <class T, int K, int MODE, int G>
+__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
+k_surface(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl, Hot<T> hot,
+          Csf<T> csf, State<T> srt, State<T> raw, const V4<T> *__restrict__ accN,
+          V2<T> *__restrict__ acc, T *__restrict__ drout, V4<T> *__restrict__ nH0,
+          V4<T> *__restrict__ nH1) {
+    unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned i = gt / G, sub = gt % G;
+    int nsrt = sc->nsrt;
+    bool active = i < (unsigned)nsrt;
+    uint8_t typ = active ? srt.type[i] : T_DEAD;
+    bool fluid = typ == T_FLUID;
+    T num = T(0), den = T(0);
+    V4<T> an = mk4<T>(T(0), T(0), T(0), T(0)), h1a = an;
+    bool Na = false;
+    if (fluid) {
+        an = accN[i];
+        h1a = hot.H1[i];
+        V2<T> nha = csf.nhat[i];
+        Na = (nha.x != T(0)) || (nha.y != T(0));
+        if (Na) {                                              // Eq. 23
+            const V4<T> *__restrict__ H0 = hot.H0;
+            const V4<T> *__restrict__ H1 = hot.H1;
+            const V2<T> *__restrict__ NH = csf.nhat;
+            V4<T> ha = H0[i];
+            for_list<G, SPH_CH_FORCES, T>(
+                P, nl, hot.pos, i, sub, ha.x, ha.y,
+                [&](unsigned b) {
+                    ForceRec<T> r;
+                    r.x = H0[b];
+                    r.h1 = mk4<T>(H1[b].x, T(0), T(0), T(0));
+                    r.nb = NH[b];
+                    return r;
+                },
+                [&](unsigned, T rx, T ry, T r2, const ForceRec<T> &r) {
+                    V2<T> nb = r.nb;
+                    if (nb.x != T(0) || nb.y != T(0)) {
+                        T q, iq;
+                        q_of(r2, P.h, P.inv_h, q, iq);
+                        T F = kernel_F<T, K>(P, q, iq);
+                        num += r.h1.x * ((nb.x - nha.x) * rx + (nb.y - nha.y) * ry) * F;
+                        den += r.h1.x * kernel_W<T, K>(P, q);
+                    }
+                });
+        }
+    }
+    num = group_sum<G>(num);
+    den = group_sum<G>(den);
+    forces_finish<T, MODE>(P, g, inf, sc, hot, csf, srt, raw, acc, drout, nH0, nH1, i, sub, nsrt,
+                           active, typ, Na, h1a, an.x, an.y, an.z, an.w, num, den);
 }
 
 // ---------------------------------------------------------------------------
@@ -888,14 +1113,64 @@ void launch_density(int lanes, const PhysT<T> &P, const Scalars *sc, const NList
 
 template <class T>
 void launch_normal(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
-                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s) {
+                   const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s,
+                   const uint32_t *key, const T *gsum, const uint2 *crange, int ncx) {
+    const bool skip = gsum != nullptr;
+    with_lanes(lanes, [&](auto Gc) {
+        constexpr int G = decltype(Gc)::value;
+        int b = sweep_blocks(cap, G);
+        if (P.kernel == 1) {
+            if (skip) launch_k(k_normal<T, 1, G, true>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf, key, gsum, crange, ncx);
+            else launch_k(k_normal<T, 1, G, false>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf, key, gsum, crange, ncx);
+        } else {
+            if (skip) launch_k(k_normal<T, 0, G, true>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf, key, gsum, crange, ncx);
+            else launch_k(k_normal<T, 0, G, false>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf, key, gsum, crange, ncx);
+        }
+    });
+}
+
+template <class T>
+void launch_pairsum(int lanes, const PhysT<T> &P, const Grid &g, const Scalars *sc,
+                    const NList &nl, const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf,
+                    const Boundary &bd, const uint8_t *type, V4<T> *accN, T *gsum, uint2 *crange,
+                    int cap, cudaStream_t s) {
     with_lanes(lanes, [&](auto Gc) {
         constexpr int G = decltype(Gc)::value;
         int b = sweep_blocks(cap, G);
         if (P.kernel == 1)
-            launch_k(k_normal<T, 1, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+            launch_k(k_pairsum<T, 1, G>, b, SWEEP_BLOCK, s, P, g, sc, nl, key, hot, csf, bd, type,
+                     accN, gsum, crange);
         else
-            launch_k(k_normal<T, 0, G>, b, SWEEP_BLOCK, s, P, sc, nl, hot, csf);
+            launch_k(k_pairsum<T, 0, G>, b, SWEEP_BLOCK, s, P, g, sc, nl, key, hot, csf, bd, type,
+                     accN, gsum, crange);
+    });
+}
+
+template <class T, int K, int G>
+static void launch_surface_k(int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
+                             Scalars *sc, const NList &nl, const Hot<T> &hot, const Csf<T> &csf,
+                             const State<T> &srt, const State<T> &raw, const V4<T> *accN,
+                             V2<T> *acc, T *dr, V4<T> *nH0, V4<T> *nH1, int cap, cudaStream_t s) {
+    int b = sweep_blocks(cap, G);
+    if (mode == 0)
+        launch_k(k_surface<T, K, 0, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, hot, csf, srt, raw, accN, acc, dr, nH0, nH1);
+    else if (mode == 1)
+        launch_k(k_surface<T, K, 1, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, hot, csf, srt, raw, accN, acc, dr, nH0, nH1);
+    else
+        launch_k(k_surface<T, K, 2, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, hot, csf, srt, raw, accN, acc, dr, nH0, nH1);
+}
+
+template <class T>
+void launch_surface(int lanes, int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
+                    Scalars *sc, const NList &nl, const Hot<T> &hot, const Csf<T> &csf,
+                    const State<T> &srt, const State<T> &raw, const V4<T> *accN, V2<T> *acc,
+                    T *dr, int cap, cudaStream_t s, V4<T> *nH0, V4<T> *nH1) {
+    with_lanes(lanes, [&](auto Gc) {
+        constexpr int G = decltype(Gc)::value;
+        if (P.kernel == 1)
+            launch_surface_k<T, 1, G>(mode, P, g, inf, sc, nl, hot, csf, srt, raw, accN, acc, dr, nH0, nH1, cap, s);
+        else
+            launch_surface_k<T, 0, G>(mode, P, g, inf, sc, nl, hot, csf, srt, raw, accN, acc, dr, nH0, nH1, cap, s);
     });
 }
 
@@ -1066,7 +1341,16 @@ void *decide_kernel() { return (void *)k_decide; }
                                     const Hot<T> &, const T *, const uint8_t *, T *, int,         \
                                     cudaStream_t, int);                                           \
     template void launch_normal<T>(int, const PhysT<T> &, const Scalars *, const NList &,         \
-                                   const Hot<T> &, const Csf<T> &, int, cudaStream_t);            \
+                                   const Hot<T> &, const Csf<T> &, int, cudaStream_t,             \
+                                   const uint32_t *, const T *, const uint2 *, int);              \
+    template void launch_pairsum<T>(int, const PhysT<T> &, const Grid &, const Scalars *,         \
+                                    const NList &, const uint32_t *, const Hot<T> &,              \
+                                    const Csf<T> &, const Boundary &, const uint8_t *, V4<T> *,   \
+                                    T *, uint2 *, int, cudaStream_t);                             \
+    template void launch_surface<T>(int, int, const PhysT<T> &, const Grid &, const Inflow &,    \
+                                    Scalars *, const NList &, const Hot<T> &, const Csf<T> &,     \
+                                    const State<T> &, const State<T> &, const V4<T> *, V2<T> *,   \
+                                    T *, int, cudaStream_t, V4<T> *, V4<T> *);                    \
     template void launch_forces<T>(int, int, const PhysT<T> &, const Grid &, const Inflow &,     \
                                    Scalars *, const NList &, const uint32_t *, const Hot<T> &,    \
                                    const Csf<T> &, const Boundary &, const State<T> &,            \

@@ -423,9 +423,12 @@ def test_start_forms_are_bit_identical(sph, density):
     assert tg == tc
     for k in ("x", "y", "u", "v", "rho", "id", "type"):
         assert np.array_equal(g[k], c[k]), k
-    # gated: both starts every step; conditional: the IF-node kernel + one start
-    # (the reuse start is the colour sweep alone, the rebuild start six kernels)
-    assert cg[0] == cg[1] >= cc[0] > cc[1]
+    # gated: both starts every step; conditional: the IF-node kernel + one
+    # start.  The rebuild start is six kernels (the Eq. 6 sweep adds one to
+    # each start); the reuse start has none with Eq. 7, one with Eq. 6.
+    reuse = 1 if density == "summation" else 0
+    assert cg[0] == cg[1] == cc[0] - 1 + reuse
+    assert cc[0] - cc[1] == 6
 
 
 def test_start_form_rejects_bad_values(sph):

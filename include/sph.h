@@ -188,6 +188,45 @@ sph_status sph_get_csf(sph_ctx *ctx, long long cap, long long *n, unsigned *id,
 sph_status sph_get_pairs(sph_ctx *ctx, long long cap, unsigned *id_a, unsigned *id_b,
                          long long *npairs);
 
+/* Checkpoint and resume (no counterpart in the paper; SPHysics writes
+ * output frames).  A checkpoint holds what a later run needs to continue
+ * bit for bit: the live fluid and buffer particles in id order exactly as
+ * the context stores them (FP64 positions; velocities, density offsets
+ * rho - rho0 with their compensation carries and masses in the pair
+ * precision), the simulated time, step count, inflow layer position, next
+ * particle id and deleted count.  sph_checkpoint_size: the bytes a save
+ * writes now.  sph_checkpoint_save: writes them to the host buffer buf of
+ * cap bytes (*bytes, nullable, receives the count; SPH_ERR_CAPACITY if cap
+ * is short).  sph_checkpoint_load: replaces the particles and clocks of ctx
+ * -- a context made with the same parameters, boundary and inflow, which
+ * keeps them -- by those of the checkpoint (SPH_ERR_ARG for a buffer that
+ * is not one, of the other pair precision, or beyond the capacity).  The
+ * next step of the loaded context rebuilds its cells and lists; its state
+ * after k steps is bit for bit that of the saved context after k steps of
+ * its own when that context also rebuilds at the first of them
+ * (sph_request_rebuild), with the same tuning: the cell order after a
+ * rebuild depends only on the positions and ids. */
+sph_status sph_checkpoint_size(sph_ctx *ctx, size_t *bytes);
+sph_status sph_checkpoint_save(sph_ctx *ctx, void *buf, size_t cap, size_t *bytes);
+sph_status sph_checkpoint_load(sph_ctx *ctx, const void *buf, size_t bytes);
+
+/* Run statistics of the current state (no counterpart in the paper): over
+ * the fluid particles, their mass, momentum sum m u, kinetic energy
+ * sum m |u|^2 / 2, potential energy -sum m g . r, the elastic energy of the
+ * Tait equation of state (Eq. 26), sum m e(rho) with
+ * e = (B/rho0) ((x^(gamma-1) - 1)/(gamma - 1) + 1/x - 1), x = rho/rho0 (the
+ * work P/rho^2 d rho stored from rho0 to rho), and max |rho - rho0|/rho0;
+ * counts of fluid, buffer and boundary particles; time, step, last step size
+ * and deleted count.  Sums in FP64 on the device. */
+typedef struct {
+    long long n_fluid, n_buffer, n_boundary, n_deleted, step;
+    double t, dt;
+    double mass, momentum_x, momentum_y;
+    double kinetic, potential, elastic;
+    double max_rel_density;
+} sph_stats_t;
+sph_status sph_stats(sph_ctx *ctx, sph_stats_t *out);
+
 /* Simulated time, completed steps, live fluid + buffer particles, and
  * particles deleted by the outflow so far. */
 sph_status sph_get_time(sph_ctx *ctx, double *t, long long *steps, long long *n_particles,

@@ -87,6 +87,11 @@ _SIGS = {
                            ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sph_get_rebuild_stats": ([_CTX, _LL, _D, _D], ctypes.c_int),
     "sph_request_rebuild": ([_CTX], ctypes.c_int),
+    "sph_checkpoint_size": ([_CTX, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "sph_checkpoint_save": ([_CTX, ctypes.c_void_p, ctypes.c_size_t,
+                             ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "sph_checkpoint_load": ([_CTX, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "sph_stats": ([_CTX, ctypes.c_void_p], ctypes.c_int),
     "sph_fma_peak": ([ctypes.c_int, ctypes.c_int, _D, _D], ctypes.c_int),
     "sph_ensemble_create": ([ctypes.POINTER(_CTX), ctypes.c_int, ctypes.c_void_p,
                              ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
@@ -310,6 +315,43 @@ def sph_get_rebuild_stats(ctx):
     _check(ctx, lib().sph_get_rebuild_stats(ctx, ctypes.byref(b), ctypes.byref(d),
                                             ctypes.byref(m)))
     return b.value, d.value, m.value
+
+
+class sph_stats_t(ctypes.Structure):
+    _fields_ = [("n_fluid", ctypes.c_longlong), ("n_buffer", ctypes.c_longlong),
+                ("n_boundary", ctypes.c_longlong), ("n_deleted", ctypes.c_longlong),
+                ("step", ctypes.c_longlong), ("t", ctypes.c_double), ("dt", ctypes.c_double),
+                ("mass", ctypes.c_double), ("momentum_x", ctypes.c_double),
+                ("momentum_y", ctypes.c_double), ("kinetic", ctypes.c_double),
+                ("potential", ctypes.c_double), ("elastic", ctypes.c_double),
+                ("max_rel_density", ctypes.c_double)]
+
+
+def sph_stats(ctx) -> dict:
+    """Run statistics of the current state (see include/sph.h)."""
+    st = sph_stats_t()
+    _check(ctx, lib().sph_stats(ctx, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in sph_stats_t._fields_}
+
+
+def sph_checkpoint_size(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(ctx, lib().sph_checkpoint_size(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def sph_checkpoint_save(ctx) -> bytes:
+    """The context's checkpoint as bytes."""
+    cap = sph_checkpoint_size(ctx)
+    buf = ctypes.create_string_buffer(max(cap, 1))
+    n = ctypes.c_size_t()
+    _check(ctx, lib().sph_checkpoint_save(ctx, buf, cap, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def sph_checkpoint_load(ctx, data: bytes):
+    buf = ctypes.create_string_buffer(data, len(data))
+    _check(ctx, lib().sph_checkpoint_load(ctx, buf, len(data)))
 
 
 def sph_request_rebuild(ctx):

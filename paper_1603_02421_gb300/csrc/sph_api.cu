@@ -55,6 +55,7 @@ struct sph_ctx {
     // Eq. 31 term), the normal bound G_a, and the colour range of each cell
     void *accN = nullptr, *gsum = nullptr;
     uint2 *crange = nullptr;
+    void *stats = nullptr;       // sph_stats scratch: 6 FP64 sums + 3 counters
     CellSort cs{};
     NList nl{};
     uint2 *cellSE = nullptr, *cellSE_b = nullptr;
@@ -1228,6 +1229,192 @@ sph_status sph_get_pairs(sph_ctx *c, long long cap, unsigned *id_a, unsigned *id
     cudaFree(da);
     cudaFree(db);
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoints: a header, then the live particles in id order as stored
+// ---------------------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];          // "SPHCKPT1"
+    int32_t tsz;            // bytes of the pair precision (4 or 8)
+    int32_t reserved;
+    int64_t n;              // particles
+    double t;               // simulated time
+    int64_t step;           // completed steps
+    double x_up;            // upstream-most inflow layer position
+    uint32_t next_id;       // next particle id
+    uint32_t reserved2;
+    int64_t deleted;        // particles deleted by the outflow
+};
+const char kCkptMagic[8] = {'S', 'P', 'H', 'C', 'K', 'P', 'T', '1'};
+size_t ckpt_bytes(size_t n, size_t ts) { return sizeof(CkptHeader) + n * (16 + 5 * ts + 1 + 4); }
+}  // namespace
+
+// Live particles of raw in id order: their raw indices.
+static sph_status live_order(sph_ctx *c, std::vector<size_t> &ord, std::vector<unsigned char> &ty,
+                             std::vector<unsigned> &ids) {
+    size_t n = (size_t)c->hsc->n;
+    ty.resize(n);
+    ids.resize(n);
+    if (n) {
+        CK(copy_sync(c, ty.data(), c->raw[5], n, cudaMemcpyDeviceToHost), "download");
+        CK(copy_sync(c, ids.data(), c->raw[6], n * 4, cudaMemcpyDeviceToHost), "download");
+    }
+    ord.clear();
+    for (size_t i = 0; i < n; ++i)
+        if (ty[i] != T_DEAD) ord.push_back(i);
+    std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return ids[a] < ids[b]; });
+    return SPH_OK;
+}
+
+sph_status sph_checkpoint_size(sph_ctx *c, size_t *bytes) {
+    if (!c || !bytes) return SPH_ERR_ARG;
+    try {
+        sph_status s = pull_scalars(c);
+        if (s) return s;
+        std::vector<size_t> ord;
+        std::vector<unsigned char> ty;
+        std::vector<unsigned> ids;
+        s = live_order(c, ord, ty, ids);
+        if (s) return s;
+        *bytes = ckpt_bytes(ord.size(), c->tsz);
+        return SPH_OK;
+    } catch (...) {
+        return fail(c, SPH_ERR_OOM, "host allocation failed");
+    }
+}
+
+sph_status sph_checkpoint_save(sph_ctx *c, void *buf, size_t cap, size_t *bytes) {
+    if (!c || (!buf && cap > 0)) return SPH_ERR_ARG;
+    try {
+        sph_status s = pull_scalars(c);
+        if (s) return s;
+        std::vector<size_t> ord;
+        std::vector<unsigned char> ty;
+        std::vector<unsigned> ids;
+        s = live_order(c, ord, ty, ids);
+        if (s) return s;
+        const size_t n = (size_t)c->hsc->n, m = ord.size(), ts = c->tsz;
+        const size_t need = ckpt_bytes(m, ts);
+        if (bytes) *bytes = need;
+        if (cap < need) return fail(c, SPH_ERR_CAPACITY, "checkpoint needs %zu bytes > cap %zu", need, cap);
+        // raw fields: pos (16), vel (2 ts), drho (ts), drc (ts), mass (ts)
+        const size_t fsz[5] = {16, 2 * ts, ts, ts, ts};
+        const int fidx[5] = {0, 1, 2, 3, 4};
+        CkptHeader hd{};
+        memcpy(hd.magic, kCkptMagic, 8);
+        hd.tsz = (int32_t)ts;
+        hd.n = (int64_t)m;
+        hd.t = c->hsc->t;
+        hd.step = c->hsc->step;
+        hd.x_up = c->hsc->x_up;
+        hd.next_id = c->hsc->next_id;
+        hd.deleted = c->hsc->deleted;
+        unsigned char *out = (unsigned char *)buf;
+        memcpy(out, &hd, sizeof hd);
+        size_t off = sizeof hd;
+        std::vector<unsigned char> tmp;
+        for (int f = 0; f < 5; ++f) {
+            tmp.resize(n * fsz[f]);
+            if (n) CK(copy_sync(c, tmp.data(), c->raw[fidx[f]], n * fsz[f], cudaMemcpyDeviceToHost), "download");
+            for (size_t r = 0; r < m; ++r) memcpy(out + off + r * fsz[f], &tmp[ord[r] * fsz[f]], fsz[f]);
+            off += m * fsz[f];
+        }
+        for (size_t r = 0; r < m; ++r) out[off + r] = ty[ord[r]];
+        off += m;
+        for (size_t r = 0; r < m; ++r) memcpy(out + off + 4 * r, &ids[ord[r]], 4);
+        return SPH_OK;
+    } catch (...) {
+        return fail(c, SPH_ERR_OOM, "host allocation failed");
+    }
+}
+
+sph_status sph_checkpoint_load(sph_ctx *c, const void *buf, size_t bytes) {
+    if (!c || !buf) return SPH_ERR_ARG;
+    if (bytes < sizeof(CkptHeader)) return fail(c, SPH_ERR_ARG, "not a checkpoint (too short)");
+    CkptHeader hd;
+    memcpy(&hd, buf, sizeof hd);
+    if (memcmp(hd.magic, kCkptMagic, 8) != 0) return fail(c, SPH_ERR_ARG, "not a checkpoint");
+    const size_t ts = c->tsz;
+    if (hd.tsz != (int32_t)ts) return fail(c, SPH_ERR_ARG, "checkpoint of the other pair precision");
+    if (hd.n < 0 || hd.n > c->cap) return fail(c, SPH_ERR_ARG, "checkpoint of %lld particles beyond capacity %lld", (long long)hd.n, c->cap);
+    const size_t m = (size_t)hd.n;
+    if (bytes != ckpt_bytes(m, ts)) return fail(c, SPH_ERR_ARG, "checkpoint size does not match its header");
+    const unsigned char *in = (const unsigned char *)buf + sizeof hd;
+    const size_t fsz[5] = {16, 2 * ts, ts, ts, ts};
+    size_t off = 0;
+    const unsigned char *ty = in;
+    for (int f = 0; f < 5; ++f) off += m * fsz[f];
+    ty = in + off;
+    for (size_t r = 0; r < m; ++r)
+        if (ty[r] != SPH_FLUID && ty[r] != SPH_BUFFER) return fail(c, SPH_ERR_ARG, "checkpoint particle %zu: bad type", r);
+    sph_status s = pull_scalars(c);
+    if (s) return s;
+    off = 0;
+    for (int f = 0; f < 5; ++f) {
+        if (m) CK(copy_sync(c, c->raw[f], in + off, m * fsz[f], cudaMemcpyHostToDevice), "upload");
+        off += m * fsz[f];
+    }
+    if (m) {
+        CK(copy_sync(c, c->raw[5], in + off, m, cudaMemcpyHostToDevice), "upload");
+        CK(copy_sync(c, c->raw[6], in + off + m, m * 4, cudaMemcpyHostToDevice), "upload");
+        CK(cudaMemsetAsync(c->raw[7], 0, m * 2 * ts, c->stream), "upload");
+    }
+    c->hsc->n = (int)m;
+    c->hsc->nsrt = 0;
+    c->hsc->t = hd.t;
+    c->hsc->step = hd.step;
+    c->hsc->x_up = hd.x_up;
+    c->hsc->next_id = hd.next_id;
+    c->hsc->deleted = hd.deleted;
+    c->force_full = true;
+    s = push_scalars(c);
+    c->n_eval = 0;
+    c->csf_valid = false;
+    return s;
+}
+
+sph_status sph_stats(sph_ctx *c, sph_stats_t *out) {
+    if (!c || !out) return SPH_ERR_ARG;
+    if (!c->stats) {
+        cudaError_t e = cudaSuccess;
+        c->stats = dalloc(c, 6 * sizeof(double) + 3 * sizeof(unsigned long long), e);
+        CK(e, "stats scratch");
+    }
+    double *acc = (double *)c->stats;
+    unsigned long long *cnt = (unsigned long long *)(acc + 6);
+    CK(cudaMemsetAsync(c->stats, 0, 6 * sizeof(double) + 3 * sizeof(unsigned long long), c->stream), "clear");
+    const double rho0 = c->prm.rho0, B = c->prm.rho0 * c->prm.c0 * c->prm.c0 / c->prm.gamma;
+    if (c->tsz == 4)
+        launch_stats<float>(c->Pf, state_of<float>(c->raw), c->sc, c->prm.gx, c->prm.gy, rho0, B,
+                            c->prm.gamma, acc, cnt, c->cap, c->stream);
+    else
+        launch_stats<double>(c->Pd, state_of<double>(c->raw), c->sc, c->prm.gx, c->prm.gy, rho0, B,
+                             c->prm.gamma, acc, cnt, c->cap, c->stream);
+    CK(cudaGetLastError(), "stats launch");
+    double h[6];
+    unsigned long long k[3];
+    CK(copy_sync(c, h, acc, sizeof h, cudaMemcpyDeviceToHost), "stats");
+    CK(copy_sync(c, k, cnt, sizeof k, cudaMemcpyDeviceToHost), "stats");
+    sph_status s = pull_scalars(c);
+    if (s) return s;
+    out->n_fluid = (long long)k[0];
+    out->n_buffer = (long long)k[1];
+    out->n_boundary = (long long)c->bx.size();
+    out->n_deleted = c->hsc->deleted;
+    out->step = c->hsc->step;
+    out->t = c->hsc->t;
+    out->dt = c->hsc->dt;
+    out->mass = h[0];
+    out->momentum_x = h[1];
+    out->momentum_y = h[2];
+    out->kinetic = h[3];
+    out->potential = h[4];
+    out->elastic = h[5];
+    long long bits = (long long)k[2];
+    memcpy(&out->max_rel_density, &bits, sizeof bits);
+    return SPH_OK;
 }
 
 sph_status sph_get_time(sph_ctx *c, double *t, long long *steps, long long *n_particles,

@@ -190,10 +190,23 @@ __device__ __forceinline__ void for_neighbours(const PhysT<T> &P, const Grid &g,
 
 // Sum of v over the G consecutive threads of a particle (all lanes of the
 // warp must call it).
-// Shift (code - 1) * sc of a list entry's 2-bit cell-offset code.
+// Shift (code - 1) * sc of a list entry's 2-bit cell-offset code (code in
+// {0, 1, 2}; the FP32 form is exact: code * sc - sc rounds once, to -sc, 0 or
+// sc).
 template <class T> __device__ __forceinline__ T code_shift(uint32_t code, T sc) {
     return code == 0u ? -sc : (code == 2u ? sc : T(0));
 }
+// FP32: one conversion and one fused multiply-add instead of two compares
+// and two selects per coordinate (1M-particle jet: normal sweep 60.6 -> 57.5
+// us, list walk 96.0 -> 95.5 us).
+#ifndef SPH_DECODE_I2F
+#define SPH_DECODE_I2F 1
+#endif
+#if SPH_DECODE_I2F
+template <> __device__ __forceinline__ float code_shift<float>(uint32_t code, float sc) {
+    return fmaf(__uint2float_rn(code), sc, -sc);
+}
+#endif
 
 // Loads CH consecutive list entries with one vector load (the address is a
 // multiple of CH entries from a row start, and rows start 384-byte aligned).

@@ -311,6 +311,13 @@ void launch_predict(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const Sta
 template <class T>
 void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State<T> &raw,
                   const double *layer_y, int cap, int cadence, cudaStream_t s);
+// Run statistics of raw[0, sc->n) (see sph_stats): acc[6] FP64 sums, cnt[3]
+// (fluid count, buffer count, bits of max |rho - rho0|/rho0), both zeroed
+// by the caller.
+template <class T>
+void launch_stats(const PhysT<T> &P, const State<T> &raw, const Scalars *sc, double gx, double gy,
+                  double rho0, double B, double gamma, double *acc, unsigned long long *cnt,
+                  int cap, cudaStream_t s);
 // Host stub of the one-thread kernel that sets a step graph's IF-node
 // condition from sc->need_full (the conditional step form).
 void *decide_kernel();

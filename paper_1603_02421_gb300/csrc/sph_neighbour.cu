@@ -116,6 +116,9 @@ k_scan_add(uint2 *__restrict__ cellSE, const uint32_t *__restrict__ bsum, unsign
             for (int k = 0; k < SCAN_THREADS / 32; ++k) t += red[k];
             sc->nsrt = (int)t;
             sc->builds += 1;
+            // the cadence counts steps from this build, whoever asked for it
+            // (the step's own decision, or a host request)
+            sc->since_full = 0;
         }
     }
     uint32_t off = off_s;

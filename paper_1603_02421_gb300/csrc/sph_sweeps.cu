@@ -33,9 +33,19 @@ namespace sph {
 #define SPH_CH_FORCES 1
 #endif
 
+// List entries per chunk of the full list walk (colour + state-only forces);
+// two, with the register budget of 8 blocks per SM (1M-particle jet, same
+// box: 95.5 -> 93.9 us per sweep at 2 lanes, 135 -> 101 us at 1 lane).
+#ifndef SPH_CH_PAIRSUM
+#define SPH_CH_PAIRSUM 2
+#endif
+
 // Blocks per SM the pair sweeps are compiled for (register budget).
 #ifndef SPH_SWEEP_MINB
 #define SPH_SWEEP_MINB 10
+#endif
+#ifndef SPH_PAIRSUM_MINB
+#define SPH_PAIRSUM_MINB 8
 #endif
 
 
@@ -77,9 +87,11 @@ __device__ __forceinline__ V4<T> hot1(const PhysT<T> &P, T drho, T mass) {
 }
 
 // ---------------------------------------------------------------------------
-// Fixes each particle's place inside its cell by its raw index (stable,
-// deterministic), gathers raw -> cell order and writes the records of
-// evaluation n.
+// Fixes each particle's place inside its cell by its id (ids are unique), so
+// the cell order depends only on the positions and ids -- not on where the
+// particles stood in raw -- which makes a rebuild from a restored checkpoint
+// reproduce the running context's order exactly.  Gathers raw -> cell order
+// and writes the records of evaluation n.
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_reorder(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, CellSort cs,
@@ -90,8 +102,9 @@ __global__ void k_reorder(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, Ce
     uint32_t j = cs.tmp[t];
     uint32_t k = cs.knew[j];
     uint2 se = cs.cellSE[k];
+    const uint32_t idj = raw.id[j];
     uint32_t rank = 0;
-    for (uint32_t u = se.x; u < se.y; ++u) rank += cs.tmp[u] < j ? 1u : 0u;
+    for (uint32_t u = se.x; u < se.y; ++u) rank += raw.id[cs.tmp[u]] < idj ? 1u : 0u;
     uint32_t i = se.x + rank;
     cs.key[i] = k;
     double2 p = raw.pos[j];
@@ -563,14 +576,21 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
     // MODE 2: corrector X^{n+1} = X^n + dt Xdot^{n+1/2}, positions with
     // u* = u^n + dt/2 a^{n+1/2}; buffer particles follow the inflow velocity.
     if (!active || sub != 0) return;
-    double dt = sc->dt, half = 0.5 * dt, t = sc->t;
-    double2 p0 = srt.pos[i];
-    V2<T> v0 = srt.vel[i];
-    T d0 = srt.drho[i], c0 = srt.drc[i];
+    // every load of the particle's state first: the stores below go to
+    // arrays the compiler cannot prove distinct from these
+    const double dt = sc->dt, t = sc->t;
+    const double2 p0 = srt.pos[i];
+    const V2<T> v0 = srt.vel[i];
+    const T d0 = srt.drho[i], c0 = srt.drc[i];
+    const T mass = srt.mass[i];
+    const uint32_t pid = srt.id[i];
+    const V4<T> h0n = nH0[i];
+    const T rho_half = P.summation ? hot.H1[i].y : T(0);
+    V2<T> ds = srt.disp[i];
+    const double half = 0.5 * dt;
     double2 p1 = p0;
     V2<T> v1 = v0;
     T d1 = d0, c1 = c0;
-    V2<T> ds = srt.disp[i];
     T stx = T(0), sty = T(0);           // this step's displacement (cell offsets)
     T srx = T(0), sry = T(0);           // the same relative to (dfx, dfy) (rebuild decision)
     if (typ == T_DEAD) {
@@ -581,7 +601,7 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
         p1 = make_double2(p0.x + dt * (P.ufx_d + (double)usx), p0.y + dt * (P.ufy_d + (double)usy));
         v1 = mk2(v0.x + tdt * ax, v0.y + tdt * ay);
         if (P.summation) {              // Eq. 6: the density of the half-step evaluation
-            d1 = hot.H1[i].y - P.rho0;
+            d1 = rho_half - P.rho0;
             c1 = T(0);
         } else {
             T y = tdt * drho - c0;      // compensated density update
@@ -607,14 +627,13 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
         typ = T_DEAD;
         atomicAdd((unsigned long long *)&sc->deleted, 1ull);
     }
-    T mass = srt.mass[i];
     raw.pos[i] = p1;
     raw.vel[i] = v1;
     raw.drho[i] = d1;
     raw.drc[i] = c1;
     raw.mass[i] = mass;
     raw.type[i] = typ;
-    raw.id[i] = srt.id[i];
+    raw.id[i] = pid;
     raw.disp[i] = ds;
     // the same state in place in the cell order of the last build, with the
     // records of evaluation n+1 on its cells: a next step that keeps the
@@ -631,7 +650,6 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
     // displacement (in T, as the displacement since the build; a few ulps
     // from the offsets of the FP64 position over the steps between builds,
     // far inside the band where pair tests are redone in FP64)
-    V4<T> h0n = nH0[i];
     T xl = h0n.x + stx, yo = h0n.y + sty;
     nH0[i] = mk4<T>(xl, yo, v1.x, v1.y);
     nH1[i] = typ == T_DEAD ? mk4<T>(T(0), P.rho0, T(0), P.c0) : hot1<T>(P, d1, mass);
@@ -762,7 +780,7 @@ __device__ __forceinline__ void colour_bits(double c, unsigned &lo, unsigned &nh
 }
 
 template <class T, int K, int G>
-__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
+__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_PAIRSUM_MINB)
 k_pairsum(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, NList nl,
           const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf, Boundary bd,
           const uint8_t *__restrict__ type, V4<T> *__restrict__ accN, T *__restrict__ gsum,
@@ -781,7 +799,7 @@ k_pairsum(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, NList nl,
         T ua = ha.z, va = ha.w;
         const V4<T> *__restrict__ H0 = hot.H0;
         const V4<T> *__restrict__ H1 = hot.H1;
-        for_list<G, SPH_CH_FORCES, T>(
+        for_list<G, SPH_CH_PAIRSUM, T>(
             P, nl, hot.pos, i, sub, ha.x, ha.y,
             [&](unsigned b) {
                 PairRec<T> r;
@@ -1111,11 +1129,15 @@ void launch_density(int lanes, const PhysT<T> &P, const Scalars *sc, const NList
     });
 }
 
+// In a step (skip) one lane per particle: every lane repeats the particle's
+// skip test, and only the particles near the surface walk (1M-particle jet,
+// same box: 57.5 us per sweep at 2 lanes, 45.6 at 1).
 template <class T>
 void launch_normal(int lanes, const PhysT<T> &P, const Scalars *sc, const NList &nl,
                    const Hot<T> &hot, const Csf<T> &csf, int cap, cudaStream_t s,
                    const uint32_t *key, const T *gsum, const uint2 *crange, int ncx) {
     const bool skip = gsum != nullptr;
+    if (skip) lanes = 1;
     with_lanes(lanes, [&](auto Gc) {
         constexpr int G = decltype(Gc)::value;
         int b = sweep_blocks(cap, G);
@@ -1160,18 +1182,18 @@ static void launch_surface_k(int mode, const PhysT<T> &P, const Grid &g, const I
         launch_k(k_surface<T, K, 2, G>, b, SWEEP_BLOCK, s, P, g, inf, sc, nl, hot, csf, srt, raw, accN, acc, dr, nH0, nH1);
 }
 
+// One lane per particle whatever the sweeps use: most particles only stream
+// through the epilogue (the curvature walk is for N_a = 1 alone), which a
+// particle's other lanes would sit out.
 template <class T>
-void launch_surface(int lanes, int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
+void launch_surface(int, int mode, const PhysT<T> &P, const Grid &g, const Inflow &inf,
                     Scalars *sc, const NList &nl, const Hot<T> &hot, const Csf<T> &csf,
                     const State<T> &srt, const State<T> &raw, const V4<T> *accN, V2<T> *acc,
                     T *dr, int cap, cudaStream_t s, V4<T> *nH0, V4<T> *nH1) {
-    with_lanes(lanes, [&](auto Gc) {
-        constexpr int G = decltype(Gc)::value;
-        if (P.kernel == 1)
-            launch_surface_k<T, 1, G>(mode, P, g, inf, sc, nl, hot, csf, srt, raw, accN, acc, dr, nH0, nH1, cap, s);
-        else
-            launch_surface_k<T, 0, G>(mode, P, g, inf, sc, nl, hot, csf, srt, raw, accN, acc, dr, nH0, nH1, cap, s);
-    });
+    if (P.kernel == 1)
+        launch_surface_k<T, 1, 1>(mode, P, g, inf, sc, nl, hot, csf, srt, raw, accN, acc, dr, nH0, nH1, cap, s);
+    else
+        launch_surface_k<T, 0, 1>(mode, P, g, inf, sc, nl, hot, csf, srt, raw, accN, acc, dr, nH0, nH1, cap, s);
 }
 
 template <class T, int K, int G>
@@ -1319,6 +1341,67 @@ void launch_surrogate_residual(int n, const uint8_t *type, const float2 *abar, f
              dr_k, sums);
 }
 
+// ---------------------------------------------------------------------------
+// Run statistics over raw[0, n): per fluid particle m, m u, m |u|^2 / 2,
+// -m g . r, m e(rho) (Tait elastic energy) accumulated in FP64; counts of
+// fluid and buffer particles; max |rho - rho0| / rho0 as ordered bits.
+// acc[0..5] = mass, px, py, kinetic, potential, elastic; cnt[0..1] = fluid,
+// buffer; cnt[2] = bits of the maximum.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_stats(State<T> raw, const Scalars *__restrict__ sc, double ufx, double ufy,
+                        double gx, double gy, double rho0, double B, double gamma,
+                        double *__restrict__ acc, unsigned long long *__restrict__ cnt) {
+    const int n = sc->n;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long nf = 0, nb = 0, mx = 0;
+    if (i < n) {
+        uint8_t typ = raw.type[i];
+        if (typ == T_FLUID) {
+            double m = (double)raw.mass[i];
+            double ux = ufx + (double)raw.vel[i].x, uy = ufy + (double)raw.vel[i].y;
+            double2 p = raw.pos[i];
+            // the compensated offset: drho - carry
+            double d = ((double)raw.drho[i] - (double)raw.drc[i]) / rho0;
+            double e = B / rho0 * (expm1((gamma - 1.0) * log1p(d)) / (gamma - 1.0) - d / (1.0 + d));
+            v[0] = m;
+            v[1] = m * ux;
+            v[2] = m * uy;
+            v[3] = 0.5 * m * (ux * ux + uy * uy);
+            v[4] = -m * (gx * p.x + gy * p.y);
+            v[5] = m * e;
+            nf = 1;
+            mx = (unsigned long long)__double_as_longlong(fabs(d));
+        } else if (typ == T_BUFFER) {
+            nb = 1;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        nf += __shfl_xor_sync(0xffffffffu, nf, o);
+        nb += __shfl_xor_sync(0xffffffffu, nb, o);
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = w > mx ? w : mx;
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) atomicAdd(&acc[k], v[k]);
+        atomicAdd(&cnt[0], nf);
+        atomicAdd(&cnt[1], nb);
+        atomicMax(&cnt[2], mx);
+    }
+}
+
+template <class T>
+void launch_stats(const PhysT<T> &P, const State<T> &raw, const Scalars *sc, double gx, double gy,
+                  double rho0, double B, double gamma, double *acc, unsigned long long *cnt,
+                  int cap, cudaStream_t s) {
+    launch_k(k_stats<T>, (cap + 255) / 256, 256, s, raw, sc, P.ufx_d, P.ufy_d, gx, gy, rho0, B,
+             gamma, acc, cnt);
+}
+
 __global__ void k_decide(cudaGraphConditionalHandle h, const Scalars *__restrict__ sc) {
     cudaGraphSetConditional(h, sc->need_full ? 1u : 0u);
 }
@@ -1360,7 +1443,10 @@ void *decide_kernel() { return (void *)k_decide; }
                                     const State<T> &, const V4<T> *, const V2<T> *, const T *,    \
                                     const Hot<T> &, int, cudaStream_t);                           \
     template void launch_spawn<T>(const PhysT<T> &, const Inflow &, Scalars *, const State<T> &, \
-                                  const double *, int, int, cudaStream_t);
+                                  const double *, int, int, cudaStream_t);                        \
+    template void launch_stats<T>(const PhysT<T> &, const State<T> &, const Scalars *, double,   \
+                                  double, double, double, double, double *,                       \
+                                  unsigned long long *, int, cudaStream_t);
 
 SPH_INST(float)
 SPH_INST(double)

@@ -51,6 +51,22 @@ def _traj_errors(g, st):
             rel_l2(g["rho"], st["rho"]))
 
 
+def _evaluation_on_oracle_state(sim, osim, orc):
+    """Per-evaluation errors (du/dt, drho/dt rel-L2) of the GPU against the
+    oracle on the oracle's current state, loaded into the GPU context."""
+    sim.set_state(osim.st)
+    sim.evaluate()
+    g = sim.state()
+    ev = osim.evaluate()
+    st = osim.st
+    assert np.array_equal(g["id"], st["id"].astype(np.uint32))
+    keep = ~ambiguous_mask(orc, osim.d, st, ev)
+    assert keep.mean() > 0.95
+    ea = rel_l2_vec(g["ax"][keep], g["ay"][keep], ev["ax"][keep], ev["ay"][keep])
+    ed = rel_l2(g["drho"], ev["drho"]) if np.abs(ev["drho"]).max() > 0 else 0.0
+    return ea, ed
+
+
 def _drho_error(g, st, rho0):
     """rel-L2 of the density offset rho - rho0 (what drives the pressure)."""
     off = np.asarray(st["rho"]) - rho0
@@ -106,6 +122,11 @@ def test_jet_c2_full_size_100_steps(sph, orc):
     report(case="jet_c2", prec="fp32", steps=100, r=er, u=eu, rho=erho, rho_offset=eoff)
     assert er < 1e-4 and eu < 1e-4 and erho < 1e-4
     assert eoff < 1e-2
+    # per-evaluation parity on the configured workload's own state after 100
+    # steps (a running flow with a pressure field)
+    ea, ed = _evaluation_on_oracle_state(sim, osim, orc)
+    report(case="jet_c2_after_100_steps", prec="fp32", accel=ea, drho_dt=ed)
+    assert ea < 1e-5 and ed < 1e-5
 
 
 def test_jet_c3_full_size_100_steps(sph, orc):
@@ -123,18 +144,22 @@ def test_jet_c3_full_size_100_steps(sph, orc):
     try:
         sim.run(100)
         osim.run(100)
+        g = sim.state()
+        assert len(g["x"]) > 990000
+        er, eu, erho = _traj_errors(g, osim.st)
+        eoff = _drho_error(g, osim.st, osim.d.rho0)
+        report(case="jet_c3", prec="fp32", steps=100, r=er, u=eu, rho=erho, rho_offset=eoff,
+               particles=int(g["x"].size))
+        assert er < 1e-4 and eu < 1e-4 and erho < 1e-4
+        assert eoff < 1e-2
+        # per-evaluation parity on the configured workload's own state after
+        # 100 steps (a running flow with a pressure field)
+        ea, ed = _evaluation_on_oracle_state(sim, osim, orc)
+        report(case="jet_c3_after_100_steps", prec="fp32", accel=ea, drho_dt=ed)
+        assert ea < 1e-5 and ed < 1e-5
     finally:
         orc.set_threads(1)
-    g = sim.state()
-    sim.close()
-    assert len(g["x"]) > 990000
-    tg = (g["x"].size, osim.nstep)
-    er, eu, erho = _traj_errors(g, osim.st)
-    eoff = _drho_error(g, osim.st, osim.d.rho0)
-    report(case="jet_c3", prec="fp32", steps=100, r=er, u=eu, rho=erho, rho_offset=eoff,
-           particles=tg[0])
-    assert er < 1e-4 and eu < 1e-4 and erho < 1e-4
-    assert eoff < 1e-2
+        sim.close()
 
 
 @pytest.mark.parametrize("kernel", ["wendland", "cubic"])
@@ -199,10 +224,15 @@ def test_breakup_length_five_seed_mean(sph, orc, lanes, cadence):
 @pytest.mark.parametrize("dx,length,label", [(1.0 / 40, 60.0, "jet_c2"),
                                              (1.0 / 100, 100.0, "jet_c3")])
 def test_uniform_start_state_surface_tension_only(sph, orc, dx, length, label):
-    # The unperturbed strip: no pressure field, du/dt is the CSF term plus a
-    # tiny viscous term.  FP32 curvature on flat surfaces has a noise floor
-    # set by the FP32 cell offsets (~1e-7 h), which dominates this nearly
-    # zero field; the error is reported and held to 5e-5.
+    # The unperturbed strip at t = 0: no pressure field, and on its flat
+    # surfaces the exact curvature (Eq. 23) and CSF term vanish, so the exact
+    # du/dt is concentrated at the two strip ends (plus a tiny viscous term).
+    # The FP32 curvature of the flat surfaces carries a rounding floor (unit
+    # normals good to ~1e-7, differenced in Eq. 23) spread over every surface
+    # particle, so this rel-L2 grows with the strip's length in particles (C2
+    # 1.2e-5, C3 2.5e-5) though the absolute error stays ~1e-5 of the rms
+    # acceleration.  Held to 5e-5 here; the 100-step tests hold the same
+    # workloads to 1e-5 per evaluation once a pressure field exists.
     case = wl.jet(seed=0, Re=200, We=20, dx=dx, length=length, prec="fp32",
                   capacity_factor=1.15)
     osim = oracle_sim(orc, case)

@@ -179,6 +179,16 @@ template <class T> static State<T> state_of(void *const a[8]) {
     return s;
 }
 
+// A cell offset as the records of precision T store it (fixed point in FP32).
+template <class T> static T store_off(double off, double sc);
+template <> float store_off<float>(double off, double sc) {
+    int v = off_fixed(off, sc);
+    float f;
+    memcpy(&f, &v, sizeof f);
+    return f;
+}
+template <> double store_off<double>(double off, double) { return off; }
+
 template <class T> static PhysT<T> make_phys(const sph_params &p, const Grid &g, bool walls) {
     PhysT<T> P{};
     double h = p.h_over_dx * p.dx;
@@ -244,8 +254,10 @@ template <class T> static PhysT<T> make_phys(const sph_params &p, const Grid &g,
     double half_skin = 0.5 * p.skin_over_h * h;
     P.dfx = walls ? T(0) : (T)p.u_frame_x;
     P.dfy = walls ? T(0) : (T)p.u_frame_y;
-    P.cell_lo = (T)(walls ? -half_skin : -2.0 * g.sc);
-    P.cell_hi = (T)(walls ? g.sc + half_skin : 3.0 * g.sc);
+    P.cell_lo = store_off<T>(walls ? -half_skin : -2.0 * g.sc, g.sc);
+    P.cell_hi = store_off<T>(walls ? g.sc + half_skin : 3.0 * g.sc, g.sc);
+    P.off_unit = (T)(g.sc / OFF_ONE);
+    P.off_scale = (T)(OFF_ONE / g.sc);
     P.courant = p.courant;
     P.dt_fixed = p.dt_fixed;
     return P;
@@ -544,7 +556,8 @@ static sph_status upload_boundary(sph_ctx *c) {
     }
     if (c->tsz == 4) {
         std::vector<float> hf(4 * nb);
-        for (size_t q = 0; q < 4 * nb; ++q) hf[q] = (float)hd[q];
+        for (size_t q = 0; q < 4 * nb; ++q)
+            hf[q] = q % 4 < 2 ? store_off<float>(hd[q], c->grid.sc) : (float)hd[q];
         CK(copy_sync(c, c->bH, hf.data(), 4 * nb * sizeof(float), cudaMemcpyHostToDevice), "upload boundary");
     } else {
         CK(copy_sync(c, c->bH, hd.data(), 4 * nb * sizeof(double), cudaMemcpyHostToDevice), "upload boundary");

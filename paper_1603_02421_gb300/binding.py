@@ -117,8 +117,8 @@ _SIGS = {
                           ctypes.c_int),
     "sph_mpnn_adam": ([ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
     "sph_surrogate_step": ([_CTX, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                            ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D],
-                           ctypes.c_int),
+                            ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D,
+                            _D], ctypes.c_int),
     "sph_run_async": ([_CTX, ctypes.c_longlong], ctypes.c_int),
     "sph_set_tuning": ([_CTX, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sph_set_start_form": ([_CTX, ctypes.c_int], ctypes.c_int),
@@ -689,14 +689,17 @@ def sph_mpnn_adam(net, lr):
     _mp_check(net, lib().sph_mpnn_adam(net, float(lr)))
 
 
-def sph_surrogate_step(ctx, net, k, u_ref, a_ref, threshold, bf16=True):
+def sph_surrogate_step(ctx, net, k, u_ref, a_ref, threshold, bf16=True, field=False):
     """One surrogate step with plain SPH as judge and fallback; returns
-    (accepted, momentum residual, density residual)."""
+    (accepted, momentum residual, density residual), with field=True also
+    the acceleration-field residual."""
     acc = ctypes.c_int()
-    rm, rd = ctypes.c_double(), ctypes.c_double()
+    rm, rd, rf = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(ctx, lib().sph_surrogate_step(ctx, net, int(k), float(u_ref), float(a_ref),
                                          float(threshold), int(bool(bf16)), ctypes.byref(acc),
-                                         ctypes.byref(rm), ctypes.byref(rd)))
+                                         ctypes.byref(rm), ctypes.byref(rd), ctypes.byref(rf)))
+    if field:
+        return bool(acc.value), rm.value, rd.value, rf.value
     return bool(acc.value), rm.value, rd.value
 
 

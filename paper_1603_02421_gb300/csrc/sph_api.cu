@@ -79,7 +79,11 @@ struct sph_ctx {
     unsigned long long graph_gen = 0;   // counts changes that invalidate captured steps
     // learned-surrogate step scratch: SPH accelerations and density rates at
     // the step start, residual sums, saved particle count
-    void *sg_an = nullptr, *sg_drn = nullptr, *sg_sums = nullptr, *sg_n = nullptr;
+    void *sg_an = nullptr, *sg_drn = nullptr, *sg_sums = nullptr;
+    // the evaluation ending the last accepted surrogate step can start the
+    // next one while the cell-build and step counters are those recorded
+    bool sg_ready = false;
+    long long sg_builds = -1, sg_step = -1;
 
     // tuning: lanes per particle in the pair sweeps, longest cell-build cadence
     int lanes = 4, cadence = 1;
@@ -769,6 +773,7 @@ sph_status sph_add_particles(sph_ctx *c, long long n, const double *x, const dou
                              const double *mass, const unsigned char *type, const double *nx,
                              const double *ny) {
     if (!c) return SPH_ERR_ARG;
+    c->sg_ready = false;
     try {
         if (n < 0) return fail(c, SPH_ERR_ARG, "n < 0");
         if (n == 0) return SPH_OK;
@@ -837,6 +842,7 @@ sph_status sph_add_particles(sph_ctx *c, long long n, const double *x, const dou
 sph_status sph_inflow(sph_ctx *c, double x_exit, double y0, double y1, double U, double amp,
                       double k, double phase, int layers) {
     if (!c) return SPH_ERR_ARG;
+    c->sg_ready = false;
     try {
         if (c->inf.on) return fail(c, SPH_ERR_STATE, "inflow already configured");
         double dx = c->prm.dx;
@@ -1156,6 +1162,7 @@ sph_status sph_set_state(sph_ctx *c, long long n, const double *x, const double 
         c->hsc->n = (int)n;
         c->hsc->nsrt = 0;
         c->force_full = true;
+        c->sg_ready = false;
         if (n > 0) c->hsc->next_id = std::max(c->hsc->next_id, maxid + 1);
         s = push_scalars(c);
         c->n_eval = 0;
@@ -1382,6 +1389,7 @@ sph_status sph_checkpoint_load(sph_ctx *c, const void *buf, size_t bytes) {
     c->hsc->next_id = hd.next_id;
     c->hsc->deleted = hd.deleted;
     c->force_full = true;
+    c->sg_ready = false;
     s = push_scalars(c);
     c->n_eval = 0;
     c->csf_valid = false;
@@ -1570,6 +1578,7 @@ static sph_status snapshot(sph_ctx *c, bool restore) {
                            c->stream), "restore");
     *c->hsc = c->snap_sc;
     c->force_full = true;
+    c->sg_ready = false;
     return push_scalars(c);
 }
 
@@ -1658,6 +1667,7 @@ sph_status sph_get_rebuild_stats(sph_ctx *c, long long *builds, double *disp_max
 sph_status sph_request_rebuild(sph_ctx *c) {
     if (!c) return SPH_ERR_ARG;
     c->force_full = true;
+    c->sg_ready = false;
     return SPH_OK;
 }
 
@@ -1720,7 +1730,7 @@ extern "C" {
 // ---------------------------------------------------------------------------
 sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, double a_ref,
                               double threshold, int bf16, int *accepted, double *res_momentum,
-                              double *res_density) {
+                              double *res_density, double *res_field) {
     if (!c) return SPH_ERR_ARG;
     if (accepted) *accepted = 0;
     if (!net) return fail(c, SPH_ERR_ARG, "network is NULL");
@@ -1738,31 +1748,42 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
         cudaError_t e = cudaSuccess;
         c->sg_an = dalloc(c, (size_t)c->cap * sizeof(float2), e);
         if (!e) c->sg_drn = dalloc(c, (size_t)c->cap * sizeof(float), e);
-        if (!e) c->sg_sums = dalloc(c, 4 * sizeof(double), e);
-        if (!e) c->sg_n = dalloc(c, sizeof(int), e);
+        if (!e) c->sg_sums = dalloc(c, 8 * sizeof(double), e);
         CK(e, "surrogate scratch");
     }
+    // the evaluation that ended the last accepted surrogate step is this
+    // step's start when nothing has touched the state since (no step, cell
+    // build or state change: same counters) and its time advance kept the
+    // lists (device rebuild decision)
+    const bool reuse = c->sg_ready && c->sg_builds == c->hsc->builds &&
+                       c->sg_step == c->hsc->step && !c->hsc->need_full;
+    c->sg_ready = false;
     s = snapshot(c, false);
     if (s) return s;
-    auto reject = [&](double rm, double rd) -> sph_status {
+    auto report = [&](double rm, double rd, double rf) {
+        if (res_momentum) *res_momentum = rm;
+        if (res_density) *res_density = rd;
+        if (res_field) *res_field = rf;
+    };
+    auto reject = [&](double rm, double rd, double rf) -> sph_status {
         sph_status r = snapshot(c, true);
         if (r) return r;
         r = sph_run_async(c, k);
         if (!r) r = sph_sync(c);
-        if (res_momentum) *res_momentum = rm;
-        if (res_density) *res_density = rd;
+        report(rm, rd, rf);
         return r;
     };
-    // SPH at the step start, with the time-step candidates of Eqs. 30-31
     State<float> raw = state_of<float>(c->raw), srt = state_of<float>(c->srt);
-    {
-        // the network reads the normals of every particle: no skipping
+    if (!reuse) {
+        // SPH at the step start on fresh lists, with the time-step
+        // candidates of Eqs. 30-31; the network reads every particle's
+        // normal, so none is skipped
         const uint32_t *key = enqueue_sort<float>(c);
         enqueue_build<float>(c, key);
         enqueue_eval<float>(c, hot_n<float>(c), 1, false);
+        s = after_work(c, "surrogate: evaluation at the start");
+        if (s) return s;
     }
-    s = after_work(c, "surrogate: evaluation at the start");
-    if (s) return s;
     c->n_eval = c->hsc->nsrt;
     c->csf_valid = true;
     const int n = c->hsc->nsrt;
@@ -1784,39 +1805,42 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
     const double dT = k * dt;
     CK(cudaMemcpyAsync(c->sg_an, c->acc, (size_t)n * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream), "copy");
     CK(cudaMemcpyAsync(c->sg_drn, c->dr, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream), "copy");
-    // prediction and update
+    // prediction and update; the time advance lays inflow layers and decides
+    // (cadence and displacements) whether the next step rebuilds the lists
     const float2 *abar = nullptr;
     s = mpnn_predict(net, c, u_ref, bf16 != 0, &abar);
     if (s) return fail(c, s, "surrogate: %s", sph_mpnn_last_error(net));
     launch_surrogate_update(c->Pf, c->inf, c->grid, c->sc, srt, raw, (const float2 *)c->sg_an,
                             abar, (float)a_ref, (const float *)c->sg_drn, dT, c->cap, c->stream);
-    launch_spawn<float>(c->Pf, c->inf, c->sc, raw, c->layer_y, c->cap, 1, c->stream);
-    CK(cudaMemcpyAsync(c->sg_n, &c->sc->n, sizeof(int), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    launch_spawn<float>(c->Pf, c->inf, c->sc, raw, c->layer_y, c->cap, c->cadence, c->stream);
     // SPH at the end, on the cell order and lists of the start (exact while
-    // no particle moved more than skin/2, which the refresh checks)
+    // no particle moved more than skin/2, which the refresh checks), with the
+    // time-step candidates, so that it can start the next surrogate step
     launch_refresh<float>(c->Pf, c->grid, c->sc, c->cs.key, raw, srt, hot_n<float>(c), c->cap,
                           c->stream);
     enqueue_cells<float>(c, false);
-    enqueue_eval<float>(c, hot_n<float>(c), 0, false);
-    CK(cudaMemcpyAsync(&c->sc->n, c->sg_n, sizeof(int), cudaMemcpyDeviceToDevice, c->stream), "copy");
-    CK(cudaMemsetAsync(c->sg_sums, 0, 4 * sizeof(double), c->stream), "clear");
-    launch_surrogate_residual(n, srt.type, abar, (float)a_ref, (const float2 *)c->sg_an,
+    enqueue_eval<float>(c, hot_n<float>(c), 1, false);
+    CK(cudaMemsetAsync(c->sg_sums, 0, 8 * sizeof(double), c->stream), "clear");
+    launch_surrogate_residual(n, srt.type, srt.mass, abar, (float)a_ref, (const float2 *)c->sg_an,
                               (const float2 *)c->acc, (const float *)c->sg_drn,
                               (const float *)c->dr, (double *)c->sg_sums, c->cap, c->stream);
-    double sums[4] = {0, 0, 0, 0};
+    double sums[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     CK(cudaMemcpyAsync(sums, c->sg_sums, sizeof sums, cudaMemcpyDeviceToHost, c->stream), "residual");
     s = after_work(c, "surrogate: evaluation at the end");
-    double rm = sums[1] > 0 ? std::sqrt(sums[0] / sums[1]) : 0.0;
-    double rd = sums[3] > 0 ? 0.5 * dT * std::sqrt(sums[2] / sums[3]) / c->prm.rho0 : 0.0;
-    if (s == SPH_ERR_SKIN) return reject(rm, rd);   // moved too far for the lists: plain steps
+    double rm = sums[2] > 0 ? std::sqrt(sums[0] * sums[0] + sums[1] * sums[1]) / sums[2] : 0.0;
+    double rd = sums[4] > 0 ? 0.5 * dT * std::sqrt(sums[3] / sums[4]) / c->prm.rho0 : 0.0;
+    double rf = sums[6] > 0 ? std::sqrt(sums[5] / sums[6]) : 0.0;
+    if (s == SPH_ERR_SKIN) return reject(rm, rd, rf);   // moved too far for the lists: plain steps
     if (s) return s;
-    if (!(rm <= threshold && rd <= threshold)) return reject(rm, rd);
+    if (!(rm <= threshold && rd <= threshold)) return reject(rm, rd, rf);
+    // plain steps after this one rebuild first; a next surrogate step may
+    // start from the evaluation just done
     c->force_full = true;
-    c->csf_valid = false;
-    c->n_eval = 0;
+    c->sg_ready = true;
+    c->sg_builds = c->hsc->builds;
+    c->sg_step = c->hsc->step;
     if (accepted) *accepted = 1;
-    if (res_momentum) *res_momentum = rm;
-    if (res_density) *res_density = rd;
+    report(rm, rd, rf);
     return SPH_OK;
 }
 

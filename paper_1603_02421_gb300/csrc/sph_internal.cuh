@@ -340,9 +340,12 @@ void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Gri
                              const State<float> &srt, const State<float> &raw, const float2 *a_n,
                              const float2 *y, float a_ref, const float *dr, double dT, int cap,
                              cudaStream_t s);
-void launch_surrogate_residual(int n, const uint8_t *type, const float2 *y, float a_ref,
-                               const float2 *a_n, const float2 *a_k, const float *dr_n,
-                               const float *dr_k, double *sums, int cap, cudaStream_t s);
+// Residual sums of a surrogate step (k_surrogate_residual): sums[7], zeroed by
+// the caller.
+void launch_surrogate_residual(int n, const uint8_t *type, const float *mass, const float2 *y,
+                               float a_ref, const float2 *a_n, const float2 *a_k,
+                               const float *dr_n, const float *dr_k, double *sums, int cap,
+                               cudaStream_t s);
 
 // Read-only view of a context's last evaluation (for the learned surrogate):
 // records, CSF fields and neighbour lists of the current state in cell

@@ -1289,6 +1289,22 @@ __global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *
     raw.type[i] = typ;
     raw.id[i] = srt.id[i];
     raw.disp[i] = ds;
+    // largest displacement since the build and in this step, for the time
+    // advance's rebuild decision (the step's move relative to the frame)
+    if (typ != T_DEAD) {
+        float d2 = ds.x * ds.x + ds.y * ds.y;
+        float mx = (float)(p1.x - p0.x) - (float)(dT * (double)P.dfx);
+        float my = (float)(p1.y - p0.y) - (float)(dT * (double)P.dfy);
+        float s2 = mx * mx + my * my;
+        unsigned m = __activemask();
+        unsigned a = __reduce_max_sync(m, __float_as_uint(d2));
+        unsigned b2 = __reduce_max_sync(m, __float_as_uint(s2));
+        if ((threadIdx.x & 31u) == (unsigned)(__ffs(m) - 1)) {
+            int slot = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) & (RED_SLOTS - 1);
+            atomicMax(&sc->max_disp2[slot], a);
+            atomicMax(&sc->max_step2[slot], b2);
+        }
+    }
 }
 
 void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Grid &g, Scalars *sc,
@@ -1299,38 +1315,49 @@ void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Gri
              dr, dT);
 }
 
-// Residuals of a surrogate step over the fluid particles (cell order): sums of
-// |abar - (a_n + a_k)/2|^2 with abar = a_n + a_ref y, |(a_n + a_k)/2|^2 and
-// (drho_k - drho_n)^2, and the fluid count, accumulated in FP64.
+// Residual sums of a surrogate step over the fluid particles present at both
+// ends (cell order; type from the end of the step), accumulated in FP64:
+//   sums[0..1] = sum m (abar - (a_n + a_k)/2)      (momentum balance)
+//   sums[2]    = sum m |(a_n + a_k)/2|
+//   sums[3]    = sum (drho/dt_k - drho/dt_n)^2     (density)
+//   sums[4]    = fluid count
+//   sums[5]    = sum |abar - (a_n + a_k)/2|^2      (acceleration field)
+//   sums[6]    = sum |(a_n + a_k)/2|^2
+// with abar = a_n + a_ref y.
 __global__ void k_surrogate_residual(int n, const uint8_t *__restrict__ type,
+                                     const float *__restrict__ mass,
                                      const float2 *__restrict__ y, float a_ref,
                                      const float2 *__restrict__ a_n, const float2 *__restrict__ a_k,
                                      const float *__restrict__ dr_n, const float *__restrict__ dr_k,
                                      double *__restrict__ sums) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (i < n && type[i] == T_FLUID) {
+        double m = (double)mass[i];
         double mx = 0.5 * ((double)a_n[i].x + a_k[i].x), my = 0.5 * ((double)a_n[i].y + a_k[i].y);
         double ex = (double)a_n[i].x + (double)a_ref * y[i].x - mx;
         double ey = (double)a_n[i].y + (double)a_ref * y[i].y - my;
         double dd = (double)dr_k[i] - dr_n[i];
-        v[0] = ex * ex + ey * ey;
-        v[1] = mx * mx + my * my;
-        v[2] = dd * dd;
-        v[3] = 1.0;
+        v[0] = m * ex;
+        v[1] = m * ey;
+        v[2] = m * sqrt(mx * mx + my * my);
+        v[3] = dd * dd;
+        v[4] = 1.0;
+        v[5] = ex * ex + ey * ey;
+        v[6] = mx * mx + my * my;
     }
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 7; ++k) {
         double x = v[k];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if ((threadIdx.x & 31) == 0) atomicAdd(&sums[k], x);
     }
 }
 
-void launch_surrogate_residual(int n, const uint8_t *type, const float2 *abar, float a_ref,
-                               const float2 *a_n, const float2 *a_k, const float *dr_n,
+void launch_surrogate_residual(int n, const uint8_t *type, const float *mass, const float2 *abar,
+                               float a_ref, const float2 *a_n, const float2 *a_k, const float *dr_n,
                                const float *dr_k, double *sums, int cap, cudaStream_t s) {
-    launch_k(k_surrogate_residual, (cap + 255) / 256, 256, s, n, type, abar, a_ref, a_n, a_k, dr_n,
-             dr_k, sums);
+    launch_k(k_surrogate_residual, (cap + 255) / 256, 256, s, n, type, mass, abar, a_ref, a_n, a_k,
+             dr_n, dr_k, sums);
 }
 
 // ---------------------------------------------------------------------------

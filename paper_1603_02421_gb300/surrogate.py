@@ -27,8 +27,9 @@ def collect(case, nsamples, every=20, k=4, warm=20, lanes_cadence=(2, 8), end_ac
     """Samples from one jet: warm-up steps, then every `every` steps a state
     with the k-step targets.  Returns a list of dicts (state arrays sorted by
     id, the correction abar - a_n and abar per particle, the validity mask;
-    with end_accel also a_end, the SPH acceleration at the end of the k
-    steps, for residual_floor)."""
+    with end_accel also a_end and drho_end, the SPH acceleration and
+    continuity rate at the end of the k steps, drho at the start and the span
+    dT, for the residual floors)."""
     sim = binding.Simulation(case)
     sim.set_tuning(*lanes_cadence)
     out = []
@@ -59,6 +60,11 @@ def collect(case, nsamples, every=20, k=4, warm=20, lanes_cadence=(2, 8), end_ac
                 a_end[i0, 0] = s1["ax"][i1]
                 a_end[i0, 1] = s1["ay"][i1]
                 out[-1]["a_end"] = np.where(valid[:, None], a_end, 0.0)
+                dr_end = np.zeros(n0)
+                dr_end[i0] = s1["drho"][i1]
+                out[-1]["drho"] = np.where(valid, s0["drho"], 0.0)
+                out[-1]["drho_end"] = np.where(valid, dr_end, 0.0)
+                out[-1]["dT"] = t1 - t0
             sim.run(max(every - k, 0))
     finally:
         sim.close()
@@ -66,11 +72,13 @@ def collect(case, nsamples, every=20, k=4, warm=20, lanes_cadence=(2, 8), end_ac
 
 
 def residual_floor(samples):
-    """The judge's momentum residual, sqrt(sum |abar - (a_n + a_k)/2|^2 /
+    """The acceleration-field residual sqrt(sum |abar - (a_n + a_k)/2|^2 /
     sum |(a_n + a_k)/2|^2) over the valid particles, evaluated with the true
     k-step mean abar of plain SPH and the SPH accelerations a_n, a_k at both
     ends of those k steps: what a perfect predictor would score.  One value
-    per sample (samples collected with end_accel=True)."""
+    per sample (samples collected with end_accel=True).  The step-to-step
+    acoustic noise of WCSPH accelerations keeps it near 0.1, which is why
+    the judge does not use it."""
     out = []
     for smp in samples:
         v = smp["valid"]
@@ -79,6 +87,40 @@ def residual_floor(samples):
         trap = 0.5 * (a_n + smp["a_end"][v])
         den = float(np.sum(trap ** 2))
         out.append(float(np.sqrt(np.sum((abar - trap) ** 2) / den)) if den > 0 else 0.0)
+    return out
+
+
+def momentum_floor(samples):
+    """The judge's momentum-balance residual |sum m (abar - (a_n + a_k)/2)|
+    / sum m |(a_n + a_k)/2| over the valid particles, with the true k-step
+    mean abar of plain SPH: what a perfect predictor would score.  The
+    internal pair forces cancel in the sums, so the step-to-step noise of
+    single particles does not enter.  One value per sample (samples with
+    end_accel=True; masses from the sample's state, unit masses without
+    one)."""
+    out = []
+    for smp in samples:
+        v = smp["valid"]
+        m = np.asarray(smp["state"]["m"], float)[v] if "state" in smp else np.ones(int(v.sum()))
+        abar = smp["abar"][v]
+        a_n = abar - smp["corr"][v]
+        trap = 0.5 * (a_n + smp["a_end"][v])
+        den = float(np.sum(m * np.hypot(trap[:, 0], trap[:, 1])))
+        num = np.sum(m[:, None] * (abar - trap), axis=0)
+        out.append(float(np.hypot(num[0], num[1]) / den) if den > 0 else 0.0)
+    return out
+
+
+def density_floor(samples, rho0):
+    """The judge's density residual (dT/2) rms(drho/dt_k - drho/dt_n) / rho0
+    over the valid particles of each sample (end_accel=True), dT the span of
+    its k plain steps: the change of the continuity rate over k plain steps,
+    which the surrogate step's end evaluation also sees."""
+    out = []
+    for smp in samples:
+        v = smp["valid"]
+        d = smp["drho_end"][v] - smp["drho"][v]
+        out.append(float(0.5 * smp["dT"] * np.sqrt(np.mean(d * d)) / rho0) if d.size else 0.0)
     return out
 
 

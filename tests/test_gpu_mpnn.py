@@ -252,6 +252,44 @@ def test_surrogate_steps_on_a_jet(sph):
     sim.close()
 
 
+def _by_id(st):
+    o = np.argsort(st["id"])
+    return {k: v[o] for k, v in st.items()}
+
+
+def test_accepted_steps_reuse_the_end_evaluation(sph):
+    # an accepted surrogate step's end evaluation starts the next one (no cell
+    # build in between) and gives what a fresh start on rebuilt lists gives,
+    # up to the FP32 order of the pair sums
+    case = wl.jet(seed=3, dx=1.0 / 20, length=6.0, Re=200, We=20)
+    case["params"]["skin_over_h"] = 0.3
+    a, b = sph.Simulation(case), sph.Simulation(case)
+    for sim in (a, b):
+        sim.set_tuning(2, 8)
+        sim.run(2)
+    net = sph.Mpnn(capacity=case["params"]["capacity"])
+    net.set_params(_params(11))
+    builds = []
+    for _ in range(3):
+        acc, rm, rd = sph.sph_surrogate_step(a.ctx, net.net, 4, 1.0, 0.1, 1e30, True)
+        assert acc
+        builds.append(sph.sph_get_rebuild_stats(a.ctx)[0])
+        sph.sph_request_rebuild(b.ctx)
+        acc, rm, rd = sph.sph_surrogate_step(b.ctx, net.net, 4, 1.0, 0.1, 1e30, True)
+        assert acc
+    assert builds[2] == builds[0], builds     # steps 2 and 3 started from the reuse
+    assert sph.sph_get_rebuild_stats(b.ctx)[0] >= builds[0] + 2
+    assert a.time()["t"] == pytest.approx(b.time()["t"], rel=1e-6)
+    sa, sb = _by_id(a.state()), _by_id(b.state())
+    assert np.array_equal(sa["id"], sb["id"])
+    assert np.max(np.abs(sa["x"] - sb["x"])) < 1e-7 and np.max(np.abs(sa["y"] - sb["y"])) < 1e-7
+    assert rel_l2(sa["u"], sb["u"]) < 1e-4 and rel_l2(sa["v"], sb["v"]) < 1e-4
+    assert rel_l2(sa["rho"] - case["params"]["rho0"], sb["rho"] - case["params"]["rho0"]) < 1e-3
+    net.close()
+    a.close()
+    b.close()
+
+
 def test_trained_network_beats_the_instantaneous_acceleration(sph):
     # what the network gains: the k-step mean acceleration it predicts on
     # jets with (Re, We) it was not trained on is closer to the truth (k plain

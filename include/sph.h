@@ -487,7 +487,10 @@ sph_status sph_mpnn_adam(sph_mpnn *net, double lr);
  *      evaluation that ended the previous accepted surrogate step, when no
  *      call has changed the state since and its time advance kept the lists;
  *   2. predict the mean acceleration over the k substeps as abar = a_n +
- *      a_ref * y, y the network's output (bf16 != 0: tensor cores);
+ *      a_ref (y - ybar), y the network's output (bf16 != 0: tensor cores)
+ *      and ybar its mass-weighted mean over the fluid: the correction moves
+ *      momentum between particles but adds none (the pair forces that make
+ *      up most of it cancel in the sum, Eqs. 9-10);
  *   3. fluid: u' = u + dT abar, r' = r + dT (u + u')/2, rho' = rho + dT
  *      drho/dt_n; inflow buffer, buffer -> fluid and outflow as in a plain
  *      step; inflow layers, time advance for dT and the device's rebuild

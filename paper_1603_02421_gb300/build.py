@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsph.so")
 SOURCES = ["sph_api.cu", "sph_neighbour.cu", "sph_sweeps.cu", "sph_noalloc.cu", "sph_mpnn.cu",
-           "sph_peak.cu"]
+           "sph_mpnn_tc.cu", "sph_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -80,6 +80,7 @@ struct sph_ctx {
     // learned-surrogate step scratch: SPH accelerations and density rates at
     // the step start, residual sums, saved particle count
     void *sg_an = nullptr, *sg_drn = nullptr, *sg_sums = nullptr;
+    MpScratchHandle *sg_net = nullptr;   // the network's inference scratch
     // the evaluation ending the last accepted surrogate step can start the
     // next one while the cell-build and step counters are those recorded
     bool sg_ready = false;
@@ -760,6 +761,7 @@ void sph_destroy(sph_ctx *c) {
         if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
     }
     for (auto p : c->snap) if (p) cudaFree(p);
+    mpnn_scratch_free(c->sg_net);
     if (c->cexec) cudaGraphExecDestroy(c->cexec);
     if (c->cgraph) cudaGraphDestroy(c->cgraph);
     for (auto &b : c->allocs) cudaFree(b.p);
@@ -1721,6 +1723,7 @@ void ctx_view(sph_ctx *c, CtxView *v) {
     v->nl = c->nl;
     v->id = (const uint32_t *)c->srt[6];
     v->type = (const uint8_t *)c->srt[5];
+    v->err = &c->sc->err;
 }
 
 extern "C" {
@@ -1748,7 +1751,7 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
         cudaError_t e = cudaSuccess;
         c->sg_an = dalloc(c, (size_t)c->cap * sizeof(float2), e);
         if (!e) c->sg_drn = dalloc(c, (size_t)c->cap * sizeof(float), e);
-        if (!e) c->sg_sums = dalloc(c, 8 * sizeof(double), e);
+        if (!e) c->sg_sums = dalloc(c, 12 * sizeof(double), e);
         CK(e, "surrogate scratch");
     }
     // the evaluation that ended the last accepted surrogate step is this
@@ -1808,10 +1811,14 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
     // prediction and update; the time advance lays inflow layers and decides
     // (cadence and displacements) whether the next step rebuilds the lists
     const float2 *abar = nullptr;
-    s = mpnn_predict(net, c, u_ref, bf16 != 0, &abar);
+    s = mpnn_predict(net, c, u_ref, bf16 != 0, &abar, &c->sg_net);
     if (s) return fail(c, s, "surrogate: %s", sph_mpnn_last_error(net));
+    double *ym = (double *)c->sg_sums + 8;
+    CK(cudaMemsetAsync(c->sg_sums, 0, 12 * sizeof(double), c->stream), "clear");
+    launch_surrogate_mean(n, srt.type, srt.mass, abar, ym, c->cap, c->stream);
     launch_surrogate_update(c->Pf, c->inf, c->grid, c->sc, srt, raw, (const float2 *)c->sg_an,
-                            abar, (float)a_ref, (const float *)c->sg_drn, dT, c->cap, c->stream);
+                            abar, ym, (float)a_ref, (const float *)c->sg_drn, dT, c->cap,
+                            c->stream);
     launch_spawn<float>(c->Pf, c->inf, c->sc, raw, c->layer_y, c->cap, c->cadence, c->stream);
     // SPH at the end, on the cell order and lists of the start (exact while
     // no particle moved more than skin/2, which the refresh checks), with the
@@ -1820,8 +1827,7 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
                           c->stream);
     enqueue_cells<float>(c, false);
     enqueue_eval<float>(c, hot_n<float>(c), 1, false);
-    CK(cudaMemsetAsync(c->sg_sums, 0, 8 * sizeof(double), c->stream), "clear");
-    launch_surrogate_residual(n, srt.type, srt.mass, abar, (float)a_ref, (const float2 *)c->sg_an,
+    launch_surrogate_residual(n, srt.type, srt.mass, abar, ym, (float)a_ref, (const float2 *)c->sg_an,
                               (const float2 *)c->acc, (const float *)c->sg_drn,
                               (const float *)c->dr, (double *)c->sg_sums, c->cap, c->stream);
     double sums[8] = {0, 0, 0, 0, 0, 0, 0, 0};

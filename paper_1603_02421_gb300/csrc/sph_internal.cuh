@@ -334,18 +334,22 @@ void launch_stats(const PhysT<T> &P, const State<T> &raw, const Scalars *sc, dou
 // Host stub of the one-thread kernel that sets a step graph's IF-node
 // condition from sc->need_full (the conditional step form).
 void *decide_kernel();
-// Learned-surrogate step (FP32 contexts): state update with a predicted mean
-// acceleration, and the residual sums against the SPH evaluations at both ends.
+// Learned-surrogate step (FP32 contexts): the mass-weighted mean of the
+// network output over the fluid (ym[3], zeroed by the caller), the state
+// update with the predicted mean acceleration a_n + a_ref (y - ybar), and the
+// residual sums against the SPH evaluations at both ends.
+void launch_surrogate_mean(int n, const uint8_t *type, const float *mass, const float2 *y,
+                           double *ym, int cap, cudaStream_t s);
 void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Grid &g, Scalars *sc,
                              const State<float> &srt, const State<float> &raw, const float2 *a_n,
-                             const float2 *y, float a_ref, const float *dr, double dT, int cap,
-                             cudaStream_t s);
+                             const float2 *y, const double *ym, float a_ref, const float *dr,
+                             double dT, int cap, cudaStream_t s);
 // Residual sums of a surrogate step (k_surrogate_residual): sums[7], zeroed by
 // the caller.
 void launch_surrogate_residual(int n, const uint8_t *type, const float *mass, const float2 *y,
-                               float a_ref, const float2 *a_n, const float2 *a_k,
-                               const float *dr_n, const float *dr_k, double *sums, int cap,
-                               cudaStream_t s);
+                               const double *ym, float a_ref, const float2 *a_n,
+                               const float2 *a_k, const float *dr_n, const float *dr_k,
+                               double *sums, int cap, cudaStream_t s);
 
 // Read-only view of a context's last evaluation (for the learned surrogate):
 // records, CSF fields and neighbour lists of the current state in cell
@@ -363,6 +367,7 @@ struct CtxView {
     NList nl;
     const uint32_t *id;      // particle ids in cell order
     const uint8_t *type;
+    unsigned *err;           // the context's sticky device error word
 };
 
 }  // namespace sph
@@ -372,7 +377,13 @@ struct sph_ctx;
 struct sph_mpnn;
 void ctx_view(struct sph_ctx *c, sph::CtxView *v);
 
+// Scratch of the tensor-core inference pass owned by a context (sph_mpnn.cu;
+// opaque here), made on first use at the context's capacity.
+struct MpScratchHandle;
+void mpnn_scratch_free(MpScratchHandle *h);
+
 // Surrogate forward pass on an evaluated context (sph_mpnn.cu): *y receives
-// the device array of the n predictions (float2, cell order).
+// the device array of the n predictions (float2, cell order).  bf16 selects
+// the tensor-core pass, which runs in *scratch (allocated or grown here).
 sph_status mpnn_predict(struct sph_mpnn *net, struct sph_ctx *c, double u_ref, bool bf16,
-                        const float2 **y);
+                        const float2 **y, MpScratchHandle **scratch);

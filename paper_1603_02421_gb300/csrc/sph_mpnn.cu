@@ -26,88 +26,12 @@
 #include <vector>
 
 #include "sph.h"
-#include "sph_device.cuh"
+#include "sph_mpnn.cuh"
 
 using namespace sph;
+using namespace mpnn;
 
 namespace {
-
-using V4f = Vec<float>::v4;
-using V2f = Vec<float>::v2;
-
-constexpr int MP_IN = 4, MP_H = 128, MP_P = 32, MP_L = 3, MP_OUT = 2;
-constexpr int MP_G = 4 * MP_P;        // aggregated features per particle
-constexpr int MP_CAT = MP_H + MP_G;   // input width of the update layers
-
-// Offsets (in floats) of the packed parameters: W_in, b_in, then per layer
-// Pi_l, U_l, c_l, then D, d; every matrix row-major (fan-in x fan-out).
-struct Layout {
-    long long W_in, b_in, Pi[MP_L], U[MP_L], c[MP_L], D, d, total;
-};
-
-constexpr Layout make_layout() {
-    Layout L{};
-    long long o = 0;
-    L.W_in = o; o += MP_IN * MP_H;
-    L.b_in = o; o += MP_H;
-    for (int l = 0; l < MP_L; ++l) {
-        L.Pi[l] = o; o += MP_H * MP_P;
-        L.U[l] = o; o += MP_CAT * MP_H;
-        L.c[l] = o; o += MP_H;
-    }
-    L.D = o; o += MP_H * MP_OUT;
-    L.d = o; o += MP_OUT;
-    L.total = o;
-    return L;
-}
-
-constexpr Layout kMP = make_layout();
-
-// ---------------------------------------------------------------------------
-// edge weights
-// ---------------------------------------------------------------------------
-struct EdgeW {
-    float w[4];
-};
-
-// Weights of the ordered pair (s, o) seen from particle s ("self") and its
-// list entry o: rx, ry = r_s - r_o; du, dv = u_s - u_o; V the volume of the
-// particle whose feature is summed (o in the forward sum over s's list).
-template <int K>
-__device__ __forceinline__ EdgeW edge_weights(const PhysT<float> &P, float rx, float ry, float r2,
-                                              float du, float dv, float V, float inv_uref) {
-    float q, iq, ri;
-    q_of(r2, P.h, P.inv_h, q, iq, ri);
-    float W = kernel_W<float, K>(P, q);
-    float F = kernel_F<float, K>(P, q, iq);
-    float VF = V * F * P.h;
-    EdgeW e;
-    e.w[0] = V * W;
-    e.w[1] = VF * rx;
-    e.w[2] = VF * ry;
-    e.w[3] = VF * (du * rx + dv * ry) * inv_uref;
-    return e;
-}
-
-// Entry k of particle s's list: returns false unless it is a pair closer than
-// 2h (the same FP32 band + exact FP64 test as the SPH sweeps); fills the
-// neighbour index and the self-minus-neighbour offsets and velocities.
-__device__ __forceinline__ bool list_pair(const PhysT<float> &P, const Hot<float> &hot,
-                                          const uint32_t *__restrict__ e, unsigned k, unsigned s,
-                                          const V4f &hs, unsigned &o, float &rx, float &ry,
-                                          float &r2, float &du, float &dv) {
-    uint32_t ent = e[k];
-    o = ent & 0x0FFFFFFFu;
-    V4f ho = hot.H0[o];
-    rx = off_diff<float>(P, hs.x, ho.x, code_cells((ent >> 28) & 3u));
-    ry = off_diff<float>(P, hs.y, ho.y, code_cells(ent >> 30));
-    r2 = rx * rx + ry * ry;
-    if (r2 >= P.H2hi) return false;
-    if (r2 >= P.H2lo && !exact_within(hot.pos[s], hot.pos[o], P.H2d)) return false;
-    du = hs.z - ho.z;
-    dv = hs.w - ho.w;
-    return true;
-}
 
 // ---------------------------------------------------------------------------
 // node inputs, aggregation and its adjoint (one warp per particle)
@@ -380,98 +304,6 @@ __global__ void __launch_bounds__(256) k_gemm_tn(int M, int N, int K, const floa
 }
 
 // ---------------------------------------------------------------------------
-// BF16 tensor-core GEMM (inference): C[M x N] = A[M x K] * Bt^T with A given
-// in FP32 (as k_gemm, converted to BF16 while staged), Bt[N x K] BF16
-// row-major (the transposed weight), FP32 accumulation, epilogue as k_gemm.
-// Block: 4 warps, 64 rows; warp w takes rows 16w .. 16w+15 and all N (N a
-// multiple of 8, <= 128) with mma.sync m16n8k16; K a multiple of 16, <= 256.
-// ---------------------------------------------------------------------------
-constexpr int TC_ROWS = 64, TC_PAD = 8;
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x = lo (lower 16 bits)
-    return *reinterpret_cast<uint32_t *>(&v);
-}
-
-template <int EPI, int NT>
-__global__ void __launch_bounds__(128) k_gemm_bf16(int M, int K, const float *__restrict__ A0,
-                                                   int lda0, int K0, const float *__restrict__ A1,
-                                                   int lda1, const __nv_bfloat16 *__restrict__ Bt,
-                                                   const float *__restrict__ bias, const float *R,
-                                                   float *C, int ldc) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int ldk = K + TC_PAD;                          // padded row (elements)
-    __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
-    __nv_bfloat16 *Bs = As + TC_ROWS * ldk;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * TC_ROWS;
-    // stage A (converted) and Bt
-    for (int t = tid; t < TC_ROWS * (K / 2); t += 128) {
-        int r = t / (K / 2), k = 2 * (t % (K / 2));
-        int m = m0 + r;
-        float v0 = 0.f, v1 = 0.f;
-        if (m < M) {
-            const float *src = k < K0 ? A0 + (size_t)m * lda0 + k : A1 + (size_t)m * lda1 + (k - K0);
-            v0 = src[0];
-            v1 = src[1];
-        }
-        *reinterpret_cast<uint32_t *>(&As[r * ldk + k]) = pack_bf16(v0, v1);
-    }
-    for (int t = tid; t < NT * (K / 2); t += 128) {
-        int r = t / (K / 2), k = 2 * (t % (K / 2));
-        *reinterpret_cast<uint32_t *>(&Bs[r * ldk + k]) =
-            *reinterpret_cast<const uint32_t *>(&Bt[(size_t)r * K + k]);
-    }
-    __syncthreads();
-    const int gid = lane >> 2, tig = lane & 3;
-    float acc[NT / 8][4];
-#pragma unroll
-    for (int j = 0; j < NT / 8; ++j)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[j][c] = 0.f;
-    const __nv_bfloat16 *Aw = As + (warp * 16) * ldk;
-    for (int k = 0; k < K; k += 16) {
-        uint32_t a0 = *reinterpret_cast<const uint32_t *>(&Aw[gid * ldk + k + 2 * tig]);
-        uint32_t a1 = *reinterpret_cast<const uint32_t *>(&Aw[(gid + 8) * ldk + k + 2 * tig]);
-        uint32_t a2 = *reinterpret_cast<const uint32_t *>(&Aw[gid * ldk + k + 2 * tig + 8]);
-        uint32_t a3 = *reinterpret_cast<const uint32_t *>(&Aw[(gid + 8) * ldk + k + 2 * tig + 8]);
-#pragma unroll
-        for (int j = 0; j < NT / 8; ++j) {
-            const __nv_bfloat16 *Bj = Bs + (j * 8 + gid) * ldk + k + 2 * tig;
-            uint32_t b0 = *reinterpret_cast<const uint32_t *>(Bj);
-            uint32_t b1 = *reinterpret_cast<const uint32_t *>(Bj + 8);
-            asm volatile(
-                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                : "+f"(acc[j][0]), "+f"(acc[j][1]), "+f"(acc[j][2]), "+f"(acc[j][3])
-                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < NT / 8; ++j) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            int m = m0 + warp * 16 + gid + (c >= 2 ? 8 : 0);
-            int nn = j * 8 + 2 * tig + (c & 1);
-            if (m >= M) continue;
-            float v = acc[j][c] + (bias ? bias[nn] : 0.f);
-            size_t at = (size_t)m * ldc + nn;
-            if (EPI == EPI_STORE) C[at] = v;
-            else if (EPI == EPI_RELU) C[at] = v > 0.f ? v : 0.f;
-            else if (EPI == EPI_RESRELU) C[at] = R[at] + (v > 0.f ? v : 0.f);
-        }
-    }
-}
-
-// Transposed BF16 copy of a row-major K x N matrix: Bt[n][k] = W[k][n].
-__global__ void k_to_bf16t(const float *__restrict__ W, int K, int N, __nv_bfloat16 *__restrict__ Bt) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= K * N) return;
-    int n = t / K, k = t % K;
-    Bt[t] = __float2bfloat16_rn(W[(size_t)k * N + n]);
-}
-
-// ---------------------------------------------------------------------------
 // loss and optimiser
 // ---------------------------------------------------------------------------
 // L = (1/n) sum |y - t|^2; dy = 2 (y - t) / n.
@@ -531,8 +363,11 @@ struct sph_mpnn {
     std::vector<void *> allocs;
     float *param = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;
     long long adam_t = 0;
-    __nv_bfloat16 *PiT[MP_L] = {}, *UT[MP_L] = {};
-    bool bf_stale = true;
+    // BF16 weight images of the tensor-core pass (rebuilt after a parameter
+    // change) and its scratch for sph_mpnn_forward
+    __nv_bfloat16 *u_img = nullptr, *pi_img = nullptr;
+    bool img_stale = true;
+    MpScratchHandle *fast = nullptr;
     // activations (capacity rows)
     float *x = nullptr, *pre_in = nullptr, *h[MP_L + 1] = {}, *z[MP_L] = {}, *g[MP_L] = {},
           *pre[MP_L] = {}, *y = nullptr;
@@ -612,58 +447,33 @@ void gemm_tn(cudaStream_t s, int M, int N, int K, const float *A0, int lda0, int
     k_gemm_tn<<<grid, block, 0, s>>>(M, N, K, A0, lda0, K0, A1, lda1, dC, ldc, dB, dbias);
 }
 
-template <int EPI, int NT>
-void gemm_bf16(cudaStream_t s, int M, int K, const float *A0, int lda0, int K0, const float *A1,
-               int lda1, const __nv_bfloat16 *Bt, const float *bias, const float *R, float *C,
-               int ldc) {
-    if (M <= 0) return;
-    size_t smem = (size_t)(TC_ROWS + NT) * (K + TC_PAD) * sizeof(__nv_bfloat16);
-    k_gemm_bf16<EPI, NT><<<nblk(M, TC_ROWS), 128, smem, s>>>(M, K, A0, lda0, K0, A1, lda1, Bt,
-                                                             bias, R, C, ldc);
-}
-
 template <class F> void with_kernel(int kernel, F &&f) {
     if (kernel == 1) f(std::integral_constant<int, 1>{});
     else f(std::integral_constant<int, 0>{});
 }
 
-// Forward pass over the n particles of the view; bf16 selects the tensor-core
-// path for the two dense layers of each step (training always runs FP32 and
-// keeps every activation for the backward pass).
-sph_status mp_forward(sph_mpnn *net, const CtxView &v, float inv_uref, bool bf16) {
+// FP32 forward pass over the n particles of the view, keeping every
+// activation for the backward pass (training; the reference for the
+// tensor-core pass of sph_mpnn_tc.cu).
+sph_status mp_forward(sph_mpnn *net, const CtxView &v, float inv_uref) {
     cudaStream_t s = v.stream;
     const int n = v.n;
     const Layout &L = kMP;
     const float *P = net->param;
-    if (bf16 && net->bf_stale) {
-        for (int l = 0; l < MP_L; ++l) {
-            k_to_bf16t<<<nblk(MP_H * MP_P, 256), 256, 0, s>>>(P + L.Pi[l], MP_H, MP_P, net->PiT[l]);
-            k_to_bf16t<<<nblk(MP_CAT * MP_H, 256), 256, 0, s>>>(P + L.U[l], MP_CAT, MP_H, net->UT[l]);
-        }
-        net->bf_stale = false;
-    }
     if (n == 0) return SPH_OK;
     k_mp_inputs<<<nblk(n, 256), 256, 0, s>>>(v.P, v.hot, v.csf, n, net->x);
     gemm(s, EPI_RELU, n, MP_H, MP_IN, net->x, MP_IN, MP_IN, nullptr, 0, P + L.W_in, MP_H, 0,
          P + L.b_in, nullptr, net->pre_in, net->h[0], MP_H);
     for (int l = 0; l < MP_L; ++l) {
-        if (bf16)
-            gemm_bf16<EPI_STORE, MP_P>(s, n, MP_H, net->h[l], MP_H, MP_H, nullptr, 0, net->PiT[l],
-                                       nullptr, nullptr, net->z[l], MP_P);
-        else
-            gemm(s, EPI_STORE, n, MP_P, MP_H, net->h[l], MP_H, MP_H, nullptr, 0, P + L.Pi[l], MP_P,
-                 0, nullptr, nullptr, nullptr, net->z[l], MP_P);
+        gemm(s, EPI_STORE, n, MP_P, MP_H, net->h[l], MP_H, MP_H, nullptr, 0, P + L.Pi[l], MP_P, 0,
+             nullptr, nullptr, nullptr, net->z[l], MP_P);
         with_kernel(v.P.kernel, [&](auto Kc) {
             constexpr int K = decltype(Kc)::value;
             k_mp_aggregate<K><<<nblk((long long)n * 32, 256), 256, 0, s>>>(
                 v.P, v.hot, v.nl, n, inv_uref, net->z[l], net->g[l]);
         });
-        if (bf16)
-            gemm_bf16<EPI_RESRELU, MP_H>(s, n, MP_CAT, net->h[l], MP_H, MP_H, net->g[l], MP_G,
-                                         net->UT[l], P + L.c[l], net->h[l], net->h[l + 1], MP_H);
-        else
-            gemm(s, EPI_RESRELU, n, MP_H, MP_CAT, net->h[l], MP_H, MP_H, net->g[l], MP_G,
-                 P + L.U[l], MP_H, 0, P + L.c[l], net->h[l], net->pre[l], net->h[l + 1], MP_H);
+        gemm(s, EPI_RESRELU, n, MP_H, MP_CAT, net->h[l], MP_H, MP_H, net->g[l], MP_G, P + L.U[l],
+             MP_H, 0, P + L.c[l], net->h[l], net->pre[l], net->h[l + 1], MP_H);
     }
     gemm(s, EPI_STORE, n, MP_OUT, MP_H, net->h[MP_L], MP_H, MP_H, nullptr, 0, P + L.D, MP_OUT, 0,
          P + L.d, nullptr, nullptr, net->y, MP_OUT);
@@ -716,13 +526,84 @@ sph_status mp_backward(sph_mpnn *net, const CtxView &v, float inv_uref) {
 
 }  // namespace
 
-sph_status mpnn_predict(sph_mpnn *net, sph_ctx *c, double u_ref, bool bf16, const float2 **y) {
-    if (!net || !y || !(u_ref > 0)) return net ? mp_fail(net, SPH_ERR_ARG, "bad arguments") : SPH_ERR_ARG;
+// Scratch of the tensor-core pass, owned by a context or by the network.
+struct MpScratchHandle {
+    MpScratch s;
+    int device = -1;
+    std::vector<void *> allocs;
+};
+
+void mpnn_scratch_free(MpScratchHandle *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    for (void *p : h->allocs) cudaFree(p);
+    delete h;
+}
+
+namespace {
+
+// *hp holds room for cap particles on the device afterwards.
+sph_status scratch_ensure(sph_mpnn *net, MpScratchHandle **hp, long long cap, int device) {
+    if (*hp && (*hp)->s.cap >= cap && (*hp)->device == device) return SPH_OK;
+    mpnn_scratch_free(*hp);
+    *hp = nullptr;
+    MpScratchHandle *h = new (std::nothrow) MpScratchHandle();
+    if (!h) return mp_fail(net, SPH_ERR_OOM, "host allocation failed");
+    h->device = device;
+    const size_t C = (size_t)std::max<long long>(cap, 1);
+    const size_t bytes[6] = {C * LIST_SLOTS * sizeof(uint4), C * sizeof(unsigned), C * MP_H * 2,
+                             C * MP_P * 2, C * MP_P * 2, C * sizeof(float2)};
+    void *p[6] = {};
+    for (int k = 0; k < 6; ++k) {
+        cudaError_t e = cudaMalloc(&p[k], bytes[k]);
+        if (e != cudaSuccess) {
+            mpnn_scratch_free(h);
+            return mp_fail(net, e == cudaErrorMemoryAllocation ? SPH_ERR_OOM : SPH_ERR_CUDA,
+                           "inference scratch: %s", cudaGetErrorString(e));
+        }
+        h->allocs.push_back(p[k]);
+    }
+    h->s.edge = (uint4 *)p[0];
+    h->s.ecnt = (unsigned *)p[1];
+    h->s.h = (__nv_bfloat16 *)p[2];
+    h->s.z[0] = (__nv_bfloat16 *)p[3];
+    h->s.z[1] = (__nv_bfloat16 *)p[4];
+    h->s.y = (float2 *)p[5];
+    h->s.cap = (long long)C;
+    *hp = h;
+    return SPH_OK;
+}
+
+// The tensor-core inference pass of the view into scratch h (sph_mpnn_tc.cu).
+sph_status mp_fast(sph_mpnn *net, const CtxView &v, float inv_uref, MpScratchHandle *h) {
+    if (net->img_stale) {
+        tc_weight_images(net->param, net->u_img, net->pi_img, v.stream);
+        MCK(net, cudaStreamSynchronize(v.stream), "weight images");
+        net->img_stale = false;
+    }
+    MCK(net, tc_forward(v, inv_uref, net->param, net->u_img, net->pi_img, h->s, v.err),
+        "tensor-core forward");
+    return SPH_OK;
+}
+
+}  // namespace
+
+sph_status mpnn_predict(sph_mpnn *net, sph_ctx *c, double u_ref, bool bf16, const float2 **y,
+                        MpScratchHandle **scratch) {
+    if (!net || !y || !scratch || !(u_ref > 0))
+        return net ? mp_fail(net, SPH_ERR_ARG, "bad arguments") : SPH_ERR_ARG;
     CtxView v;
     sph_status s = mp_view(net, c, v);
     if (s) return s;
-    s = mp_forward(net, v, (float)(1.0 / u_ref), bf16);
-    *y = reinterpret_cast<const float2 *>(net->y);
+    if (!bf16) {
+        s = mp_forward(net, v, (float)(1.0 / u_ref));
+        *y = reinterpret_cast<const float2 *>(net->y);
+        return s;
+    }
+    s = scratch_ensure(net, scratch, v.cap, v.device);
+    if (s) return s;
+    s = mp_fast(net, v, (float)(1.0 / u_ref), *scratch);
+    *y = (*scratch)->s.y;
     return s;
 }
 
@@ -738,6 +619,7 @@ void sph_mpnn_destroy(sph_mpnn *net) {
     if (!net) return;
     cudaSetDevice(net->device);
     cudaDeviceSynchronize();
+    mpnn_scratch_free(net->fast);
     for (void *p : net->allocs) cudaFree(p);
     delete net;
 }
@@ -769,24 +651,14 @@ sph_status sph_mpnn_create(int device, long long capacity, sph_mpnn **out) {
     for (int l = 0; l < MP_L; ++l) { A(&net->z[l], C * MP_P); A(&net->g[l], C * MP_G); A(&net->pre[l], C * MP_H); }
     A(&net->y, C * MP_OUT); A(&net->t, C * MP_OUT); A(&net->dy, C * MP_OUT);
     A(&net->dh, C * MP_H); A(&net->dcat, C * MP_H); A(&net->dz, C * MP_P); A(&net->dtmp, C * MP_G);
-    for (int l = 0; l < MP_L && !s; ++l) {
-        s = mp_alloc(net, &net->PiT[l], (size_t)MP_H * MP_P);
-        if (!s) s = mp_alloc(net, &net->UT[l], (size_t)MP_CAT * MP_H);
-    }
+    if (!s) s = mp_alloc(net, &net->u_img, MP_L * TC_U_BYTES / 2);
+    if (!s) s = mp_alloc(net, &net->pi_img, MP_L * TC_PI_BYTES / 2);
     if (!s) s = mp_alloc(net, &net->loss, 1);
     if (!s) s = mp_alloc(net, &net->ecount, 1);
     if (s) return bail(s);
     if (cudaMemset(net->param, 0, NP * 4) != cudaSuccess || cudaMemset(net->am, 0, NP * 4) != cudaSuccess ||
         cudaMemset(net->av, 0, NP * 4) != cudaSuccess || cudaMemset(net->grad, 0, NP * 4) != cudaSuccess)
         return bail(mp_fail(net, SPH_ERR_CUDA, "clear"));
-    // the tensor-core GEMM of the update layers needs more than the default
-    // 48 KB of dynamic shared memory
-    size_t smem = (size_t)(TC_ROWS + MP_H) * (MP_CAT + TC_PAD) * sizeof(__nv_bfloat16);
-    if (cudaFuncSetAttribute(k_gemm_bf16<EPI_RESRELU, MP_H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_gemm_bf16<EPI_STORE, MP_P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return bail(mp_fail(net, SPH_ERR_CUDA, "shared-memory attribute"));
     *out = net;
     return SPH_OK;
 }
@@ -798,7 +670,7 @@ sph_status sph_mpnn_set_params(sph_mpnn *net, const float *host, long long n) {
     MCK(net, cudaMemset(net->am, 0, (size_t)n * 4), "reset optimiser");
     MCK(net, cudaMemset(net->av, 0, (size_t)n * 4), "reset optimiser");
     net->adam_t = 0;
-    net->bf_stale = true;
+    net->img_stale = true;
     return SPH_OK;
 }
 
@@ -885,10 +757,17 @@ sph_status sph_mpnn_forward(sph_mpnn *net, sph_ctx *ctx, double u_ref, int bf16,
     if (s) return s;
     *n = v.n;
     if (v.n > cap || (v.n > 0 && (!id || !y))) return mp_fail(net, SPH_ERR_CAPACITY, "need room for %d particles", v.n);
-    s = mp_forward(net, v, (float)(1.0 / u_ref), bf16 != 0);
+    const float *dev_y = net->y;
+    if (bf16) {
+        s = scratch_ensure(net, &net->fast, net->cap, net->device);
+        if (!s) s = mp_fast(net, v, (float)(1.0 / u_ref), net->fast);
+        if (!s) dev_y = reinterpret_cast<const float *>(net->fast->s.y);
+    } else {
+        s = mp_forward(net, v, (float)(1.0 / u_ref));
+    }
     if (s) return s;
     if (v.n > 0) {
-        MCK(net, cudaMemcpyAsync(y, net->y, (size_t)v.n * 8, cudaMemcpyDeviceToHost, v.stream), "outputs");
+        MCK(net, cudaMemcpyAsync(y, dev_y, (size_t)v.n * 8, cudaMemcpyDeviceToHost, v.stream), "outputs");
         MCK(net, cudaMemcpyAsync(id, v.id, (size_t)v.n * 4, cudaMemcpyDeviceToHost, v.stream), "ids");
     }
     MCK(net, cudaStreamSynchronize(v.stream), "synchronize");
@@ -903,7 +782,7 @@ sph_status sph_mpnn_backward(sph_mpnn *net, sph_ctx *ctx, double u_ref, const fl
     if (s) return s;
     if (n != v.n || (n > 0 && !target)) return mp_fail(net, SPH_ERR_ARG, "target must hold %d rows", v.n);
     float inv = (float)(1.0 / u_ref);
-    s = mp_forward(net, v, inv, false);
+    s = mp_forward(net, v, inv);
     if (s) return s;
     cudaStream_t st = v.stream;
     MCK(net, cudaMemsetAsync(net->loss, 0, sizeof(double), st), "clear loss");
@@ -930,7 +809,7 @@ sph_status sph_mpnn_adam(sph_mpnn *net, double lr) {
     MCK(net, cudaSetDevice(net->device), "cudaSetDevice");
     k_adam<<<nblk(kMP.total, 256), 256, 0, net->stream>>>(kMP.total, net->param, net->grad, net->am,
                                                           net->av, b1, b2, a1, a2, 1e-8f);
-    net->bf_stale = true;
+    net->img_stale = true;
     MCK(net, cudaGetLastError(), "adam");
     return SPH_OK;
 }

@@ -1242,13 +1242,48 @@ void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State
 // corrector.  Writes raw in the cell order of the evaluation and sets the
 // step length for the time advance that follows.
 // ---------------------------------------------------------------------------
+// Mass-weighted sums of the network's output over the fluid particles of the
+// step start: ym[0..1] = sum m y, ym[2] = sum m (FP64).  The correction
+// a_ref (y - ybar), ybar = ym[0..1] / ym[2], then changes the fluid's
+// momentum by nothing: the pair forces that make up most of the k-step
+// correction cancel in the sum (Eqs. 9, 10 are antisymmetric in a, b).
+__global__ void k_surrogate_mean(int n, const uint8_t *__restrict__ type,
+                                 const float *__restrict__ mass, const float2 *__restrict__ y,
+                                 double *__restrict__ ym) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (i < n && type[i] == T_FLUID) {
+        double m = (double)mass[i];
+        v[0] = m * y[i].x;
+        v[1] = m * y[i].y;
+        v[2] = m;
+    }
+    for (int k = 0; k < 3; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&ym[k], x);
+    }
+}
+
+void launch_surrogate_mean(int n, const uint8_t *type, const float *mass, const float2 *y,
+                           double *ym, int cap, cudaStream_t s) {
+    launch_k(k_surrogate_mean, (cap + 255) / 256, 256, s, n, type, mass, y, ym);
+}
+
+__device__ __forceinline__ float2 mean_of(const double *__restrict__ ym) {
+    double w = ym[2];
+    return w > 0.0 ? make_float2((float)(ym[0] / w), (float)(ym[1] / w)) : make_float2(0.f, 0.f);
+}
+
 __global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *__restrict__ sc,
                                    State<float> srt, State<float> raw,
                                    const float2 *__restrict__ a_n, const float2 *__restrict__ y,
-                                   float a_ref, const float *__restrict__ dr, double dT) {
+                                   const double *__restrict__ ym, float a_ref,
+                                   const float *__restrict__ dr, double dT) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) sc->dt = dT;
     if (i >= sc->nsrt) return;
+    const float2 yb = mean_of(ym);
     double t = sc->t, half = 0.5 * dT;
     double2 p0 = srt.pos[i];
     float2 v0 = srt.vel[i];
@@ -1260,7 +1295,7 @@ __global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *
     float2 ds = srt.disp[i];
     if (typ == T_FLUID) {
         float tdt = (float)dT;
-        float ax = a_n[i].x + a_ref * y[i].x, ay = a_n[i].y + a_ref * y[i].y;
+        float ax = a_n[i].x + a_ref * (y[i].x - yb.x), ay = a_n[i].y + a_ref * (y[i].y - yb.y);
         float uhx = v0.x + 0.5f * tdt * ax, uhy = v0.y + 0.5f * tdt * ay;
         p1 = make_double2(p0.x + dT * (P.ufx_d + (double)uhx), p0.y + dT * (P.ufy_d + (double)uhy));
         v1 = make_float2(v0.x + tdt * ax, v0.y + tdt * ay);
@@ -1309,10 +1344,10 @@ __global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *
 
 void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Grid &g, Scalars *sc,
                              const State<float> &srt, const State<float> &raw, const float2 *a_n,
-                             const float2 *y, float a_ref, const float *dr, double dT, int cap,
-                             cudaStream_t s) {
-    launch_k(k_surrogate_update, (cap + 255) / 256, 256, s, P, inf, g, sc, srt, raw, a_n, y, a_ref,
-             dr, dT);
+                             const float2 *y, const double *ym, float a_ref, const float *dr,
+                             double dT, int cap, cudaStream_t s) {
+    launch_k(k_surrogate_update, (cap + 255) / 256, 256, s, P, inf, g, sc, srt, raw, a_n, y, ym,
+             a_ref, dr, dT);
 }
 
 // Residual sums of a surrogate step over the fluid particles present at both
@@ -1323,20 +1358,22 @@ void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Gri
 //   sums[4]    = fluid count
 //   sums[5]    = sum |abar - (a_n + a_k)/2|^2      (acceleration field)
 //   sums[6]    = sum |(a_n + a_k)/2|^2
-// with abar = a_n + a_ref y.
+// with abar = a_n + a_ref (y - ybar) (k_surrogate_mean).
 __global__ void k_surrogate_residual(int n, const uint8_t *__restrict__ type,
                                      const float *__restrict__ mass,
-                                     const float2 *__restrict__ y, float a_ref,
+                                     const float2 *__restrict__ y, const double *__restrict__ ym,
+                                     float a_ref,
                                      const float2 *__restrict__ a_n, const float2 *__restrict__ a_k,
                                      const float *__restrict__ dr_n, const float *__restrict__ dr_k,
                                      double *__restrict__ sums) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const float2 yb = mean_of(ym);
     if (i < n && type[i] == T_FLUID) {
         double m = (double)mass[i];
         double mx = 0.5 * ((double)a_n[i].x + a_k[i].x), my = 0.5 * ((double)a_n[i].y + a_k[i].y);
-        double ex = (double)a_n[i].x + (double)a_ref * y[i].x - mx;
-        double ey = (double)a_n[i].y + (double)a_ref * y[i].y - my;
+        double ex = (double)a_n[i].x + (double)a_ref * (y[i].x - yb.x) - mx;
+        double ey = (double)a_n[i].y + (double)a_ref * (y[i].y - yb.y) - my;
         double dd = (double)dr_k[i] - dr_n[i];
         v[0] = m * ex;
         v[1] = m * ey;
@@ -1354,10 +1391,11 @@ __global__ void k_surrogate_residual(int n, const uint8_t *__restrict__ type,
 }
 
 void launch_surrogate_residual(int n, const uint8_t *type, const float *mass, const float2 *abar,
-                               float a_ref, const float2 *a_n, const float2 *a_k, const float *dr_n,
-                               const float *dr_k, double *sums, int cap, cudaStream_t s) {
-    launch_k(k_surrogate_residual, (cap + 255) / 256, 256, s, n, type, mass, abar, a_ref, a_n, a_k,
-             dr_n, dr_k, sums);
+                               const double *ym, float a_ref, const float2 *a_n, const float2 *a_k,
+                               const float *dr_n, const float *dr_k, double *sums, int cap,
+                               cudaStream_t s) {
+    launch_k(k_surrogate_residual, (cap + 255) / 256, 256, s, n, type, mass, abar, ym, a_ref, a_n,
+             a_k, dr_n, dr_k, sums);
 }
 
 // ---------------------------------------------------------------------------

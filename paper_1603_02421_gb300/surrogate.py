@@ -6,8 +6,9 @@ predict there: the correction y* = (abar - a_n) / a_ref, where abar =
 (u_{n+k} - u_n) / (t_{n+k} - t_n) is the mean acceleration of a particle over
 the next k plain steps and a_n its SPH acceleration at s_n (Eq. 25).  Only
 fluid particles present at both ends carry a target; the others get y* = 0.
-The surrogate step then advances with abar = a_n + a_ref y (plain SPH judges
-it and takes over when its residuals exceed the threshold).
+The surrogate step then advances with abar = a_n + a_ref (y - ybar), ybar
+the mass-weighted mean of y over the fluid (plain SPH judges it and takes
+over when its residuals exceed the threshold).
 
 Everything runs through the C ABI of libsph (binding.py); nothing here
 computes SPH or network arithmetic itself.
@@ -182,17 +183,24 @@ class Trainer:
 
     def prediction_errors(self, data, a_ref, bf16=True):
         """Relative L2 errors, over the valid particles of all samples, of the
-        predicted mean acceleration a_n + a_ref y against the true k-step
-        mean, and of a_n alone (the method without the network)."""
+        predicted mean acceleration a_n + a_ref (y - ybar) against the true
+        k-step mean, and of a_n alone (the method without the network); ybar
+        is the mass-weighted mean of y over the fluid, which the surrogate
+        step removes (sph_surrogate_step)."""
         num_net = num_zero = den = 0.0
         for ci, smp in data:
             sim = self._load(ci, smp)
             ids, y = binding.sph_mpnn_forward(self.net.net, sim.ctx, self.u_ref, bf16,
                                               self.capacity)
             pos = np.searchsorted(smp["state"]["id"], ids)
+            y = y.astype(np.float64)
+            fl = smp["state"]["type"][pos] == binding.FLUID
+            m = smp["state"]["m"][pos][fl]
+            if m.sum() > 0:
+                y = y - (m[:, None] * y[fl]).sum(0) / m.sum()
             v = smp["valid"][pos]
             corr = smp["corr"][pos][v]
-            pred = a_ref * y.astype(np.float64)[v]
+            pred = a_ref * y[v]
             num_net += float(np.sum((pred - corr) ** 2))
             num_zero += float(np.sum(corr ** 2))
             den += float(np.sum(smp["abar"][pos][v] ** 2))

@@ -196,8 +196,12 @@ def test_accepted_surrogate_step_applies_the_prediction(sph):
     assert abs(dT - k * dt) < 0.05 * k * dt
     yb = np.zeros_like(y, dtype=np.float64)
     yb[ids] = y
-    ax = before["ax"] + a_ref * yb[:, 0]       # a_n + the network's correction
-    ay = before["ay"] + a_ref * yb[:, 1]
+    # the correction less its mass-weighted mean over the fluid
+    fl = before["type"] == sph.FLUID
+    ym = (before["m"][fl, None] * yb[fl]).sum(0) / before["m"][fl].sum()
+    assert np.abs(ym).max() > 1e-3            # the removal is seen
+    ax = before["ax"] + a_ref * (yb[:, 0] - ym[0])   # a_n + the network's correction
+    ay = before["ay"] + a_ref * (yb[:, 1] - ym[1])
     u1 = before["u"] + dT * ax
     v1 = before["v"] + dT * ay
     x1 = before["x"] + dT * (before["u"] + 0.5 * dT * ax)

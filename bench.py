@@ -931,25 +931,31 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
     clocks = ClockSampler(local)
     accepted = steps = 0
     rms, rds, rfs = [], [], []
+    ctxs = [sm.ctx for sm in sims]
+    builds0 = sum(binding.sph_get_rebuild_stats(c)[0] for c in ctxs)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for sm in sims:
-        for _ in range(K // SUR_K):
-            ok, rm, rd, rf = binding.sph_surrogate_step(sm.ctx, net.net, SUR_K, 1.0, a_ref,
-                                                        args.threshold, True, field=True)
-            accepted += int(ok)
-            steps += 1
-            rms.append(rm)
-            rds.append(rd)
-            rfs.append(rf)
+    for _ in range(K // SUR_K):
+        ok, rm, rd, rf = binding.sph_surrogate_batch(ctxs, net.net, SUR_K, 1.0, a_ref,
+                                                     args.threshold, True)
+        accepted += int(ok.sum())
+        steps += len(ctxs)
+        rms.extend(rm.tolist())
+        rds.extend(rd.tolist())
+        rfs.extend(rf.tolist())
     torch.cuda.synchronize(dev)
     sur_s = time.perf_counter() - t0
+    fresh_starts = sum(binding.sph_get_rebuild_stats(c)[0] for c in ctxs) - builds0
     clk = clocks.stop()
     L_sur = [binding.sph_breakup_length(sm.ctx)[0] for sm in sims]
     t_sur = [sm.time()["t"] - t0_ for sm, t0_ in zip(sims, t_sur0)]
     value, total_s, _ = reduce_rate(sur_s, n0 * K, dist, dev)
     per_full = binding.sph_kernel_counts(sims[0].ctx)[0]
-    launches = steps * 27 + (steps - accepted) * SUR_K * per_full
+    # a surrogate step launches 13 kernels when it starts from the last
+    # evaluation (network 5, mean, update, spawn, refresh, 3 SPH sweeps,
+    # residual), 9 more (sort 5, lists, 3 sweeps) when it starts afresh; a
+    # rejected one adds k plain steps (whose rebuilds are counted as starts)
+    launches = steps * 13 + fresh_starts * 9 + (steps - accepted) * SUR_K * per_full
 
     # ---- end to end: host state in, surrogate steps, host state out -------
     Ke = 5
@@ -959,8 +965,9 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
     t0 = time.perf_counter()
     for sm, st in zip(sims, pinned):
         binding.sph_set_state(sm.ctx, st)
-        for _ in range(Ke):
-            binding.sph_surrogate_step(sm.ctx, net.net, SUR_K, 1.0, a_ref, args.threshold, True)
+    for _ in range(Ke):
+        binding.sph_surrogate_batch(ctxs, net.net, SUR_K, 1.0, a_ref, args.threshold, True)
+    for sm in sims:
         binding.sph_get_state(sm.ctx)
     e2e_s = time.perf_counter() - t0
     e2e_value, _, _ = reduce_rate(e2e_s, n0 * Ke * SUR_K, dist, dev)
@@ -992,6 +999,7 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
                        "members_per_gpu": len(sims), "particles_total": n0,
                        "k_substeps": SUR_K, "threshold": args.threshold,
                        "surrogate_steps": steps, "accepted": accepted,
+                       "fresh_starts": fresh_starts,
                        "acceptance_rate": accepted / max(steps, 1),
                        "residual_median": {
                            "momentum": float(np.median(rms)) if rms else None,
@@ -1022,8 +1030,9 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / (Ke * SUR_K),
                     "d2h_bytes_per_step": d2h / (Ke * SUR_K),
-                    "how": "per member: sph_set_state from pinned host arrays, %d surrogate "
-                           "steps of %d substeps, sph_get_state; host wall clock" % (Ke, SUR_K)},
+                    "how": "sph_set_state of every member from pinned host arrays, %d batched "
+                           "surrogate steps of %d substeps, sph_get_state of every member; host "
+                           "wall clock" % (Ke, SUR_K)},
             "gpu_launches": launches,
             "clocks": clk,
         }

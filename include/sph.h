@@ -496,7 +496,7 @@ sph_status sph_mpnn_adam(sph_mpnn *net, double lr);
  *      step; inflow layers, time advance for dT and the device's rebuild
  *      decision (cadence counted in surrogate steps, displacements);
  *   4. evaluate SPH at the new state (same cell order and lists) and form,
- *      over the fluid particles, the momentum balance residual
+ *      over the particles fluid at both ends, the momentum balance residual
  *      r_m = |sum m (abar - (a_n + a_k)/2)| / sum m |(a_n + a_k)/2| (the
  *      step's momentum change against the trapezoidal impulse of the SPH
  *      forces at its ends), the density residual
@@ -512,6 +512,20 @@ sph_status sph_mpnn_adam(sph_mpnn *net, double lr);
 sph_status sph_surrogate_step(sph_ctx *ctx, sph_mpnn *net, int k, double u_ref, double a_ref,
                               double threshold, int bf16, int *accepted, double *res_momentum,
                               double *res_density, double *res_field);
+
+/* sph_surrogate_step on m contexts at once (an ensemble of jets): every
+ * context's work is enqueued on its own stream before the host waits, so the
+ * batch pays one round of host synchronisations (two when some context
+ * cannot reuse its last evaluation), not m.  accepted, res_momentum,
+ * res_density and res_field are arrays of m (each nullable); the contexts
+ * may share a stream; all use the one network (read-only here).  On an
+ * error *bad_member (nullable) names the context that failed; the contexts
+ * before it have completed their step, those after it may have a step in
+ * progress (call sph_sync on each before using them). */
+sph_status sph_surrogate_batch(sph_ctx *const *ctx, int m, sph_mpnn *net, int k, double u_ref,
+                               double a_ref, double threshold, int bf16, int *accepted,
+                               double *res_momentum, double *res_density, double *res_field,
+                               int *bad_member);
 
 #ifdef __cplusplus
 }

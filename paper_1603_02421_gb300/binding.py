@@ -119,6 +119,10 @@ _SIGS = {
     "sph_surrogate_step": ([_CTX, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                             ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D,
                             _D], ctypes.c_int),
+    "sph_surrogate_batch": ([ctypes.POINTER(_CTX), ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_int), _D, _D, _D,
+                             ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sph_run_async": ([_CTX, ctypes.c_longlong], ctypes.c_int),
     "sph_set_tuning": ([_CTX, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sph_set_start_form": ([_CTX, ctypes.c_int], ctypes.c_int),
@@ -687,6 +691,25 @@ def sph_mpnn_backward(net, ctx, u_ref, target):
 
 def sph_mpnn_adam(net, lr):
     _mp_check(net, lib().sph_mpnn_adam(net, float(lr)))
+
+
+def sph_surrogate_batch(ctxs, net, k, u_ref, a_ref, threshold, bf16=True):
+    """One surrogate step on each context of the list, sharing the host
+    synchronisations; returns (accepted, momentum, density, field residuals)
+    as numpy arrays of len(ctxs)."""
+    m = len(ctxs)
+    arr = (_CTX * max(m, 1))(*ctxs)
+    acc = (ctypes.c_int * max(m, 1))()
+    rm, rd, rf = (np.zeros(max(m, 1)) for _ in range(3))
+    bad = ctypes.c_int(-1)
+    st = lib().sph_surrogate_batch(arr, m, net, int(k), float(u_ref), float(a_ref),
+                                   float(threshold), int(bool(bf16)), acc, _d(rm), _d(rd), _d(rf),
+                                   ctypes.byref(bad))
+    if st != SPH_OK:
+        i = bad.value
+        msg = lib().sph_last_error(ctxs[i]).decode(errors="replace") if 0 <= i < m else ""
+        raise SphError(st, "member %d: %s" % (i, msg))
+    return (np.array([bool(acc[i]) for i in range(m)]), rm[:m], rd[:m], rf[:m])
 
 
 def sph_surrogate_step(ctx, net, k, u_ref, a_ref, threshold, bf16=True, field=False):

@@ -79,8 +79,11 @@ struct sph_ctx {
     unsigned long long graph_gen = 0;   // counts changes that invalidate captured steps
     // learned-surrogate step scratch: SPH accelerations and density rates at
     // the step start, residual sums, saved particle count
-    void *sg_an = nullptr, *sg_drn = nullptr, *sg_sums = nullptr;
+    void *sg_an = nullptr, *sg_drn = nullptr, *sg_sums = nullptr, *sg_t0 = nullptr;
     MpScratchHandle *sg_net = nullptr;   // the network's inference scratch
+    double *sg_hsum = nullptr;           // pinned host copy of the residual sums
+    bool sg_reuse = false;               // this step starts from the last evaluation
+    double sg_dT = 0.0;                  // this step's span
     // the evaluation ending the last accepted surrogate step can start the
     // next one while the cell-build and step counters are those recorded
     bool sg_ready = false;
@@ -762,6 +765,7 @@ void sph_destroy(sph_ctx *c) {
     }
     for (auto p : c->snap) if (p) cudaFree(p);
     mpnn_scratch_free(c->sg_net);
+    if (c->sg_hsum) cudaFreeHost(c->sg_hsum);
     if (c->cexec) cudaGraphExecDestroy(c->cexec);
     if (c->cgraph) cudaGraphDestroy(c->cgraph);
     for (auto &b : c->allocs) cudaFree(b.p);
@@ -914,6 +918,7 @@ sph_status sph_step(sph_ctx *c, double *dt_used) {
 sph_status sph_evaluate(sph_ctx *c) {
     if (!c) return SPH_ERR_ARG;
     c->force_full = true;
+    c->sg_ready = false;
     if (c->tsz == 4) enqueue_evaluate<float>(c); else enqueue_evaluate<double>(c);
     sph_status s = after_work(c, "evaluate");
     c->n_eval = c->hsc->nsrt;
@@ -1018,6 +1023,7 @@ static sph_status ensure_graph(sph_ctx *c) {
 }
 
 static sph_status launch_step_graph(sph_ctx *c) {
+    c->sg_ready = false;
     if (c->prof || c->cadence <= 1) {
         // host-chosen graphs: while profiling, and for cadence 1, where every
         // step rebuilds and the gated reuse kernels would only add overhead
@@ -1554,12 +1560,16 @@ sph_status sph_get_start_form(sph_ctx *c, int *form) {
 }
 
 // Copies of the raw state and scalars, to run trial steps and come back.
-static sph_status snapshot(sph_ctx *c, bool restore) {
+static sph_status snapshot(sph_ctx *c, bool restore, bool scalars_current = false) {
     size_t ts = c->tsz;
     size_t sizes[8] = {16, 2 * ts, ts, ts, ts, 1, 4, 2 * ts};
     if (!restore) {
-        sph_status s = pull_scalars(c);
-        if (s) return s;
+        // the copies are ordered on the context's stream; with the host
+        // scalars already current (scalars_current) nothing waits here
+        if (!scalars_current) {
+            sph_status s = pull_scalars(c);
+            if (s) return s;
+        }
         size_t n = (size_t)c->hsc->n;
         if (n > c->snap_n || !c->snap[0]) {
             for (auto &p : c->snap) if (p) { cudaFree(p); p = nullptr; }
@@ -1571,7 +1581,7 @@ static sph_status snapshot(sph_ctx *c, bool restore) {
             CK(cudaMemcpyAsync(c->snap[k], c->raw[k], n * sizes[k], cudaMemcpyDeviceToDevice,
                                c->stream), "snapshot");
         c->snap_sc = *c->hsc;
-        CK(cudaStreamSynchronize(c->stream), "snapshot");
+        if (!scalars_current) CK(cudaStreamSynchronize(c->stream), "snapshot");
         return SPH_OK;
     }
     size_t n = (size_t)c->snap_sc.n;
@@ -1729,21 +1739,53 @@ void ctx_view(sph_ctx *c, CtxView *v) {
 extern "C" {
 
 // ---------------------------------------------------------------------------
-// Learned-surrogate step
+// Learned-surrogate step, in three stages so that a batch of contexts shares
+// its host synchronisations: begin (checks, reuse decision, snapshot, and the
+// start evaluation when the last one cannot be reused), enqueue (prediction,
+// update, end evaluation, residual sums, copies to the host), decide (after
+// the stream synchronised: accept, or restore and enqueue k plain steps).
 // ---------------------------------------------------------------------------
-sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, double a_ref,
-                              double threshold, int bf16, int *accepted, double *res_momentum,
-                              double *res_density, double *res_field) {
-    if (!c) return SPH_ERR_ARG;
-    if (accepted) *accepted = 0;
-    if (!net) return fail(c, SPH_ERR_ARG, "network is NULL");
+}  // extern "C"
+
+namespace {
+
+struct SgArgs {
+    sph_mpnn *net;
+    int k;
+    double u_ref, a_ref, threshold;
+    int bf16;
+};
+
+sph_status sg_check(sph_ctx *c, const SgArgs &g) {
+    if (!g.net) return fail(c, SPH_ERR_ARG, "network is NULL");
     if (c->tsz != 4) return fail(c, SPH_ERR_ARG, "the surrogate step needs an FP32 context");
     if (c->prm.density != SPH_DENSITY_CONTINUITY)
         return fail(c, SPH_ERR_ARG, "the surrogate step needs the continuity density (Eq. 7)");
-    if (k < 1 || k > 64) return fail(c, SPH_ERR_ARG, "k must lie in [1, 64]");
-    if (!(u_ref > 0) || !(a_ref > 0) || !(threshold > 0))
+    if (g.k < 1 || g.k > 64) return fail(c, SPH_ERR_ARG, "k must lie in [1, 64]");
+    if (!(g.u_ref > 0) || !(g.a_ref > 0) || !(g.threshold > 0))
         return fail(c, SPH_ERR_ARG, "u_ref, a_ref and threshold must be > 0");
-    sph_status s = pull_scalars(c);
+    return SPH_OK;
+}
+
+// The scalars copied to the host by an enqueued copy, once the stream has
+// synchronised: the context's error word decides the status.
+sph_status sg_scalars_arrived(sph_ctx *c, const char *what) {
+    CK(cudaStreamSynchronize(c->stream), what);
+    CK(cudaGetLastError(), what);
+    c->hsc_fresh = true;
+    collect_profile(c);
+    return status_from_err(c, c->hsc->err);
+}
+
+// Stage 1.  *pull: the start evaluation was enqueued with a copy of the
+// scalars, which must arrive (sg_scalars_arrived) before stage 2.
+sph_status sg_begin(sph_ctx *c, const SgArgs &g, bool *pull) {
+    *pull = false;
+    sph_status s = sg_check(c, g);
+    if (s) return s;
+    // the host scalars are current after the synchronising end of an
+    // accepted surrogate step that nothing has followed (sg_ready)
+    s = c->sg_ready ? SPH_OK : pull_scalars(c);
     if (s) return s;
     s = status_from_err(c, c->hsc->err);
     if (s) return s;
@@ -1752,44 +1794,39 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
         c->sg_an = dalloc(c, (size_t)c->cap * sizeof(float2), e);
         if (!e) c->sg_drn = dalloc(c, (size_t)c->cap * sizeof(float), e);
         if (!e) c->sg_sums = dalloc(c, 12 * sizeof(double), e);
+        if (!e) c->sg_t0 = dalloc(c, (size_t)c->cap, e);
+        if (!e) e = cudaMallocHost(&c->sg_hsum, 8 * sizeof(double));
         CK(e, "surrogate scratch");
     }
     // the evaluation that ended the last accepted surrogate step is this
     // step's start when nothing has touched the state since (no step, cell
     // build or state change: same counters) and its time advance kept the
     // lists (device rebuild decision)
-    const bool reuse = c->sg_ready && c->sg_builds == c->hsc->builds &&
-                       c->sg_step == c->hsc->step && !c->hsc->need_full;
+    c->sg_reuse = c->sg_ready && c->sg_builds == c->hsc->builds && c->sg_step == c->hsc->step &&
+                  !c->hsc->need_full;
     c->sg_ready = false;
-    s = snapshot(c, false);
+    s = snapshot(c, false, true);
     if (s) return s;
-    auto report = [&](double rm, double rd, double rf) {
-        if (res_momentum) *res_momentum = rm;
-        if (res_density) *res_density = rd;
-        if (res_field) *res_field = rf;
-    };
-    auto reject = [&](double rm, double rd, double rf) -> sph_status {
-        sph_status r = snapshot(c, true);
-        if (r) return r;
-        r = sph_run_async(c, k);
-        if (!r) r = sph_sync(c);
-        report(rm, rd, rf);
-        return r;
-    };
-    State<float> raw = state_of<float>(c->raw), srt = state_of<float>(c->srt);
-    if (!reuse) {
+    if (!c->sg_reuse) {
         // SPH at the step start on fresh lists, with the time-step
         // candidates of Eqs. 30-31; the network reads every particle's
         // normal, so none is skipped
         const uint32_t *key = enqueue_sort<float>(c);
         enqueue_build<float>(c, key);
         enqueue_eval<float>(c, hot_n<float>(c), 1, false);
-        s = after_work(c, "surrogate: evaluation at the start");
-        if (s) return s;
+        CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream),
+           "copy scalars");
+        *pull = true;
     }
+    return SPH_OK;
+}
+
+// Stage 2 (host scalars current).
+sph_status sg_enqueue(sph_ctx *c, const SgArgs &g) {
     c->n_eval = c->hsc->nsrt;
     c->csf_valid = true;
     const int n = c->hsc->nsrt;
+    State<float> raw = state_of<float>(c->raw), srt = state_of<float>(c->srt);
     // Eq. 32: the plain step's dt at this state; the surrogate step spans k
     double dt = c->prm.dt_fixed;
     if (!(dt > 0)) {
@@ -1805,20 +1842,23 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
         }
         dt = c->prm.courant * (double)m;
     }
-    const double dT = k * dt;
-    CK(cudaMemcpyAsync(c->sg_an, c->acc, (size_t)n * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream), "copy");
-    CK(cudaMemcpyAsync(c->sg_drn, c->dr, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    const double dT = g.k * dt;
+    c->sg_dT = dT;
+    CK(cudaMemcpyAsync(c->sg_an, c->acc, (size_t)n * sizeof(float2), cudaMemcpyDeviceToDevice,
+                       c->stream), "copy");
+    CK(cudaMemcpyAsync(c->sg_drn, c->dr, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice,
+                       c->stream), "copy");
     // prediction and update; the time advance lays inflow layers and decides
     // (cadence and displacements) whether the next step rebuilds the lists
     const float2 *abar = nullptr;
-    s = mpnn_predict(net, c, u_ref, bf16 != 0, &abar, &c->sg_net);
-    if (s) return fail(c, s, "surrogate: %s", sph_mpnn_last_error(net));
+    sph_status s = mpnn_predict(g.net, c, g.u_ref, g.bf16 != 0, &abar, &c->sg_net);
+    if (s) return fail(c, s, "surrogate: %s", sph_mpnn_last_error(g.net));
     double *ym = (double *)c->sg_sums + 8;
     CK(cudaMemsetAsync(c->sg_sums, 0, 12 * sizeof(double), c->stream), "clear");
     launch_surrogate_mean(n, srt.type, srt.mass, abar, ym, c->cap, c->stream);
     launch_surrogate_update(c->Pf, c->inf, c->grid, c->sc, srt, raw, (const float2 *)c->sg_an,
-                            abar, ym, (float)a_ref, (const float *)c->sg_drn, dT, c->cap,
-                            c->stream);
+                            abar, ym, (float)g.a_ref, (const float *)c->sg_drn, dT,
+                            (uint8_t *)c->sg_t0, c->cap, c->stream);
     launch_spawn<float>(c->Pf, c->inf, c->sc, raw, c->layer_y, c->cap, c->cadence, c->stream);
     // SPH at the end, on the cell order and lists of the start (exact while
     // no particle moved more than skin/2, which the refresh checks), with the
@@ -1827,27 +1867,120 @@ sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, do
                           c->stream);
     enqueue_cells<float>(c, false);
     enqueue_eval<float>(c, hot_n<float>(c), 1, false);
-    launch_surrogate_residual(n, srt.type, srt.mass, abar, ym, (float)a_ref, (const float2 *)c->sg_an,
-                              (const float2 *)c->acc, (const float *)c->sg_drn,
-                              (const float *)c->dr, (double *)c->sg_sums, c->cap, c->stream);
-    double sums[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    CK(cudaMemcpyAsync(sums, c->sg_sums, sizeof sums, cudaMemcpyDeviceToHost, c->stream), "residual");
-    s = after_work(c, "surrogate: evaluation at the end");
-    double rm = sums[2] > 0 ? std::sqrt(sums[0] * sums[0] + sums[1] * sums[1]) / sums[2] : 0.0;
-    double rd = sums[4] > 0 ? 0.5 * dT * std::sqrt(sums[3] / sums[4]) / c->prm.rho0 : 0.0;
-    double rf = sums[6] > 0 ? std::sqrt(sums[5] / sums[6]) : 0.0;
-    if (s == SPH_ERR_SKIN) return reject(rm, rd, rf);   // moved too far for the lists: plain steps
-    if (s) return s;
-    if (!(rm <= threshold && rd <= threshold)) return reject(rm, rd, rf);
+    launch_surrogate_residual(n, (const uint8_t *)c->sg_t0, srt.type, srt.mass, abar, ym,
+                              (float)g.a_ref,
+                              (const float2 *)c->sg_an, (const float2 *)c->acc,
+                              (const float *)c->sg_drn, (const float *)c->dr,
+                              (double *)c->sg_sums, c->cap, c->stream);
+    CK(cudaMemcpyAsync(c->sg_hsum, c->sg_sums, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream), "residual");
+    CK(cudaMemcpyAsync(c->hsc, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream),
+       "copy scalars");
+    CK(cudaGetLastError(), "surrogate launch");
+    return SPH_OK;
+}
+
+// Stage 3 (after sg_scalars_arrived gave s): res = (r_m, r_rho, r_a);
+// *replay: the step was rejected and k plain steps are enqueued (the caller
+// synchronises with sph_sync).
+sph_status sg_decide(sph_ctx *c, const SgArgs &g, sph_status s, int *accepted, double res[3],
+                     bool *replay) {
+    *replay = false;
+    *accepted = 0;
+    const double *sums = c->sg_hsum;
+    const double dT = c->sg_dT;
+    res[0] = sums[2] > 0 ? std::sqrt(sums[0] * sums[0] + sums[1] * sums[1]) / sums[2] : 0.0;
+    res[1] = sums[4] > 0 ? 0.5 * dT * std::sqrt(sums[3] / sums[4]) / c->prm.rho0 : 0.0;
+    res[2] = sums[6] > 0 ? std::sqrt(sums[5] / sums[6]) : 0.0;
+    if (s && s != SPH_ERR_SKIN) return s;
+    if (s == SPH_ERR_SKIN || !(res[0] <= g.threshold && res[1] <= g.threshold)) {
+        // moved too far for the lists, or judged off: plain steps instead
+        sph_status r = snapshot(c, true);
+        if (!r) r = sph_run_async(c, g.k);
+        *replay = r == SPH_OK;
+        return r;
+    }
     // plain steps after this one rebuild first; a next surrogate step may
     // start from the evaluation just done
     c->force_full = true;
     c->sg_ready = true;
     c->sg_builds = c->hsc->builds;
     c->sg_step = c->hsc->step;
-    if (accepted) *accepted = 1;
-    report(rm, rd, rf);
+    *accepted = 1;
     return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sph_status sph_surrogate_batch(sph_ctx *const *ctx, int m, sph_mpnn *net, int k, double u_ref,
+                               double a_ref, double threshold, int bf16, int *accepted,
+                               double *res_momentum, double *res_density, double *res_field,
+                               int *bad_member) {
+    if (bad_member) *bad_member = -1;
+    if (m < 0 || (m > 0 && !ctx)) return SPH_ERR_ARG;
+    for (int i = 0; i < m; ++i)
+        if (!ctx[i]) {
+            if (bad_member) *bad_member = i;
+            return SPH_ERR_ARG;
+        }
+    const SgArgs g{net, k, u_ref, a_ref, threshold, bf16};
+    auto bad = [&](int i, sph_status s) {
+        if (bad_member) *bad_member = i;
+        return s;
+    };
+    std::vector<char> pull(m, 0), replay(m, 0);
+    for (int i = 0; i < m; ++i) {
+        if (accepted) accepted[i] = 0;
+        bool p = false;
+        sph_status s = sg_begin(ctx[i], g, &p);
+        if (s) return bad(i, s);
+        pull[i] = p;
+    }
+    for (int i = 0; i < m; ++i) {
+        if (!pull[i]) continue;
+        sph_status s = sg_scalars_arrived(ctx[i], "surrogate: evaluation at the start");
+        if (s) return bad(i, s);
+    }
+    for (int i = 0; i < m; ++i) {
+        sph_status s = sg_enqueue(ctx[i], g);
+        if (s) return bad(i, s);
+    }
+    for (int i = 0; i < m; ++i) {
+        sph_status s = sg_scalars_arrived(ctx[i], "surrogate: evaluation at the end");
+        int acc = 0;
+        double res[3];
+        bool rp = false;
+        s = sg_decide(ctx[i], g, s, &acc, res, &rp);
+        if (s) return bad(i, s);
+        replay[i] = rp;
+        if (accepted) accepted[i] = acc;
+        if (res_momentum) res_momentum[i] = res[0];
+        if (res_density) res_density[i] = res[1];
+        if (res_field) res_field[i] = res[2];
+    }
+    for (int i = 0; i < m; ++i) {
+        if (!replay[i]) continue;
+        sph_status s = sph_sync(ctx[i]);
+        if (s) return bad(i, s);
+    }
+    return SPH_OK;
+}
+
+sph_status sph_surrogate_step(sph_ctx *c, sph_mpnn *net, int k, double u_ref, double a_ref,
+                              double threshold, int bf16, int *accepted, double *res_momentum,
+                              double *res_density, double *res_field) {
+    if (!c) return SPH_ERR_ARG;
+    int acc = 0;
+    double rm = 0.0, rd = 0.0, rf = 0.0;
+    sph_status s = sph_surrogate_batch(&c, 1, net, k, u_ref, a_ref, threshold, bf16, &acc, &rm,
+                                       &rd, &rf, nullptr);
+    if (accepted) *accepted = acc;
+    if (res_momentum) *res_momentum = rm;
+    if (res_density) *res_density = rd;
+    if (res_field) *res_field = rf;
+    return s;
 }
 
 // ---------------------------------------------------------------------------
@@ -1954,6 +2087,7 @@ sph_status sph_ensemble_run(sph_ensemble *e, long long nsteps) {
         ECK(e, cudaEventRecord(e->ev, c->stream), "order members");
         ECK(e, cudaStreamWaitEvent(e->stream, e->ev, 0), "order members");
     }
+    for (sph_ctx *c : e->m) c->sg_ready = false;
     for (long long k = 0; k < nsteps; ++k) {
         for (sph_ctx *c : e->m) {
             if (c->force_full && c->cadence > 1)

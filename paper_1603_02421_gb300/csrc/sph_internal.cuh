@@ -343,13 +343,14 @@ void launch_surrogate_mean(int n, const uint8_t *type, const float *mass, const 
 void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Grid &g, Scalars *sc,
                              const State<float> &srt, const State<float> &raw, const float2 *a_n,
                              const float2 *y, const double *ym, float a_ref, const float *dr,
-                             double dT, int cap, cudaStream_t s);
-// Residual sums of a surrogate step (k_surrogate_residual): sums[7], zeroed by
-// the caller.
-void launch_surrogate_residual(int n, const uint8_t *type, const float *mass, const float2 *y,
-                               const double *ym, float a_ref, const float2 *a_n,
-                               const float2 *a_k, const float *dr_n, const float *dr_k,
-                               double *sums, int cap, cudaStream_t s);
+                             double dT, uint8_t *type0, int cap, cudaStream_t s);
+// Residual sums of a surrogate step (k_surrogate_residual) over the particles
+// fluid at both ends (type0: the start types the update recorded): sums[7],
+// zeroed by the caller.
+void launch_surrogate_residual(int n, const uint8_t *type0, const uint8_t *type, const float *mass,
+                               const float2 *y, const double *ym, float a_ref,
+                               const float2 *a_n, const float2 *a_k, const float *dr_n,
+                               const float *dr_k, double *sums, int cap, cudaStream_t s);
 
 // Read-only view of a context's last evaluation (for the learned surrogate):
 // records, CSF fields and neighbour lists of the current state in cell

@@ -105,7 +105,7 @@ constexpr size_t TC_PI_BYTES = (size_t)MP_P * MP_H * 2;
 // Per-pass scratch of the inference pass, capacity rows each.
 struct MpScratch {
     uint4 *edge = nullptr;          // LIST_SLOTS edge records per particle
-    unsigned *ecnt = nullptr;       // records per particle (a multiple of 4)
+    unsigned *ecnt = nullptr;       // records per particle (a multiple of 8)
     __nv_bfloat16 *h = nullptr;     // hidden state, MP_H per particle
     __nv_bfloat16 *z[2] = {};       // messages, MP_P per particle (ping-pong)
     float2 *y = nullptr;            // output
@@ -117,9 +117,9 @@ void tc_weight_images(const float *param, __nv_bfloat16 *u_img, __nv_bfloat16 *p
                       cudaStream_t s);
 
 // The inference pass over the view's n particles: y = network(state) into
-// scr.y.  Four launches (edges, input layer and first messages; the three
-// message-passing layers).  err (the context's sticky error word) receives
-// ERR_TIMEOUT if a bounded wait ran out.
+// scr.y.  Five launches: the edge records, the input layer with the first
+// messages, the three message-passing layers.  err (the context's sticky
+// error word) receives ERR_TIMEOUT if a bounded wait ran out.
 cudaError_t tc_forward(const CtxView &v, float inv_uref, const float *param,
                        const __nv_bfloat16 *u_img, const __nv_bfloat16 *pi_img,
                        const MpScratch &scr, unsigned *err);

@@ -1,23 +1,24 @@
 // Tensor-core inference pass of the learned surrogate (the network of
 // sph_mpnn.cu: node inputs, three message-passing layers, output layer).
 //
-// One persistent kernel per layer, 1024 threads and one CTA per SM, over
-// tiles of TC_M = 128 particles in cell order:
+// One persistent kernel per layer, one CTA of 25 warps per SM, over tiles of
+// TC_M = 128 particles in cell order:
 //   * the layer's weights (U_l^T, Pi_{l+1}^T as BF16 core-matrix images) are
 //     copied once per CTA into shared memory with cp.async.bulk;
 //   * per tile, the hidden state h_l arrives by TMA (cp.async.bulk.tensor,
-//     16 boxes of 128 rows x 8 columns) while the 1024 threads aggregate the
+//     16 boxes of 128 rows x 8 columns) while 16 warps aggregate the
 //     messages g_a[32k + j] = sum_b w_k,ab z_b[j] from precomputed edge
-//     records, eight threads per particle, straight into the operand tile;
+//     records, four threads per particle, straight into the operand tile;
 //   * one thread issues tcgen05.mma (kind::f16, BF16 operands, FP32
 //     accumulators in tensor memory) for [h, g] U_l^T, the warps read the
 //     accumulators back with tcgen05.ld and form h_{l+1} = h_l + relu(. +
 //     c_l), which goes to global memory and, in place, back into the operand
 //     tile; a second tcgen05.mma gives the next layer's messages z = h Pi;
 //   * the last layer forms y = h D + d in the epilogue instead.
-// The first launch builds the edge records (the four weights of every pair
-// closer than 2h, FP16, with the neighbour index), the input layer h_0 =
-// relu(x W_in + b_in) and z_0.
+// Before them, one warp per particle writes the edge records (the four
+// weights of every pair closer than 2h, FP16, with the neighbour index), and
+// the first layer launch forms the input layer h_0 = relu(x W_in + b_in) and
+// z_0.
 //
 // Operand layout in shared memory (K-major, no swizzle): a matrix of R rows
 // and K columns is stored as K/8 blocks of R x 16 bytes, block b holding
@@ -104,6 +105,10 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 __device__ __forceinline__ void fence_async_smem() {
@@ -202,28 +207,35 @@ __device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
 }
 
 // ---------------------------------------------------------------------------
-// shared-memory plan of the layer kernel (bytes from a 1024-aligned base)
+// roles and shared-memory plan of the layer kernel (bytes from a 1024-aligned
+// base).  Warps 0..15 aggregate (or, in the first layer, form h_0), warps
+// 16..23 run the epilogue (warp w reads tensor-memory lanes 32 (w % 4) ..
+// +31), warp 24 allocates tensor memory and its lane 0 issues the TMA loads
+// and the tcgen05.mma; the operand tile and the accumulators are double
+// buffered, so the aggregation of one tile overlaps the MMAs and epilogue of
+// the one before.
 // ---------------------------------------------------------------------------
-constexpr int TC_THREADS = 1024;
+constexpr int TC_AGG_WARPS = 16, TC_EPI_WARPS = 8;
+constexpr int TC_CTL_WARP = TC_AGG_WARPS + TC_EPI_WARPS;
+constexpr int TC_THREADS = 32 * (TC_CTL_WARP + 1);
 constexpr uint32_t BLK_A = TC_M * 16;                  // one 8-column block of 128 rows
 constexpr uint32_t BLK_PI = MP_P * 16;                 // one 8-column block of Pi^T (32 rows)
+constexpr uint32_t A_BYTES = (MP_CAT / 8) * BLK_A;     // one operand tile [h, g]
 constexpr uint32_t SM_BU = 0;                          // U_l^T image, 32 blocks
-constexpr uint32_t SM_A = SM_BU + (uint32_t)TC_U_BYTES;   // operand tile [h, g], 32 blocks
-constexpr uint32_t SM_BPI = SM_A + (MP_CAT / 8) * BLK_A;  // Pi^T image, 16 blocks
+constexpr uint32_t SM_A = SM_BU + (uint32_t)TC_U_BYTES;   // two operand tiles
+constexpr uint32_t SM_BPI = SM_A + 2 * A_BYTES;        // Pi^T image, 16 blocks
 constexpr uint32_t SM_PAR = SM_BPI + (uint32_t)TC_PI_BYTES;   // FP32 parameters
-constexpr uint32_t SM_Y = SM_PAR + 4096;               // output partial sums
-constexpr uint32_t SM_BAR = SM_Y + 8 * TC_M * 8;       // mbarriers and the TMEM address
-// The allocation reaches past what the plan uses so that every operand read
-// of the descriptors stays inside it even with the leading and stride
-// offsets taken the other way round (157,952 bytes at most).
-constexpr uint32_t SM_TOTAL = 163840;
+constexpr uint32_t SM_BAR = SM_PAR + 4096;             // mbarriers, then the TMEM address
+constexpr uint32_t SM_TOTAL = SM_BAR + 256;
 constexpr size_t SM_REQUEST = SM_TOTAL + 1024;         // + alignment of the base
-static_assert(SM_BAR + 64 <= SM_TOTAL, "shared-memory plan");
 static_assert(SM_REQUEST <= 227 * 1024, "shared memory per CTA");
 static_assert(TC_U_BYTES == 32 * BLK_A && TC_PI_BYTES == 16 * BLK_PI, "weight image sizes");
+static_assert(TC_AGG_WARPS * 32 == TC_M * 4, "one aggregation pass of 4 lanes per row");
 
-constexpr uint32_t TMEM_COLS = 256;    // [0, 128): U accumulator; [128, 160): messages
-constexpr uint32_t TMEM_Z = 128;
+// Tensor memory: the U accumulators of the two buffers at columns 0 and 128,
+// the message accumulators at 256 and 288.
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TMEM_Z = 256;
 
 enum TcMode { TC_FIRST = 0, TC_MID = 1, TC_LAST = 2 };
 
@@ -272,36 +284,46 @@ struct TcArgs {
     unsigned *err;
 };
 
-// Edge records of particle a (FIRST): every pair closer than 2h in list
-// order as {b, (w0, w1), (w2, w3), 0} with FP16 weights (Sec. 2-7 pairs;
-// weights of the network's edge inputs), padded with zero-weight records
-// pointing at a itself to a multiple of four.  One warp.
+// Edge records of particle a: every pair closer than 2h as {b, (w0, w1),
+// (w2, w3), 0} with FP16 weights (the pairs of Sec. 2-7; the network's edge
+// weights), padded with zero-weight records pointing at a itself to a
+// multiple of eight.  Eight lanes per particle (four particles per warp), lane
+// j taking list entries j, j + 8, ...; the records of one pass keep the list
+// order.
 template <int K>
-__device__ __forceinline__ void edge_records(const TcArgs &A, unsigned a, unsigned lane) {
-    const unsigned cnt = A.nl.cnt[a];
-    const uint32_t *__restrict__ e = A.nl.e + (size_t)a * LIST_SLOTS;
-    uint4 *__restrict__ out = A.edge + (size_t)a * LIST_SLOTS;
-    const V4f ha = A.hot.H0[a];
+__global__ void __launch_bounds__(256) k_tc_edges(PhysT<float> P, Hot<float> hot, NList nl, int n,
+                                                  float inv_uref, uint4 *__restrict__ edge,
+                                                  unsigned *__restrict__ ecnt) {
+    const unsigned lane = threadIdx.x & 31u, j = lane & 7u, gbit = lane & 24u;
+    const unsigned a = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const bool live = a < (unsigned)n;
+    const unsigned cnt = live ? nl.cnt[a] : 0u;
+    const unsigned cmax = __reduce_max_sync(0xffffffffu, cnt);
+    const uint32_t *__restrict__ e = nl.e + (size_t)(live ? a : 0u) * LIST_SLOTS;
+    uint4 *__restrict__ out = edge + (size_t)(live ? a : 0u) * LIST_SLOTS;
+    V4f ha{};
+    if (live) ha = hot.H0[a];
     unsigned outc = 0;
-    for (unsigned base = 0; base < cnt; base += 32) {
-        unsigned k = base + lane, o = 0;
+    for (unsigned base = 0; base < cmax; base += 8) {
+        unsigned k = base + j, o = 0;
         EdgeW ew{};
         bool ok = false;
         if (k < cnt) {
             float rx, ry, r2, du, dv;
-            ok = list_pair(A.P, A.hot, e, k, a, ha, o, rx, ry, r2, du, dv);
-            if (ok) ew = edge_weights<K>(A.P, rx, ry, r2, du, dv, A.hot.H1[o].x, A.inv_uref);
+            ok = list_pair(P, hot, e, k, a, ha, o, rx, ry, r2, du, dv);
+            if (ok) ew = edge_weights<K>(P, rx, ry, r2, du, dv, hot.H1[o].x, inv_uref);
         }
-        unsigned m = __ballot_sync(0xffffffffu, ok);
+        const unsigned m = (__ballot_sync(0xffffffffu, ok) >> gbit) & 0xFFu;
         if (ok) {
-            unsigned slot = outc + __popc(m & ((1u << lane) - 1u));
+            unsigned slot = outc + __popc(m & ((1u << j) - 1u));
             out[slot] = make_uint4(o, pack_h2(ew.w[0], ew.w[1]), pack_h2(ew.w[2], ew.w[3]), 0u);
         }
         outc += __popc(m);
     }
-    unsigned c4 = (outc + 3u) & ~3u;
-    if (lane < c4 - outc) out[outc + lane] = make_uint4(a, 0u, 0u, 0u);
-    if (lane == 0) A.ecnt[a] = c4;
+    if (!live) return;
+    const unsigned c8 = (outc + 7u) & ~7u;      // <= LIST_SLOTS, a multiple of 8
+    if (j < c8 - outc) out[outc + j] = make_uint4(a, 0u, 0u, 0u);
+    if (j == 0) ecnt[a] = c8;
 }
 
 // Node inputs of particle a (as k_mp_inputs): 100 (rho/rho0 - 1), N_a,
@@ -316,32 +338,59 @@ __device__ __forceinline__ void node_inputs(const TcArgs &A, unsigned a, float (
     x[3] = A.P.h * sqrtf(nv.x * nv.x + nv.y * nv.y);
 }
 
-// Messages of particle a, channels 4j .. 4j+3, all four weights:
-// acc[k][i] = sum_b w_k,ab z_b[4j + i] over the edge records.
-__device__ __forceinline__ void aggregate(const TcArgs &A, unsigned a, unsigned j,
-                                          float (&acc)[4][4]) {
-    const unsigned c4 = A.ecnt[a];
-    const uint4 *__restrict__ E = A.edge + (size_t)a * LIST_SLOTS;
-    const __nv_bfloat16 *__restrict__ z = A.zin + 4 * j;
-    for (unsigned e = 0; e < c4; e += 4) {
-        uint4 q[4];
-        uint2 zz[4];
+// Messages of row a of the tile, channels 8j .. 8j+7 (j = lane % 4), all
+// four weights: acc[k][i] = sum_b w_k,ab z_b[8j + i] over the edge records.
+// The four lanes of a row hold eight records at a time (two each; the next
+// eight load while these are used) and pass them round by shuffles; every
+// lane of the warp takes part until the longest of its eight rows is done
+// (rows past n, and rows that finished, add zero-weight records of particle
+// `self`).
+__device__ __forceinline__ void aggregate(const TcArgs &A, unsigned a, bool live, unsigned lane,
+                                          float (&acc)[4][8]) {
+    const unsigned j = lane & 3u, g0 = lane & ~3u;
+    const unsigned self = live ? a : 0u;
+    const uint4 *__restrict__ E = A.edge + (size_t)self * LIST_SLOTS;
+    // the first records load beside the count (slots past the count hold
+    // stale records and are replaced by pad below)
+    const uint4 f0 = __ldg(E + j), f1 = __ldg(E + 4 + j);
+    const unsigned c8 = live ? A.ecnt[a] : 0u;
+    const unsigned cmax = __reduce_max_sync(0xffffffffu, c8);
+    const __nv_bfloat16 *__restrict__ z = A.zin + 8 * j;
+    const uint4 pad = make_uint4(self, 0u, 0u, 0u);
+    uint4 cur[2] = {c8 > 0 ? f0 : pad, c8 > 0 ? f1 : pad};
+    for (unsigned e = 0; e < cmax; e += 8) {
+        const bool more = e + 8 < c8;
+        // slots clamped into the row so that the loads need no branch
+        const unsigned s0 = min(e + 8 + j, (unsigned)LIST_SLOTS - 8), s1 = s0 + 4;
+        const uint4 l0 = __ldg(E + s0), l1 = __ldg(E + s1);
+        const uint4 nxt[2] = {more ? l0 : pad, more ? l1 : pad};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = __ldg(E + e + u);
+        for (int half = 0; half < 2; ++half) {
+            uint4 zz[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            zz[u] = __ldg(reinterpret_cast<const uint2 *>(z + (size_t)q[u].x * MP_P));
+            for (int u = 0; u < 4; ++u) {
+                const unsigned idx = __shfl_sync(0xffffffffu, cur[half].x, g0 + u);
+                zz[u] = __ldg(reinterpret_cast<const uint4 *>(z + (size_t)idx * MP_P));
+            }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            float2 w01 = unpack_h2(q[u].y), w23 = unpack_h2(q[u].z);
-            float2 z01 = unpack2(zz[u].x), z23 = unpack2(zz[u].y);
-            const float w[4] = {w01.x, w01.y, w23.x, w23.y};
-            const float zv[4] = {z01.x, z01.y, z23.x, z23.y};
+            for (int u = 0; u < 4; ++u) {
+                const float2 w01 = unpack_h2(__shfl_sync(0xffffffffu, cur[half].y, g0 + u));
+                const float2 w23 = unpack_h2(__shfl_sync(0xffffffffu, cur[half].z, g0 + u));
+                const float w[4] = {w01.x, w01.y, w23.x, w23.y};
+                const uint32_t zw[4] = {zz[u].x, zz[u].y, zz[u].z, zz[u].w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+                for (int p = 0; p < 4; ++p) {
+                    const float2 zp = unpack2(zw[p]);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[k][i] = fmaf(w[k], zv[i], acc[k][i]);
+                    for (int k = 0; k < 4; ++k) {
+                        acc[k][2 * p] = fmaf(w[k], zp.x, acc[k][2 * p]);
+                        acc[k][2 * p + 1] = fmaf(w[k], zp.y, acc[k][2 * p + 1]);
+                    }
+                }
+            }
         }
+        cur[0] = nxt[0];
+        cur[1] = nxt[1];
     }
 }
 
@@ -351,10 +400,24 @@ __device__ __forceinline__ void store16(void *p0, void *p1, const uint32_t (&pk)
     *reinterpret_cast<uint4 *>(p1) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // One layer of the inference pass (MODE: TC_FIRST, TC_MID or TC_LAST), one
-// persistent CTA of 1024 threads per SM, tiles of 128 particles.  hmap: the
-// TMA map of the hidden state h (n rows of 128 BF16; boxes of 8 columns x
-// 128 rows, rows past n read as zeros).
+// persistent CTA per SM over the tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ...; hmap: the TMA map of the hidden state h (n rows of 128 BF16; boxes of
+// 8 columns x 128 rows, rows past n read as zeros).  The i-th tile of a CTA
+// uses buffer b = i % 2; the mbarriers of buffer b complete once per tile
+// that uses it (parity (i / 2) % 2):
+//   full[b]  the operand tile is in place: 16 aggregation warps + the
+//            control thread's arrival (with the TMA bytes of h);
+//   acc[b]   the U accumulator is complete (tcgen05.commit);
+//   hnew[b]  the epilogue wrote h_{l+1} into the tile (8 warps);
+//   zf[b]    the message accumulator is complete (tcgen05.commit);
+//   free[b]  the epilogue is done with the tile and its tensor memory.
+// Every wait gives up after about a second: the error word gets
+// ERR_TIMEOUT, the role stops, and the block ends.
 template <int MODE, int K>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_layer(const __grid_constant__ CUtensorMap hmap, const TcArgs A) {
@@ -364,31 +427,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                           ~static_cast<uintptr_t>(1023));
     const uint32_t sbase = smem_u32(base);
     const unsigned tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
-    const uint32_t bar_w = sbase + SM_BAR, bar_h = sbase + SM_BAR + 8, bar_mma = sbase + SM_BAR + 16;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + SM_BAR + 32);
+    const uint32_t BAR = sbase + SM_BAR;
+    const uint32_t bar_w = BAR;
+    auto bar_full = [&](int b) { return BAR + 8u + 8u * b; };
+    auto bar_acc = [&](int b) { return BAR + 24u + 8u * b; };
+    auto bar_hnew = [&](int b) { return BAR + 40u + 8u * b; };
+    auto bar_zf = [&](int b) { return BAR + 56u + 8u * b; };
+    auto bar_free = [&](int b) { return BAR + 72u + 8u * b; };
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + SM_BAR + 128);
     float *par = reinterpret_cast<float *>(base + SM_PAR);
-    float2 *ypart = reinterpret_cast<float2 *>(base + SM_Y);
     const int n = A.n, ntiles = (n + TC_M - 1) / TC_M;
-
-    // a wait that ran out (about a second) ends the kernel: the error is
-    // recorded, thread 0 waits once more for what is still in flight, and
-    // the tensor memory is released below
-    auto all_ok = [&](bool mine, uint32_t bar, uint32_t parity) -> bool {
-        bool all = __syncthreads_and(mine) != 0;
-        if (!all && tid == 0) {
-            atomicOr(A.err, (unsigned)ERR_TIMEOUT);
-            mbar_wait(bar, parity);
-        }
-        return all;
-    };
+    const int my_tiles =
+        (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto tile_row0 = [&](int i) { return ((int)blockIdx.x + i * (int)gridDim.x) * TC_M; };
+    auto tile_at = [&](int b) { return base + SM_A + b * A_BYTES; };
+    auto timeout = [&]() { atomicOr(A.err, (unsigned)ERR_TIMEOUT); };
 
     if (tid == 0) {
         mbar_init(bar_w, 1);
-        mbar_init(bar_h, 1);
-        mbar_init(bar_mma, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_full(b), TC_AGG_WARPS + 1);
+            mbar_init(bar_acc(b), 1);
+            mbar_init(bar_hnew(b), TC_EPI_WARPS);
+            mbar_init(bar_zf(b), 1);
+            mbar_init(bar_free(b), TC_EPI_WARPS);
+        }
         fence_mbar_init();
     }
-    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    if (warp == TC_CTL_WARP) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
     // FP32 parameters: W_in and b_in (FIRST; contiguous), c_l (MID, LAST), D
     // and d (LAST; contiguous)
     if (MODE == TC_FIRST) {
@@ -403,192 +469,241 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tmem_slot);
-    if (tid == 0) {
-        uint32_t bytes = (MODE != TC_FIRST ? (uint32_t)TC_U_BYTES : 0u) +
-                         (MODE != TC_LAST ? (uint32_t)TC_PI_BYTES : 0u);
-        mbar_expect_tx(bar_w, bytes);
-        if (MODE != TC_FIRST) bulk_g2s(sbase + SM_BU, A.u_img, (uint32_t)TC_U_BYTES, bar_w);
-        if (MODE != TC_LAST) bulk_g2s(sbase + SM_BPI, A.pi_img, (uint32_t)TC_PI_BYTES, bar_w);
-    }
-    bool ok = all_ok(mbar_wait(bar_w, 0), bar_w, 0);
-    uint32_t ph_h = 0, ph_mma = 0;
 
-    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-        const int m0 = tile * TC_M;
-        if (MODE != TC_FIRST) {
-            // h_l by TMA into columns 0..127 of the operand, while the
-            // threads aggregate the messages into columns 128..255
-            if (tid == 0) {
-                mbar_expect_tx(bar_h, (uint32_t)(TC_M * MP_H * 2));
-                for (int b = 0; b < MP_H / 8; ++b)
-                    tma_load_2d(sbase + SM_A + b * BLK_A, &hmap, 8 * b, m0, bar_h);
+    if (warp < TC_AGG_WARPS) {
+        // ---- operand producers ------------------------------------------
+        for (int i = 0; i < my_tiles; ++i) {
+            const int b = i & 1, m0 = tile_row0(i);
+            if (i >= 2 && !mbar_wait(bar_free(b), ((i >> 1) - 1) & 1)) {
+                timeout();
+                break;
             }
-            const unsigned r = tid >> 3, j = tid & 7u, a = (unsigned)m0 + r;
-            float acc[4][4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) acc[k][i] = 0.f;
-            if (a < (unsigned)n) aggregate(A, a, j, acc);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                // columns 128 + 32k + 4j .. +3: block 16 + 4k + j/2, half j % 2
-                unsigned char *dst = base + SM_A + (16 + 4 * k + (j >> 1)) * BLK_A + r * 16 + (j & 1u) * 8;
-                *reinterpret_cast<uint2 *>(dst) =
-                    make_uint2(pack2(acc[k][0], acc[k][1]), pack2(acc[k][2], acc[k][3]));
-            }
-            const bool mine = mbar_wait(bar_h, ph_h);
-            fence_async_smem();
-            tc_fence_before();
-            ok = all_ok(mine, bar_h, ph_h);
-            ph_h ^= 1u;
-            if (!ok) break;
-        } else {
-            // edge records: warp w takes the rows w, w + 32, w + 64, w + 96
-            for (int i = 0; i < TC_M / 32; ++i) {
-                unsigned a = (unsigned)m0 + warp + 32u * i;
-                if (a < (unsigned)n) edge_records<K>(A, a, lane);
-            }
-            // input layer: row r, columns 16 cg .. 16 cg + 15
-            const unsigned r = tid & (TC_M - 1), cg = tid >> 7, a = (unsigned)m0 + r;
-            const bool live = a < (unsigned)n;
-            float x[4] = {0.f, 0.f, 0.f, 0.f};
-            if (live) node_inputs(A, a, x);
-            uint32_t pk[8];
-#pragma unroll
-            for (int c = 0; c < 16; c += 2) {
-                float v[2];
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int col = 16 * cg + c + e;
-                    float s = par[MP_IN * MP_H + col];
-#pragma unroll
-                    for (int i = 0; i < MP_IN; ++i) s = fmaf(x[i], par[i * MP_H + col], s);
-                    v[e] = live ? fmaxf(s, 0.f) : 0.f;
+            unsigned char *Ab = tile_at(b);
+            if (MODE != TC_FIRST) {
+                // messages into columns 128..255: four lanes per row
+                const unsigned r = tid >> 2, j = tid & 3u, a = (unsigned)m0 + r;
+                // the next tile's records (its first 32 slots) on their way to L2
+                if (i + 1 < my_tiles) {
+                    const unsigned an = (unsigned)tile_row0(i + 1) + r;
+                    if (an < (unsigned)n) prefetch_l2(A.edge + (size_t)an * LIST_SLOTS + 8 * j);
                 }
-                pk[c / 2] = pack2(v[0], v[1]);
-            }
-            store16(base + SM_A + (2 * cg) * BLK_A + r * 16, base + SM_A + (2 * cg + 1) * BLK_A + r * 16, pk);
-            if (live) {
-                uint4 *g = reinterpret_cast<uint4 *>(A.h + (size_t)a * MP_H + 16 * cg);
-                store16(g, g + 1, pk);
-            }
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-        }
-
-        if (MODE != TC_FIRST) {
-            // acc = [h, g] U_l (K = 256 in 16 steps)
-            if (tid == 0) {
-                tc_fence_after();
-#pragma unroll 1
-                for (int ks = 0; ks < MP_CAT / 16; ++ks) {
-                    uint64_t ad = smem_desc(sbase + SM_A + 2 * ks * BLK_A, BLK_A, 128);
-                    uint64_t bd = smem_desc(sbase + SM_BU + 2 * ks * BLK_A, BLK_A, 128);
-                    tc_mma(tmem, ad, bd, idesc_bf16(TC_M, MP_H), ks > 0 ? 1u : 0u);
-                }
-                tc_commit(bar_mma);
-            }
-            ok = all_ok(mbar_wait(bar_mma, ph_mma), bar_mma, ph_mma);
-            ph_mma ^= 1u;
-            if (!ok) break;
-            tc_fence_after();
-            // h_{l+1} = h_l + relu(acc + c_l): warp w reads rows 32 (w % 4)
-            // .. +31, columns 16 (w / 4) .. +15
-            const unsigned q = warp & 3u, cg = warp >> 2, r = 32 * q + lane, a = (unsigned)m0 + r;
-            float v[16];
-            tc_ld16(tmem + ((32 * q) << 16) + 16 * cg, v);
-            unsigned char *hs0 = base + SM_A + (2 * cg) * BLK_A + r * 16;
-            unsigned char *hs1 = base + SM_A + (2 * cg + 1) * BLK_A + r * 16;
-            const uint4 o0 = *reinterpret_cast<const uint4 *>(hs0);
-            const uint4 o1 = *reinterpret_cast<const uint4 *>(hs1);
-            const uint32_t ow[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
-            float hn[16];
+                float acc[4][8];
 #pragma unroll
-            for (int c = 0; c < 16; c += 2) {
-                float2 ho = unpack2(ow[c / 2]);
-                hn[c] = ho.x + fmaxf(v[c] + par[16 * cg + c], 0.f);
-                hn[c + 1] = ho.y + fmaxf(v[c + 1] + par[16 * cg + c + 1], 0.f);
-            }
-            if (MODE == TC_MID) {
-                uint32_t pk[8];
+                for (int k = 0; k < 4; ++k)
 #pragma unroll
-                for (int c = 0; c < 16; c += 2) pk[c / 2] = pack2(hn[c], hn[c + 1]);
-                store16(hs0, hs1, pk);
-                if (a < (unsigned)n) {
-                    uint4 *g = reinterpret_cast<uint4 *>(A.h + (size_t)a * MP_H + 16 * cg);
-                    store16(g, g + 1, pk);
+                    for (int q = 0; q < 8; ++q) acc[k][q] = 0.f;
+                aggregate(A, a, a < (unsigned)n, lane, acc);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    // columns 128 + 32k + 8j .. +7: block 16 + 4k + j
+                    *reinterpret_cast<uint4 *>(Ab + (16 + 4 * k + j) * BLK_A + r * 16) =
+                        make_uint4(pack2(acc[k][0], acc[k][1]), pack2(acc[k][2], acc[k][3]),
+                                   pack2(acc[k][4], acc[k][5]), pack2(acc[k][6], acc[k][7]));
                 }
             } else {
-                // y = h D + d: this thread's 16 columns of the sum
-                float p0 = 0.f, p1 = 0.f;
+                // input layer: row r, columns 32 cg .. 32 cg + 31
+                const unsigned r = tid & (TC_M - 1), cg = tid >> 7, a = (unsigned)m0 + r;
+                const bool live = a < (unsigned)n;
+                float x[4] = {0.f, 0.f, 0.f, 0.f};
+                if (live) node_inputs(A, a, x);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    p0 = fmaf(hn[c], par[MP_H + 2 * (16 * cg + c)], p0);
-                    p1 = fmaf(hn[c], par[MP_H + 2 * (16 * cg + c) + 1], p1);
-                }
-                ypart[cg * TC_M + r] = make_float2(p0, p1);
-            }
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-        }
-
-        if (MODE != TC_LAST) {
-            // z = h Pi (K = 128 in 8 steps, N = 32) into tensor-memory
-            // columns 128..159
-            if (tid == 0) {
-                tc_fence_after();
-#pragma unroll 1
-                for (int ks = 0; ks < MP_H / 16; ++ks) {
-                    uint64_t ad = smem_desc(sbase + SM_A + 2 * ks * BLK_A, BLK_A, 128);
-                    uint64_t bd = smem_desc(sbase + SM_BPI + 2 * ks * BLK_PI, BLK_PI, 128);
-                    tc_mma(tmem + TMEM_Z, ad, bd, idesc_bf16(TC_M, MP_P), ks > 0 ? 1u : 0u);
-                }
-                tc_commit(bar_mma);
-            }
-            ok = all_ok(mbar_wait(bar_mma, ph_mma), bar_mma, ph_mma);
-            ph_mma ^= 1u;
-            if (!ok) break;
-            tc_fence_after();
-            if (warp < 8) {
-                const unsigned q = warp & 3u, cg = warp >> 2, r = 32 * q + lane, a = (unsigned)m0 + r;
-                float v[16];
-                tc_ld16(tmem + ((32 * q) << 16) + TMEM_Z + 16 * cg, v);
-                if (a < (unsigned)n) {
+                for (int half = 0; half < 2; ++half) {
+                    const int c0 = 32 * cg + 16 * half;
                     uint32_t pk[8];
 #pragma unroll
-                    for (int c = 0; c < 16; c += 2) pk[c / 2] = pack2(v[c], v[c + 1]);
-                    uint4 *g = reinterpret_cast<uint4 *>(A.zout + (size_t)a * MP_P + 16 * cg);
-                    store16(g, g + 1, pk);
-                }
-            }
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-        } else {
-            if (tid < (unsigned)TC_M) {
-                const unsigned a = (unsigned)m0 + tid;
-                if (a < (unsigned)n) {
-                    float2 s = make_float2(par[MP_H + MP_H * MP_OUT], par[MP_H + MP_H * MP_OUT + 1]);
+                    for (int c = 0; c < 16; c += 2) {
+                        float v[2];
 #pragma unroll
-                    for (int cg = 0; cg < 8; ++cg) {
-                        float2 p = ypart[cg * TC_M + tid];
-                        s.x += p.x;
-                        s.y += p.y;
+                        for (int e = 0; e < 2; ++e) {
+                            const int col = c0 + c + e;
+                            float sum = par[MP_IN * MP_H + col];
+#pragma unroll
+                            for (int q = 0; q < MP_IN; ++q) sum = fmaf(x[q], par[q * MP_H + col], sum);
+                            v[e] = live ? fmaxf(sum, 0.f) : 0.f;
+                        }
+                        pk[c / 2] = pack2(v[0], v[1]);
                     }
-                    A.y[a] = s;
+                    store16(Ab + (c0 / 8) * BLK_A + r * 16, Ab + (c0 / 8 + 1) * BLK_A + r * 16, pk);
+                    if (live) {
+                        uint4 *g = reinterpret_cast<uint4 *>(A.h + (size_t)a * MP_H + c0);
+                        store16(g, g + 1, pk);
+                    }
                 }
             }
             fence_async_smem();
-            __syncthreads();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_full(b));
+        }
+    } else if (warp < TC_CTL_WARP) {
+        // ---- epilogue ---------------------------------------------------
+        const unsigned q = warp & 3u, ch = (warp - TC_AGG_WARPS) >> 2, r = 32 * q + lane;
+        const uint32_t tl = tmem + ((32 * q) << 16);
+        for (int i = 0; i < my_tiles; ++i) {
+            const int b = i & 1;
+            const uint32_t par_u = (uint32_t)(i >> 1) & 1u;
+            const unsigned a = (unsigned)tile_row0(i) + r;
+            const bool live = a < (unsigned)n;
+            unsigned char *Ab = tile_at(b);
+            if (MODE != TC_FIRST) {
+                // the tile (h_l by TMA) and the U accumulator
+                if (!mbar_wait(bar_full(b), par_u) || !mbar_wait(bar_acc(b), par_u)) {
+                    timeout();
+                    break;
+                }
+                tc_fence_after();
+                // MID: warp halves ch = 0, 1 take columns 0..63 and 64..127;
+                // LAST: the ch = 0 warps take all 128 (y needs the whole row)
+                float yp0 = 0.f, yp1 = 0.f;
+                const int nchunk = MODE == TC_MID ? 4 : (ch == 0 ? 8 : 0);
+#pragma unroll 1
+                for (int c4 = 0; c4 < nchunk; ++c4) {
+                    const int c0 = (MODE == TC_MID ? 64 * ch : 0) + 16 * c4;
+                    float v[16];
+                    tc_ld16(tl + b * 128 + c0, v);
+                    unsigned char *hs0 = Ab + (c0 / 8) * BLK_A + r * 16;
+                    unsigned char *hs1 = Ab + (c0 / 8 + 1) * BLK_A + r * 16;
+                    const uint4 o0 = *reinterpret_cast<const uint4 *>(hs0);
+                    const uint4 o1 = *reinterpret_cast<const uint4 *>(hs1);
+                    const uint32_t ow[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+                    float hn[16];
+#pragma unroll
+                    for (int c = 0; c < 16; c += 2) {
+                        const float2 ho = unpack2(ow[c / 2]);
+                        hn[c] = ho.x + fmaxf(v[c] + par[c0 + c], 0.f);
+                        hn[c + 1] = ho.y + fmaxf(v[c + 1] + par[c0 + c + 1], 0.f);
+                    }
+                    if (MODE == TC_MID) {
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int c = 0; c < 16; c += 2) pk[c / 2] = pack2(hn[c], hn[c + 1]);
+                        store16(hs0, hs1, pk);
+                        if (live) {
+                            uint4 *g = reinterpret_cast<uint4 *>(A.h + (size_t)a * MP_H + c0);
+                            store16(g, g + 1, pk);
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            yp0 = fmaf(hn[c], par[MP_H + 2 * (c0 + c)], yp0);
+                            yp1 = fmaf(hn[c], par[MP_H + 2 * (c0 + c) + 1], yp1);
+                        }
+                    }
+                }
+                if (MODE == TC_MID) {
+                    fence_async_smem();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar_hnew(b));
+                } else {
+                    // y = h D + d
+                    if (ch == 0 && live)
+                        A.y[a] = make_float2(par[MP_H + MP_H * MP_OUT] + yp0,
+                                             par[MP_H + MP_H * MP_OUT + 1] + yp1);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar_free(b));
+                    continue;
+                }
+            }
+            // the messages z = h Pi of this tile: columns 16 ch .. 16 ch + 15
+            if (!mbar_wait(bar_zf(b), par_u)) {
+                timeout();
+                break;
+            }
+            tc_fence_after();
+            float v[16];
+            tc_ld16(tl + TMEM_Z + 32 * b + 16 * ch, v);
+            if (live) {
+                uint32_t pk[8];
+#pragma unroll
+                for (int c = 0; c < 16; c += 2) pk[c / 2] = pack2(v[c], v[c + 1]);
+                uint4 *g = reinterpret_cast<uint4 *>(A.zout + (size_t)a * MP_P + 16 * ch);
+                store16(g, g + 1, pk);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_free(b));
+        }
+    } else if (lane == 0) {
+        // ---- control: weights, TMA loads, tcgen05.mma --------------------
+        bool ok = true;
+        uint32_t pend_bar = 0, pend_par = 0;   // the last commit, for a drain on failure
+        mbar_expect_tx(bar_w, (MODE != TC_FIRST ? (uint32_t)TC_U_BYTES : 0u) +
+                                  (MODE != TC_LAST ? (uint32_t)TC_PI_BYTES : 0u));
+        if (MODE != TC_FIRST) bulk_g2s(sbase + SM_BU, A.u_img, (uint32_t)TC_U_BYTES, bar_w);
+        if (MODE != TC_LAST) bulk_g2s(sbase + SM_BPI, A.pi_img, (uint32_t)TC_PI_BYTES, bar_w);
+        if (!mbar_wait(bar_w, 0)) {
+            timeout();
+            ok = false;
+        }
+        auto load = [&](int i) {
+            const int b = i & 1;
+            if (MODE != TC_FIRST) {
+                mbar_expect_tx(bar_full(b), (uint32_t)(TC_M * MP_H * 2));
+                const uint32_t dst = sbase + SM_A + b * A_BYTES;
+                for (int blk = 0; blk < MP_H / 8; ++blk)
+                    tma_load_2d(dst + blk * BLK_A, &hmap, 8 * blk, tile_row0(i), bar_full(b));
+            } else {
+                mbar_arrive(bar_full(b));
+            }
+        };
+        for (int i = 0; ok && i < my_tiles && i < 2; ++i) load(i);
+        for (int i = 0; ok && i < my_tiles; ++i) {
+            const int b = i & 1;
+            const uint32_t par_u = (uint32_t)(i >> 1) & 1u;
+            const uint32_t at = sbase + SM_A + b * A_BYTES;
+            if (!mbar_wait(bar_full(b), par_u)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            if (MODE != TC_FIRST) {
+                // acc = [h, g] U_l (K = 256 in 16 steps)
+#pragma unroll 1
+                for (int ks = 0; ks < MP_CAT / 16; ++ks)
+                    tc_mma(tmem + b * 128, smem_desc(at + 2 * ks * BLK_A, BLK_A, 128),
+                           smem_desc(sbase + SM_BU + 2 * ks * BLK_A, BLK_A, 128),
+                           idesc_bf16(TC_M, MP_H), ks > 0 ? 1u : 0u);
+                tc_commit(bar_acc(b));
+                pend_bar = bar_acc(b);
+                pend_par = par_u;
+            }
+            if (MODE != TC_LAST) {
+                if (MODE == TC_MID) {
+                    if (!mbar_wait(bar_hnew(b), par_u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                // z = h Pi (K = 128 in 8 steps, N = 32)
+#pragma unroll 1
+                for (int ks = 0; ks < MP_H / 16; ++ks)
+                    tc_mma(tmem + TMEM_Z + 32 * b, smem_desc(at + 2 * ks * BLK_A, BLK_A, 128),
+                           smem_desc(sbase + SM_BPI + 2 * ks * BLK_PI, BLK_PI, 128),
+                           idesc_bf16(TC_M, MP_P), ks > 0 ? 1u : 0u);
+                tc_commit(bar_zf(b));
+                pend_bar = bar_zf(b);
+                pend_par = par_u;
+            }
+            if (i + 2 < my_tiles) {
+                if (!mbar_wait(bar_free(b), par_u)) {
+                    ok = false;
+                    break;
+                }
+                load(i + 2);
+            }
+        }
+        if (!ok) {
+            timeout();
+            if (pend_bar) mbar_wait(pend_bar, pend_par);   // let the last MMAs finish
         }
     }
+    __syncwarp();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+    if (warp == TC_CTL_WARP) tmem_dealloc(tmem, TMEM_COLS);
 }
 
 // cuTensorMapEncodeTiled from the driver (through the runtime's entry-point
@@ -627,6 +742,7 @@ cudaError_t forward_k(int grid, const CUtensorMap &hmap, TcArgs A, const __nv_bf
     A.pi_img = pi_img;
     A.zout = scr.z[0];
     A.off0 = kMP.W_in;
+    k_tc_edges<K><<<(A.n + 31) / 32, 256, 0, s>>>(A.P, A.hot, A.nl, A.n, A.inv_uref, A.edge, A.ecnt);
     cudaError_t e = launch_layer<TC_FIRST, K>(grid, hmap, A, s);
     for (int l = 0; l < MP_L && e == cudaSuccess; ++l) {
         A.off0 = kMP.c[l];

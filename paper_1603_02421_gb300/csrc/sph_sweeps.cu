@@ -16,6 +16,7 @@
 // block and the finds are compacted with a G-lane ballot; later sweeps split
 // each particle's list G ways; partial sums are combined with warp shuffles.  Consecutive particles are spatially
 // adjacent, so their neighbours' records are served from L1.
+#include <algorithm>
 #include <type_traits>
 
 #include "sph_device.cuh"
@@ -1242,6 +1243,34 @@ void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State
 // corrector.  Writes raw in the cell order of the evaluation and sets the
 // step length for the time advance that follows.
 // ---------------------------------------------------------------------------
+// Adds the block's sums of v[0..NV) to out[0..NV): FP32 within a warp (a few
+// terms per thread and 32 threads: rounding far below what the sums are
+// compared with), FP64 across the warps of the block and across blocks (one
+// atomic per value and block; blockDim.x a multiple of 32, <= 1024).  FP64
+// arithmetic runs at a small fraction of the FP32 rate on this GPU, so none
+// of it is per particle.
+template <int NV>
+__device__ __forceinline__ void block_sum_atomic(float (&v)[NV], double *__restrict__ out) {
+    __shared__ double part[32][NV];
+    const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        float x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) part[w][k] = (double)x;
+    }
+    __syncthreads();
+    if (threadIdx.x < (unsigned)NV) {
+        double t = 0.0;
+        for (unsigned q = 0; q < nw; ++q) t += part[q][threadIdx.x];
+        atomicAdd(&out[threadIdx.x], t);
+    }
+}
+
+// Blocks of a grid-stride reduction over n items: few enough that the
+// per-block atomics on the same addresses stay cheap.
+inline int reduce_blocks(int n) { return std::max(1, std::min((n + 511) / 512, 128)); }
+
 // Mass-weighted sums of the network's output over the fluid particles of the
 // step start: ym[0..1] = sum m y, ym[2] = sum m (FP64).  The correction
 // a_ref (y - ybar), ybar = ym[0..1] / ym[2], then changes the fluid's
@@ -1250,24 +1279,22 @@ void launch_spawn(const PhysT<T> &P, const Inflow &inf, Scalars *sc, const State
 __global__ void k_surrogate_mean(int n, const uint8_t *__restrict__ type,
                                  const float *__restrict__ mass, const float2 *__restrict__ y,
                                  double *__restrict__ ym) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[3] = {0.0, 0.0, 0.0};
-    if (i < n && type[i] == T_FLUID) {
-        double m = (double)mass[i];
-        v[0] = m * y[i].x;
-        v[1] = m * y[i].y;
-        v[2] = m;
+    float v[3] = {0.f, 0.f, 0.f};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (type[i] != T_FLUID) continue;
+        const float m = mass[i];
+        const float2 yi = y[i];
+        v[0] += m * yi.x;
+        v[1] += m * yi.y;
+        v[2] += m;
     }
-    for (int k = 0; k < 3; ++k) {
-        double x = v[k];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&ym[k], x);
-    }
+    block_sum_atomic<3>(v, ym);
 }
 
 void launch_surrogate_mean(int n, const uint8_t *type, const float *mass, const float2 *y,
                            double *ym, int cap, cudaStream_t s) {
-    launch_k(k_surrogate_mean, (cap + 255) / 256, 256, s, n, type, mass, y, ym);
+    (void)cap;
+    launch_k(k_surrogate_mean, reduce_blocks(n), 512, s, n, type, mass, y, ym);
 }
 
 __device__ __forceinline__ float2 mean_of(const double *__restrict__ ym) {
@@ -1275,24 +1302,24 @@ __device__ __forceinline__ float2 mean_of(const double *__restrict__ ym) {
     return w > 0.0 ? make_float2((float)(ym[0] / w), (float)(ym[1] / w)) : make_float2(0.f, 0.f);
 }
 
-__global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *__restrict__ sc,
-                                   State<float> srt, State<float> raw,
-                                   const float2 *__restrict__ a_n, const float2 *__restrict__ y,
-                                   const double *__restrict__ ym, float a_ref,
-                                   const float *__restrict__ dr, double dT) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) sc->dt = dT;
-    if (i >= sc->nsrt) return;
-    const float2 yb = mean_of(ym);
+// The update of particle i; d2o, s2o receive its squared displacement since
+// the build and in this step (0 when it left the domain).
+__device__ __forceinline__ void surrogate_update_one(
+    const PhysT<float> &P, const Inflow &inf, const Grid &g, Scalars *__restrict__ sc,
+    const State<float> &srt, const State<float> &raw, const float2 *__restrict__ a_n,
+    const float2 *__restrict__ y, const float2 yb, float a_ref, const float *__restrict__ dr,
+    double dT, int i, float &d2o, float &s2o, uint8_t *__restrict__ type0) {
     double t = sc->t, half = 0.5 * dT;
     double2 p0 = srt.pos[i];
     float2 v0 = srt.vel[i];
     float d0 = srt.drho[i], c0 = srt.drc[i];
     uint8_t typ = srt.type[i];
+    type0[i] = typ;
     double2 p1 = p0;
     float2 v1 = v0;
     float d1 = d0, c1 = c0;
     float2 ds = srt.disp[i];
+    float2 st = make_float2(0.f, 0.f);   // this step's move relative to the frame
     if (typ == T_FLUID) {
         float tdt = (float)dT;
         float ax = a_n[i].x + a_ref * (y[i].x - yb.x), ay = a_n[i].y + a_ref * (y[i].y - yb.y);
@@ -1303,13 +1330,15 @@ __global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *
         float s = d0 + y;
         c1 = (s - d0) - y;
         d1 = s;
-        ds = make_float2(ds.x + tdt * (P.ufx - P.dfx + uhx), ds.y + tdt * (P.ufy - P.dfy + uhy));
+        st = make_float2(tdt * (P.ufx - P.dfx + uhx), tdt * (P.ufy - P.dfy + uhy));
+        ds = make_float2(ds.x + st.x, ds.y + st.y);
     } else if (typ == T_BUFFER) {
         double uh = inf.on ? inflow_u(inf, t + half) : P.ufx_d + (double)v0.x;
         p1 = make_double2(p0.x + dT * uh, p0.y);
         v1 = inf.on ? make_float2((float)(inflow_u(inf, t + dT) - P.ufx_d), (float)(-P.ufy_d)) : v0;
         if (inf.on && p1.x >= inf.x_exit) typ = T_FLUID;
-        ds = make_float2(ds.x + (float)(dT * (uh - (double)P.dfx)), ds.y);
+        st = make_float2((float)(dT * (uh - (double)P.dfx)), (float)(-dT * (double)P.dfy));
+        ds = make_float2(ds.x + st.x, ds.y);
     }
     if (typ == T_FLUID &&
         !(p1.x >= g.xmin && p1.x < g.xmax && p1.y >= g.ymin && p1.y < g.ymax)) {
@@ -1327,31 +1356,56 @@ __global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *
     // largest displacement since the build and in this step, for the time
     // advance's rebuild decision (the step's move relative to the frame)
     if (typ != T_DEAD) {
-        float d2 = ds.x * ds.x + ds.y * ds.y;
-        float mx = (float)(p1.x - p0.x) - (float)(dT * (double)P.dfx);
-        float my = (float)(p1.y - p0.y) - (float)(dT * (double)P.dfy);
-        float s2 = mx * mx + my * my;
-        unsigned m = __activemask();
-        unsigned a = __reduce_max_sync(m, __float_as_uint(d2));
-        unsigned b2 = __reduce_max_sync(m, __float_as_uint(s2));
-        if ((threadIdx.x & 31u) == (unsigned)(__ffs(m) - 1)) {
-            int slot = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) & (RED_SLOTS - 1);
-            atomicMax(&sc->max_disp2[slot], a);
-            atomicMax(&sc->max_step2[slot], b2);
-        }
+        d2o = ds.x * ds.x + ds.y * ds.y;
+        s2o = st.x * st.x + st.y * st.y;
+    }
+}
+
+__global__ void k_surrogate_update(PhysT<float> P, Inflow inf, Grid g, Scalars *__restrict__ sc,
+                                   State<float> srt, State<float> raw,
+                                   const float2 *__restrict__ a_n, const float2 *__restrict__ y,
+                                   const double *__restrict__ ym, float a_ref,
+                                   const float *__restrict__ dr, double dT,
+                                   uint8_t *__restrict__ type0) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) sc->dt = dT;
+    __shared__ float2 s_yb;
+    if (threadIdx.x == 0) s_yb = mean_of(ym);
+    __syncthreads();
+    float d2 = 0.f, s2 = 0.f;
+    if (i < sc->nsrt)
+        surrogate_update_one(P, inf, g, sc, srt, raw, a_n, y, s_yb, a_ref, dr, dT, i, d2, s2, type0);
+    // block maxima (non-negative floats order as their bits), then one atomic
+    // per block and value
+    __shared__ unsigned bm[2];
+    if (threadIdx.x == 0) bm[0] = bm[1] = 0u;
+    __syncthreads();
+    const unsigned a = __reduce_max_sync(0xffffffffu, __float_as_uint(d2));
+    const unsigned b2 = __reduce_max_sync(0xffffffffu, __float_as_uint(s2));
+    if ((threadIdx.x & 31u) == 0) {
+        atomicMax(&bm[0], a);
+        atomicMax(&bm[1], b2);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (bm[0] | bm[1])) {
+        const int slot = blockIdx.x & (RED_SLOTS - 1);
+        atomicMax(&sc->max_disp2[slot], bm[0]);
+        atomicMax(&sc->max_step2[slot], bm[1]);
     }
 }
 
 void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Grid &g, Scalars *sc,
                              const State<float> &srt, const State<float> &raw, const float2 *a_n,
                              const float2 *y, const double *ym, float a_ref, const float *dr,
-                             double dT, int cap, cudaStream_t s) {
+                             double dT, uint8_t *type0, int cap, cudaStream_t s) {
     launch_k(k_surrogate_update, (cap + 255) / 256, 256, s, P, inf, g, sc, srt, raw, a_n, y, ym,
-             a_ref, dr, dT);
+             a_ref, dr, dT, type0);
 }
 
-// Residual sums of a surrogate step over the fluid particles present at both
-// ends (cell order; type from the end of the step), accumulated in FP64:
+// Residual sums of a surrogate step over the particles that are fluid at
+// both ends (cell order; type0 from the start, type from the end of the
+// step: inflow particles that became fluid during the step and outflow
+// deletions are left out), accumulated in FP64 across blocks:
 //   sums[0..1] = sum m (abar - (a_n + a_k)/2)      (momentum balance)
 //   sums[2]    = sum m |(a_n + a_k)/2|
 //   sums[3]    = sum (drho/dt_k - drho/dt_n)^2     (density)
@@ -1359,43 +1413,48 @@ void launch_surrogate_update(const PhysT<float> &P, const Inflow &inf, const Gri
 //   sums[5]    = sum |abar - (a_n + a_k)/2|^2      (acceleration field)
 //   sums[6]    = sum |(a_n + a_k)/2|^2
 // with abar = a_n + a_ref (y - ybar) (k_surrogate_mean).
-__global__ void k_surrogate_residual(int n, const uint8_t *__restrict__ type,
+__global__ void k_surrogate_residual(int n, const uint8_t *__restrict__ type0,
+                                     const uint8_t *__restrict__ type,
                                      const float *__restrict__ mass,
                                      const float2 *__restrict__ y, const double *__restrict__ ym,
                                      float a_ref,
                                      const float2 *__restrict__ a_n, const float2 *__restrict__ a_k,
                                      const float *__restrict__ dr_n, const float *__restrict__ dr_k,
                                      double *__restrict__ sums) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    const float2 yb = mean_of(ym);
-    if (i < n && type[i] == T_FLUID) {
-        double m = (double)mass[i];
-        double mx = 0.5 * ((double)a_n[i].x + a_k[i].x), my = 0.5 * ((double)a_n[i].y + a_k[i].y);
-        double ex = (double)a_n[i].x + (double)a_ref * (y[i].x - yb.x) - mx;
-        double ey = (double)a_n[i].y + (double)a_ref * (y[i].y - yb.y) - my;
-        double dd = (double)dr_k[i] - dr_n[i];
-        v[0] = m * ex;
-        v[1] = m * ey;
-        v[2] = m * sqrt(mx * mx + my * my);
-        v[3] = dd * dd;
-        v[4] = 1.0;
-        v[5] = ex * ex + ey * ey;
-        v[6] = mx * mx + my * my;
+    float v[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    __shared__ float2 s_yb;
+    if (threadIdx.x == 0) s_yb = mean_of(ym);
+    __syncthreads();
+    const float2 yb = s_yb;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (type0[i] != T_FLUID || type[i] != T_FLUID) continue;
+        // per particle in FP32 (the rounding of a term is far below the
+        // threshold)
+        const float m = mass[i];
+        const float2 an = a_n[i], ak = a_k[i], yi = y[i];
+        const float mx = 0.5f * (an.x + ak.x), my = 0.5f * (an.y + ak.y);
+        const float ex = an.x + a_ref * (yi.x - yb.x) - mx;
+        const float ey = an.y + a_ref * (yi.y - yb.y) - my;
+        const float dd = dr_k[i] - dr_n[i];
+        const float t2 = mx * mx + my * my;
+        v[0] += m * ex;
+        v[1] += m * ey;
+        v[2] += m * sqrtf(t2);
+        v[3] += dd * dd;
+        v[4] += 1.f;
+        v[5] += ex * ex + ey * ey;
+        v[6] += t2;
     }
-    for (int k = 0; k < 7; ++k) {
-        double x = v[k];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&sums[k], x);
-    }
+    block_sum_atomic<7>(v, sums);
 }
 
-void launch_surrogate_residual(int n, const uint8_t *type, const float *mass, const float2 *abar,
-                               const double *ym, float a_ref, const float2 *a_n, const float2 *a_k,
-                               const float *dr_n, const float *dr_k, double *sums, int cap,
-                               cudaStream_t s) {
-    launch_k(k_surrogate_residual, (cap + 255) / 256, 256, s, n, type, mass, abar, ym, a_ref, a_n,
-             a_k, dr_n, dr_k, sums);
+void launch_surrogate_residual(int n, const uint8_t *type0, const uint8_t *type, const float *mass,
+                               const float2 *abar, const double *ym, float a_ref,
+                               const float2 *a_n, const float2 *a_k, const float *dr_n,
+                               const float *dr_k, double *sums, int cap, cudaStream_t s) {
+    (void)cap;
+    launch_k(k_surrogate_residual, reduce_blocks(n), 512, s, n, type0, type, mass, abar, ym, a_ref,
+             a_n, a_k, dr_n, dr_k, sums);
 }
 
 // ---------------------------------------------------------------------------

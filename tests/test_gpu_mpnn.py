@@ -294,6 +294,44 @@ def test_accepted_steps_reuse_the_end_evaluation(sph):
     b.close()
 
 
+def test_batched_steps_equal_single_steps(sph):
+    # sph_surrogate_batch on two jets (one threshold rejecting, one
+    # accepting) does what sph_surrogate_step does on each alone; the
+    # FP64 sums of the mean removal and the residuals may differ in their
+    # last bits (atomics), nothing more
+    def jet(seed):
+        c = wl.jet(seed=seed, dx=1.0 / 20, length=6.0, Re=200, We=20)
+        c["params"]["skin_over_h"] = 0.3
+        return c
+
+    cases = [jet(6), jet(7)]
+    single = [sph.Simulation(c) for c in cases]
+    batch = [sph.Simulation(c) for c in cases]
+    for sim in single + batch:
+        sim.set_tuning(2, 8)
+        sim.run(2)
+    net = sph.Mpnn(capacity=max(c["params"]["capacity"] for c in cases))
+    net.set_params(_params(12))
+    for it, thr in enumerate((1e30, 1e30, 1e-30, 1e30)):
+        acc, rm, rd, rf = sph.sph_surrogate_batch([s.ctx for s in batch], net.net, 4, 1.0, 0.1, thr)
+        for i, sim in enumerate(single):
+            a1, m1, d1, f1 = sph.sph_surrogate_step(sim.ctx, net.net, 4, 1.0, 0.1, thr, True,
+                                                   field=True)
+            assert a1 == acc[i], (it, i)
+            assert m1 == pytest.approx(rm[i], rel=1e-6, abs=1e-12)
+            assert d1 == pytest.approx(rd[i], rel=1e-6, abs=1e-15)
+            assert f1 == pytest.approx(rf[i], rel=1e-6)
+    for a, b in zip(single, batch):
+        assert a.time()["t"] == b.time()["t"]
+        sa, sb = _by_id(a.state()), _by_id(b.state())
+        assert np.array_equal(sa["id"], sb["id"])
+        assert np.max(np.abs(sa["x"] - sb["x"])) < 1e-9
+        assert rel_l2(sa["u"], sb["u"]) < 1e-6 and rel_l2(sa["v"], sb["v"]) < 1e-6
+    net.close()
+    for sim in single + batch:
+        sim.close()
+
+
 def test_trained_network_beats_the_instantaneous_acceleration(sph):
     # what the network gains: the k-step mean acceleration it predicts on
     # jets with (Re, We) it was not trained on is closer to the truth (k plain

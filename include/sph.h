@@ -50,7 +50,9 @@ typedef enum {
     SPH_ERR_CUDA = -4,       /* CUDA runtime / launch error                  */
     SPH_ERR_NONFINITE = -5,  /* NaN / Inf in an acceleration or density rate */
     SPH_ERR_TIMEOUT = -6,    /* a bounded device loop hit its limit          */
-    SPH_ERR_STATE = -7,      /* call not valid in the current state          */
+    SPH_ERR_STATE = -7,      /* call not valid in the current state; in the
+                                bounds-check build (SPH_BOUNDS_CHECK) also a
+                                particle index out of range                  */
     SPH_ERR_SKIN = -8        /* a particle moved more than skin/2 between the
                                 cell build and an evaluation (reduce dt or
                                 raise skin_over_h)                           */
@@ -341,7 +343,9 @@ sph_status sph_kernel_counts(sph_ctx *ctx, int *per_full_step, int *per_reused_s
  * order unspecified); *npairs (host) receives the total count (a 64-bit
  * count, whatever the density of the input).  Work runs on `stream` (a
  * cudaStream_t, NULL = legacy default stream) of the current device; the call
- * waits for it and copies the count to the host.
+ * waits for it and copies the count to the host, so it cannot be part of a
+ * stream capture: on a stream being captured it returns SPH_ERR_ARG before
+ * enqueuing anything.
  *
  * Errors decided on the device still report the pairs found: particles
  * outside the box or with a NaN coordinate are left out of the search and

@@ -21,6 +21,12 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsph.so")
+# the bounds-check build (SPH_BOUNDS_CHECK): the same library with every
+# particle index met by the neighbour walks and the network's gathers checked
+# against the capacity (ERR_BOUNDS, SPH_ERR_STATE); a diagnostic, not the
+# product path
+BUILD_BOUNDS = os.path.join(PKG, "_build_bounds")
+LIB_BOUNDS = os.path.join(PKG, "libsph_bounds.so")
 SOURCES = ["sph_api.cu", "sph_neighbour.cu", "sph_sweeps.cu", "sph_noalloc.cu", "sph_mpnn.cu",
            "sph_mpnn_tc.cu", "sph_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -45,23 +51,26 @@ def _deps():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile and link libsph.so; returns its path."""
-    if not force and not extra and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), bounds_check: bool = False) -> str:
+    """Compile and link libsph.so (bounds_check: libsph_bounds.so, with
+    SPH_BOUNDS_CHECK defined); returns its path."""
+    lib = LIB_BOUNDS if bounds_check else LIB
+    bdir = BUILD_BOUNDS if bounds_check else BUILD
+    if not force and not extra and up_to_date(lib):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
-    flags = _flags() + list(extra)
+    flags = _flags() + list(extra) + (["-DSPH_BOUNDS_CHECK"] if bounds_check else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         cmd = [cc, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -74,13 +83,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         for obj, err in results:
             if err.strip():
                 print(err, file=sys.stderr)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [cc, *ARCH, "-shared", "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

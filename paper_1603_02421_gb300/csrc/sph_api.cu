@@ -171,6 +171,8 @@ static sph_status status_from_err(sph_ctx *c, unsigned err) {
     if (err & ERR_NODT) return fail(c, SPH_ERR_STATE, "adaptive time step without fluid particles");
     if (err & ERR_NLIST)
         return fail(c, SPH_ERR_CAPACITY, "a particle has more neighbours than its list holds");
+    if (err & ERR_BOUNDS)
+        return fail(c, SPH_ERR_STATE, "a particle index out of range (bounds-check build)");
     return SPH_OK;
 }
 
@@ -530,6 +532,8 @@ static void rebuild_phys(sph_ctx *c) {
     bool walls = !c->bx.empty();
     c->Pf = make_phys<float>(c->prm, c->grid, walls);
     c->Pd = make_phys<double>(c->prm, c->grid, walls);
+    c->Pf.cap = c->Pd.cap = (int)c->cap;
+    c->Pf.err = c->Pd.err = c->sc ? &c->sc->err : nullptr;
     mark_graph_dirty(c);
 }
 

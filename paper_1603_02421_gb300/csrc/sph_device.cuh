@@ -200,6 +200,22 @@ __device__ __forceinline__ void q_of(double r2, double h, double inv_h, double &
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
+// Bounds-check build (SPH_BOUNDS_CHECK): true, with ERR_BOUNDS recorded in
+// the context's error word, when particle index k is not below the capacity
+// of the particle arrays; the walks then skip the entry.  Without the macro
+// the test is the constant false and costs nothing.
+template <class T> __device__ __forceinline__ bool index_bad(const PhysT<T> &P, unsigned k) {
+#ifdef SPH_BOUNDS_CHECK
+    if (k < (unsigned)P.cap) return false;
+    if (P.err) atomicOr(P.err, (unsigned)ERR_BOUNDS);
+    return true;
+#else
+    (void)P;
+    (void)k;
+    return false;
+#endif
+}
+
 // Visit every particle b != i of the 3x3 cell block of particle i whose FP64
 // distance is below the threshold.  Squared distances in T inside [lo, hi)
 // are re-tested exactly in FP64 on the stored positions, so the visited set
@@ -221,6 +237,7 @@ __device__ __forceinline__ void for_neighbours(const PhysT<T> &P, const Grid &g,
         RowRange rr = row_range(cellSE, (int)key + dy * g.ncx);
 #pragma unroll 2
         for (unsigned b = rr.lo + sub; b < rr.hi; b += G) {
+            if (index_bad(P, b)) break;
             typename Vec<T>::v4 hb = H0[b];
             T rx = off_diff<T>(P, xa, hb.x, row_step(rr, b));
             T ry = off_diff<T>(P, ya, hb.y, -dy);
@@ -284,15 +301,19 @@ __device__ __forceinline__ void for_list(const PhysT<T> &P, const NList &nl,
         // the next chunk's entries load while this chunk is processed
         if (base + G * CH < cnt) load_entries<CH>(e + base + G * CH, nxt);
         Rec rec[CH];
-        unsigned bb[CH];
+        unsigned bb[CH], skip = 0u;
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
             bb[u] = base + u < cnt ? (ent[u] & 0x0FFFFFFFu) : i;
+            if (index_bad(P, bb[u])) {
+                bb[u] = i;
+                skip |= 1u << u;
+            }
             rec[u] = gather(bb[u]);
         }
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
-            if (base + u >= cnt) continue;
+            if (base + u >= cnt || ((skip >> u) & 1u)) continue;
             T rx = off_diff<T>(P, xa, rec[u].x.x, code_cells((ent[u] >> 28) & 3u));
             T ry = off_diff<T>(P, ya, rec[u].x.y, code_cells(ent[u] >> 30));
             T r2 = rx * rx + ry * ry;

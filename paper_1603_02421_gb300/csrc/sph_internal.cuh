@@ -27,7 +27,8 @@ enum ErrBits : unsigned {
     ERR_CAPACITY = 4u,
     ERR_TIMEOUT = 8u,
     ERR_NODT = 16u,
-    ERR_NLIST = 32u
+    ERR_NLIST = 32u,
+    ERR_BOUNDS = 64u
 };
 
 struct __align__(16) f4 { float x, y, z, w; };
@@ -106,6 +107,11 @@ template <class T> struct PhysT {
     double courant, dt_fixed;
     double ufx_d, ufy_d;
     double half_skin2;   // (skin/2)^2: largest displacement between list build and use
+    // bounds-check build (SPH_BOUNDS_CHECK): particle indices the walks meet
+    // must lie below cap; one that does not sets ERR_BOUNDS in *err and is
+    // skipped
+    int cap;
+    unsigned *err;
 };
 
 // Inflow of the planar jet.

@@ -78,6 +78,7 @@ __device__ __forceinline__ bool list_pair(const PhysT<float> &P, const Hot<float
                                           float &r2, float &du, float &dv) {
     uint32_t ent = e[k];
     o = ent & 0x0FFFFFFFu;
+    if (index_bad(P, o)) return false;
     V4f ho = hot.H0[o];
     rx = off_diff<float>(P, hs.x, ho.x, code_cells((ent >> 28) & 3u));
     ry = off_diff<float>(P, hs.y, ho.y, code_cells(ent >> 30));

@@ -369,7 +369,8 @@ __device__ __forceinline__ void aggregate(const TcArgs &A, unsigned a, bool live
             uint4 zz[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const unsigned idx = __shfl_sync(0xffffffffu, cur[half].x, g0 + u);
+                unsigned idx = __shfl_sync(0xffffffffu, cur[half].x, g0 + u);
+                if (index_bad(A.P, idx)) idx = self;
                 zz[u] = __ldg(reinterpret_cast<const uint4 *>(z + (size_t)idx * MP_P));
             }
 #pragma unroll

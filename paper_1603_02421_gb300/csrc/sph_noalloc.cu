@@ -130,6 +130,12 @@ extern "C" sph_status sph_pairs_noalloc(const double *x, const double *y, long l
     if (n > 0 && (!x || !y)) return SPH_ERR_ARG;
     if (cap > 0 && (!pair_a || !pair_b)) return SPH_ERR_ARG;
     *npairs = 0;
+    // the call synchronises and reads back a count, which a stream capture
+    // cannot hold: refuse before anything is enqueued
+    cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &capture) != cudaSuccess ||
+        capture != cudaStreamCaptureStatusNone)
+        return SPH_ERR_ARG;
     // the grid of a context with skin_over_h = 0.1
     double sc = 2.0 * h + 0.1 * h;
     double ncx = std::floor((xmax - xmin) / sc) + 3, ncy = std::floor((ymax - ymin) / sc) + 3;
@@ -160,6 +166,8 @@ extern "C" sph_status sph_pairs_noalloc(const double *x, const double *y, long l
     P.off_scale = (float)(OFF_ONE / sc);
 
     Scalars *scal = (Scalars *)(base + kL.sc);
+    P.cap = (int)n;
+    P.err = &scal->err;
     State<float> raw{};
     raw.pos = (double2 *)(base + kL.pos);
     raw.type = base + kL.type;

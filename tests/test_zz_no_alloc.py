@@ -119,3 +119,30 @@ def test_noalloc_rejects_oversize_inputs():
         binding.sph_pairs_noalloc(x.data_ptr(), x.data_ptr(), 4, 1e-4,
                                   (0.0, 0.0, 1.0, 1.0), x.data_ptr(), x.data_ptr(), 0)
     assert e.value.status == -3
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    # the call synchronises, which a capture cannot hold: it returns
+    # SPH_ERR_ARG before enqueuing anything, and the caller's capture stays
+    # valid
+    binding, torch, dev = _setup()
+    x = torch.zeros(16, dtype=torch.float64, device=dev)
+    a = torch.zeros(16, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize(dev)
+    status = None
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        y = x + 1.0
+        try:
+            binding.sph_pairs_noalloc(x.data_ptr(), x.data_ptr(), 4, 0.1, (0.0, 0.0, 1.0, 1.0),
+                                      a.data_ptr(), a.data_ptr(), 4, stream=s.cuda_stream)
+        except binding.SphError as e:
+            status = e.status
+        finally:
+            g.capture_end()
+    assert status == -1
+    g.replay()
+    torch.cuda.synchronize(dev)
+    assert float(y[0]) == 1.0

@@ -515,10 +515,12 @@ def test_summation_density_jet_with_inflow(sph, orc):
 # ---------------------------------------------------------------------------
 # paper-faithful variants: nozzle walls, inviscid jet
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_nozzle_jet_trajectory(sph, orc, prec):
-    # inflow buffer -> nozzle with repulsive walls (Eq. 29) -> free jet
-    case = wl.jet(seed=7, dx=1.0 / 20, length=4.0, nozzle=2.0, Re=200, We=20, prec=prec)
+@pytest.mark.parametrize("prec,nozzle,dx", [("fp32", 2.0, 1.0 / 20), ("fp64", 2.0, 1.0 / 20),
+                                             ("fp32", 15.0, 1.0 / 10), ("fp64", 15.0, 1.0 / 10)])
+def test_nozzle_jet_trajectory(sph, orc, prec, nozzle, dx):
+    # inflow buffer -> nozzle with repulsive walls (Eq. 29) -> free jet; the
+    # paper's nozzle has aspect ratio 15 (length 15 D)
+    case = wl.jet(seed=7, dx=dx, length=4.0, nozzle=nozzle, Re=200, We=20, prec=prec)
     case["params"]["dt_fixed"] = 1e-3
     sim = sph.Simulation(case)
     osim = oracle_sim(orc, case)

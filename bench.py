@@ -164,7 +164,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="jet_c3",
-                    choices=["jet_c2", "jet_c3", "dam_c1", "ensemble_c4", "surrogate_c5"])
+                    choices=["jet_c2", "jet_c3", "dam_c1", "ensemble_c4", "surrogate_c5",
+                             "surrogate_step"])
     ap.add_argument("--train-seconds", type=float, default=60.0,
                     help="surrogate_c5: GPU training time of the network")
     ap.add_argument("--threshold", type=float, default=1e-3,
@@ -357,6 +358,11 @@ def main():
     from paper_1603_02421_gb300.replicas import rank_members
     if args.workload == "ensemble_c4":
         bench_ensemble(args, binding, dist, dev, rank, world, local)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    if args.workload == "surrogate_step":
+        bench_surrogate_step(args, binding, dev, rank, local)
         if dist is not None:
             dist.destroy_process_group()
         return
@@ -846,6 +852,54 @@ SUR_TRAIN = [(100, 5), (200, 20), (400, 40), (700, 10), (1000, 60), (1500, 15), 
 SUR_HELD_RE = [150, 300, 550, 850, 1250, 1750, 2500, 2750]
 SUR_HELD_WE = [7.5, 25.0]
 SUR_K = 4
+
+
+def bench_surrogate_step(args, binding, dev, rank, local):
+    """The cost of one surrogate step against k plain steps on one C5-shaped
+    member (a 200k-particle held-out jet at D/60), every step accepted
+    (threshold 1e30) and the network untrained: the speed of the path, apart
+    from how often the judge accepts (which surrogate_c5 measures)."""
+    import torch
+    dx = 1.0 / 60
+    case = wl.jet(seed=201, Re=300, We=7.5, dx=dx, length=200000 * dx * dx, kernel="wendland",
+                  prec="fp32", capacity_factor=1.15)
+    case["params"]["skin_over_h"] = 0.3
+    stream = torch.cuda.Stream(device=dev)
+    sim = binding.Simulation(case, stream=stream.cuda_stream, device=local)
+    sim.set_tuning(2, 8)
+    sim.run(20)
+    n = sim.time()["n"]
+    net = binding.Mpnn(case["params"]["capacity"], local)
+    net.set_params(wl.mpnn_init(7))
+    K = max(4, min(args.steps, 200) // SUR_K * SUR_K)
+    for _ in range(max(args.warmup, 3)):
+        binding.sph_surrogate_step(sim.ctx, net.net, SUR_K, 1.0, 0.04, 1e30, True)
+    sim.run(SUR_K * max(args.warmup, 3))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    sim.run(K)
+    torch.cuda.synchronize(dev)
+    plain_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for _ in range(K // SUR_K):
+        binding.sph_surrogate_step(sim.ctx, net.net, SUR_K, 1.0, 0.04, 1e30, True)
+    torch.cuda.synchronize(dev)
+    sur_s = time.perf_counter() - t0
+    net.close()
+    sim.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": n * K / sur_s, "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sur_s / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "surrogate_step: one planar jet, Re=300, We=7.5, dx = D/60, "
+                                   "%d particles; k = %d substeps per surrogate step, every "
+                                   "step accepted, untrained network" % (n, SUR_K),
+                       "plain_value": n * K / plain_s, "surrogate_over_plain": plain_s / sur_s,
+                       "ms_per_surrogate_step": 1e3 * sur_s / (K // SUR_K),
+                       "ms_per_plain_step": 1e3 * plain_s / K,
+                       "timing": "host wall clock with device synchronisation around each arm"},
+        }), flush=True)
 
 
 def bench_surrogate(args, binding, dist, dev, rank, world, local):

@@ -597,7 +597,16 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
     } else if (typ == T_FLUID) {
         T th = (T)half, tdt = (T)dt;
         T usx = v0.x + th * ax, usy = v0.y + th * ay;
-        p1 = make_double2(p0.x + dt * (P.ufx_d + (double)usx), p0.y + dt * (P.ufy_d + (double)usy));
+        stx = tdt * (P.ufx + usx);
+        sty = tdt * (P.ufy + usy);
+        if constexpr (sizeof(T) == 4) {
+            // the FP32 step added to the FP64 position (its rounding, ~6e-8
+            // of a step's move, is far below the FP32 pair sums'; the cell
+            // offsets take the same increment)
+            p1 = make_double2(p0.x + (double)stx, p0.y + (double)sty);
+        } else {
+            p1 = make_double2(p0.x + dt * (P.ufx_d + (double)usx), p0.y + dt * (P.ufy_d + (double)usy));
+        }
         v1 = mk2(v0.x + tdt * ax, v0.y + tdt * ay);
         if (P.summation) {              // Eq. 6: the density of the half-step evaluation
             d1 = rho_half - P.rho0;
@@ -608,8 +617,6 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
             c1 = (s - d0) - y;
             d1 = s;
         }
-        stx = tdt * (P.ufx + usx);
-        sty = tdt * (P.ufy + usy);
         srx = tdt * (P.ufx - P.dfx + usx);
         sry = tdt * (P.ufy - P.dfy + usy);
     } else {
@@ -932,17 +939,28 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
         // every warp folds the 32 minimum slots itself (cached loads), so no
         // warp waits for another at a block barrier
         const int lane = threadIdx.x & 31;
-        double m = sizeof(T) == 4 ? (double)__uint_as_float(sc->dtmin_f[lane])
-                                  : __longlong_as_double((long long)sc->dtmin_d[lane]);
-        for (int o = 16; o > 0; o >>= 1) {
-            double w = __shfl_xor_sync(0xffffffffu, m, o);
-            m = w < m ? w : m;
+        double m;
+        if constexpr (sizeof(T) == 4) {
+            // FP32 slots: the minimum in FP32 (exact), one conversion and the
+            // Courant product on lane 0 only (FP64 runs at a small fraction
+            // of the FP32 rate), broadcast to the warp
+            float mf = __uint_as_float(sc->dtmin_f[lane]);
+            for (int o = 16; o > 0; o >>= 1) mf = fminf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+            double d0 = 0.0;
+            if (lane == 0) d0 = mf < 1.0e37f ? P.courant * (double)mf : 0.0;
+            m = mf;
+            dt = __shfl_sync(0xffffffffu, d0, 0);
+        } else {
+            m = __longlong_as_double((long long)sc->dtmin_d[lane]);
+            for (int o = 16; o > 0; o >>= 1) {
+                double w = __shfl_xor_sync(0xffffffffu, m, o);
+                m = w < m ? w : m;
+            }
+            dt = m < 1.0e37 ? P.courant * m : 0.0;
         }
         if (!(m < 1.0e37)) {
             if (i == 0) atomicOr(&sc->err, ERR_NODT);
-            m = 0.0;
         }
-        dt = P.courant * m;
     }
     if (i == 0) sc->dt = dt;
     if (i >= nsrt) return;
@@ -951,7 +969,14 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
     T th = (T)hdt;
     // displacement over the half step (absolute velocity = frame + stored)
     T ddx = th * (P.ufx + v.x), ddy = th * (P.ufy + v.y);
-    double2 ph = make_double2(p.x + hdt * (P.ufx_d + (double)v.x), p.y + hdt * (P.ufy_d + (double)v.y));
+    double2 ph;
+    if constexpr (sizeof(T) == 4) {
+        // the FP32 increment added to the FP64 position (its rounding,
+        // ~6e-8 of a half-step move, is far below the FP32 pair sums')
+        ph = make_double2(p.x + (double)ddx, p.y + (double)ddy);
+    } else {
+        ph = make_double2(p.x + hdt * (P.ufx_d + (double)v.x), p.y + hdt * (P.ufy_d + (double)v.y));
+    }
     V2<T> vh = v;
     T dh = d;
     if (typ == T_FLUID) {

@@ -157,7 +157,7 @@ def jet_params(Re, We, D=1.0, U=1.0, rho0=1000.0, dx=None, kernel="wendland",
 
 def jet(seed=0, Re=200.0, We=20.0, D=1.0, U=1.0, rho0=1000.0, dx=None,
         length=60.0, kernel="wendland", prec="fp32", amp=0.01, layers=3,
-        fill=None, capacity_factor=1.3, Fr=None, drho=0.0, nozzle=0.0):
+        fill=None, capacity_factor=1.3, Fr=None, drho=0.0, nozzle=0.0, tank=0.0):
     """Planar jet of width D issuing at x = 0 along +x (Sec. 3-2 setting,
     inflow buffer in place of the paper's tank).  The strip [0, fill*D) is
     prefilled on a dx lattice with u = u_in(-x/U), the velocity the inflow
@@ -170,7 +170,14 @@ def jet(seed=0, Re=200.0, We=20.0, D=1.0, U=1.0, rho0=1000.0, dx=None,
     repulsive boundary particles (Eq. 29) at y = +-D/2, spacing dx/2, normals
     into the channel; the inflow buffer then enters at the nozzle inlet
     x = -nozzle D and the channel is prefilled like the strip (the paper's
-    jets leave a tank through a nozzle of aspect ratio 15)."""
+    jets leave a tank through a nozzle of aspect ratio 15).  tank > 1 (with
+    nozzle > 0) widens that channel into a reservoir of width tank D closed
+    by an orifice plate at x = 0 with an opening of width D (Sec. 3-2: the
+    jet leaves a particle-filled tank through an orifice; aspect ratio =
+    tank height / orifice width): side walls at y = +-tank D/2, the plate's
+    two parts facing upstream, diagonal normals at the inner corners and at
+    the orifice edges; the inflow then spans the tank width at U / tank (the
+    orifice's mass flux) and the tank is prefilled at that speed."""
     rng = np.random.default_rng(seed)
     p = jet_params(Re, We, D=D, U=U, rho0=rho0, dx=dx, kernel=kernel, prec=prec,
                    length=length, layers=layers)
@@ -183,26 +190,56 @@ def jet(seed=0, Re=200.0, We=20.0, D=1.0, U=1.0, rho0=1000.0, dx=None,
     x0 = -nozzle * D
     if nozzle > 0:
         p["xmin"] = x0 - (layers + 5) * dx
+    W = tank * D if (tank > 1.0 and nozzle > 0) else D
+    if W > D:
+        p["ymin"] = min(p["ymin"], -0.5 * W - 5 * dx)
+        p["ymax"] = max(p["ymax"], 0.5 * W + 5 * dx)
     # whole lattice columns inside [x0, fill): the last column centre stays
     # below the box end even when fill is not a whole number of spacings
-    nxp = int(math.floor((fill * D - x0) / dx + 1e-6))
     nyp = int(round(D / dx))
-    x, y = lattice(x0, -0.5 * D, nxp, nyp, dx)
-    u = U * (1.0 + amp * np.sin(k * U * (-x / U) + phase))
+    if W > D:
+        # the tank [x0, 0) x [-W/2, W/2) at U D / W, then the strip [0, fill)
+        nxt = int(math.floor(-x0 / dx + 1e-6))
+        nyt = int(round(W / dx))
+        xt, yt = lattice(x0, -0.5 * W, nxt, nyt, dx)
+        nxs = int(math.floor(fill * D / dx + 1e-6))
+        xs_, ys_ = lattice(x0 + nxt * dx, -0.5 * D, nxs, nyp, dx)
+        x, y = np.concatenate([xt, xs_]), np.concatenate([yt, ys_])
+        u = np.concatenate([np.full(len(xt), U * D / W),
+                            U * (1.0 + amp * np.sin(k * U * (-xs_ / U) + phase))])
+        n_layer = nyt
+    else:
+        nxp = int(math.floor((fill * D - x0) / dx + 1e-6))
+        x, y = lattice(x0, -0.5 * D, nxp, nyp, dx)
+        u = U * (1.0 + amp * np.sin(k * U * (-x / U) + phase))
+        n_layer = nyp
     rho = rho0 * (1.0 + rng.uniform(-drho, drho, len(x))) if drho > 0 else None
     fluid = _fluid(x, y, u=u, rho=rho, rho0=rho0, dx=dx)
-    p["capacity"] = int(capacity_factor * (len(x) + layers * nyp)) + 1024
-    inflow = dict(x_exit=x0, y0=-0.5 * D, y1=0.5 * D, U=U, amp=amp, k=k, phase=phase,
+    p["capacity"] = int(capacity_factor * (len(x) + layers * n_layer)) + 1024
+    inflow = dict(x_exit=x0, y0=-0.5 * W, y1=0.5 * W, U=U * D / W, amp=amp, k=k, phase=phase,
                   layers=layers)
     boundary = None
-    if nozzle > 0:
+    if W > D:
+        db = 0.5 * dx
+        s2 = 1.0 / math.sqrt(2.0)
+        pts = [_segment((x0, 0.5 * W), (-db, 0.5 * W), db, (0.0, -1.0)),       # side walls
+               _segment((x0, -0.5 * W), (-db, -0.5 * W), db, (0.0, 1.0)),
+               _segment((0.0, 0.5 * D + db), (0.0, 0.5 * W - db), db, (-1.0, 0.0)),   # plate
+               _segment((0.0, -0.5 * W + db), (0.0, -0.5 * D - db), db, (-1.0, 0.0))]
+        corners = [((0.0, 0.5 * W), (-s2, -s2)), ((0.0, -0.5 * W), (-s2, s2)),   # inner corners
+                   ((0.0, 0.5 * D), (-s2, -s2)), ((0.0, -0.5 * D), (-s2, s2))]   # orifice edges
+        for (cx, cy), (nx_, ny_) in corners:
+            pts.append((np.array([cx]), np.array([cy]), np.array([nx_]), np.array([ny_])))
+        boundary = {"x": np.concatenate([q[0] for q in pts]), "y": np.concatenate([q[1] for q in pts]),
+                    "nx": np.concatenate([q[2] for q in pts]), "ny": np.concatenate([q[3] for q in pts])}
+    elif nozzle > 0:
         db = 0.5 * dx
         top = _segment((x0, 0.5 * D), (0.0, 0.5 * D), db, (0.0, -1.0))
         bot = _segment((x0, -0.5 * D), (0.0, -0.5 * D), db, (0.0, 1.0))
         boundary = {"x": np.concatenate([top[0], bot[0]]), "y": np.concatenate([top[1], bot[1]]),
                     "nx": np.concatenate([top[2], bot[2]]), "ny": np.concatenate([top[3], bot[3]])}
     return {"name": "jet", "params": p, "fluid": fluid, "boundary": boundary, "inflow": inflow,
-            "D": D, "nozzle": nozzle * D}
+            "D": D, "nozzle": nozzle * D, "tank": W}
 
 
 # --------------------------------------------------------------------------

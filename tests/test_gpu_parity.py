@@ -530,6 +530,22 @@ def test_nozzle_jet_trajectory(sph, orc, prec, nozzle, dx):
     _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4, rho0=osim.d.rho0)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_tank_jet_trajectory(sph, orc, prec):
+    # the jet of Sec. 3-2 leaving a tank (width 4 D, aspect ratio 15)
+    # through an orifice plate: wide inflow, side walls, plate, inner and
+    # orifice-edge corners (Eq. 29), the contraction into the free jet
+    case = wl.jet(seed=9, dx=1.0 / 10, length=4.0, nozzle=15.0, tank=4.0, Re=200, We=20,
+                  prec=prec)
+    case["params"]["dt_fixed"] = 1e-3
+    sim = sph.Simulation(case)
+    osim = oracle_sim(orc, case)
+    sim.run(80)
+    osim.run(80)
+    assert sim.time()["deleted"] == osim.deleted
+    _compare_states(sim.state(), osim.st, prec, 1e-4, 1e-4, 1e-4, rho0=osim.d.rho0)
+
+
 def test_inviscid_jet_trajectory(sph, orc):
     # alpha = 0: the inviscid setting of the paper's Fig. 8 comparison
     case = wl.jet(seed=8, dx=1.0 / 20, length=6.0, Re=200, We=20)

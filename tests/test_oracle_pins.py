@@ -642,3 +642,31 @@ def test_nozzle_walls_confine_the_jet(orc):
     assert inside.sum() > 100
     assert np.all(np.abs(st["y"][inside]) < 0.5)
     assert np.all(np.isfinite(st["u"]))
+
+
+def test_tank_orifice_confines_and_feeds_the_jet(orc):
+    # the tank of Sec. 3-2: a reservoir of width 4 D and length (aspect ratio)
+    # 15 D closed by an orifice plate; the repulsive walls (Eq. 29) keep the
+    # fluid inside the tank, and what passes the plate passes through the
+    # opening |y| < D/2 and leaves at about the orifice speed (mass flux U D
+    # through the tank width: U / 4 upstream)
+    case = wl.jet(seed=4, dx=1.0 / 10, length=3.0, nozzle=15.0, tank=4.0, Re=200, We=20)
+    case["params"]["dt_fixed"] = 2e-3
+    sim = orc.OracleSim(case["params"], case["fluid"], case["boundary"])
+    inf = case["inflow"]
+    assert inf["U"] == pytest.approx(0.25) and inf["y1"] - inf["y0"] == pytest.approx(4.0)
+    sim.add_inflow(inf["x_exit"], inf["y0"], inf["y1"], inf["U"], inf["amp"], inf["k"],
+                   inf["phase"], inf["layers"])
+    sim.run(150)
+    st = sim.st
+    fl = st["type"] == 0
+    x, y = st["x"][fl], st["y"][fl]
+    assert np.all(np.isfinite(st["u"]))
+    in_tank = (x > -15.0 + 0.1) & (x < -0.05)
+    assert in_tank.sum() > 4000
+    assert np.all(np.abs(y[in_tank]) < 2.0)                  # side walls
+    past_plate = (x > 0.02) & (x < 0.3)                      # downstream of the plate plane
+    assert past_plate.sum() > 10
+    assert np.all(np.abs(y[past_plate]) < 0.5 + 0.05)        # through the opening only
+    jet = fl & (st["x"] > 0.5) & (st["x"] < 2.5)
+    assert np.median(st["u"][jet]) > 0.5                     # the orifice accelerates the flow

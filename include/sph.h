@@ -485,6 +485,15 @@ sph_status sph_mpnn_backward(sph_mpnn *net, sph_ctx *ctx, double u_ref, const fl
 /* One Adam update (beta 0.9 / 0.999, eps 1e-8) from the last gradients. */
 sph_status sph_mpnn_adam(sph_mpnn *net, double lr);
 
+/* Test hook for the bounded waits of the tensor-core inference pass: with
+ * on != 0 the following passes issue no operand loads, so every mbarrier
+ * wait of the layer kernels runs out (after about a second each), the
+ * kernels record ERR_TIMEOUT in the context's error word, free their tensor
+ * memory and return; sph_mpnn_forward and sph_surrogate_step then report
+ * SPH_ERR_TIMEOUT (the context keeps the error: make a new one).  No GPU
+ * fault or hang is involved.  on = 0 restores normal passes. */
+sph_status sph_mpnn_inject_stall(sph_mpnn *net, int on);
+
 /* One surrogate step of length dT = k dt (dt from Eq. 32 at the current
  * state, or dt_fixed), with plain SPH as judge and fallback:
  *   1. evaluate SPH at the current state (a_n, drho/dt_n) -- or take the

@@ -116,6 +116,7 @@ _SIGS = {
     "sph_mpnn_backward": ([ctypes.c_void_p, _CTX, ctypes.c_double, _F32, ctypes.c_longlong, _D],
                           ctypes.c_int),
     "sph_mpnn_adam": ([ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
+    "sph_mpnn_inject_stall": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "sph_surrogate_step": ([_CTX, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                             ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D,
                             _D], ctypes.c_int),
@@ -691,6 +692,12 @@ def sph_mpnn_backward(net, ctx, u_ref, target):
 
 def sph_mpnn_adam(net, lr):
     _mp_check(net, lib().sph_mpnn_adam(net, float(lr)))
+
+
+def sph_mpnn_inject_stall(net, on):
+    """Test hook: the following inference passes issue no operand loads, so
+    their bounded waits run out and the calls report SPH_ERR_TIMEOUT."""
+    _mp_check(net, lib().sph_mpnn_inject_stall(net, int(bool(on))))
 
 
 def sph_surrogate_batch(ctxs, net, k, u_ref, a_ref, threshold, bf16=True):

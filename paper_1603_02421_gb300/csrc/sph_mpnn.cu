@@ -368,6 +368,7 @@ struct sph_mpnn {
     __nv_bfloat16 *u_img = nullptr, *pi_img = nullptr;
     bool img_stale = true;
     MpScratchHandle *fast = nullptr;
+    int stall = 0;                   // sph_mpnn_inject_stall
     // activations (capacity rows)
     float *x = nullptr, *pre_in = nullptr, *h[MP_L + 1] = {}, *z[MP_L] = {}, *g[MP_L] = {},
           *pre[MP_L] = {}, *y = nullptr;
@@ -581,7 +582,8 @@ sph_status mp_fast(sph_mpnn *net, const CtxView &v, float inv_uref, MpScratchHan
         MCK(net, cudaStreamSynchronize(v.stream), "weight images");
         net->img_stale = false;
     }
-    MCK(net, tc_forward(v, inv_uref, net->param, net->u_img, net->pi_img, h->s, v.err),
+    MCK(net, tc_forward(v, inv_uref, net->param, net->u_img, net->pi_img, h->s, v.err,
+                        net->stall),
         "tensor-core forward");
     return SPH_OK;
 }
@@ -770,7 +772,11 @@ sph_status sph_mpnn_forward(sph_mpnn *net, sph_ctx *ctx, double u_ref, int bf16,
         MCK(net, cudaMemcpyAsync(y, dev_y, (size_t)v.n * 8, cudaMemcpyDeviceToHost, v.stream), "outputs");
         MCK(net, cudaMemcpyAsync(id, v.id, (size_t)v.n * 4, cudaMemcpyDeviceToHost, v.stream), "ids");
     }
+    unsigned err = 0;
+    if (bf16) MCK(net, cudaMemcpyAsync(&err, v.err, sizeof err, cudaMemcpyDeviceToHost, v.stream), "error word");
     MCK(net, cudaStreamSynchronize(v.stream), "synchronize");
+    if (err & ERR_TIMEOUT)
+        return mp_fail(net, SPH_ERR_TIMEOUT, "a bounded wait of the inference pass ran out");
     return SPH_OK;
 }
 
@@ -797,6 +803,12 @@ sph_status sph_mpnn_backward(sph_mpnn *net, sph_ctx *ctx, double u_ref, const fl
     MCK(net, cudaStreamSynchronize(st), "synchronize");
     if (loss) *loss = l;
     if (!std::isfinite(l)) return mp_fail(net, SPH_ERR_NONFINITE, "non-finite loss");
+    return SPH_OK;
+}
+
+sph_status sph_mpnn_inject_stall(sph_mpnn *net, int on) {
+    if (!net) return SPH_ERR_ARG;
+    net->stall = on != 0;
     return SPH_OK;
 }
 

@@ -121,8 +121,9 @@ void tc_weight_images(const float *param, __nv_bfloat16 *u_img, __nv_bfloat16 *p
 // scr.y.  Five launches: the edge records, the input layer with the first
 // messages, the three message-passing layers.  err (the context's sticky
 // error word) receives ERR_TIMEOUT if a bounded wait ran out.
+// stall != 0: the test hook of sph_mpnn_inject_stall (no operand loads).
 cudaError_t tc_forward(const CtxView &v, float inv_uref, const float *param,
                        const __nv_bfloat16 *u_img, const __nv_bfloat16 *pi_img,
-                       const MpScratch &scr, unsigned *err);
+                       const MpScratch &scr, unsigned *err, int stall = 0);
 
 }  // namespace mpnn

@@ -282,6 +282,7 @@ struct TcArgs {
     __nv_bfloat16 *zout;
     float2 *y;
     unsigned *err;
+    int stall;                      // test hook: issue no operand loads
 };
 
 // Edge records of particle a: every pair closer than 2h as {b, (w0, w1),
@@ -648,7 +649,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 mbar_arrive(bar_full(b));
             }
         };
-        for (int i = 0; ok && i < my_tiles && i < 2; ++i) load(i);
+        for (int i = 0; ok && !A.stall && i < my_tiles && i < 2; ++i) load(i);
         for (int i = 0; ok && i < my_tiles; ++i) {
             const int b = i & 1;
             const uint32_t par_u = (uint32_t)(i >> 1) & 1u;
@@ -776,7 +777,7 @@ void tc_weight_images(const float *param, __nv_bfloat16 *u_img, __nv_bfloat16 *p
 
 cudaError_t tc_forward(const CtxView &v, float inv_uref, const float *param,
                        const __nv_bfloat16 *u_img, const __nv_bfloat16 *pi_img,
-                       const MpScratch &scr, unsigned *err) {
+                       const MpScratch &scr, unsigned *err, int stall) {
     if (v.n <= 0) return cudaSuccess;
     if (v.n > scr.cap) return cudaErrorInvalidValue;
     EncodeTiled enc = encode_tiled();
@@ -808,6 +809,7 @@ cudaError_t tc_forward(const CtxView &v, float inv_uref, const float *param,
     A.h = scr.h;
     A.y = scr.y;
     A.err = err;
+    A.stall = stall;
     if (v.P.kernel == 1) return forward_k<1>(grid, hmap, A, u_img, pi_img, scr, v.stream);
     return forward_k<0>(grid, hmap, A, u_img, pi_img, scr, v.stream);
 }

@@ -150,6 +150,34 @@ def test_training_lowers_the_loss(sph, evaluated):
     assert losses[-1] < 0.3 * losses[0]
 
 
+def test_layer_kernel_waits_are_bounded(sph):
+    # the stall hook issues no operand loads, so every mbarrier wait of the
+    # tensor-core layer kernels runs out (about a second each): the kernels
+    # record ERR_TIMEOUT, free their tensor memory and return, the call
+    # reports SPH_ERR_TIMEOUT, and the GPU stays usable
+    import time
+    p, st = _drop(5)
+    n = len(st["x"])
+    sim = sph.Simulation({"params": p, "fluid": st, "boundary": None, "inflow": None})
+    sim.evaluate()
+    net = sph.Mpnn(capacity=n + 64)
+    net.set_params(_params(13))
+    sph.sph_mpnn_inject_stall(net.net, 1)
+    t0 = time.time()
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_mpnn_forward(net.net, sim.ctx, 1.0, True, n + 64)
+    assert e.value.status == -6
+    assert time.time() - t0 < 60
+    sph.sph_mpnn_inject_stall(net.net, 0)
+    sim.close()
+    fresh = sph.Simulation({"params": p, "fluid": st, "boundary": None, "inflow": None})
+    fresh.evaluate()
+    ids, y = sph.sph_mpnn_forward(net.net, fresh.ctx, 1.0, True, n + 64)
+    assert len(ids) == n and np.all(np.isfinite(y))
+    net.close()
+    fresh.close()
+
+
 def test_needs_an_evaluated_state(sph):
     p, st = _drop(5)
     sim = sph.Simulation({"params": p, "fluid": st, "boundary": None, "inflow": None})

@@ -471,8 +471,10 @@ sph_status sph_mpnn_features(sph_mpnn *net, sph_ctx *ctx, double u_ref, long lon
                              long long *ne, int *ea, int *eb, float *w);
 
 /* Forward pass: y[2n] for the *n particles (ids to id[]).  bf16 != 0 runs
- * the dense layers on the tensor cores (BF16 operands, FP32 accumulation);
- * otherwise everything is FP32. */
+ * the tensor-core inference pass: tcgen05.mma with BF16 operands and FP32
+ * accumulation for the dense layers, BF16 hidden state and messages, FP16
+ * edge weights, FP32 message sums; otherwise everything is FP32.  A bounded
+ * wait of the tensor-core pass that ran out returns SPH_ERR_TIMEOUT. */
 sph_status sph_mpnn_forward(sph_mpnn *net, sph_ctx *ctx, double u_ref, int bf16, long long cap,
                             long long *n, unsigned *id, float *y);
 

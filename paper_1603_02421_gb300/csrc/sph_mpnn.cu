@@ -13,9 +13,9 @@
 //   for l < 3:  z = h Pi_l;  g_a[32k + j] = sum_b w_k,ab z_b[j];
 //               h = h + relu([h, g] U_l + c_l)
 //   y = h D + d.
-// Training runs in FP32 (SIMT GEMMs, the aggregation and its adjoint, Adam);
-// inference can run its dense layers on the tensor cores in BF16 with FP32
-// accumulation (mma.sync m16n8k16).
+// Training runs in FP32 (SIMT GEMMs, the aggregation and its adjoint, Adam),
+// as does the reference forward here; inference runs on the tensor cores
+// (tcgen05, BF16 operands with FP32 accumulation) in sph_mpnn_tc.cu.
 #include <cuda_bf16.h>
 
 #include <algorithm>

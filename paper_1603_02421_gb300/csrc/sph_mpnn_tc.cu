@@ -10,15 +10,17 @@
 //     messages g_a[32k + j] = sum_b w_k,ab z_b[j] from precomputed edge
 //     records, four threads per particle, straight into the operand tile;
 //   * one thread issues tcgen05.mma (kind::f16, BF16 operands, FP32
-//     accumulators in tensor memory) for [h, g] U_l^T, the warps read the
-//     accumulators back with tcgen05.ld and form h_{l+1} = h_l + relu(. +
+//     accumulators in tensor memory) for [h, g] U_l^T, 8 epilogue warps read
+//     the accumulators back with tcgen05.ld and form h_{l+1} = h_l + relu(. +
 //     c_l), which goes to global memory and, in place, back into the operand
 //     tile; a second tcgen05.mma gives the next layer's messages z = h Pi;
 //   * the last layer forms y = h D + d in the epilogue instead.
-// Before them, one warp per particle writes the edge records (the four
-// weights of every pair closer than 2h, FP16, with the neighbour index), and
-// the first layer launch forms the input layer h_0 = relu(x W_in + b_in) and
-// z_0.
+// The operand tile and the accumulators are double-buffered, so the
+// aggregation of one tile overlaps the MMAs and the epilogue of the one
+// before.  Before the layers, eight lanes per particle write the edge records
+// (the four weights of every pair closer than 2h, FP16, with the neighbour
+// index), and the first layer launch forms the input layer h_0 = relu(x W_in
+// + b_in) and z_0.
 //
 // Operand layout in shared memory (K-major, no swizzle): a matrix of R rows
 // and K columns is stored as K/8 blocks of R x 16 bytes, block b holding

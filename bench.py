@@ -242,14 +242,12 @@ def reference_arm(args):
         desc = "member 0 of the 64-jet ensemble"
     else:
         case, desc = workload(args.workload, seed=0)
-    # the oracle runs ~0.75 M particle-steps/s on one core: size the sample so
-    # that the K steps take about a minute
     from oracle import oracle as orc
     orc.build()
     cores = orc.max_threads()
     orc.set_threads(cores)
-    # the oracle runs ~2e6 particle-steps/s on all cores of a 16-core host:
-    # size the sample so that the K steps take about a minute
+    # the oracle runs ~6e6 particle-steps/s on the 16 cores of the GPU host:
+    # the sample is sized so that the K steps take well under a minute
     budget = 1.2e8 / max(args.steps, 1)
     sample = oracle_sample(case, int(min(24000, max(2000, budget))))
     run_oracle(sample, 0, max_steps=max(args.warmup, 0) or 1)

@@ -1096,6 +1096,27 @@ sph_status sph_run(sph_ctx *c, long long nsteps, int breakup_every, double D, do
     return s;
 }
 
+}  // extern "C"
+
+// Orders the indices in ord by ids[ord[.]] (ids unique): a scatter by id in
+// O(n) when the ids are dense (they are handed out in sequence), else a
+// comparison sort.
+static void order_by_id(std::vector<size_t> &ord, const std::vector<unsigned> &ids) {
+    unsigned max_id = 0;
+    for (size_t i : ord) max_id = std::max(max_id, ids[i]);
+    if (!ord.empty() && (size_t)max_id < 8 * ord.size() + 1024) {
+        std::vector<int64_t> slot((size_t)max_id + 1, -1);
+        for (size_t i : ord) slot[ids[i]] = (int64_t)i;
+        ord.clear();
+        for (int64_t q : slot)
+            if (q >= 0) ord.push_back((size_t)q);
+    } else {
+        std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return ids[a] < ids[b]; });
+    }
+}
+
+extern "C" {
+
 sph_status sph_get_state(sph_ctx *c, long long cap, long long *n_out, double *x, double *y,
                          double *u, double *v, double *rho, double *mass, unsigned char *type,
                          unsigned *id, double *ax, double *ay, double *drho) {
@@ -1123,7 +1144,7 @@ sph_status sph_get_state(sph_ctx *c, long long cap, long long *n_out, double *x,
         ord.reserve(n);
         for (size_t i = 0; i < n; ++i)
             if (ty[i] != T_DEAD) ord.push_back(i);
-        std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return ids[a] < ids[b]; });
+        order_by_id(ord, ids);
         *n_out = (long long)ord.size();
         if ((long long)ord.size() > cap) return fail(c, SPH_ERR_CAPACITY, "%zu particles > cap %lld", ord.size(), cap);
         for (size_t r = 0; r < ord.size(); ++r) {
@@ -1156,10 +1177,21 @@ sph_status sph_set_state(sph_ctx *c, long long n, const double *x, const double 
         if (n > 0 && (!x || !y || !u || !v || !rho || !mass || !type || !id))
             return fail(c, SPH_ERR_ARG, "all arrays are required");
         unsigned maxid = 0;
-        std::vector<unsigned> sid(id, id + n);
-        std::sort(sid.begin(), sid.end());
-        for (long long i = 1; i < n; ++i)
-            if (sid[i] == sid[i - 1]) return fail(c, SPH_ERR_ARG, "duplicate id %u", sid[i]);
+        for (long long i = 0; i < n; ++i) maxid = std::max(maxid, id[i]);
+        // duplicate ids: a mark per id when they are dense, else a sort
+        if (n > 0 && (size_t)maxid < 8 * (size_t)n + 1024) {
+            std::vector<unsigned char> seen((size_t)maxid + 1, 0);
+            for (long long i = 0; i < n; ++i) {
+                if (seen[id[i]]) return fail(c, SPH_ERR_ARG, "duplicate id %u", id[i]);
+                seen[id[i]] = 1;
+            }
+        } else if (n > 0) {
+            std::vector<unsigned> sid(id, id + n);
+            std::sort(sid.begin(), sid.end());
+            for (long long i = 1; i < n; ++i)
+                if (sid[i] == sid[i - 1]) return fail(c, SPH_ERR_ARG, "duplicate id %u", sid[i]);
+        }
+        maxid = 0;
         for (long long i = 0; i < n; ++i) {
             if (type[i] != SPH_FLUID && type[i] != SPH_BUFFER)
                 return fail(c, SPH_ERR_ARG, "particle %lld: set_state takes fluid or buffer particles", i);
@@ -1207,7 +1239,7 @@ sph_status sph_get_csf(sph_ctx *c, long long cap, long long *n_out, unsigned *id
         }
         std::vector<size_t> ord(n);
         std::iota(ord.begin(), ord.end(), 0);
-        std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return ids[a] < ids[b]; });
+        order_by_id(ord, ids);
         for (size_t r = 0; r < n; ++r) {
             size_t i = ord[r];
             if (id) id[r] = ids[i];
@@ -1296,7 +1328,7 @@ static sph_status live_order(sph_ctx *c, std::vector<size_t> &ord, std::vector<u
     ord.clear();
     for (size_t i = 0; i < n; ++i)
         if (ty[i] != T_DEAD) ord.push_back(i);
-    std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return ids[a] < ids[b]; });
+    order_by_id(ord, ids);
     return SPH_OK;
 }
 

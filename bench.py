@@ -969,7 +969,6 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
     plain_s = e0.elapsed_time(e1) / 1e3
     L_plain = [binding.sph_breakup_length(sm.ctx)[0] for sm in sims]
     plain_value, _, _ = reduce_rate(plain_s, n0 * K, dist, dev)
-    ens.close()
     t_plain = [sm.time()["t"] - t0_ for sm, t0_ in zip(sims, t_start)]
 
     # ---- surrogate arm: the same members from the same states (the state
@@ -981,17 +980,19 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
     net = binding.Mpnn(cap, local)
     net.set_params(params)
     clocks = ClockSampler(local)
-    accepted = steps = 0
+    accepted = steps = rejected_lists = 0
     rms, rds, rfs = [], [], []
     ctxs = [sm.ctx for sm in sims]
     builds0 = sum(binding.sph_get_rebuild_stats(c)[0] for c in ctxs)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(K // SUR_K):
-        ok, rm, rd, rf = binding.sph_surrogate_batch(ctxs, net.net, SUR_K, 1.0, a_ref,
-                                                     args.threshold, True)
+        ok, rm, rd, rf = ens.surrogate_step(net.net, SUR_K, 1.0, a_ref, args.threshold)
         accepted += int(ok.sum())
         steps += len(ctxs)
+        # rejected with both residuals within the threshold: the particles
+        # moved too far for the start's neighbour lists
+        rejected_lists += int(np.sum(~ok & (rm <= args.threshold) & (rd <= args.threshold)))
         rms.extend(rm.tolist())
         rds.extend(rd.tolist())
         rfs.extend(rf.tolist())
@@ -1018,9 +1019,10 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
     for sm, st in zip(sims, pinned):
         binding.sph_set_state(sm.ctx, st)
     for _ in range(Ke):
-        binding.sph_surrogate_batch(ctxs, net.net, SUR_K, 1.0, a_ref, args.threshold, True)
+        ens.surrogate_step(net.net, SUR_K, 1.0, a_ref, args.threshold)
     for sm in sims:
         binding.sph_get_state(sm.ctx)
+    ens.close()
     e2e_s = time.perf_counter() - t0
     e2e_value, _, _ = reduce_rate(e2e_s, n0 * Ke * SUR_K, dist, dev)
     h2d = n0 * (16 + 8 + 4 + 4 + 4 + 1 + 4)
@@ -1052,6 +1054,8 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
                        "k_substeps": SUR_K, "threshold": args.threshold,
                        "surrogate_steps": steps, "accepted": accepted,
                        "fresh_starts": fresh_starts,
+                       "rejected_by_residual": steps - accepted - rejected_lists,
+                       "rejected_by_lists": rejected_lists,
                        "acceptance_rate": accepted / max(steps, 1),
                        "residual_median": {
                            "momentum": float(np.median(rms)) if rms else None,
@@ -1082,9 +1086,9 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / (Ke * SUR_K),
                     "d2h_bytes_per_step": d2h / (Ke * SUR_K),
-                    "how": "sph_set_state of every member from pinned host arrays, %d batched "
-                           "surrogate steps of %d substeps, sph_get_state of every member; host "
-                           "wall clock" % (Ke, SUR_K)},
+                    "how": "sph_set_state of every member from pinned host arrays, %d "
+                           "ensemble surrogate steps of %d substeps, sph_get_state of every "
+                           "member; host wall clock" % (Ke, SUR_K)},
             "gpu_launches": launches,
             "clocks": clk,
         }

@@ -542,6 +542,16 @@ sph_status sph_surrogate_batch(sph_ctx *const *ctx, int m, sph_mpnn *net, int k,
                                double *res_momentum, double *res_density, double *res_field,
                                int *bad_member);
 
+/* One surrogate step of every member (the ensemble's batched surrogate
+ * form): waits for the enqueued ensemble steps, then sph_surrogate_batch over
+ * the members in order (arrays of the member count, nullable); plain
+ * ensemble steps after it rebuild the members' lists first.  Errors as
+ * sph_surrogate_batch, *bad_member naming the member. */
+sph_status sph_ensemble_surrogate_step(sph_ensemble *e, sph_mpnn *net, int k, double u_ref,
+                                       double a_ref, double threshold, int bf16, int *accepted,
+                                       double *res_momentum, double *res_density,
+                                       double *res_field, int *bad_member);
+
 #ifdef __cplusplus
 }
 #endif

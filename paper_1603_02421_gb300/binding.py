@@ -97,6 +97,10 @@ _SIGS = {
                              ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "sph_ensemble_run": ([ctypes.c_void_p, ctypes.c_longlong], ctypes.c_int),
     "sph_ensemble_sync": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "sph_ensemble_surrogate_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, _D, _D,
+                                     ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sph_ensemble_autotune": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                ctypes.POINTER(ctypes.c_int), _D], ctypes.c_int),
     "sph_ensemble_destroy": ([ctypes.c_void_p], None),
@@ -563,6 +567,20 @@ def sph_ensemble_sync(ens):
     _ens_check(ens, st, bad.value)
 
 
+def sph_ensemble_surrogate_step(ens, m, net, k, u_ref, a_ref, threshold, bf16=True):
+    """One surrogate step of each of the m members (sph_surrogate_batch over
+    the ensemble); returns (accepted, momentum, density, field residuals) as
+    numpy arrays of m."""
+    acc = (ctypes.c_int * max(m, 1))()
+    rm, rd, rf = (np.zeros(max(m, 1)) for _ in range(3))
+    bad = ctypes.c_int(-1)
+    st = lib().sph_ensemble_surrogate_step(ens, net, int(k), float(u_ref), float(a_ref),
+                                           float(threshold), int(bool(bf16)), acc, _d(rm),
+                                           _d(rd), _d(rf), ctypes.byref(bad))
+    _ens_check(ens, st, bad.value)
+    return (np.array([bool(acc[i]) for i in range(m)]), rm[:m], rd[:m], rf[:m])
+
+
 def sph_ensemble_autotune(ens, trial_steps=16):
     a, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _ens_check(ens, lib().sph_ensemble_autotune(ens, int(trial_steps), ctypes.byref(a),
@@ -596,6 +614,11 @@ class Ensemble:
 
     def autotune(self, trial_steps=16):
         return sph_ensemble_autotune(self.ens, trial_steps)
+
+    def surrogate_step(self, net, k, u_ref, a_ref, threshold, bf16=True):
+        """One surrogate step of every member; (accepted, residuals...)."""
+        return sph_ensemble_surrogate_step(self.ens, len(self.sims), net, k, u_ref, a_ref,
+                                           threshold, bf16)
 
     def close(self):
         if getattr(self, "ens", None):

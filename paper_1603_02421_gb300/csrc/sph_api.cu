@@ -2157,6 +2157,24 @@ sph_status sph_ensemble_sync(sph_ensemble *e, int *bad_member) {
     return SPH_OK;
 }
 
+sph_status sph_ensemble_surrogate_step(sph_ensemble *e, sph_mpnn *net, int k, double u_ref,
+                                       double a_ref, double threshold, int bf16, int *accepted,
+                                       double *res_momentum, double *res_density,
+                                       double *res_field, int *bad_member) {
+    if (bad_member) *bad_member = -1;
+    if (!e) return SPH_ERR_ARG;
+    sph_status s = sph_ensemble_sync(e, bad_member);
+    if (s) return s;
+    s = sph_surrogate_batch(e->m.data(), (int)e->m.size(), net, k, u_ref, a_ref, threshold, bf16,
+                            accepted, res_momentum, res_density, res_field, bad_member);
+    if (s) {
+        int b = bad_member ? *bad_member : -1;
+        return ens_fail(e, s, "member %d: %s", b,
+                        b >= 0 && b < (int)e->m.size() ? e->m[b]->err.c_str() : "");
+    }
+    return SPH_OK;
+}
+
 sph_status sph_ensemble_autotune(sph_ensemble *e, int trial_steps, int *lanes, int *cadence,
                                  double *ms_per_step) {
     if (!e) return SPH_ERR_ARG;

@@ -360,6 +360,47 @@ def test_batched_steps_equal_single_steps(sph):
         sim.close()
 
 
+def test_ensemble_surrogate_step_and_plain_steps_after_it(sph):
+    # the ensemble's batched surrogate form: sph_ensemble_surrogate_step on
+    # two members equals sph_surrogate_batch on twin contexts, and plain
+    # ensemble steps continue from the surrogate's states (rebuilding first)
+    def jet(seed):
+        c = wl.jet(seed=seed, dx=1.0 / 20, length=6.0, Re=200, We=20)
+        c["params"]["skin_over_h"] = 0.3
+        return c
+
+    cases = [jet(14), jet(15)]
+    ens_sims = [sph.Simulation(c) for c in cases]
+    twins = [sph.Simulation(c) for c in cases]
+    for sim in ens_sims + twins:
+        sim.set_tuning(2, 8)
+    ens = sph.Ensemble(ens_sims)
+    ens.run(2)
+    for sim in twins:
+        sim.run(2)
+    net = sph.Mpnn(capacity=max(c["params"]["capacity"] for c in cases))
+    net.set_params(_params(16))
+    acc, rm, rd, rf = ens.surrogate_step(net.net, 4, 1.0, 0.1, 1e30)
+    acc2, rm2, rd2, rf2 = sph.sph_surrogate_batch([s.ctx for s in twins], net.net, 4, 1.0, 0.1,
+                                                   1e30)
+    assert acc.all() and acc2.all()
+    assert np.allclose(rm, rm2, rtol=1e-6) and np.allclose(rd, rd2, rtol=1e-6, atol=1e-15)
+    ens.run(3)
+    for sim in twins:
+        sim.run(3)
+    for a, b in zip(ens_sims, twins):
+        assert a.time()["t"] == pytest.approx(b.time()["t"], rel=1e-12)
+        sa, sb = _by_id(a.state()), _by_id(b.state())
+        assert np.array_equal(sa["id"], sb["id"])
+        assert np.all(np.isfinite(sa["u"]))
+        assert np.max(np.abs(sa["x"] - sb["x"])) < 1e-9
+        assert rel_l2(sa["u"], sb["u"]) < 1e-6
+    ens.close()
+    net.close()
+    for sim in ens_sims + twins:
+        sim.close()
+
+
 def test_trained_network_beats_the_instantaneous_acceleration(sph):
     # what the network gains: the k-step mean acceleration it predicts on
     # jets with (Re, We) it was not trained on is closer to the truth (k plain

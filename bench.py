@@ -373,9 +373,11 @@ def main():
     case["params"]["skin_over_h"] = args.skin
     line, sim = bench_plain(args, binding, dist, dev, rank, world, local, case, desc)
     sim.close()
-    if rank == 0 and args.workload == "jet_c3" and not args.no_ensemble:
+    if world == 1 and args.workload == "jet_c3" and not args.no_ensemble:
         # the metric compares plain with batched: the 64-jet ensemble of the
         # paper's Re x We sweeps, batched and member by member, beside it
+        # (one GPU only: with N > 1 the other GPUs would idle meanwhile; the
+        # ensemble's own scaling run is --workload ensemble_c4)
         ens = bench_ensemble(args, binding, None, dev, 0, 1, local, steps=args.ensemble_steps,
                              emit=False, cpu=False)
         line["batched_c4"] = {k: ens[k] for k in ("value", "plain_value", "batched_over_plain",

@@ -534,9 +534,11 @@ sph_status sph_surrogate_step(sph_ctx *ctx, sph_mpnn *net, int k, double u_ref, 
  * cannot reuse its last evaluation), not m.  accepted, res_momentum,
  * res_density and res_field are arrays of m (each nullable); the contexts
  * may share a stream; all use the one network (read-only here).  On an
- * error *bad_member (nullable) names the context that failed; the contexts
- * before it have completed their step, those after it may have a step in
- * progress (call sph_sync on each before using them). */
+ * error *bad_member (nullable) names the context that failed.  Argument
+ * errors (a NULL network, an FP64 context, summation density, k or the
+ * scalars out of range) are found before any context is touched; after a
+ * later error the contexts' steps may be incomplete: call sph_sync on each
+ * before using them. */
 sph_status sph_surrogate_batch(sph_ctx *const *ctx, int m, sph_mpnn *net, int k, double u_ref,
                                double a_ref, double threshold, int bf16, int *accepted,
                                double *res_momentum, double *res_density, double *res_field,

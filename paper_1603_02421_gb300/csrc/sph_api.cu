@@ -1967,8 +1967,13 @@ sph_status sph_surrogate_batch(sph_ctx *const *ctx, int m, sph_mpnn *net, int k,
         return s;
     };
     std::vector<char> pull(m, 0), replay(m, 0);
+    // argument errors before any member is touched
     for (int i = 0; i < m; ++i) {
         if (accepted) accepted[i] = 0;
+        sph_status s = sg_check(ctx[i], g);
+        if (s) return bad(i, s);
+    }
+    for (int i = 0; i < m; ++i) {
         bool p = false;
         sph_status s = sg_begin(ctx[i], g, &p);
         if (s) return bad(i, s);

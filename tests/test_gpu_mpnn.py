@@ -401,6 +401,26 @@ def test_ensemble_surrogate_step_and_plain_steps_after_it(sph):
         sim.close()
 
 
+def test_batch_names_the_failing_member(sph):
+    # an FP64 context cannot take a surrogate step: the batch reports
+    # SPH_ERR_ARG and names it before it touches any member
+    case = wl.jet(seed=17, dx=1.0 / 20, length=6.0, Re=200, We=20)
+    a = sph.Simulation(case)
+    b = sph.Simulation(wl.jet(seed=18, dx=1.0 / 20, length=6.0, Re=200, We=20, prec="fp64"))
+    a.run(2)
+    b.run(2)
+    net = sph.Mpnn(capacity=case["params"]["capacity"])
+    net.set_params(_params(19))
+    t0 = a.time()["t"]
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_surrogate_batch([a.ctx, b.ctx], net.net, 4, 1.0, 0.1, 1e30)
+    assert e.value.status == -1 and "member 1" in str(e.value)
+    assert a.time()["t"] == t0
+    net.close()
+    a.close()
+    b.close()
+
+
 def test_trained_network_beats_the_instantaneous_acceleration(sph):
     # what the network gains: the k-step mean acceleration it predicts on
     # jets with (Re, We) it was not trained on is closer to the truth (k plain

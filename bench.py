@@ -665,7 +665,8 @@ def end_to_end(binding, case, stream, local, K, tuning):
     el = time.perf_counter() - t0
     sim.close()
     h2d = n * (16 + 8 + 4 + 4 + 4 + 1 + 4)
-    d2h_state = len(out["x"]) * (16 + 8 + 4 + 4 + 1 + 4 + 8 + 4)
+    # the state's arrays, plus the types once more for the binding's count query
+    d2h_state = len(out["x"]) * (16 + 8 + 4 + 4 + 1 + 4 + 8 + 4 + 1)
     scal = 736   # bytes of the device scalars read back by each sph_step
     return {"value": psteps / el, "unit": UNIT,
             "h2d_bytes_per_step": h2d / K,

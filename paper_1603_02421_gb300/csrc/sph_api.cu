@@ -12,6 +12,7 @@
 #include <map>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "sph.h"
@@ -67,6 +68,11 @@ struct sph_ctx {
 
     // host-side boundary particles (static)
     std::vector<double> bx, by, bnx, bny;
+
+    // pinned host staging of state transfers (sized for the capacity on
+    // first use, kept until the context is destroyed)
+    unsigned char *pin = nullptr;
+    size_t pin_bytes = 0;
 
     // derivative rows valid for raw[0, n_eval)
     long long n_eval = 0;
@@ -387,7 +393,7 @@ static void enqueue_eval(sph_ctx *c, const Hot<T> &hot, int mode, bool skip,
     tick(c, mode == 2 ? "pairsum_correct" : "pairsum");
     cudaMemsetAsync(c->crange, 0xFF, (size_t)c->grid.ncells * sizeof(uint2), c->stream);
     launch_pairsum<T>(c->lanes, P, c->grid, c->sc, c->nl, key, hot, csf_of<T>(c), bd_of(c),
-                      srt.type, accN, gsum, c->crange, c->cap, c->stream);
+                      srt.type, accN, gsum, c->crange, c->cap, c->stream, mode == 1);
     tick(c, "normal");
     launch_normal<T>(c->lanes, P, c->sc, c->nl, hot, csf_of<T>(c), c->cap, c->stream, key,
                      skip ? gsum : nullptr, c->crange, c->grid.ncx);
@@ -582,38 +588,112 @@ static sph_status upload_boundary(sph_ctx *c) {
 }
 
 // Upload n particles into raw[at, at+n).
+// Runs f(lo, hi) over [0, n) in up to 8 host threads of at least `grain`
+// items each (a million-particle state crosses the ABI in milliseconds); f
+// must not throw.
+// A chunk whose thread cannot be started runs on the calling thread.
+template <class F> static void host_for(size_t n, F &&f, size_t grain = (size_t)1 << 16) {
+    unsigned hw = std::thread::hardware_concurrency();
+    size_t nt = std::min<size_t>(std::min<size_t>(hw ? hw : 1u, 8u), (n + grain - 1) / grain);
+    if (nt <= 1) {
+        f((size_t)0, n);
+        return;
+    }
+    size_t chunk = (n + nt - 1) / nt;
+    std::vector<std::thread> th;
+    th.reserve(nt);
+    for (size_t k = 1; k < nt; ++k) {
+        size_t lo = k * chunk, hi = std::min(n, lo + chunk);
+        if (lo >= hi) continue;
+        try {
+            th.emplace_back([&f, lo, hi] { f(lo, hi); });
+        } catch (...) {
+            f(lo, hi);
+        }
+    }
+    f((size_t)0, std::min(n, chunk));
+    for (auto &t : th) t.join();
+}
+
+static size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Bytes of pinned staging one particle needs in a state transfer: position,
+// velocity, density, mass, type, id, acceleration, density rate (each array
+// padded to 16 bytes).
+static size_t staging_bytes(const sph_ctx *c, size_t n) {
+    size_t ts = c->tsz;
+    return al16(n) + al16(16 * n) + 2 * al16(2 * n * ts) + 3 * al16(n * ts) + al16(4 * n);
+}
+
+// The context's pinned staging buffer, at least `bytes` long (grown to the
+// capacity's needs on first use).  Callers synchronise the stream before they
+// return, so no copy from or to it is in flight when it is replaced.
+static unsigned char *staging(sph_ctx *c, size_t bytes, cudaError_t &e) {
+    e = cudaSuccess;
+    if (bytes <= c->pin_bytes) return c->pin;
+    size_t want = std::max(bytes, staging_bytes(c, (size_t)c->cap));
+    if (c->pin) cudaFreeHost(c->pin);
+    c->pin = nullptr;
+    c->pin_bytes = 0;
+    e = cudaMallocHost((void **)&c->pin, want);
+    if (e != cudaSuccess) {
+        c->pin = nullptr;
+        return nullptr;
+    }
+    c->pin_bytes = want;
+    return c->pin;
+}
+
+// Converts n host particles into the device layout in the pinned staging,
+// then one asynchronous copy per array and one wait for all of them.
 static sph_status upload_particles(sph_ctx *c, long long at, long long n, const double *x,
                                    const double *y, const double *u, const double *v,
                                    const double *rho, const double *mass,
                                    const unsigned char *type, const unsigned *id) {
     if (n == 0) return SPH_OK;
-    std::vector<double2> pos(n);
-    for (long long i = 0; i < n; ++i) pos[i] = make_double2(x[i], y[i]);
-    CK(copy_sync(c, (double2 *)c->raw[0] + at, pos.data(), n * sizeof(double2), cudaMemcpyHostToDevice), "upload");
-    size_t ts = c->tsz;
-    std::vector<unsigned char> vel(2 * n * ts), drho(n * ts), zero(n * ts, 0), m(n * ts);
-    for (long long i = 0; i < n; ++i) {
-        double d = rho[i] - c->prm.rho0;
+    const size_t N = (size_t)n, ts = c->tsz;
+    const size_t o_pos = 0, o_vel = al16(16 * N), o_dr = o_vel + al16(2 * N * ts),
+                 o_m = o_dr + al16(N * ts), o_ty = o_m + al16(N * ts), o_id = o_ty + al16(N),
+                 total = o_id + al16(4 * N);
+    cudaError_t e;
+    unsigned char *pin = staging(c, total, e);
+    CK(e, "pinned staging");
+    const double ufx = c->prm.u_frame_x, ufy = c->prm.u_frame_y, rho0 = c->prm.rho0;
+    double2 *pos = (double2 *)(pin + o_pos);
+    host_for(N, [&](size_t lo, size_t hi) {
+        for (size_t i = lo; i < hi; ++i) pos[i] = make_double2(x[i], y[i]);
         if (ts == 4) {
-            float f2[2] = {(float)(u[i] - c->prm.u_frame_x), (float)(v[i] - c->prm.u_frame_y)},
-                  fd = (float)d, fm = (float)mass[i];
-            memcpy(&vel[2 * i * ts], f2, 8);
-            memcpy(&drho[i * ts], &fd, 4);
-            memcpy(&m[i * ts], &fm, 4);
+            float *vel = (float *)(pin + o_vel), *dr = (float *)(pin + o_dr),
+                  *m = (float *)(pin + o_m);
+            for (size_t i = lo; i < hi; ++i) {
+                vel[2 * i] = (float)(u[i] - ufx);
+                vel[2 * i + 1] = (float)(v[i] - ufy);
+                dr[i] = (float)(rho[i] - rho0);
+                m[i] = (float)mass[i];
+            }
         } else {
-            double d2[2] = {u[i] - c->prm.u_frame_x, v[i] - c->prm.u_frame_y};
-            memcpy(&vel[2 * i * ts], d2, 16);
-            memcpy(&drho[i * ts], &d, 8);
-            memcpy(&m[i * ts], &mass[i], 8);
+            double *vel = (double *)(pin + o_vel), *dr = (double *)(pin + o_dr),
+                   *m = (double *)(pin + o_m);
+            for (size_t i = lo; i < hi; ++i) {
+                vel[2 * i] = u[i] - ufx;
+                vel[2 * i + 1] = v[i] - ufy;
+                dr[i] = rho[i] - rho0;
+                m[i] = mass[i];
+            }
         }
-    }
-    CK(copy_sync(c, (char *)c->raw[1] + 2 * at * ts, vel.data(), 2 * n * ts, cudaMemcpyHostToDevice), "upload");
-    CK(copy_sync(c, (char *)c->raw[2] + at * ts, drho.data(), n * ts, cudaMemcpyHostToDevice), "upload");
-    CK(copy_sync(c, (char *)c->raw[3] + at * ts, zero.data(), n * ts, cudaMemcpyHostToDevice), "upload");
-    CK(cudaMemsetAsync((char *)c->raw[7] + 2 * at * ts, 0, 2 * n * ts, c->stream), "upload");
-    CK(copy_sync(c, (char *)c->raw[4] + at * ts, m.data(), n * ts, cudaMemcpyHostToDevice), "upload");
-    CK(copy_sync(c, (uint8_t *)c->raw[5] + at, type, n, cudaMemcpyHostToDevice), "upload");
-    CK(copy_sync(c, (uint32_t *)c->raw[6] + at, id, n * sizeof(unsigned), cudaMemcpyHostToDevice), "upload");
+        memcpy(pin + o_ty + lo, type + lo, hi - lo);
+        memcpy(pin + o_id + 4 * lo, id + lo, 4 * (hi - lo));
+    });
+    const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync((double2 *)c->raw[0] + at, pin + o_pos, 16 * N, h2d, c->stream), "upload");
+    CK(cudaMemcpyAsync((char *)c->raw[1] + 2 * at * ts, pin + o_vel, 2 * N * ts, h2d, c->stream), "upload");
+    CK(cudaMemcpyAsync((char *)c->raw[2] + at * ts, pin + o_dr, N * ts, h2d, c->stream), "upload");
+    CK(cudaMemsetAsync((char *)c->raw[3] + at * ts, 0, N * ts, c->stream), "upload");
+    CK(cudaMemsetAsync((char *)c->raw[7] + 2 * at * ts, 0, 2 * N * ts, c->stream), "upload");
+    CK(cudaMemcpyAsync((char *)c->raw[4] + at * ts, pin + o_m, N * ts, h2d, c->stream), "upload");
+    CK(cudaMemcpyAsync((uint8_t *)c->raw[5] + at, pin + o_ty, N, h2d, c->stream), "upload");
+    CK(cudaMemcpyAsync((uint32_t *)c->raw[6] + at, pin + o_id, 4 * N, h2d, c->stream), "upload");
+    CK(cudaStreamSynchronize(c->stream), "upload");
     return SPH_OK;
 }
 
@@ -774,6 +854,7 @@ void sph_destroy(sph_ctx *c) {
     if (c->cgraph) cudaGraphDestroy(c->cgraph);
     for (auto &b : c->allocs) cudaFree(b.p);
     if (c->hsc) cudaFreeHost(c->hsc);
+    if (c->pin) cudaFreeHost(c->pin);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -1101,12 +1182,15 @@ sph_status sph_run(sph_ctx *c, long long nsteps, int breakup_every, double D, do
 // Orders the indices in ord by ids[ord[.]] (ids unique): a scatter by id in
 // O(n) when the ids are dense (they are handed out in sequence), else a
 // comparison sort.
-static void order_by_id(std::vector<size_t> &ord, const std::vector<unsigned> &ids) {
+static void order_by_id(std::vector<size_t> &ord, const unsigned *ids) {
     unsigned max_id = 0;
     for (size_t i : ord) max_id = std::max(max_id, ids[i]);
     if (!ord.empty() && (size_t)max_id < 8 * ord.size() + 1024) {
         std::vector<int64_t> slot((size_t)max_id + 1, -1);
-        for (size_t i : ord) slot[ids[i]] = (int64_t)i;
+        // distinct ids: the threads write distinct slots
+        host_for(ord.size(), [&](size_t lo, size_t hi) {
+            for (size_t r = lo; r < hi; ++r) slot[ids[ord[r]]] = (int64_t)ord[r];
+        });
         ord.clear();
         for (int64_t q : slot)
             if (q >= 0) ord.push_back((size_t)q);
@@ -1125,43 +1209,65 @@ sph_status sph_get_state(sph_ctx *c, long long cap, long long *n_out, double *x,
         sph_status s = pull_scalars(c);
         if (s) return s;
         if (c->n_eval < 0) c->n_eval = c->hsc->nsrt;
-        size_t n = (size_t)c->hsc->n, ts = c->tsz;
-        std::vector<double2> pos(n);
-        std::vector<unsigned char> vel(2 * n * ts), dr(n * ts), m(n * ts), ac(2 * n * ts), drt(n * ts);
-        std::vector<unsigned char> ty(n);
-        std::vector<unsigned> ids(n);
-        if (n) {
-            CK(copy_sync(c, pos.data(), c->raw[0], n * 16, cudaMemcpyDeviceToHost), "download");
-            CK(copy_sync(c, vel.data(), c->raw[1], 2 * n * ts, cudaMemcpyDeviceToHost), "download");
-            CK(copy_sync(c, dr.data(), c->raw[2], n * ts, cudaMemcpyDeviceToHost), "download");
-            CK(copy_sync(c, m.data(), c->raw[4], n * ts, cudaMemcpyDeviceToHost), "download");
-            CK(copy_sync(c, ty.data(), c->raw[5], n, cudaMemcpyDeviceToHost), "download");
-            CK(copy_sync(c, ids.data(), c->raw[6], n * 4, cudaMemcpyDeviceToHost), "download");
-            CK(copy_sync(c, ac.data(), c->acc, 2 * n * ts, cudaMemcpyDeviceToHost), "download");
-            CK(copy_sync(c, drt.data(), c->dr, n * ts, cudaMemcpyDeviceToHost), "download");
-        }
+        const size_t n = (size_t)c->hsc->n, ts = c->tsz;
+        // pinned staging: type | position | velocity | density | mass | id |
+        // acceleration | density rate
+        const size_t o_ty = 0, o_pos = al16(n), o_vel = o_pos + al16(16 * n),
+                     o_dr = o_vel + al16(2 * n * ts), o_m = o_dr + al16(n * ts),
+                     o_id = o_m + al16(n * ts), o_ac = o_id + al16(4 * n),
+                     o_drt = o_ac + al16(2 * n * ts), total = o_drt + al16(n * ts);
+        cudaError_t e;
+        unsigned char *pin = staging(c, total, e);
+        CK(e, "pinned staging");
+        // the types first: a call that only asks for the count (cap too
+        // small) moves one byte per particle
+        if (n) CK(copy_sync(c, pin + o_ty, c->raw[5], n, cudaMemcpyDeviceToHost), "download");
+        const unsigned char *ty = pin + o_ty;
         std::vector<size_t> ord;
         ord.reserve(n);
         for (size_t i = 0; i < n; ++i)
             if (ty[i] != T_DEAD) ord.push_back(i);
-        order_by_id(ord, ids);
         *n_out = (long long)ord.size();
         if ((long long)ord.size() > cap) return fail(c, SPH_ERR_CAPACITY, "%zu particles > cap %lld", ord.size(), cap);
-        for (size_t r = 0; r < ord.size(); ++r) {
-            size_t i = ord[r];
-            bool has = (long long)i < c->n_eval;
-            if (x) x[r] = pos[i].x;
-            if (y) y[r] = pos[i].y;
-            if (u) u[r] = c->prm.u_frame_x + rd(c, vel, i, 0, 2);
-            if (v) v[r] = c->prm.u_frame_y + rd(c, vel, i, 1, 2);
-            if (rho) rho[r] = c->prm.rho0 + rd(c, dr, i, 0, 1);
-            if (mass) mass[r] = rd(c, m, i, 0, 1);
-            if (type) type[r] = ty[i];
-            if (id) id[r] = ids[i];
-            if (ax) ax[r] = has ? rd(c, ac, i, 0, 2) : 0.0;
-            if (ay) ay[r] = has ? rd(c, ac, i, 1, 2) : 0.0;
-            if (drho) drho[r] = has ? rd(c, drt, i, 0, 1) : 0.0;
-        }
+        if (ord.empty()) return SPH_OK;
+        const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
+        CK(cudaMemcpyAsync(pin + o_pos, c->raw[0], 16 * n, d2h, c->stream), "download");
+        CK(cudaMemcpyAsync(pin + o_vel, c->raw[1], 2 * n * ts, d2h, c->stream), "download");
+        CK(cudaMemcpyAsync(pin + o_dr, c->raw[2], n * ts, d2h, c->stream), "download");
+        CK(cudaMemcpyAsync(pin + o_m, c->raw[4], n * ts, d2h, c->stream), "download");
+        CK(cudaMemcpyAsync(pin + o_id, c->raw[6], 4 * n, d2h, c->stream), "download");
+        CK(cudaMemcpyAsync(pin + o_ac, c->acc, 2 * n * ts, d2h, c->stream), "download");
+        CK(cudaMemcpyAsync(pin + o_drt, c->dr, n * ts, d2h, c->stream), "download");
+        CK(cudaStreamSynchronize(c->stream), "download");
+        const double2 *pos = (const double2 *)(pin + o_pos);
+        const unsigned *ids = (const unsigned *)(pin + o_id);
+        order_by_id(ord, ids);
+        const double ufx = c->prm.u_frame_x, ufy = c->prm.u_frame_y, rho0 = c->prm.rho0;
+        const long long n_eval = c->n_eval;
+        auto convert = [&](auto tag) {
+            using T = decltype(tag);
+            const T *vel = (const T *)(pin + o_vel), *dr = (const T *)(pin + o_dr),
+                    *m = (const T *)(pin + o_m), *ac = (const T *)(pin + o_ac),
+                    *drt = (const T *)(pin + o_drt);
+            host_for(ord.size(), [&](size_t lo, size_t hi) {
+                for (size_t r = lo; r < hi; ++r) {
+                    size_t i = ord[r];
+                    bool has = (long long)i < n_eval;
+                    if (x) x[r] = pos[i].x;
+                    if (y) y[r] = pos[i].y;
+                    if (u) u[r] = ufx + (double)vel[2 * i];
+                    if (v) v[r] = ufy + (double)vel[2 * i + 1];
+                    if (rho) rho[r] = rho0 + (double)dr[i];
+                    if (mass) mass[r] = (double)m[i];
+                    if (type) type[r] = ty[i];
+                    if (id) id[r] = ids[i];
+                    if (ax) ax[r] = has ? (double)ac[2 * i] : 0.0;
+                    if (ay) ay[r] = has ? (double)ac[2 * i + 1] : 0.0;
+                    if (drho) drho[r] = has ? (double)drt[i] : 0.0;
+                }
+            });
+        };
+        if (ts == 4) convert(0.0f); else convert(0.0);
         return SPH_OK;
     } catch (...) {
         return fail(c, SPH_ERR_OOM, "host allocation failed");
@@ -1176,8 +1282,35 @@ sph_status sph_set_state(sph_ctx *c, long long n, const double *x, const double 
         if (n < 0 || n > c->cap) return fail(c, SPH_ERR_CAPACITY, "n = %lld outside [0, capacity]", n);
         if (n > 0 && (!x || !y || !u || !v || !rho || !mass || !type || !id))
             return fail(c, SPH_ERR_ARG, "all arrays are required");
+        // one pass over the particles in a few threads: the largest id and,
+        // per chunk, the first particle that fails a check (type, domain,
+        // density and mass), reported after the duplicate-id test as before
+        const size_t N = n > 0 ? (size_t)n : 0;
+        const size_t nchunk = 64;
+        std::vector<unsigned> cmax(nchunk, 0u);
+        std::vector<long long> cbad(nchunk, -1);
+        std::vector<int> cwhy(nchunk, 0);
+        host_for(nchunk, [&](size_t k0, size_t k1) {
+            for (size_t k = k0; k < k1; ++k) {
+                size_t lo = N * k / nchunk, hi = N * (k + 1) / nchunk;
+                unsigned mx = 0;
+                for (size_t i = lo; i < hi; ++i) {
+                    mx = std::max(mx, id[i]);
+                    if (cbad[k] >= 0) continue;
+                    int why = 0;
+                    if (type[i] != SPH_FLUID && type[i] != SPH_BUFFER) why = 1;
+                    else if (!inside(c, x[i], y[i])) why = 2;
+                    else if (!(rho[i] > 0) || !(mass[i] > 0)) why = 3;
+                    if (why) {
+                        cbad[k] = (long long)i;
+                        cwhy[k] = why;
+                    }
+                }
+                cmax[k] = mx;
+            }
+        }, N >= ((size_t)1 << 16) ? 1 : nchunk);
         unsigned maxid = 0;
-        for (long long i = 0; i < n; ++i) maxid = std::max(maxid, id[i]);
+        for (unsigned m : cmax) maxid = std::max(maxid, m);
         // duplicate ids: a mark per id when they are dense, else a sort
         if (n > 0 && (size_t)maxid < 8 * (size_t)n + 1024) {
             std::vector<unsigned char> seen((size_t)maxid + 1, 0);
@@ -1191,13 +1324,13 @@ sph_status sph_set_state(sph_ctx *c, long long n, const double *x, const double 
             for (long long i = 1; i < n; ++i)
                 if (sid[i] == sid[i - 1]) return fail(c, SPH_ERR_ARG, "duplicate id %u", sid[i]);
         }
-        maxid = 0;
-        for (long long i = 0; i < n; ++i) {
-            if (type[i] != SPH_FLUID && type[i] != SPH_BUFFER)
+        for (size_t k = 0; k < nchunk; ++k) {
+            long long i = cbad[k];
+            if (i < 0) continue;
+            if (cwhy[k] == 1)
                 return fail(c, SPH_ERR_ARG, "particle %lld: set_state takes fluid or buffer particles", i);
-            if (!inside(c, x[i], y[i])) return fail(c, SPH_ERR_ARG, "particle %lld lies outside the domain", i);
-            if (!(rho[i] > 0) || !(mass[i] > 0)) return fail(c, SPH_ERR_ARG, "particle %lld needs rho, mass > 0", i);
-            maxid = std::max(maxid, id[i]);
+            if (cwhy[k] == 2) return fail(c, SPH_ERR_ARG, "particle %lld lies outside the domain", i);
+            return fail(c, SPH_ERR_ARG, "particle %lld needs rho, mass > 0", i);
         }
         sph_status s = pull_scalars(c);
         if (s) return s;
@@ -1239,7 +1372,7 @@ sph_status sph_get_csf(sph_ctx *c, long long cap, long long *n_out, unsigned *id
         }
         std::vector<size_t> ord(n);
         std::iota(ord.begin(), ord.end(), 0);
-        order_by_id(ord, ids);
+        order_by_id(ord, ids.data());
         for (size_t r = 0; r < n; ++r) {
             size_t i = ord[r];
             if (id) id[r] = ids[i];
@@ -1328,7 +1461,7 @@ static sph_status live_order(sph_ctx *c, std::vector<size_t> &ord, std::vector<u
     ord.clear();
     for (size_t i = 0; i < n; ++i)
         if (ty[i] != T_DEAD) ord.push_back(i);
-    order_by_id(ord, ids);
+    order_by_id(ord, ids.data());
     return SPH_OK;
 }
 

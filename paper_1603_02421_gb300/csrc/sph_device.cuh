@@ -329,6 +329,13 @@ __device__ __forceinline__ void for_list(const PhysT<T> &P, const NList &nl,
     }
 }
 
+// p lies in the box [xmin, xmax) x [ymin, ymax) (false for NaN), decided on
+// the ordered integer keys of the coordinates.
+__device__ __forceinline__ bool in_box(const Grid &g, double2 p) {
+    const long long kx = ordered_key(p.x), ky = ordered_key(p.y);
+    return kx >= g.kxmin && kx < g.kxmax && ky >= g.kymin && ky < g.kymax;
+}
+
 template <int G, class T> __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
     for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -15,6 +15,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "sph.h"
 
@@ -46,10 +47,30 @@ struct Grid {
     int ncx, ncy;
     unsigned ncells, sentinel;   // sentinel key sorts after every cell
     int keybits;
+    long long kxmin, kymin, kxmax, kymax;   // ordered_key of the box bounds
 };
+
+// Orders doubles as signed 64-bit integers: for non-NaN a and b, a < b
+// exactly when ordered_key(a) < ordered_key(b) (-0 and +0 share the key 0).
+// A NaN lies above +inf or below -inf by its sign bit, so it passes no
+// two-sided bound test, as it passes no double comparison.  Bound tests on
+// the keys run on the integer pipes instead of the FP64 pipe.
+__host__ __device__ inline long long ordered_key(double d) {
+#ifdef __CUDA_ARCH__
+    long long b = __double_as_longlong(d);
+#else
+    long long b;
+    memcpy(&b, &d, sizeof b);
+#endif
+    return b >= 0 ? b : -(b & 0x7FFFFFFFFFFFFFFFLL);
+}
 
 // Completes a grid whose box, cell size and cell counts are set.
 inline void grid_finish(Grid &g) {
+    g.kxmin = ordered_key(g.xmin);
+    g.kymin = ordered_key(g.ymin);
+    g.kxmax = ordered_key(g.xmax);
+    g.kymax = ordered_key(g.ymax);
     g.ncells = (unsigned)(g.ncx * g.ncy);
     int bits = 1;
     while (((1ull << bits) - 1ull) < (unsigned long long)g.ncells) ++bits;
@@ -284,13 +305,14 @@ void launch_normal(int lanes, const PhysT<T> &P, const Scalars *sc, const NList 
 // With surface tension: the one full list walk of an evaluation -- colour
 // (Eq. 14, to csf.C and csf.CX) and, for fluid particles, the pair sums that
 // need only the state (Eqs. 7, 9, 10, 29, 31) to accN = (ax, ay, drho/dt,
-// max Eq. 31 term); gsum_a = sum_b V_b |grad_a W_ab|; the colour range of
-// each cell to crange (min, ~max as float bits; reset to all ones before).
+// max Eq. 31 term, or 0 unless dt_term: only an evaluation whose end takes
+// the time step needs it); gsum_a = sum_b V_b |grad_a W_ab|; the colour range
+// of each cell to crange (min, ~max as float bits; reset to all ones before).
 template <class T>
 void launch_pairsum(int lanes, const PhysT<T> &P, const Grid &g, const Scalars *sc,
                     const NList &nl, const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf,
                     const Boundary &bd, const uint8_t *type, typename Vec<T>::v4 *accN, T *gsum,
-                    uint2 *crange, int cap, cudaStream_t s);
+                    uint2 *crange, int cap, cudaStream_t s, bool dt_term);
 // With surface tension: curvature (Eq. 23) of the particles with N_a = 1, CSF
 // acceleration (Eq. 24), gravity, and the end of launch_forces' mode (0, 1
 // or 2) from the sums of launch_pairsum.

@@ -466,9 +466,10 @@ __device__ __forceinline__ void wall_forces(const PhysT<T> &P, const Grid &g, co
 
 // ---------------------------------------------------------------------------
 // Pair terms of the momentum and continuity equations for fluid particle a
-// with neighbour b (Eqs. 7, 9, 10) and the Eq. 31 term.
+// with neighbour b (Eqs. 7, 9, 10) and, when DT (an evaluation whose end
+// takes the time step), the Eq. 31 term.
 // ---------------------------------------------------------------------------
-template <class T>
+template <class T, bool DT>
 __device__ __forceinline__ void pair_forces(const PhysT<T> &P, T rx, T ry, T r2, T ri, T F,
                                             T ua, T va, T rhoa, T PAa, T ca, const V4<T> &hb,
                                             const V4<T> &h1b, T &ax, T &ay, T &drho, T &vmax) {
@@ -484,8 +485,10 @@ __device__ __forceinline__ void pair_forces(const PhysT<T> &P, T rx, T ry, T r2,
     T coef = mb * (PAa + h1b.z + Pi) * F;         // Eq. 9 / 25
     ax -= coef * rx;
     ay -= coef * ry;
-    T cv = abs_t(P.h * udotr) * (ri * ri);        // Eq. 31 (0 if r = 0)
-    vmax = cv > vmax ? cv : vmax;
+    if constexpr (DT) {                           // only the time step uses it
+        T cv = abs_t(P.h * udotr) * (ri * ri);    // Eq. 31 (0 if r = 0)
+        vmax = cv > vmax ? cv : vmax;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -574,10 +577,26 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
 
     // MODE 2: corrector X^{n+1} = X^n + dt Xdot^{n+1/2}, positions with
     // u* = u^n + dt/2 a^{n+1/2}; buffer particles follow the inflow velocity.
+    const double dt = sc->dt, t = sc->t;
+    // the step's factors in T: in FP32 lane 0 rounds them and the warp
+    // shares them (FP64 runs at a small fraction of the FP32 rate; every
+    // lane of the warp is here)
+    T th, tdt;
+    if constexpr (sizeof(T) == 4) {
+        float a = 0.0f, b = 0.0f;
+        if ((threadIdx.x & 31u) == 0u) {
+            a = (float)(0.5 * dt);
+            b = (float)dt;
+        }
+        th = __shfl_sync(0xffffffffu, a, 0);
+        tdt = __shfl_sync(0xffffffffu, b, 0);
+    } else {
+        th = 0.5 * dt;
+        tdt = dt;
+    }
     if (!active || sub != 0) return;
     // every load of the particle's state first: the stores below go to
     // arrays the compiler cannot prove distinct from these
-    const double dt = sc->dt, t = sc->t;
     const double2 p0 = srt.pos[i];
     const V2<T> v0 = srt.vel[i];
     const T d0 = srt.drho[i], c0 = srt.drc[i];
@@ -586,7 +605,6 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
     const V4<T> h0n = nH0[i];
     const T rho_half = P.summation ? hot.H1[i].y : T(0);
     V2<T> ds = srt.disp[i];
-    const double half = 0.5 * dt;
     double2 p1 = p0;
     V2<T> v1 = v0;
     T d1 = d0, c1 = c0;
@@ -595,7 +613,6 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
     if (typ == T_DEAD) {
         // deleted since the last cell build: kept as is until it is dropped
     } else if (typ == T_FLUID) {
-        T th = (T)half, tdt = (T)dt;
         T usx = v0.x + th * ax, usy = v0.y + th * ay;
         stx = tdt * (P.ufx + usx);
         sty = tdt * (P.ufy + usy);
@@ -620,6 +637,7 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
         srx = tdt * (P.ufx - P.dfx + usx);
         sry = tdt * (P.ufy - P.dfy + usy);
     } else {
+        const double half = 0.5 * dt;
         double uh = inf.on ? inflow_u(inf, t + half) : P.ufx_d + (double)v0.x;
         p1 = make_double2(p0.x + dt * uh, p0.y);
         v1 = inf.on ? mk2((T)(inflow_u(inf, t + dt) - P.ufx_d), (T)(-P.ufy_d)) : v0;
@@ -628,8 +646,7 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
         srx = (T)(dt * (uh - (double)P.dfx));
     }
     ds = mk2(ds.x + srx, ds.y + sry);
-    if (typ == T_FLUID &&
-        !(p1.x >= g.xmin && p1.x < g.xmax && p1.y >= g.ymin && p1.y < g.ymax)) {
+    if (typ == T_FLUID && !in_box(g, p1)) {
         typ = T_DEAD;
         atomicAdd((unsigned long long *)&sc->deleted, 1ull);
     }
@@ -726,8 +743,8 @@ k_forces(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl,
                 T q, iq, ri;
                 q_of(r2, P.h, P.inv_h, q, iq, ri);
                 T F = kernel_F<T, K>(P, q, iq);
-                pair_forces<T>(P, rx, ry, r2, ri, F, ua, va, rhoa, PAa, ca, r.x, r.h1, ax, ay,
-                               drho, vmax);
+                pair_forces<T, MODE == 1>(P, rx, ry, r2, ri, F, ua, va, rhoa, PAa, ca, r.x, r.h1,
+                                          ax, ay, drho, vmax);
                 if (Na) {                                      // Eq. 23
                     V2<T> nb = r.nb;
                     if (nb.x != T(0) || nb.y != T(0)) {
@@ -784,7 +801,7 @@ __device__ __forceinline__ void colour_bits(double c, unsigned &lo, unsigned &nh
     nhi = ~__float_as_uint(__double2float_ru(c));
 }
 
-template <class T, int K, int G>
+template <class T, int K, int G, bool DT>
 __global__ void __launch_bounds__(SWEEP_BLOCK, SPH_PAIRSUM_MINB)
 k_pairsum(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, NList nl,
           const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf, Boundary bd,
@@ -819,8 +836,8 @@ k_pairsum(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, NList nl,
                 csum += r.h1.x * kernel_W<T, K>(P, q);                 // Eq. 14
                 gs += r.h1.x * abs_t(F) * (r2 * ri);
                 if (fluid)
-                    pair_forces<T>(P, rx, ry, r2, ri, F, ua, va, rhoa, PAa, ca, r.x, r.h1, ax,
-                                   ay, drho, vmax);
+                    pair_forces<T, DT>(P, rx, ry, r2, ri, F, ua, va, rhoa, PAa, ca, r.x, r.h1,
+                                       ax, ay, drho, vmax);
             });
         if (fluid && P.walls) {
             double2 pa = hot.pos[i];
@@ -932,41 +949,46 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
     const T dri = dr[j];
     const T mass = srt.mass[j];
     const V2<T> ds = srt.disp[j];
+    // dt, and the half step th in T; every warp folds the 32 minimum slots
+    // itself (cached loads), so no warp waits for another at a block barrier
+    const int lane = threadIdx.x & 31;
     double dt;
-    if (P.dt_fixed > 0.0) {
-        dt = P.dt_fixed;
-    } else {
-        // every warp folds the 32 minimum slots itself (cached loads), so no
-        // warp waits for another at a block barrier
-        const int lane = threadIdx.x & 31;
-        double m;
-        if constexpr (sizeof(T) == 4) {
-            // FP32 slots: the minimum in FP32 (exact), one conversion and the
-            // Courant product on lane 0 only (FP64 runs at a small fraction
-            // of the FP32 rate), broadcast to the warp
+    T th;
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the slots' minimum in FP32 (exact); the Courant product and
+        // the half step's rounding on lane 0 only (FP64 runs at a small
+        // fraction of the FP32 rate), broadcast to the warp.  dt_fixed >= 0
+        // (checked at init), so its sign test is an integer one.
+        double d0 = 0.0;
+        float t0 = 0.0f;
+        if (__double_as_longlong(P.dt_fixed) > 0) {
+            if (lane == 0) d0 = P.dt_fixed;
+        } else {
             float mf = __uint_as_float(sc->dtmin_f[lane]);
             for (int o = 16; o > 0; o >>= 1) mf = fminf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
-            double d0 = 0.0;
             if (lane == 0) d0 = mf < 1.0e37f ? P.courant * (double)mf : 0.0;
-            m = mf;
-            dt = __shfl_sync(0xffffffffu, d0, 0);
+            if (!(mf < 1.0e37f) && i == 0) atomicOr(&sc->err, ERR_NODT);
+        }
+        if (lane == 0) t0 = (float)(0.5 * d0);
+        dt = __shfl_sync(0xffffffffu, d0, 0);
+        th = __shfl_sync(0xffffffffu, t0, 0);
+    } else {
+        if (P.dt_fixed > 0.0) {
+            dt = P.dt_fixed;
         } else {
-            m = __longlong_as_double((long long)sc->dtmin_d[lane]);
+            double m = __longlong_as_double((long long)sc->dtmin_d[lane]);
             for (int o = 16; o > 0; o >>= 1) {
                 double w = __shfl_xor_sync(0xffffffffu, m, o);
                 m = w < m ? w : m;
             }
             dt = m < 1.0e37 ? P.courant * m : 0.0;
+            if (!(m < 1.0e37) && i == 0) atomicOr(&sc->err, ERR_NODT);
         }
-        if (!(m < 1.0e37)) {
-            if (i == 0) atomicOr(&sc->err, ERR_NODT);
-        }
+        th = 0.5 * dt;
     }
     if (i == 0) sc->dt = dt;
     if (i >= nsrt) return;
-    double hdt = 0.5 * dt;
     V2<T> v = mk2(h0.z, h0.w);
-    T th = (T)hdt;
     // displacement over the half step (absolute velocity = frame + stored)
     T ddx = th * (P.ufx + v.x), ddy = th * (P.ufy + v.y);
     double2 ph;
@@ -975,6 +997,7 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
         // ~6e-8 of a half-step move, is far below the FP32 pair sums')
         ph = make_double2(p.x + (double)ddx, p.y + (double)ddy);
     } else {
+        const double hdt = 0.5 * dt;
         ph = make_double2(p.x + hdt * (P.ufx_d + (double)v.x), p.y + hdt * (P.ufy_d + (double)v.y));
     }
     V2<T> vh = v;
@@ -983,7 +1006,7 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
         vh = mk2(v.x + th * a.x, v.y + th * a.y);
         dh = d + th * dri;
     } else if (typ == T_BUFFER && inf.on) {
-        vh = mk2((T)(inflow_u(inf, sc->t + hdt) - P.ufx_d), (T)(-P.ufy_d));
+        vh = mk2((T)(inflow_u(inf, sc->t + 0.5 * dt) - P.ufx_d), (T)(-P.ufy_d));
     }
     T xo = off_add<T>(P, h0.x, ddx), yo = off_add<T>(P, h0.y, ddy);
     half.pos[i] = ph;
@@ -1173,16 +1196,19 @@ template <class T>
 void launch_pairsum(int lanes, const PhysT<T> &P, const Grid &g, const Scalars *sc,
                     const NList &nl, const uint32_t *key, const Hot<T> &hot, const Csf<T> &csf,
                     const Boundary &bd, const uint8_t *type, V4<T> *accN, T *gsum, uint2 *crange,
-                    int cap, cudaStream_t s) {
+                    int cap, cudaStream_t s, bool dt_term) {
     with_lanes(lanes, [&](auto Gc) {
         constexpr int G = decltype(Gc)::value;
         int b = sweep_blocks(cap, G);
-        if (P.kernel == 1)
-            launch_k(k_pairsum<T, 1, G>, b, SWEEP_BLOCK, s, P, g, sc, nl, key, hot, csf, bd, type,
-                     accN, gsum, crange);
-        else
-            launch_k(k_pairsum<T, 0, G>, b, SWEEP_BLOCK, s, P, g, sc, nl, key, hot, csf, bd, type,
-                     accN, gsum, crange);
+        auto go = [&](auto kern) {
+            launch_k(kern, b, SWEEP_BLOCK, s, P, g, sc, nl, key, hot, csf, bd, type, accN, gsum,
+                     crange);
+        };
+        if (P.kernel == 1) {
+            if (dt_term) go(k_pairsum<T, 1, G, true>); else go(k_pairsum<T, 1, G, false>);
+        } else {
+            if (dt_term) go(k_pairsum<T, 0, G, true>); else go(k_pairsum<T, 0, G, false>);
+        }
     });
 }
 
@@ -1365,8 +1391,7 @@ __device__ __forceinline__ void surrogate_update_one(
         st = make_float2((float)(dT * (uh - (double)P.dfx)), (float)(-dT * (double)P.dfy));
         ds = make_float2(ds.x + st.x, ds.y);
     }
-    if (typ == T_FLUID &&
-        !(p1.x >= g.xmin && p1.x < g.xmax && p1.y >= g.ymin && p1.y < g.ymax)) {
+    if (typ == T_FLUID && !in_box(g, p1)) {
         typ = T_DEAD;
         atomicAdd((unsigned long long *)&sc->deleted, 1ull);
     }
@@ -1570,7 +1595,7 @@ void *decide_kernel() { return (void *)k_decide; }
     template void launch_pairsum<T>(int, const PhysT<T> &, const Grid &, const Scalars *,         \
                                     const NList &, const uint32_t *, const Hot<T> &,              \
                                     const Csf<T> &, const Boundary &, const uint8_t *, V4<T> *,   \
-                                    T *, uint2 *, int, cudaStream_t);                             \
+                                    T *, uint2 *, int, cudaStream_t, bool);                       \
     template void launch_surface<T>(int, int, const PhysT<T> &, const Grid &, const Inflow &,    \
                                     Scalars *, const NList &, const Hot<T> &, const Csf<T> &,     \
                                     const State<T> &, const State<T> &, const V4<T> *, V2<T> *,   \

@@ -128,3 +128,41 @@ def test_stats_match_the_state_and_the_oracle(sph, orc):
     assert abs(E1 - E0) <= 0.02 * abs(E0)
     assert math.isfinite(s["max_rel_density"]) and s["max_rel_density"] < 0.05
     sim.close()
+
+
+def test_state_round_trip_count_query_and_first_bad_particle(sph):
+    """sph_set_state -> sph_get_state returns the state unchanged (FP32
+    velocities and density offsets round-trip exactly through their FP64
+    host form); a call with too small a cap returns SPH_ERR_CAPACITY with the
+    full count; set_state names the first invalid particle.  The jet has more
+    than 2^16 particles, so the host loops run split over threads."""
+    import ctypes
+    case = wl.jet(seed=3, dx=1.0 / 40, length=42.0, Re=200, We=20)
+    a = sph.Simulation(case)
+    a.run(3)
+    st = a.state()
+    n = len(st["x"])
+    assert n > (1 << 16)
+    assert np.all(np.diff(st["id"].astype(np.int64)) > 0)
+    cnt = ctypes.c_longlong()
+    status = sph.lib().sph_get_state(a.ctx, 10, ctypes.byref(cnt), *([None] * 11))
+    assert status == -3 and cnt.value == n
+    b = sph.Simulation(case)
+    b.set_state(st)
+    sb = b.state()
+    for k in ("x", "y", "u", "v", "rho", "m", "id", "type"):
+        assert np.array_equal(st[k], sb[k]), k
+    # the first invalid particle is the one reported, whichever chunk of the
+    # threaded check finds it
+    bad = {k: v.copy() for k, v in st.items()}
+    bad["x"][n - 7] = case["params"]["xmax"] + 1.0
+    bad["type"][40001] = 9
+    with pytest.raises(sph.SphError) as e:
+        b.set_state(bad)
+    assert e.value.status == -1 and "particle 40001:" in str(e.value)
+    bad["type"][40001] = st["type"][40001]
+    with pytest.raises(sph.SphError) as e:
+        b.set_state(bad)
+    assert e.value.status == -1 and ("particle %d lies outside" % (n - 7)) in str(e.value)
+    a.close()
+    b.close()

@@ -329,6 +329,22 @@ __device__ __forceinline__ void for_list(const PhysT<T> &P, const NList &nl,
     }
 }
 
+// (double)f, exactly, for a normal or zero float by moving its bits into the
+// FP64 layout (exponent rebiased by 1023 - 127, mantissa shifted up by 29)
+// on the integer pipes; subnormals, infinities and NaN take the hardware
+// conversion.  FP64 conversions run on the FP64 pipe, which on this GPU has a
+// small fraction of the FP32 rate.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e - 1u < 254u) {
+        const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+        return __hiloint2double((int)hi, (int)(u << 29));
+    }
+    if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)f;
+}
+
 // p lies in the box [xmin, xmax) x [ymin, ymax) (false for NaN), decided on
 // the ordered integer keys of the coordinates.
 __device__ __forceinline__ bool in_box(const Grid &g, double2 p) {

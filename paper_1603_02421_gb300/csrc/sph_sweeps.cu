@@ -620,7 +620,7 @@ __device__ __forceinline__ void forces_finish(const PhysT<T> &P, const Grid &g, 
             // the FP32 step added to the FP64 position (its rounding, ~6e-8
             // of a step's move, is far below the FP32 pair sums'; the cell
             // offsets take the same increment)
-            p1 = make_double2(p0.x + (double)stx, p0.y + (double)sty);
+            p1 = make_double2(p0.x + f2d_exact(stx), p0.y + f2d_exact(sty));
         } else {
             p1 = make_double2(p0.x + dt * (P.ufx_d + (double)usx), p0.y + dt * (P.ufy_d + (double)usy));
         }
@@ -995,7 +995,7 @@ __global__ void k_predict(PhysT<T> P, Inflow inf, Scalars *__restrict__ sc, Stat
     if constexpr (sizeof(T) == 4) {
         // the FP32 increment added to the FP64 position (its rounding,
         // ~6e-8 of a half-step move, is far below the FP32 pair sums')
-        ph = make_double2(p.x + (double)ddx, p.y + (double)ddy);
+        ph = make_double2(p.x + f2d_exact(ddx), p.y + f2d_exact(ddy));
     } else {
         const double hdt = 0.5 * dt;
         ph = make_double2(p.x + hdt * (P.ufx_d + (double)v.x), p.y + hdt * (P.ufy_d + (double)v.y));

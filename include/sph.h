@@ -161,11 +161,15 @@ sph_status sph_breakup_length(sph_ctx *ctx, double D, double *L_over_D, int *bro
 sph_status sph_evaluate(sph_ctx *ctx);
 
 /* Copy out the fluid + buffer state, sorted by id.  cap = length of every
- * output array; *n receives the particle count (SPH_ERR_CAPACITY if > cap).
- * rho is the density; ax, ay, drho the derivatives du/dt (Eq. 25) and
- * drho/dt (Eq. 7) of the last evaluation at the start of a step (or of
- * sph_evaluate), zero for particles laid since.  Any output pointer except n
- * may be NULL. */
+ * output array; *n receives the particle count (SPH_ERR_CAPACITY if > cap;
+ * such a call, e.g. cap = 0 to ask for the count, downloads only the
+ * particle types).  rho is the density; ax, ay, drho the derivatives du/dt
+ * (Eq. 25) and drho/dt (Eq. 7) of the last evaluation at the start of a step
+ * (or of sph_evaluate), zero for particles laid since.  Any output pointer
+ * except n may be NULL.  State transfers (this call, sph_set_state,
+ * sph_add_particles) go through a pinned host buffer of the context, about
+ * 49 (FP32) or 77 (FP64) bytes per particle of capacity, allocated on first
+ * use and freed by sph_destroy. */
 sph_status sph_get_state(sph_ctx *ctx, long long cap, long long *n, double *x, double *y,
                          double *u, double *v, double *rho, double *mass,
                          unsigned char *type, unsigned *id, double *ax, double *ay,

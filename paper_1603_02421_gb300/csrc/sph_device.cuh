@@ -117,6 +117,15 @@ __device__ __forceinline__ float off_diff<float>(const PhysT<float> &P, float a,
     return __int2float_rn((int)d) * P.off_unit;
 }
 
+// FP32 separation from a1 = (own offset bits) - 2^29 and a neighbour's stored
+// offset b, with shift = (cell code of the list entry) << 29, the code being
+// the cell difference + 1: the same exact difference as off_diff.
+__device__ __forceinline__ float off_sep_code(const PhysT<float> &P, unsigned a1, float b,
+                                              unsigned shift) {
+    unsigned d = a1 - (unsigned)__float_as_int(b) + shift;
+    return __int2float_rn((int)d) * P.off_unit;
+}
+
 // A stored offset moved by the displacement `disp` (length units).
 template <class T> __device__ __forceinline__ T off_add(const PhysT<T> &P, T a, T disp) {
     return a + disp;
@@ -293,6 +302,15 @@ __device__ __forceinline__ void for_list(const PhysT<T> &P, const NList &nl,
     double2 pa = make_double2(0.0, 0.0);
     bool have_pa = false;
     uint32_t ent[CH], nxt[CH];
+    // FP32: the own fixed-point offsets less one cell edge, so that an
+    // entry's 2-bit cell code (cell difference + 1), moved to the offset's
+    // cell bit, completes the exact separation in one three-input add
+    static_assert(OFF_BITS == 29, "cell codes are moved to bits 29-30");
+    unsigned xa1 = 0u, ya1 = 0u;
+    if constexpr (sizeof(T) == 4) {
+        xa1 = (unsigned)__float_as_int(xa) - (1u << OFF_BITS);
+        ya1 = (unsigned)__float_as_int(ya) - (1u << OFF_BITS);
+    }
 #pragma unroll
     for (int u = 0; u < CH; ++u) nxt[u] = 0u;
     if (sub * CH < cnt) load_entries<CH>(e + sub * CH, ent);
@@ -314,11 +332,17 @@ __device__ __forceinline__ void for_list(const PhysT<T> &P, const NList &nl,
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
             if (base + u >= cnt || ((skip >> u) & 1u)) continue;
-            T rx = off_diff<T>(P, xa, rec[u].x.x, code_cells((ent[u] >> 28) & 3u));
-            T ry = off_diff<T>(P, ya, rec[u].x.y, code_cells(ent[u] >> 30));
+            T rx, ry;
+            if constexpr (sizeof(T) == 4) {
+                rx = off_sep_code(P, xa1, rec[u].x.x, (ent[u] << 1) & 0x60000000u);
+                ry = off_sep_code(P, ya1, rec[u].x.y, (ent[u] >> 1) & 0x60000000u);
+            } else {
+                rx = off_diff<T>(P, xa, rec[u].x.x, code_cells((ent[u] >> 28) & 3u));
+                ry = off_diff<T>(P, ya, rec[u].x.y, code_cells(ent[u] >> 30));
+            }
             T r2 = rx * rx + ry * ry;
-            if (r2 >= P.H2hi) continue;
-            if (r2 >= P.H2lo) {
+            if (r2 >= P.H2lo) {   // one compare for the pairs well inside 2h
+                if (r2 >= P.H2hi) continue;
                 if (!have_pa) { pa = pos[i]; have_pa = true; }
                 if (!exact_within(pa, pos[bb[u]], P.H2d)) continue;
             }

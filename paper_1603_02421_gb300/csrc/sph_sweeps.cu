@@ -807,6 +807,8 @@ k_pairsum(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, NList nl,
           const uint32_t *__restrict__ key, Hot<T> hot, Csf<T> csf, Boundary bd,
           const uint8_t *__restrict__ type, V4<T> *__restrict__ accN, T *__restrict__ gsum,
           uint2 *__restrict__ crange) {
+    // FP32 Wendland: the kernel's constant factors are taken once per particle
+    constexpr bool WSCALED = K == 1 && sizeof(T) == 4;
     unsigned gt = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned i = gt / G, sub = gt % G;
     bool active = i < (unsigned)sc->nsrt;
@@ -832,13 +834,34 @@ k_pairsum(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, NList nl,
             [&](unsigned, T rx, T ry, T r2, const PairRec<T> &r) {
                 T q, iq, ri;
                 q_of(r2, P.h, P.inv_h, q, iq, ri);
-                T F = kernel_F<T, K>(P, q, iq);
-                csum += r.h1.x * kernel_W<T, K>(P, q);                 // Eq. 14
-                gs += r.h1.x * abs_t(F) * (r2 * ri);
-                if (fluid)
-                    pair_forces<T, DT>(P, rx, ry, r2, ri, F, ua, va, rhoa, PAa, ca, r.x, r.h1,
-                                       ax, ay, drho, vmax);
+                if constexpr (WSCALED) {
+                    // Wendland (Eq. 28) without its constant factors, which
+                    // the sums take once below: W / wn = (1 + 2q) t^4 and
+                    // F / gn = t^3, t = 2 - q
+                    T t = T(2) - q;
+                    t = t > T(0) ? t : T(0);
+                    T t2 = t * t, t3 = t2 * t;
+                    csum += r.h1.x * ((T(1) + T(2) * q) * (t2 * t2));  // Eq. 14
+                    gs += r.h1.x * t3 * (r2 * ri);
+                    if (fluid)
+                        pair_forces<T, DT>(P, rx, ry, r2, ri, t3, ua, va, rhoa, PAa, ca, r.x,
+                                           r.h1, ax, ay, drho, vmax);
+                } else {
+                    T F = kernel_F<T, K>(P, q, iq);
+                    csum += r.h1.x * kernel_W<T, K>(P, q);             // Eq. 14
+                    gs += r.h1.x * abs_t(F) * (r2 * ri);
+                    if (fluid)
+                        pair_forces<T, DT>(P, rx, ry, r2, ri, F, ua, va, rhoa, PAa, ca, r.x,
+                                           r.h1, ax, ay, drho, vmax);
+                }
             });
+        if constexpr (WSCALED) {
+            csum *= P.wn;
+            gs *= -P.gn;          // gn < 0 for the Wendland kernel: |F| = -gn t^3
+            ax *= P.gn;
+            ay *= P.gn;
+            drho *= P.gn;
+        }
         if (fluid && P.walls) {
             double2 pa = hot.pos[i];
             wall_forces<T, G>(P, g, bd, key[i], sub, ha.x, ha.y, ua, va, (T)pa.y, ax, ay);

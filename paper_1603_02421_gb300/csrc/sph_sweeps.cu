@@ -46,7 +46,11 @@ namespace sph {
 #define SPH_SWEEP_MINB 10
 #endif
 #ifndef SPH_PAIRSUM_MINB
-#define SPH_PAIRSUM_MINB 8
+#define SPH_PAIRSUM_MINB 9
+#endif
+// k_surface (mostly streaming: one lane per particle, walks only where N_a = 1)
+#ifndef SPH_SURFACE_MINB
+#define SPH_SURFACE_MINB 10
 #endif
 
 
@@ -901,7 +905,7 @@ k_pairsum(PhysT<T> P, Grid g, const Scalars *__restrict__ sc, NList nl,
 }
 
 template <class T, int K, int MODE, int G>
-__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SWEEP_MINB)
+__global__ void __launch_bounds__(SWEEP_BLOCK, SPH_SURFACE_MINB)
 k_surface(PhysT<T> P, Grid g, Inflow inf, Scalars *__restrict__ sc, NList nl, Hot<T> hot,
           Csf<T> csf, State<T> srt, State<T> raw, const V4<T> *__restrict__ accN,
           V2<T> *__restrict__ acc, T *__restrict__ drout, V4<T> *__restrict__ nH0,

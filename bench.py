@@ -88,6 +88,15 @@ FLOP_PER_PAIR_NO_CSF = {"forces": 45, "forces_correct": 45}
 FLOP_PER_PARTICLE = {"pairsum": 22, "pairsum_correct": 22, "normal": 8, "forces": 20,
                      "forces_correct": 30}
 FLOP_METHOD_PER_PAIR = 87
+FLOP_METHOD_PER_PAIR_NO_CSF = 45
+# Lower bound of the HBM bytes per particle-step of the method (FP32 state):
+# two evaluations each reading the state (28 B) and writing and reading C (8 B)
+# and n (16 B), the predictor's half-step save and reload (56 B), the final
+# state write (28 B): 190 B; plus ~100 B per cell sort (key and index passes,
+# state permutation), taken at the measured fraction of steps that rebuild.
+# Neighbour re-reads are not counted (cache reuse).
+STEP_BYTES_LOWER = 190.0
+STEP_BYTES_PER_SORT = 100.0
 # Algorithmic HBM bytes per particle of the streaming kernel groups (FP32 path).
 BYTES_PER_PARTICLE = {"cell_sort": 16 + 1 + 4 + 4 + 4 + 4 + 4, "reorder": 2 * 41 + 4 + 4 + 32,
                       "predict": 41 + 12 + 48, "spawn": 0}
@@ -134,6 +143,27 @@ def sources_sha256() -> str:
         with open(os.path.join(csrc, name), "rb") as f:
             hsh.update(name.encode() + b"\0" + f.read())
     return hsh.hexdigest()
+
+
+def measured_step_traffic(workload: str):
+    """DRAM bytes per particle of a step that keeps its cell build, summed over
+    the step's launches in an ncu capture summarised under profiles/ (a line
+    'step-traffic: workload=... bytes_per_particle=... sources_sha256=...');
+    None when no capture of this workload exists or the sources changed."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    want = sources_sha256()
+    for name in sorted(os.listdir(pdir)):
+        if not name.endswith(".md"):
+            continue
+        for line in open(os.path.join(pdir, name)):
+            if not line.startswith("step-traffic:"):
+                continue
+            kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+            if kv.get("workload") == workload and kv.get("sources_sha256") == want:
+                return float(kv["bytes_per_particle"])
+    return None
 
 
 def measured_traffic(group: str, particles: float):
@@ -560,6 +590,39 @@ def bench_plain(args, binding, dist, dev, rank, world, local, case, desc):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                 "algorithmic_per_launch": nbytes}
 
+    # ---- the whole step against both rooflines ----------------------------
+    # at the steady-state rate: the method's FLOPs (each equation with its own
+    # geometry, pairs r < 2h, two evaluations per step), the lower-bound bytes
+    # and the DRAM bytes ncu measured for a step that keeps its build
+    fp64 = case["params"].get("prec") == "fp64"
+    mp_hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    s_rebuild = s_full / Ks
+    step_flop = 2.0 * pairs_per_particle * (FLOP_METHOD_PER_PAIR if csf
+                                            else FLOP_METHOD_PER_PAIR_NO_CSF)
+    step_lower = STEP_BYTES_LOWER + STEP_BYTES_PER_SORT * s_rebuild
+    step_meas = measured_step_traffic(args.workload)
+    arith_peak = peaks["fp64_tflops" if fp64 else "fp32_tflops"]
+    step_roof = {
+        "rate": steady_value,
+        "flop_per_particle_step": step_flop,
+        "arith_tflops": step_flop * steady_value / 1e12,
+        "arith_peak_tflops": arith_peak,
+        "arith_frac": step_flop * steady_value / 1e12 / arith_peak,
+        "bytes_lower_bound_per_particle_step": step_lower,
+        "hbm_frac_lower_bound": step_lower * steady_value / 1e9 / mp_hbm,
+        "dram_bytes_measured_per_particle_step": step_meas,
+        "hbm_frac_measured": (step_meas * steady_value / 1e9 / mp_hbm
+                              if step_meas is not None else None),
+        "hbm_peak_gbs": mp_hbm,
+        "how": "steady-state particle-steps/s times the method's FLOPs (%d per pair r < 2h, "
+               "two evaluations) over the measured %s FMA peak, and times bytes per "
+               "particle-step over MEASURED_PEAKS hbm_gbs: the lower bound 190 + 100 x "
+               "(fraction of steps that rebuild), and the DRAM traffic ncu measured for a "
+               "step that keeps its build (profiles/, null when the kernels changed since)"
+               % (FLOP_METHOD_PER_PAIR if csf else FLOP_METHOD_PER_PAIR_NO_CSF,
+                  "FP64" if fp64 else "FP32"),
+    }
+
     # ---- end to end through the public API with host buffers -------------
     e2e = None
     if rank == 0:
@@ -597,6 +660,7 @@ def bench_plain(args, binding, dist, dev, rank, world, local, case, desc):
                          "how": "a second window of max(K, 64 x cadence, 1000) steps from a "
                                 "forced rebuild"},
         "roofline": roof,
+        "step_roofline": step_roof,
         "measured_peaks": peaks,
         "cpu_baseline": cpu,
         "e2e": e2e,

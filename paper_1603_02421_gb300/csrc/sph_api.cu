@@ -1186,14 +1186,35 @@ static void order_by_id(std::vector<size_t> &ord, const unsigned *ids) {
     unsigned max_id = 0;
     for (size_t i : ord) max_id = std::max(max_id, ids[i]);
     if (!ord.empty() && (size_t)max_id < 8 * ord.size() + 1024) {
-        std::vector<int64_t> slot((size_t)max_id + 1, -1);
+        const size_t ns = (size_t)max_id + 1, n = ord.size();
+        std::vector<int64_t> slot(ns);
+        const size_t par = n >= ((size_t)1 << 16) ? 1 : 64;   // grain: threads only when large
+        host_for(ns, [&](size_t lo, size_t hi) {
+            std::fill(slot.begin() + lo, slot.begin() + hi, (int64_t)-1);
+        });
         // distinct ids: the threads write distinct slots
-        host_for(ord.size(), [&](size_t lo, size_t hi) {
+        host_for(n, [&](size_t lo, size_t hi) {
             for (size_t r = lo; r < hi; ++r) slot[ids[ord[r]]] = (int64_t)ord[r];
         });
-        ord.clear();
-        for (int64_t q : slot)
-            if (q >= 0) ord.push_back((size_t)q);
+        // compaction in id order: count per chunk of slots, then each chunk
+        // writes from its prefix
+        const size_t nchunk = 64;
+        std::vector<size_t> cnt(nchunk + 1, 0);
+        host_for(nchunk, [&](size_t k0, size_t k1) {
+            for (size_t k = k0; k < k1; ++k) {
+                size_t c = 0;
+                for (size_t q = ns * k / nchunk; q < ns * (k + 1) / nchunk; ++q) c += slot[q] >= 0;
+                cnt[k + 1] = c;
+            }
+        }, par);
+        for (size_t k = 0; k < nchunk; ++k) cnt[k + 1] += cnt[k];
+        host_for(nchunk, [&](size_t k0, size_t k1) {
+            for (size_t k = k0; k < k1; ++k) {
+                size_t w = cnt[k];
+                for (size_t q = ns * k / nchunk; q < ns * (k + 1) / nchunk; ++q)
+                    if (slot[q] >= 0) ord[w++] = (size_t)slot[q];
+            }
+        }, par);
     } else {
         std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return ids[a] < ids[b]; });
     }
@@ -1311,13 +1332,21 @@ sph_status sph_set_state(sph_ctx *c, long long n, const double *x, const double 
         }, N >= ((size_t)1 << 16) ? 1 : nchunk);
         unsigned maxid = 0;
         for (unsigned m : cmax) maxid = std::max(maxid, m);
-        // duplicate ids: a mark per id when they are dense, else a sort
+        // duplicate ids: a mark per id when they are dense (set in a few
+        // threads with atomic exchanges; every repeated id is met by the
+        // second of its marks, and the smallest one is reported), else a sort
         if (n > 0 && (size_t)maxid < 8 * (size_t)n + 1024) {
             std::vector<unsigned char> seen((size_t)maxid + 1, 0);
-            for (long long i = 0; i < n; ++i) {
-                if (seen[id[i]]) return fail(c, SPH_ERR_ARG, "duplicate id %u", id[i]);
-                seen[id[i]] = 1;
-            }
+            std::vector<unsigned> cdup(nchunk, 0xFFFFFFFFu);
+            host_for(nchunk, [&](size_t k0, size_t k1) {
+                for (size_t k = k0; k < k1; ++k)
+                    for (size_t i = N * k / nchunk; i < N * (k + 1) / nchunk; ++i)
+                        if (__atomic_exchange_n(&seen[id[i]], (unsigned char)1, __ATOMIC_RELAXED))
+                            cdup[k] = std::min(cdup[k], id[i]);
+            }, N >= ((size_t)1 << 16) ? 1 : nchunk);
+            unsigned dup = 0xFFFFFFFFu;
+            for (unsigned d : cdup) dup = std::min(dup, d);
+            if (dup != 0xFFFFFFFFu) return fail(c, SPH_ERR_ARG, "duplicate id %u", dup);
         } else if (n > 0) {
             std::vector<unsigned> sid(id, id + n);
             std::sort(sid.begin(), sid.end());

@@ -164,5 +164,17 @@ def test_state_round_trip_count_query_and_first_bad_particle(sph):
     with pytest.raises(sph.SphError) as e:
         b.set_state(bad)
     assert e.value.status == -1 and ("particle %d lies outside" % (n - 7)) in str(e.value)
+    # repeated ids, found by the threaded marking: the smallest one is named
+    dup = {k: v.copy() for k, v in st.items()}
+    ids = dup["id"]
+    dup["id"][n - 3] = ids[50000]
+    dup["id"][9] = ids[20000]
+    with pytest.raises(sph.SphError) as e:
+        b.set_state(dup)
+    assert e.value.status == -1
+    assert ("duplicate id %d" % min(ids[50000], ids[20000])) in str(e.value)
+    # the context still holds the state set before the failed calls
+    sb = b.state()
+    assert np.array_equal(sb["id"], st["id"]) and np.array_equal(sb["x"], st["x"])
     a.close()
     b.close()

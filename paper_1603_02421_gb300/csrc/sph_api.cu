@@ -587,7 +587,6 @@ static sph_status upload_boundary(sph_ctx *c) {
     return SPH_OK;
 }
 
-// Upload n particles into raw[at, at+n).
 // Runs f(lo, hi) over [0, n) in up to 8 host threads of at least `grain`
 // items each (a million-particle state crosses the ABI in milliseconds); f
 // must not throw.
@@ -644,8 +643,10 @@ static unsigned char *staging(sph_ctx *c, size_t bytes, cudaError_t &e) {
     return c->pin;
 }
 
-// Converts n host particles into the device layout in the pinned staging,
-// then one asynchronous copy per array and one wait for all of them.
+// Upload n particles into raw[at, at+n): converted into the device layout in
+// the pinned staging, then one asynchronous copy per array and one wait for
+// all of them (also when one fails, so that no copy from the staging is in
+// flight when the call returns).
 static sph_status upload_particles(sph_ctx *c, long long at, long long n, const double *x,
                                    const double *y, const double *u, const double *v,
                                    const double *rho, const double *mass,
@@ -685,15 +686,17 @@ static sph_status upload_particles(sph_ctx *c, long long at, long long n, const 
         memcpy(pin + o_id + 4 * lo, id + lo, 4 * (hi - lo));
     });
     const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync((double2 *)c->raw[0] + at, pin + o_pos, 16 * N, h2d, c->stream), "upload");
-    CK(cudaMemcpyAsync((char *)c->raw[1] + 2 * at * ts, pin + o_vel, 2 * N * ts, h2d, c->stream), "upload");
-    CK(cudaMemcpyAsync((char *)c->raw[2] + at * ts, pin + o_dr, N * ts, h2d, c->stream), "upload");
-    CK(cudaMemsetAsync((char *)c->raw[3] + at * ts, 0, N * ts, c->stream), "upload");
-    CK(cudaMemsetAsync((char *)c->raw[7] + 2 * at * ts, 0, 2 * N * ts, c->stream), "upload");
-    CK(cudaMemcpyAsync((char *)c->raw[4] + at * ts, pin + o_m, N * ts, h2d, c->stream), "upload");
-    CK(cudaMemcpyAsync((uint8_t *)c->raw[5] + at, pin + o_ty, N, h2d, c->stream), "upload");
-    CK(cudaMemcpyAsync((uint32_t *)c->raw[6] + at, pin + o_id, 4 * N, h2d, c->stream), "upload");
-    CK(cudaStreamSynchronize(c->stream), "upload");
+    cudaStream_t st = c->stream;
+    cudaError_t err = cudaMemcpyAsync((double2 *)c->raw[0] + at, pin + o_pos, 16 * N, h2d, st);
+    if (!err) err = cudaMemcpyAsync((char *)c->raw[1] + 2 * at * ts, pin + o_vel, 2 * N * ts, h2d, st);
+    if (!err) err = cudaMemcpyAsync((char *)c->raw[2] + at * ts, pin + o_dr, N * ts, h2d, st);
+    if (!err) err = cudaMemsetAsync((char *)c->raw[3] + at * ts, 0, N * ts, st);
+    if (!err) err = cudaMemsetAsync((char *)c->raw[7] + 2 * at * ts, 0, 2 * N * ts, st);
+    if (!err) err = cudaMemcpyAsync((char *)c->raw[4] + at * ts, pin + o_m, N * ts, h2d, st);
+    if (!err) err = cudaMemcpyAsync((uint8_t *)c->raw[5] + at, pin + o_ty, N, h2d, st);
+    if (!err) err = cudaMemcpyAsync((uint32_t *)c->raw[6] + at, pin + o_id, 4 * N, h2d, st);
+    cudaError_t es = cudaStreamSynchronize(st);
+    CK(err ? err : es, "upload");
     return SPH_OK;
 }
 
@@ -1251,15 +1254,19 @@ sph_status sph_get_state(sph_ctx *c, long long cap, long long *n_out, double *x,
         *n_out = (long long)ord.size();
         if ((long long)ord.size() > cap) return fail(c, SPH_ERR_CAPACITY, "%zu particles > cap %lld", ord.size(), cap);
         if (ord.empty()) return SPH_OK;
+        // one asynchronous copy per array and one wait for all of them (also
+        // when one fails: no copy into the staging outlives the call)
         const cudaMemcpyKind d2h = cudaMemcpyDeviceToHost;
-        CK(cudaMemcpyAsync(pin + o_pos, c->raw[0], 16 * n, d2h, c->stream), "download");
-        CK(cudaMemcpyAsync(pin + o_vel, c->raw[1], 2 * n * ts, d2h, c->stream), "download");
-        CK(cudaMemcpyAsync(pin + o_dr, c->raw[2], n * ts, d2h, c->stream), "download");
-        CK(cudaMemcpyAsync(pin + o_m, c->raw[4], n * ts, d2h, c->stream), "download");
-        CK(cudaMemcpyAsync(pin + o_id, c->raw[6], 4 * n, d2h, c->stream), "download");
-        CK(cudaMemcpyAsync(pin + o_ac, c->acc, 2 * n * ts, d2h, c->stream), "download");
-        CK(cudaMemcpyAsync(pin + o_drt, c->dr, n * ts, d2h, c->stream), "download");
-        CK(cudaStreamSynchronize(c->stream), "download");
+        cudaStream_t st = c->stream;
+        cudaError_t err = cudaMemcpyAsync(pin + o_pos, c->raw[0], 16 * n, d2h, st);
+        if (!err) err = cudaMemcpyAsync(pin + o_vel, c->raw[1], 2 * n * ts, d2h, st);
+        if (!err) err = cudaMemcpyAsync(pin + o_dr, c->raw[2], n * ts, d2h, st);
+        if (!err) err = cudaMemcpyAsync(pin + o_m, c->raw[4], n * ts, d2h, st);
+        if (!err) err = cudaMemcpyAsync(pin + o_id, c->raw[6], 4 * n, d2h, st);
+        if (!err) err = cudaMemcpyAsync(pin + o_ac, c->acc, 2 * n * ts, d2h, st);
+        if (!err) err = cudaMemcpyAsync(pin + o_drt, c->dr, n * ts, d2h, st);
+        cudaError_t es = cudaStreamSynchronize(st);
+        CK(err ? err : es, "download");
         const double2 *pos = (const double2 *)(pin + o_pos);
         const unsigned *ids = (const unsigned *)(pin + o_id);
         order_by_id(ord, ids);

@@ -577,6 +577,43 @@ def test_wall_force_constant_along_a_straight_wall(orc):
     assert np.mean(ays) == pytest.approx(d.wall_A * (1 - q) / np.sqrt(q), rel=1e-12)
 
 
+
+def test_wall_force_repels_and_grows_with_depth_and_approach_speed(orc):
+    # Sec. 2-6, Eq. 29: R(psi) repels along the wall normal and depends on the
+    # normal distance psi alone; the factor eps(z, u_perp) raises the force
+    # with the local depth of the fluid and with the speed at which the
+    # particle approaches the wall.  A vertical wall x = 0 with normal +x and
+    # one particle: the force along +x only, decreasing in psi and zero from
+    # psi = 2h on; at fixed psi larger for a deeper particle (the surface
+    # height h0 is wall_h0) and for one moving towards the wall, unchanged for
+    # one moving away.
+    dx = 0.02
+    p = wl.test_params(dx=dx, alpha=0.0, c0=10.0, box=(-1, -1, 2, 2))
+    p["wall_h0"] = 0.5
+    d = orc.derive(p)
+    db = d.wall_db
+    by = np.arange(-60, 61) * db
+    bd = {"x": np.zeros(len(by)), "y": by, "nx": np.ones(len(by)), "ny": np.zeros(len(by))}
+
+    def force(psi, y, u=0.0):
+        st = wl._fluid([psi], [y], u=[u], dx=dx)
+        ev = orc.evaluate(d, st, bd)
+        assert abs(ev["ay"][0]) <= 1e-9 * max(abs(ev["ax"][0]), 1e-300)
+        return ev["ax"][0]
+
+    h = d.h
+    fs = [force(psi, 0.2) for psi in (0.2 * h, 0.5 * h, 1.0 * h, 1.5 * h, 1.9 * h)]
+    assert all(f > 0 for f in fs) and all(a > b for a, b in zip(fs, fs[1:]))
+    assert force(2.0 * h, 0.2) == 0.0 and force(2.3 * h, 0.2) == 0.0
+    psi = 0.6 * h
+    depth = [force(psi, y) for y in (0.55, 0.45, 0.3, 0.1, -0.1)]   # surface at y = 0.5
+    assert all(a < b for a, b in zip(depth[:-1], depth[1:]))
+    assert depth[0] > 0
+    rest = force(psi, 0.2)
+    assert force(psi, 0.2, u=-0.05) > rest          # approaching the wall
+    assert force(psi, 0.2, u=-0.2) > force(psi, 0.2, u=-0.05)
+    assert force(psi, 0.2, u=+0.2) == rest          # moving away
+
 # ---------------------------------------------------------------------------
 # summation density (Eq. 6), the alternative to integrating Eq. 7
 # ---------------------------------------------------------------------------

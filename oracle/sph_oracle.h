@@ -15,9 +15,12 @@
  * Parity is pinned for every function by the tests under tests/ (closed
  * forms, invariants, brute force).  The repulsive wall force (Sec. 2-6,
  * Eq. 29) prints only the product structure of the force; its factor
- * functions follow the literature reading documented in the design notes,
- * and that part is "parity unpinned" against the paper beyond its partition
- * of unity along a straight wall.
+ * functions follow a literature reading, and their magnitudes are "parity
+ * unpinned" against the paper; pinned are only the properties the paper
+ * states: the force acts along the wall normal, stays constant along a
+ * straight wall, repels with a strength that decreases with the normal
+ * distance (zero from 2h on), and grows with the local depth of the fluid and
+ * with the speed at which a particle approaches the wall.
  */
 #ifndef SPH_ORACLE_H
 #define SPH_ORACLE_H

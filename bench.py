@@ -849,7 +849,17 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local, steps=None, emi
     flop_ps = 2 * (pairs_pp * FLOP_METHOD_PER_PAIR + 2 + FLOP_PER_PARTICLE["normal"] +
                    FLOP_PER_PARTICLE["forces_correct"])
     sm_mhz = clk["sm_mhz"] if clk else 1900.0
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    peaks = None
+    if emit:
+        # the ensemble's own line: the FP32 FMA peak measured on this GPU
+        peaks = measured_peaks(binding, local)
+        peak = peaks["fp32_tflops"]
+        peak_source = ("measured on this GPU by the library's FMA probe (sph_fma_peak, FP32, "
+                       "median SM clock %s MHz during the probe)"
+                       % (peaks["clocks"]["sm_mhz"] if peaks["clocks"] else "n/a"))
+    else:
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        peak_source = "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz
     achieved = flop_ps * value / world / 1e12
     cpu_line = None
     if cpu and rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -881,9 +891,10 @@ def bench_ensemble(args, binding, dist, dev, rank, world, local, steps=None, emi
             "roofline": {"kernel": "whole ensemble step (all kernels)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz,
+                         "peak_source": peak_source,
                          "algorithmic_per_particle_step": flop_ps,
                          "pairs_per_particle": pairs_pp},
+            "measured_peaks": peaks,
             "cpu_baseline": cpu_line,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / Ke,
                     "d2h_bytes_per_step": d2h / Ke,

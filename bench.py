@@ -145,6 +145,21 @@ def sources_sha256() -> str:
     return hsh.hexdigest()
 
 
+# Fallback roofline denominators when MEASURED_PEAKS.json (measured on this
+# pool's GPUs) is absent: one earlier measurement on a GB300.
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def pool_peak(key: str):
+    """(value, "of measured" | "of fallback") of a MEASURED_PEAKS.json entry."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)[key]), "of measured"
+    except (OSError, ValueError, KeyError, TypeError):
+        return FALLBACK_PEAKS[key], "of fallback"
+
+
 def measured_step_traffic(workload: str):
     """DRAM bytes per particle of a step that keeps its cell build, summed over
     the step's launches in an ncu capture summarised under profiles/ (a line
@@ -581,13 +596,13 @@ def bench_plain(args, binding, dist, dev, rank, world, local, case, desc):
                                   peaks["clocks"]["sm_mhz"] if peaks["clocks"] else "n/a"),
                 "algorithmic_per_launch": flops}
     else:
-        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm, hbm_src = pool_peak("hbm_gbs")
         nbytes = n_mean * BYTES_PER_PARTICLE.get(dom, 0)
         achieved = nbytes / avg_s / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": mp["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / mp["hbm_gbs"],
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": measured_traffic(dom, n_mean),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % hbm_src,
                 "algorithmic_per_launch": nbytes}
 
     # ---- the whole step against both rooflines ----------------------------
@@ -595,7 +610,7 @@ def bench_plain(args, binding, dist, dev, rank, world, local, case, desc):
     # geometry, pairs r < 2h, two evaluations per step), the lower-bound bytes
     # and the DRAM bytes ncu measured for a step that keeps its build
     fp64 = case["params"].get("prec") == "fp64"
-    mp_hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    mp_hbm, hbm_src = pool_peak("hbm_gbs")
     s_rebuild = s_full / Ks
     step_flop = 2.0 * pairs_per_particle * (FLOP_METHOD_PER_PAIR if csf
                                             else FLOP_METHOD_PER_PAIR_NO_CSF)
@@ -614,6 +629,7 @@ def bench_plain(args, binding, dist, dev, rank, world, local, case, desc):
         "hbm_frac_measured": (step_meas * steady_value / 1e9 / mp_hbm
                               if step_meas is not None else None),
         "hbm_peak_gbs": mp_hbm,
+        "hbm_peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % hbm_src,
         "how": "steady-state particle-steps/s times the method's FLOPs (%d per pair r < 2h, "
                "two evaluations) over the measured %s FMA peak, and times bytes per "
                "particle-step over MEASURED_PEAKS hbm_gbs: the lower bound 190 + 100 x "
@@ -1109,7 +1125,7 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
 
     # network GEMM work per surrogate step on the tensor cores (BF16)
     tensor_flop = 2.0 * 3 * (128 * 32 + 256 * 128) * n0 * (K // SUR_K)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    bf16, bf16_src = pool_peak("bf16_tflops")
     achieved = tensor_flop / sur_s / 1e12
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1157,10 +1173,10 @@ def bench_surrogate(args, binding, dist, dev, rank, world, local):
                                                  "surrogate": float(np.mean(L_sur))},
                        "l2": "inputs larger than L2 (all members resident)"},
             "roofline": {"kernel": "BF16 tensor-core GEMMs of the network (whole surrogate-arm time)",
-                         "bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"],
-                         "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"],
+                         "bound": "tensor", "achieved": achieved, "peak": bf16,
+                         "unit": "TFLOP/s", "frac": achieved / bf16,
                          "traffic": None,
-                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (of measured)"},
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (%s)" % bf16_src},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / (Ke * SUR_K),
                     "d2h_bytes_per_step": d2h / (Ke * SUR_K),

@@ -46,3 +46,14 @@ def test_gpu_arm_fails_without_a_gpu():
     r = _run("--steps", "2", "--warmup", "3")
     assert r.returncode != 0
     assert not r.stdout.strip(), "no bench line without a GPU"
+
+
+def test_pool_peaks_fall_back_when_the_measured_file_is_absent(monkeypatch, tmp_path):
+    # the roofline denominators come from MEASURED_PEAKS.json when present
+    # ("of measured"), else from the documented fallback ("of fallback")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.pool_peak("hbm_gbs") == (6800.0, "of fallback")
+    assert bench.pool_peak("bf16_tflops") == (1900.0, "of fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6805.1}))
+    assert bench.pool_peak("hbm_gbs") == (6805.1, "of measured")
+    assert bench.pool_peak("bf16_tflops") == (1900.0, "of fallback")

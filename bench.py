@@ -89,14 +89,21 @@ FLOP_PER_PARTICLE = {"pairsum": 22, "pairsum_correct": 22, "normal": 8, "forces"
                      "forces_correct": 30}
 FLOP_METHOD_PER_PAIR = 87
 FLOP_METHOD_PER_PAIR_NO_CSF = 45
-# Lower bound of the HBM bytes per particle-step of the method (FP32 state):
-# two evaluations each reading the state (28 B) and writing and reading C (8 B)
-# and n (16 B), the predictor's half-step save and reload (56 B), the final
-# state write (28 B): 190 B; plus ~100 B per cell sort (key and index passes,
-# state permutation), taken at the measured fraction of steps that rebuild.
-# Neighbour re-reads are not counted (cache reuse).
-STEP_BYTES_LOWER = 190.0
 STEP_BYTES_PER_SORT = 100.0
+
+
+def step_bytes_lower(fp64: bool, csf: bool, rebuild_fraction: float) -> float:
+    """Lower bound of the HBM bytes per particle-step of the method: two
+    evaluations, each reading the state S (position 16 B, velocity and
+    density: 28 B in FP32, 40 B in FP64) and, with surface tension, writing
+    and reading the colour and the normal (24 B in FP32, 48 B in FP64); the
+    predictor's half-step save and reload (2 S); the final state write (S);
+    ~100 B per cell sort (key and index passes, state permutation) at the
+    fraction of steps that rebuild.  Neighbour re-reads are not counted (cache
+    reuse).  FP32 with surface tension: 188 B + 100 B per sort."""
+    S = 40.0 if fp64 else 28.0
+    c = (48.0 if fp64 else 24.0) if csf else 0.0
+    return 2.0 * (S + c) + 2.0 * S + S + STEP_BYTES_PER_SORT * rebuild_fraction
 # Algorithmic HBM bytes per particle of the streaming kernel groups (FP32 path).
 BYTES_PER_PARTICLE = {"cell_sort": 16 + 1 + 4 + 4 + 4 + 4 + 4, "reorder": 2 * 41 + 4 + 4 + 32,
                       "predict": 41 + 12 + 48, "spawn": 0}
@@ -614,7 +621,7 @@ def bench_plain(args, binding, dist, dev, rank, world, local, case, desc):
     s_rebuild = s_full / Ks
     step_flop = 2.0 * pairs_per_particle * (FLOP_METHOD_PER_PAIR if csf
                                             else FLOP_METHOD_PER_PAIR_NO_CSF)
-    step_lower = STEP_BYTES_LOWER + STEP_BYTES_PER_SORT * s_rebuild
+    step_lower = step_bytes_lower(fp64, csf, s_rebuild)
     step_meas = measured_step_traffic(args.workload)
     arith_peak = peaks["fp64_tflops" if fp64 else "fp32_tflops"]
     step_roof = {
@@ -632,8 +639,9 @@ def bench_plain(args, binding, dist, dev, rank, world, local, case, desc):
         "hbm_peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % hbm_src,
         "how": "steady-state particle-steps/s times the method's FLOPs (%d per pair r < 2h, "
                "two evaluations) over the measured %s FMA peak, and times bytes per "
-               "particle-step over MEASURED_PEAKS hbm_gbs: the lower bound 190 + 100 x "
-               "(fraction of steps that rebuild), and the DRAM traffic ncu measured for a "
+               "particle-step over MEASURED_PEAKS hbm_gbs: the method's lower bound (188 B "
+               "in FP32 with surface tension, + 100 B x the fraction of steps that rebuild), "
+               "and the DRAM traffic ncu measured for a "
                "step that keeps its build (profiles/, null when the kernels changed since)"
                % (FLOP_METHOD_PER_PAIR if csf else FLOP_METHOD_PER_PAIR_NO_CSF,
                   "FP64" if fp64 else "FP32"),

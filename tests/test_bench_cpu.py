@@ -11,6 +11,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 import bench
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -57,3 +59,12 @@ def test_pool_peaks_fall_back_when_the_measured_file_is_absent(monkeypatch, tmp_
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6805.1}))
     assert bench.pool_peak("hbm_gbs") == (6805.1, "of measured")
     assert bench.pool_peak("bf16_tflops") == (1900.0, "of fallback")
+
+
+def test_step_bytes_lower_bound_itemised():
+    # FP32 with surface tension: 2 x (28 + 8 + 16) + 56 + 28 = 188 B, the
+    # method's ~190 B per particle-step, plus 100 B per cell sort
+    assert bench.step_bytes_lower(False, True, 0.0) == 188.0
+    assert bench.step_bytes_lower(False, True, 0.13) == pytest.approx(201.0)
+    assert bench.step_bytes_lower(False, False, 0.0) == 2 * 28 + 56 + 28
+    assert bench.step_bytes_lower(True, False, 0.0) == 2 * 40 + 80 + 40
